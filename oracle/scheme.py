@@ -1,0 +1,128 @@
+"""Algorithm 1 (fixed-point algorithm on patterns) for the oracle.
+
+Test infrastructure only (see ``oracle/__init__``).  float64 throughout.
+
+Sec. 3.2, Algorithm 1 (collocation of the Lippmann-Schwinger equation at the
+pattern points 2 pi y, y in P(M)):
+    eps^(0)_y <- E for all y
+    repeat
+        tau_y      <- (C_y - C0) : eps^(n)_y                 (polarization)
+        tau_hat    <- F(M) tau                                (forward, with 1/m)
+        epshat_h   <- -Gamma0(h) : tau_hat_h,  h in G(M^T) \\ {0}
+        epshat_0   <- E
+        eps^(n+1)  <- F(M)^{-1} epshat                        (inverse, no 1/m)
+    until converged
+with the Cauchy criterion of Sec. 5.2,
+    r_n = ||eps^(n+1) - eps^(n)|| / ||eps^(0)|| < tol,
+the norm being the l2 norm over the pattern of the Frobenius norm.
+Outputs also the stress sigma_y = C_y : eps_y and its mean, which is
+C^eff : E (Sec. 3.1, definition of the effective matrix).
+
+Readings where the paper is silent (each listed in the design notes):
+  * Gamma0 is evaluated at the integer frequency h in G(M^T) itself: the
+    Fourier multiplier of the symmetric gradient at coefficient index h.
+  * The strain is real (Sec. 3.2 seeks real symmetric eps_y).  At boundary
+    frequencies of the symmetric cell (even divisors) h(k) and h(-k) are not
+    negatives of each other, so F^{-1} of the literal spectrum is complex;
+    the iterate is its real part.  ``boundary='zero'`` instead sets those
+    frequencies to zero (the usual Nyquist convention), as an option.
+  * ||eps^(0)|| is sqrt(m) ||E||_F also for a warm start (1 if E = 0), so cold
+    and warm runs share one threshold.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import elasticity as el
+from .lattice import Lattice
+from .transform import dft_fast, dft_naive
+
+
+def _transform(lat, a, inverse, mode):
+    if mode == 'naive' or (mode == 'auto' and lat.m <= 1024):
+        return dft_naive(lat, a, inverse)
+    return dft_fast(lat, a, inverse)
+
+
+def boundary_mask(lat):
+    """True at k where h(-k) != -h(k) (frequencies on the boundary of the symmetric cell)."""
+    m = lat.m
+    e = np.array(lat.e, dtype=np.int64)
+    neg = (-lat.lam) % e
+    flat = np.zeros(m, dtype=np.int64)
+    for j in range(lat.d):
+        flat = flat * e[j] + neg[:, j]
+    return np.any(lat.h[flat] != -lat.h, axis=1)
+
+
+def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
+                 transform='auto', boundary='literal'):
+    """Run Algorithm 1.
+
+    M        integer matrix (d x d) or an ``oracle.lattice.Lattice``
+    phase    (m,) int phase index per pattern point, in lattice (lambda) order
+    stiff    (n_phases, d, d, d, d) stiffness tensors C_p
+    C0       (lam0, mu0) isotropic reference medium
+    E        (d, d) macroscopic strain (tensor components)
+    tol      Cauchy threshold; maxit caps the iteration count
+    eps0     optional (m, d, d) warm start
+    Returns dict(eps, sigma, sigma_bar, iters, history).
+    """
+    lat = M if isinstance(M, Lattice) else Lattice(M)
+    d, m = lat.d, lat.m
+    phase = np.asarray(phase, dtype=np.int64)
+    stiff = np.asarray(stiff, dtype=np.float64)
+    lam0, mu0 = C0
+    E = np.asarray(E, dtype=np.float64)
+    C0t = el.iso_tensor(lam0, mu0, d)
+    dC = stiff - C0t                                   # (C_p - C0)
+    h = lat.h.astype(np.float64)
+    nz = np.any(lat.h != 0, axis=1)
+    assert nz.sum() == m - 1 and not nz[0], "h = 0 must be exactly k = 0"
+    bmask = boundary_mask(lat) if boundary == 'zero' else None
+
+    eps = np.broadcast_to(E, (m, d, d)).copy() if eps0 is None else np.array(eps0, dtype=np.float64)
+    nE = np.sqrt(el.frob2(E))
+    norm0 = np.sqrt(m) * nE if nE > 0 else 1.0
+    history = []
+    it = 0
+    while it < maxit:
+        tau = el.ddot(dC[phase], eps)                                  # polarization
+        tau_hat = _transform(lat, tau, False, transform)               # F(M) tau
+        eps_hat = np.zeros_like(tau_hat)
+        eps_hat[nz] = -el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
+        if bmask is not None:
+            eps_hat[bmask] = 0.0
+        eps_hat[~nz] = E                                               # mean strain
+        eps_new = _transform(lat, eps_hat, True, transform).real       # F(M)^{-1}
+        r = np.sqrt(el.frob2(eps_new - eps).sum()) / norm0
+        eps = eps_new
+        it += 1
+        history.append(float(r))
+        if r < tol:
+            break
+    sigma = el.ddot(stiff[phase], eps)
+    return dict(eps=eps, sigma=sigma, sigma_bar=sigma.mean(axis=0), iters=it, history=history)
+
+
+def unit_load(d, a):
+    """Unit load case a in Voigt order: eps_11 = 1, ..., or eps_ij = eps_ji = 1/2 for shear."""
+    (i, j) = el.voigt_pairs(d)[a]
+    E = np.zeros((d, d))
+    if i == j:
+        E[i, i] = 1.0
+    else:
+        E[i, j] = E[j, i] = 0.5
+    return E
+
+
+def effective_voigt(M, phase, stiff, C0, tol=1e-8, maxit=1000, **kw):
+    """C^eff in Voigt form (engineering shear): column a = sigma_bar of unit load case a."""
+    lat = M if isinstance(M, Lattice) else Lattice(M)
+    d = lat.d
+    n_c = len(el.voigt_pairs(d))
+    Ceff = np.zeros((n_c, n_c))
+    for a in range(n_c):
+        res = basic_scheme(lat, phase, stiff, C0, unit_load(d, a), tol, maxit, **kw)
+        Ceff[:, a] = el.sym_to_comps(res['sigma_bar'])
+    return Ceff

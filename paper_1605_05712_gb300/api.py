@@ -1,0 +1,205 @@
+"""Python binding of liblatms (ctypes): argument marshalling only.
+
+Every step of the lattice Basic Scheme runs in the CUDA library; this module
+allocates device buffers with torch (plumbing), passes raw pointers and the
+current CUDA stream through the C ABI of ``include/lattice_ms.h`` and turns
+status codes into exceptions.  There is no CPU fallback: if the shared
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB
+
+LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
+LAT_FP64, LAT_MIXED = 0, 1
+LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
+HIST_CAP = 16384
+
+_lib = None
+
+
+class LatticeError(RuntimeError):
+    """A negative status returned by liblatms."""
+
+    def __init__(self, code, msg):
+        super().__init__("liblatms error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("resid_history", ctypes.POINTER(ctypes.c_double))]
+
+
+def lib():
+    """Load liblatms.so (built in-tree by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError("liblatms.so is not built (%s); run __graft_entry__.build()" % LIB)
+    L = ctypes.CDLL(LIB)
+    vp, i64p, i32p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_double)
+    L.lattice_plan.argtypes = [i64p, ctypes.c_int, ctypes.POINTER(vp)]
+    L.lattice_plan.restype = ctypes.c_int
+    L.lattice_plan_destroy.argtypes = [vp]
+    L.lattice_plan_destroy.restype = None
+    L.lattice_plan_info.argtypes = [vp, i64p, i32p, i64p]
+    L.lattice_points.argtypes = [vp, i64p]
+    L.lattice_freqs.argtypes = [vp, i64p]
+    L.lattice_last_error.restype = ctypes.c_char_p
+    L.lattice_fft_workspace_bytes.argtypes = [vp, ctypes.c_int]
+    L.lattice_fft_workspace_bytes.restype = ctypes.c_size_t
+    L.lattice_fft.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp]
+    L.lattice_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lattice_workspace_bytes.restype = ctypes.c_size_t
+    L.basic_scheme_solve.argtypes = [vp, vp, ctypes.c_int, f64p, f64p, f64p, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.POINTER(_Opts), vp, vp, f64p, i32p, f64p, vp,
+                                     ctypes.c_size_t, vp]
+    for f in ("lattice_plan", "lattice_plan_info", "lattice_points", "lattice_freqs", "lattice_fft",
+              "basic_scheme_solve"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc < 0:
+        raise LatticeError(rc, lib().lattice_last_error().decode())
+    return rc
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class LatticePlan:
+    """Plan for the pattern P(M) of a regular integer matrix M (d = 2 or 3)."""
+
+    def __init__(self, M):
+        M = np.asarray(M, dtype=np.int64)
+        if M.ndim != 2 or M.shape[0] != M.shape[1]:
+            raise ValueError("M must be square")
+        self.M = M.copy()
+        self.d = M.shape[0]
+        self._h = ctypes.c_void_p()
+        Mc = np.ascontiguousarray(M)
+        _check(lib().lattice_plan(Mc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), self.d,
+                                  ctypes.byref(self._h)))
+        m = ctypes.c_int64()
+        dM = ctypes.c_int()
+        div = (ctypes.c_int64 * 3)()
+        _check(lib().lattice_plan_info(self._h, ctypes.byref(m), ctypes.byref(dM), div))
+        self.m = m.value
+        self.d_M = dM.value
+        self.divisors = [div[i] for i in range(self.d)]
+        self.n_c = self.d * (self.d + 1) // 2
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.lattice_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def points(self):
+        """(m, d) int64 numerators p of the pattern points y = p / m, in plan order."""
+        p = np.empty((self.m, self.d), dtype=np.int64)
+        _check(lib().lattice_points(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return p
+
+    def freqs(self):
+        """(m, d) int64 frequencies h in G(M^T), in the spectral order of lattice_fft."""
+        h = np.empty((self.m, self.d), dtype=np.int64)
+        _check(lib().lattice_freqs(self._h, h.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return h
+
+    def workspace_bytes(self, n_loads=1, precision=LAT_FP64):
+        return int(lib().lattice_workspace_bytes(self._h, n_loads, precision))
+
+
+def lattice_plan(M):
+    return LatticePlan(M)
+
+
+def lattice_fft(plan, x, inverse=False, stream=None):
+    """Pattern DFT F(M) (forward, with 1/m) or its inverse of complex128 CUDA data (n_fields, m)."""
+    import torch
+    if x.dtype != torch.complex128 or not x.is_cuda:
+        raise TypeError("x must be a complex128 CUDA tensor")
+    x = x.contiguous()
+    n_f = x.numel() // plan.m
+    out = torch.empty_like(x)
+    _check(lib().lattice_fft(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n_f,
+                             1 if inverse else 0, None, 0, _stream(stream)))
+    return out
+
+
+def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
+                       boundary="average", eps0=None, want_sigma=False, history=False, workspace=None,
+                       eps_out=None, stream=None):
+    """Algorithm 1 on the GPU.  Returns a dict of torch/numpy results.
+
+    phase      uint8 CUDA tensor (m,), plan order
+    stiffness  (n_phases, 6, 6) Voigt matrices (host)
+    C0         (lam0, mu0)
+    E          (n_loads, n_c) tensor components (host)
+    eps0       optional CUDA float64 tensor (n_loads, n_c, m): warm start
+    """
+    import torch
+    stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
+    n_ph = stiff.shape[0]
+    C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
+    E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
+    n_loads = E.shape[0]
+    Ea, Ep = _f64(E)
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+        raise TypeError("phase must be a uint8 CUDA tensor with m entries")
+    dev = phase.device
+    if eps_out is not None:
+        eps = eps_out
+    elif eps0 is not None:
+        eps = eps0.clone()
+    else:
+        eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=dev)
+    if eps0 is not None and eps_out is not None:
+        eps.copy_(eps0)
+    sigma = torch.empty_like(eps) if want_sigma else None
+    wsb = plan.workspace_bytes(n_loads, prec)
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sbar = np.zeros((n_loads, plan.n_c))
+    iters = np.zeros(n_loads, dtype=np.int32)
+    resid = np.zeros(n_loads)
+    hist = np.zeros((n_loads, max(maxit, 1))) if history else None
+    opts = _Opts(prec, bnd, 1 if eps0 is not None else 0,
+                 hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None)
+    rc = lib().basic_scheme_solve(
+        plan.handle, ctypes.c_void_p(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
+        ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
+        ctypes.c_void_p(sigma.data_ptr()) if sigma is not None else None,
+        sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    _check(rc)
+    out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
+    if history:
+        out["history"] = [hist[i, :min(int(iters[i]), maxit, HIST_CAP)] for i in range(n_loads)]
+    return out

@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs for the lattice Basic Scheme: geometries, phases, materials, lattices.
+
+This module serves both the CUDA path and the CPU oracle and holds none of the
+method's arithmetic (no transform, no Green operator, no iteration).  Phases
+are decided from the exact integer numerators p = m y of the pattern points
+that each side enumerates on its own, so both sides label every point alike.
+
+Workloads (shaped like the paper's examples, Sec. 4 and 5):
+  * laminate: two isotropic layers with rational normal n_int (Sec. 4.1),
+    phase 0 where frac(n_int . y) < f1;
+  * coated ellipsoid (Sec. 4.2): core / coating / matrix by the confocal
+    ellipsoid inequalities, optionally rotated;
+  * random ellipsoidal inclusions in a matrix, periodic, seeded.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+BASE_SEED = 20160621
+
+
+def iso_voigt(lam, mu):
+    """6x6 Voigt stiffness (engineering shear) of an isotropic material with Lame constants (lam, mu)."""
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    for i in range(3):
+        C[i, i] = lam + 2 * mu
+        C[i + 3, i + 3] = mu
+    return C
+
+
+def c0_mean_extremes(lams, mus):
+    """Reference medium: arithmetic mean of the extreme Lame constants of the phases."""
+    return (0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus)))
+
+
+def laminate_phase(p, m, n_int, f1=Fraction(1, 2)):
+    """Phase 0 where frac(n_int . y) in [0, f1), else 1; y = p / m, exact integer test."""
+    p = np.asarray(p, dtype=np.int64)
+    f1 = Fraction(f1)
+    t = (p @ np.asarray(n_int, dtype=np.int64)) % m
+    return np.where(t * f1.denominator < f1.numerator * m, 0, 1).astype(np.uint8)
+
+
+def euler_zyz(a, b, c):
+    """Rotation matrix R = Rz(a) Ry(b) Rz(c)."""
+    def rz(t):
+        return np.array([[np.cos(t), -np.sin(t), 0], [np.sin(t), np.cos(t), 0], [0, 0, 1.0]])
+
+    def ry(t):
+        return np.array([[np.cos(t), 0, np.sin(t)], [0, 1.0, 0], [-np.sin(t), 0, np.cos(t)]])
+    return rz(a) @ ry(b) @ rz(c)
+
+
+def coated_ellipsoid_phase(p, m, c, rho_c, rho_e, R=None, center=None):
+    """0 = core (rho <= rho_c), 1 = coating (rho_c < rho <= rho_e), 2 = matrix.
+
+    rho(x) <= rho_0  iff  sum_i x~_i^2 / (c_i^2 + rho_0) <= 1 (the left side
+    decreases in rho), x~ = R^T (y - center) taken with the minimum-image
+    convention on the unit torus.  c_i = inf (2-D cylinder) drops the term.
+    """
+    p = np.asarray(p, dtype=np.int64)
+    d = p.shape[1]
+    y = p.astype(np.float64) / m
+    if center is not None:
+        y = y - np.asarray(center)[:d]
+        y -= np.round(y)
+    if d == 2:
+        y = np.concatenate([y, np.zeros((y.shape[0], 1))], axis=1)
+    R = np.eye(3) if R is None else np.asarray(R)
+    xt = y @ R  # rows: (R^T y)^T
+    c = np.asarray(c, dtype=np.float64)
+
+    def inside(rho0):
+        s = np.zeros(len(xt))
+        for i in range(3):
+            if np.isfinite(c[i]):
+                s += xt[:, i] ** 2 / (c[i] ** 2 + rho0)
+        return s <= 1.0
+    ph = np.full(len(xt), 2, dtype=np.uint8)
+    ph[inside(rho_e)] = 1
+    ph[inside(rho_c)] = 0
+    return ph
+
+
+def random_inclusions(seed, d, n_incl, vol_frac):
+    """Seeded ellipsoidal inclusions: centres, semi-axes, rotations (d = 2 or 3)."""
+    rng = np.random.default_rng(seed)
+    cen = rng.random((n_incl, d))
+    aspect = rng.uniform(1.0, 3.0, size=(n_incl, d))
+    if d == 2:
+        unit_vol = np.pi * np.prod(aspect, axis=1)
+    else:
+        unit_vol = 4.0 / 3.0 * np.pi * np.prod(aspect, axis=1)
+    scale = (vol_frac / unit_vol.sum()) ** (1.0 / d)
+    axes = np.minimum(aspect * scale, 0.45)
+    rots = []
+    for _ in range(n_incl):
+        if d == 2:
+            t = rng.uniform(0, np.pi)
+            rots.append(np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]]))
+        else:
+            rots.append(euler_zyz(*rng.uniform(0, 2 * np.pi, 3)))
+    return dict(centers=cen, axes=axes, rots=np.array(rots))
+
+
+def inclusions_phase(p, m, incl):
+    """1 inside any inclusion (periodic minimum image), else 0."""
+    p = np.asarray(p, dtype=np.int64)
+    y = p.astype(np.float64) / m
+    ph = np.zeros(len(y), dtype=np.uint8)
+    for c, a, R in zip(incl["centers"], incl["axes"], incl["rots"]):
+        z = y - c
+        z -= np.round(z)
+        zt = z @ R
+        ph[np.sum((zt / a) ** 2, axis=1) <= 1.0] = 1
+    return ph
+
+
+# lattices of the paper's experiments and of the benchmark workloads
+def shear_matrix(j, k, alpha):
+    """M_{j,k,alpha} of Sec. 5.1 (Eq. M-shear), restricted to the first two axes."""
+    return [[2 ** j, alpha * k], [(1 - alpha) * k, 2 ** (14 - j)]]
+
+
+LATTICES = {
+    # 2-D, m = 4096: aligned rank-1 lattice (every frequency parallel to (1,3)) and a spread one
+    "laminate4096_aligned": [[4096, 12288], [0, 1]],
+    "laminate4096_rank1": [[64, 1], [0, 64]],
+    # 2-D, m = 262144: tensor grid, rank-1, sheared rank-2
+    "grid512": [[512, 0], [0, 512]],
+    "rank1_262144": [[512, 1], [0, 512]],
+    "rank2_262144": [[512, 16], [0, 512]],
+    # 3-D, m = 2^21
+    "grid128": [[128, 0, 0], [0, 128, 0], [0, 0, 128]],
+    "sheared128": [[128, 16, 0], [0, 128, 16], [0, 0, 128]],
+    "rank1_2097152": [[128, 1, 0], [0, 128, 1], [0, 0, 128]],
+}
