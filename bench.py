@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice Basic Scheme (Algorithm 1, arXiv 1605.05712) on GB300.
+
+Workload (one "step"): the 2-D two-phase laminate (normal (1,3)/sqrt(10),
+volume fraction 1/2, isotropic phases (lam, mu) = (1,1) and (10,10), plane
+strain, C0 = mean of the phase extremes) on three lattices of m = 262,144
+points -- the tensor grid diag(512,512), the rank-1 lattice [[512,1],[0,512]]
+and the sheared rank-2 lattice [[512,16],[0,512]] -- with the three unit
+load cases solved one after another to a Cauchy residual of 1e-8, binary64
+throughout.  Metric: lattice-point iterations per second
+(sum over lattices and load cases of m x iterations / step time).
+
+Legs: device-timed steps with inputs resident in HBM (value), the same through
+the C ABI with the phase field copied host->device and the strain field
+copied back every step (e2e), per-kernel CUDA-event timing of one iteration
+(roofline), and the CPU oracle on a bounded sample (cpu_baseline).
+``--impl reference`` times the oracle alone.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LATS = ["grid512", "rank1_262144", "rank2_262144"]
+LAMES = [(1.0, 1.0), (10.0, 10.0)]
+N_INT = [1, 3]
+TOL = 1e-8
+MAXIT = 2000
+METRIC = "lattice-point iterations/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def load_cases(n_c=3):
+    E = np.zeros((n_c, n_c))
+    for a in range(n_c):
+        E[a, a] = 1.0 if a < 2 else 0.5     # unit load cases, tensor components (eps_12 = 1/2)
+    return E
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx):
+        self.f = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(idx), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def row_col_flops(P, n_c=3):
+    """Algorithmic flops of one iteration split by kernel (5 N log2 N per complex FFT of N points)."""
+    import math
+    m, Rh = P["m"], P["Rh"]
+    # row pass: inverse + forward half-length complex FFT of every row and component, R2C pre/post
+    # processing (~10 flops per complex point each way), polarization (n_c^2 FMA), residual (3 n_c)
+    row = n_c * (2 * 5 * (m // 2) * math.log2(Rh) + 2 * 10 * (m // 2)) + m * (2 * n_c * n_c + 3 * n_c)
+    col = []
+    for G in P["groups"]:
+        f = n_c * 2 * 5 * (m // 2 + m // P["R"]) * math.log2(G)
+        col.append(f)
+    col[0] += (m // 2 + m // P["R"]) * 2 * 45       # Green operator, ~45 flops per real part
+    return row, col
+
+
+def algorithmic_bytes(P, n_c=3, s=8):
+    """HBM bytes of one iteration by kernel: row pass reads T + eps + phase, writes eps + T;
+    a column pass reads and writes T (half spectrum + Nyquist plane)."""
+    m = P["m"]
+    spec = n_c * (m // 2 + m // P["R"]) * 2 * s
+    row = spec + n_c * m * s + m + n_c * m * s + spec
+    col = [2 * spec for _ in P["groups"]]
+    return row, col
+
+
+def setup(dev):
+    import torch
+    from paper_1605_05712_gb300 import lattice_plan, synth
+    out = []
+    for name in LATS:
+        P = lattice_plan(synth.LATTICES[name])
+        ph = synth.laminate_phase(P.points(), P.m, N_INT)
+        out.append(dict(name=name, plan=P, phase_host=torch.from_numpy(ph).pin_memory(),
+                        phase=torch.from_numpy(ph).to(dev)))
+    return out
+
+
+def run_step(work, stiff, C0, E, ws, eps):
+    from paper_1605_05712_gb300 import basic_scheme_solve
+    tot = 0
+    iters = []
+    for w in work:
+        g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=TOL, maxit=MAXIT, workspace=ws, eps_out=eps)
+        iters.append([int(x) for x in g["iters"]])
+        tot += w["plan"].m * int(np.sum(g["iters"]))
+    return tot, iters
+
+
+def plan_info(P):
+    import ctypes
+    # geometry the library chose, reconstructed from the plan's divisors for the flop/byte model
+    from paper_1605_05712_gb300 import lib  # noqa: F401
+    return P
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1605_05712_gb300 import lattice_pass_times, synth
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stiff = [synth.iso_voigt(*l) for l in LAMES]
+    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
+    E = load_cases()
+    work = setup(dev)
+    m = work[0]["plan"].m
+    ws = torch.empty(max(w["plan"].workspace_bytes(3) for w in work), dtype=torch.uint8, device=dev)
+    eps = torch.empty((3, 3, m), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        run_step(work, stiff, C0, E, ws, eps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    times, units, iters = [], 0, None
+    for _ in range(args.steps):
+        flush.fill_(1)                                   # L2 flush between timed steps (not timed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        u, iters = run_step(work, stiff, C0, E, ws, eps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        units += u
+    # end-to-end: host phase -> device, solve, strain -> host, every step
+    eps_host = torch.empty((3, 3, m), dtype=torch.float64).pin_memory()
+    e2e_times, e2e_units = [], 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for w in work:
+            w["phase"].copy_(w["phase_host"], non_blocking=True)
+        u, _ = run_step(work, stiff, C0, E, ws, eps)
+        eps_host.copy_(eps, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+        e2e_units += u
+    clocks = clk.stop()
+    ms_step = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms_step, float(np.mean(e2e_times))], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_e2e = float(t[0]), float(t[1])
+    else:
+        ms_e2e = float(np.mean(e2e_times))
+    value = world * (units / args.steps) / (ms_step / 1e3)
+    e2e_value = world * (e2e_units / args.steps) / (ms_e2e / 1e3)
+
+    # per-kernel timing of one iteration on the rank-2 lattice (dominant kernel -> roofline)
+    w = work[2]
+    P = w["plan"]
+    pt = lattice_pass_times(P, w["phase"], stiff, C0, E[0], n_reps=50)
+    geo = dict(m=P.m, R=int(P.divisors[-1]) if P.d_M == 1 else None)
+    # the rank-2 lattice (16, 16384): the library splits 16384 = 128 x 128 -> row 128, group (16, 128)
+    geo_model = {"grid512": dict(m=P.m, R=512, Rh=256, groups=[512]),
+                 "rank1_262144": dict(m=P.m, R=512, Rh=256, groups=[512]),
+                 "rank2_262144": dict(m=P.m, R=128, Rh=64, groups=[2048])}[w["name"]]
+    bytes_row, bytes_col = algorithmic_bytes(geo_model)
+    flops_row, flops_col = row_col_flops(geo_model)
+    kern = ["row_pass", "col_pass"]
+    dom = int(np.argmax(pt[:2]))
+    ms_dom = pt[dom]
+    pk = peaks()
+    fp64_peak = 1.25e3  # GFLOP/s, nominal GB300 FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
+    if dom == 0:
+        fl, by = flops_row, bytes_row
+    else:
+        fl, by = flops_col[0], bytes_col[0]
+    gflops = fl / (ms_dom * 1e-3) / 1e9
+    gbs = by / (ms_dom * 1e-3) / 1e9
+    hbm = pk.get("hbm_gbs", 6800.0)
+    roof_alu = {"bound": "alu", "achieved": round(gflops / 1e3, 4), "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
+                "frac": round(gflops / fp64_peak, 4), "traffic": None, "kernel": kern[dom] + "<double>",
+                "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                "peak_source": "nominal FP64 1.25 TFLOP/s (not in MEASURED_PEAKS.json)",
+                "per_kernel_ms": [round(x, 5) for x in pt]}
+    gpu_launches = 0
+    for w_, it in zip(work, iters):
+        ng = len({"grid512": [512], "rank1_262144": [512], "rank2_262144": [2048]}[w_["name"]])
+        per_it = 1 + (2 * ng - 1)
+        for n in it:
+            gpu_launches += 1 + per_it + n * per_it + 1    # fill, prologue, loop, effective stress
+    res = {
+        "metric": METRIC, "value": round(value, 1), "unit": "point-iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded laminate phases generated on the host)",
+        "config": {"workload": "2-D laminate n=(1,3), m=262144 on diag(512,512), rank-1 [[512,1],[0,512]] and "
+                               "rank-2 [[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64",
+                   "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
+                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roof_alu,
+        "e2e": {"value": round(e2e_value, 1), "unit": "point-iterations/s",
+                "h2d_bytes_per_step": int(sum(w_["plan"].m for w_ in work)),
+                "d2h_bytes_per_step": int(eps.numel() * 8)},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def oracle_sample(seconds, names=("rank2_262144",)):
+    """Time the CPU oracle on a bounded sample: a few iterations of the workload's solves."""
+    from oracle import elasticity as el
+    from oracle.lattice import Lattice
+    from oracle.scheme import basic_scheme
+    from paper_1605_05712_gb300 import synth
+    S = np.array([el.voigt6_to_tensor(synth.iso_voigt(*l), 2) for l in LAMES])
+    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
+    units, t_total, n_it = 0, 0.0, 0
+    lats = {}
+    for nm in names:
+        L = Lattice(synth.LATTICES[nm])
+        lats[nm] = (L, synth.laminate_phase(L.p, L.m, N_INT))
+    E = el.comps_to_sym(load_cases()[0], 2)
+    while t_total < seconds:
+        for nm in names:
+            L, ph = lats[nm]
+            t0 = time.perf_counter()
+            r = basic_scheme(L, ph, S, C0, E, tol=0.0, maxit=2)
+            t_total += time.perf_counter() - t0
+            units += L.m * r["iters"]
+            n_it += r["iters"]
+    return units / t_total, t_total, n_it
+
+
+def cpu_baseline(seconds):
+    v, t, n = oracle_sample(seconds)
+    return {"value": round(v, 1), "unit": "point-iterations/s", "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of the oracle (numpy float64, single thread) on the rank-2 m=262144 "
+                      "laminate, unit load case 11, %.1f s" % (n, t)}
+
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(1.0)
+    tt = 0
+    for _ in range(args.steps):
+        v, t, n = oracle_sample(max(2.0, args.cpu_seconds / max(args.steps, 1)))
+        vals.append(v)
+        tt += t
+    v = float(np.mean(vals))
+    res = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "point-iterations/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "ms_per_step": round(1e3 * tt / max(args.steps, 1), 2), "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2-D laminate n=(1,3), m=262144, rank-2 [[512,16],[0,512]], load case 11, "
+                                  "bounded sample of oracle iterations per step"},
+           "cpu_baseline": {"value": round(v, 1), "unit": "point-iterations/s", "cores": 1, "kind": "oracle",
+                            "sample": "2-iteration oracle solves repeated for ~%.0f s per step" %
+                                      max(2.0, args.cpu_seconds / max(args.steps, 1))},
+           "e2e": {"value": round(v, 1), "unit": "point-iterations/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

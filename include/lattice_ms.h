@@ -1,0 +1,194 @@
+/*
+ * lattice_ms.h -- C ABI of the GB300 lattice Basic Scheme library (liblatms.so).
+ *
+ * FFT-based elastic homogenization on an arbitrary sampling lattice: the
+ * generalized Moulinec-Suquet Basic Scheme of Bergmann & Merkert,
+ * "A framework for FFT-based homogenization on anisotropic lattices"
+ * (arXiv 1605.05712), Sec. 3.2, Algorithm 1, on the pattern P(M) of a regular
+ * integer matrix M (Sec. 2.1) with the pattern FFT of Sec. 2.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: LAT_OK (0) on success, a positive LAT_* outcome for a
+ *    solve that ran but did not meet the tolerance (outputs still written),
+ *    a negative LAT_ERR_* code on error.  lattice_last_error() returns a
+ *    thread-local message for the last failing call.
+ *  - Ownership: the library allocates device memory only inside
+ *    lattice_plan() (index constants and twiddle tables, freed by
+ *    lattice_plan_destroy()).  Every field buffer and the workspace belong to
+ *    the caller; solves never allocate.
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary host memory.  `stream` is a cudaStream_t
+ *    passed as void* (NULL = the legacy default stream).
+ *  - Point order ("plan order"): every spatial field is an array over the m
+ *    pattern points in the order reported by lattice_points().  The paper
+ *    leaves the ordering free (Sec. 2.2, after Eq. FourierTransform); this
+ *    library uses the storage order of its FFT (a permutation of the
+ *    lexicographic lambda order when the largest elementary divisor is split
+ *    for the four-step FFT).  Spectral data is in the order reported by
+ *    lattice_freqs().
+ *  - Tensor components: symmetric d x d tensors are stored as n_c = d(d+1)/2
+ *    planes of m values ("SoA"), components ordered (11, 22, 12) for d = 2
+ *    and (11, 22, 33, 23, 13, 12) for d = 3, as tensor (not engineering)
+ *    components.  Stiffness matrices are 6 x 6 Voigt matrices acting on
+ *    engineering strain; d = 2 is plane strain and uses the (11, 22, 12)
+ *    block.
+ */
+#ifndef LATTICE_MS_H
+#define LATTICE_MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* outcomes (>= 0) */
+#define LAT_OK               0
+#define LAT_NOT_CONVERGED    1   /* maxit reached with r >= tol; outputs hold the last iterate */
+#define LAT_DIVERGED         2   /* the residual became non-finite; outputs hold the last iterate */
+/* errors (< 0) */
+#define LAT_ERR_ARG         -1   /* NULL pointer, bad count, bad option */
+#define LAT_ERR_SINGULAR    -2   /* det M == 0 */
+#define LAT_ERR_DIM         -3   /* d not in {2, 3} */
+#define LAT_ERR_SIZE        -4   /* m or an entry too large, workspace too small */
+#define LAT_ERR_UNSUPPORTED -5   /* a divisor structure this build cannot transform */
+#define LAT_ERR_CUDA        -6   /* a CUDA runtime call failed (message has the CUDA error) */
+
+/* precision of a solve */
+#define LAT_FP64   0   /* every step in IEEE binary64 */
+#define LAT_MIXED  1   /* binary32 FFT / Green operator / polarization; binary64 strain,
+                          residual, averages and convergence test */
+
+/* treatment of boundary frequencies of the symmetric cell (k with h(-k) != -h(k)) */
+#define LAT_BOUNDARY_AVERAGE 0  /* Gamma0 averaged over h(k) and -h(-k): the real part of the
+                                   paper's complex update (default) */
+#define LAT_BOUNDARY_ZERO    1  /* those frequencies set to zero */
+
+typedef struct lat_plan lat_plan;
+
+/*
+ * lattice_plan -- build the plan for the pattern P(M).
+ *   M    host, d*d int64, row-major, det M != 0.
+ *   d    2 or 3.
+ *   out  receives the plan (caller frees with lattice_plan_destroy).
+ * Computes the Smith normal form M = Q E R (Sec. 2.2), the pattern
+ * dimension d_M, the FFT decomposition over the elementary divisors and
+ * uploads twiddle tables to the current device.
+ * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
+ * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (an elementary divisor
+ * with an odd factor > 1, or one that needs more than one four-step split),
+ * LAT_ERR_CUDA.
+ */
+int lattice_plan(const int64_t* M, int d, lat_plan** out);
+
+/* Free a plan and its device tables.  NULL is ignored. */
+void lattice_plan_destroy(lat_plan* plan);
+
+/*
+ * lattice_plan_info -- m = |det M|, d_M = #{e_j > 1} and the d elementary
+ * divisors e_1 | e_2 | ... (Sec. 2.2).  Any output pointer may be NULL.
+ */
+int lattice_plan_info(const lat_plan* plan, int64_t* m, int* d_M, int64_t* divisors);
+
+/*
+ * lattice_points -- the pattern P(M) in plan order (Sec. 2.1): p is host,
+ * m*d int64, point i is y_i = p[i*d .. i*d+d-1] / m, every coordinate in
+ * [-1/2, 1/2).  (m y is integral because m M^{-1} = +-adj M.)
+ */
+int lattice_points(const lat_plan* plan, int64_t* p);
+
+/*
+ * lattice_freqs -- the generating set G(M^T) in spectral order (Sec. 2.1):
+ * h is host, m*d int64, M^{-T} h in [-1/2, 1/2)^d.
+ */
+int lattice_freqs(const lat_plan* plan, int64_t* h);
+
+/* Thread-local description of the last error (never NULL). */
+const char* lattice_last_error(void);
+
+/*
+ * lattice_fft -- the Fourier transform on the pattern, Eq. (Fouriermatrix):
+ * forward  a_hat = F(M) a      (carries the 1/m),
+ * inverse  a     = F(M)^{-1} a_hat (no scaling).
+ *   in, out   device, n_fields * m complex binary64, interleaved (re, im);
+ *             forward: in is in plan order and out in spectral order;
+ *             inverse: the reverse.  in and out must not overlap.
+ *   workspace device, at least lattice_fft_workspace_bytes(plan, n_fields).
+ * Asynchronous on `stream`.
+ */
+size_t lattice_fft_workspace_bytes(const lat_plan* plan, int n_fields);
+int lattice_fft(const lat_plan* plan, const double* in, double* out, int n_fields,
+                int inverse, void* workspace, size_t workspace_bytes, void* stream);
+
+typedef struct lat_solve_opts {
+  int precision;        /* LAT_FP64 or LAT_MIXED */
+  int boundary;         /* LAT_BOUNDARY_AVERAGE or LAT_BOUNDARY_ZERO */
+  int warm_start;       /* 0: eps^(0) = E (Algorithm 1); 1: eps holds eps^(0) on entry */
+  double* resid_history;/* host or NULL: n_loads * maxit residuals r_0, r_1, ... (rest untouched) */
+} lat_solve_opts;
+
+/*
+ * lattice_workspace_bytes -- device workspace a solve with n_loads load
+ * cases needs (spectrum buffers, reduction partials, device scalars).
+ */
+size_t lattice_workspace_bytes(const lat_plan* plan, int n_loads, int precision);
+
+/*
+ * basic_scheme_solve -- Algorithm 1 (Sec. 3.2) for n_loads macroscopic strains:
+ *   eps^(0) = E; repeat  tau = (C_y - C0) : eps_y ;  tau_hat = F(M) tau ;
+ *   eps_hat_h = -Gamma0(h) : tau_hat_h (h != 0), eps_hat_0 = E ;
+ *   eps = F(M)^{-1} eps_hat  until r_n < tol or n = maxit,
+ * with the Cauchy residual of Sec. 5.2, r_n = ||eps^(n+1) - eps^(n)|| /
+ * (sqrt(m) ||E||_F) (l2 over points of the Frobenius norm; 1 replaces the
+ * denominator when E = 0), then sigma_y = C_y : eps_y and its mean
+ * sigma_bar = C^eff : E (Sec. 3.1).  Gamma0 is the isotropic closed form
+ * evaluated at the integer frequency h in G(M^T).
+ *   phase      device, m uint8, phase id per point in plan order (< n_phases).
+ *   n_phases   1..256.
+ *   stiffness  host, n_phases * 36 binary64: 6x6 Voigt matrix per phase (row-major).
+ *   C0         host, {lambda0, mu0}: isotropic reference medium (mu0 > 0, lambda0 + 2 mu0 > 0).
+ *   E          host, n_loads * n_c binary64 tensor components.
+ *   tol, maxit Cauchy threshold and iteration cap (maxit >= 0).
+ *   opts       may be NULL (= FP64, average, cold start, no history).
+ *   eps        device, n_loads * n_c * m binary64 (output; input too for a warm start).
+ *   sigma      device or NULL, n_loads * n_c * m binary64: the stress field.
+ *   sigma_bar  host or NULL, n_loads * n_c: mean stress per load case.
+ *   iters      host or NULL, n_loads: iterations performed.
+ *   resid      host or NULL, n_loads: last residual r.
+ *   workspace  device, >= lattice_workspace_bytes(plan, n_loads, precision).
+ * Runs on `stream` and returns after synchronizing it (host outputs valid).
+ * Load cases are solved one after another; each stops on its own residual.
+ * Returns LAT_OK when every load case met tol, else the worst outcome.
+ */
+int basic_scheme_solve(const lat_plan* plan, const uint8_t* phase, int n_phases,
+                       const double* stiffness, const double* C0,
+                       const double* E, int n_loads, double tol, int maxit,
+                       const lat_solve_opts* opts,
+                       double* eps, double* sigma, double* sigma_bar,
+                       int* iters, double* resid,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * lattice_pass_times -- profiling helper: average device time of each kernel
+ * of one Basic Scheme iteration (no counterpart in the paper; it measures
+ * the passes the solve above runs inside its CUDA graph).  Runs the
+ * prologue once and then n_reps iterations of load case 0 with plain
+ * launches, a CUDA event pair around every launch on `stream`.  Arguments
+ * as for basic_scheme_solve (eps is overwritten).
+ *   ms_out  host, >= 8 floats: [0] row pass, [1..] column passes in
+ *           launch order (forward mid groups, Gamma group, inverse mid groups),
+ *           unused entries set to 0.
+ *   n_out   receives the number of kernels per iteration.
+ */
+int lattice_pass_times(const lat_plan* plan, const uint8_t* phase, int n_phases,
+                       const double* stiffness, const double* C0, const double* E,
+                       int precision, int n_reps, double* eps,
+                       void* workspace, size_t workspace_bytes, void* stream,
+                       float* ms_out, int* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LATTICE_MS_H */

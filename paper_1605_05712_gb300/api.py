@@ -203,3 +203,26 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     if history:
         out["history"] = [hist[i, :min(int(iters[i]), maxit, HIST_CAP)] for i in range(n_loads)]
     return out
+
+
+def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=20, stream=None):
+    """Average device milliseconds per launch of each kernel of one iteration (profiling helper)."""
+    import torch
+    stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
+    C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
+    Ea, Ep = _f64(np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)[0])
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    eps = torch.empty((plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
+    ws = torch.empty(plan.workspace_bytes(1, prec), dtype=torch.uint8, device=phase.device)
+    ms = (ctypes.c_float * 8)()
+    n = ctypes.c_int()
+    L = lib()
+    L.lattice_pass_times.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + \
+        [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_int)]
+    L.lattice_pass_times.restype = ctypes.c_int
+    _check(L.lattice_pass_times(plan.handle, ctypes.c_void_p(phase.data_ptr()), stiff.shape[0], stiff_p, C0p, Ep,
+                                prec, int(n_reps), ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream), ms, ctypes.byref(n)))
+    return [ms[i] for i in range(n.value)]

@@ -1,0 +1,83 @@
+// internal.h -- plan layout and kernel parameter blocks of liblatms (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lattice_ms.h"
+
+#define LAT_MAX_AX 6
+#define LAT_MAX_GROUPS 3
+#define LAT_HIST_CAP 16384  // residuals kept per load case in the workspace
+
+// One logical FFT axis in storage order (row-major, last = contiguous row).
+struct LatAxis {
+  int len;         // length (power of two)
+  int log2len;
+  int snf;         // elementary-divisor axis j this axis belongs to
+  int64_t mult;    // k_j += mult * (spectral index on this axis)
+  int64_t cv[3];   // (mult * c_j) mod e_d: contribution to v = Q^{-T} E^{-1} k * e_d
+};
+
+// One column pass: FFT over the logical axes [a0, a1) on tiles of columns.
+struct LatGroup {
+  int a0, a1;
+  int G;            // product of the group's lengths
+  int64_t outer;    // product of lengths of axes [0, a0)
+  int64_t inner;    // product of lengths of axes [a1, nax-1) (row axis excluded)
+  int has_twiddle;  // the split axis' n1 lies in this group (four-step twiddle before/after)
+};
+
+struct lat_plan {
+  int d;
+  int64_t M[3][3];
+  int64_t det, m;
+  int64_t Q[3][3], R[3][3], Rinv[3][3], P[3][3];  // M = Q diag(e) R, P = Q^{-T}
+  int64_t e[3];
+  int dM;
+  int64_t ed;        // largest elementary divisor (lcm of all)
+  // FFT decomposition
+  int nax;           // logical axes, ax[nax-1] is the contiguous row
+  LatAxis ax[LAT_MAX_AX];
+  int Rlen, Rh, log2Rh;  // row length (real samples) and its half
+  int64_t nrows;     // m / Rlen
+  int ngroups;       // column passes; grp[0] holds axis 0 and applies Gamma0
+  LatGroup grp[LAT_MAX_GROUPS];
+  int split;         // 1 if the largest divisor is split into (n1, n2 = row)
+  int split_n1;      // logical index of n1
+  int64_t split_e;   // the split divisor e = A * B
+  int split_lo_log2; // two-level twiddle table split: W_e^j = hi[j >> s] * lo[j & (2^s-1)]
+  // device tables (owned)
+  int tw_log2;       // twiddle table W_N^t, N = 2^tw_log2
+  double2* d_tw;
+  float2* d_twf;
+  double2* d_stw;    // split twiddles: [hi (e >> s) | lo (2^s)]
+  float2* d_stwf;
+  int64_t stw_hi_n, stw_lo_n;
+  int device;
+  // cached solver graph
+  void* graph_cache;
+};
+
+// Parameters shared by the solver kernels (passed by value).
+struct LatDev {
+  int d, n_c, nax;
+  int Rlen, Rh, log2Rh;
+  int64_t m, nrows;
+  int64_t ed, ed_mask;        // ed_mask = ed - 1 if ed is a power of two, else -1
+  int64_t MT[3][3];           // M^T (h = M^T v' / e_d)
+  int ax_len[LAT_MAX_AX], ax_log2[LAT_MAX_AX];
+  int64_t ax_cv[LAT_MAX_AX][3];
+  int split, split_n1, split_lo_log2;
+  int64_t split_e;
+  int64_t stw_hi_n;
+  int tw_log2;
+  const void* tw;             // twiddle table (double2 or float2, per precision)
+  const void* stw;            // split twiddles [hi | lo]
+};
+
+void lat_set_error(const std::string& s);
+// upload twiddle tables to the current device on first use (plans are host-only until then)
+int lat_ensure_tables(lat_plan* P);
+int lat_fail(int code, const std::string& s);

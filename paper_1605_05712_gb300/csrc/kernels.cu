@@ -1,0 +1,599 @@
+// kernels.cu -- the Basic Scheme iteration on sm_103a: row pass, column pass, update, averages.
+//
+// One iteration of Algorithm 1 (Sec. 3.2, arXiv 1605.05712) is two or three
+// passes over HBM:
+//   row pass    : inverse R2C FFT of the previous spectrum along the contiguous
+//                 axis -> eps^(n+1) (Re of F^{-1}), Cauchy residual against eps^(n)
+//                 in binary64, eps written, polarization tau = (C_y - C0) : eps,
+//                 forward R2C FFT along the row;                 (fused)
+//   column pass : four-step twiddle, forward FFT over the remaining divisor
+//                 axes, eps_hat = -Gamma0(h) : tau_hat / m (h != 0), eps_hat_0 = E,
+//                 inverse FFT, inverse twiddle;                 (fused)
+//   (mid pass   : FFT over one more axis group when a tile would not fit)
+// The residual reduction ends in the last block of the row pass, which also
+// decides convergence and sets the CUDA-graph WHILE condition.
+#include <math.h>
+
+#include "fft_smem.cuh"
+#include "kernels.cuh"
+
+// ------------------------------------------------------------------ Green operator (Sec. 3.1)
+// Gamma0(h) : tau for isotropic C0 (closed form of grad (grad^H C0 grad)^{-1} grad^H):
+//   (Gamma0 : tau)_ij = [c1 (h_i w_j + h_j w_i) - c2 s h_i h_j / |h|^2] / |h|^2,
+//   w = tau h, s = h . w, c1 = 1/(2 mu0), c2 = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)).
+template <typename Real>
+__device__ __forceinline__ void gamma_apply(int d, const Real* h, Real c1, Real c2, const Real* t, Real* out) {
+  Real A[3][3];
+  if (d == 2) {
+    A[0][0] = t[0]; A[1][1] = t[1]; A[0][1] = A[1][0] = t[2];
+    A[2][2] = A[0][2] = A[2][0] = A[1][2] = A[2][1] = 0;
+  } else {
+    A[0][0] = t[0]; A[1][1] = t[1]; A[2][2] = t[2];
+    A[1][2] = A[2][1] = t[3]; A[0][2] = A[2][0] = t[4]; A[0][1] = A[1][0] = t[5];
+  }
+  Real n2 = 0, w[3], s = 0;
+  for (int i = 0; i < d; ++i) n2 += h[i] * h[i];
+  const Real a = Real(1) / n2;
+  for (int i = 0; i < d; ++i) {
+    Real acc = 0;
+    for (int j = 0; j < d; ++j) acc += A[i][j] * h[j];
+    w[i] = acc;
+    s += h[i] * acc;
+  }
+  const Real q = c2 * a * s;
+#define GAM(i, j) (a * (c1 * (h[i] * w[j] + h[j] * w[i]) - q * h[i] * h[j]))
+  if (d == 2) {
+    out[0] = GAM(0, 0); out[1] = GAM(1, 1); out[2] = GAM(0, 1);
+  } else {
+    out[0] = GAM(0, 0); out[1] = GAM(1, 1); out[2] = GAM(2, 2);
+    out[3] = GAM(1, 2); out[4] = GAM(0, 2); out[5] = GAM(0, 1);
+  }
+#undef GAM
+}
+
+__device__ __forceinline__ int64_t mod_ed(const LatDev& dv, int64_t v) {
+  if (dv.ed_mask >= 0) return v & dv.ed_mask;
+  int64_t r = v % dv.ed;
+  return r < 0 ? r + dv.ed : r;
+}
+
+// h~ = M^T v' with v' the symmetric representative of v (mod e_d) in [-e_d/2, e_d/2)
+__device__ __forceinline__ void v_to_h(const LatDev& dv, const int64_t* v, int64_t* h) {
+  int64_t vp[3];
+  for (int r = 0; r < dv.d; ++r) vp[r] = (2 * v[r] >= dv.ed) ? v[r] - dv.ed : v[r];
+  for (int i = 0; i < dv.d; ++i) {
+    int64_t acc = 0;
+    for (int j = 0; j < dv.d; ++j) acc += dv.MT[i][j] * vp[j];
+    h[i] = acc;
+  }
+}
+
+// eps_hat = -Gammabar0(k) : tau_hat / m at the frequency with v = e_d Q^{-T} E^{-1} k (mod e_d);
+// in/out are n_c complex values.  v == 0 (k = 0) -> E (or 0 for an increment).
+template <typename Real>
+__device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt, const int64_t* v,
+                                            typename cplx_of<Real>::type* val) {
+  typedef typename cplx_of<Real>::type C;
+  const int d = dv.d, n_c = dv.n_c;
+  if (v[0] == 0 && v[1] == 0 && v[2] == 0) {
+    for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(mt.E[c], 0.0);
+    return;
+  }
+  int64_t hi[3], vn[3], hn[3];
+  v_to_h(dv, v, hi);
+  bool boundary = false;
+  for (int r = 0; r < d; ++r) {
+    vn[r] = mod_ed(dv, dv.ed - v[r]);
+    if (2 * v[r] == dv.ed) boundary = true;  // v' = -e_d/2: -v has the same representative
+  }
+  vn[2] = (d == 3) ? vn[2] : 0;
+  if (boundary && mt.boundary_zero) {
+    for (int c = 0; c < n_c; ++c) val[c] = cmake<C>(0.0, 0.0);
+    return;
+  }
+  const Real c1 = Real(0.5 / mt.mu0);
+  const Real c2 = Real((mt.lam0 + mt.mu0) / (mt.mu0 * (mt.lam0 + 2.0 * mt.mu0)));
+  const Real sc = Real(-1.0 / (double)dv.m);
+  Real h[3] = {(Real)hi[0], (Real)hi[1], (Real)(d == 3 ? hi[2] : 0)};
+  Real tr[6], ti[6], gr[6], gi[6];
+  for (int c = 0; c < n_c; ++c) tr[c] = val[c].x, ti[c] = val[c].y;
+  gamma_apply<Real>(d, h, c1, c2, tr, gr);
+  gamma_apply<Real>(d, h, c1, c2, ti, gi);
+  if (boundary) {
+    // average with -h(-k): Gamma0 is even in h, so evaluate at h(-k) directly
+    v_to_h(dv, vn, hn);
+    Real h2[3] = {(Real)hn[0], (Real)hn[1], (Real)(d == 3 ? hn[2] : 0)};
+    Real gr2[6], gi2[6];
+    gamma_apply<Real>(d, h2, c1, c2, tr, gr2);
+    gamma_apply<Real>(d, h2, c1, c2, ti, gi2);
+    for (int c = 0; c < n_c; ++c) gr[c] = Real(0.5) * (gr[c] + gr2[c]), gi[c] = Real(0.5) * (gi[c] + gi2[c]);
+  }
+  for (int c = 0; c < n_c; ++c) {
+    val[c].x = sc * gr[c];
+    val[c].y = sc * gi[c];
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// block sum of x into out (valid on thread 0); red has >= 32 doubles
+__device__ double block_sum(double x, double* red) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = x;
+  __syncthreads();
+  double t = 0;
+  if (wid == 0) {
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// ordered sum of n values written by other blocks (bypasses L1), result on every lane of warp 0
+__device__ double ordered_sum(const double* p, int n) {
+  double t = 0;
+  for (int i = threadIdx.x; i < n; i += 32) t += __ldcg(p + i);
+  return warp_sum(t);
+}
+
+// ------------------------------------------------------------------ row pass
+template <typename Real>
+__global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
+  typedef typename cplx_of<Real>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_c = dv.n_c, Rh = dv.Rh, lgRh = dv.log2Rh, rpc = a.rpc;
+  const int nlines = n_c * rpc;
+  C* buf = (C*)smem_raw;
+  C* nyq = buf + (size_t)nlines * Rh;
+  double* red = (double*)(nyq + nlines);
+  __shared__ int s_last;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t m = dv.m, R = dv.Rlen, half_m = m / 2, nrows = dv.nrows;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  C* T = (C*)a.T;
+  C* TN = (C*)a.TN;
+  const C* tw = (const C*)dv.tw;
+  const int tw_log2 = dv.tw_log2, lgR = lgRh + 1;
+  const int npl = Rh / 2 + 1;
+
+  if (a.flags & ROW_LOAD_EPS) {
+    for (int idx = tid; idx < nlines * Rh; idx += nthr) {
+      const int line = idx / Rh, n = idx - line * Rh;
+      const int c = line / rpc, row = line - c * rpc;
+      const double2 v = *(const double2*)(a.eps + c * m + (r0 + row) * R + 2 * n);
+      buf[idx] = cmake<C>(v.x, v.y);
+    }
+    __syncthreads();
+  } else {
+    for (int idx = tid; idx < nlines * Rh; idx += nthr) {
+      const int line = idx / Rh, pos = idx - line * Rh;
+      const int c = line / rpc, row = line - c * rpc;
+      buf[idx] = T[c * half_m + (r0 + row) * Rh + pos];
+    }
+    for (int idx = tid; idx < nlines; idx += nthr) {
+      const int c = idx / rpc, row = idx - c * rpc;
+      nyq[idx] = TN[c * nrows + r0 + row];
+    }
+    __syncthreads();
+    // half spectrum X[0..Rh] -> Z = E + i O (inverse of the R2C post-processing), in place
+    for (int idx = tid; idx < nlines * npl; idx += nthr) {
+      const int line = idx / npl, k = idx - line * npl;
+      C* L = buf + (size_t)line * Rh;
+      if (k == 0) {
+        const Real X0 = L[0].x, XN = nyq[line].x;
+        L[0].x = X0 + XN;
+        L[0].y = X0 - XN;
+      } else {
+        const int kp = Rh - k;
+        const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+        const C Xk = L[pk], Xkp = L[pkp];
+        const C wk = twid(tw, tw_log2, lgR, k);
+        L[pk] = cadd(cadd(Xk, cconj(Xkp)), cmuli(cmulc(csub(Xk, cconj(Xkp)), wk)));
+        if (kp != k) {
+          const C wkp = twid(tw, tw_log2, lgR, kp);
+          L[pkp] = cadd(cadd(Xkp, cconj(Xk)), cmuli(cmulc(csub(Xkp, cconj(Xk)), wkp)));
+        }
+      }
+    }
+    __syncthreads();
+    fft_dit_inv(buf, lgRh, 1, nlines, tw, tw_log2);
+  }
+
+  // pointwise: update, residual, polarization
+  double dsum = 0.0;
+  const bool update = (a.flags & ROW_UPDATE) != 0;
+  const bool incr = (a.flags & ROW_INCREMENT) != 0;
+  for (int idx = tid; idx < rpc * Rh; idx += nthr) {
+    const int row = idx / Rh, n = idx - row * Rh;
+    const int64_t g = (r0 + row) * R + 2 * n;
+    Real e0[6], e1[6];
+    for (int c = 0; c < n_c; ++c) {
+      const C z = buf[((size_t)c * rpc + row) * Rh + n];
+      e0[c] = z.x;
+      e1[c] = z.y;
+    }
+    if (update) {
+      for (int c = 0; c < n_c; ++c) {
+        double2* pe = (double2*)(a.eps + c * m + g);
+        const double2 old = *pe;
+        double n0 = (double)e0[c], n1 = (double)e1[c];
+        double d0, d1;
+        if (incr) {
+          d0 = n0;
+          d1 = n1;
+          n0 += old.x;
+          n1 += old.y;
+        } else {
+          d0 = n0 - old.x;
+          d1 = n1 - old.y;
+        }
+        const double wgt = (c >= dv.d) ? 2.0 : 1.0;
+        dsum += wgt * (d0 * d0 + d1 * d1);
+        *pe = make_double2(n0, n1);
+      }
+    }
+    const uchar2 ph = *(const uchar2*)(a.phase + g);
+    const double* D0 = a.mat.Dtab + (int)ph.x * n_c * n_c;
+    const double* D1 = a.mat.Dtab + (int)ph.y * n_c * n_c;
+    for (int c = 0; c < n_c; ++c) {
+      Real t0 = 0, t1 = 0;
+      for (int q = 0; q < n_c; ++q) {
+        t0 += (Real)__ldg(D0 + c * n_c + q) * e0[q];
+        t1 += (Real)__ldg(D1 + c * n_c + q) * e1[q];
+      }
+      buf[((size_t)c * rpc + row) * Rh + n] = cmake<C>(t0, t1);
+    }
+  }
+  __syncthreads();
+  fft_dif(buf, lgRh, 1, nlines, tw, tw_log2);
+  // R2C post-processing: X[k] = 1/2 (A - i W_R^k B), A = Z_k + conj Z_{Rh-k}, B = Z_k - conj Z_{Rh-k}
+  for (int idx = tid; idx < nlines * npl; idx += nthr) {
+    const int line = idx / npl, k = idx - line * npl;
+    C* L = buf + (size_t)line * Rh;
+    if (k == 0) {
+      const C Z0 = L[0];
+      L[0] = cmake<C>((double)(Z0.x + Z0.y), 0.0);
+      nyq[line] = cmake<C>((double)(Z0.x - Z0.y), 0.0);
+    } else {
+      const int kp = Rh - k;
+      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+      const C Zk = L[pk], Zkp = L[pkp];
+      const C wk = twid(tw, tw_log2, lgR, k);
+      const C A1 = cadd(Zk, cconj(Zkp)), B1 = csub(Zk, cconj(Zkp));
+      L[pk] = cscale(csub(A1, cmuli(cmul(B1, wk))), Real(0.5));
+      if (kp != k) {
+        const C wkp = twid(tw, tw_log2, lgR, kp);
+        const C A2 = cadd(Zkp, cconj(Zk)), B2 = csub(Zkp, cconj(Zk));
+        L[pkp] = cscale(csub(A2, cmuli(cmul(B2, wkp))), Real(0.5));
+      }
+    }
+  }
+  __syncthreads();
+  if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
+    for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
+      const int row = idx / (Rh + 1), k = idx - row * (Rh + 1);
+      C val[6];
+      for (int c = 0; c < n_c; ++c) {
+        const int line = c * rpc + row;
+        val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
+      }
+      int64_t v[3] = {0, 0, 0};
+      for (int r = 0; r < dv.d; ++r) v[r] = mod_ed(dv, (int64_t)k * dv.ax_cv[dv.nax - 1][r]);
+      green_point<Real>(dv, a.mat, v, val);
+      for (int c = 0; c < n_c; ++c) {
+        const int line = c * rpc + row;
+        if (k == Rh) nyq[line] = val[c];
+        else buf[(size_t)line * Rh + bitrev(k, lgRh)] = val[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nlines * Rh; idx += nthr) {
+    const int line = idx / Rh, pos = idx - line * Rh;
+    const int c = line / rpc, row = line - c * rpc;
+    T[c * half_m + (r0 + row) * Rh + pos] = buf[idx];
+  }
+  for (int idx = tid; idx < nlines; idx += nthr) {
+    const int c = idx / rpc, row = idx - c * rpc;
+    TN[c * nrows + r0 + row] = nyq[idx];
+  }
+  if (!update) return;
+  // residual: block partial -> last block sums in block order, decides convergence
+  const double bs = block_sum(dsum, red);
+  if (tid == 0) {
+    a.it.partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned t = atomicAdd(a.it.counter, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid < 32) {
+    __threadfence();
+    const double s = ordered_sum(a.it.partials, gridDim.x);
+    if (tid == 0) {
+      const double r = sqrt(s) / a.it.norm0;
+      const int n = *a.it.iter + 1;
+      *a.it.iter = n;
+      if (n - 1 < LAT_HIST_CAP) a.it.hist[n - 1] = r;
+      *a.it.last_r = r;
+      const bool cont = isfinite(r) && !(r < a.it.tol) && n < a.it.maxit;
+      if (!cont) *a.it.done = 1;
+      *a.it.counter = 0u;
+      if (a.it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.it.cond, cont ? 1u : 0u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ column pass
+template <typename Real>
+__global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
+  typedef typename cplx_of<Real>::type C;
+  if (a.done && *(volatile const int*)a.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = (C*)smem_raw;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int n_f = a.n_f, G = a.G;
+  int64_t b = blockIdx.x;
+  const int64_t main_blocks = a.outer * a.tiles_main;
+  const bool nyqt = b >= main_blocks;
+  int64_t o, t, inner_count;
+  int w;
+  if (!nyqt) {
+    o = b / a.tiles_main;
+    t = b - o * a.tiles_main;
+    w = a.w;
+    inner_count = a.inner * a.row_slots;
+  } else {
+    b -= main_blocks;
+    o = b / a.tiles_nyq;
+    t = b - o * a.tiles_nyq;
+    w = a.wN;
+    inner_count = a.inner;
+  }
+  const int64_t i0 = t * w;
+  const int wv = (int)min((int64_t)w, inner_count - i0);
+  const int64_t plane = a.outer * (int64_t)G * inner_count;
+  C* dst = (C*)(nyqt ? a.TN : a.T);
+  const C* src = (a.Tin && !nyqt) ? (const C*)a.Tin : dst;
+  const C* tw = (const C*)dv.tw;
+  const int lg_slots = __ffs(a.row_slots) - 1;
+
+  for (int idx = tid; idx < n_f * G * w; idx += nthr) {
+    const int col = idx % w;
+    const int g = (idx / w) % G;
+    const int f = idx / (w * G);
+    s[idx] = (col < wv) ? src[f * plane + (o * G + g) * inner_count + i0 + col] : cmake<C>(0.0, 0.0);
+  }
+  __syncthreads();
+
+  // four-step twiddle W_e^{n1 k2} (k2 = row frequency of this column)
+  int64_t after_n1 = 1;
+  int len_n1 = 1;
+  if (a.has_twiddle) {
+    for (int x = dv.split_n1 + 1; x < a.a1; ++x) after_n1 *= dv.ax_len[x];
+    len_n1 = dv.ax_len[dv.split_n1];
+  }
+  auto col_krow = [&](int col) -> int64_t {
+    const int64_t ii = i0 + col;
+    if (nyqt) return (int64_t)dv.Rh;
+    return (int64_t)bitrev((uint32_t)(ii % a.row_slots), lg_slots);
+  };
+  auto split_tw = [&](int64_t j) -> C {
+    const C* st = (const C*)dv.stw;
+    const int sh = dv.split_lo_log2;
+    const C hi = __ldg(st + (j >> sh));
+    const C lo = __ldg(st + dv.stw_hi_n + (j & ((int64_t(1) << sh) - 1)));
+    return cmul(hi, lo);
+  };
+  if (a.has_twiddle && a.mode != COL_INV) {
+    for (int idx = tid; idx < G * w; idx += nthr) {
+      const int col = idx % w, g = idx / w;
+      const int64_t n1 = (g / after_n1) % len_n1;
+      const C W = split_tw(n1 * col_krow(col));
+      for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmul(s[(size_t)f * G * w + idx], W);
+    }
+    __syncthreads();
+  }
+  if (a.mode != COL_INV) {
+    int64_t after = 1;
+    for (int x = a.a1 - 1; x >= a.a0; --x) {
+      int64_t before = 1;
+      for (int y = a.a0; y < x; ++y) before *= dv.ax_len[y];
+      fft_dif(s, dv.ax_log2[x], (int)(w * after), (int)(n_f * before), tw, dv.tw_log2);
+      after *= dv.ax_len[x];
+    }
+  }
+  if (a.mode == COL_GAMMA) {
+    for (int idx = tid; idx < G * w; idx += nthr) {
+      const int col = idx % w, g = idx / w;
+      int64_t v[3] = {0, 0, 0};
+      // group axes (bit-reversed after the DIF)
+      int64_t rem = g;
+      for (int x = a.a1 - 1; x >= a.a0; --x) {
+        const int pos = (int)(rem % dv.ax_len[x]);
+        rem /= dv.ax_len[x];
+        const int64_t k = bitrev(pos, dv.ax_log2[x]);
+        for (int r = 0; r < dv.d; ++r) v[r] += k * dv.ax_cv[x][r];
+      }
+      // axes between the group and the row (transformed by the mid passes, bit-reversed)
+      const int64_t ii = i0 + col;
+      int64_t mid = nyqt ? ii : ii / a.row_slots;
+      for (int x = dv.nax - 2; x >= a.a1; --x) {
+        const int pos = (int)(mid % dv.ax_len[x]);
+        mid /= dv.ax_len[x];
+        const int64_t k = bitrev(pos, dv.ax_log2[x]);
+        for (int r = 0; r < dv.d; ++r) v[r] += k * dv.ax_cv[x][r];
+      }
+      const int64_t kr = col_krow(col);
+      for (int r = 0; r < dv.d; ++r) v[r] = mod_ed(dv, v[r] + kr * dv.ax_cv[dv.nax - 1][r]);
+      C val[6];
+      for (int f = 0; f < n_f; ++f) val[f] = s[(size_t)f * G * w + idx];
+      green_point<Real>(dv, a.mat, v, val);
+      for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = val[f];
+    }
+    __syncthreads();
+  }
+  if (a.mode != COL_FWD) {
+    int64_t before = 1;
+    for (int x = a.a0; x < a.a1; ++x) {
+      int64_t after = 1;
+      for (int y = x + 1; y < a.a1; ++y) after *= dv.ax_len[y];
+      fft_dit_inv(s, dv.ax_log2[x], (int)(w * after), (int)(n_f * before), tw, dv.tw_log2);
+      before *= dv.ax_len[x];
+    }
+    if (a.has_twiddle) {
+      for (int idx = tid; idx < G * w; idx += nthr) {
+        const int col = idx % w, g = idx / w;
+        const int64_t n1 = (g / after_n1) % len_n1;
+        const C W = split_tw(n1 * col_krow(col));
+        for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmulc(s[(size_t)f * G * w + idx], W);
+      }
+      __syncthreads();
+    }
+  }
+  const Real sc = (Real)a.scale;
+  for (int idx = tid; idx < n_f * G * w; idx += nthr) {
+    const int col = idx % w;
+    if (col >= wv) continue;
+    const int g = (idx / w) % G;
+    const int f = idx / (w * G);
+    C val = s[idx];
+    if (a.scale != 1.0) val = cscale(val, sc);
+    dst[f * plane + (o * G + g) * inner_count + i0 + col] = val;
+  }
+}
+
+// ------------------------------------------------------------------ complex row transform (lattice_fft)
+template <typename Real>
+__global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void* in, void* out, int n_f,
+                                                          int inverse, double scale, int rpc) {
+  typedef typename cplx_of<Real>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = (C*)smem_raw;
+  const int R = dv.Rlen, lgR = dv.log2Rh + 1, nlines = n_f * rpc;
+  const int64_t m = dv.m, r0 = (int64_t)blockIdx.x * rpc;
+  const C* src = (const C*)in;
+  C* dst = (C*)out;
+  for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
+    const int line = idx / R, pos = idx - line * R;
+    const int f = line / rpc, row = line - f * rpc;
+    buf[idx] = src[f * m + (r0 + row) * R + pos];
+  }
+  __syncthreads();
+  if (inverse) fft_dit_inv(buf, lgR, 1, nlines, (const C*)dv.tw, dv.tw_log2);
+  else fft_dif(buf, lgR, 1, nlines, (const C*)dv.tw, dv.tw_log2);
+  const Real sc = (Real)scale;
+  for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
+    const int line = idx / R, pos = idx - line * R;
+    const int f = line / rpc, row = line - f * rpc;
+    C v = buf[idx];
+    if (scale != 1.0) v = cscale(v, sc);
+    dst[f * m + (r0 + row) * R + pos] = v;
+  }
+}
+
+// ------------------------------------------------------------------ fill, effective stress
+struct FillArgs {
+  double E[6];
+};
+__global__ void fill_kernel(double* eps, int n_c, int64_t m, FillArgs fa) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    for (int c = 0; c < n_c; ++c) eps[c * m + i] = fa.E[c];
+}
+
+// sigma_y = C_y : eps_y and sigma_bar = (1/m) sum_y sigma_y  (Sec. 3.1, effective matrix)
+__global__ void __launch_bounds__(256) eff_kernel(LatDev dv, EffArgs a) {
+  __shared__ double red[32];
+  __shared__ int s_last;
+  const int n_c = dv.n_c;
+  const int64_t m = dv.m, stride = (int64_t)gridDim.x * blockDim.x;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const double* Cp = a.Ctab + (int)a.phase[i] * n_c * n_c;
+    double e[6];
+    for (int c = 0; c < n_c; ++c) e[c] = a.eps[c * m + i];
+    for (int c = 0; c < n_c; ++c) {
+      double sgm = 0;
+      for (int q = 0; q < n_c; ++q) sgm += __ldg(Cp + c * n_c + q) * e[q];
+      if (a.sigma) a.sigma[c * m + i] = sgm;
+      acc[c] += sgm;
+    }
+  }
+  for (int c = 0; c < n_c; ++c) {
+    const double bs = block_sum(acc[c], red);
+    if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * n_c + c] = bs;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    for (int c = 0; c < n_c; ++c) {
+      double t = 0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(a.partials + (int64_t)b * n_c + c);
+      t = warp_sum(t);
+      if (threadIdx.x == 0) a.sigma_bar[c] = t / (double)m;
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename Real>
+void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int nthreads, size_t smem, cudaStream_t st) {
+  row_pass_kernel<Real><<<nblocks, nthreads, smem, st>>>(dv, a);
+}
+template <typename Real>
+void launch_col_pass(const LatDev& dv, const ColArgs& a, int nthreads, size_t smem, cudaStream_t st) {
+  const int64_t nb = a.outer * (a.tiles_main + a.tiles_nyq);
+  col_pass_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
+}
+template <typename Real>
+void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale, int rpc,
+                        int nthreads, size_t smem, cudaStream_t st) {
+  const int64_t nb = dv.nrows / rpc;
+  row_complex_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, in, out, n_f, inverse, scale, rpc);
+}
+void launch_fill(double* eps, int n_c, int64_t m, const double* E, cudaStream_t st) {
+  FillArgs fa;
+  for (int c = 0; c < 6; ++c) fa.E[c] = c < n_c ? E[c] : 0.0;
+  int64_t nb = (m + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  fill_kernel<<<(unsigned)nb, 256, 0, st>>>(eps, n_c, m, fa);
+}
+void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, cudaStream_t st) {
+  eff_kernel<<<nblocks, 256, 0, st>>>(dv, a);
+}
+
+template void launch_row_pass<double>(const LatDev&, const RowArgs&, int, int, size_t, cudaStream_t);
+template void launch_row_pass<float>(const LatDev&, const RowArgs&, int, int, size_t, cudaStream_t);
+template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, size_t, cudaStream_t);
+template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, size_t, cudaStream_t);
+template void launch_row_complex<double>(const LatDev&, const void*, void*, int, int, double, int, int, size_t,
+                                         cudaStream_t);
+
+int lat_kernel_attrs(size_t max_smem) {
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(row_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(row_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(col_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(col_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(row_complex_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)max_smem);
+  return e == cudaSuccess ? 0 : (int)e;
+}

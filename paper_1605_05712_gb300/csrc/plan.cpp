@@ -1,0 +1,493 @@
+// plan.cpp -- lattice_plan: Smith normal form, FFT decomposition, index maps, twiddles.
+//
+// Sec. 2.1-2.2 of arXiv 1605.05712: the pattern P(M) of a regular integer
+// matrix M, its Smith normal form M = Q E R (E = diag(e), e_j | e_{j+1}), and
+// the statement that with lexicographic addressing lambda of P(M) and k of
+// G(M^T) the pattern DFT is an ordinary d_M-dimensional DFT over the e_j > 1:
+//   h(k)^T y(lambda) = sum_j k_j lambda_j / e_j  (mod 1),
+//   y(lambda) = R^{-1} E^{-1} lambda (mod 1),  h(k) = R^T k (mod M^T Z^d).
+// The frequency in the symmetric cell is found from the fractional coordinates
+//   M^{-T} R^T k = Q^{-T} E^{-1} k = v / e_d,  v = sum_j k_j (e_d / e_j) P e_j,
+// P = Q^{-T}: reduce v into [-e_d/2, e_d/2) componentwise and h = M^T v / e_d.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+static thread_local std::string g_err;
+void lat_set_error(const std::string& s) { g_err = s; }
+int lat_fail(int code, const std::string& s) {
+  g_err = s;
+  return code;
+}
+extern "C" const char* lattice_last_error(void) { return g_err.c_str(); }
+
+typedef __int128 i128;
+
+namespace {
+
+struct Mat {
+  int d;
+  i128 a[3][3];
+};
+
+Mat ident(int d) {
+  Mat I;
+  I.d = d;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) I.a[i][j] = (i == j);
+  return I;
+}
+
+i128 det(const Mat& A) {
+  if (A.d == 2) return A.a[0][0] * A.a[1][1] - A.a[0][1] * A.a[1][0];
+  return A.a[0][0] * (A.a[1][1] * A.a[2][2] - A.a[1][2] * A.a[2][1]) -
+         A.a[0][1] * (A.a[1][0] * A.a[2][2] - A.a[1][2] * A.a[2][0]) +
+         A.a[0][2] * (A.a[1][0] * A.a[2][1] - A.a[1][1] * A.a[2][0]);
+}
+
+// adjugate: adj(A) A = det(A) I
+Mat adjugate(const Mat& A) {
+  Mat B;
+  B.d = A.d;
+  if (A.d == 2) {
+    B.a[0][0] = A.a[1][1];
+    B.a[0][1] = -A.a[0][1];
+    B.a[1][0] = -A.a[1][0];
+    B.a[1][1] = A.a[0][0];
+    return B;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+      B.a[i][j] = A.a[r0][c0] * A.a[r1][c1] - A.a[r0][c1] * A.a[r1][c0];
+    }
+  return B;
+}
+
+i128 iabs(i128 x) { return x < 0 ? -x : x; }
+
+// floor(a / b) for b != 0
+i128 floordiv(i128 a, i128 b) {
+  i128 q = a / b, r = a % b;
+  if (r != 0 && ((r < 0) != (b < 0))) --q;
+  return q;
+}
+i128 mod(i128 a, i128 b) {  // b > 0, result in [0, b)
+  i128 r = a % b;
+  return r < 0 ? r + b : r;
+}
+
+// Smith normal form by textbook elimination: U A V = diag(e), returns Q = U^-1, R = V^-1.
+bool smith(const Mat& M, Mat& Q, i128 e[3], Mat& R) {
+  const int d = M.d;
+  Mat A = M, U = ident(d), V = ident(d);
+  const i128 LIM = ((i128)1) << 100;
+  for (int t = 0; t < d; ++t) {
+    for (int guard = 0; guard < 100000; ++guard) {
+      int bi = -1, bj = -1;
+      for (int i = t; i < d; ++i)
+        for (int j = t; j < d; ++j)
+          if (A.a[i][j] != 0 && (bi < 0 || iabs(A.a[i][j]) < iabs(A.a[bi][bj]))) bi = i, bj = j;
+      if (bi < 0) return false;
+      if (bi != t)
+        for (int j = 0; j < d; ++j) std::swap(A.a[bi][j], A.a[t][j]), std::swap(U.a[bi][j], U.a[t][j]);
+      if (bj != t)
+        for (int i = 0; i < d; ++i) std::swap(A.a[i][bj], A.a[i][t]), std::swap(V.a[i][bj], V.a[i][t]);
+      const i128 p = A.a[t][t];
+      bool clean = true;
+      for (int i = t + 1; i < d; ++i) {
+        i128 q = floordiv(A.a[i][t], p);
+        if (q != 0)
+          for (int j = 0; j < d; ++j) A.a[i][j] -= q * A.a[t][j], U.a[i][j] -= q * U.a[t][j];
+        if (A.a[i][t] != 0) clean = false;
+      }
+      for (int j = t + 1; j < d; ++j) {
+        i128 q = floordiv(A.a[t][j], p);
+        if (q != 0)
+          for (int i = 0; i < d; ++i) A.a[i][j] -= q * A.a[i][t], V.a[i][j] -= q * V.a[i][t];
+        if (A.a[t][j] != 0) clean = false;
+      }
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+          if (iabs(A.a[i][j]) > LIM || iabs(U.a[i][j]) > LIM || iabs(V.a[i][j]) > LIM) return false;
+      if (!clean) continue;
+      int bad = -1;
+      for (int i = t + 1; i < d && bad < 0; ++i)
+        for (int j = t + 1; j < d; ++j)
+          if (A.a[i][j] % p != 0) {
+            bad = i;
+            break;
+          }
+      if (bad >= 0) {
+        for (int j = 0; j < d; ++j) A.a[t][j] += A.a[bad][j], U.a[t][j] += U.a[bad][j];
+        continue;
+      }
+      break;
+    }
+    if (A.a[t][t] < 0)
+      for (int j = 0; j < d; ++j) A.a[t][j] = -A.a[t][j], U.a[t][j] = -U.a[t][j];
+  }
+  for (int i = 0; i < d; ++i) e[i] = A.a[i][i];
+  // inverses of unimodular U, V: adj * det (det = +-1)
+  i128 du = det(U), dv = det(V);
+  if (iabs(du) != 1 || iabs(dv) != 1) return false;
+  Q = adjugate(U);
+  R = adjugate(V);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Q.a[i][j] *= du, R.a[i][j] *= dv;
+  return true;
+}
+
+int ilog2(int64_t x) {
+  int l = 0;
+  while ((int64_t(1) << l) < x) ++l;
+  return l;
+}
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// W_N^t = exp(-2 pi i t / N) with octant reduction so that cos/sin only see |angle| <= pi/4
+void twiddle(int64_t t, int64_t N, double* re, double* im) {
+  t = (int64_t)mod(t, N);
+  // angle = 2 pi t / N = pi * (8t/N) / 4 ; octant o = floor(8t / N)
+  int64_t o8 = 8 * t;
+  int64_t o = o8 / N;
+  // residual fraction r = 8t/N - o in [0,1); angle = (o + r) * pi/4
+  double r = (double)(o8 - o * N) / (double)N;
+  double c, s;
+  int oo = (int)(o & 7);
+  // reduce to phi in [0, pi/4]
+  double phi = (oo & 1) ? (1.0 - r) * M_PI / 4 : r * M_PI / 4;
+  double cp = cos(phi), sp = sin(phi);
+  // angle = k*pi/4 + (+-)phi, map through octant symmetries
+  switch (oo) {
+    case 0: c = cp; s = sp; break;     // [0, pi/4)
+    case 1: c = sp; s = cp; break;     // [pi/4, pi/2): angle = pi/2 - phi
+    case 2: c = -sp; s = cp; break;    // angle = pi/2 + phi
+    case 3: c = -cp; s = sp; break;    // angle = pi - phi
+    case 4: c = -cp; s = -sp; break;   // angle = pi + phi
+    case 5: c = -sp; s = -cp; break;   // angle = 3pi/2 - phi
+    case 6: c = sp; s = -cp; break;    // angle = 3pi/2 + phi
+    default: c = cp; s = -sp; break;   // angle = 2pi - phi
+  }
+  *re = c;
+  *im = -s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+static int choose_layout(lat_plan* P) {
+  const int d = P->d;
+  std::vector<int> paxes;
+  for (int j = 0; j < d; ++j)
+    if (P->e[j] > 1) paxes.push_back(j);
+  P->dM = (int)paxes.size();
+  for (int j : paxes)
+    if (!is_pow2(P->e[j]))
+      return lat_fail(LAT_ERR_UNSUPPORTED,
+                      "elementary divisor " + std::to_string((long long)P->e[j]) +
+                          " is not a power of two (mixed-radix pattern FFT not built)");
+  if (P->dM == 0) {  // m == 1
+    P->nax = 0;
+    P->ngroups = 0;
+    return LAT_OK;
+  }
+  const int n_c = d * (d + 1) / 2;
+  // shared-memory budgets, sized for binary64 complex (16 B)
+  const int64_t RH_MAX = (n_c == 3) ? 2048 : 1024;          // row half-length
+  const int64_t G_MAX = (n_c == 3) ? 2048 : 1024;           // column group length
+  const int jL = paxes.back();
+  const int64_t eL = P->e[jL];
+  const int lgL = ilog2(eL);
+  // candidate row lengths B (power of two dividing eL, B <= 2*RH_MAX); B = eL means no split
+  int best_groups = 1 << 30;
+  int64_t bestB = -1;
+  std::vector<int64_t> cands;
+  if (eL <= 2 * RH_MAX) cands.push_back(eL);
+  for (int lb = (lgL + 1) / 2; lb < lgL; ++lb) {
+    int64_t B = int64_t(1) << lb;
+    if (B <= 2 * RH_MAX && B >= 2) cands.push_back(B);
+  }
+  for (int64_t B : cands) {
+    std::vector<int64_t> lens;
+    for (size_t i = 0; i + 1 < paxes.size(); ++i) lens.push_back(P->e[paxes[i]]);
+    if (B != eL) lens.push_back(eL / B);
+    // greedy grouping from the left
+    int ng = 0;
+    size_t i = 0;
+    bool ok = true;
+    while (i < lens.size()) {
+      int64_t g = 1;
+      size_t j = i;
+      while (j < lens.size() && g * lens[j] <= G_MAX) g *= lens[j++];
+      if (j == i) {
+        ok = false;
+        break;
+      }
+      ++ng;
+      i = j;
+    }
+    if (!ok) continue;
+    if (ng < best_groups) best_groups = ng, bestB = B;
+  }
+  if (bestB < 0) return lat_fail(LAT_ERR_UNSUPPORTED, "no FFT decomposition fits shared memory");
+  const int64_t B = bestB;
+  // logical axes
+  int na = 0;
+  for (size_t i = 0; i + 1 < paxes.size(); ++i) {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)P->e[paxes[i]];
+    a.snf = paxes[i];
+    a.mult = 1;
+  }
+  P->split = (B != eL);
+  if (P->split) {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)(eL / B);
+    a.snf = jL;
+    a.mult = B;  // k = k2 + B k1
+    P->split_n1 = na - 1;
+    P->split_e = eL;
+    P->split_lo_log2 = (lgL + 1) / 2;
+  }
+  {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)B;
+    a.snf = jL;
+    a.mult = 1;
+  }
+  P->nax = na;
+  for (int i = 0; i < na; ++i) P->ax[i].log2len = ilog2(P->ax[i].len);
+  P->Rlen = (int)B;
+  P->Rh = (int)(B / 2);
+  P->log2Rh = ilog2(P->Rh);
+  P->nrows = P->m / B;
+  // groups
+  P->ngroups = 0;
+  int i = 0;
+  while (i < na - 1) {
+    int64_t g = 1;
+    int j = i;
+    while (j < na - 1 && g * P->ax[j].len <= G_MAX) g *= P->ax[j++].len;
+    LatGroup& G = P->grp[P->ngroups++];
+    G.a0 = i;
+    G.a1 = j;
+    G.G = (int)g;
+    G.outer = 1;
+    for (int t = 0; t < i; ++t) G.outer *= P->ax[t].len;
+    G.inner = 1;
+    for (int t = j; t < na - 1; ++t) G.inner *= P->ax[t].len;
+    G.has_twiddle = P->split && (P->split_n1 >= i && P->split_n1 < j);
+    i = j;
+  }
+  // v contributions
+  for (int t = 0; t < na; ++t) {
+    LatAxis& a = P->ax[t];
+    int j = a.snf;
+    for (int r = 0; r < d; ++r) {
+      i128 c = (i128)(P->ed / P->e[j]) * P->P[r][j];
+      a.cv[r] = (int64_t)mod((i128)a.mult * mod(c, P->ed), P->ed);
+    }
+  }
+  return LAT_OK;
+}
+
+int lat_ensure_tables(lat_plan* P) {
+  if (P->nax == 0 || P->d_tw) return LAT_OK;
+  cudaGetDevice(&P->device);
+  int lg = 1;
+  for (int i = 0; i < P->nax; ++i) lg = std::max(lg, P->ax[i].log2len);
+  P->tw_log2 = lg;
+  const int64_t N = int64_t(1) << lg;
+  std::vector<double2> tw(N);
+  std::vector<float2> twf(N);
+  for (int64_t t = 0; t < N; ++t) {
+    double re, im;
+    twiddle(t, N, &re, &im);
+    tw[t] = make_double2(re, im);
+    twf[t] = make_float2((float)re, (float)im);
+  }
+  cudaError_t err;
+  if ((err = cudaMalloc(&P->d_tw, N * sizeof(double2))) != cudaSuccess ||
+      (err = cudaMalloc(&P->d_twf, N * sizeof(float2))) != cudaSuccess ||
+      (err = cudaMemcpy(P->d_tw, tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(P->d_twf, twf.data(), N * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return lat_fail(LAT_ERR_CUDA, std::string("twiddle upload: ") + cudaGetErrorString(err));
+  if (P->split) {
+    const int64_t e = P->split_e;
+    const int s = P->split_lo_log2;
+    P->stw_lo_n = int64_t(1) << s;
+    P->stw_hi_n = e >> s;
+    std::vector<double2> st(P->stw_hi_n + P->stw_lo_n);
+    std::vector<float2> stf(st.size());
+    for (int64_t j = 0; j < P->stw_hi_n; ++j) {
+      double re, im;
+      twiddle(j << s, e, &re, &im);
+      st[j] = make_double2(re, im);
+    }
+    for (int64_t j = 0; j < P->stw_lo_n; ++j) {
+      double re, im;
+      twiddle(j, e, &re, &im);
+      st[P->stw_hi_n + j] = make_double2(re, im);
+    }
+    for (size_t j = 0; j < st.size(); ++j) stf[j] = make_float2((float)st[j].x, (float)st[j].y);
+    size_t nb = st.size();
+    if ((err = cudaMalloc(&P->d_stw, nb * sizeof(double2))) != cudaSuccess ||
+        (err = cudaMalloc(&P->d_stwf, nb * sizeof(float2))) != cudaSuccess ||
+        (err = cudaMemcpy(P->d_stw, st.data(), nb * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(P->d_stwf, stf.data(), nb * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return lat_fail(LAT_ERR_CUDA, std::string("split twiddle upload: ") + cudaGetErrorString(err));
+  }
+  return LAT_OK;
+}
+
+extern "C" int lattice_plan(const int64_t* Min, int d, lat_plan** out) {
+  if (!Min || !out) return lat_fail(LAT_ERR_ARG, "lattice_plan: NULL argument");
+  *out = nullptr;
+  if (d != 2 && d != 3) return lat_fail(LAT_ERR_DIM, "lattice_plan: d must be 2 or 3");
+  Mat M;
+  M.d = d;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      if (Min[i * d + j] > (int64_t(1) << 40) || Min[i * d + j] < -(int64_t(1) << 40))
+        return lat_fail(LAT_ERR_SIZE, "lattice_plan: |M_ij| > 2^40");
+      M.a[i][j] = Min[i * d + j];
+    }
+  i128 D = det(M);
+  if (D == 0) return lat_fail(LAT_ERR_SINGULAR, "lattice_plan: det M = 0");
+  if (iabs(D) > (((i128)1) << 28)) return lat_fail(LAT_ERR_SIZE, "lattice_plan: m = |det M| > 2^28");
+  Mat Q, R;
+  i128 e[3];
+  if (!smith(M, Q, e, R)) return lat_fail(LAT_ERR_SIZE, "lattice_plan: Smith normal form left the exact range");
+  lat_plan* P = new lat_plan();
+  memset(P, 0, sizeof(lat_plan));
+  P->d = d;
+  P->det = (int64_t)D;
+  P->m = (int64_t)iabs(D);
+  Mat Rinv = adjugate(R);
+  i128 dR = det(R);
+  Mat Qinv = adjugate(Q);
+  i128 dQ = det(Q);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      bool in = i < d && j < d;
+      P->M[i][j] = in ? (int64_t)M.a[i][j] : 0;
+      P->Q[i][j] = in ? (int64_t)Q.a[i][j] : 0;
+      P->R[i][j] = in ? (int64_t)R.a[i][j] : 0;
+      P->Rinv[i][j] = in ? (int64_t)(Rinv.a[i][j] * dR) : 0;
+      P->P[i][j] = in ? (int64_t)(Qinv.a[j][i] * dQ) : 0;  // Q^{-T}
+    }
+  P->ed = 1;
+  for (int j = 0; j < d; ++j) P->e[j] = (int64_t)e[j], P->ed = std::max(P->ed, P->e[j]);
+  for (int j = d; j < 3; ++j) P->e[j] = 1;
+  int rc = choose_layout(P);
+  if (rc != LAT_OK) {
+    lattice_plan_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return LAT_OK;
+}
+
+void lat_graph_cache_free(lat_plan* P);
+
+extern "C" void lattice_plan_destroy(lat_plan* P) {
+  if (!P) return;
+  lat_graph_cache_free(P);
+  if (P->d_tw) cudaFree(P->d_tw);
+  if (P->d_twf) cudaFree(P->d_twf);
+  if (P->d_stw) cudaFree(P->d_stw);
+  if (P->d_stwf) cudaFree(P->d_stwf);
+  delete P;
+}
+
+extern "C" int lattice_plan_info(const lat_plan* P, int64_t* m, int* d_M, int64_t* divisors) {
+  if (!P) return lat_fail(LAT_ERR_ARG, "lattice_plan_info: NULL plan");
+  if (m) *m = P->m;
+  if (d_M) *d_M = P->dM;
+  if (divisors)
+    for (int j = 0; j < P->d; ++j) divisors[j] = P->e[j];
+  return LAT_OK;
+}
+
+// storage slot -> lambda (spatial).  Split axis: lambda = n1 + A * n2.
+static void slot_lambda(const lat_plan* P, int64_t slot, int64_t lam[3]) {
+  lam[0] = lam[1] = lam[2] = 0;
+  int64_t rest = slot;
+  for (int a = P->nax - 1; a >= 0; --a) {
+    int64_t idx = rest % P->ax[a].len;
+    rest /= P->ax[a].len;
+    int64_t smult = 1;
+    if (P->split && a == P->nax - 1) smult = P->ax[P->split_n1].len;  // n2 carries A
+    lam[P->ax[a].snf] += smult * idx;
+  }
+}
+
+extern "C" int lattice_points(const lat_plan* P, int64_t* p) {
+  if (!P || !p) return lat_fail(LAT_ERR_ARG, "lattice_points: NULL argument");
+  const int d = P->d;
+  const int64_t m = P->m;
+  for (int64_t s = 0; s < m; ++s) {
+    int64_t lam[3];
+    slot_lambda(P, s, lam);
+    for (int i = 0; i < d; ++i) {
+      i128 acc = 0;
+      for (int j = 0; j < d; ++j) acc += (i128)P->Rinv[i][j] * lam[j] * (m / P->e[j]);
+      i128 r = mod(acc, m);
+      if (2 * r >= m) r -= m;
+      p[s * d + i] = (int64_t)r;
+    }
+  }
+  return LAT_OK;
+}
+
+// spectral slot of the complex transform (bit-reversed positions on every axis) -> k
+static void slot_k(const lat_plan* P, int64_t slot, int64_t k[3]) {
+  k[0] = k[1] = k[2] = 0;
+  int64_t rest = slot;
+  for (int a = P->nax - 1; a >= 0; --a) {
+    int64_t pos = rest % P->ax[a].len;
+    rest /= P->ax[a].len;
+    int lg = P->ax[a].log2len;
+    int64_t kk = 0;
+    for (int b = 0; b < lg; ++b)
+      if (pos & (int64_t(1) << b)) kk |= int64_t(1) << (lg - 1 - b);
+    k[P->ax[a].snf] += P->ax[a].mult * kk;
+  }
+}
+
+extern "C" int lattice_freqs(const lat_plan* P, int64_t* h) {
+  if (!P || !h) return lat_fail(LAT_ERR_ARG, "lattice_freqs: NULL argument");
+  const int d = P->d;
+  Mat MT;
+  MT.d = d;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) MT.a[i][j] = P->M[j][i];
+  Mat A = adjugate(MT);
+  const i128 D = P->det;
+  for (int64_t s = 0; s < P->m; ++s) {
+    int64_t k[3];
+    slot_k(P, s, k);
+    i128 g[3], u[3], z[3];
+    for (int i = 0; i < d; ++i) {
+      g[i] = 0;
+      for (int j = 0; j < d; ++j) g[i] += (i128)P->R[j][i] * k[j];  // R^T k
+    }
+    for (int i = 0; i < d; ++i) {
+      u[i] = 0;
+      for (int j = 0; j < d; ++j) u[i] += A.a[i][j] * g[j];
+      z[i] = floordiv(2 * u[i] + D, 2 * D);  // floor(u/D + 1/2)
+    }
+    for (int i = 0; i < d; ++i) {
+      i128 acc = g[i];
+      for (int j = 0; j < d; ++j) acc -= MT.a[i][j] * z[j];
+      h[s * d + i] = (int64_t)acc;
+    }
+  }
+  return LAT_OK;
+}

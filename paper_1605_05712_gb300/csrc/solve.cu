@@ -1,0 +1,576 @@
+// solve.cu -- basic_scheme_solve and lattice_fft: workspace layout, launch geometry and the
+// CUDA-graph WHILE loop that runs Algorithm 1 (Sec. 3.2, arXiv 1605.05712) without a host
+// round trip per iteration.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace {
+
+const size_t kMaxSmem = 232448;       // sm_100/sm_103 opt-in dynamic shared memory per block
+const size_t kRowSmemTarget = 64 * 1024;
+const size_t kColSmemMax = 200 * 1024;
+const int kThreads = 256;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  return n;
+}
+
+int ensure_attrs() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (done[dev]) return 0;
+  int rc = lat_kernel_attrs(kMaxSmem);
+  if (rc == 0) done[dev] = true;
+  return rc;
+}
+
+LatDev make_dev(const lat_plan* P, bool fp32) {
+  LatDev dv;
+  memset(&dv, 0, sizeof(dv));
+  dv.d = P->d;
+  dv.n_c = P->d * (P->d + 1) / 2;
+  dv.nax = P->nax;
+  dv.Rlen = P->Rlen;
+  dv.Rh = P->Rh;
+  dv.log2Rh = P->log2Rh;
+  dv.m = P->m;
+  dv.nrows = P->nrows;
+  dv.ed = P->ed;
+  dv.ed_mask = ((P->ed & (P->ed - 1)) == 0) ? P->ed - 1 : -1;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) dv.MT[i][j] = P->M[j][i];
+  for (int a = 0; a < P->nax; ++a) {
+    dv.ax_len[a] = P->ax[a].len;
+    dv.ax_log2[a] = P->ax[a].log2len;
+    for (int r = 0; r < 3; ++r) dv.ax_cv[a][r] = P->ax[a].cv[r];
+  }
+  dv.split = P->split;
+  dv.split_n1 = P->split_n1;
+  dv.split_lo_log2 = P->split_lo_log2;
+  dv.split_e = P->split_e;
+  dv.stw_hi_n = P->stw_hi_n;
+  dv.tw_log2 = P->tw_log2;
+  dv.tw = fp32 ? (const void*)P->d_twf : (const void*)P->d_tw;
+  dv.stw = fp32 ? (const void*)P->d_stwf : (const void*)P->d_stw;
+  return dv;
+}
+
+struct Geometry {
+  int rpc, row_blocks;
+  size_t row_smem;
+  int w[LAT_MAX_GROUPS], wN[LAT_MAX_GROUPS];
+  int64_t tiles_main[LAT_MAX_GROUPS], tiles_nyq[LAT_MAX_GROUPS];
+  size_t col_smem[LAT_MAX_GROUPS];
+};
+
+// row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile
+int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g) {
+  const int nsm = num_sms();
+  const int64_t nrows = P->nrows;
+  const int row_len = nyq ? P->Rh : P->Rlen;
+  auto rsm = [&](int rpc) {
+    return ((size_t)n_f * rpc * row_len + (nyq ? (size_t)n_f * rpc : 0)) * cs + 32 * sizeof(double);
+  };
+  int rpc = 1;
+  while (nrows % (2 * rpc) == 0 && rsm(2 * rpc) <= kRowSmemTarget && nrows / (2 * rpc) >= 2 * nsm) rpc *= 2;
+  g.rpc = rpc;
+  g.row_blocks = (int)(nrows / rpc);
+  g.row_smem = rsm(rpc);
+  if (g.row_smem > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
+  const int wmin = (cs == 16) ? 2 : 4;
+  for (int k = 0; k < P->ngroups; ++k) {
+    const LatGroup& G = P->grp[k];
+    const int64_t ic = G.inner * row_slots;
+    int64_t w = std::min<int64_t>(32, ic);
+    auto csm = [&](int64_t ww) { return (size_t)n_f * G.G * ww * cs; };
+    while (w > 1 && (csm(w) > kColSmemMax || (G.outer * (ic / w) < 2 * nsm && w > wmin))) w /= 2;
+    if (csm(w) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column group does not fit in shared memory");
+    const int64_t wN = std::min<int64_t>(w, G.inner);
+    g.w[k] = (int)w;
+    g.wN[k] = (int)wN;
+    g.tiles_main[k] = ic / w;
+    g.tiles_nyq[k] = nyq ? G.inner / wN : 0;
+    g.col_smem[k] = csm(w);
+  }
+  return LAT_OK;
+}
+
+struct Work {
+  size_t T, TN, Dtab, Ctab, partials, scal, hist, total;
+  size_t t_per_lc, tn_per_lc;
+};
+const int kMaxPhases = 256;
+const size_t kScalBytes = 256;  // per load case
+
+Work layout(const lat_plan* P, int n_loads, int precision) {
+  const int n_c = P->d * (P->d + 1) / 2;
+  const size_t cs = (precision == LAT_MIXED) ? 8 : 16;
+  Work w;
+  w.t_per_lc = (size_t)n_c * (P->m / 2) * cs;
+  w.tn_per_lc = (size_t)n_c * P->nrows * cs;
+  size_t off = 0;
+  w.T = off;
+  off = align256(off + n_loads * w.t_per_lc);
+  w.TN = off;
+  off = align256(off + n_loads * w.tn_per_lc);
+  w.Dtab = off;
+  off = align256(off + (size_t)kMaxPhases * 36 * sizeof(double));
+  w.Ctab = off;
+  off = align256(off + (size_t)kMaxPhases * 36 * sizeof(double));
+  w.partials = off;
+  off = align256(off + (size_t)std::max<int64_t>(P->nrows, 1024 * 6) * sizeof(double));
+  w.scal = off;
+  off = align256(off + (size_t)n_loads * kScalBytes);
+  w.hist = off;
+  off = align256(off + (size_t)n_loads * LAT_HIST_CAP * sizeof(double));
+  w.total = off;
+  return w;
+}
+
+// tensor-component form of a 6x6 Voigt matrix: out[I][J] = V[vi][vj] * (J shear ? 2 : 1)
+void voigt_to_tc(const double* V, int d, double* out) {
+  static const int idx3[6] = {0, 1, 2, 3, 4, 5};
+  static const int idx2[3] = {0, 1, 5};
+  const int n_c = d * (d + 1) / 2;
+  const int* vi = d == 3 ? idx3 : idx2;
+  for (int I = 0; I < n_c; ++I)
+    for (int J = 0; J < n_c; ++J) out[I * n_c + J] = V[vi[I] * 6 + vi[J]] * (J >= d ? 2.0 : 1.0);
+}
+
+#define CK(x)                                                                        \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string(#x) + ": " +   \
+                                                             cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename Real>
+void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, cudaStream_t st) {
+  // forward over mid groups (innermost first), Gamma group, inverse mid groups
+  for (int k = P->ngroups - 1; k >= 0; --k) {
+    ColArgs c = base;
+    const LatGroup& G = P->grp[k];
+    c.mode = (k == 0) ? COL_GAMMA : COL_FWD;
+    c.gidx = k;
+    c.a0 = G.a0;
+    c.a1 = G.a1;
+    c.G = G.G;
+    c.outer = G.outer;
+    c.inner = G.inner;
+    c.has_twiddle = G.has_twiddle;
+    c.w = g.w[k];
+    c.wN = g.wN[k];
+    c.tiles_main = g.tiles_main[k];
+    c.tiles_nyq = g.tiles_nyq[k];
+    launch_col_pass<Real>(dv, c, kThreads, g.col_smem[k], st);
+  }
+  for (int k = 1; k < P->ngroups; ++k) {
+    ColArgs c = base;
+    const LatGroup& G = P->grp[k];
+    c.mode = COL_INV;
+    c.gidx = k;
+    c.a0 = G.a0;
+    c.a1 = G.a1;
+    c.G = G.G;
+    c.outer = G.outer;
+    c.inner = G.inner;
+    c.has_twiddle = G.has_twiddle;
+    c.w = g.w[k];
+    c.wN = g.wN[k];
+    c.tiles_main = g.tiles_main[k];
+    c.tiles_nyq = g.tiles_nyq[k];
+    launch_col_pass<Real>(dv, c, kThreads, g.col_smem[k], st);
+  }
+}
+
+template <typename Real>
+int solve_one(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs ra, ColArgs ca, int maxit,
+              cudaStream_t st) {
+  const bool gamma_in_row = (P->nax == 1);
+  // prologue: tau^(0) from eps^(0), forward transform, Gamma, first inverse column passes
+  RowArgs first = ra;
+  first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
+  launch_row_pass<Real>(dv, first, g.row_blocks, kThreads, g.row_smem, st);
+  CK(cudaGetLastError());
+  ColArgs c0 = ca;
+  c0.done = nullptr;
+  enqueue_columns<Real>(dv, P, g, c0, st);
+  CK(cudaGetLastError());
+  // WHILE loop: body = row pass (update + residual + convergence) + column passes
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  RowArgs full = ra;
+  full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (ra.flags & ROW_INCREMENT);
+  full.it.cond = (unsigned long long)handle;
+  launch_row_pass<Real>(dv, full, g.row_blocks, kThreads, g.row_smem, cap);
+  enqueue_columns<Real>(dv, P, g, ca, cap);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cap, &captured);
+  cudaStreamDestroy(cap);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return lat_fail(LAT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, st);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+  (void)maxit;
+  return LAT_OK;
+}
+
+}  // namespace
+
+void lat_graph_cache_free(lat_plan* P) { (void)P; }
+
+extern "C" size_t lattice_workspace_bytes(const lat_plan* P, int n_loads, int precision) {
+  if (!P || n_loads <= 0) return 0;
+  return layout(P, n_loads, precision).total;
+}
+
+extern "C" size_t lattice_fft_workspace_bytes(const lat_plan* P, int n_fields) {
+  (void)P;
+  (void)n_fields;
+  return 0;
+}
+
+extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,
+                                  const double* C0, const double* E, int n_loads, double tol, int maxit,
+                                  const lat_solve_opts* opts, double* eps, double* sigma, double* sigma_bar,
+                                  int* iters, double* resid, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+  if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: NULL argument");
+  if (n_phases < 1 || n_phases > kMaxPhases) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: n_phases not in 1..256");
+  if (n_loads < 1 || maxit < 0 || !(tol >= 0)) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: bad n_loads/maxit/tol");
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precision != LAT_FP64 && o.precision != LAT_MIXED) return lat_fail(LAT_ERR_ARG, "bad precision");
+  if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
+  const double lam0 = C0[0], mu0 = C0[1];
+  if (!(mu0 > 0) || !(lam0 + 2 * mu0 > 0)) return lat_fail(LAT_ERR_ARG, "C0 must have mu0 > 0 and lam0 + 2 mu0 > 0");
+  const Work wl = layout(P, n_loads, o.precision);
+  if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = P->d, n_c = d * (d + 1) / 2;
+  const int64_t m = P->m;
+  char* ws = (char*)workspace;
+  // material tables
+  std::vector<double> D(n_phases * n_c * n_c), Cc(n_phases * n_c * n_c);
+  double C0v[36];
+  memset(C0v, 0, sizeof(C0v));
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) C0v[i * 6 + j] = lam0;
+    C0v[i * 6 + i] = lam0 + 2 * mu0;
+    C0v[(i + 3) * 6 + (i + 3)] = mu0;
+  }
+  double c0tc[36];
+  voigt_to_tc(C0v, d, c0tc);
+  for (int p = 0; p < n_phases; ++p) {
+    voigt_to_tc(stiffness + 36 * p, d, &Cc[p * n_c * n_c]);
+    for (int k = 0; k < n_c * n_c; ++k) D[p * n_c * n_c + k] = Cc[p * n_c * n_c + k] - c0tc[k];
+  }
+  CK(cudaMemcpyAsync(ws + wl.Dtab, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ws + wl.Ctab, Cc.data(), Cc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_loads * kScalBytes, st));
+
+  const bool fp32 = (o.precision == LAT_MIXED);
+  const size_t cs = fp32 ? 8 : 16;
+  const LatDev dv = make_dev(P, fp32);
+  Geometry geo;
+  memset(&geo, 0, sizeof(geo));
+  if (P->nax > 0) {
+    int rc = geometry(P, n_c, cs, P->Rh, true, geo);
+    if (rc != LAT_OK) return rc;
+  }
+  const int eff_blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (m + 255) / 256));
+  for (int lc = 0; lc < n_loads; ++lc) {
+    char* sc = ws + wl.scal + (size_t)lc * kScalBytes;
+    double* eps_lc = eps + (size_t)lc * n_c * m;
+    const double* E_lc = E + (size_t)lc * n_c;
+    double nE2 = 0;
+    for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * E_lc[c] * E_lc[c];
+    const double norm0 = nE2 > 0 ? sqrt((double)m * nE2) : 1.0;
+    if (!o.warm_start) launch_fill(eps_lc, n_c, m, E_lc, st);
+    CK(cudaGetLastError());
+    if (P->nax > 0 && maxit > 0) {
+      RowArgs ra;
+      memset(&ra, 0, sizeof(ra));
+      ra.rpc = geo.rpc;
+      ra.eps = eps_lc;
+      ra.phase = phase;
+      ra.T = ws + wl.T + lc * wl.t_per_lc;
+      ra.TN = ws + wl.TN + lc * wl.tn_per_lc;
+      ra.mat.Dtab = (const double*)(ws + wl.Dtab);
+      for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E_lc[c] : 0.0;
+      ra.mat.lam0 = lam0;
+      ra.mat.mu0 = mu0;
+      ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
+      ra.it.partials = (double*)(ws + wl.partials);
+      ra.it.counter = (unsigned*)(sc + 0);
+      ra.it.done = (int*)(sc + 4);
+      ra.it.iter = (int*)(sc + 8);
+      ra.it.last_r = (double*)(sc + 16);
+      ra.it.hist = (double*)(ws + wl.hist) + (size_t)lc * LAT_HIST_CAP;
+      ra.it.norm0 = norm0;
+      ra.it.tol = tol;
+      ra.it.maxit = maxit;
+      ColArgs ca;
+      memset(&ca, 0, sizeof(ca));
+      ca.row_slots = P->Rh;
+      ca.has_nyq = 1;
+      ca.n_f = n_c;
+      ca.T = ra.T;
+      ca.TN = ra.TN;
+      ca.Tin = nullptr;
+      ca.scale = 1.0;
+      ca.mat = ra.mat;
+      ca.done = ra.it.done;
+      int rc = fp32 ? solve_one<float>(P, dv, geo, ra, ca, maxit, st) : solve_one<double>(P, dv, geo, ra, ca, maxit, st);
+      if (rc != LAT_OK) return rc;
+    }
+    EffArgs ea;
+    ea.eps = eps_lc;
+    ea.sigma = sigma ? sigma + (size_t)lc * n_c * m : nullptr;
+    ea.phase = phase;
+    ea.Ctab = (const double*)(ws + wl.Ctab);
+    ea.partials = (double*)(ws + wl.partials);
+    ea.counter = (unsigned*)(sc + 24);
+    ea.sigma_bar = (double*)(sc + 32);
+    launch_eff(dv, ea, eff_blocks, st);
+    CK(cudaGetLastError());
+  }
+  // scalars back to the host
+  std::vector<char> scal((size_t)n_loads * kScalBytes);
+  CK(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hist;
+  if (o.resid_history && maxit > 0) {
+    hist.resize((size_t)n_loads * LAT_HIST_CAP);
+    CK(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  int status = LAT_OK;
+  for (int lc = 0; lc < n_loads; ++lc) {
+    const char* sc = scal.data() + (size_t)lc * kScalBytes;
+    int it = *(const int*)(sc + 8);
+    double r = *(const double*)(sc + 16);
+    if (P->nax == 0) {  // m = 1: one iteration reproduces E exactly
+      it = maxit > 0 ? 1 : 0;
+      r = 0.0;
+    } else if (maxit == 0) {
+      r = NAN;
+    }
+    if (iters) iters[lc] = it;
+    if (resid) resid[lc] = r;
+    if (sigma_bar)
+      for (int c = 0; c < n_c; ++c) sigma_bar[lc * n_c + c] = ((const double*)(sc + 32))[c];
+    if (o.resid_history && maxit > 0) {
+      if (P->nax == 0) o.resid_history[(size_t)lc * maxit] = 0.0;
+      for (int k = 0; k < std::min(it, std::min(maxit, LAT_HIST_CAP)) && P->nax > 0; ++k)
+        o.resid_history[(size_t)lc * maxit + k] = hist[(size_t)lc * LAT_HIST_CAP + k];
+    }
+    int s = LAT_OK;
+    if (!isfinite(r) && maxit > 0) s = LAT_DIVERGED;
+    else if (!(r < tol)) s = LAT_NOT_CONVERGED;
+    status = std::max(status, s);
+  }
+  return status;
+}
+
+extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,
+                                  const double* C0, const double* E, int precision, int n_reps, double* eps,
+                                  void* workspace, size_t workspace_bytes, void* stream, float* ms_out, int* n_out) {
+  if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace || !ms_out || n_reps < 1)
+    return lat_fail(LAT_ERR_ARG, "lattice_pass_times: bad argument");
+  if (P->nax == 0) return lat_fail(LAT_ERR_ARG, "lattice_pass_times: m = 1 has no passes");
+  // one cold solve with maxit = 1 sets up tables, workspace and T; then time plain launches
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  o.precision = precision;
+  int rc = basic_scheme_solve(P, phase, n_phases, stiffness, C0, E, 1, 0.0, 1, &o, eps, nullptr, nullptr, nullptr,
+                              nullptr, workspace, workspace_bytes, stream);
+  if (rc < 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = P->d, n_c = d * (d + 1) / 2;
+  const Work wl = layout(P, 1, precision);
+  char* ws = (char*)workspace;
+  const bool fp32 = (precision == LAT_MIXED);
+  const LatDev dv = make_dev(P, fp32);
+  Geometry geo;
+  memset(&geo, 0, sizeof(geo));
+  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo)) != LAT_OK) return rc;
+  char* sc = ws + wl.scal;
+  RowArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0);
+  ra.rpc = geo.rpc;
+  ra.eps = eps;
+  ra.phase = phase;
+  ra.T = ws + wl.T;
+  ra.TN = ws + wl.TN;
+  ra.mat.Dtab = (const double*)(ws + wl.Dtab);
+  for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E[c] : 0.0;
+  ra.mat.lam0 = C0[0];
+  ra.mat.mu0 = C0[1];
+  ra.it.partials = (double*)(ws + wl.partials);
+  ra.it.counter = (unsigned*)(sc + 0);
+  ra.it.done = (int*)(sc + 4);
+  ra.it.iter = (int*)(sc + 8);
+  ra.it.last_r = (double*)(sc + 16);
+  ra.it.hist = (double*)(ws + wl.hist);
+  ra.it.norm0 = 1.0;
+  ra.it.tol = 0.0;
+  ra.it.maxit = 1 << 30;
+  ra.it.cond = 0;  // plain launches: the kernel skips the graph condition when cond == 0
+  CK(cudaMemsetAsync(sc, 0, kScalBytes, st));
+  ColArgs ca;
+  memset(&ca, 0, sizeof(ca));
+  ca.row_slots = P->Rh;
+  ca.has_nyq = 1;
+  ca.n_f = n_c;
+  ca.T = ra.T;
+  ca.TN = ra.TN;
+  ca.scale = 1.0;
+  ca.mat = ra.mat;
+  const int nk = 1 + 2 * P->ngroups - 1 + (P->ngroups == 0 ? 1 : 0);
+  std::vector<cudaEvent_t> ev(2 * nk);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  std::vector<double> acc(nk, 0.0);
+  for (int rep = 0; rep < n_reps; ++rep) {
+    int k = 0;
+    CK(cudaEventRecord(ev[2 * k], st));
+    if (fp32) launch_row_pass<float>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
+    else launch_row_pass<double>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
+    CK(cudaEventRecord(ev[2 * k + 1], st));
+    ++k;
+    auto one = [&](int g, int mode) {
+      ColArgs c = ca;
+      const LatGroup& G = P->grp[g];
+      c.mode = mode;
+      c.gidx = g;
+      c.a0 = G.a0;
+      c.a1 = G.a1;
+      c.G = G.G;
+      c.outer = G.outer;
+      c.inner = G.inner;
+      c.has_twiddle = G.has_twiddle;
+      c.w = geo.w[g];
+      c.wN = geo.wN[g];
+      c.tiles_main = geo.tiles_main[g];
+      c.tiles_nyq = geo.tiles_nyq[g];
+      cudaEventRecord(ev[2 * k], st);
+      if (fp32) launch_col_pass<float>(dv, c, kThreads, geo.col_smem[g], st);
+      else launch_col_pass<double>(dv, c, kThreads, geo.col_smem[g], st);
+      cudaEventRecord(ev[2 * k + 1], st);
+      ++k;
+    };
+    for (int g = P->ngroups - 1; g >= 0; --g) one(g, g == 0 ? COL_GAMMA : COL_FWD);
+    for (int g = 1; g < P->ngroups; ++g) one(g, COL_INV);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < k; ++j) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]));
+      acc[j] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  const int nkern = 1 + (P->ngroups > 0 ? 2 * P->ngroups - 1 : 0);
+  for (int j = 0; j < 8; ++j) ms_out[j] = j < nkern ? (float)(acc[j] / n_reps) : 0.0f;
+  if (n_out) *n_out = nkern;
+  return LAT_OK;
+}
+
+extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int n_fields, int inverse,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  (void)workspace;
+  (void)workspace_bytes;
+  if (!P || !in || !out || n_fields < 1) return lat_fail(LAT_ERR_ARG, "lattice_fft: bad argument");
+  if (in == out) return lat_fail(LAT_ERR_ARG, "lattice_fft: in and out must not overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t m = P->m;
+  if (P->nax == 0) {
+    CK(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return LAT_OK;
+  }
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
+  const LatDev dv = make_dev(P, false);
+  Geometry geo;
+  int rc = geometry(P, 1, 16, P->Rlen, false, geo);
+  if (rc != LAT_OK) return rc;
+  const double inv_m = 1.0 / (double)m;
+  for (int f = 0; f < n_fields; ++f) {
+    const double2* fin = (const double2*)in + (size_t)f * m;
+    double2* fout = (double2*)out + (size_t)f * m;
+    ColArgs base;
+    memset(&base, 0, sizeof(base));
+    base.row_slots = P->Rlen;
+    base.has_nyq = 0;
+    base.n_f = 1;
+    base.T = fout;
+    base.TN = nullptr;
+    base.scale = 1.0;
+    auto col = [&](int k, int mode, const void* tin, double scale) {
+      ColArgs c = base;
+      const LatGroup& G = P->grp[k];
+      c.mode = mode;
+      c.gidx = k;
+      c.a0 = G.a0;
+      c.a1 = G.a1;
+      c.G = G.G;
+      c.outer = G.outer;
+      c.inner = G.inner;
+      c.has_twiddle = G.has_twiddle;
+      c.w = geo.w[k];
+      c.wN = geo.wN[k];
+      c.tiles_main = geo.tiles_main[k];
+      c.tiles_nyq = 0;
+      c.Tin = tin;
+      c.scale = scale;
+      launch_col_pass<double>(dv, c, kThreads, geo.col_smem[k], st);
+    };
+    if (!inverse) {
+      launch_row_complex<double>(dv, fin, fout, 1, 0, P->ngroups == 0 ? inv_m : 1.0, geo.rpc, kThreads,
+                                 geo.row_smem, st);
+      for (int k = P->ngroups - 1; k >= 0; --k) col(k, COL_FWD, nullptr, k == 0 ? inv_m : 1.0);
+    } else {
+      for (int k = 0; k < P->ngroups; ++k) col(k, COL_INV, k == 0 ? (const void*)fin : nullptr, 1.0);
+      launch_row_complex<double>(dv, P->ngroups == 0 ? (const void*)fin : (const void*)fout, fout, 1, 1, 1.0,
+                                 geo.rpc, kThreads, geo.row_smem, st);
+    }
+    CK(cudaGetLastError());
+  }
+  return LAT_OK;
+}

@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: the binary64 path must agree with the oracle to 1e-10 relative
+(max |difference| / max |value| per field); residual histories likewise; the
+iteration count of a converged solve must match exactly unless the oracle's
+residual at the stopping iteration lies within 1e-6 relative of tol.
+"""
+import numpy as np
+import pytest
+
+from oracle import elasticity as el
+from oracle.lattice import Lattice
+from oracle.scheme import basic_scheme
+from oracle.transform import dft_fast, dft_naive
+from paper_1605_05712_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def _index(rows):
+    return {tuple(r): i for i, r in enumerate(rows.tolist())}
+
+
+def to_oracle_order(plan_pts, lat):
+    """perm[i] = oracle index of plan slot i (matching exact point numerators)."""
+    idx = _index(lat.p)
+    return np.array([idx[tuple(p)] for p in plan_pts.tolist()])
+
+
+def stiff_tensors(voigts, d):
+    return np.array([el.voigt6_to_tensor(v, d) for v in voigts])
+
+
+def comps_to_tensor(comps, d):
+    # (n_c, m) -> (m, d, d)
+    return el.comps_to_sym(np.asarray(comps).T, d)
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+FFT_MATS = [[[1, 0], [0, 1]], [[2, 0], [0, 1]], [[8, -4], [2, 7]], [[4, 4], [-4, 4]], [[16, 0], [4, 8]],
+            [[64, 1], [0, 64]], [[512, 16], [0, 512]], [[512, 1], [0, 512]], [[64, 0], [0, 64]],
+            [[8, 0, 0], [0, 8, 0], [0, 0, 8]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[4, 0, 0], [0, 8, 0], [0, 0, 1]],
+            [[16, 4, 0], [0, 16, 4], [0, 0, 16]], [[64, 0, 0], [0, 64, 0], [0, 0, 64]],
+            [[128, 1, 0], [0, 128, 1], [0, 0, 64]]]
+
+
+@pytest.mark.parametrize("M", FFT_MATS)
+def test_lattice_fft_matches_oracle(cuda, M):
+    import torch
+    from paper_1605_05712_gb300 import lattice_fft, lattice_plan
+    P = lattice_plan(M)
+    L = Lattice(M)
+    perm = to_oracle_order(P.points(), L)
+    hidx = _index(L.h)
+    hperm = np.array([hidx[tuple(h)] for h in P.freqs().tolist()])
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, P.m)) + 1j * rng.standard_normal((2, P.m))
+    X = lattice_fft(P, torch.from_numpy(x).to(cuda)).cpu().numpy()
+    a = np.empty((P.m, 2), dtype=complex)
+    a[perm] = x.T
+    ref = (dft_naive(L, a) if L.m <= 512 else dft_fast(L, a))[hperm].T
+    assert relerr(X, ref) < 1e-12
+    back = lattice_fft(P, torch.from_numpy(X).to(cuda), inverse=True).cpu().numpy()
+    assert relerr(back, x) < 1e-12
+
+
+def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=None, cuda=None):
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan(M)
+    L = Lattice(M)
+    d = L.d
+    ph_plan = phase_fn(P.points(), P.m)
+    ph_or = phase_fn(L.p, L.m)
+    perm = to_oracle_order(P.points(), L)
+    assert np.array_equal(ph_plan, ph_or[perm])
+    E = np.atleast_2d(E)
+    eps0 = None
+    if warm is not None:
+        eps0 = torch.from_numpy(np.ascontiguousarray(warm)).to(cuda)
+    g = basic_scheme_solve(P, torch.from_numpy(ph_plan).to(cuda), voigts, C0, E, tol=tol, maxit=maxit,
+                           boundary=boundary, history=True, want_sigma=True, eps0=eps0)
+    S = stiff_tensors(voigts, d)
+    outs = []
+    for lc in range(E.shape[0]):
+        Et = el.comps_to_sym(E[lc], d)
+        w0 = None
+        if warm is not None:
+            w0 = np.empty((L.m, d, d))
+            w0[perm] = comps_to_tensor(warm[lc], d)
+        o = basic_scheme(L, ph_or, S, C0, Et, tol=tol, maxit=maxit, eps0=w0, boundary=("zero" if boundary == "zero" else "literal"))
+        outs.append(o)
+    return P, L, perm, g, outs
+
+
+def check_pair(P, L, perm, g, outs, d, rtol=RTOL, check_iters=True, tol=0.0):
+    for lc, o in enumerate(outs):
+        eg = comps_to_tensor(g["eps"][lc].cpu().numpy(), d)
+        assert relerr(eg, o["eps"][perm]) < rtol, "strain field"
+        sg = comps_to_tensor(g["sigma"][lc].cpu().numpy(), d)
+        assert relerr(sg, o["sigma"][perm]) < rtol, "stress field"
+        sb = el.comps_to_sym(g["sigma_bar"][lc], d)
+        assert relerr(sb, o["sigma_bar"]) < rtol, "mean stress"
+        if check_iters:
+            if int(g["iters"][lc]) != o["iters"]:
+                h = o["history"]
+                assert tol > 0 and abs(h[min(len(h), int(g["iters"][lc])) - 1] - tol) < 1e-6 * tol
+        n = min(len(g["history"][lc]), len(o["history"]))
+        hg, ho = np.array(g["history"][lc][:n]), np.array(o["history"][:n])
+        assert np.all(np.abs(hg - ho) <= 1e-9 * np.maximum(ho, 1e-14) + 1e-15), "residual history"
+
+
+LAM2 = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(10.0, 10.0)]
+
+
+def laminate(n_int):
+    return lambda p, m: synth.laminate_phase(p, m, n_int)
+
+
+def inclusions(seed, d, n, vf):
+    incl = synth.random_inclusions(seed, d, n, vf)
+    return lambda p, m: synth.inclusions_phase(p, m, incl)
+
+
+SOLVE_2D = [[[1, 0], [0, 1]], [[2, 0], [0, 1]], [[2, 1], [0, 2]], [[8, -4], [2, 7]], [[4, 4], [-4, 4]],
+            [[16, 0], [4, 8]], [[64, 1], [0, 64]], [[64, 32], [0, 1]], [[32, 0], [0, 64]], [[256, 16], [0, 256]],
+            [[128, 1], [0, 128]], [[4096, 12288], [0, 1]], [[2048, 0], [0, 4]]]
+
+
+@pytest.mark.parametrize("M", SOLVE_2D)
+def test_solve_fp64_fixed_iterations_2d(cuda, M):
+    E = np.array([[1.0, 0.0, 0.0], [0.3, -0.2, 0.4]])
+    out = run_pair(M, inclusions(3, 2, 3, 0.3), LAM2, (5.5, 5.5), E, tol=0.0, maxit=7, cuda=cuda)
+    check_pair(*out, d=2)
+
+
+SOLVE_3D = [[[2, 0, 0], [0, 2, 0], [0, 0, 2]], [[8, 0, 0], [0, 8, 0], [0, 0, 8]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]],
+            [[4, 0, 0], [0, 8, 0], [0, 0, 1]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]],
+            [[64, 0, 0], [0, 64, 0], [0, 0, 32]], [[32, 1, 0], [0, 32, 1], [0, 0, 64]]]
+
+
+@pytest.mark.parametrize("M", SOLVE_3D)
+def test_solve_fp64_fixed_iterations_3d(cuda, M):
+    E = np.array([[1.0, 0.0, 0.0, 0.0, 0.0, 0.0], [0.1, -0.3, 0.2, 0.25, -0.15, 0.4]])
+    voigts = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(10.0, 10.0), synth.iso_voigt(3.0, 0.5)]
+
+    def ph(p, m):
+        a = inclusions(5, 3, 2, 0.2)(p, m)
+        b = inclusions(9, 3, 1, 0.1)(p, m)
+        return np.where(b == 1, 2, a).astype(np.uint8)
+    out = run_pair(M, ph, voigts, (5.5, 5.5), E, tol=0.0, maxit=5, cuda=cuda)
+    check_pair(*out, d=3)
+
+
+@pytest.mark.parametrize("M", [[[64, 0], [0, 64]], [[512, 16], [0, 512]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]]])
+def test_solve_fp64_converged(cuda, M):
+    d = len(M)
+    n_c = d * (d + 1) // 2
+    E = np.zeros((1, n_c))
+    E[0, 0] = 1.0
+    ph = laminate([1, 3]) if d == 2 else inclusions(2, 3, 3, 0.25)
+    out = run_pair(M, ph, LAM2, (5.5, 5.5), E, tol=1e-8, maxit=500, cuda=cuda)
+    check_pair(*out, d=d, tol=1e-8)
+    assert out[3]["status"] == 0
+
+
+def test_boundary_zero_option(cuda):
+    out = run_pair([[16, 2], [0, 8]], inclusions(4, 2, 2, 0.3), LAM2, (5.5, 5.5), np.array([[0.2, 1.0, 0.3]]),
+                   tol=0.0, maxit=6, boundary="zero", cuda=cuda)
+    check_pair(*out, d=2)
+
+
+def test_warm_start_continues_the_iteration(cuda):
+    M = [[32, 4], [0, 16]]
+    P_L = Lattice(M)
+    from paper_1605_05712_gb300 import lattice_plan
+    P = lattice_plan(M)
+    perm = to_oracle_order(P.points(), P_L)
+    ph = inclusions(8, 2, 2, 0.3)
+    E = np.array([[1.0, 0.5, -0.25]])
+    S = stiff_tensors(LAM2, 2)
+    o3 = basic_scheme(P_L, ph(P_L.p, P_L.m), S, (5.5, 5.5), el.comps_to_sym(E[0], 2), tol=0.0, maxit=3)
+    warm = el.sym_to_comps(o3["eps"][perm]).T[None]
+    out = run_pair(M, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=4, warm=warm, cuda=cuda)
+    o7 = basic_scheme(P_L, ph(P_L.p, P_L.m), S, (5.5, 5.5), el.comps_to_sym(E[0], 2), tol=0.0, maxit=7)
+    g = out[3]
+    eg = comps_to_tensor(g["eps"][0].cpu().numpy(), 2)
+    assert relerr(eg, o7["eps"][perm]) < RTOL
+
+
+def test_edge_cases(cuda):
+    import torch
+    from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
+    P = lattice_plan([[16, 0], [4, 8]])
+    ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 1])).to(cuda)
+    # maxit = 0: eps = E, no iteration
+    g = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), np.array([[1.0, 2.0, 3.0]]), tol=1e-8, maxit=0)
+    assert int(g["iters"][0]) == 0 and g["status"] == 1
+    e = g["eps"][0].cpu().numpy()
+    assert np.all(e[0] == 1.0) and np.all(e[1] == 2.0) and np.all(e[2] == 3.0)
+    # E = 0: the solution is zero
+    g = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), np.zeros((1, 3)), tol=1e-8, maxit=10)
+    assert np.abs(g["eps"].cpu().numpy()).max() == 0.0 and g["status"] == 0
+    # invalid inputs are reported, not run
+    with pytest.raises(LatticeError):
+        lattice_plan([[2, 4], [1, 2]])          # singular
+    with pytest.raises(LatticeError):
+        lattice_plan([[3, 0], [0, 5]])          # odd divisor: mixed-radix FFT not built
+    with pytest.raises(LatticeError):
+        basic_scheme_solve(P, ph, LAM2, (1.0, -1.0), np.ones((1, 3)), tol=1e-8, maxit=3)   # mu0 <= 0
+
+
+def test_aligned_laminate_config1_matches_analytic(cuda):
+    # 2-D rank-1 lattice M = [[4096, 12288], [0, 1]]: all frequencies parallel to (1,3); exact laminate
+    import torch
+    from oracle import analytic as an
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan(synth.LATTICES["laminate4096_aligned"])
+    ph = synth.laminate_phase(P.points(), P.m, [1, 3])
+    E = np.array([[1.0, 0.0, 0.0]])
+    g = basic_scheme_solve(P, torch.from_numpy(ph).to(cuda), LAM2, synth.c0_mean_extremes([1, 10], [1, 10]), E,
+                           tol=1e-14, maxit=100)
+    S = stiff_tensors(LAM2, 2)
+    e1, e2, sb = an.laminate_fields(S[0], S[1], 0.5, np.array([1.0, 3.0]), el.comps_to_sym(E[0], 2))
+    ex = np.where(ph[:, None, None] == 0, e1, e2)
+    assert relerr(comps_to_tensor(g["eps"][0].cpu().numpy(), 2), ex) < 1e-12
+    assert relerr(el.comps_to_sym(g["sigma_bar"][0], 2), sb) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["grid512", "rank1_262144", "rank2_262144"])
+def test_full_size_262144_fixed_iterations(cuda, name):
+    # the benchmark workload: laminate n = (1,3), m = 262144, three unit load cases, compared field-wise
+    E = np.eye(3)
+    E[2, 2] = 0.5
+    out = run_pair(synth.LATTICES[name], laminate([1, 3]), LAM2, (5.5, 5.5), E, tol=0.0, maxit=4, cuda=cuda)
+    check_pair(*out, d=2)
