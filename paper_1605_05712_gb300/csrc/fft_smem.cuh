@@ -13,7 +13,7 @@
 // in place, a thread keeps only the 4 values of the butterfly it is working
 // on, and stages are separated by __syncthreads().
 //
-// Line addressing: a line l = l_hi * nlo + l_lo has its element idx at
+// Line addressing: a line l = l_hi * nlo + l_lo (nlo a power of two) has its element idx at
 //   l_hi * L * nlo + idx * nlo + l_lo,
 // which covers contiguous rows (nlo = 1) and tiles of columns (nlo = tile
 // width x inner axes) alike.  Butterfly numbering puts l_lo fastest, so
@@ -54,51 +54,53 @@ __device__ __forceinline__ C twid(const C* __restrict__ tw, int tw_log2, int log
   return __ldg(&tw[j << (tw_log2 - log2L)]);
 }
 
-// Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L.
+// Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.
 // Output in bit-reversed order.  Must be called by all threads of the block.
 template <typename C>
-__device__ void fft_dif(C* s, int log2L, int nlo, int nhi, const C* __restrict__ tw, int tw_log2) {
+__device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
   if (log2L == 0) return;
-  const int L = 1 << log2L;
-  const int nthr = blockDim.x;
+  const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
   int lg = log2L;  // log2 of current block size N
   if (lg & 1) {    // one radix-2 stage on the full length
-    const int half = L >> 1;
-    const long total = (long)nhi * nlo * half;
-    for (long b = threadIdx.x; b < total; b += nthr) {
-      int l_lo = (int)(b % nlo);
-      long rest = b / nlo;
-      int j = (int)(rest % half);
-      int l_hi = (int)(rest / half);
-      C* base = s + (long)l_hi * L * nlo + l_lo;
-      C a = base[(long)j * nlo], c = base[(long)(j + half) * nlo];
-      C w = twid(tw, tw_log2, log2L, j);
-      base[(long)j * nlo] = cadd(a, c);
-      base[(long)(j + half) * nlo] = cmul(csub(a, c), w);
+    const int lgh = log2L - 1;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgh);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned j = rest & ((1u << lgh) - 1u), l_hi = rest >> lgh;
+      C* base = s + ((l_hi << (log2L + lgnlo)) | l_lo);
+      C* p0 = base + (j << lgnlo);
+      C* p1 = base + ((j + (1u << lgh)) << lgnlo);
+      const C a = *p0, c = *p1;
+      *p0 = cadd(a, c);
+      *p1 = cmul(csub(a, c), twid(tw, tw_log2, log2L, j));
     }
     __syncthreads();
     lg -= 1;
   }
+  const int lgq_line = log2L - 2;  // radix-4 butterflies per line = L/4
   for (; lg >= 2; lg -= 2) {
-    const int N = 1 << lg, q = N >> 2;
-    const long per_line = L >> 2;
-    const long total = (long)nhi * nlo * per_line;
-    for (long b = threadIdx.x; b < total; b += nthr) {
-      int l_lo = (int)(b % nlo);
-      long rest = b / nlo;
-      int r = (int)(rest % per_line);
-      int l_hi = (int)(rest / per_line);
-      int blk = r >> (lg - 2), j = r & (q - 1);
-      C* base = s + (long)l_hi * L * nlo + l_lo + (long)blk * N * nlo;
-      C x0 = base[(long)j * nlo], x1 = base[(long)(j + q) * nlo];
-      C x2 = base[(long)(j + 2 * q) * nlo], x3 = base[(long)(j + 3 * q) * nlo];
-      C s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = csub(x1, x3);
-      C w1 = twid(tw, tw_log2, lg, j), w2 = twid(tw, tw_log2, lg, 2 * j), w3 = twid(tw, tw_log2, lg, 3 * j);
-      C id13 = cmuli(d13);
-      base[(long)j * nlo] = cadd(s02, s13);
-      base[(long)(j + q) * nlo] = cmul(csub(s02, s13), w2);
-      base[(long)(j + 2 * q) * nlo] = cmul(csub(d02, id13), w1);
-      base[(long)(j + 3 * q) * nlo] = cmul(cadd(d02, id13), w3);
+    const int lgq = lg - 2;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgq_line);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned r = rest & ((1u << lgq_line) - 1u), l_hi = rest >> lgq_line;
+      const unsigned blk = r >> lgq, j = r & ((1u << lgq) - 1u);
+      C* base = s + ((l_hi << (log2L + lgnlo)) | l_lo) + ((blk << lg) << lgnlo);
+      C* p0 = base + (j << lgnlo);
+      const unsigned q = 1u << (lgq + lgnlo);
+      const C x0 = p0[0], x1 = p0[q], x2 = p0[2 * q], x3 = p0[3 * q];
+      const C s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = csub(x1, x3);
+      const C id13 = cmuli(d13);
+      p0[0] = cadd(s02, s13);
+      if (j == 0) {  // all three twiddles are 1
+        p0[q] = csub(s02, s13);
+        p0[2 * q] = csub(d02, id13);
+        p0[3 * q] = cadd(d02, id13);
+      } else {
+        p0[q] = cmul(csub(s02, s13), twid(tw, tw_log2, lg, 2 * j));
+        p0[2 * q] = cmul(csub(d02, id13), twid(tw, tw_log2, lg, j));
+        p0[3 * q] = cmul(cadd(d02, id13), twid(tw, tw_log2, lg, 3 * j));
+      }
     }
     __syncthreads();
   }
@@ -107,50 +109,50 @@ __device__ void fft_dif(C* s, int log2L, int nlo, int nhi, const C* __restrict__
 // Inverse DIT FFT (sign +1, unnormalized): the adjoint of fft_dif.
 // Input in bit-reversed order, output natural.  All threads must call.
 template <typename C>
-__device__ void fft_dit_inv(C* s, int log2L, int nlo, int nhi, const C* __restrict__ tw, int tw_log2) {
+__device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
   if (log2L == 0) return;
-  const int L = 1 << log2L;
-  const int nthr = blockDim.x;
+  const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
+  const int lgq_line = log2L - 2;
   // the DIF ran its radix-4 stages on block sizes 2^(log2L - (log2L&1)) ... 4; mirror them
   const int lgmax = log2L - (log2L & 1);
   for (int lg = 2; lg <= lgmax; lg += 2) {
-    const int N = 1 << lg, q = N >> 2;
-    const long per_line = L >> 2;
-    const long total = (long)nhi * nlo * per_line;
-    for (long b = threadIdx.x; b < total; b += nthr) {
-      int l_lo = (int)(b % nlo);
-      long rest = b / nlo;
-      int r = (int)(rest % per_line);
-      int l_hi = (int)(rest / per_line);
-      int blk = r >> (lg - 2), j = r & (q - 1);
-      C* base = s + (long)l_hi * L * nlo + l_lo + (long)blk * N * nlo;
-      C c0 = base[(long)j * nlo], c1 = base[(long)(j + q) * nlo];
-      C c2 = base[(long)(j + 2 * q) * nlo], c3 = base[(long)(j + 3 * q) * nlo];
-      // conj twiddles: u^1, u^2, u^3 with u = conj(W_N^j)
-      C p1 = cmulc(c1, twid(tw, tw_log2, lg, 2 * j));
-      C p2 = cmulc(c2, twid(tw, tw_log2, lg, j));
-      C p3 = cmulc(c3, twid(tw, tw_log2, lg, 3 * j));
-      C a = cadd(c0, p1), bb = csub(c0, p1), sp = cadd(p2, p3), dp = cmuli(csub(p2, p3));
-      base[(long)j * nlo] = cadd(a, sp);
-      base[(long)(j + 2 * q) * nlo] = csub(a, sp);
-      base[(long)(j + q) * nlo] = cadd(bb, dp);
-      base[(long)(j + 3 * q) * nlo] = csub(bb, dp);
+    const int lgq = lg - 2;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgq_line);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned r = rest & ((1u << lgq_line) - 1u), l_hi = rest >> lgq_line;
+      const unsigned blk = r >> lgq, j = r & ((1u << lgq) - 1u);
+      C* base = s + ((l_hi << (log2L + lgnlo)) | l_lo) + ((blk << lg) << lgnlo);
+      C* p0 = base + (j << lgnlo);
+      const unsigned q = 1u << (lgq + lgnlo);
+      const C c0 = p0[0];
+      C p1 = p0[q], p2 = p0[2 * q], p3 = p0[3 * q];
+      if (j != 0) {  // conj twiddles u^2, u^1, u^3 with u = conj(W_N^j)
+        p1 = cmulc(p1, twid(tw, tw_log2, lg, 2 * j));
+        p2 = cmulc(p2, twid(tw, tw_log2, lg, j));
+        p3 = cmulc(p3, twid(tw, tw_log2, lg, 3 * j));
+      }
+      const C a = cadd(c0, p1), bb = csub(c0, p1), sp = cadd(p2, p3), dp = cmuli(csub(p2, p3));
+      p0[0] = cadd(a, sp);
+      p0[2 * q] = csub(a, sp);
+      p0[q] = cadd(bb, dp);
+      p0[3 * q] = csub(bb, dp);
     }
     __syncthreads();
   }
   if (log2L & 1) {   // adjoint of the leading radix-2 stage, applied last
-    const int half = L >> 1;
-    const long total = (long)nhi * nlo * half;
-    for (long b = threadIdx.x; b < total; b += nthr) {
-      int l_lo = (int)(b % nlo);
-      long rest = b / nlo;
-      int j = (int)(rest % half);
-      int l_hi = (int)(rest / half);
-      C* base = s + (long)l_hi * L * nlo + l_lo;
-      C a = base[(long)j * nlo];
-      C c = cmulc(base[(long)(j + half) * nlo], twid(tw, tw_log2, log2L, j));
-      base[(long)j * nlo] = cadd(a, c);
-      base[(long)(j + half) * nlo] = csub(a, c);
+    const int lgh = log2L - 1;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgh);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned j = rest & ((1u << lgh) - 1u), l_hi = rest >> lgh;
+      C* base = s + ((l_hi << (log2L + lgnlo)) | l_lo);
+      C* p0 = base + (j << lgnlo);
+      C* p1 = base + ((j + (1u << lgh)) << lgnlo);
+      const C a = *p0;
+      const C c = cmulc(*p1, twid(tw, tw_log2, log2L, j));
+      *p0 = cadd(a, c);
+      *p1 = csub(a, c);
     }
     __syncthreads();
   }

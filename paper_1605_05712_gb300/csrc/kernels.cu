@@ -22,7 +22,7 @@
 //   (Gamma0 : tau)_ij = [c1 (h_i w_j + h_j w_i) - c2 s h_i h_j / |h|^2] / |h|^2,
 //   w = tau h, s = h . w, c1 = 1/(2 mu0), c2 = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)).
 template <typename Real>
-__device__ __forceinline__ void gamma_apply(int d, const Real* h, Real c1, Real c2, const Real* t, Real* out) {
+__device__ __forceinline__ void gamma_apply(int d, const Real* h, Real a, Real c1, Real c2, const Real* t, Real* out) {
   Real A[3][3];
   if (d == 2) {
     A[0][0] = t[0]; A[1][1] = t[1]; A[0][1] = A[1][0] = t[2];
@@ -31,9 +31,7 @@ __device__ __forceinline__ void gamma_apply(int d, const Real* h, Real c1, Real 
     A[0][0] = t[0]; A[1][1] = t[1]; A[2][2] = t[2];
     A[1][2] = A[2][1] = t[3]; A[0][2] = A[2][0] = t[4]; A[0][1] = A[1][0] = t[5];
   }
-  Real n2 = 0, w[3], s = 0;
-  for (int i = 0; i < d; ++i) n2 += h[i] * h[i];
-  const Real a = Real(1) / n2;
+  Real w[3], s = 0;
   for (int i = 0; i < d; ++i) {
     Real acc = 0;
     for (int j = 0; j < d; ++j) acc += A[i][j] * h[j];
@@ -58,54 +56,59 @@ __device__ __forceinline__ int64_t mod_ed(const LatDev& dv, int64_t v) {
 }
 
 // h~ = M^T v' with v' the symmetric representative of v (mod e_d) in [-e_d/2, e_d/2)
+template <int D>
 __device__ __forceinline__ void v_to_h(const LatDev& dv, const int64_t* v, int64_t* h) {
-  int64_t vp[3];
-  for (int r = 0; r < dv.d; ++r) vp[r] = (2 * v[r] >= dv.ed) ? v[r] - dv.ed : v[r];
-  for (int i = 0; i < dv.d; ++i) {
+  int64_t vp[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) vp[r] = (2 * v[r] >= dv.ed) ? v[r] - dv.ed : v[r];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
     int64_t acc = 0;
-    for (int j = 0; j < dv.d; ++j) acc += dv.MT[i][j] * vp[j];
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += dv.MT[i][j] * vp[j];
     h[i] = acc;
   }
 }
 
 // eps_hat = -Gammabar0(k) : tau_hat / m at the frequency with v = e_d Q^{-T} E^{-1} k (mod e_d);
 // in/out are n_c complex values.  v == 0 (k = 0) -> E (or 0 for an increment).
-template <typename Real>
+template <typename Real, int NC>
 __device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt, const int64_t* v,
                                             typename cplx_of<Real>::type* val) {
   typedef typename cplx_of<Real>::type C;
-  const int d = dv.d, n_c = dv.n_c;
+  constexpr int d = (NC == 6) ? 3 : 2, n_c = NC;
   if (v[0] == 0 && v[1] == 0 && v[2] == 0) {
     for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(mt.E[c], 0.0);
     return;
   }
-  int64_t hi[3], vn[3], hn[3];
-  v_to_h(dv, v, hi);
+  int64_t hi[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, hn[3] = {0, 0, 0};
+  v_to_h<d>(dv, v, hi);
   bool boundary = false;
+#pragma unroll
   for (int r = 0; r < d; ++r) {
     vn[r] = mod_ed(dv, dv.ed - v[r]);
     if (2 * v[r] == dv.ed) boundary = true;  // v' = -e_d/2: -v has the same representative
   }
-  vn[2] = (d == 3) ? vn[2] : 0;
   if (boundary && mt.boundary_zero) {
     for (int c = 0; c < n_c; ++c) val[c] = cmake<C>(0.0, 0.0);
     return;
   }
-  const Real c1 = Real(0.5 / mt.mu0);
-  const Real c2 = Real((mt.lam0 + mt.mu0) / (mt.mu0 * (mt.lam0 + 2.0 * mt.mu0)));
-  const Real sc = Real(-1.0 / (double)dv.m);
+  const Real c1 = (Real)mt.c1, c2 = (Real)mt.c2, sc = (Real)mt.gscale;
   Real h[3] = {(Real)hi[0], (Real)hi[1], (Real)(d == 3 ? hi[2] : 0)};
-  Real tr[6], ti[6], gr[6], gi[6];
+  Real tr[NC], ti[NC], gr[NC], gi[NC];
+#pragma unroll
   for (int c = 0; c < n_c; ++c) tr[c] = val[c].x, ti[c] = val[c].y;
-  gamma_apply<Real>(d, h, c1, c2, tr, gr);
-  gamma_apply<Real>(d, h, c1, c2, ti, gi);
+  const Real a = Real(1) / (h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+  gamma_apply<Real>(d, h, a, c1, c2, tr, gr);
+  gamma_apply<Real>(d, h, a, c1, c2, ti, gi);
   if (boundary) {
     // average with -h(-k): Gamma0 is even in h, so evaluate at h(-k) directly
-    v_to_h(dv, vn, hn);
+    v_to_h<d>(dv, vn, hn);
     Real h2[3] = {(Real)hn[0], (Real)hn[1], (Real)(d == 3 ? hn[2] : 0)};
-    Real gr2[6], gi2[6];
-    gamma_apply<Real>(d, h2, c1, c2, tr, gr2);
-    gamma_apply<Real>(d, h2, c1, c2, ti, gi2);
+    const Real a2 = Real(1) / (h2[0] * h2[0] + h2[1] * h2[1] + h2[2] * h2[2]);
+    Real gr2[NC], gi2[NC];
+    gamma_apply<Real>(d, h2, a2, c1, c2, tr, gr2);
+    gamma_apply<Real>(d, h2, a2, c1, c2, ti, gi2);
     for (int c = 0; c < n_c; ++c) gr[c] = Real(0.5) * (gr[c] + gr2[c]), gi[c] = Real(0.5) * (gi[c] + gi2[c]);
   }
   for (int c = 0; c < n_c; ++c) {
@@ -143,11 +146,12 @@ __device__ double ordered_sum(const double* p, int n) {
 }
 
 // ------------------------------------------------------------------ row pass
-template <typename Real>
+template <typename Real, int NC>
 __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   typedef typename cplx_of<Real>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n_c = dv.n_c, Rh = dv.Rh, lgRh = dv.log2Rh, rpc = a.rpc;
+  constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;
+  const int Rh = dv.Rh, lgRh = dv.log2Rh, rpc = a.rpc, lgrpc = __ffs(a.rpc) - 1;
   const int nlines = n_c * rpc;
   C* buf = (C*)smem_raw;
   C* nyq = buf + (size_t)nlines * Rh;
@@ -164,20 +168,20 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 
   if (a.flags & ROW_LOAD_EPS) {
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
-      const int line = idx / Rh, n = idx - line * Rh;
-      const int c = line / rpc, row = line - c * rpc;
+      const int line = idx >> lgRh, n = idx & (Rh - 1);
+      const int c = line >> lgrpc, row = line & (rpc - 1);
       const double2 v = *(const double2*)(a.eps + c * m + (r0 + row) * R + 2 * n);
       buf[idx] = cmake<C>(v.x, v.y);
     }
     __syncthreads();
   } else {
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
-      const int line = idx / Rh, pos = idx - line * Rh;
-      const int c = line / rpc, row = line - c * rpc;
+      const int line = idx >> lgRh, pos = idx & (Rh - 1);
+      const int c = line >> lgrpc, row = line & (rpc - 1);
       buf[idx] = T[c * half_m + (r0 + row) * Rh + pos];
     }
     for (int idx = tid; idx < nlines; idx += nthr) {
-      const int c = idx / rpc, row = idx - c * rpc;
+      const int c = idx >> lgrpc, row = idx & (rpc - 1);
       nyq[idx] = TN[c * nrows + r0 + row];
     }
     __syncthreads();
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
       }
     }
     __syncthreads();
-    fft_dit_inv(buf, lgRh, 1, nlines, tw, tw_log2);
+    fft_dit_inv(buf, lgRh, 0, nlines, tw, tw_log2);
   }
 
   // pointwise: update, residual, polarization
@@ -210,15 +214,17 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const bool update = (a.flags & ROW_UPDATE) != 0;
   const bool incr = (a.flags & ROW_INCREMENT) != 0;
   for (int idx = tid; idx < rpc * Rh; idx += nthr) {
-    const int row = idx / Rh, n = idx - row * Rh;
+    const int row = idx >> lgRh, n = idx & (Rh - 1);
     const int64_t g = (r0 + row) * R + 2 * n;
-    Real e0[6], e1[6];
+    Real e0[NC], e1[NC];
+#pragma unroll
     for (int c = 0; c < n_c; ++c) {
       const C z = buf[((size_t)c * rpc + row) * Rh + n];
       e0[c] = z.x;
       e1[c] = z.y;
     }
     if (update) {
+#pragma unroll
       for (int c = 0; c < n_c; ++c) {
         double2* pe = (double2*)(a.eps + c * m + g);
         const double2 old = *pe;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
           d0 = n0 - old.x;
           d1 = n1 - old.y;
         }
-        const double wgt = (c >= dv.d) ? 2.0 : 1.0;
+        const double wgt = (c >= D) ? 2.0 : 1.0;
         dsum += wgt * (d0 * d0 + d1 * d1);
         *pe = make_double2(n0, n1);
       }
@@ -241,8 +247,10 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     const uchar2 ph = *(const uchar2*)(a.phase + g);
     const double* D0 = a.mat.Dtab + (int)ph.x * n_c * n_c;
     const double* D1 = a.mat.Dtab + (int)ph.y * n_c * n_c;
+#pragma unroll
     for (int c = 0; c < n_c; ++c) {
       Real t0 = 0, t1 = 0;
+#pragma unroll
       for (int q = 0; q < n_c; ++q) {
         t0 += (Real)__ldg(D0 + c * n_c + q) * e0[q];
         t1 += (Real)__ldg(D1 + c * n_c + q) * e1[q];
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     }
   }
   __syncthreads();
-  fft_dif(buf, lgRh, 1, nlines, tw, tw_log2);
+  fft_dif(buf, lgRh, 0, nlines, tw, tw_log2);
   // R2C post-processing: X[k] = 1/2 (A - i W_R^k B), A = Z_k + conj Z_{Rh-k}, B = Z_k - conj Z_{Rh-k}
   for (int idx = tid; idx < nlines * npl; idx += nthr) {
     const int line = idx / npl, k = idx - line * npl;
@@ -278,14 +286,17 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
     for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
       const int row = idx / (Rh + 1), k = idx - row * (Rh + 1);
-      C val[6];
+      C val[NC];
+#pragma unroll
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
         val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
       }
       int64_t v[3] = {0, 0, 0};
-      for (int r = 0; r < dv.d; ++r) v[r] = mod_ed(dv, (int64_t)k * dv.ax_cv[dv.nax - 1][r]);
-      green_point<Real>(dv, a.mat, v, val);
+#pragma unroll
+      for (int r = 0; r < D; ++r) v[r] = mod_ed(dv, (int64_t)k * dv.ax_cv[dv.nax - 1][r]);
+      green_point<Real, NC>(dv, a.mat, v, val);
+#pragma unroll
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
         if (k == Rh) nyq[line] = val[c];
@@ -295,12 +306,12 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     __syncthreads();
   }
   for (int idx = tid; idx < nlines * Rh; idx += nthr) {
-    const int line = idx / Rh, pos = idx - line * Rh;
-    const int c = line / rpc, row = line - c * rpc;
+    const int line = idx >> lgRh, pos = idx & (Rh - 1);
+    const int c = line >> lgrpc, row = line & (rpc - 1);
     T[c * half_m + (r0 + row) * Rh + pos] = buf[idx];
   }
   for (int idx = tid; idx < nlines; idx += nthr) {
-    const int c = idx / rpc, row = idx - c * rpc;
+    const int c = idx >> lgrpc, row = idx & (rpc - 1);
     TN[c * nrows + r0 + row] = nyq[idx];
   }
   if (!update) return;
@@ -332,14 +343,15 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 }
 
 // ------------------------------------------------------------------ column pass
-template <typename Real>
+template <typename Real, int NC>
 __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   typedef typename cplx_of<Real>::type C;
   if (a.done && *(volatile const int*)a.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = (C*)smem_raw;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int n_f = a.n_f, G = a.G;
+  constexpr int n_f = NC, D = (NC == 6) ? 3 : 2;
+  const int G = a.G;
   int64_t b = blockIdx.x;
   const int64_t main_blocks = a.outer * a.tiles_main;
   const bool nyqt = b >= main_blocks;
@@ -359,6 +371,7 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   }
   const int64_t i0 = t * w;
   const int wv = (int)min((int64_t)w, inner_count - i0);
+  const int lgw = __ffs(w) - 1, lgG = __ffs(G) - 1;
   const int64_t plane = a.outer * (int64_t)G * inner_count;
   C* dst = (C*)(nyqt ? a.TN : a.T);
   const C* src = (a.Tin && !nyqt) ? (const C*)a.Tin : dst;
@@ -366,9 +379,9 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   const int lg_slots = __ffs(a.row_slots) - 1;
 
   for (int idx = tid; idx < n_f * G * w; idx += nthr) {
-    const int col = idx % w;
-    const int g = (idx / w) % G;
-    const int f = idx / (w * G);
+    const int col = idx & (w - 1);
+    const int g = (idx >> lgw) & (G - 1);
+    const int f = idx >> (lgw + lgG);
     s[idx] = (col < wv) ? src[f * plane + (o * G + g) * inner_count + i0 + col] : cmake<C>(0.0, 0.0);
   }
   __syncthreads();
@@ -394,9 +407,10 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   };
   if (a.has_twiddle && a.mode != COL_INV) {
     for (int idx = tid; idx < G * w; idx += nthr) {
-      const int col = idx % w, g = idx / w;
+      const int col = idx & (w - 1), g = idx >> lgw;
       const int64_t n1 = (g / after_n1) % len_n1;
       const C W = split_tw(n1 * col_krow(col));
+#pragma unroll
       for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmul(s[(size_t)f * G * w + idx], W);
     }
     __syncthreads();
@@ -406,13 +420,13 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     for (int x = a.a1 - 1; x >= a.a0; --x) {
       int64_t before = 1;
       for (int y = a.a0; y < x; ++y) before *= dv.ax_len[y];
-      fft_dif(s, dv.ax_log2[x], (int)(w * after), (int)(n_f * before), tw, dv.tw_log2);
+      fft_dif(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw, dv.tw_log2);
       after *= dv.ax_len[x];
     }
   }
-  if (a.mode == COL_GAMMA) {
+  if (NC >= 3 && a.mode == COL_GAMMA) {
     for (int idx = tid; idx < G * w; idx += nthr) {
-      const int col = idx % w, g = idx / w;
+      const int col = idx & (w - 1), g = idx >> lgw;
       int64_t v[3] = {0, 0, 0};
       // group axes (bit-reversed after the DIF)
       int64_t rem = g;
@@ -420,7 +434,8 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
         const int pos = (int)(rem % dv.ax_len[x]);
         rem /= dv.ax_len[x];
         const int64_t k = bitrev(pos, dv.ax_log2[x]);
-        for (int r = 0; r < dv.d; ++r) v[r] += k * dv.ax_cv[x][r];
+#pragma unroll
+        for (int r = 0; r < D; ++r) v[r] += k * dv.ax_cv[x][r];
       }
       // axes between the group and the row (transformed by the mid passes, bit-reversed)
       const int64_t ii = i0 + col;
@@ -429,13 +444,17 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
         const int pos = (int)(mid % dv.ax_len[x]);
         mid /= dv.ax_len[x];
         const int64_t k = bitrev(pos, dv.ax_log2[x]);
-        for (int r = 0; r < dv.d; ++r) v[r] += k * dv.ax_cv[x][r];
+#pragma unroll
+        for (int r = 0; r < D; ++r) v[r] += k * dv.ax_cv[x][r];
       }
       const int64_t kr = col_krow(col);
-      for (int r = 0; r < dv.d; ++r) v[r] = mod_ed(dv, v[r] + kr * dv.ax_cv[dv.nax - 1][r]);
-      C val[6];
+#pragma unroll
+      for (int r = 0; r < D; ++r) v[r] = mod_ed(dv, v[r] + kr * dv.ax_cv[dv.nax - 1][r]);
+      C val[NC];
+#pragma unroll
       for (int f = 0; f < n_f; ++f) val[f] = s[(size_t)f * G * w + idx];
-      green_point<Real>(dv, a.mat, v, val);
+      if constexpr (NC >= 3) green_point<Real, NC>(dv, a.mat, v, val);
+#pragma unroll
       for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = val[f];
     }
     __syncthreads();
@@ -445,14 +464,15 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     for (int x = a.a0; x < a.a1; ++x) {
       int64_t after = 1;
       for (int y = x + 1; y < a.a1; ++y) after *= dv.ax_len[y];
-      fft_dit_inv(s, dv.ax_log2[x], (int)(w * after), (int)(n_f * before), tw, dv.tw_log2);
+      fft_dit_inv(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw, dv.tw_log2);
       before *= dv.ax_len[x];
     }
     if (a.has_twiddle) {
       for (int idx = tid; idx < G * w; idx += nthr) {
-        const int col = idx % w, g = idx / w;
+        const int col = idx & (w - 1), g = idx >> lgw;
         const int64_t n1 = (g / after_n1) % len_n1;
         const C W = split_tw(n1 * col_krow(col));
+#pragma unroll
         for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmulc(s[(size_t)f * G * w + idx], W);
       }
       __syncthreads();
@@ -460,10 +480,10 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   }
   const Real sc = (Real)a.scale;
   for (int idx = tid; idx < n_f * G * w; idx += nthr) {
-    const int col = idx % w;
+    const int col = idx & (w - 1);
     if (col >= wv) continue;
-    const int g = (idx / w) % G;
-    const int f = idx / (w * G);
+    const int g = (idx >> lgw) & (G - 1);
+    const int f = idx >> (lgw + lgG);
     C val = s[idx];
     if (a.scale != 1.0) val = cscale(val, sc);
     dst[f * plane + (o * G + g) * inner_count + i0 + col] = val;
@@ -487,8 +507,8 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
     buf[idx] = src[f * m + (r0 + row) * R + pos];
   }
   __syncthreads();
-  if (inverse) fft_dit_inv(buf, lgR, 1, nlines, (const C*)dv.tw, dv.tw_log2);
-  else fft_dif(buf, lgR, 1, nlines, (const C*)dv.tw, dv.tw_log2);
+  if (inverse) fft_dit_inv(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2);
+  else fft_dif(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2);
   const Real sc = (Real)scale;
   for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
     const int line = idx / R, pos = idx - line * R;
@@ -552,12 +572,15 @@ __global__ void __launch_bounds__(256) eff_kernel(LatDev dv, EffArgs a) {
 // ------------------------------------------------------------------ launchers
 template <typename Real>
 void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int nthreads, size_t smem, cudaStream_t st) {
-  row_pass_kernel<Real><<<nblocks, nthreads, smem, st>>>(dv, a);
+  if (dv.n_c == 6) row_pass_kernel<Real, 6><<<nblocks, nthreads, smem, st>>>(dv, a);
+  else row_pass_kernel<Real, 3><<<nblocks, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
 void launch_col_pass(const LatDev& dv, const ColArgs& a, int nthreads, size_t smem, cudaStream_t st) {
   const int64_t nb = a.outer * (a.tiles_main + a.tiles_nyq);
-  col_pass_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
+  if (a.n_f == 6) col_pass_kernel<Real, 6><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
+  else if (a.n_f == 3) col_pass_kernel<Real, 3><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
+  else col_pass_kernel<Real, 1><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale, int rpc,
@@ -583,17 +606,28 @@ template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, size_t,
 template void launch_row_complex<double>(const LatDev&, const void*, void*, int, int, double, int, int, size_t,
                                          cudaStream_t);
 
+template <typename K>
+static cudaError_t set_smem(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 int lat_kernel_attrs(size_t max_smem) {
-  cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(row_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(row_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(col_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(col_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(row_complex_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)max_smem);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+    optin = (int)max_smem;
+  cudaError_t e = set_smem(row_pass_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 1>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(row_complex_kernel<double>, optin);
   return e == cudaSuccess ? 0 : (int)e;
 }

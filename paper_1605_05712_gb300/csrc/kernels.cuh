@@ -17,6 +17,8 @@ struct MatArgs {
   const double* Dtab;   // n_phases x n_c x n_c, (C_p - C0) acting on tensor components
   double E[6];          // macroscopic strain, tensor components
   double lam0, mu0;
+  double c1, c2;        // 1/(2 mu0), (lam0 + mu0) / (mu0 (lam0 + 2 mu0))
+  double gscale;        // -1/m: the forward 1/m of F(M) and the minus sign of the update
   int boundary_zero;
   int increment;        // 1: spectrum carries an increment, k = 0 gets 0 instead of E
 };

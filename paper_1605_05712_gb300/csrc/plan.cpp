@@ -207,12 +207,13 @@ static int choose_layout(lat_plan* P) {
   // candidate row lengths B (power of two dividing eL, B <= 2*RH_MAX); B = eL means no split
   int best_groups = 1 << 30;
   int64_t bestB = -1;
+  double best_dist = 1e300;
   std::vector<int64_t> cands;
-  if (eL <= 2 * RH_MAX) cands.push_back(eL);
   for (int lb = (lgL + 1) / 2; lb < lgL; ++lb) {
     int64_t B = int64_t(1) << lb;
     if (B <= 2 * RH_MAX && B >= 2) cands.push_back(B);
   }
+  if (eL <= 2 * RH_MAX) cands.push_back(eL);
   for (int64_t B : cands) {
     std::vector<int64_t> lens;
     for (size_t i = 0; i + 1 < paxes.size(); ++i) lens.push_back(P->e[paxes[i]]);
@@ -233,7 +234,11 @@ static int choose_layout(lat_plan* P) {
       i = j;
     }
     if (!ok) continue;
-    if (ng < best_groups) best_groups = ng, bestB = B;
+    // fewest column passes first; then rows and columns balanced (B close to sqrt(2m)),
+    // ties to the shorter row
+    const double target = 0.5 * log2(2.0 * (double)P->m);
+    const double dist = fabs(log2((double)B) - target);
+    if (ng < best_groups || (ng == best_groups && dist < best_dist - 1e-9)) best_groups = ng, bestB = B, best_dist = dist;
   }
   if (bestB < 0) return lat_fail(LAT_ERR_UNSUPPORTED, "no FFT decomposition fits shared memory");
   const int64_t B = bestB;

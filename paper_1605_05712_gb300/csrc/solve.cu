@@ -89,13 +89,12 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
   g.row_blocks = (int)(nrows / rpc);
   g.row_smem = rsm(rpc);
   if (g.row_smem > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
-  const int wmin = (cs == 16) ? 2 : 4;
   for (int k = 0; k < P->ngroups; ++k) {
     const LatGroup& G = P->grp[k];
     const int64_t ic = G.inner * row_slots;
     int64_t w = std::min<int64_t>(32, ic);
     auto csm = [&](int64_t ww) { return (size_t)n_f * G.G * ww * cs; };
-    while (w > 1 && (csm(w) > kColSmemMax || (G.outer * (ic / w) < 2 * nsm && w > wmin))) w /= 2;
+    while (w > 1 && (csm(w) > kColSmemMax || G.outer * (ic / w) < 2 * nsm)) w /= 2;
     if (csm(w) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column group does not fit in shared memory");
     const int64_t wN = std::min<int64_t>(w, G.inner);
     g.w[k] = (int)w;
@@ -336,6 +335,9 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
       for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E_lc[c] : 0.0;
       ra.mat.lam0 = lam0;
       ra.mat.mu0 = mu0;
+      ra.mat.c1 = 0.5 / mu0;
+      ra.mat.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+      ra.mat.gscale = -1.0 / (double)m;
       ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
       ra.it.partials = (double*)(ws + wl.partials);
       ra.it.counter = (unsigned*)(sc + 0);
@@ -385,9 +387,9 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
     const char* sc = scal.data() + (size_t)lc * kScalBytes;
     int it = *(const int*)(sc + 8);
     double r = *(const double*)(sc + 16);
-    if (P->nax == 0) {  // m = 1: one iteration reproduces E exactly
-      it = maxit > 0 ? 1 : 0;
-      r = 0.0;
+    if (P->nax == 0) {  // m = 1: every iterate equals E, r_n = 0; stop at the first r_n < tol
+      it = (maxit > 0 && tol > 0) ? 1 : maxit;
+      r = maxit > 0 ? 0.0 : NAN;
     } else if (maxit == 0) {
       r = NAN;
     }
@@ -396,7 +398,8 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
     if (sigma_bar)
       for (int c = 0; c < n_c; ++c) sigma_bar[lc * n_c + c] = ((const double*)(sc + 32))[c];
     if (o.resid_history && maxit > 0) {
-      if (P->nax == 0) o.resid_history[(size_t)lc * maxit] = 0.0;
+      if (P->nax == 0)
+        for (int k = 0; k < it; ++k) o.resid_history[(size_t)lc * maxit + k] = 0.0;
       for (int k = 0; k < std::min(it, std::min(maxit, LAT_HIST_CAP)) && P->nax > 0; ++k)
         o.resid_history[(size_t)lc * maxit + k] = hist[(size_t)lc * LAT_HIST_CAP + k];
     }
@@ -443,6 +446,9 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E[c] : 0.0;
   ra.mat.lam0 = C0[0];
   ra.mat.mu0 = C0[1];
+  ra.mat.c1 = 0.5 / C0[1];
+  ra.mat.c2 = (C0[0] + C0[1]) / (C0[1] * (C0[0] + 2.0 * C0[1]));
+  ra.mat.gscale = -1.0 / (double)P->m;
   ra.it.partials = (double*)(ws + wl.partials);
   ra.it.counter = (unsigned*)(sc + 0);
   ra.it.done = (int*)(sc + 4);
