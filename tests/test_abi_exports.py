@@ -1,0 +1,47 @@
+"""liblatms.so builds, loads without a GPU and exports every function include/*.h declares."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+            if m.group(1) not in ("defined",):
+                names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1605_05712_gb300._build import build
+    lib_path = build()
+    L = ctypes.CDLL(lib_path)
+    names = declared_functions()
+    assert {"lattice_plan", "basic_scheme_solve", "lattice_fft", "basic_scheme_solve_noalloc"} <= names
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_host_side_plan_without_gpu():
+    # plan construction, points and frequencies are host code; they work with no GPU present
+    import numpy as np
+    from oracle.lattice import Lattice
+    from paper_1605_05712_gb300 import LatticeError, lattice_plan
+    for M in ([[8, -4], [2, 7]], [[512, 16], [0, 512]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]]):
+        P = lattice_plan(M)
+        L = Lattice(M)
+        assert P.m == L.m and P.divisors == L.e
+        assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
+        assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
+    for bad, code in (([[2, 4], [1, 2]], -2), ([[3, 0], [0, 5]], -5)):
+        try:
+            lattice_plan(bad)
+            raise AssertionError("expected an error")
+        except LatticeError as e:
+            assert e.code == code
