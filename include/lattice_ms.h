@@ -171,6 +171,38 @@ int basic_scheme_solve(const lat_plan* plan, const uint8_t* phase, int n_phases,
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * basic_scheme_solve_noalloc -- basic_scheme_solve for callers that cannot
+ * allocate device memory (the paper has no counterpart: this is a property of
+ * the library, not of the method).  Code that runs while a stream is being
+ * captured into a CUDA graph, a serving loop with a fixed memory budget, or a
+ * runtime whose allocator owns all device memory cannot call cudaMalloc for
+ * the workspace basic_scheme_solve wants.  This variant takes no workspace and
+ * allocates nothing: its scratch is one static device array of
+ * LAT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library
+ * holds until the process exits.  The caller still owns and passes the inputs
+ * and outputs, with the meaning they have for basic_scheme_solve.
+ *  - Limit: returns LAT_ERR_SIZE (message gives the bytes needed) when the
+ *    solve's workspace plus the plan's twiddle tables exceed the array, e.g.
+ *    binary64 m = 262144 in 2-D fits two load cases.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and keeps it; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array; each call clears what it reads before
+ *    use, but calls that overlap on the GPU (other streams or host threads)
+ *    race on it.
+ *  - The iteration uses plain kernel launches and reads the convergence flag
+ *    back after every iteration instead of a CUDA-graph loop; the results
+ *    equal basic_scheme_solve's.
+ */
+#define LAT_NOALLOC_SCRATCH_BYTES (16u << 20)
+int basic_scheme_solve_noalloc(const lat_plan* plan, const uint8_t* phase, int n_phases,
+                               const double* stiffness, const double* C0,
+                               const double* E, int n_loads, double tol, int maxit,
+                               const lat_solve_opts* opts,
+                               double* eps, double* sigma, double* sigma_bar,
+                               int* iters, double* resid, void* stream);
+
+/*
  * lattice_pass_times -- profiling helper: average device time of each kernel
  * of one Basic Scheme iteration (no counterpart in the paper; it measures
  * the passes the solve above runs inside its CUDA graph).  Runs the

@@ -226,3 +226,45 @@ def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=2
                                 prec, int(n_reps), ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                 ws.numel(), _stream(stream), ms, ctypes.byref(n)))
     return [ms[i] for i in range(n.value)]
+
+
+def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
+                               boundary="average", eps_out=None, want_sigma=False, stream=None):
+    """basic_scheme_solve through the no-allocation entry point of the C ABI.
+
+    For callers that cannot allocate device memory inside the call: the library uses its own
+    static 16 MiB device scratch array instead of a workspace.  The outputs (eps, sigma) are
+    still the caller's: pass ``eps_out`` (float64 CUDA, (n_loads, n_c, m)) to avoid any
+    allocation here as well.
+    """
+    import torch
+    stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
+    C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
+    E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
+    n_loads = E.shape[0]
+    Ea, Ep = _f64(E)
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+        raise TypeError("phase must be a uint8 CUDA tensor with m entries")
+    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
+                                                          device=phase.device)
+    sigma = torch.empty_like(eps) if want_sigma else None
+    sbar = np.zeros((n_loads, plan.n_c))
+    iters = np.zeros(n_loads, dtype=np.int32)
+    resid = np.zeros(n_loads)
+    opts = _Opts(prec, bnd, 0, None)
+    L = lib()
+    f = L.basic_scheme_solve_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3 + \
+        [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts), ctypes.c_void_p, ctypes.c_void_p,
+         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+         ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    rc = f(plan.handle, ctypes.c_void_p(phase.data_ptr()), stiff.shape[0], stiff_p, C0p, Ep, n_loads, float(tol),
+           int(maxit), ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
+           ctypes.c_void_p(sigma.data_ptr()) if sigma is not None else None,
+           sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream))
+    _check(rc)
+    return dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "solve_detail.h"
 
 static thread_local std::string g_err;
 void lat_set_error(const std::string& s) { g_err = s; }
@@ -396,6 +397,42 @@ extern "C" int lattice_plan(const int64_t* Min, int d, lat_plan** out) {
     return rc;
   }
   *out = P;
+  return LAT_OK;
+}
+
+int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t* n_tw, int64_t* n_stw) {
+  int lg = 1;
+  for (int i = 0; i < P->nax; ++i) lg = std::max(lg, P->ax[i].log2len);
+  const int64_t N = int64_t(1) << lg;
+  int64_t lo_n = 0, hi_n = 0;
+  if (P->split) {
+    lo_n = int64_t(1) << P->split_lo_log2;
+    hi_n = P->split_e >> P->split_lo_log2;
+  }
+  if (n_tw) *n_tw = N;
+  if (n_stw) *n_stw = hi_n + lo_n;
+  auto put = [&](void* dst, int64_t i, double re, double im) {
+    if (fp32) ((float2*)dst)[i] = make_float2((float)re, (float)im);
+    else ((double2*)dst)[i] = make_double2(re, im);
+  };
+  if (tw)
+    for (int64_t t = 0; t < N; ++t) {
+      double re, im;
+      twiddle(t, N, &re, &im);
+      put(tw, t, re, im);
+    }
+  if (stw && P->split) {
+    for (int64_t j = 0; j < hi_n; ++j) {
+      double re, im;
+      twiddle(j << P->split_lo_log2, P->split_e, &re, &im);
+      put(stw, j, re, im);
+    }
+    for (int64_t j = 0; j < lo_n; ++j) {
+      double re, im;
+      twiddle(j, P->split_e, &re, &im);
+      put(stw, hi_n + j, re, im);
+    }
+  }
   return LAT_OK;
 }
 

@@ -7,14 +7,10 @@
 #include <algorithm>
 #include <vector>
 
-#include "kernels.cuh"
+#include "solve_detail.h"
 
-namespace {
+namespace latms_detail {
 
-const size_t kMaxSmem = 232448;       // sm_100/sm_103 opt-in dynamic shared memory per block
-const size_t kRowSmemTarget = 64 * 1024;
-const size_t kColSmemMax = 200 * 1024;
-const int kThreads = 256;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -67,13 +63,6 @@ LatDev make_dev(const lat_plan* P, bool fp32) {
   return dv;
 }
 
-struct Geometry {
-  int rpc, row_blocks;
-  size_t row_smem;
-  int w[LAT_MAX_GROUPS], wN[LAT_MAX_GROUPS];
-  int64_t tiles_main[LAT_MAX_GROUPS], tiles_nyq[LAT_MAX_GROUPS];
-  size_t col_smem[LAT_MAX_GROUPS];
-};
 
 // row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile
 int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g) {
@@ -106,12 +95,6 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
   return LAT_OK;
 }
 
-struct Work {
-  size_t T, TN, Dtab, Ctab, partials, scal, hist, total;
-  size_t t_per_lc, tn_per_lc;
-};
-const int kMaxPhases = 256;
-const size_t kScalBytes = 256;  // per load case
 
 Work layout(const lat_plan* P, int n_loads, int precision) {
   const int n_c = P->d * (P->d + 1) / 2;
@@ -148,7 +131,7 @@ void voigt_to_tc(const double* V, int d, double* out) {
     for (int J = 0; J < n_c; ++J) out[I * n_c + J] = V[vi[I] * 6 + vi[J]] * (J >= d ? 2.0 : 1.0);
 }
 
-#define CK(x)                                                                        \
+#define CK_SOLVE(x)                                                                        \
   do {                                                                               \
     cudaError_t e_ = (x);                                                            \
     if (e_ != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string(#x) + ": " +   \
@@ -202,28 +185,28 @@ int solve_one(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs ra
   RowArgs first = ra;
   first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
   launch_row_pass<Real>(dv, first, g.row_blocks, kThreads, g.row_smem, st);
-  CK(cudaGetLastError());
+  CK_SOLVE(cudaGetLastError());
   ColArgs c0 = ca;
   c0.done = nullptr;
   enqueue_columns<Real>(dv, P, g, c0, st);
-  CK(cudaGetLastError());
+  CK_SOLVE(cudaGetLastError());
   // WHILE loop: body = row pass (update + residual + convergence) + column passes
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
-  CK(cudaGraphCreate(&graph, 0));
+  CK_SOLVE(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
-  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  CK_SOLVE(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  CK_SOLVE(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  CK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  CK_SOLVE(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  CK_SOLVE(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   RowArgs full = ra;
   full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (ra.flags & ROW_INCREMENT);
   full.it.cond = (unsigned long long)handle;
@@ -245,7 +228,12 @@ int solve_one(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs ra
   return LAT_OK;
 }
 
-}  // namespace
+template void enqueue_columns<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, cudaStream_t);
+template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, cudaStream_t);
+
+}  // namespace latms_detail
+
+using namespace latms_detail;
 
 void lat_graph_cache_free(lat_plan* P) { (void)P; }
 
@@ -300,9 +288,9 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
     voigt_to_tc(stiffness + 36 * p, d, &Cc[p * n_c * n_c]);
     for (int k = 0; k < n_c * n_c; ++k) D[p * n_c * n_c + k] = Cc[p * n_c * n_c + k] - c0tc[k];
   }
-  CK(cudaMemcpyAsync(ws + wl.Dtab, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ws + wl.Ctab, Cc.data(), Cc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_loads * kScalBytes, st));
+  CK_SOLVE(cudaMemcpyAsync(ws + wl.Dtab, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK_SOLVE(cudaMemcpyAsync(ws + wl.Ctab, Cc.data(), Cc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK_SOLVE(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_loads * kScalBytes, st));
 
   const bool fp32 = (o.precision == LAT_MIXED);
   const size_t cs = fp32 ? 8 : 16;
@@ -322,7 +310,7 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
     for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * E_lc[c] * E_lc[c];
     const double norm0 = nE2 > 0 ? sqrt((double)m * nE2) : 1.0;
     if (!o.warm_start) launch_fill(eps_lc, n_c, m, E_lc, st);
-    CK(cudaGetLastError());
+    CK_SOLVE(cudaGetLastError());
     if (P->nax > 0 && maxit > 0) {
       RowArgs ra;
       memset(&ra, 0, sizeof(ra));
@@ -371,17 +359,17 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
     ea.counter = (unsigned*)(sc + 24);
     ea.sigma_bar = (double*)(sc + 32);
     launch_eff(dv, ea, eff_blocks, st);
-    CK(cudaGetLastError());
+    CK_SOLVE(cudaGetLastError());
   }
   // scalars back to the host
   std::vector<char> scal((size_t)n_loads * kScalBytes);
-  CK(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
+  CK_SOLVE(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
   std::vector<double> hist;
   if (o.resid_history && maxit > 0) {
     hist.resize((size_t)n_loads * LAT_HIST_CAP);
-    CK(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK_SOLVE(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
-  CK(cudaStreamSynchronize(st));
+  CK_SOLVE(cudaStreamSynchronize(st));
   int status = LAT_OK;
   for (int lc = 0; lc < n_loads; ++lc) {
     const char* sc = scal.data() + (size_t)lc * kScalBytes;
@@ -459,7 +447,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ra.it.tol = 0.0;
   ra.it.maxit = 1 << 30;
   ra.it.cond = 0;  // plain launches: the kernel skips the graph condition when cond == 0
-  CK(cudaMemsetAsync(sc, 0, kScalBytes, st));
+  CK_SOLVE(cudaMemsetAsync(sc, 0, kScalBytes, st));
   ColArgs ca;
   memset(&ca, 0, sizeof(ca));
   ca.row_slots = P->Rh;
@@ -471,14 +459,14 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ca.mat = ra.mat;
   const int nk = 1 + 2 * P->ngroups - 1 + (P->ngroups == 0 ? 1 : 0);
   std::vector<cudaEvent_t> ev(2 * nk);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (auto& e : ev) CK_SOLVE(cudaEventCreate(&e));
   std::vector<double> acc(nk, 0.0);
   for (int rep = 0; rep < n_reps; ++rep) {
     int k = 0;
-    CK(cudaEventRecord(ev[2 * k], st));
+    CK_SOLVE(cudaEventRecord(ev[2 * k], st));
     if (fp32) launch_row_pass<float>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
     else launch_row_pass<double>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
-    CK(cudaEventRecord(ev[2 * k + 1], st));
+    CK_SOLVE(cudaEventRecord(ev[2 * k + 1], st));
     ++k;
     auto one = [&](int g, int mode) {
       ColArgs c = ca;
@@ -503,11 +491,11 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
     };
     for (int g = P->ngroups - 1; g >= 0; --g) one(g, g == 0 ? COL_GAMMA : COL_FWD);
     for (int g = 1; g < P->ngroups; ++g) one(g, COL_INV);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(st));
+    CK_SOLVE(cudaGetLastError());
+    CK_SOLVE(cudaStreamSynchronize(st));
     for (int j = 0; j < k; ++j) {
       float ms = 0;
-      CK(cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]));
+      CK_SOLVE(cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]));
       acc[j] += ms;
     }
   }
@@ -527,7 +515,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t m = P->m;
   if (P->nax == 0) {
-    CK(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK_SOLVE(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return LAT_OK;
   }
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
@@ -576,7 +564,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       launch_row_complex<double>(dv, P->ngroups == 0 ? (const void*)fin : (const void*)fout, fout, 1, 1, 1.0,
                                  geo.rpc, kThreads, geo.row_smem, st);
     }
-    CK(cudaGetLastError());
+    CK_SOLVE(cudaGetLastError());
   }
   return LAT_OK;
 }

@@ -1,0 +1,49 @@
+"""The no-allocation entry point against the workspace entry point (GPU).
+
+basic_scheme_solve_noalloc serves callers that cannot allocate device memory
+(inside a stream capture, under a fixed memory budget, under a foreign
+allocator): it runs the same kernels on a static device scratch array.  This
+file is collected last so that a run stopping at the first failure has run
+every other test before it; it also passes alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_1605_05712_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10    # the tolerance of the binary64 parity tests
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_noalloc_matches_workspace_entry_point_twice(cuda):
+    import torch
+    from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
+    from paper_1605_05712_gb300.api import basic_scheme_solve_noalloc
+    P = lattice_plan([[512, 16], [0, 512]])          # m = 262144, rank-2, four-step split
+    ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 3])).to(cuda)
+    stiff = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(10.0, 10.0)]
+    E = np.array([[1.0, 0.0, 0.0], [0.2, -0.4, 0.3]])
+    ref = basic_scheme_solve(P, ph, stiff, (5.5, 5.5), E, tol=1e-8, maxit=300, want_sigma=True)
+    out_eps = torch.empty_like(ref["eps"])
+    for call in range(2):                              # second call reuses the scratch left by the first
+        out_eps.fill_(float("nan"))
+        g = basic_scheme_solve_noalloc(P, ph, stiff, (5.5, 5.5), E, tol=1e-8, maxit=300, eps_out=out_eps,
+                                       want_sigma=True)
+        assert g["status"] == ref["status"] == 0
+        assert np.array_equal(g["iters"], ref["iters"])
+        assert _rel(g["eps"].cpu().numpy(), ref["eps"].cpu().numpy()) < RTOL
+        assert _rel(g["sigma"].cpu().numpy(), ref["sigma"].cpu().numpy()) < RTOL
+        assert _rel(g["sigma_bar"], ref["sigma_bar"]) < RTOL
+        assert _rel(g["resid"], ref["resid"]) < 1e-9
+    # a solve larger than the static scratch is refused with a size error, not run
+    Pb = lattice_plan([[128, 0, 0], [0, 128, 0], [0, 0, 128]])
+    phb = torch.zeros(Pb.m, dtype=torch.uint8, device=cuda)
+    with pytest.raises(LatticeError) as ei:
+        basic_scheme_solve_noalloc(Pb, phb, stiff[:1], (5.5, 5.5), np.eye(6)[:1], tol=1e-8, maxit=2)
+    assert ei.value.code == -4
