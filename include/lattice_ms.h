@@ -127,6 +127,9 @@ typedef struct lat_solve_opts {
   int boundary;         /* LAT_BOUNDARY_AVERAGE or LAT_BOUNDARY_ZERO */
   int warm_start;       /* 0: eps^(0) = E (Algorithm 1); 1: eps holds eps^(0) on entry */
   double* resid_history;/* host or NULL: n_loads * maxit residuals r_0, r_1, ... (rest untouched) */
+  int mixed_increment;  /* LAT_MIXED only: 1 = binary32 kernels carry the increment
+                           eps^(n+1) - eps^(n) (accumulated into the binary64 strain), 0 = they
+                           carry the strain itself */
 } lat_solve_opts;
 
 /*
@@ -159,8 +162,10 @@ size_t lattice_workspace_bytes(const lat_plan* plan, int n_loads, int precision)
  *   resid      host or NULL, n_loads: last residual r.
  *   workspace  device, >= lattice_workspace_bytes(plan, n_loads, precision).
  * Runs on `stream` and returns after synchronizing it (host outputs valid).
- * Load cases are solved one after another; each stops on its own residual.
- * Returns LAT_OK when every load case met tol, else the worst outcome.
+ * The load cases are solved together (one batch, see basic_scheme_solve_batch);
+ * each stops on its own residual.  Residual histories keep at most 4096
+ * entries per load case.  Returns LAT_OK when every load case met tol, else
+ * the worst outcome.
  */
 int basic_scheme_solve(const lat_plan* plan, const uint8_t* phase, int n_phases,
                        const double* stiffness, const double* C0,
@@ -169,6 +174,37 @@ int basic_scheme_solve(const lat_plan* plan, const uint8_t* phase, int n_phases,
                        double* eps, double* sigma, double* sigma_bar,
                        int* iters, double* resid,
                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Batches of independent microstructures on one lattice (shared plan): each
+ * item has its own phase field, material, reference medium, macroscopic
+ * strain and outputs, and stops on its own residual.  All items run in the
+ * same kernel launches (one CUDA-graph loop); finished items drop out.
+ */
+#define LAT_BATCH_MAX_PHASES 16
+typedef struct lat_batch_item {
+  const uint8_t* phase;     /* device, m phase ids in plan order (< n_phases) */
+  int n_phases;             /* 1..LAT_BATCH_MAX_PHASES */
+  const double* stiffness;  /* host, n_phases * 36: 6x6 Voigt matrix per phase */
+  double C0[2];             /* isotropic reference medium (lambda0, mu0) */
+  const double* E;          /* host, n_c tensor components */
+  double* eps;              /* device, n_c * m (output) */
+  double* sigma;            /* device or NULL, n_c * m */
+} lat_batch_item;
+
+/* workspace of basic_scheme_solve_batch for n_items items */
+size_t lattice_batch_workspace_bytes(const lat_plan* plan, int n_items, int precision);
+
+/*
+ * basic_scheme_solve_batch -- Algorithm 1 (Sec. 3.2) for n_items independent
+ * problems sharing the lattice of `plan`; per item as basic_scheme_solve with
+ * one load case.  Host outputs are n_items (x n_c) arrays.  Returns the worst
+ * outcome over the items.
+ */
+int basic_scheme_solve_batch(const lat_plan* plan, const lat_batch_item* items, int n_items,
+                             double tol, int maxit, const lat_solve_opts* opts,
+                             double* sigma_bar, int* iters, double* resid,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * basic_scheme_solve_noalloc -- basic_scheme_solve for callers that cannot

@@ -18,7 +18,8 @@ from ._build import LIB
 LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
 LAT_FP64, LAT_MIXED = 0, 1
 LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
-HIST_CAP = 16384
+HIST_CAP = 4096
+BATCH_MAX_PHASES = 16
 
 _lib = None
 
@@ -33,7 +34,8 @@ class LatticeError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("resid_history", ctypes.POINTER(ctypes.c_double))]
+                ("warm_start", ctypes.c_int), ("resid_history", ctypes.POINTER(ctypes.c_double)),
+                ("mixed_increment", ctypes.c_int)]
 
 
 def lib():
@@ -153,7 +155,7 @@ def lattice_fft(plan, x, inverse=False, stream=None):
 
 def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
                        boundary="average", eps0=None, want_sigma=False, history=False, workspace=None,
-                       eps_out=None, stream=None):
+                       eps_out=None, stream=None, mixed_increment=True):
     """Algorithm 1 on the GPU.  Returns a dict of torch/numpy results.
 
     phase      uint8 CUDA tensor (m,), plan order
@@ -190,7 +192,8 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     resid = np.zeros(n_loads)
     hist = np.zeros((n_loads, max(maxit, 1))) if history else None
     opts = _Opts(prec, bnd, 1 if eps0 is not None else 0,
-                 hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None)
+                 hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
+                 1 if mixed_increment else 0)
     rc = lib().basic_scheme_solve(
         plan.handle, ctypes.c_void_p(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
         ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
@@ -253,7 +256,7 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
     resid = np.zeros(n_loads)
-    opts = _Opts(prec, bnd, 0, None)
+    opts = _Opts(prec, bnd, 0, None, 1)
     L = lib()
     f = L.basic_scheme_solve_noalloc
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3 + \
@@ -268,3 +271,71 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
            resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream))
     _check(rc)
     return dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int), ("stiffness", ctypes.POINTER(ctypes.c_double)),
+                ("C0", ctypes.c_double * 2), ("E", ctypes.POINTER(ctypes.c_double)), ("eps", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p)]
+
+
+def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit=1000, precision="fp64",
+                             boundary="average", want_sigma=False, history=False, workspace=None, eps_out=None,
+                             stream=None, mixed_increment=True):
+    """Algorithm 1 for a batch of independent microstructures on one lattice, in one set of launches.
+
+    phases       list of uint8 CUDA tensors (m,)
+    stiffnesses  list of (n_phases_i, 6, 6) Voigt matrices (n_phases_i <= 16)
+    C0s          list of (lam0, mu0)
+    Es           (n_items, n_c) macroscopic strains
+    Returns dict(eps (n_items, n_c, m) torch, sigma, sigma_bar, iters, resid, status[, history]).
+    """
+    import torch
+    n = len(phases)
+    Es = np.asarray(Es, dtype=np.float64).reshape(n, plan.n_c)
+    dev = phases[0].device
+    eps = eps_out if eps_out is not None else torch.empty((n, plan.n_c, plan.m), dtype=torch.float64, device=dev)
+    sigma = torch.empty_like(eps) if want_sigma else None
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    keep = []
+    items = (_BatchItem * n)()
+    for i in range(n):
+        if phases[i].dtype != torch.uint8 or not phases[i].is_cuda or phases[i].numel() != plan.m:
+            raise TypeError("phase %d must be a uint8 CUDA tensor with m entries" % i)
+        st_i, st_p = _f64(np.asarray(stiffnesses[i], dtype=np.float64).reshape(-1, 36))
+        e_i, e_p = _f64(Es[i])
+        keep += [st_i, e_i]
+        it = items[i]
+        it.phase = phases[i].data_ptr()
+        it.n_phases = st_i.shape[0]
+        it.stiffness = st_p
+        it.C0[0], it.C0[1] = float(C0s[i][0]), float(C0s[i][1])
+        it.E = e_p
+        it.eps = eps[i].data_ptr()
+        it.sigma = sigma[i].data_ptr() if sigma is not None else None
+    L = lib()
+    L.lattice_batch_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    L.lattice_batch_workspace_bytes.restype = ctypes.c_size_t
+    wsb = int(L.lattice_batch_workspace_bytes(plan.handle, n, prec))
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sbar = np.zeros((n, plan.n_c))
+    iters = np.zeros(n, dtype=np.int32)
+    resid = np.zeros(n)
+    hist = np.zeros((n, max(maxit, 1))) if history else None
+    opts = _Opts(prec, bnd, 0, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
+                 1 if mixed_increment else 0)
+    f = L.basic_scheme_solve_batch
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(_BatchItem), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                  ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    rc = f(plan.handle, items, n, float(tol), int(maxit), ctypes.byref(opts),
+           sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+           _stream(stream))
+    _check(rc)
+    out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
+    if history:
+        out["history"] = [hist[i, :min(int(iters[i]), maxit, HIST_CAP)] for i in range(n)]
+    return out

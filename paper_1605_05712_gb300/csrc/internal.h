@@ -9,7 +9,7 @@
 
 #define LAT_MAX_AX 6
 #define LAT_MAX_GROUPS 3
-#define LAT_HIST_CAP 16384  // residuals kept per load case in the workspace
+#define LAT_HIST_CAP 4096  // residuals kept per item in the workspace
 
 // One logical FFT axis in storage order (row-major, last = contiguous row).
 struct LatAxis {

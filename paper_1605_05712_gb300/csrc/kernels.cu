@@ -73,12 +73,12 @@ __device__ __forceinline__ void v_to_h(const LatDev& dv, const int64_t* v, int64
 // eps_hat = -Gammabar0(k) : tau_hat / m at the frequency with v = e_d Q^{-T} E^{-1} k (mod e_d);
 // in/out are n_c complex values.  v == 0 (k = 0) -> E (or 0 for an increment).
 template <typename Real, int NC>
-__device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt, const int64_t* v,
-                                            typename cplx_of<Real>::type* val) {
+__device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
+                                            const int64_t* v, typename cplx_of<Real>::type* val) {
   typedef typename cplx_of<Real>::type C;
   constexpr int d = (NC == 6) ? 3 : 2, n_c = NC;
   if (v[0] == 0 && v[1] == 0 && v[2] == 0) {
-    for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(mt.E[c], 0.0);
+    for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(item->E[c], 0.0);
     return;
   }
   int64_t hi[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, hn[3] = {0, 0, 0};
@@ -93,7 +93,7 @@ __device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt,
     for (int c = 0; c < n_c; ++c) val[c] = cmake<C>(0.0, 0.0);
     return;
   }
-  const Real c1 = (Real)mt.c1, c2 = (Real)mt.c2, sc = (Real)mt.gscale;
+  const Real c1 = (Real)item->c1, c2 = (Real)item->c2, sc = (Real)mt.gscale;
   Real h[3] = {(Real)hi[0], (Real)hi[1], (Real)(d == 3 ? hi[2] : 0)};
   Real tr[NC], ti[NC], gr[NC], gi[NC];
 #pragma unroll
@@ -146,6 +146,7 @@ __device__ double ordered_sum(const double* p, int n) {
 }
 
 // ------------------------------------------------------------------ row pass
+// grid: (row blocks, items); one block = rpc rows x n_c components of one item
 template <typename Real, int NC>
 __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   typedef typename cplx_of<Real>::type C;
@@ -153,6 +154,11 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;
   const int Rh = dv.Rh, lgRh = dv.log2Rh, rpc = a.rpc, lgrpc = __ffs(a.rpc) - 1;
   const int nlines = n_c * rpc;
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
+  const bool update = (a.flags & ROW_UPDATE) != 0;
+  if (update && *(volatile const int*)&isc->done) return;  // this item finished earlier
   C* buf = (C*)smem_raw;
   C* nyq = buf + (size_t)nlines * Rh;
   double* red = (double*)(nyq + nlines);
@@ -160,8 +166,11 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int64_t m = dv.m, R = dv.Rlen, half_m = m / 2, nrows = dv.nrows;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
-  C* T = (C*)a.T;
-  C* TN = (C*)a.TN;
+  C* T = (C*)a.T + item_i * a.t_stride;
+  C* TN = (C*)a.TN + item_i * a.tn_stride;
+  double* eps = item->eps;
+  const uint8_t* phase = item->phase;
+  const double* Dtab = item->Dtab;
   const C* tw = (const C*)dv.tw;
   const int tw_log2 = dv.tw_log2, lgR = lgRh + 1;
   const int npl = Rh / 2 + 1;
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, n = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
-      const double2 v = *(const double2*)(a.eps + c * m + (r0 + row) * R + 2 * n);
+      const double2 v = *(const double2*)(eps + c * m + (r0 + row) * R + 2 * n);
       buf[idx] = cmake<C>(v.x, v.y);
     }
     __syncthreads();
@@ -211,8 +220,10 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 
   // pointwise: update, residual, polarization
   double dsum = 0.0;
-  const bool update = (a.flags & ROW_UPDATE) != 0;
-  const bool incr = (a.flags & ROW_INCREMENT) != 0;
+  // increment form: T carries delta^(n-1) once the first update is done (iteration counter > 0);
+  // the polarization is always taken of the increment
+  const bool tau_of_delta = update && (a.flags & ROW_INCREMENT) != 0;
+  const bool incr = tau_of_delta && (*(volatile const int*)&isc->iter > 0);
   for (int idx = tid; idx < rpc * Rh; idx += nthr) {
     const int row = idx >> lgRh, n = idx & (Rh - 1);
     const int64_t g = (r0 + row) * R + 2 * n;
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     if (update) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
-        double2* pe = (double2*)(a.eps + c * m + g);
+        double2* pe = (double2*)(eps + c * m + g);
         const double2 old = *pe;
         double n0 = (double)e0[c], n1 = (double)e1[c];
         double d0, d1;
@@ -242,11 +253,15 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
         const double wgt = (c >= D) ? 2.0 : 1.0;
         dsum += wgt * (d0 * d0 + d1 * d1);
         *pe = make_double2(n0, n1);
+        if (tau_of_delta) {
+          e0[c] = (Real)d0;
+          e1[c] = (Real)d1;
+        }
       }
     }
-    const uchar2 ph = *(const uchar2*)(a.phase + g);
-    const double* D0 = a.mat.Dtab + (int)ph.x * n_c * n_c;
-    const double* D1 = a.mat.Dtab + (int)ph.y * n_c * n_c;
+    const uchar2 ph = *(const uchar2*)(phase + g);
+    const double* D0 = Dtab + (int)ph.x * n_c * n_c;
+    const double* D1 = Dtab + (int)ph.y * n_c * n_c;
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
       Real t0 = 0, t1 = 0;
@@ -295,7 +310,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
       int64_t v[3] = {0, 0, 0};
 #pragma unroll
       for (int r = 0; r < D; ++r) v[r] = mod_ed(dv, (int64_t)k * dv.ax_cv[dv.nax - 1][r]);
-      green_point<Real, NC>(dv, a.mat, v, val);
+      green_point<Real, NC>(dv, a.mat, item, v, val);
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
@@ -315,29 +330,41 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     TN[c * nrows + r0 + row] = nyq[idx];
   }
   if (!update) return;
-  // residual: block partial -> last block sums in block order, decides convergence
+  // residual: block partial -> the item's last block sums in block order and decides its
+  // convergence; the last item to arrive in this iteration sets the WHILE condition
+  double* partials = a.it.partials + item_i * a.it.pstride;
   const double bs = block_sum(dsum, red);
   if (tid == 0) {
-    a.it.partials[blockIdx.x] = bs;
+    partials[blockIdx.x] = bs;
     __threadfence();
-    const unsigned t = atomicAdd(a.it.counter, 1u);
+    const unsigned t = atomicAdd(&isc->counter, 1u);
     s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return;
   if (tid < 32) {
     __threadfence();
-    const double s = ordered_sum(a.it.partials, gridDim.x);
+    const double s = ordered_sum(partials, gridDim.x);
     if (tid == 0) {
-      const double r = sqrt(s) / a.it.norm0;
-      const int n = *a.it.iter + 1;
-      *a.it.iter = n;
-      if (n - 1 < LAT_HIST_CAP) a.it.hist[n - 1] = r;
-      *a.it.last_r = r;
+      const double r = sqrt(s) / item->norm0;
+      const int n = isc->iter + 1;
+      isc->iter = n;
+      if (n - 1 < LAT_HIST_CAP) a.it.hist[(size_t)item_i * LAT_HIST_CAP + n - 1] = r;
+      isc->last_r = r;
       const bool cont = isfinite(r) && !(r < a.it.tol) && n < a.it.maxit;
-      if (!cont) *a.it.done = 1;
-      *a.it.counter = 0u;
-      if (a.it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.it.cond, cont ? 1u : 0u);
+      isc->counter = 0u;
+      if (!cont) isc->done = 1;
+      __threadfence();
+      GlobScal* gs = a.it.glob;
+      const unsigned arrived = atomicAdd(&gs->arrivals, 1u);
+      if ((int)arrived == *(volatile int*)&gs->active - 1) {  // every active item has reported
+        int active = 0;
+        for (int i = 0; i < a.it.n_items; ++i)
+          active += !*(volatile const int*)&((const ItemScal*)((const char*)a.it.scal + (size_t)i * 256))->done;
+        gs->active = active;
+        gs->arrivals = 0u;
+        if (a.it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.it.cond, active > 0 ? 1u : 0u);
+      }
     }
   }
 }
@@ -346,7 +373,8 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 template <typename Real, int NC>
 __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   typedef typename cplx_of<Real>::type C;
-  if (a.done && *(volatile const int*)a.done) return;
+  const int item_i = blockIdx.y;
+  if (a.scal && *(volatile const int*)&((const ItemScal*)((const char*)a.scal + (size_t)item_i * 256))->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = (C*)smem_raw;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -373,7 +401,7 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   const int wv = (int)min((int64_t)w, inner_count - i0);
   const int lgw = __ffs(w) - 1, lgG = __ffs(G) - 1;
   const int64_t plane = a.outer * (int64_t)G * inner_count;
-  C* dst = (C*)(nyqt ? a.TN : a.T);
+  C* dst = nyqt ? (C*)a.TN + item_i * a.tn_stride : (C*)a.T + item_i * a.t_stride;
   const C* src = (a.Tin && !nyqt) ? (const C*)a.Tin : dst;
   const C* tw = (const C*)dv.tw;
   const int lg_slots = __ffs(a.row_slots) - 1;
@@ -453,7 +481,7 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
       C val[NC];
 #pragma unroll
       for (int f = 0; f < n_f; ++f) val[f] = s[(size_t)f * G * w + idx];
-      if constexpr (NC >= 3) green_point<Real, NC>(dv, a.mat, v, val);
+      if constexpr (NC >= 3) green_point<Real, NC>(dv, a.mat, a.items + item_i, v, val);
 #pragma unroll
       for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = val[f];
     }
@@ -520,40 +548,41 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
 }
 
 // ------------------------------------------------------------------ fill, effective stress
-struct FillArgs {
-  double E[6];
-};
-__global__ void fill_kernel(double* eps, int n_c, int64_t m, FillArgs fa) {
+__global__ void fill_kernel(const ItemDev* items, int n_c, int64_t m) {
+  const ItemDev* it = items + blockIdx.y;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
-    for (int c = 0; c < n_c; ++c) eps[c * m + i] = fa.E[c];
+    for (int c = 0; c < n_c; ++c) it->eps[c * m + i] = it->E[c];
 }
 
-// sigma_y = C_y : eps_y and sigma_bar = (1/m) sum_y sigma_y  (Sec. 3.1, effective matrix)
+// sigma_y = C_y : eps_y and sigma_bar = (1/m) sum_y sigma_y  (Sec. 3.1, effective matrix); grid.y = item
 __global__ void __launch_bounds__(256) eff_kernel(LatDev dv, EffArgs a) {
   __shared__ double red[32];
   __shared__ int s_last;
   const int n_c = dv.n_c;
+  const ItemDev* it = a.items + blockIdx.y;
+  ItemScal* isc = (ItemScal*)((char*)a.scal + (size_t)blockIdx.y * 256);
+  double* partials = a.partials + blockIdx.y * a.pstride;
   const int64_t m = dv.m, stride = (int64_t)gridDim.x * blockDim.x;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const double* Cp = a.Ctab + (int)a.phase[i] * n_c * n_c;
+    const double* Cp = it->Ctab + (int)it->phase[i] * n_c * n_c;
     double e[6];
-    for (int c = 0; c < n_c; ++c) e[c] = a.eps[c * m + i];
+    for (int c = 0; c < n_c; ++c) e[c] = it->eps[c * m + i];
     for (int c = 0; c < n_c; ++c) {
       double sgm = 0;
       for (int q = 0; q < n_c; ++q) sgm += __ldg(Cp + c * n_c + q) * e[q];
-      if (a.sigma) a.sigma[c * m + i] = sgm;
+      if (it->sigma) it->sigma[c * m + i] = sgm;
       acc[c] += sgm;
     }
   }
   for (int c = 0; c < n_c; ++c) {
     const double bs = block_sum(acc[c], red);
-    if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * n_c + c] = bs;
+    if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * n_c + c] = bs;
   }
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    s_last = (atomicAdd(&isc->eff_counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -561,26 +590,28 @@ __global__ void __launch_bounds__(256) eff_kernel(LatDev dv, EffArgs a) {
   if (threadIdx.x < 32) {
     for (int c = 0; c < n_c; ++c) {
       double t = 0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(a.partials + (int64_t)b * n_c + c);
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (int64_t)b * n_c + c);
       t = warp_sum(t);
-      if (threadIdx.x == 0) a.sigma_bar[c] = t / (double)m;
+      if (threadIdx.x == 0) isc->sigma_bar[c] = t / (double)m;
     }
-    if (threadIdx.x == 0) *a.counter = 0u;
+    if (threadIdx.x == 0) isc->eff_counter = 0u;
   }
 }
 
 // ------------------------------------------------------------------ launchers
 template <typename Real>
-void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int nthreads, size_t smem, cudaStream_t st) {
-  if (dv.n_c == 6) row_pass_kernel<Real, 6><<<nblocks, nthreads, smem, st>>>(dv, a);
-  else row_pass_kernel<Real, 3><<<nblocks, nthreads, smem, st>>>(dv, a);
+void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
+                     cudaStream_t st) {
+  const dim3 grid(nblocks, n_items);
+  if (dv.n_c == 6) row_pass_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+  else row_pass_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
-void launch_col_pass(const LatDev& dv, const ColArgs& a, int nthreads, size_t smem, cudaStream_t st) {
-  const int64_t nb = a.outer * (a.tiles_main + a.tiles_nyq);
-  if (a.n_f == 6) col_pass_kernel<Real, 6><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
-  else if (a.n_f == 3) col_pass_kernel<Real, 3><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
-  else col_pass_kernel<Real, 1><<<(unsigned)nb, nthreads, smem, st>>>(dv, a);
+void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st) {
+  const dim3 grid((unsigned)(a.outer * (a.tiles_main + a.tiles_nyq)), n_items);
+  if (a.n_f == 6) col_pass_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+  else if (a.n_f == 3) col_pass_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
+  else col_pass_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale, int rpc,
@@ -588,21 +619,19 @@ void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, in
   const int64_t nb = dv.nrows / rpc;
   row_complex_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, in, out, n_f, inverse, scale, rpc);
 }
-void launch_fill(double* eps, int n_c, int64_t m, const double* E, cudaStream_t st) {
-  FillArgs fa;
-  for (int c = 0; c < 6; ++c) fa.E[c] = c < n_c ? E[c] : 0.0;
+void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st) {
   int64_t nb = (m + 255) / 256;
-  if (nb > 4096) nb = 4096;
-  fill_kernel<<<(unsigned)nb, 256, 0, st>>>(eps, n_c, m, fa);
+  if (nb > 2048) nb = 2048;
+  fill_kernel<<<dim3((unsigned)nb, n_items), 256, 0, st>>>(items, n_c, m);
 }
-void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, cudaStream_t st) {
-  eff_kernel<<<nblocks, 256, 0, st>>>(dv, a);
+void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cudaStream_t st) {
+  eff_kernel<<<dim3(nblocks, n_items), 256, 0, st>>>(dv, a);
 }
 
-template void launch_row_pass<double>(const LatDev&, const RowArgs&, int, int, size_t, cudaStream_t);
-template void launch_row_pass<float>(const LatDev&, const RowArgs&, int, int, size_t, cudaStream_t);
-template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, size_t, cudaStream_t);
-template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, size_t, cudaStream_t);
+template void launch_row_pass<double>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_row_pass<float>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
+template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_row_complex<double>(const LatDev&, const void*, void*, int, int, double, int, int, size_t,
                                          cudaStream_t);
 

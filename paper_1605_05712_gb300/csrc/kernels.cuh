@@ -1,4 +1,4 @@
-// kernels.cuh -- argument blocks shared by kernels.cu and solve.cu.
+// kernels.cuh -- argument blocks shared by kernels.cu and the solve drivers.
 #pragma once
 #include "internal.h"
 
@@ -13,76 +13,99 @@
 #define COL_GAMMA 1
 #define COL_INV 2
 
+// One independent problem of a batched solve (a load case and/or a microstructure).
+struct ItemDev {
+  double* eps;           // n_c planes of m binary64 (plan order)
+  double* sigma;         // NULL or n_c planes
+  const uint8_t* phase;  // m phase ids
+  const double* Dtab;    // n_phases x n_c x n_c: (C_p - C0) on tensor components
+  const double* Ctab;    // n_phases x n_c x n_c: C_p on tensor components
+  double E[6];           // macroscopic strain, tensor components
+  double c1, c2;         // Green operator constants of this item's C0
+  double norm0;          // sqrt(m) ||E||_F (1 if E = 0)
+};
+
+// Device scalars of one item (the first bytes of its 256-byte slot)
+struct ItemScal {
+  unsigned counter;      // last-block-done counter of the row pass (reset by the last block)
+  int done;              // item finished (converged, maxit, or non-finite residual)
+  int iter;              // iterations performed
+  unsigned eff_counter;  // last-block counter of the effective-stress kernel
+  double last_r;         // last residual
+  double sigma_bar[6];   // mean stress
+};
+
+// Batch-wide device scalars
+struct GlobScal {
+  unsigned arrivals;     // items whose row pass finished in this iteration
+  int active;            // items still iterating
+};
+
 struct MatArgs {
-  const double* Dtab;   // n_phases x n_c x n_c, (C_p - C0) acting on tensor components
-  double E[6];          // macroscopic strain, tensor components
-  double lam0, mu0;
-  double c1, c2;        // 1/(2 mu0), (lam0 + mu0) / (mu0 (lam0 + 2 mu0))
-  double gscale;        // -1/m: the forward 1/m of F(M) and the minus sign of the update
+  double gscale;         // -1/m: the forward 1/m of F(M) and the minus sign of the update
   int boundary_zero;
-  int increment;        // 1: spectrum carries an increment, k = 0 gets 0 instead of E
+  int increment;         // 1: spectrum carries an increment, k = 0 gets 0 instead of E
 };
 
 struct IterArgs {
-  double* partials;     // per-block residual partial sums
-  unsigned* counter;    // last-block-done counter (reset to 0 by the last block)
-  int* done;            // stop flag read by the column passes
-  int* iter;            // iterations performed
-  double* hist;         // residual history (LAT_HIST_CAP)
-  double* last_r;       // last residual
-  double norm0, tol;
+  double* partials;      // per item: row-pass block partial sums (stride pstride)
+  int64_t pstride;
+  ItemScal* scal;        // per item, stride 256 bytes
+  GlobScal* glob;
+  double* hist;          // per item residual history, stride LAT_HIST_CAP
+  double tol;
   int maxit;
-  unsigned long long cond;  // cudaGraphConditionalHandle of the enclosing WHILE node
+  int n_items;
+  unsigned long long cond;  // cudaGraphConditionalHandle of the enclosing WHILE node (0: none)
 };
 
 struct RowArgs {
   int flags;
-  int rpc;              // rows per block
-  double* eps;          // n_c planes of m binary64 (plan order)
-  const uint8_t* phase;
-  void* T;              // n_c planes of m/2 complex (Real2), row slots bit-reversed
-  void* TN;             // n_c planes of nrows complex: the Nyquist column
+  int rpc;               // rows per block
+  const ItemDev* items;  // device item table
+  void* T;               // per item: n_c planes of m/2 complex (Real2), row slots bit-reversed
+  void* TN;              // per item: n_c planes of nrows complex, the Nyquist column
+  int64_t t_stride, tn_stride;  // elements (complex) per item
   MatArgs mat;
   IterArgs it;
 };
 
 struct ColArgs {
   int mode;
-  int gidx;             // group index in the plan
+  int gidx;              // group index in the plan
   int a0, a1, G;
-  int64_t outer, inner; // inner excludes the row axis
+  int64_t outer, inner;  // inner excludes the row axis
   int has_twiddle;
-  int w, wN;            // tile widths for T and for the Nyquist plane
-  int64_t tiles_main;   // per outer index
+  int w, wN;             // tile widths for T and for the Nyquist plane
+  int64_t tiles_main;    // per outer index
   int64_t tiles_nyq;
-  int row_slots;        // Rh (solver, half spectrum) or Rlen (complex transform)
+  int row_slots;         // Rh (solver, half spectrum) or Rlen (complex transform)
   int has_nyq;
-  int n_f;              // planes (components or fields)
+  int n_f;               // planes (components or fields)
   void* T;
   void* TN;
-  const void* Tin;      // first pass of the complex transform reads here (else = T)
-  double scale;         // multiply on store (1/m for the last forward pass of lattice_fft), 1 = none
+  int64_t t_stride, tn_stride;  // per item (blockIdx.y)
+  const void* Tin;       // first pass of the complex transform reads here (else = T)
+  double scale;          // multiply on store (1/m for the last forward pass of lattice_fft), 1 = none
+  const ItemDev* items;  // solver: E and Green constants per item
   MatArgs mat;
-  const int* done;      // NULL or stop flag
+  const ItemScal* scal;  // NULL or per-item scalars (skip finished items)
 };
 
 struct EffArgs {
-  const double* eps;
-  double* sigma;        // NULL or n_c planes
-  const uint8_t* phase;
-  const double* Ctab;   // n_phases x n_c x n_c, C_p on tensor components
-  double* partials;     // blocks x n_c
-  unsigned* counter;
-  double* sigma_bar;    // n_c
+  const ItemDev* items;
+  double* partials;      // per item: blocks x n_c
+  int64_t pstride;
+  ItemScal* scal;
 };
 
 template <typename Real>
-void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int nthreads, size_t smem,
+void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
                      cudaStream_t st);
 template <typename Real>
-void launch_col_pass(const LatDev& dv, const ColArgs& a, int nthreads, size_t smem, cudaStream_t st);
-void launch_fill(double* eps, int n_c, int64_t m, const double* E, cudaStream_t st);
-void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, cudaStream_t st);
+void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st);
+void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st);
+void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cudaStream_t st);
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
                         int rpc, int nthreads, size_t smem, cudaStream_t st);

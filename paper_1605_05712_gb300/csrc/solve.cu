@@ -1,6 +1,11 @@
-// solve.cu -- basic_scheme_solve and lattice_fft: workspace layout, launch geometry and the
-// CUDA-graph WHILE loop that runs Algorithm 1 (Sec. 3.2, arXiv 1605.05712) without a host
-// round trip per iteration.
+// solve.cu -- the solve drivers: workspace layout, launch geometry, batching of independent
+// problems and the CUDA-graph WHILE loop that runs Algorithm 1 (Sec. 3.2, arXiv 1605.05712)
+// without a host round trip per iteration.
+//
+// Every solve is a batch of "items" (load cases of one microstructure, or independent
+// microstructures on one lattice): each kernel launch covers all items (grid.y), each item keeps
+// its own strain, spectrum, material tables, reference medium and convergence state, and blocks of
+// finished items return at once.  The loop runs until every item has stopped.
 #include <math.h>
 #include <string.h>
 
@@ -10,7 +15,6 @@
 #include "solve_detail.h"
 
 namespace latms_detail {
-
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -63,9 +67,8 @@ LatDev make_dev(const lat_plan* P, bool fp32) {
   return dv;
 }
 
-
-// row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile
-int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g) {
+// row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile; n_items blocks in grid.y
+int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items) {
   const int nsm = num_sms();
   const int64_t nrows = P->nrows;
   const int row_len = nyq ? P->Rh : P->Rlen;
@@ -73,7 +76,7 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
     return ((size_t)n_f * rpc * row_len + (nyq ? (size_t)n_f * rpc : 0)) * cs + 32 * sizeof(double);
   };
   int rpc = 1;
-  while (nrows % (2 * rpc) == 0 && rsm(2 * rpc) <= kRowSmemTarget && nrows / (2 * rpc) >= 2 * nsm) rpc *= 2;
+  while (nrows % (2 * rpc) == 0 && rsm(2 * rpc) <= kRowSmemTarget && n_items * (nrows / (2 * rpc)) >= 2 * nsm) rpc *= 2;
   g.rpc = rpc;
   g.row_blocks = (int)(nrows / rpc);
   g.row_smem = rsm(rpc);
@@ -83,7 +86,7 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
     const int64_t ic = G.inner * row_slots;
     int64_t w = std::min<int64_t>(32, ic);
     auto csm = [&](int64_t ww) { return (size_t)n_f * G.G * ww * cs; };
-    while (w > 1 && (csm(w) > kColSmemMax || G.outer * (ic / w) < 2 * nsm)) w /= 2;
+    while (w > 1 && (csm(w) > kColSmemMax || n_items * G.outer * (ic / w) < 2 * nsm)) w /= 2;
     if (csm(w) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column group does not fit in shared memory");
     const int64_t wN = std::min<int64_t>(w, G.inner);
     g.w[k] = (int)w;
@@ -95,28 +98,29 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
   return LAT_OK;
 }
 
-
-Work layout(const lat_plan* P, int n_loads, int precision) {
+Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables) {
   const int n_c = P->d * (P->d + 1) / 2;
   const size_t cs = (precision == LAT_MIXED) ? 8 : 16;
   Work w;
   w.t_per_lc = (size_t)n_c * (P->m / 2) * cs;
   w.tn_per_lc = (size_t)n_c * P->nrows * cs;
+  w.pstride = std::max<int64_t>(P->nrows, (int64_t)kEffBlocksMax * 6);
+  w.table_bytes = (size_t)phases_per_table * n_c * n_c * sizeof(double);
   size_t off = 0;
   w.T = off;
-  off = align256(off + n_loads * w.t_per_lc);
+  off = align256(off + n_items * w.t_per_lc);
   w.TN = off;
-  off = align256(off + n_loads * w.tn_per_lc);
-  w.Dtab = off;
-  off = align256(off + (size_t)kMaxPhases * 36 * sizeof(double));
-  w.Ctab = off;
-  off = align256(off + (size_t)kMaxPhases * 36 * sizeof(double));
+  off = align256(off + n_items * w.tn_per_lc);
+  w.items = off;
+  off = align256(off + (size_t)n_items * sizeof(ItemDev));
+  w.tables = off;
+  off = align256(off + (size_t)n_tables * 2 * w.table_bytes);
   w.partials = off;
-  off = align256(off + (size_t)std::max<int64_t>(P->nrows, 1024 * 6) * sizeof(double));
+  off = align256(off + (size_t)n_items * w.pstride * sizeof(double));
   w.scal = off;
-  off = align256(off + (size_t)n_loads * kScalBytes);
+  off = align256(off + (size_t)n_items * kScalBytes + kScalBytes);
   w.hist = off;
-  off = align256(off + (size_t)n_loads * LAT_HIST_CAP * sizeof(double));
+  off = align256(off + (size_t)n_items * LAT_HIST_CAP * sizeof(double));
   w.total = off;
   return w;
 }
@@ -131,20 +135,20 @@ void voigt_to_tc(const double* V, int d, double* out) {
     for (int J = 0; J < n_c; ++J) out[I * n_c + J] = V[vi[I] * 6 + vi[J]] * (J >= d ? 2.0 : 1.0);
 }
 
-#define CK_SOLVE(x)                                                                        \
-  do {                                                                               \
-    cudaError_t e_ = (x);                                                            \
-    if (e_ != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string(#x) + ": " +   \
-                                                             cudaGetErrorString(e_)); \
+#define CK(x)                                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = (x);                                                                      \
+    if (e_ != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
 template <typename Real>
-void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, cudaStream_t st) {
+void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,
+                     cudaStream_t st) {
   // forward over mid groups (innermost first), Gamma group, inverse mid groups
-  for (int k = P->ngroups - 1; k >= 0; --k) {
+  auto one = [&](int k, int mode) {
     ColArgs c = base;
     const LatGroup& G = P->grp[k];
-    c.mode = (k == 0) ? COL_GAMMA : COL_FWD;
+    c.mode = mode;
     c.gidx = k;
     c.a0 = G.a0;
     c.a1 = G.a1;
@@ -156,62 +160,39 @@ void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, Col
     c.wN = g.wN[k];
     c.tiles_main = g.tiles_main[k];
     c.tiles_nyq = g.tiles_nyq[k];
-    launch_col_pass<Real>(dv, c, kThreads, g.col_smem[k], st);
-  }
-  for (int k = 1; k < P->ngroups; ++k) {
-    ColArgs c = base;
-    const LatGroup& G = P->grp[k];
-    c.mode = COL_INV;
-    c.gidx = k;
-    c.a0 = G.a0;
-    c.a1 = G.a1;
-    c.G = G.G;
-    c.outer = G.outer;
-    c.inner = G.inner;
-    c.has_twiddle = G.has_twiddle;
-    c.w = g.w[k];
-    c.wN = g.wN[k];
-    c.tiles_main = g.tiles_main[k];
-    c.tiles_nyq = g.tiles_nyq[k];
-    launch_col_pass<Real>(dv, c, kThreads, g.col_smem[k], st);
-  }
+    launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
+  };
+  for (int k = P->ngroups - 1; k >= 0; --k) one(k, k == 0 ? COL_GAMMA : COL_FWD);
+  for (int k = 1; k < P->ngroups; ++k) one(k, COL_INV);
 }
+template void enqueue_columns<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
+template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
 
+namespace {
+
+// the WHILE loop as a CUDA graph: body = row pass (update, residual, convergence) + column passes
 template <typename Real>
-int solve_one(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs ra, ColArgs ca, int maxit,
-              cudaStream_t st) {
-  const bool gamma_in_row = (P->nax == 1);
-  // prologue: tau^(0) from eps^(0), forward transform, Gamma, first inverse column passes
-  RowArgs first = ra;
-  first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
-  launch_row_pass<Real>(dv, first, g.row_blocks, kThreads, g.row_smem, st);
-  CK_SOLVE(cudaGetLastError());
-  ColArgs c0 = ca;
-  c0.done = nullptr;
-  enqueue_columns<Real>(dv, P, g, c0, st);
-  CK_SOLVE(cudaGetLastError());
-  // WHILE loop: body = row pass (update + residual + convergence) + column passes
+int launch_loop_graph(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs full, ColArgs ca, int n_items,
+                      cudaStream_t st) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
-  CK_SOLVE(cudaGraphCreate(&graph, 0));
+  CK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
-  CK_SOLVE(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  CK_SOLVE(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK_SOLVE(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  CK_SOLVE(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  RowArgs full = ra;
-  full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (ra.flags & ROW_INCREMENT);
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   full.it.cond = (unsigned long long)handle;
-  launch_row_pass<Real>(dv, full, g.row_blocks, kThreads, g.row_smem, cap);
-  enqueue_columns<Real>(dv, P, g, ca, cap);
+  launch_row_pass<Real>(dv, full, g.row_blocks, n_items, kThreads, g.row_smem, cap);
+  enqueue_columns<Real>(dv, P, g, ca, n_items, cap);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cap, &captured);
   cudaStreamDestroy(cap);
@@ -224,12 +205,244 @@ int solve_one(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs ra
   if (exec) cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
-  (void)maxit;
   return LAT_OK;
 }
 
-template void enqueue_columns<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, cudaStream_t);
-template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, cudaStream_t);
+// the WHILE loop with plain launches: the host reads the number of active items after each iteration
+template <typename Real>
+int launch_loop_plain(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs full, ColArgs ca, int n_items,
+                      int maxit, cudaStream_t st) {
+  full.it.cond = 0;
+  for (int n = 0; n < maxit; ++n) {
+    launch_row_pass<Real>(dv, full, g.row_blocks, n_items, kThreads, g.row_smem, st);
+    enqueue_columns<Real>(dv, P, g, ca, n_items, st);
+    CK(cudaGetLastError());
+    int active = 0;
+    CK(cudaMemcpyAsync(&active, &full.it.glob->active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (active == 0) break;
+  }
+  return LAT_OK;
+}
+
+}  // namespace
+
+int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
+              const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws, const Work& wl,
+              const LatDev& dv, bool use_graph, double* sigma_bar, int* iters, double* resid, cudaStream_t st) {
+  const int n_items = (int)items.size();
+  const int d = P->d, n_c = d * (d + 1) / 2;
+  const int64_t m = P->m;
+  const bool fp32 = (o.precision == LAT_MIXED);
+  // material tables (one per distinct table entry) and the item table
+  const int n_tables = (int)stiff.size();
+  std::vector<double> tabs((size_t)n_tables * 2 * (wl.table_bytes / sizeof(double)), 0.0);
+  const size_t tstride = wl.table_bytes / sizeof(double);
+  for (int t = 0; t < n_tables; ++t) {
+    double C0v[36];
+    memset(C0v, 0, sizeof(C0v));
+    const double lam0 = items[0].C0[0], mu0 = items[0].C0[1];
+    (void)lam0;
+    (void)mu0;
+    for (int p = 0; p < nph[t]; ++p) {
+      double* Dp = &tabs[(size_t)(2 * t) * tstride + (size_t)p * n_c * n_c];
+      double* Cp = &tabs[(size_t)(2 * t + 1) * tstride + (size_t)p * n_c * n_c];
+      voigt_to_tc(stiff[t] + 36 * p, d, Cp);
+      for (int k = 0; k < n_c * n_c; ++k) Dp[k] = Cp[k];
+    }
+  }
+  std::vector<ItemDev> hdev(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const ItemHost& it = items[i];
+    ItemDev& v = hdev[i];
+    memset(&v, 0, sizeof(v));
+    v.eps = it.eps;
+    v.sigma = it.sigma;
+    v.phase = it.phase;
+    v.Ctab = (const double*)(ws + wl.tables + (size_t)(2 * it.table + 1) * wl.table_bytes);
+    v.Dtab = (const double*)(ws + wl.tables + (size_t)(2 * it.table) * wl.table_bytes);
+    const double lam0 = it.C0[0], mu0 = it.C0[1];
+    v.c1 = 0.5 / mu0;
+    v.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+    double nE2 = 0;
+    for (int c = 0; c < 6; ++c) v.E[c] = c < n_c ? it.E[c] : 0.0;
+    for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * it.E[c] * it.E[c];
+    v.norm0 = nE2 > 0 ? sqrt((double)m * nE2) : 1.0;
+  }
+  // D = C - C0 per table (the reference medium is the table's; items sharing a table share C0)
+  for (int t = 0; t < n_tables; ++t) {
+    int owner = -1;
+    for (int i = 0; i < n_items && owner < 0; ++i)
+      if (items[i].table == t) owner = i;
+    if (owner < 0) continue;
+    double C0v[36];
+    memset(C0v, 0, sizeof(C0v));
+    const double lam0 = items[owner].C0[0], mu0 = items[owner].C0[1];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) C0v[i * 6 + j] = lam0;
+      C0v[i * 6 + i] = lam0 + 2 * mu0;
+      C0v[(i + 3) * 6 + (i + 3)] = mu0;
+    }
+    double c0tc[36];
+    voigt_to_tc(C0v, d, c0tc);
+    for (int p = 0; p < nph[t]; ++p) {
+      double* Dp = &tabs[(size_t)(2 * t) * tstride + (size_t)p * n_c * n_c];
+      for (int k = 0; k < n_c * n_c; ++k) Dp[k] -= c0tc[k];
+    }
+  }
+  CK(cudaMemcpyAsync(ws + wl.tables, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ws + wl.items, hdev.data(), hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
+  // device scalars start from zero; the batch starts with every item active
+  CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_items * kScalBytes + kScalBytes, st));
+  GlobScal g0;
+  g0.arrivals = 0;
+  g0.active = n_items;
+  GlobScal* glob = (GlobScal*)(ws + wl.scal + (size_t)n_items * kScalBytes);
+  CK(cudaMemcpyAsync(glob, &g0, sizeof(g0), cudaMemcpyHostToDevice, st));
+  const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
+  if (!o.warm_start) launch_fill(ditems, n_items, n_c, m, st);
+  CK(cudaGetLastError());
+  if (P->nax > 0 && maxit > 0) {
+    Geometry geo;
+    memset(&geo, 0, sizeof(geo));
+    int rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, n_items);
+    if (rc != LAT_OK) return rc;
+    RowArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.rpc = geo.rpc;
+    ra.items = ditems;
+    ra.T = ws + wl.T;
+    ra.TN = ws + wl.TN;
+    ra.t_stride = (int64_t)(wl.t_per_lc / (fp32 ? 8 : 16));
+    ra.tn_stride = (int64_t)(wl.tn_per_lc / (fp32 ? 8 : 16));
+    ra.mat.gscale = -1.0 / (double)m;
+    ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
+    ra.it.partials = (double*)(ws + wl.partials);
+    ra.it.pstride = wl.pstride;
+    ra.it.scal = (ItemScal*)(ws + wl.scal);
+    ra.it.glob = glob;
+    ra.it.hist = (double*)(ws + wl.hist);
+    ra.it.tol = tol;
+    ra.it.maxit = maxit;
+    ra.it.n_items = n_items;
+    ColArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.row_slots = P->Rh;
+    ca.has_nyq = 1;
+    ca.n_f = n_c;
+    ca.T = ra.T;
+    ca.TN = ra.TN;
+    ca.t_stride = ra.t_stride;
+    ca.tn_stride = ra.tn_stride;
+    ca.scale = 1.0;
+    ca.items = ditems;
+    ca.mat = ra.mat;
+    const bool incr = fp32 && o.mixed_increment;
+    const bool gamma_in_row = (P->nax == 1);
+    // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns
+    RowArgs first = ra;
+    first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
+    first.mat.increment = 0;
+    ColArgs c0 = ca;
+    c0.scal = nullptr;
+    c0.mat.increment = 0;
+    RowArgs full = ra;
+    full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0);
+    full.mat.increment = incr ? 1 : 0;
+    ColArgs cl = ca;
+    cl.scal = ra.it.scal;
+    cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
+    if (fp32) {
+      launch_row_pass<float>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+      enqueue_columns<float>(dv, P, geo, c0, n_items, st);
+    } else {
+      launch_row_pass<double>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+      enqueue_columns<double>(dv, P, geo, c0, n_items, st);
+    }
+    CK(cudaGetLastError());
+    if (use_graph)
+      rc = fp32 ? launch_loop_graph<float>(P, dv, geo, full, cl, n_items, st)
+                : launch_loop_graph<double>(P, dv, geo, full, cl, n_items, st);
+    else
+      rc = fp32 ? launch_loop_plain<float>(P, dv, geo, full, cl, n_items, maxit, st)
+                : launch_loop_plain<double>(P, dv, geo, full, cl, n_items, maxit, st);
+    if (rc != LAT_OK) return rc;
+  }
+  EffArgs ea;
+  ea.items = ditems;
+  ea.partials = (double*)(ws + wl.partials);
+  ea.pstride = wl.pstride;
+  ea.scal = (ItemScal*)(ws + wl.scal);
+  const int eff_blocks = (int)std::min<int64_t>(kEffBlocksMax, std::max<int64_t>(1, (m + 255) / 256));
+  launch_eff(dv, ea, eff_blocks, n_items, st);
+  CK(cudaGetLastError());
+  // scalars back to the host
+  std::vector<char> scal((size_t)n_items * kScalBytes);
+  CK(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hist;
+  if (o.resid_history && maxit > 0) {
+    hist.resize((size_t)n_items * LAT_HIST_CAP);
+    CK(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  int status = LAT_OK;
+  for (int i = 0; i < n_items; ++i) {
+    const ItemScal* sc = (const ItemScal*)(scal.data() + (size_t)i * kScalBytes);
+    int it = sc->iter;
+    double r = sc->last_r;
+    if (P->nax == 0) {  // m = 1: every iterate equals E, r_n = 0; stop at the first r_n < tol
+      it = (maxit > 0 && tol > 0) ? 1 : maxit;
+      r = maxit > 0 ? 0.0 : NAN;
+    } else if (maxit == 0) {
+      r = NAN;
+    }
+    if (iters) iters[i] = it;
+    if (resid) resid[i] = r;
+    if (sigma_bar)
+      for (int c = 0; c < n_c; ++c) sigma_bar[i * n_c + c] = sc->sigma_bar[c];
+    if (o.resid_history && maxit > 0) {
+      if (P->nax == 0)
+        for (int k = 0; k < it; ++k) o.resid_history[(size_t)i * maxit + k] = 0.0;
+      for (int k = 0; k < std::min(it, std::min(maxit, LAT_HIST_CAP)) && P->nax > 0; ++k)
+        o.resid_history[(size_t)i * maxit + k] = hist[(size_t)i * LAT_HIST_CAP + k];
+    }
+    int s = LAT_OK;
+    if (!isfinite(r) && maxit > 0) s = LAT_DIVERGED;
+    else if (!(r < tol)) s = LAT_NOT_CONVERGED;
+    status = std::max(status, s);
+  }
+  return status;
+}
+
+int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts& o) {
+  if (maxit < 0 || !(tol >= 0)) return lat_fail(LAT_ERR_ARG, "bad maxit/tol");
+  if (o.precision != LAT_FP64 && o.precision != LAT_MIXED) return lat_fail(LAT_ERR_ARG, "bad precision");
+  if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
+  (void)P;
+  return LAT_OK;
+}
+
+int check_c0(const double* C0) {
+  if (!(C0[1] > 0) || !(C0[0] + 2 * C0[1] > 0)) return lat_fail(LAT_ERR_ARG, "C0 must have mu0 > 0 and lam0 + 2 mu0 > 0");
+  return LAT_OK;
+}
+
+// items of basic_scheme_solve: n_loads load cases of one microstructure
+void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, const double* E, int n_loads,
+                     double* eps, double* sigma, std::vector<ItemHost>& items) {
+  const int n_c = P->d * (P->d + 1) / 2;
+  items.resize(n_loads);
+  for (int lc = 0; lc < n_loads; ++lc) {
+    ItemHost& it = items[lc];
+    it.phase = phase;
+    it.table = 0;
+    it.C0[0] = C0[0];
+    it.C0[1] = C0[1];
+    for (int c = 0; c < n_c; ++c) it.E[c] = E[(size_t)lc * n_c + c];
+    it.eps = eps + (size_t)lc * n_c * P->m;
+    it.sigma = sigma ? sigma + (size_t)lc * n_c * P->m : nullptr;
+  }
+}
 
 }  // namespace latms_detail
 
@@ -239,7 +452,12 @@ void lat_graph_cache_free(lat_plan* P) { (void)P; }
 
 extern "C" size_t lattice_workspace_bytes(const lat_plan* P, int n_loads, int precision) {
   if (!P || n_loads <= 0) return 0;
-  return layout(P, n_loads, precision).total;
+  return layout(P, n_loads, precision, kMaxPhases, 1).total;
+}
+
+extern "C" size_t lattice_batch_workspace_bytes(const lat_plan* P, int n_items, int precision) {
+  if (!P || n_items <= 0) return 0;
+  return layout(P, n_items, precision, LAT_BATCH_MAX_PHASES, n_items).total;
 }
 
 extern "C" size_t lattice_fft_workspace_bytes(const lat_plan* P, int n_fields) {
@@ -256,147 +474,61 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace)
     return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: NULL argument");
   if (n_phases < 1 || n_phases > kMaxPhases) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: n_phases not in 1..256");
-  if (n_loads < 1 || maxit < 0 || !(tol >= 0)) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: bad n_loads/maxit/tol");
+  if (n_loads < 1) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve: n_loads < 1");
   lat_solve_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precision != LAT_FP64 && o.precision != LAT_MIXED) return lat_fail(LAT_ERR_ARG, "bad precision");
-  if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
-  const double lam0 = C0[0], mu0 = C0[1];
-  if (!(mu0 > 0) || !(lam0 + 2 * mu0 > 0)) return lat_fail(LAT_ERR_ARG, "C0 must have mu0 > 0 and lam0 + 2 mu0 > 0");
-  const Work wl = layout(P, n_loads, o.precision);
+  if (int rc = check_common(P, tol, maxit, o)) return rc;
+  if (int rc = check_c0(C0)) return rc;
+  const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
   if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int d = P->d, n_c = d * (d + 1) / 2;
-  const int64_t m = P->m;
-  char* ws = (char*)workspace;
-  // material tables
-  std::vector<double> D(n_phases * n_c * n_c), Cc(n_phases * n_c * n_c);
-  double C0v[36];
-  memset(C0v, 0, sizeof(C0v));
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) C0v[i * 6 + j] = lam0;
-    C0v[i * 6 + i] = lam0 + 2 * mu0;
-    C0v[(i + 3) * 6 + (i + 3)] = mu0;
-  }
-  double c0tc[36];
-  voigt_to_tc(C0v, d, c0tc);
-  for (int p = 0; p < n_phases; ++p) {
-    voigt_to_tc(stiffness + 36 * p, d, &Cc[p * n_c * n_c]);
-    for (int k = 0; k < n_c * n_c; ++k) D[p * n_c * n_c + k] = Cc[p * n_c * n_c + k] - c0tc[k];
-  }
-  CK_SOLVE(cudaMemcpyAsync(ws + wl.Dtab, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK_SOLVE(cudaMemcpyAsync(ws + wl.Ctab, Cc.data(), Cc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK_SOLVE(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_loads * kScalBytes, st));
+  std::vector<ItemHost> items;
+  load_case_items(P, phase, C0, E, n_loads, eps, sigma, items);
+  const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
+  return run_batch(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, true, sigma_bar,
+                   iters, resid, (cudaStream_t)stream);
+}
 
-  const bool fp32 = (o.precision == LAT_MIXED);
-  const size_t cs = fp32 ? 8 : 16;
-  const LatDev dv = make_dev(P, fp32);
-  Geometry geo;
-  memset(&geo, 0, sizeof(geo));
-  if (P->nax > 0) {
-    int rc = geometry(P, n_c, cs, P->Rh, true, geo);
-    if (rc != LAT_OK) return rc;
+extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item* bitems, int n_items, double tol,
+                                        int maxit, const lat_solve_opts* opts, double* sigma_bar, int* iters,
+                                        double* resid, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!P || !bitems || !workspace || n_items < 1) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_batch: bad argument");
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (int rc = check_common(P, tol, maxit, o)) return rc;
+  const int n_c = P->d * (P->d + 1) / 2;
+  std::vector<ItemHost> items(n_items);
+  std::vector<const double*> stiff(n_items);
+  std::vector<int> nph(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const lat_batch_item& b = bitems[i];
+    if (!b.phase || !b.stiffness || !b.E || !b.eps) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_batch: NULL item field");
+    if (b.n_phases < 1 || b.n_phases > LAT_BATCH_MAX_PHASES)
+      return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_batch: item n_phases not in 1..LAT_BATCH_MAX_PHASES");
+    if (int rc = check_c0(b.C0)) return rc;
+    if (((uintptr_t)b.eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+    ItemHost& it = items[i];
+    it.phase = b.phase;
+    it.table = i;
+    it.C0[0] = b.C0[0];
+    it.C0[1] = b.C0[1];
+    for (int c = 0; c < n_c; ++c) it.E[c] = b.E[c];
+    it.eps = b.eps;
+    it.sigma = b.sigma;
+    stiff[i] = b.stiffness;
+    nph[i] = b.n_phases;
   }
-  const int eff_blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (m + 255) / 256));
-  for (int lc = 0; lc < n_loads; ++lc) {
-    char* sc = ws + wl.scal + (size_t)lc * kScalBytes;
-    double* eps_lc = eps + (size_t)lc * n_c * m;
-    const double* E_lc = E + (size_t)lc * n_c;
-    double nE2 = 0;
-    for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * E_lc[c] * E_lc[c];
-    const double norm0 = nE2 > 0 ? sqrt((double)m * nE2) : 1.0;
-    if (!o.warm_start) launch_fill(eps_lc, n_c, m, E_lc, st);
-    CK_SOLVE(cudaGetLastError());
-    if (P->nax > 0 && maxit > 0) {
-      RowArgs ra;
-      memset(&ra, 0, sizeof(ra));
-      ra.rpc = geo.rpc;
-      ra.eps = eps_lc;
-      ra.phase = phase;
-      ra.T = ws + wl.T + lc * wl.t_per_lc;
-      ra.TN = ws + wl.TN + lc * wl.tn_per_lc;
-      ra.mat.Dtab = (const double*)(ws + wl.Dtab);
-      for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E_lc[c] : 0.0;
-      ra.mat.lam0 = lam0;
-      ra.mat.mu0 = mu0;
-      ra.mat.c1 = 0.5 / mu0;
-      ra.mat.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
-      ra.mat.gscale = -1.0 / (double)m;
-      ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
-      ra.it.partials = (double*)(ws + wl.partials);
-      ra.it.counter = (unsigned*)(sc + 0);
-      ra.it.done = (int*)(sc + 4);
-      ra.it.iter = (int*)(sc + 8);
-      ra.it.last_r = (double*)(sc + 16);
-      ra.it.hist = (double*)(ws + wl.hist) + (size_t)lc * LAT_HIST_CAP;
-      ra.it.norm0 = norm0;
-      ra.it.tol = tol;
-      ra.it.maxit = maxit;
-      ColArgs ca;
-      memset(&ca, 0, sizeof(ca));
-      ca.row_slots = P->Rh;
-      ca.has_nyq = 1;
-      ca.n_f = n_c;
-      ca.T = ra.T;
-      ca.TN = ra.TN;
-      ca.Tin = nullptr;
-      ca.scale = 1.0;
-      ca.mat = ra.mat;
-      ca.done = ra.it.done;
-      int rc = fp32 ? solve_one<float>(P, dv, geo, ra, ca, maxit, st) : solve_one<double>(P, dv, geo, ra, ca, maxit, st);
-      if (rc != LAT_OK) return rc;
-    }
-    EffArgs ea;
-    ea.eps = eps_lc;
-    ea.sigma = sigma ? sigma + (size_t)lc * n_c * m : nullptr;
-    ea.phase = phase;
-    ea.Ctab = (const double*)(ws + wl.Ctab);
-    ea.partials = (double*)(ws + wl.partials);
-    ea.counter = (unsigned*)(sc + 24);
-    ea.sigma_bar = (double*)(sc + 32);
-    launch_eff(dv, ea, eff_blocks, st);
-    CK_SOLVE(cudaGetLastError());
-  }
-  // scalars back to the host
-  std::vector<char> scal((size_t)n_loads * kScalBytes);
-  CK_SOLVE(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
-  std::vector<double> hist;
-  if (o.resid_history && maxit > 0) {
-    hist.resize((size_t)n_loads * LAT_HIST_CAP);
-    CK_SOLVE(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  }
-  CK_SOLVE(cudaStreamSynchronize(st));
-  int status = LAT_OK;
-  for (int lc = 0; lc < n_loads; ++lc) {
-    const char* sc = scal.data() + (size_t)lc * kScalBytes;
-    int it = *(const int*)(sc + 8);
-    double r = *(const double*)(sc + 16);
-    if (P->nax == 0) {  // m = 1: every iterate equals E, r_n = 0; stop at the first r_n < tol
-      it = (maxit > 0 && tol > 0) ? 1 : maxit;
-      r = maxit > 0 ? 0.0 : NAN;
-    } else if (maxit == 0) {
-      r = NAN;
-    }
-    if (iters) iters[lc] = it;
-    if (resid) resid[lc] = r;
-    if (sigma_bar)
-      for (int c = 0; c < n_c; ++c) sigma_bar[lc * n_c + c] = ((const double*)(sc + 32))[c];
-    if (o.resid_history && maxit > 0) {
-      if (P->nax == 0)
-        for (int k = 0; k < it; ++k) o.resid_history[(size_t)lc * maxit + k] = 0.0;
-      for (int k = 0; k < std::min(it, std::min(maxit, LAT_HIST_CAP)) && P->nax > 0; ++k)
-        o.resid_history[(size_t)lc * maxit + k] = hist[(size_t)lc * LAT_HIST_CAP + k];
-    }
-    int s = LAT_OK;
-    if (!isfinite(r) && maxit > 0) s = LAT_DIVERGED;
-    else if (!(r < tol)) s = LAT_NOT_CONVERGED;
-    status = std::max(status, s);
-  }
-  return status;
+  const Work wl = layout(P, n_items, o.precision, LAT_BATCH_MAX_PHASES, n_items);
+  if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
+  const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
+  return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, true, sigma_bar, iters, resid,
+                   (cudaStream_t)stream);
 }
 
 extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,
@@ -405,7 +537,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace || !ms_out || n_reps < 1)
     return lat_fail(LAT_ERR_ARG, "lattice_pass_times: bad argument");
   if (P->nax == 0) return lat_fail(LAT_ERR_ARG, "lattice_pass_times: m = 1 has no passes");
-  // one cold solve with maxit = 1 sets up tables, workspace and T; then time plain launches
+  // one solve with maxit = 1 sets up tables, workspace and the spectrum; then time plain launches
   lat_solve_opts o;
   memset(&o, 0, sizeof(o));
   o.precision = precision;
@@ -414,40 +546,36 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   if (rc < 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int d = P->d, n_c = d * (d + 1) / 2;
-  const Work wl = layout(P, 1, precision);
+  const Work wl = layout(P, 1, precision, kMaxPhases, 1);
   char* ws = (char*)workspace;
   const bool fp32 = (precision == LAT_MIXED);
   const LatDev dv = make_dev(P, fp32);
   Geometry geo;
   memset(&geo, 0, sizeof(geo));
-  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo)) != LAT_OK) return rc;
-  char* sc = ws + wl.scal;
+  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, 1)) != LAT_OK) return rc;
+  // keep the item active for every timed launch: maxit far away, tol 0
+  CK(cudaMemsetAsync(ws + wl.scal, 0, 2 * kScalBytes, st));
   RowArgs ra;
   memset(&ra, 0, sizeof(ra));
   ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0);
   ra.rpc = geo.rpc;
-  ra.eps = eps;
-  ra.phase = phase;
+  ra.items = (const ItemDev*)(ws + wl.items);
   ra.T = ws + wl.T;
   ra.TN = ws + wl.TN;
-  ra.mat.Dtab = (const double*)(ws + wl.Dtab);
-  for (int c = 0; c < 6; ++c) ra.mat.E[c] = c < n_c ? E[c] : 0.0;
-  ra.mat.lam0 = C0[0];
-  ra.mat.mu0 = C0[1];
-  ra.mat.c1 = 0.5 / C0[1];
-  ra.mat.c2 = (C0[0] + C0[1]) / (C0[1] * (C0[0] + 2.0 * C0[1]));
   ra.mat.gscale = -1.0 / (double)P->m;
   ra.it.partials = (double*)(ws + wl.partials);
-  ra.it.counter = (unsigned*)(sc + 0);
-  ra.it.done = (int*)(sc + 4);
-  ra.it.iter = (int*)(sc + 8);
-  ra.it.last_r = (double*)(sc + 16);
+  ra.it.pstride = wl.pstride;
+  ra.it.scal = (ItemScal*)(ws + wl.scal);
+  ra.it.glob = (GlobScal*)(ws + wl.scal + kScalBytes);
   ra.it.hist = (double*)(ws + wl.hist);
-  ra.it.norm0 = 1.0;
   ra.it.tol = 0.0;
   ra.it.maxit = 1 << 30;
-  ra.it.cond = 0;  // plain launches: the kernel skips the graph condition when cond == 0
-  CK_SOLVE(cudaMemsetAsync(sc, 0, kScalBytes, st));
+  ra.it.n_items = 1;
+  ra.it.cond = 0;
+  GlobScal g0;
+  g0.arrivals = 0;
+  g0.active = 1;
+  CK(cudaMemcpyAsync(ra.it.glob, &g0, sizeof(g0), cudaMemcpyHostToDevice, st));
   ColArgs ca;
   memset(&ca, 0, sizeof(ca));
   ca.row_slots = P->Rh;
@@ -456,53 +584,53 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ca.T = ra.T;
   ca.TN = ra.TN;
   ca.scale = 1.0;
+  ca.items = ra.items;
   ca.mat = ra.mat;
-  const int nk = 1 + 2 * P->ngroups - 1 + (P->ngroups == 0 ? 1 : 0);
+  const int nk = 1 + (P->ngroups > 0 ? 2 * P->ngroups - 1 : 0);
   std::vector<cudaEvent_t> ev(2 * nk);
-  for (auto& e : ev) CK_SOLVE(cudaEventCreate(&e));
+  for (auto& e : ev) CK(cudaEventCreate(&e));
   std::vector<double> acc(nk, 0.0);
   for (int rep = 0; rep < n_reps; ++rep) {
     int k = 0;
-    CK_SOLVE(cudaEventRecord(ev[2 * k], st));
-    if (fp32) launch_row_pass<float>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
-    else launch_row_pass<double>(dv, ra, geo.row_blocks, kThreads, geo.row_smem, st);
-    CK_SOLVE(cudaEventRecord(ev[2 * k + 1], st));
+    CK(cudaEventRecord(ev[2 * k], st));
+    if (fp32) launch_row_pass<float>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
+    else launch_row_pass<double>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
+    CK(cudaEventRecord(ev[2 * k + 1], st));
     ++k;
-    auto one = [&](int g, int mode) {
+    auto one = [&](int gi, int mode) {
       ColArgs c = ca;
-      const LatGroup& G = P->grp[g];
+      const LatGroup& G = P->grp[gi];
       c.mode = mode;
-      c.gidx = g;
+      c.gidx = gi;
       c.a0 = G.a0;
       c.a1 = G.a1;
       c.G = G.G;
       c.outer = G.outer;
       c.inner = G.inner;
       c.has_twiddle = G.has_twiddle;
-      c.w = geo.w[g];
-      c.wN = geo.wN[g];
-      c.tiles_main = geo.tiles_main[g];
-      c.tiles_nyq = geo.tiles_nyq[g];
+      c.w = geo.w[gi];
+      c.wN = geo.wN[gi];
+      c.tiles_main = geo.tiles_main[gi];
+      c.tiles_nyq = geo.tiles_nyq[gi];
       cudaEventRecord(ev[2 * k], st);
-      if (fp32) launch_col_pass<float>(dv, c, kThreads, geo.col_smem[g], st);
-      else launch_col_pass<double>(dv, c, kThreads, geo.col_smem[g], st);
+      if (fp32) launch_col_pass<float>(dv, c, 1, kThreads, geo.col_smem[gi], st);
+      else launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[gi], st);
       cudaEventRecord(ev[2 * k + 1], st);
       ++k;
     };
-    for (int g = P->ngroups - 1; g >= 0; --g) one(g, g == 0 ? COL_GAMMA : COL_FWD);
-    for (int g = 1; g < P->ngroups; ++g) one(g, COL_INV);
-    CK_SOLVE(cudaGetLastError());
-    CK_SOLVE(cudaStreamSynchronize(st));
+    for (int gi = P->ngroups - 1; gi >= 0; --gi) one(gi, gi == 0 ? COL_GAMMA : COL_FWD);
+    for (int gi = 1; gi < P->ngroups; ++gi) one(gi, COL_INV);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
     for (int j = 0; j < k; ++j) {
       float ms = 0;
-      CK_SOLVE(cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]));
+      CK(cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]));
       acc[j] += ms;
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  const int nkern = 1 + (P->ngroups > 0 ? 2 * P->ngroups - 1 : 0);
-  for (int j = 0; j < 8; ++j) ms_out[j] = j < nkern ? (float)(acc[j] / n_reps) : 0.0f;
-  if (n_out) *n_out = nkern;
+  for (int j = 0; j < 8; ++j) ms_out[j] = j < nk ? (float)(acc[j] / n_reps) : 0.0f;
+  if (n_out) *n_out = nk;
   return LAT_OK;
 }
 
@@ -515,14 +643,14 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t m = P->m;
   if (P->nax == 0) {
-    CK_SOLVE(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return LAT_OK;
   }
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   const LatDev dv = make_dev(P, false);
   Geometry geo;
-  int rc = geometry(P, 1, 16, P->Rlen, false, geo);
+  int rc = geometry(P, 1, 16, P->Rlen, false, geo, 1);
   if (rc != LAT_OK) return rc;
   const double inv_m = 1.0 / (double)m;
   for (int f = 0; f < n_fields; ++f) {
@@ -553,7 +681,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       c.tiles_nyq = 0;
       c.Tin = tin;
       c.scale = scale;
-      launch_col_pass<double>(dv, c, kThreads, geo.col_smem[k], st);
+      launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[k], st);
     };
     if (!inverse) {
       launch_row_complex<double>(dv, fin, fout, 1, 0, P->ngroups == 0 ? inv_m : 1.0, geo.rpc, kThreads,
@@ -564,7 +692,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       launch_row_complex<double>(dv, P->ngroups == 0 ? (const void*)fin : (const void*)fout, fout, 1, 1, 1.0,
                                  geo.rpc, kThreads, geo.row_smem, st);
     }
-    CK_SOLVE(cudaGetLastError());
+    CK(cudaGetLastError());
   }
   return LAT_OK;
 }

@@ -1,6 +1,8 @@
-// solve_detail.h -- launch geometry and workspace layout shared by the solve drivers (not installed).
+// solve_detail.h -- launch geometry, workspace layout and the batch driver shared by the solve
+// entry points (not installed).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -10,8 +12,9 @@ const size_t kMaxSmem = 232448;       // sm_100/sm_103 opt-in dynamic shared mem
 const size_t kRowSmemTarget = 64 * 1024;
 const size_t kColSmemMax = 200 * 1024;
 const int kThreads = 256;
-const int kMaxPhases = 256;
-const size_t kScalBytes = 256;        // device scalars per load case
+const int kMaxPhases = 256;           // phases of the single material of basic_scheme_solve
+const int kEffBlocksMax = 256;        // blocks of the effective-stress reduction per item
+const size_t kScalBytes = 256;        // device scalars per item (ItemScal), plus one slot for GlobScal
 
 struct Geometry {
   int rpc, row_blocks;
@@ -21,19 +24,40 @@ struct Geometry {
   size_t col_smem[LAT_MAX_GROUPS];
 };
 
-// byte offsets of the workspace regions of a solve
+// byte offsets of the workspace regions of a batched solve
 struct Work {
-  size_t T, TN, Dtab, Ctab, partials, scal, hist, total;
-  size_t t_per_lc, tn_per_lc;
+  size_t T, TN, items, tables, partials, scal, hist, total;
+  size_t t_per_lc, tn_per_lc, table_bytes;
+  int64_t pstride;  // doubles of reduction partials per item
+};
+
+// host description of one item of a batch
+struct ItemHost {
+  const uint8_t* phase;
+  int table;        // index of its material table
+  double C0[2];
+  double E[6];
+  double* eps;
+  double* sigma;
 };
 
 int ensure_attrs();
 LatDev make_dev(const lat_plan* P, bool fp32);
-int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g);
-Work layout(const lat_plan* P, int n_loads, int precision);
+int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items);
+Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables);
 void voigt_to_tc(const double* V, int d, double* out);
 template <typename Real>
-void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, cudaStream_t st);
+void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,
+                     cudaStream_t st);
+int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts& o);
+int check_c0(const double* C0);
+void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, const double* E, int n_loads,
+                     double* eps, double* sigma, std::vector<ItemHost>& items);
+// runs a batch on workspace `ws` laid out by `wl`; dv carries the twiddle-table pointers;
+// use_graph: CUDA-graph WHILE loop, else plain launches with a host check per iteration
+int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
+              const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws, const Work& wl,
+              const LatDev& dv, bool use_graph, double* sigma_bar, int* iters, double* resid, cudaStream_t st);
 
 }  // namespace latms_detail
 

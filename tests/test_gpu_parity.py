@@ -239,3 +239,81 @@ def test_full_size_262144_fixed_iterations(cuda, name):
     E[2, 2] = 0.5
     out = run_pair(synth.LATTICES[name], laminate([1, 3]), LAM2, (5.5, 5.5), E, tol=0.0, maxit=4, cuda=cuda)
     check_pair(*out, d=2)
+
+
+# ---------------------------------------------------------------- mixed precision (binary32 bulk)
+MIXED_STRAIN_RTOL = 1e-5     # max relative strain-field error against the binary64 oracle at tol 1e-6
+MIXED_CEFF_RTOL = 1e-6       # relative error of the mean stress (a column of C^eff)
+
+
+@pytest.mark.parametrize("M", [[[256, 0], [0, 256]], [[512, 16], [0, 512]], [[64, 1], [0, 64]],
+                               [[32, 0, 0], [0, 32, 0], [0, 0, 32]], [[64, 1, 0], [0, 64, 1], [0, 0, 64]]])
+def test_mixed_precision_within_stated_tolerance(cuda, M):
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    L = Lattice(M)
+    incl = synth.random_inclusions(3, d, 4, 0.3)
+    ph_p = synth.inclusions_phase(P.points(), P.m, incl)
+    ph_o = synth.inclusions_phase(L.p, L.m, incl)
+    perm = to_oracle_order(P.points(), L)
+    C0 = synth.c0_mean_extremes([1, 10], [1, 10])
+    E = np.zeros((2, P.n_c))
+    E[0, 0] = 1.0
+    E[1, -1] = 0.5
+    g = basic_scheme_solve(P, torch.from_numpy(ph_p).to(cuda), LAM2, C0, E, tol=1e-6, maxit=2000, precision="mixed")
+    assert g["status"] == 0
+    S = stiff_tensors(LAM2, d)
+    for lc in range(2):
+        o = basic_scheme(L, ph_o, S, C0, el.comps_to_sym(E[lc], d), tol=1e-6, maxit=2000)
+        # the increment form reports the same residual sequence up to rounding: same stopping iteration
+        assert abs(int(g["iters"][lc]) - o["iters"]) <= 1
+        eg = comps_to_tensor(g["eps"][lc].cpu().numpy(), d)
+        assert relerr(eg, o["eps"][perm]) < MIXED_STRAIN_RTOL
+        assert relerr(el.comps_to_sym(g["sigma_bar"][lc], d), o["sigma_bar"]) < MIXED_CEFF_RTOL
+
+
+# ---------------------------------------------------------------- batches of microstructures
+@pytest.mark.parametrize("M,prec", [([[128, 8], [0, 64]], "fp64"), ([[16, 4, 0], [0, 16, 4], [0, 0, 16]], "fp64"),
+                                    ([[256, 16], [0, 256]], "mixed")])
+def test_batch_of_microstructures_matches_oracle(cuda, M, prec):
+    # items with different phase fields, phase counts, stiffness, reference media and strains, one launch set
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve_batch, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    L = Lattice(M)
+    perm = to_oracle_order(P.points(), L)
+    rng = np.random.default_rng(11)
+    phases, stiffs, C0s, Es, ph_or = [], [], [], [], []
+    for i in range(5):
+        incl = synth.random_inclusions(100 + i, d, 1 + i, 0.1 + 0.05 * i)
+        ph_p = synth.inclusions_phase(P.points(), P.m, incl)
+        ph_o = synth.inclusions_phase(L.p, L.m, incl)
+        if i % 2:                                    # a third phase in some items
+            ph_p = np.where(P.points()[:, 0] > P.m // 4, 2, ph_p).astype(np.uint8)
+            ph_o = np.where(L.p[:, 0] > L.m // 4, 2, ph_o).astype(np.uint8)
+        contrast = 10.0 ** rng.uniform(-1, 1)
+        st = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(contrast, contrast), synth.iso_voigt(2.0, 0.7)][:2 + i % 2]
+        lams = [1.0, contrast, 2.0][:2 + i % 2]
+        mus = [1.0, contrast, 0.7][:2 + i % 2]
+        phases.append(torch.from_numpy(ph_p).to(cuda))
+        ph_or.append(ph_o)
+        stiffs.append(st)
+        C0s.append(synth.c0_mean_extremes(lams, mus))
+        Es.append(rng.standard_normal(P.n_c))
+    tol = 1e-6 if prec == "mixed" else 1e-9
+    g = basic_scheme_solve_batch(P, phases, stiffs, C0s, np.array(Es), tol=tol, maxit=3000, precision=prec)
+    for i in range(5):
+        S = stiff_tensors(stiffs[i], d)
+        o = basic_scheme(L, ph_or[i], S, C0s[i], el.comps_to_sym(Es[i], d), tol=tol, maxit=3000)
+        eg = comps_to_tensor(g["eps"][i].cpu().numpy(), d)
+        sb = el.comps_to_sym(g["sigma_bar"][i], d)
+        if prec == "fp64":
+            assert int(g["iters"][i]) == o["iters"]
+            assert relerr(eg, o["eps"][perm]) < RTOL and relerr(sb, o["sigma_bar"]) < RTOL
+        else:
+            assert abs(int(g["iters"][i]) - o["iters"]) <= 1
+            assert relerr(eg, o["eps"][perm]) < MIXED_STRAIN_RTOL
+            assert relerr(sb, o["sigma_bar"]) < MIXED_CEFF_RTOL
