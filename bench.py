@@ -35,6 +35,7 @@ N_INT = [1, 3]
 TOL = 1e-8
 MAXIT = 2000
 METRIC = "lattice-point iterations/s"
+FP64_PEAK_TFLOPS = 1.25
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -128,22 +129,69 @@ def setup(dev):
     return out
 
 
-def run_step(work, stiff, C0, E, ws, eps):
+def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
+    """One pass of the workload.  fp64_separate: each load case its own solve (the configured
+    form); fp64_batched / mixed_batched: the three load cases of a lattice in one batched solve."""
     from paper_1605_05712_gb300 import basic_scheme_solve
     tot = 0
     iters = []
     for w in work:
-        g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=TOL, maxit=MAXIT, workspace=ws, eps_out=eps)
-        iters.append([int(x) for x in g["iters"]])
-        tot += w["plan"].m * int(np.sum(g["iters"]))
+        if mode == "fp64_separate":
+            its = []
+            for lc in range(E.shape[0]):
+                g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E[lc:lc + 1], tol=tol, maxit=MAXIT,
+                                       workspace=ws, eps_out=eps[lc:lc + 1])
+                its.append(int(g["iters"][0]))
+        else:
+            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
+                                   eps_out=eps, precision="mixed" if mode.startswith("mixed") else "fp64")
+            its = [int(x) for x in g["iters"]]
+        iters.append(its)
+        tot += w["plan"].m * int(np.sum(its))
     return tot, iters
 
 
-def plan_info(P):
-    import ctypes
-    # geometry the library chose, reconstructed from the plan's divisors for the flop/byte model
-    from paper_1605_05712_gb300 import lib  # noqa: F401
-    return P
+def timed(fn, steps, flush, st):
+    import torch
+    times, units, last = [], 0, None
+    for _ in range(steps):
+        flush.fill_(1)                                   # L2 flush between timed steps (not timed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        u, last = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        units += u
+    return float(np.mean(times)), units / steps, last
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("kernels.cu", "fft_smem.cuh", "kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1605_05712_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel_tag):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it was taken on the
+    current kernel sources (sha recorded in the summary); else None."""
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        txt = open(f).read()
+        if "kernel_tag: " + kernel_tag not in txt:
+            continue
+        sha = tr = None
+        for line in txt.splitlines():
+            if line.startswith("kernel_sources_sha: "):
+                sha = line.split(": ", 1)[1].strip()
+            if line.startswith("dram_bytes_per_launch: "):
+                tr = float(line.split(": ", 1)[1])
+        if sha == kernel_sha() and tr is not None:
+            return tr
+    return None
 
 
 def bench_gpu(args):
@@ -173,78 +221,64 @@ def bench_gpu(args):
     if world > 1:
         dist.barrier()
     clk = Clocks(local)
-    times, units, iters = [], 0, None
-    for _ in range(args.steps):
-        flush.fill_(1)                                   # L2 flush between timed steps (not timed)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        u, iters = run_step(work, stiff, C0, E, ws, eps)
-        e1.record(st)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        units += u
-    # end-to-end: host phase -> device, solve, strain -> host, every step
+    ms_step, units, iters = timed(lambda: run_step(work, stiff, C0, E, ws, eps), args.steps, flush, st)
+    # end-to-end: host phase -> device, solves, strain -> host, every step
     eps_host = torch.empty((3, 3, m), dtype=torch.float64).pin_memory()
-    e2e_times, e2e_units = [], 0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
+
+    def e2e_step():
         for w in work:
             w["phase"].copy_(w["phase_host"], non_blocking=True)
-        u, _ = run_step(work, stiff, C0, E, ws, eps)
+        u, it = run_step(work, stiff, C0, E, ws, eps)
         eps_host.copy_(eps, non_blocking=True)
-        e1.record(st)
-        torch.cuda.synchronize()
-        e2e_times.append(e0.elapsed_time(e1))
-        e2e_units += u
+        return u, it
+    ms_e2e, e2e_units, _ = timed(e2e_step, args.steps, flush, st)
     clocks = clk.stop()
-    ms_step = float(np.mean(times))
     if world > 1:
-        t = torch.tensor([ms_step, float(np.mean(e2e_times))], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms_step, ms_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step, ms_e2e = float(t[0]), float(t[1])
-    else:
-        ms_e2e = float(np.mean(e2e_times))
-    value = world * (units / args.steps) / (ms_step / 1e3)
-    e2e_value = world * (e2e_units / args.steps) / (ms_e2e / 1e3)
+    value = world * units / (ms_step / 1e3)
+    e2e_value = world * e2e_units / (ms_e2e / 1e3)
+
+    # variants on the same inputs: batched load cases (binary64, mixed) and time to a 1e-6 residual
+    variants = {}
+    if not args.no_variants:
+        for mode in ("fp64_batched", "mixed_batched"):
+            run_step(work, stiff, C0, E, ws, eps, mode)
+            ms_v, u_v, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode), args.steps, flush, st)
+            variants[mode] = {"value": round(u_v / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 4), "iterations": it_v}
+        ttt = {}
+        for mode in ("fp64_separate", "fp64_batched", "mixed_batched"):
+            run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6)
+            ms_v, _, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6), args.steps, flush, st)
+            ttt[mode] = {"ms": round(ms_v, 4), "iterations": it_v}
+        variants["time_to_resid_1e-6_ms"] = ttt
 
     # per-kernel timing of one iteration on the rank-2 lattice (dominant kernel -> roofline)
     w = work[2]
     P = w["plan"]
     pt = lattice_pass_times(P, w["phase"], stiff, C0, E[0], n_reps=50)
-    geo = dict(m=P.m, R=int(P.divisors[-1]) if P.d_M == 1 else None)
-    # the rank-2 lattice (16, 16384): the library splits 16384 = 128 x 128 -> row 128, group (16, 128)
-    geo_model = {"grid512": dict(m=P.m, R=512, Rh=256, groups=[512]),
-                 "rank1_262144": dict(m=P.m, R=512, Rh=256, groups=[512]),
-                 "rank2_262144": dict(m=P.m, R=128, Rh=64, groups=[2048])}[w["name"]]
-    bytes_row, bytes_col = algorithmic_bytes(geo_model)
-    flops_row, flops_col = row_col_flops(geo_model)
-    kern = ["row_pass", "col_pass"]
+    model = {"m": P.m, "R": 512, "Rh": 256, "groups": [512]}   # the planner's decomposition of all three lattices
+    bytes_row, bytes_col = algorithmic_bytes(model)
+    flops_row, flops_col = row_col_flops(model)
     dom = int(np.argmax(pt[:2]))
     ms_dom = pt[dom]
     pk = peaks()
-    fp64_peak = 1.25e3  # GFLOP/s, nominal GB300 FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
-    if dom == 0:
-        fl, by = flops_row, bytes_row
-    else:
-        fl, by = flops_col[0], bytes_col[0]
-    gflops = fl / (ms_dom * 1e-3) / 1e9
-    gbs = by / (ms_dom * 1e-3) / 1e9
-    hbm = pk.get("hbm_gbs", 6800.0)
-    roof_alu = {"bound": "alu", "achieved": round(gflops / 1e3, 4), "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
-                "frac": round(gflops / fp64_peak, 4), "traffic": None, "kernel": kern[dom] + "<double>",
-                "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                "peak_source": "nominal FP64 1.25 TFLOP/s (not in MEASURED_PEAKS.json)",
-                "per_kernel_ms": [round(x, 5) for x in pt]}
+    fl, by = (flops_row, bytes_row) if dom == 0 else (flops_col[0], bytes_col[0])
+    tag = ("row_pass" if dom == 0 else "col_pass") + "<double,3>/rank2_262144"
+    fp64_peak = FP64_PEAK_TFLOPS
+    roof = {"bound": "alu", "achieved": round(fl / (ms_dom * 1e-3) / 1e12, 4), "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": round(fl / (ms_dom * 1e-3) / 1e12 / fp64_peak, 4),
+            "traffic": profiled_traffic(tag), "kernel": tag,
+            "peak_source": "nominal GB300 binary64 rate 1.25 TFLOP/s (no FP64 entry in the measured peaks; an "
+                           "FMA-loop probe measured 1.19)",
+            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+            "hbm_achieved_gbs": round(by / (ms_dom * 1e-3) / 1e9, 1),
+            "hbm_peak_gbs": pk.get("hbm_gbs"), "per_kernel_ms": [round(x, 5) for x in pt]}
     gpu_launches = 0
-    for w_, it in zip(work, iters):
-        ng = len({"grid512": [512], "rank1_262144": [512], "rank2_262144": [2048]}[w_["name"]])
-        per_it = 1 + (2 * ng - 1)
-        for n in it:
-            gpu_launches += 1 + per_it + n * per_it + 1    # fill, prologue, loop, effective stress
+    for it in iters:
+        for n in it:   # per solve: fill, prologue (row + column), n loop iterations, effective stress
+            gpu_launches += 1 + 2 + 2 * n + 1
     res = {
         "metric": METRIC, "value": round(value, 1), "unit": "point-iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -254,12 +288,13 @@ def bench_gpu(args):
                                "rank-2 [[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64",
                    "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": roof_alu,
+        "roofline": roof,
         "e2e": {"value": round(e2e_value, 1), "unit": "point-iterations/s",
                 "h2d_bytes_per_step": int(sum(w_["plan"].m for w_ in work)),
                 "d2h_bytes_per_step": int(eps.numel() * 8)},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
+        "variants": variants,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -267,6 +302,20 @@ def bench_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res))
+
+
+def profile_case(args):
+    """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
+    import torch
+    from paper_1605_05712_gb300 import lattice_pass_times, lattice_plan, synth
+    prec, M = args.profile_case[0], json.loads(args.profile_case[1])
+    P = lattice_plan(M)
+    ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 3] if P.d == 2 else [1, 3, 2])).cuda()
+    st = [synth.iso_voigt(*l) for l in LAMES]
+    E = np.zeros(P.n_c)
+    E[0] = 1.0
+    ms = lattice_pass_times(P, ph, st, (5.5, 5.5), E, precision=prec, n_reps=args.steps)
+    print(json.dumps({"profile_case": M, "precision": prec, "m": P.m, "ms_per_kernel": ms}))
 
 
 def oracle_sample(seconds, names=("rank2_262144",)):
@@ -335,8 +384,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_gpu(args)

@@ -85,3 +85,145 @@ def laminate_ceff_milton(C1, C2, f1, n, s0=None):
     # S = s0 (s0 I - C^eff)^{-1}  =>  C^eff = s0 I - s0 S^{-1}
     Ceff = s0 * Id - s0 * np.linalg.inv(S)
     return from_mandel(Ceff, d)
+
+
+# ------------------------------------------------------------------ generalized Hashin structure
+"""Coated confocal ellipsoid (Sec. 4.2, after Milton's neutral coated ellipsoid).
+
+Geometry: x~ = R^{-1} x; the ellipsoidal radius rho(x~) is the largest root of
+sum_i x~_i^2 / (c_i^2 + rho) = 1; core rho <= rho_c, coating rho_c < rho <= rho_e,
+matrix outside.  Semi-axes l_j(rho) = sqrt(c_j^2 + rho); c_3 = inf is the
+elliptic cylinder (2-D problem run in 3-D).
+
+Readings of garbled passages (listed in the design notes):
+  * depolarization factors: the general ellipsoid uses the depolarization integral
+        d_i(rho) = (l1 l2 l3 / 2) int_0^inf ds / ((l_i^2 + s) sqrt(prod_j (l_j^2 + s)))
+    (sum_i d_i = 1); the paper's prolate/oblate formulas are special cases once the
+    garbles are fixed (prolate d3 carries a "-1", d1 = d2 = (1 - d3)/2; oblate
+    d2 = d3 = (1 - d1)/2); the cylinder formulas are used as printed;
+  * grad rho: (grad rho)_i = (2 x~_i / (c_i^2 + rho)) / sum_j x~_j^2 / (c_j^2 + rho)^2,
+    from implicit differentiation of the defining equation;
+  * the rotation R takes e_1 to n (Rodrigues), or is given directly.
+"""
+
+
+def depolarization(c, rho):
+    """d_i(rho) for semi-axes c (c_3 may be inf: elliptic cylinder)."""
+    from scipy.integrate import quad
+    c = np.asarray(c, dtype=np.float64)
+    if not np.isfinite(c[2]):
+        l1, l2 = np.sqrt(c[0] ** 2 + rho), np.sqrt(c[1] ** 2 + rho)
+        return np.array([l2 / (l1 + l2), l1 / (l1 + l2), 0.0])
+    l2 = c ** 2 + rho
+    pref = np.sqrt(np.prod(l2)) / 2.0
+    out = []
+    for i in range(3):
+        f = lambda s, i=i: 1.0 / ((l2[i] + s) * np.sqrt((l2[0] + s) * (l2[1] + s) * (l2[2] + s)))
+        # substitute s = t / (1 - t) to map [0, inf) onto [0, 1)
+        g = lambda t, f=f: f(t / (1.0 - t)) / (1.0 - t) ** 2
+        val, _ = quad(g, 0.0, 1.0, epsabs=0.0, epsrel=1e-13, limit=400)
+        out.append(pref * val)
+    return np.array(out)
+
+
+def g_of(c, rho):
+    c = np.asarray(c, dtype=np.float64)
+    fin = np.isfinite(c)
+    return np.prod(c[fin] ** 2 + rho)
+
+
+def ellipsoidal_radius(c, xt):
+    """Largest root rho of sum_i xt_i^2 / (c_i^2 + rho) = 1 (rows of xt), bisection then Newton."""
+    c = np.asarray(c, dtype=np.float64)
+    xt = np.atleast_2d(np.asarray(xt, dtype=np.float64))
+    fin = np.isfinite(c)
+    cc = c[fin] ** 2
+    x2 = xt[:, fin] ** 2
+    F = lambda r: np.sum(x2 / (cc + r[:, None]), axis=1) - 1.0
+    lo = np.full(len(xt), -cc.min() + 1e-300)
+    hi = np.full(len(xt), 1.0)
+    while np.any(F(hi) > 0):
+        hi = np.where(F(hi) > 0, 2 * hi + 1.0, hi)
+    for _ in range(200):      # F decreases on (-c_min^2, inf)
+        mid = 0.5 * (lo + hi)
+        pos = F(mid) > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    r = 0.5 * (lo + hi)
+    for _ in range(3):
+        dF = -np.sum(x2 / (cc + r[:, None]) ** 2, axis=1)
+        r = r - F(r) / dF
+    return r
+
+
+def rotation_to(n):
+    """Rotation taking e_1 to the unit vector n (Rodrigues form of the matrix of Sec. 4.2)."""
+    n = np.asarray(n, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    if np.allclose(n, [1, 0, 0]):
+        return np.eye(3)
+    if np.allclose(n, [-1, 0, 0]):
+        return np.diag([-1.0, -1.0, 1.0])
+    K = np.array([[0, -n[1], -n[2]], [n[1], 0, 0], [n[2], 0, 0]])
+    return np.eye(3) + K + K @ K / (1.0 + n[0])
+
+
+class Hashin:
+    """Neutral coated ellipsoid: eps0, C^eff eps0 and the strain field (Sec. 4.2).
+
+    c: (c1, c2, c3) with c3 = inf for the cylinder; rho_c < rho_e; core (lam_c, mu_c) and
+    coating (lam_e, mu_e) isotropic; R rotation (x = R x~).
+    """
+
+    def __init__(self, c, rho_c, rho_e, lam_c, mu_c, lam_e, mu_e, R=None):
+        self.c = np.asarray(c, dtype=np.float64)
+        self.rho_c, self.rho_e = float(rho_c), float(rho_e)
+        self.R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+        self.kc, self.ke = lam_c + 2.0 * mu_c / 3.0, lam_e + 2.0 * mu_e / 3.0
+        self.mu_e = mu_e
+        self.Cc = el.iso_tensor(lam_c, mu_c, 3)
+        self.Ce = el.iso_tensor(lam_e, mu_e, 3)
+        self.Dc = np.diag(depolarization(self.c, self.rho_c))
+        self.fe = self.f(self.rho_e)
+        self.alpha = (3 * self.ke + 4 * self.mu_e) / (9 * (self.kc - self.ke))
+        Se = self.S(self.rho_e)
+        R = self.R
+        self.eps0 = R @ (self.alpha * np.eye(3) + (1 - self.fe) * Se) @ R.T
+        a = self.ke / (self.kc - self.ke) * (self.kc + 4.0 / 3.0 * mu_e) + 4.0 / 3.0 * mu_e * self.fe
+        self.ceff_eps0 = R @ (a * np.eye(3)) @ R.T + R @ (2.0 / 3.0 * mu_e * (1 - self.fe) * (3 * Se - np.eye(3))) @ R.T
+
+    def f(self, rho):
+        return np.sqrt(g_of(self.c, self.rho_c)) / np.sqrt(g_of(self.c, rho))
+
+    def S(self, rho):
+        f = self.f(rho)
+        return (self.Dc - f * np.diag(depolarization(self.c, rho))) / (1.0 - f)
+
+    def region(self, x):
+        """0 core, 1 coating, 2 matrix for points x (rows, cell coordinates centred at the inclusion)."""
+        xt = np.atleast_2d(x) @ self.R  # rows of R^T x
+        rho = ellipsoidal_radius(self.c, xt)
+        return np.where(rho <= self.rho_c, 0, np.where(rho <= self.rho_e, 1, 2)), rho, xt
+
+    def strain(self, x):
+        """Analytic strain field at points x (rows)."""
+        reg, rho, xt = self.region(x)
+        n = len(reg)
+        out = np.empty((n, 3, 3))
+        out[reg == 2] = self.eps0
+        out[reg == 0] = self.R @ (self.alpha * np.eye(3)) @ self.R.T
+        idx = np.nonzero(reg == 1)[0]
+        c = self.c
+        fin = np.isfinite(c)
+        cc = np.where(fin, c, 0.0) ** 2
+        sgc = np.sqrt(g_of(c, self.rho_c))
+        for i in idx:
+            r = rho[i]
+            x_ = xt[i]
+            den = cc + r
+            q = np.where(fin, x_ / den, 0.0) / np.sqrt(g_of(c, r))
+            grad = np.where(fin, 2 * x_ / den, 0.0) / np.sum(np.where(fin, x_ ** 2 / den ** 2, 0.0))
+            Dr = np.diag(depolarization(c, r))
+            loc = self.alpha * np.eye(3) + self.Dc - self.f(r) * Dr + 0.5 * sgc * np.outer(q, grad)
+            out[i] = self.R @ loc @ self.R.T
+        return out

@@ -66,6 +66,7 @@ struct LatDev {
   int Rlen, Rh, log2Rh;
   int64_t m, nrows;
   int64_t ed, ed_mask;        // ed_mask = ed - 1 if ed is a power of two, else -1
+  int h32;                    // 1: e_d is a power of two <= 2^31 and every |h~_i| < 2^31 (32-bit path)
   int64_t MT[3][3];           // M^T (h = M^T v' / e_d)
   int ax_len[LAT_MAX_AX], ax_log2[LAT_MAX_AX];
   int64_t ax_cv[LAT_MAX_AX][3];

@@ -70,51 +70,157 @@ __device__ __forceinline__ void v_to_h(const LatDev& dv, const int64_t* v, int64
   }
 }
 
+// Green-operator constants of one item in the kernel's precision
+template <typename Real>
+struct GreenK {
+  Real c1, c2, sc;
+};
+template <typename Real>
+__device__ __forceinline__ GreenK<Real> green_consts(const ItemDev* item, const MatArgs& mt) {
+  GreenK<Real> g;
+  if constexpr (sizeof(Real) == 4) {
+    g.c1 = item->c1f;
+    g.c2 = item->c2f;
+  } else {
+    g.c1 = item->c1;
+    g.c2 = item->c2;
+  }
+  g.sc = (Real)mt.gscale;
+  return g;
+}
+
+// symmetric representative and h~ = M^T v' in 32-bit arithmetic (plan guarantees the range)
+template <int D>
+__device__ __forceinline__ void v_to_h32(const LatDev& dv, const uint32_t* v, int32_t* h) {
+  const int32_t ed = (int32_t)dv.ed;
+  int32_t vp[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) vp[r] = (2u * v[r] >= (uint32_t)ed) ? (int32_t)v[r] - ed : (int32_t)v[r];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    int32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += (int32_t)dv.MT[i][j] * vp[j];
+    h[i] = acc;
+  }
+}
+
 // eps_hat = -Gammabar0(k) : tau_hat / m at the frequency with v = e_d Q^{-T} E^{-1} k (mod e_d);
 // in/out are n_c complex values.  v == 0 (k = 0) -> E (or 0 for an increment).
+// Real h~ components come from the 32-bit path when the plan allows it, else from int64.
 template <typename Real, int NC>
-__device__ __forceinline__ void green_point(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
-                                            const int64_t* v, typename cplx_of<Real>::type* val) {
+__device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
+                                              const GreenK<Real>& gk, bool zero, bool boundary, const Real* h,
+                                              const Real* h2, typename cplx_of<Real>::type* val) {
   typedef typename cplx_of<Real>::type C;
   constexpr int d = (NC == 6) ? 3 : 2, n_c = NC;
-  if (v[0] == 0 && v[1] == 0 && v[2] == 0) {
+  if (zero) {
+#pragma unroll
     for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(item->E[c], 0.0);
     return;
   }
-  int64_t hi[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, hn[3] = {0, 0, 0};
-  v_to_h<d>(dv, v, hi);
-  bool boundary = false;
-#pragma unroll
-  for (int r = 0; r < d; ++r) {
-    vn[r] = mod_ed(dv, dv.ed - v[r]);
-    if (2 * v[r] == dv.ed) boundary = true;  // v' = -e_d/2: -v has the same representative
-  }
   if (boundary && mt.boundary_zero) {
+#pragma unroll
     for (int c = 0; c < n_c; ++c) val[c] = cmake<C>(0.0, 0.0);
     return;
   }
-  const Real c1 = (Real)item->c1, c2 = (Real)item->c2, sc = (Real)mt.gscale;
-  Real h[3] = {(Real)hi[0], (Real)hi[1], (Real)(d == 3 ? hi[2] : 0)};
   Real tr[NC], ti[NC], gr[NC], gi[NC];
 #pragma unroll
   for (int c = 0; c < n_c; ++c) tr[c] = val[c].x, ti[c] = val[c].y;
   const Real a = Real(1) / (h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-  gamma_apply<Real>(d, h, a, c1, c2, tr, gr);
-  gamma_apply<Real>(d, h, a, c1, c2, ti, gi);
+  gamma_apply<Real>(d, h, a, gk.c1, gk.c2, tr, gr);
+  gamma_apply<Real>(d, h, a, gk.c1, gk.c2, ti, gi);
   if (boundary) {
     // average with -h(-k): Gamma0 is even in h, so evaluate at h(-k) directly
-    v_to_h<d>(dv, vn, hn);
-    Real h2[3] = {(Real)hn[0], (Real)hn[1], (Real)(d == 3 ? hn[2] : 0)};
     const Real a2 = Real(1) / (h2[0] * h2[0] + h2[1] * h2[1] + h2[2] * h2[2]);
     Real gr2[NC], gi2[NC];
-    gamma_apply<Real>(d, h2, a2, c1, c2, tr, gr2);
-    gamma_apply<Real>(d, h2, a2, c1, c2, ti, gi2);
+    gamma_apply<Real>(d, h2, a2, gk.c1, gk.c2, tr, gr2);
+    gamma_apply<Real>(d, h2, a2, gk.c1, gk.c2, ti, gi2);
+#pragma unroll
     for (int c = 0; c < n_c; ++c) gr[c] = Real(0.5) * (gr[c] + gr2[c]), gi[c] = Real(0.5) * (gi[c] + gi2[c]);
   }
+#pragma unroll
   for (int c = 0; c < n_c; ++c) {
-    val[c].x = sc * gr[c];
-    val[c].y = sc * gi[c];
+    val[c].x = gk.sc * gr[c];
+    val[c].y = gk.sc * gi[c];
   }
+}
+
+// frequency from the per-axis spectral indices: kk[x] for the logical axes (row last)
+template <typename Real, int NC>
+__device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
+                                         const GreenK<Real>& gk, const int* kk,
+                                         typename cplx_of<Real>::type* val) {
+  constexpr int d = (NC == 6) ? 3 : 2;
+  Real h[3] = {0, 0, 0}, h2[3] = {0, 0, 0};
+  bool zero = true, boundary = false;
+  if (dv.h32) {
+    uint32_t v[3] = {0u, 0u, 0u}, vn[3];
+    for (int x = 0; x < dv.nax; ++x)
+#pragma unroll
+      for (int r = 0; r < d; ++r) v[r] += (uint32_t)kk[x] * (uint32_t)dv.ax_cv[x][r];  // exact mod 2^32
+    const uint32_t mask = (uint32_t)dv.ed_mask;
+#pragma unroll
+    for (int r = 0; r < d; ++r) {
+      v[r] &= mask;
+      zero = zero && (v[r] == 0u);
+      boundary = boundary || (2u * v[r] == (uint32_t)dv.ed);  // v' = -e_d/2: -v has the same representative
+      vn[r] = (0u - v[r]) & mask;
+    }
+    if (!zero) {
+      int32_t hi[3] = {0, 0, 0};
+      v_to_h32<d>(dv, v, hi);
+#pragma unroll
+      for (int i = 0; i < d; ++i) h[i] = (Real)hi[i];
+      if (boundary) {
+        v_to_h32<d>(dv, vn, hi);
+#pragma unroll
+        for (int i = 0; i < d; ++i) h2[i] = (Real)hi[i];
+      }
+    }
+  } else {
+    int64_t v[3] = {0, 0, 0}, vn[3] = {0, 0, 0};
+    for (int x = 0; x < dv.nax; ++x)
+#pragma unroll
+      for (int r = 0; r < d; ++r) v[r] += (int64_t)kk[x] * dv.ax_cv[x][r];
+#pragma unroll
+    for (int r = 0; r < d; ++r) {
+      v[r] = mod_ed(dv, v[r]);
+      zero = zero && (v[r] == 0);
+      boundary = boundary || (2 * v[r] == dv.ed);
+      vn[r] = mod_ed(dv, dv.ed - v[r]);
+    }
+    if (!zero) {
+      int64_t hi[3] = {0, 0, 0};
+      v_to_h<d>(dv, v, hi);
+#pragma unroll
+      for (int i = 0; i < d; ++i) h[i] = (Real)hi[i];
+      if (boundary) {
+        v_to_h<d>(dv, vn, hi);
+#pragma unroll
+        for (int i = 0; i < d; ++i) h2[i] = (Real)hi[i];
+      }
+    }
+  }
+  green_point_h<Real, NC>(dv, mt, item, gk, zero, boundary, h, h2, val);
+}
+
+// ------------------------------------------------------------------ double-float accumulation
+// Sum of squares carried as an unevaluated pair of binary32 values (hi + lo), with Knuth's TwoSum
+// for the addition and the FMA-based exact product (Dekker) for the square: about 2^-48 relative,
+// the accuracy of a binary64 accumulator, computed on the binary32 pipes.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_sq(DF& acc, float x) {
+  const float p = x * x;
+  const float pe = fmaf(x, x, -p);           // x*x = p + pe exactly
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float e = (acc.hi - (s - bb)) + (p - bb);  // TwoSum error of acc.hi + p
+  const float lo = acc.lo + pe + e;
+  acc.hi = s + lo;                           // renormalise
+  acc.lo = lo - (acc.hi - s);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -166,11 +272,13 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int64_t m = dv.m, R = dv.Rlen, half_m = m / 2, nrows = dv.nrows;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const uint32_t m32 = (uint32_t)m, hm32 = (uint32_t)half_m;
   C* T = (C*)a.T + item_i * a.t_stride;
   C* TN = (C*)a.TN + item_i * a.tn_stride;
   double* eps = item->eps;
   const uint8_t* phase = item->phase;
   const double* Dtab = item->Dtab;
+  const float* Dtab_f = item->Dtab_f;
   const C* tw = (const C*)dv.tw;
   const int tw_log2 = dv.tw_log2, lgR = lgRh + 1;
   const int npl = Rh / 2 + 1;
@@ -179,7 +287,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, n = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
-      const double2 v = *(const double2*)(eps + c * m + (r0 + row) * R + 2 * n);
+      const double2 v = *(const double2*)(eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 2u * n));
       buf[idx] = cmake<C>(v.x, v.y);
     }
     __syncthreads();
@@ -187,7 +295,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, pos = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
-      buf[idx] = T[c * half_m + (r0 + row) * Rh + pos];
+      buf[idx] = T[(uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos];
     }
     for (int idx = tid; idx < nlines; idx += nthr) {
       const int c = idx >> lgrpc, row = idx & (rpc - 1);
@@ -224,9 +332,10 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   // the polarization is always taken of the increment
   const bool tau_of_delta = update && (a.flags & ROW_INCREMENT) != 0;
   const bool incr = tau_of_delta && (*(volatile const int*)&isc->iter > 0);
+  DF dfs = {0.f, 0.f}, dfs_shear = {0.f, 0.f};  // m <= 2^28: in-item offsets stay below 2^31
   for (int idx = tid; idx < rpc * Rh; idx += nthr) {
     const int row = idx >> lgRh, n = idx & (Rh - 1);
-    const int64_t g = (r0 + row) * R + 2 * n;
+    const uint32_t g = (uint32_t)(r0 + row) * (uint32_t)R + 2u * n;
     Real e0[NC], e1[NC];
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
@@ -237,8 +346,21 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     if (update) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
-        double2* pe = (double2*)(eps + c * m + g);
+        double2* pe = (double2*)(eps + (uint32_t)(c * m32) + (uint32_t)g);
         const double2 old = *pe;
+        if constexpr (sizeof(Real) == 4) {
+          if (incr) {  // T carried the binary32 increment itself: no round trip, residual in double-float
+            *pe = make_double2(old.x + (double)e0[c], old.y + (double)e1[c]);
+            if (c >= D) {
+              df_add_sq(dfs_shear, e0[c]);
+              df_add_sq(dfs_shear, e1[c]);
+            } else {
+              df_add_sq(dfs, e0[c]);
+              df_add_sq(dfs, e1[c]);
+            }
+            continue;
+          }
+        }
         double n0 = (double)e0[c], n1 = (double)e1[c];
         double d0, d1;
         if (incr) {
@@ -259,16 +381,19 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
         }
       }
     }
-    const uchar2 ph = *(const uchar2*)(phase + g);
-    const double* D0 = Dtab + (int)ph.x * n_c * n_c;
-    const double* D1 = Dtab + (int)ph.y * n_c * n_c;
+    const uchar2 ph = *(const uchar2*)(phase + g);  // g even
+    const Real* Dt;
+    if constexpr (sizeof(Real) == 4) Dt = (const Real*)Dtab_f;
+    else Dt = (const Real*)Dtab;
+    const Real* D0 = Dt + (int)ph.x * n_c * n_c;
+    const Real* D1 = Dt + (int)ph.y * n_c * n_c;
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
       Real t0 = 0, t1 = 0;
 #pragma unroll
       for (int q = 0; q < n_c; ++q) {
-        t0 += (Real)__ldg(D0 + c * n_c + q) * e0[q];
-        t1 += (Real)__ldg(D1 + c * n_c + q) * e1[q];
+        t0 += __ldg(D0 + c * n_c + q) * e0[q];
+        t1 += __ldg(D1 + c * n_c + q) * e1[q];
       }
       buf[((size_t)c * rpc + row) * Rh + n] = cmake<C>(t0, t1);
     }
@@ -299,6 +424,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   }
   __syncthreads();
   if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
+    const GreenK<Real> gk = green_consts<Real>(item, a.mat);
     for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
       const int row = idx / (Rh + 1), k = idx - row * (Rh + 1);
       C val[NC];
@@ -307,10 +433,9 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
         const int line = c * rpc + row;
         val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
       }
-      int64_t v[3] = {0, 0, 0};
-#pragma unroll
-      for (int r = 0; r < D; ++r) v[r] = mod_ed(dv, (int64_t)k * dv.ax_cv[dv.nax - 1][r]);
-      green_point<Real, NC>(dv, a.mat, item, v, val);
+      int kk[LAT_MAX_AX] = {0};
+      kk[dv.nax - 1] = k;
+      green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
@@ -323,7 +448,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   for (int idx = tid; idx < nlines * Rh; idx += nthr) {
     const int line = idx >> lgRh, pos = idx & (Rh - 1);
     const int c = line >> lgrpc, row = line & (rpc - 1);
-    T[c * half_m + (r0 + row) * Rh + pos] = buf[idx];
+    T[(uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos] = buf[idx];
   }
   for (int idx = tid; idx < nlines; idx += nthr) {
     const int c = idx >> lgrpc, row = idx & (rpc - 1);
@@ -333,6 +458,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   // residual: block partial -> the item's last block sums in block order and decides its
   // convergence; the last item to arrive in this iteration sets the WHILE condition
   double* partials = a.it.partials + item_i * a.it.pstride;
+  dsum += ((double)dfs.hi + (double)dfs.lo) + 2.0 * ((double)dfs_shear.hi + (double)dfs_shear.lo);
   const double bs = block_sum(dsum, red);
   if (tid == 0) {
     partials[blockIdx.x] = bs;
@@ -406,11 +532,14 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   const C* tw = (const C*)dv.tw;
   const int lg_slots = __ffs(a.row_slots) - 1;
 
+  // in-item offsets: plane * n_f <= 6 * 2^27 < 2^31
+  const uint32_t plane32 = (uint32_t)plane, ic32 = (uint32_t)inner_count;
+  const uint32_t base32 = (uint32_t)(o * G) * ic32 + (uint32_t)i0;
   for (int idx = tid; idx < n_f * G * w; idx += nthr) {
     const int col = idx & (w - 1);
     const int g = (idx >> lgw) & (G - 1);
     const int f = idx >> (lgw + lgG);
-    s[idx] = (col < wv) ? src[f * plane + (o * G + g) * inner_count + i0 + col] : cmake<C>(0.0, 0.0);
+    s[idx] = (col < wv) ? src[(uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col] : cmake<C>(0.0, 0.0);
   }
   __syncthreads();
 
@@ -453,35 +582,31 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     }
   }
   if (NC >= 3 && a.mode == COL_GAMMA) {
+    const ItemDev* item = a.items + item_i;
+    const GreenK<Real> gk = green_consts<Real>(item, a.mat);
     for (int idx = tid; idx < G * w; idx += nthr) {
       const int col = idx & (w - 1), g = idx >> lgw;
-      int64_t v[3] = {0, 0, 0};
+      int kk[LAT_MAX_AX] = {0};
       // group axes (bit-reversed after the DIF)
-      int64_t rem = g;
+      int rem = g;
       for (int x = a.a1 - 1; x >= a.a0; --x) {
-        const int pos = (int)(rem % dv.ax_len[x]);
-        rem /= dv.ax_len[x];
-        const int64_t k = bitrev(pos, dv.ax_log2[x]);
-#pragma unroll
-        for (int r = 0; r < D; ++r) v[r] += k * dv.ax_cv[x][r];
+        const int pos = rem & (dv.ax_len[x] - 1);
+        rem >>= dv.ax_log2[x];
+        kk[x] = (int)bitrev(pos, dv.ax_log2[x]);
       }
       // axes between the group and the row (transformed by the mid passes, bit-reversed)
       const int64_t ii = i0 + col;
-      int64_t mid = nyqt ? ii : ii / a.row_slots;
+      int64_t mid = nyqt ? ii : (ii >> lg_slots);
       for (int x = dv.nax - 2; x >= a.a1; --x) {
-        const int pos = (int)(mid % dv.ax_len[x]);
-        mid /= dv.ax_len[x];
-        const int64_t k = bitrev(pos, dv.ax_log2[x]);
-#pragma unroll
-        for (int r = 0; r < D; ++r) v[r] += k * dv.ax_cv[x][r];
+        const int pos = (int)(mid & (dv.ax_len[x] - 1));
+        mid >>= dv.ax_log2[x];
+        kk[x] = (int)bitrev(pos, dv.ax_log2[x]);
       }
-      const int64_t kr = col_krow(col);
-#pragma unroll
-      for (int r = 0; r < D; ++r) v[r] = mod_ed(dv, v[r] + kr * dv.ax_cv[dv.nax - 1][r]);
+      kk[dv.nax - 1] = (int)col_krow(col);
       C val[NC];
 #pragma unroll
       for (int f = 0; f < n_f; ++f) val[f] = s[(size_t)f * G * w + idx];
-      if constexpr (NC >= 3) green_point<Real, NC>(dv, a.mat, a.items + item_i, v, val);
+      if constexpr (NC >= 3) green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
 #pragma unroll
       for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = val[f];
     }
@@ -507,14 +632,15 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     }
   }
   const Real sc = (Real)a.scale;
+  const bool do_scale = a.scale != 1.0;
   for (int idx = tid; idx < n_f * G * w; idx += nthr) {
     const int col = idx & (w - 1);
     if (col >= wv) continue;
     const int g = (idx >> lgw) & (G - 1);
     const int f = idx >> (lgw + lgG);
     C val = s[idx];
-    if (a.scale != 1.0) val = cscale(val, sc);
-    dst[f * plane + (o * G + g) * inner_count + i0 + col] = val;
+    if (do_scale) val = cscale(val, sc);
+    dst[(uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col] = val;
   }
 }
 

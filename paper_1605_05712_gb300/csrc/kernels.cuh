@@ -19,9 +19,11 @@ struct ItemDev {
   double* sigma;         // NULL or n_c planes
   const uint8_t* phase;  // m phase ids
   const double* Dtab;    // n_phases x n_c x n_c: (C_p - C0) on tensor components
+  const float* Dtab_f;   // the same in binary32 (for the binary32 kernels)
   const double* Ctab;    // n_phases x n_c x n_c: C_p on tensor components
   double E[6];           // macroscopic strain, tensor components
   double c1, c2;         // Green operator constants of this item's C0
+  float c1f, c2f;
   double norm0;          // sqrt(m) ||E||_F (1 if E = 0)
 };
 

@@ -51,6 +51,15 @@ LatDev make_dev(const lat_plan* P, bool fp32) {
   dv.ed_mask = ((P->ed & (P->ed - 1)) == 0) ? P->ed - 1 : -1;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) dv.MT[i][j] = P->M[j][i];
+  {  // |h~_i| = |sum_j M_ji v'_j| <= (e_d / 2) sum_j |M_ji|
+    double hb = 0;
+    for (int i = 0; i < P->d; ++i) {
+      double r = 0;
+      for (int j = 0; j < P->d; ++j) r += fabs((double)P->M[j][i]);
+      hb = std::max(hb, r * (double)P->ed / 2);
+    }
+    dv.h32 = (dv.ed_mask >= 0 && P->ed <= (int64_t(1) << 31) && hb < 2147483647.0) ? 1 : 0;
+  }
   for (int a = 0; a < P->nax; ++a) {
     dv.ax_len[a] = P->ax[a].len;
     dv.ax_log2[a] = P->ax[a].log2len;
@@ -115,6 +124,8 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   off = align256(off + (size_t)n_items * sizeof(ItemDev));
   w.tables = off;
   off = align256(off + (size_t)n_tables * 2 * w.table_bytes);
+  w.tables_f = off;
+  off = align256(off + (size_t)n_tables * w.table_bytes / 2);
   w.partials = off;
   off = align256(off + (size_t)n_items * w.pstride * sizeof(double));
   w.scal = off;
@@ -261,9 +272,12 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
     v.phase = it.phase;
     v.Ctab = (const double*)(ws + wl.tables + (size_t)(2 * it.table + 1) * wl.table_bytes);
     v.Dtab = (const double*)(ws + wl.tables + (size_t)(2 * it.table) * wl.table_bytes);
+    v.Dtab_f = (const float*)(ws + wl.tables_f + (size_t)it.table * wl.table_bytes / 2);
     const double lam0 = it.C0[0], mu0 = it.C0[1];
     v.c1 = 0.5 / mu0;
     v.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+    v.c1f = (float)v.c1;
+    v.c2f = (float)v.c2;
     double nE2 = 0;
     for (int c = 0; c < 6; ++c) v.E[c] = c < n_c ? it.E[c] : 0.0;
     for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * it.E[c] * it.E[c];
@@ -291,6 +305,11 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
     }
   }
   CK(cudaMemcpyAsync(ws + wl.tables, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  // binary32 copies of the (C - C0) tables for the binary32 kernels
+  std::vector<float> tabs_f((size_t)n_tables * tstride, 0.0f);
+  for (int t = 0; t < n_tables; ++t)
+    for (size_t k = 0; k < tstride; ++k) tabs_f[(size_t)t * tstride + k] = (float)tabs[(size_t)(2 * t) * tstride + k];
+  CK(cudaMemcpyAsync(ws + wl.tables_f, tabs_f.data(), tabs_f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ws + wl.items, hdev.data(), hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
   // device scalars start from zero; the batch starts with every item active
   CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_items * kScalBytes + kScalBytes, st));

@@ -26,7 +26,7 @@ struct Geometry {
 
 // byte offsets of the workspace regions of a batched solve
 struct Work {
-  size_t T, TN, items, tables, partials, scal, hist, total;
+  size_t T, TN, items, tables, tables_f, partials, scal, hist, total;
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
 };

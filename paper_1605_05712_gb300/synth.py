@@ -138,3 +138,78 @@ LATTICES = {
     "sheared128": [[128, 16, 0], [0, 128, 16], [0, 0, 128]],
     "rank1_2097152": [[128, 1, 0], [0, 128, 1], [0, 0, 128]],
 }
+
+
+# ------------------------------------------------------------------ coated-ellipsoid (Hashin) workload
+def _depol_carlson(c, rho):
+    """Depolarization factors of the ellipsoid with semi-axes sqrt(c_j^2 + rho) by Carlson's R_D
+    (d_i = l1 l2 l3 / 3 * R_D(l_j^2, l_k^2, l_i^2)); c_3 = inf gives the elliptic-cylinder factors."""
+    from scipy.special import elliprd
+    c = np.asarray(c, dtype=np.float64)
+    if not np.isfinite(c[2]):
+        l1, l2 = np.sqrt(c[0] ** 2 + rho), np.sqrt(c[1] ** 2 + rho)
+        return np.array([l2 / (l1 + l2), l1 / (l1 + l2), 0.0])
+    q = c ** 2 + rho
+    pref = np.sqrt(np.prod(q)) / 3.0
+    return np.array([pref * elliprd(q[(i + 1) % 3], q[(i + 2) % 3], q[i]) for i in range(3)])
+
+
+def iso_tensor3(lam, mu):
+    I = np.eye(3)
+    return (lam * np.einsum('ij,kl->ijkl', I, I)
+            + mu * (np.einsum('ik,jl->ijkl', I, I) + np.einsum('il,jk->ijkl', I, I)))
+
+
+def tensor_to_voigt(C):
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    V = np.zeros((6, 6))
+    for a, (i, j) in enumerate(pairs):
+        for b, (k, l) in enumerate(pairs):
+            V[a, b] = C[i, j, k, l]
+    return V
+
+
+def iso_projection(V):
+    """(lam, mu) of the isotropic projection of a 6x6 Voigt stiffness."""
+    kappa = V[:3, :3].sum() / 9.0
+    mu = (V[0, 0] + V[1, 1] + V[2, 2] - (V[0, 1] + V[0, 2] + V[1, 2]) + 3 * (V[3, 3] + V[4, 4] + V[5, 5])) / 15.0
+    return kappa - 2.0 * mu / 3.0, mu
+
+
+def hashin_workload(seed=BASE_SEED, c=(0.1, 0.15, 0.2), total_fraction=0.25, core=(10.0, 10.0),
+                    coating=(1.0, 1.0), matrix_base=(1.0, 1.0)):
+    """Coated ellipsoid of the generalized Hashin structure (Sec. 4.2) as a benchmark input.
+
+    Core semi-axes c (rho_c = 0), a confocal coating to the given total inclusion volume fraction,
+    rotated by seeded ZYZ Euler angles; isotropic core and coating; the matrix is isotropic
+    matrix_base plus the rank-one correction u (x) u / (u : eps0), u = C^eff eps0 - C_base eps0,
+    the smallest change that makes the inclusion neutral for eps0 (an isotropic matrix has two
+    constants against three conditions for a triaxial ellipsoid).
+    Returns dict(c, rho_c, rho_e, R, stiffness [core, coating, matrix] Voigt, eps0, ceff_eps0, C0).
+    """
+    from scipy.optimize import brentq
+    c = np.asarray(c, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    R = euler_zyz(*rng.uniform(0, 2 * np.pi, 3))
+    vol = lambda r: 4.0 / 3.0 * np.pi * np.prod(np.sqrt(c ** 2 + r)) - total_fraction
+    rho_e = brentq(vol, 0.0, 1.0, xtol=1e-15)
+    rho_c = 0.0
+    lc, mc = core
+    le, me = coating
+    kc, ke = lc + 2 * mc / 3, le + 2 * me / 3
+    g = lambda r: np.prod(c ** 2 + r)
+    f = lambda r: np.sqrt(g(rho_c) / g(r))
+    Dc = np.diag(_depol_carlson(c, rho_c))
+    fe = f(rho_e)
+    Se = (Dc - fe * np.diag(_depol_carlson(c, rho_e))) / (1 - fe)
+    alpha = (3 * ke + 4 * me) / (9 * (kc - ke))
+    eps0 = R @ (alpha * np.eye(3) + (1 - fe) * Se) @ R.T
+    a = ke / (kc - ke) * (kc + 4.0 / 3.0 * me) + 4.0 / 3.0 * me * fe
+    ceff_eps0 = R @ (a * np.eye(3) + 2.0 / 3.0 * me * (1 - fe) * (3 * Se - np.eye(3))) @ R.T
+    Cb = iso_tensor3(*matrix_base)
+    u = ceff_eps0 - np.einsum('ijkl,kl->ij', Cb, eps0)
+    Cm = Cb + np.einsum('ij,kl->ijkl', u, u) / np.einsum('ij,ij', u, eps0)
+    stiff = [iso_voigt(*core), iso_voigt(*coating), tensor_to_voigt(Cm)]
+    lams, mus = zip(*[iso_projection(V) for V in stiff])
+    return dict(c=c, rho_c=rho_c, rho_e=rho_e, R=R, stiffness=stiff, eps0=eps0, ceff_eps0=ceff_eps0,
+                C0=c0_mean_extremes(lams, mus))
