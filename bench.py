@@ -304,6 +304,123 @@ def bench_gpu(args):
         print(json.dumps(res))
 
 
+def bench_hashin(args):
+    """Config-3 workload: the coated-ellipsoid (generalized Hashin) structure at m = 2^21 on the tensor grid,
+    the rank-1 and the sheared 3-D lattices; six unit load cases batched in one solve, tol 1e-6, mixed
+    precision (binary32 FFT/Gamma0/polarization, binary64 residual, averages and strain), timed against
+    the plain binary64 form on the same inputs; C^eff eps0 against the analytic value."""
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan, synth
+    dev = torch.device("cuda", 0)
+    w = synth.hashin_workload()
+    E = np.eye(6)
+    E[3:, 3:] *= 0.5
+    e0 = np.array([w["eps0"][0, 0], w["eps0"][1, 1], w["eps0"][2, 2], 2 * w["eps0"][1, 2], 2 * w["eps0"][0, 2],
+                   2 * w["eps0"][0, 1]])
+    ce_ref = np.array([w["ceff_eps0"][0, 0], w["ceff_eps0"][1, 1], w["ceff_eps0"][2, 2], w["ceff_eps0"][1, 2],
+                       w["ceff_eps0"][0, 2], w["ceff_eps0"][0, 1]])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    out = {}
+    for name in ("grid128", "rank1_2097152", "sheared128"):
+        P = lattice_plan(synth.LATTICES[name])
+        ph = torch.from_numpy(synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"],
+                                                            R=w["R"])).to(dev)
+        eps = torch.empty((6, 6, P.m), dtype=torch.float64, device=dev)
+        res = {}
+        for prec in ("mixed", "fp64"):
+            ws = torch.empty(P.workspace_bytes(6, 1 if prec == "mixed" else 0), dtype=torch.uint8, device=dev)
+            run = lambda: basic_scheme_solve(P, ph, w["stiffness"], w["C0"], E, tol=1e-6, maxit=2000,
+                                             precision=prec, workspace=ws, eps_out=eps)
+            for _ in range(args.warmup if prec == "mixed" else 1):
+                g = run()
+            steps = args.steps if prec == "mixed" else 1
+            last = {}
+
+            def step():
+                g = run()
+                last["g"] = g
+                return P.m * int(np.sum(g["iters"])), None
+            ms, units, _ = timed(step, steps, flush, st)
+            g = last["g"]
+            ce = (g["sigma_bar"].T @ e0)
+            res[prec] = {"ms": round(ms, 3), "value": round(units / (ms / 1e3), 1),
+                         "iterations": [int(x) for x in g["iters"]],
+                         "ceff_eps0_rel_err_vs_analytic": float(np.linalg.norm(ce - ce_ref) / np.linalg.norm(ce_ref)),
+                         "sigma_bar": g["sigma_bar"].tolist()}
+            del ws
+        sb_m, sb_d = np.array(res["mixed"]["sigma_bar"]), np.array(res["fp64"]["sigma_bar"])
+        res["mixed_vs_fp64_ceff_rel"] = float(np.abs(sb_m - sb_d).max() / np.abs(sb_d).max())
+        for prec in ("mixed", "fp64"):
+            res[prec].pop("sigma_bar")
+        out[name] = res
+    print(json.dumps({"workload": "hashin3d (config 3): coated ellipsoid c=(0.1,0.15,0.2), fraction 0.25, "
+                                  "core/coating/matrix 10/1/1+rank-one, m=2^21, 6 load cases batched, tol 1e-6",
+                      "metric": METRIC, "unit": "point-iterations/s", "results": out}))
+
+
+def bench_warmstart(args):
+    """Learned warm start: train the network on the GPU (own kernels) on plain-scheme solutions of random
+    ellipsoidal-inclusion microstructures at 64^3 (contrast 10^U(-1,2)), evaluate on held-out seeds at
+    128^3: iterations and wall time to a 1e-6 residual for the six unit load cases batched, from the cold
+    start, the raw prediction, and both after the two-iteration start filter, in binary64 and in mixed
+    precision; every result judged against the plain binary64 cold start (effective stress)."""
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    from paper_1605_05712_gb300.warmstart import (UNIT_E, WarmStartNet, feature_table, random_microstructure,
+                                                  solve_filtered, solve_warm, train)
+    dev = torch.device("cuda", 0)
+    net = WarmStartNet(dev, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(net, args.ws_train_n, args.ws_samples, 2, 3e-4, seed0=5000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n = args.ws_eval_n
+    P = lattice_plan(np.diag([n, n, n]).tolist())
+    E = UNIT_E
+    names = ["cold", "warm", "cold_filtered", "warm_filtered"]
+    tot = {prec: {k: {"iters": 0, "s": 0.0} for k in names} for prec in ("fp64", "mixed")}
+    per_seed, judge = [], 0.0
+    for s in range(args.ws_eval):
+        ph, stiff, C0 = random_microstructure(900000 + s, n, dev)
+        ref = None
+        row = {"contrast": float(stiff[1][0, 0] / 3)}
+        for prec in ("fp64", "mixed"):
+            fns = {"cold": lambda: basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-6, maxit=5000, precision=prec),
+                   "warm": lambda: solve_warm(P, net, ph, stiff, C0, E, n, tol=1e-6, precision=prec, filtered=False),
+                   "cold_filtered": lambda: solve_filtered(P, ph, stiff, C0, E, tol=1e-6, precision=prec),
+                   "warm_filtered": lambda: solve_warm(P, net, ph, stiff, C0, E, n, tol=1e-6, precision=prec)}
+            for k in names:
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                r = fns[k]()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t1
+                it = int(np.sum(r["iters"]))
+                tot[prec][k]["iters"] += it
+                tot[prec][k]["s"] += dt
+                row["%s_%s" % (prec, k)] = it
+                if ref is None:
+                    ref = r["sigma_bar"]
+                judge = max(judge, float(np.abs(r["sigma_bar"] - ref).max() / np.abs(ref).max()))
+        tab = torch.from_numpy(feature_table(stiff, C0[1]).reshape(-1)).to(dev)
+        eps0 = net.predict(ph, tab, n, E)
+        cold = basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-6, maxit=5000)
+        Eb = torch.from_numpy(E).to(dev)[:, :, None]
+        row["pred_err2"] = round(float(((eps0 - cold["eps"]) ** 2).sum() / ((cold["eps"] - Eb) ** 2).sum()), 4)
+        per_seed.append(row)
+    for prec in tot:
+        for k in names:
+            tot[prec][k]["s"] = round(tot[prec][k]["s"], 3)
+    print(json.dumps({"workload": "warmstart (config 5): train %d samples x 2 Adam steps at %d^3, evaluate %d "
+                                  "held-out seeds at %d^3, 6 unit load cases batched, tol 1e-6"
+                                  % (args.ws_samples, args.ws_train_n, args.ws_eval, n),
+                      "train_s": round(t_train, 1), "train_loss_first_last": [float(np.mean(losses[:100])),
+                                                                               float(np.mean(losses[-100:]))],
+                      "totals": tot, "judge_max_sigma_bar_rel_diff_vs_fp64_cold": judge, "per_seed": per_seed}))
+
+
 def profile_case(args):
     """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
     import torch
@@ -386,9 +503,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
+    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart"])
+    ap.add_argument("--ws-samples", type=int, default=2000)
+    ap.add_argument("--ws-train-n", type=int, default=64)
+    ap.add_argument("--ws-eval-n", type=int, default=128)
+    ap.add_argument("--ws-eval", type=int, default=4)
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)
+    elif args.workload == "hashin3d":
+        bench_hashin(args)
+    elif args.workload == "warmstart":
+        bench_warmstart(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

@@ -239,6 +239,70 @@ int basic_scheme_solve_noalloc(const lat_plan* plan, const uint8_t* phase, int n
                                int* iters, double* resid, void* stream);
 
 /*
+ * Learned warm start (not in the paper; an addition measured against the
+ * plain scheme): a periodic 3-D U-Net, 4 levels x 32 channels, BF16 weights
+ * and activations with FP32 accumulation, mapping the stiffness field of a
+ * cubic n^3 tensor grid (M = diag(n, n, n), plan order = grid order) to the
+ * strain-localization field A, eps^(0) = A : E with <A> = I, so that
+ * basic_scheme_solve can start warm and run to the same tolerance.
+ * Device buffers are the caller's:
+ *   params  lat_wsnet_param_bytes(): fp32 parameters, gradients, Adam moments,
+ *           bf16 copies of the convolution weights;
+ *   work    lat_wsnet_work_bytes(n): activations and gradients of one n^3 sample
+ *           (n in 16..256, divisible by 8).
+ * Parameter vector (lat_wsnet_num_params floats): for each of the 7 convolutions
+ * (c0 c1 c2 c3 d2 d1 d0) W[27][32][32] (taps (dz,dy,dx) lexicographic, ci, co)
+ * then b[32]; then the 1x1 head H[32][36] and hb[36].
+ * Feature table: per phase 21 floats, the upper triangle of its Voigt matrix / mu0.
+ */
+size_t lat_wsnet_param_bytes(void);
+int64_t lat_wsnet_num_params(void);
+size_t lat_wsnet_work_bytes(int n);
+int lat_wsnet_set_params(void* params, const float* host_params, void* stream);      /* also resets Adam */
+int lat_wsnet_get_params(const void* params, float* host_params, float* host_grads, void* stream);
+int lat_wsnet_features(const uint8_t* phase, const float* table, int n, void* work, size_t work_bytes,
+                       void* stream);
+/* forward of the features in `work`; y_out (device, n^3 x 36 fp32, channel 6 i + j = A'_ij) or NULL */
+int lat_wsnet_forward(const void* params, int n, float* y_out, void* work, size_t work_bytes, void* stream);
+/* backward after lat_wsnet_forward on the same work: parameter gradients from dL/dy (device n^3 x 36) */
+int lat_wsnet_backward(void* params, int n, const float* dy, void* work, size_t work_bytes, void* stream);
+/* one Adam step on the centred relative squared error sum (y~ - t~)^2 / (sum t~^2 + N 1e-6), x~ = x minus
+ * its spatial mean per channel (the prediction's mean is discarded when it is used), against the
+ * localization t of the six unit load cases (loss_out: host, that ratio, before the step):
+ * eps_unit device, 6 x 6 x n^3 binary64 (load case, component, point), as basic_scheme_solve writes */
+int lat_wsnet_train_step(void* params, const uint8_t* phase, const float* table, const double* eps_unit,
+                         int n, float lr, int step, double* loss_out, void* work, size_t work_bytes,
+                         void* stream);
+/* copy a forward activation of `work` to host fp32 (n_l^3 x 32, n_l = n >> level): which = 0 features,
+ * 1..4 encoder outputs s0..s3, 5..7 pooled inputs p1..p3, 8/9 level-0 decoder input/output, 10/11
+ * level 1, 12/13 level 2 (for inspecting and checking the network) */
+int lat_wsnet_get_activation(const void* work, size_t work_bytes, int n, int which, float* host_out,
+                             void* stream);
+/* eps0 (device, n_loads x 6 x n^3 binary64) = E + (A' - <A'>) : E for n_loads macroscopic strains */
+int lat_wsnet_predict(const void* params, const uint8_t* phase, const float* table, int n,
+                      const double* E, int n_loads, double* eps0, void* work, size_t work_bytes,
+                      void* stream);
+
+/*
+ * lattice_start_filter -- two-iteration filter of an initial strain (an
+ * addition to the paper, used with the warm start): out = (G^2(eps0) -
+ * rho^2 eps0) / (1 - rho^2), where G^2(eps0) is the iterate after two plain
+ * iterations from eps0 (basic_scheme_solve with maxit = 2, tol = 0).  Since
+ * G is affine with fixed point eps*, the error of out is p(T) (eps0 - eps*)
+ * with T the linear part of G and p(t) = (t^2 - rho^2) / (1 - rho^2): the
+ * solution is kept (p(1) = 1) and the error components of eigenvalue +-rho,
+ * the slowest ones, are removed.  For phases whose stiffness is a multiple
+ * c_p C0 of the reference, rho = max_p |c_p - 1| and those components are
+ * the compatible strains confined to one phase; the exact solution has none
+ * (equilibrium in each phase), a predicted start in general has.
+ *   out, eps_g2, eps0  device, count binary64 each; out may alias either input.
+ *   rho               in [0, 1).
+ * Returns LAT_ERR_ARG for NULL pointers or rho outside [0, 1); asynchronous.
+ */
+int lattice_start_filter(double* out, const double* eps_g2, const double* eps0, double rho, size_t count,
+                         void* stream);
+
+/*
  * lattice_pass_times -- profiling helper: average device time of each kernel
  * of one Basic Scheme iteration (no counterpart in the paper; it measures
  * the passes the solve above runs inside its CUDA graph).  Runs the

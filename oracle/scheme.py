@@ -38,6 +38,15 @@ from .lattice import Lattice
 from .transform import dft_fast, dft_naive
 
 
+def _phase_ddot(C, phase, eps):
+    """(C_{phase(y)} : eps_y)_y, one phase at a time (no (m, d, d, d, d) temporary)."""
+    out = np.zeros_like(eps)
+    for p in np.unique(phase):
+        sel = phase == p
+        out[sel] = el.ddot(C[p], eps[sel])
+    return out
+
+
 def _transform(lat, a, inverse, mode):
     if mode == 'naive' or (mode == 'auto' and lat.m <= 1024):
         return dft_naive(lat, a, inverse)
@@ -87,7 +96,7 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
     history = []
     it = 0
     while it < maxit:
-        tau = el.ddot(dC[phase], eps)                                  # polarization
+        tau = _phase_ddot(dC, phase, eps)                              # polarization
         tau_hat = _transform(lat, tau, False, transform)               # F(M) tau
         eps_hat = np.zeros_like(tau_hat)
         eps_hat[nz] = -el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
@@ -101,8 +110,19 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
         history.append(float(r))
         if r < tol:
             break
-    sigma = el.ddot(stiff[phase], eps)
+    sigma = _phase_ddot(stiff, phase, eps)
     return dict(eps=eps, sigma=sigma, sigma_bar=sigma.mean(axis=0), iters=it, history=history)
+
+
+def filtered_start(M, phase, stiff, C0, E, eps0, rho, **kw):
+    """(G^2(eps0) - rho^2 eps0) / (1 - rho^2), G one step of Algorithm 1 (not in the paper).
+
+    G is affine with fixed point eps*, so the error of the result is p(T)(eps0 - eps*) with T the
+    linear part of G and p(t) = (t^2 - rho^2) / (1 - rho^2): p(1) = 1 keeps eps*, p(+-rho) = 0
+    removes the error components of eigenvalue +-rho.
+    """
+    g2 = basic_scheme(M, phase, stiff, C0, E, tol=0.0, maxit=2, eps0=eps0, **kw)['eps']
+    return (g2 - rho * rho * np.asarray(eps0, dtype=np.float64)) / (1.0 - rho * rho)
 
 
 def unit_load(d, a):

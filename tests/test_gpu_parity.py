@@ -317,3 +317,62 @@ def test_batch_of_microstructures_matches_oracle(cuda, M, prec):
             assert abs(int(g["iters"][i]) - o["iters"]) <= 1
             assert relerr(eg, o["eps"][perm]) < MIXED_STRAIN_RTOL
             assert relerr(sb, o["sigma_bar"]) < MIXED_CEFF_RTOL
+
+
+# ---------------------------------------------------------------- generalized Hashin structure (3-D)
+def _hashin_case(M, cuda, precision, tol, maxit):
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    w = synth.hashin_workload()
+    P = lattice_plan(M)
+    ph = synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+    E = np.eye(6)
+    E[3:, 3:] *= 0.5                                   # unit load cases in tensor components
+    g = basic_scheme_solve(P, torch.from_numpy(ph).to(cuda), w["stiffness"], w["C0"], E, tol=tol, maxit=maxit,
+                           precision=precision)
+    return w, P, ph, E, g
+
+
+@pytest.mark.parametrize("M", [[[32, 0, 0], [0, 32, 0], [0, 0, 32]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]],
+                               [[32, 4, 0], [0, 32, 4], [0, 0, 32]]])
+def test_hashin_mixed_six_load_cases_against_oracle(cuda, M):
+    # config-3 shape at m = 32768: mixed precision, the six unit load cases in one batch, tol 1e-6
+    w, P, ph, E, g = _hashin_case(M, cuda, "mixed", 1e-6, 2000)
+    assert g["status"] == 0
+    L = Lattice(M)
+    perm = to_oracle_order(P.points(), L)
+    ph_o = synth.coated_ellipsoid_phase(L.p, L.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+    S = np.array([el.voigt6_to_tensor(V, 3) for V in w["stiffness"]])
+    Ceff = np.zeros((6, 6))
+    for lc in range(6):
+        o = basic_scheme(L, ph_o, S, w["C0"], el.comps_to_sym(E[lc], 3), tol=1e-6, maxit=2000)
+        assert abs(int(g["iters"][lc]) - o["iters"]) <= 1
+        eg = comps_to_tensor(g["eps"][lc].cpu().numpy(), 3)
+        assert relerr(eg, o["eps"][perm]) < MIXED_STRAIN_RTOL
+        assert relerr(el.comps_to_sym(g["sigma_bar"][lc], 3), o["sigma_bar"]) < MIXED_CEFF_RTOL
+        Ceff[:, lc] = g["sigma_bar"][lc]
+    # C^eff eps0 from the six columns against the analytic value (discretisation error at 32^3)
+    e0 = el.sym_to_comps(w["eps0"])
+    e0_eng = e0 * np.array([1, 1, 1, 2, 2, 2])
+    ce = el.comps_to_sym(Ceff @ e0_eng, 3)
+    assert np.linalg.norm(ce - w["ceff_eps0"]) / np.linalg.norm(w["ceff_eps0"]) < 0.05
+
+
+@pytest.mark.parametrize("name", ["grid128", "rank1_2097152", "sheared128"])
+def test_hashin_full_size_fp64_fixed_iterations(cuda, name):
+    # full config-3 size (m = 2^21), the eps0 load case, binary64, two iterations compared field-wise
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    w = synth.hashin_workload()
+    M = synth.LATTICES[name]
+    P = lattice_plan(M)
+    L = Lattice(M)
+    perm = to_oracle_order(P.points(), L)
+    ph = synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+    ph_o = synth.coated_ellipsoid_phase(L.p, L.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+    E = el.sym_to_comps(w["eps0"])[None]
+    g = basic_scheme_solve(P, torch.from_numpy(ph).to(cuda), w["stiffness"], w["C0"], E, tol=0.0, maxit=2)
+    S = np.array([el.voigt6_to_tensor(V, 3) for V in w["stiffness"]])
+    o = basic_scheme(L, ph_o, S, w["C0"], w["eps0"], tol=0.0, maxit=2)
+    assert relerr(comps_to_tensor(g["eps"][0].cpu().numpy(), 3), o["eps"][perm]) < RTOL
+    assert relerr(el.comps_to_sym(g["sigma_bar"][0], 3), o["sigma_bar"]) < RTOL

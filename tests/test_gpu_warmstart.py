@@ -1,0 +1,242 @@
+"""GPU tests of the learned warm start: forward and gradients of the network kernels against the CPU
+oracle (oracle/warmstart.py), and the gain of the trained network over the cold start.
+
+The GPU stores activations in BF16 (after each ReLU, pool and skip addition) and feeds BF16 operands
+to the convolutions with FP32 accumulation; the reference below rounds at the same points and
+accumulates in float64, so the remaining differences are accumulation order and rare rounding ties.
+"""
+import numpy as np
+import pytest
+
+from oracle import warmstart as ows
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(x):
+    """Round float64/float32 values to bfloat16 (nearest even), returned as float64."""
+    a = np.asarray(x, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unpack(p):
+    """Flat parameter vector -> oracle dict (W[27][ci][co], b, head)."""
+    d = {}
+    off = 0
+    for name in ows.CONV_NAMES:
+        d[name + ".W"] = p[off:off + 27 * 1024].reshape(27, 32, 32).astype(np.float64)
+        off += 27 * 1024
+        d[name + ".b"] = p[off:off + 32].astype(np.float64)
+        off += 32
+    d["head.W"] = p[off:off + 32 * 36].reshape(32, 36).astype(np.float64)
+    off += 32 * 36
+    d["head.b"] = p[off:off + 36].astype(np.float64)
+    return d
+
+
+def to_cf(a, n, C):
+    """GPU channels-last (V, C) -> oracle (C, n, n, n)."""
+    return np.asarray(a).reshape(n, n, n, C).transpose(3, 0, 1, 2)
+
+
+def ref_forward(p, x0):
+    """Network forward with BF16 rounding where the GPU rounds."""
+    W = {k: (bf16(v) if k.endswith(".W") and not k.startswith("head") else v) for k, v in p.items()}
+    c = {"x0": x0}
+    conv = lambda x, name: bf16(ows.relu(ows.conv3(x, W[name + ".W"], W[name + ".b"])))
+    c["s0"] = conv(x0, "c0")
+    c["p1"] = bf16(ows.pool(c["s0"]))
+    c["s1"] = conv(c["p1"], "c1")
+    c["p2"] = bf16(ows.pool(c["s1"]))
+    c["s2"] = conv(c["p2"], "c2")
+    c["p3"] = bf16(ows.pool(c["s2"]))
+    c["s3"] = conv(c["p3"], "c3")
+    c["i2"] = bf16(ows.up(c["s3"]) + c["s2"])
+    c["u2"] = conv(c["i2"], "d2")
+    c["i1"] = bf16(ows.up(c["u2"]) + c["s1"])
+    c["u1"] = conv(c["i1"], "d1")
+    c["i0"] = bf16(ows.up(c["u1"]) + c["s0"])
+    c["u0"] = conv(c["i0"], "d0")
+    y = ows.head(c["u0"], p["head.W"], p["head.b"])
+    return y, c, W
+
+
+def ref_backward(W, p, c, dy):
+    g = {}
+    du0, g["head.W"], g["head.b"] = ows.head_backward(c["u0"], p["head.W"], dy)
+
+    def convb(x, name, gout, y):
+        dpre = bf16(gout * ows.relu_grad(y))
+        dx, g[name + ".W"], g[name + ".b"] = ows.conv3_backward(x, W[name + ".W"], dpre)
+        return dx
+    di0 = convb(c["i0"], "d0", du0, c["u0"])
+    di1 = convb(c["i1"], "d1", ows.up_backward(di0), c["u1"])
+    di2 = convb(c["i2"], "d2", ows.up_backward(di1), c["u2"])
+    dp3 = convb(c["p3"], "c3", ows.up_backward(di2), c["s3"])
+    dp2 = convb(c["p2"], "c2", di2 + ows.pool_backward(dp3), c["s2"])
+    dp1 = convb(c["p1"], "c1", di1 + ows.pool_backward(dp2), c["s1"])
+    convb(c["x0"], "c0", di0 + ows.pool_backward(dp1), c["s0"])
+    return g
+
+
+def setup_net(cuda, n, seed):
+    import torch
+    from paper_1605_05712_gb300.warmstart import WarmStartNet
+    rng = np.random.default_rng(seed)
+    net = WarmStartNet(cuda, seed=seed)
+    p = net.init_params(seed)
+    p[:] = p + 0.0
+    off = 0
+    for _ in range(7):
+        off += 27 * 1024
+        p[off:off + 32] = rng.uniform(-0.1, 0.1, 32)   # nonzero biases exercise the bias paths
+        off += 32
+    p[off:off + 32 * 36] = rng.standard_normal(32 * 36) * np.sqrt(1.0 / 32)   # the trained head is not zero
+    net.set_params(p)
+    phase = rng.integers(0, 3, size=n ** 3).astype(np.uint8)
+    table = rng.uniform(0.0, 2.0, size=(3, 21)).astype(np.float32)
+    net.features(torch.from_numpy(phase).to(cuda), table, n)
+    feat = np.zeros((n ** 3, 32))
+    feat[:, :21] = table[phase]
+    x0 = bf16(to_cf(feat, n, 32))
+    return net, p, x0, phase, table
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_network_forward_matches_oracle(cuda, n):
+    net, p, x0, _, _ = setup_net(cuda, n, 7)
+    y = net.forward(n).cpu().numpy()
+    yr, _, _ = ref_forward(unpack(p), x0)
+    yr = yr.transpose(1, 2, 3, 0).reshape(-1, 36)
+    assert rel(y, yr) < 5e-3
+    assert np.abs(y - yr).max() < 3e-2 * np.abs(yr).max()
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_network_gradients_match_oracle(cuda, n):
+    # the reference backward runs on the GPU's own forward activations (read back through the C ABI):
+    # BF16 rounding ties and activation-slope flips make independent forwards differ by ~1e-3, which the
+    # gradients amplify.  With the same activations the backpropagated gradient is still rounded to BF16
+    # before each convolution on both sides, from float32 on the GPU and float64 here, so rounding ties
+    # differ (2^-9 relative each) and compound over the seven layers: a few 1e-3 in the deepest layers
+    import torch
+    net, p, x0, _, _ = setup_net(cuda, n, 11)
+    net.forward(n)
+    rng = np.random.default_rng(3)
+    dy = rng.standard_normal((n ** 3, 36)).astype(np.float32) / n ** 3
+    net.backward(n, torch.from_numpy(dy).to(cuda))
+    _, gflat = net.get_params(grads=True)
+    g = unpack(gflat)
+    pd = unpack(p)
+    _, _, W = ref_forward(pd, x0)
+    cache = {}
+    for name in net.ACT:
+        a = net.activation(n, name).astype(np.float64)
+        nl = round(a.shape[0] ** (1.0 / 3.0))
+        cache[name] = to_cf(a, nl, 32)
+    assert rel(cache["x0"], x0) == 0.0
+    gr = ref_backward(W, pd, cache, to_cf(dy.astype(np.float64), n, 36))
+    errs = {name: rel(g[name], gr[name]) for name in gr}
+    worst = sorted(errs.items(), key=lambda kv: -kv[1])[:4]
+    assert worst[0][1] < 5e-3, worst
+
+
+def test_training_step_loss_and_adam_update(cuda):
+    # one training step: the loss it reports is the oracle's centred relative loss of the forward output
+    # against the targets of the given unit-load strains, and the first Adam step moves every parameter
+    # by lr g / (|g| + 1e-8) (bias-corrected moments of a single gradient)
+    import torch
+    n = 16
+    net, p, x0, phase, table = setup_net(cuda, n, 13)
+    y = net.forward(n).cpu().numpy().astype(np.float64)          # (V, 36) channels-last
+    rng = np.random.default_rng(21)
+    E_unit = np.diag([1.0, 1.0, 1.0, 0.5, 0.5, 0.5])
+    eps_unit = E_unit[:, :, None] + 0.3 * rng.standard_normal((6, 6, n ** 3))
+    # the step recomputes the same features from phase and table
+    phase_dev = torch.from_numpy(phase).to(cuda)
+    tab = torch.from_numpy(table.reshape(-1)).to(cuda)
+    lr = 1e-3
+    loss = net.train_step(phase_dev, tab, torch.from_numpy(eps_unit).to(cuda), n, lr)
+    t = ows.localization_targets(eps_unit, E_unit)                 # (36, V)
+    L_ref, _ = ows.centered_rel_loss(y.T, t)
+    assert abs(loss - L_ref) < 1e-5 * L_ref
+    p1, g = net.get_params(grads=True)
+    step = p.astype(np.float64) - p1
+    expect = lr * g.astype(np.float64) / (np.abs(g) + 1e-8)
+    assert np.abs(step - expect).max() < 1e-6
+
+
+def test_start_filter_matches_oracle(cuda):
+    # two plain iterations plus the filter kernel against oracle.scheme.filtered_start, binary64
+    import torch
+    from oracle import elasticity as el
+    from oracle.lattice import Lattice
+    from oracle.scheme import filtered_start
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan, synth
+    from paper_1605_05712_gb300.warmstart import filter_rho, start_filter
+    M = [[32, 4], [0, 16]]
+    P, L = lattice_plan(M), Lattice(M)
+    idx = {tuple(r): i for i, r in enumerate(L.p.tolist())}
+    perm = np.array([idx[tuple(r)] for r in P.points().tolist()])
+    incl = synth.random_inclusions(4, 2, 3, 0.3)
+    k = 9.0
+    V = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(k, k)]
+    C0 = (0.5 * (1 + k), 0.5 * (1 + k))
+    rho = filter_rho(V, C0)
+    assert abs(rho - 0.8) < 1e-12
+    E = np.array([[1.0, 0.5, -0.25]])
+    rng = np.random.default_rng(8)
+    s = E[0][:, None] + 0.2 * rng.standard_normal((3, P.m))
+    ph = torch.from_numpy(synth.inclusions_phase(P.points(), P.m, incl)).to(cuda)
+    s_dev = torch.from_numpy(s[None].copy()).to(cuda)
+    g2 = basic_scheme_solve(P, ph, V, C0, E, tol=0.0, maxit=2, eps0=s_dev)["eps"]
+    out = start_filter(torch.empty_like(g2), g2, s_dev, rho).cpu().numpy()[0]
+    s_or = np.empty((P.m, 2, 2))
+    s_or[perm] = el.comps_to_sym(s.T, 2)
+    ref = filtered_start(L, synth.inclusions_phase(L.p, L.m, incl), np.array([el.voigt6_to_tensor(v, 2) for v in V]),
+                         C0, el.comps_to_sym(E[0], 2), s_or, rho)[perm]
+    got = el.comps_to_sym(out.T, 2)
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_trained_warm_start_against_cold_start(cuda):
+    # train on the GPU (own kernels), then measure on held-out microstructures: prediction error against
+    # the converged field (the cold start's is 1), and iterations to tol 1e-6 from the cold start, the raw
+    # prediction, and both after the start filter; the plain cold start judges every result
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    from paper_1605_05712_gb300.warmstart import (UNIT_E, WarmStartNet, feature_table, random_microstructure,
+                                                  solve_filtered, solve_warm, train)
+    n = 32
+    net = WarmStartNet(cuda, seed=1)
+    losses = train(net, n, n_samples=1000, steps_per_sample=2, lr=3e-4, seed0=5000)
+    assert np.mean(losses[-200:]) < 0.5 * np.mean(losses[:20])
+    P = lattice_plan(np.diag([n, n, n]).tolist())
+    E = UNIT_E
+    its = {"cold": 0, "warm": 0, "cold_filtered": 0, "warm_filtered": 0}
+    errs = []
+    for s in range(4):                                   # held-out seeds
+        ph, stiff, C0 = random_microstructure(900000 + s, n, cuda)
+        tab = torch.from_numpy(feature_table(stiff, C0[1]).reshape(-1)).to(cuda)
+        cold = basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-6, maxit=5000)
+        eps0 = net.predict(ph, tab, n, E)
+        Eb = torch.from_numpy(E).to(cuda)[:, :, None]
+        errs.append(float(((eps0 - cold["eps"]) ** 2).sum() / ((cold["eps"] - Eb) ** 2).sum()))
+        runs = {"cold": cold,
+                "warm": solve_warm(P, net, ph, stiff, C0, E, n, tol=1e-6, filtered=False),
+                "cold_filtered": solve_filtered(P, ph, stiff, C0, E, tol=1e-6),
+                "warm_filtered": solve_warm(P, net, ph, stiff, C0, E, n, tol=1e-6)}
+        for name, r in runs.items():
+            assert r["status"] == 0
+            its[name] += int(np.sum(r["iters"]))
+            # the plain scheme judges: every start converges to the cold start's effective stress
+            assert np.abs(r["sigma_bar"] - cold["sigma_bar"]).max() < 1e-5 * np.abs(cold["sigma_bar"]).max()
+    print("held-out prediction error^2 (cold start = 1):", np.round(errs, 3), "iterations:", its)
+    assert max(errs) < 0.5
+    assert its["warm_filtered"] < its["cold"]
