@@ -129,6 +129,9 @@ def setup(dev):
     return out
 
 
+PLAIN_LAUNCHES = False   # --plain-launches: iterate with plain launches instead of the CUDA-graph loop
+
+
 def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
     """One pass of the workload.  fp64_separate: each load case its own solve (the configured
     form); fp64_batched / mixed_batched: the three load cases of a lattice in one batched solve."""
@@ -140,11 +143,12 @@ def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
             its = []
             for lc in range(E.shape[0]):
                 g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E[lc:lc + 1], tol=tol, maxit=MAXIT,
-                                       workspace=ws, eps_out=eps[lc:lc + 1])
+                                       workspace=ws, eps_out=eps[lc:lc + 1], plain_launches=PLAIN_LAUNCHES)
                 its.append(int(g["iters"][0]))
         else:
             g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
-                                   eps_out=eps, precision="mixed" if mode.startswith("mixed") else "fp64")
+                                   eps_out=eps, precision="mixed" if mode.startswith("mixed") else "fp64",
+                                   plain_launches=PLAIN_LAUNCHES)
             its = [int(x) for x in g["iters"]]
         iters.append(its)
         tot += w["plan"].m * int(np.sum(its))
@@ -287,7 +291,9 @@ def bench_gpu(args):
         "config": {"workload": "2-D laminate n=(1,3), m=262144 on diag(512,512), rank-1 [[512,1],[0,512]] and "
                                "rank-2 [[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64",
                    "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
-                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "launch": "plain launches, host convergence check per iteration" if PLAIN_LAUNCHES
+                             else "one CUDA-graph WHILE loop per solve"},
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 1), "unit": "point-iterations/s",
                 "h2d_bytes_per_step": int(sum(w_["plan"].m for w_ in work)),
@@ -503,12 +509,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
     ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart"])
     ap.add_argument("--ws-samples", type=int, default=2000)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)
     ap.add_argument("--ws-eval", type=int, default=4)
     args = ap.parse_args()
+    global PLAIN_LAUNCHES
+    PLAIN_LAUNCHES = args.plain_launches
     if args.profile_case:
         profile_case(args)
     elif args.workload == "hashin3d":

@@ -130,6 +130,10 @@ typedef struct lat_solve_opts {
   int mixed_increment;  /* LAT_MIXED only: 1 = binary32 kernels carry the increment
                            eps^(n+1) - eps^(n) (accumulated into the binary64 strain), 0 = they
                            carry the strain itself */
+  int plain_launches;   /* 0: the iteration is a CUDA-graph WHILE loop (one replay per solve);
+                           nonzero: plain kernel launches with a host read of the convergence
+                           state after every iteration, same results (for profilers that do not
+                           trace kernels inside graphs with conditional nodes) */
 } lat_solve_opts;
 
 /*

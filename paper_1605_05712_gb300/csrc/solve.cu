@@ -507,7 +507,7 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   std::vector<ItemHost> items;
   load_case_items(P, phase, C0, E, n_loads, eps, sigma, items);
   const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
-  return run_batch(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, true, sigma_bar,
+  return run_batch(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar,
                    iters, resid, (cudaStream_t)stream);
 }
 
@@ -546,7 +546,7 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
-  return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, true, sigma_bar, iters, resid,
+  return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar, iters, resid,
                    (cudaStream_t)stream);
 }
 

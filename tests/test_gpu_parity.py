@@ -376,3 +376,20 @@ def test_hashin_full_size_fp64_fixed_iterations(cuda, name):
     o = basic_scheme(L, ph_o, S, w["C0"], w["eps0"], tol=0.0, maxit=2)
     assert relerr(comps_to_tensor(g["eps"][0].cpu().numpy(), 3), o["eps"][perm]) < RTOL
     assert relerr(el.comps_to_sym(g["sigma_bar"][0], 3), o["sigma_bar"]) < RTOL
+
+
+def test_plain_launches_equal_graph_loop(cuda):
+    # the plain-launch iteration (host convergence check) runs the same kernels in the same order
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    for M, prec in (([[512, 16], [0, 512]], "fp64"), ([[32, 4, 0], [0, 32, 4], [0, 0, 32]], "mixed")):
+        P = lattice_plan(M)
+        d = len(M)
+        ph = torch.from_numpy(inclusions(3, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+        E = np.eye(3 if d == 2 else 6)[:2]
+        a = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec)
+        b = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec, plain_launches=True)
+        assert a["status"] == b["status"] == 0
+        assert np.array_equal(a["iters"], b["iters"])
+        assert torch.equal(a["eps"], b["eps"])
+        assert np.array_equal(a["sigma_bar"], b["sigma_bar"])
