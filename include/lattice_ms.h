@@ -139,6 +139,9 @@ typedef struct lat_solve_opts {
 /*
  * lattice_workspace_bytes -- device workspace a solve with n_loads load
  * cases needs (spectrum buffers, reduction partials, device scalars).
+ * Returns 0 for invalid arguments or when a row or column tile of the plan
+ * does not fit in shared memory at this precision (the solve would return
+ * LAT_ERR_UNSUPPORTED); the same holds for the batch and multi variants.
  */
 size_t lattice_workspace_bytes(const lat_plan* plan, int n_loads, int precision);
 
@@ -209,6 +212,47 @@ int basic_scheme_solve_batch(const lat_plan* plan, const lat_batch_item* items, 
                              double tol, int maxit, const lat_solve_opts* opts,
                              double* sigma_bar, int* iters, double* resid,
                              void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * basic_scheme_solve_multi -- Algorithm 1 (Sec. 3.2) for independent problems
+ * on different lattices (any mix of d, M and load-case counts) in one call.
+ * Items that share a plan run as one batch (as basic_scheme_solve_batch, all
+ * their load cases in the same kernel launches); the batches of different
+ * plans run concurrently as the parallel branches of one CUDA graph, each with
+ * its own WHILE loop, so small lattices do not wait for large ones.
+ *   items      host array of n_items; per item:
+ *     plan       the item's lattice (lattice_plan); items with the same pointer batch together
+ *     phase      device, m phase ids in plan order (< n_phases)
+ *     n_phases   1..LAT_BATCH_MAX_PHASES; stiffness host, n_phases * 36 Voigt
+ *     C0         isotropic reference medium (lambda0, mu0), lambda0 + 2 mu0 > 0, mu0 > 0
+ *     E, n_loads host, n_loads x n_c macroscopic strains (tensor components), n_loads >= 1
+ *     eps        device, n_loads x n_c x m binary64, 16-byte aligned (output; input with warm_start)
+ *     sigma      device or NULL, n_loads x n_c x m
+ *     sigma_bar, iters, resid  host or NULL, n_loads (x n_c) outputs per item
+ *   opts       as basic_scheme_solve; resid_history must be NULL (LAT_ERR_ARG otherwise)
+ *   workspace  device, >= lattice_multi_workspace_bytes(items, n_items, precision), carved per plan
+ *              in order of first appearance
+ * Runs on `stream` and returns after synchronizing it.  Returns the worst outcome over all load
+ * cases of all items; argument errors are reported before anything runs.
+ */
+typedef struct lat_multi_item {
+  const lat_plan* plan;
+  const uint8_t* phase;
+  int n_phases;
+  const double* stiffness;
+  double C0[2];
+  const double* E;
+  int n_loads;
+  double* eps;
+  double* sigma;
+  double* sigma_bar;
+  int* iters;
+  double* resid;
+} lat_multi_item;
+size_t lattice_multi_workspace_bytes(const lat_multi_item* items, int n_items, int precision);
+int basic_scheme_solve_multi(const lat_multi_item* items, int n_items, double tol, int maxit,
+                             const lat_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                             void* stream);
 
 /*
  * basic_scheme_solve_noalloc -- basic_scheme_solve for callers that cannot

@@ -16,6 +16,7 @@ import numpy as np
 from ._build import LIB
 
 LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
+LAT_ERR_ARG = -1
 LAT_FP64, LAT_MIXED = 0, 1
 LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
 HIST_CAP = 4096
@@ -339,3 +340,96 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     if history:
         out["history"] = [hist[i, :min(int(iters[i]), maxit, HIST_CAP)] for i in range(n)]
     return out
+
+
+class _MultiItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("phase", ctypes.c_void_p), ("n_phases", ctypes.c_int),
+                ("stiffness", ctypes.POINTER(ctypes.c_double)), ("C0", ctypes.c_double * 2),
+                ("E", ctypes.POINTER(ctypes.c_double)), ("n_loads", ctypes.c_int), ("eps", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("sigma_bar", ctypes.POINTER(ctypes.c_double)),
+                ("iters", ctypes.POINTER(ctypes.c_int)), ("resid", ctypes.POINTER(ctypes.c_double))]
+
+
+def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", boundary="average",
+                             want_sigma=False, workspace=None, stream=None, mixed_increment=True,
+                             plain_launches=False, warm_start=False):
+    """Algorithm 1 for independent problems on different lattices in one call (one CUDA graph).
+
+    problems  list of dicts: plan (LatticePlan), phase (uint8 CUDA tensor (m,)), stiffness
+              ((n_phases <= 16, 6, 6) Voigt), C0 (lam0, mu0), E ((n_loads, n_c) tensor components), and
+              optionally eps (CUDA float64 (n_loads, n_c, m): output buffer; with warm_start=True it holds
+              eps^(0) on entry)
+    Returns (status, list of dicts eps, sigma, sigma_bar, iters, resid per problem).
+    """
+    import torch
+    n = len(problems)
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    items = (_MultiItem * n)()
+    keep, outs = [], []
+    for i, pb in enumerate(problems):
+        plan, phase = pb["plan"], pb["phase"]
+        if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+            raise TypeError("problem %d: phase must be a uint8 CUDA tensor with m entries" % i)
+        E = np.asarray(pb["E"], dtype=np.float64).reshape(-1, plan.n_c)
+        nl = E.shape[0]
+        eps = pb.get("eps")
+        if eps is None:
+            if warm_start:
+                raise ValueError("problem %d: warm_start needs eps" % i)
+            eps = torch.empty((nl, plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
+        sigma = torch.empty_like(eps) if want_sigma else None
+        st_i, st_p = _f64(np.asarray(pb["stiffness"], dtype=np.float64).reshape(-1, 36))
+        e_i, e_p = _f64(E)
+        o = dict(eps=eps, sigma=sigma, sigma_bar=np.zeros((nl, plan.n_c)), iters=np.zeros(nl, dtype=np.int32),
+                 resid=np.zeros(nl))
+        keep += [st_i, e_i]
+        outs.append(o)
+        it = items[i]
+        it.plan = plan.handle
+        it.phase = phase.data_ptr()
+        it.n_phases = st_i.shape[0]
+        it.stiffness = st_p
+        it.C0[0], it.C0[1] = float(pb["C0"][0]), float(pb["C0"][1])
+        it.E = e_p
+        it.n_loads = nl
+        it.eps = eps.data_ptr()
+        it.sigma = sigma.data_ptr() if sigma is not None else None
+        it.sigma_bar = o["sigma_bar"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        it.iters = o["iters"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        it.resid = o["resid"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    L = lib()
+    L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
+    L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
+    wsb = int(L.lattice_multi_workspace_bytes(items, n, prec))
+    if wsb == 0:
+        raise LatticeError(LAT_ERR_ARG, "lattice_multi_workspace_bytes: invalid items")
+    dev = problems[0]["phase"].device
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    opts = _Opts(prec, bnd, 1 if warm_start else 0, None, 1 if mixed_increment else 0, 1 if plain_launches else 0)
+    f = L.basic_scheme_solve_multi
+    f.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts),
+                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    rc = f(items, n, float(tol), int(maxit), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+           _stream(stream))
+    _check(rc)
+    return rc, outs
+
+
+def multi_workspace_bytes(problems, precision="fp64"):
+    """Workspace bytes basic_scheme_solve_multi needs for these problems."""
+    n = len(problems)
+    items = (_MultiItem * n)()
+    for i, pb in enumerate(problems):
+        items[i].plan = pb["plan"].handle
+        items[i].phase = 1                     # only checked for NULL
+        items[i].n_phases = len(pb["stiffness"])
+        items[i].stiffness = ctypes.cast(1, ctypes.POINTER(ctypes.c_double))
+        items[i].E = ctypes.cast(1, ctypes.POINTER(ctypes.c_double))
+        items[i].eps = 16
+        items[i].n_loads = int(np.asarray(pb["E"]).reshape(-1, pb["plan"].n_c).shape[0])
+    L = lib()
+    L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
+    L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
+    return int(L.lattice_multi_workspace_bytes(items, n, {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]))

@@ -181,85 +181,94 @@ template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geome
 
 namespace {
 
-// the WHILE loop as a CUDA graph: body = row pass (update, residual, convergence) + column passes
+// adds the WHILE loop of one group to `top` as a root node: body = row pass (update, residual,
+// convergence; its last block sets the node's condition) + column passes
 template <typename Real>
-int launch_loop_graph(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs full, ColArgs ca, int n_items,
-                      cudaStream_t st) {
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cap = nullptr;
-  CK(cudaGraphCreate(&graph, 0));
+int add_loop_node(const GroupRun& g, cudaGraph_t top) {
   cudaGraphConditionalHandle handle;
-  CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&handle, top, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  CK(cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cap = nullptr;
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  CK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  full.it.cond = (unsigned long long)handle;
-  launch_row_pass<Real>(dv, full, g.row_blocks, n_items, kThreads, g.row_smem, cap);
-  enqueue_columns<Real>(dv, P, g, ca, n_items, cap);
-  cudaGraph_t captured = nullptr;
-  cudaError_t ce = cudaStreamEndCapture(cap, &captured);
-  cudaStreamDestroy(cap);
-  if (ce != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return lat_fail(LAT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (ce == cudaSuccess) {
+    RowArgs full = g.full;
+    full.it.cond = (unsigned long long)handle;
+    launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, cap);
+    enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, cap);
+    cudaGraph_t captured = nullptr;
+    ce = cudaStreamEndCapture(cap, &captured);
   }
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, st);
-  if (exec) cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+  cudaStreamDestroy(cap);
+  if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
   return LAT_OK;
 }
 
-// the WHILE loop with plain launches: the host reads the number of active items after each iteration
+// one iteration of one group with plain launches (no graph condition)
 template <typename Real>
-int launch_loop_plain(const lat_plan* P, const LatDev& dv, const Geometry& g, RowArgs full, ColArgs ca, int n_items,
-                      int maxit, cudaStream_t st) {
+int plain_iteration(const GroupRun& g, cudaStream_t st) {
+  RowArgs full = g.full;
   full.it.cond = 0;
-  for (int n = 0; n < maxit; ++n) {
-    launch_row_pass<Real>(dv, full, g.row_blocks, n_items, kThreads, g.row_smem, st);
-    enqueue_columns<Real>(dv, P, g, ca, n_items, st);
-    CK(cudaGetLastError());
-    int active = 0;
-    CK(cudaMemcpyAsync(&active, &full.it.glob->active, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (active == 0) break;
-  }
+  launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+  enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
+  CK(cudaGetLastError());
   return LAT_OK;
 }
 
 }  // namespace
 
-int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
-              const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws, const Work& wl,
-              const LatDev& dv, bool use_graph, double* sigma_bar, int* iters, double* resid, cudaStream_t st) {
+int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
+                  const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws,
+                  const Work& wl, const LatDev& dv, GroupRun& g, cudaStream_t st) {
   const int n_items = (int)items.size();
   const int d = P->d, n_c = d * (d + 1) / 2;
   const int64_t m = P->m;
   const bool fp32 = (o.precision == LAT_MIXED);
-  // material tables (one per distinct table entry) and the item table
+  g.P = P;
+  g.n_items = n_items;
+  g.n_c = n_c;
+  g.tol = tol;
+  g.maxit = maxit;
+  g.fp32 = fp32;
+  g.dv = dv;
+  g.ws = ws;
+  g.wl = wl;
+  g.loop = false;
+  g.want_hist = o.resid_history != nullptr && maxit > 0;
+  // material tables: per table, D = C - C0 (binary64 and binary32) and C, in tensor-component form;
+  // the reference medium is the table's (items sharing a table share C0)
   const int n_tables = (int)stiff.size();
-  std::vector<double> tabs((size_t)n_tables * 2 * (wl.table_bytes / sizeof(double)), 0.0);
   const size_t tstride = wl.table_bytes / sizeof(double);
+  std::vector<double> tabs((size_t)n_tables * 2 * tstride, 0.0);
   for (int t = 0; t < n_tables; ++t) {
-    double C0v[36];
-    memset(C0v, 0, sizeof(C0v));
-    const double lam0 = items[0].C0[0], mu0 = items[0].C0[1];
-    (void)lam0;
-    (void)mu0;
+    int owner = -1;
+    for (int i = 0; i < n_items && owner < 0; ++i)
+      if (items[i].table == t) owner = i;
+    double c0tc[36];
+    memset(c0tc, 0, sizeof(c0tc));
+    if (owner >= 0) {
+      double C0v[36];
+      memset(C0v, 0, sizeof(C0v));
+      const double lam0 = items[owner].C0[0], mu0 = items[owner].C0[1];
+      for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) C0v[i * 6 + j] = lam0;
+        C0v[i * 6 + i] = lam0 + 2 * mu0;
+        C0v[(i + 3) * 6 + (i + 3)] = mu0;
+      }
+      voigt_to_tc(C0v, d, c0tc);
+    }
     for (int p = 0; p < nph[t]; ++p) {
       double* Dp = &tabs[(size_t)(2 * t) * tstride + (size_t)p * n_c * n_c];
       double* Cp = &tabs[(size_t)(2 * t + 1) * tstride + (size_t)p * n_c * n_c];
       voigt_to_tc(stiff[t] + 36 * p, d, Cp);
-      for (int k = 0; k < n_c * n_c; ++k) Dp[k] = Cp[k];
+      for (int k = 0; k < n_c * n_c; ++k) Dp[k] = Cp[k] - c0tc[k];
     }
   }
   std::vector<ItemDev> hdev(n_items);
@@ -283,46 +292,26 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
     for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * it.E[c] * it.E[c];
     v.norm0 = nE2 > 0 ? sqrt((double)m * nE2) : 1.0;
   }
-  // D = C - C0 per table (the reference medium is the table's; items sharing a table share C0)
-  for (int t = 0; t < n_tables; ++t) {
-    int owner = -1;
-    for (int i = 0; i < n_items && owner < 0; ++i)
-      if (items[i].table == t) owner = i;
-    if (owner < 0) continue;
-    double C0v[36];
-    memset(C0v, 0, sizeof(C0v));
-    const double lam0 = items[owner].C0[0], mu0 = items[owner].C0[1];
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) C0v[i * 6 + j] = lam0;
-      C0v[i * 6 + i] = lam0 + 2 * mu0;
-      C0v[(i + 3) * 6 + (i + 3)] = mu0;
-    }
-    double c0tc[36];
-    voigt_to_tc(C0v, d, c0tc);
-    for (int p = 0; p < nph[t]; ++p) {
-      double* Dp = &tabs[(size_t)(2 * t) * tstride + (size_t)p * n_c * n_c];
-      for (int k = 0; k < n_c * n_c; ++k) Dp[k] -= c0tc[k];
-    }
-  }
-  CK(cudaMemcpyAsync(ws + wl.tables, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  // binary32 copies of the (C - C0) tables for the binary32 kernels
-  std::vector<float> tabs_f((size_t)n_tables * tstride, 0.0f);
+  g.tabs.swap(tabs);
+  g.tabs_f.assign((size_t)n_tables * tstride, 0.0f);
   for (int t = 0; t < n_tables; ++t)
-    for (size_t k = 0; k < tstride; ++k) tabs_f[(size_t)t * tstride + k] = (float)tabs[(size_t)(2 * t) * tstride + k];
-  CK(cudaMemcpyAsync(ws + wl.tables_f, tabs_f.data(), tabs_f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ws + wl.items, hdev.data(), hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
+    for (size_t k = 0; k < tstride; ++k) g.tabs_f[(size_t)t * tstride + k] = (float)g.tabs[(size_t)(2 * t) * tstride + k];
+  g.hdev.swap(hdev);
+  g.glob0.arrivals = 0;
+  g.glob0.active = n_items;
+  // host buffers stay alive in g until the caller synchronizes
+  CK(cudaMemcpyAsync(ws + wl.tables, g.tabs.data(), g.tabs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ws + wl.tables_f, g.tabs_f.data(), g.tabs_f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ws + wl.items, g.hdev.data(), g.hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
   // device scalars start from zero; the batch starts with every item active
   CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_items * kScalBytes + kScalBytes, st));
-  GlobScal g0;
-  g0.arrivals = 0;
-  g0.active = n_items;
   GlobScal* glob = (GlobScal*)(ws + wl.scal + (size_t)n_items * kScalBytes);
-  CK(cudaMemcpyAsync(glob, &g0, sizeof(g0), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(glob, &g.glob0, sizeof(GlobScal), cudaMemcpyHostToDevice, st));
   const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
   if (!o.warm_start) launch_fill(ditems, n_items, n_c, m, st);
   CK(cudaGetLastError());
   if (P->nax > 0 && maxit > 0) {
-    Geometry geo;
+    Geometry& geo = g.geo;
     memset(&geo, 0, sizeof(geo));
     int rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, n_items);
     if (rc != LAT_OK) return rc;
@@ -365,12 +354,12 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
     ColArgs c0 = ca;
     c0.scal = nullptr;
     c0.mat.increment = 0;
-    RowArgs full = ra;
-    full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0);
-    full.mat.increment = incr ? 1 : 0;
-    ColArgs cl = ca;
-    cl.scal = ra.it.scal;
-    cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
+    g.full = ra;
+    g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0);
+    g.full.mat.increment = incr ? 1 : 0;
+    g.cl = ca;
+    g.cl.scal = ra.it.scal;
+    g.cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
     if (fp32) {
       launch_row_pass<float>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
       enqueue_columns<float>(dv, P, geo, c0, n_items, st);
@@ -379,34 +368,47 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
       enqueue_columns<double>(dv, P, geo, c0, n_items, st);
     }
     CK(cudaGetLastError());
-    if (use_graph)
-      rc = fp32 ? launch_loop_graph<float>(P, dv, geo, full, cl, n_items, st)
-                : launch_loop_graph<double>(P, dv, geo, full, cl, n_items, st);
-    else
-      rc = fp32 ? launch_loop_plain<float>(P, dv, geo, full, cl, n_items, maxit, st)
-                : launch_loop_plain<double>(P, dv, geo, full, cl, n_items, maxit, st);
-    if (rc != LAT_OK) return rc;
+    g.loop = true;
   }
-  EffArgs ea;
-  ea.items = ditems;
-  ea.partials = (double*)(ws + wl.partials);
-  ea.pstride = wl.pstride;
-  ea.scal = (ItemScal*)(ws + wl.scal);
-  const int eff_blocks = (int)std::min<int64_t>(kEffBlocksMax, std::max<int64_t>(1, (m + 255) / 256));
-  launch_eff(dv, ea, eff_blocks, n_items, st);
+  g.ea.items = ditems;
+  g.ea.partials = (double*)(ws + wl.partials);
+  g.ea.pstride = wl.pstride;
+  g.ea.scal = (ItemScal*)(ws + wl.scal);
+  g.eff_blocks = (int)std::min<int64_t>(kEffBlocksMax, std::max<int64_t>(1, (m + 255) / 256));
+  return LAT_OK;
+}
+
+int group_add_loop(const GroupRun& g, cudaGraph_t top) {
+  if (!g.loop) return LAT_OK;
+  return g.fp32 ? add_loop_node<float>(g, top) : add_loop_node<double>(g, top);
+}
+
+int group_plain_iteration(const GroupRun& g, cudaStream_t st) {
+  if (!g.loop) return LAT_OK;
+  return g.fp32 ? plain_iteration<float>(g, st) : plain_iteration<double>(g, st);
+}
+
+const int* group_active_flag(const GroupRun& g) { return &g.full.it.glob->active; }
+
+int group_finish(GroupRun& g, cudaStream_t st) {
+  launch_eff(g.dv, g.ea, g.eff_blocks, g.n_items, st);
   CK(cudaGetLastError());
-  // scalars back to the host
-  std::vector<char> scal((size_t)n_items * kScalBytes);
-  CK(cudaMemcpyAsync(scal.data(), ws + wl.scal, scal.size(), cudaMemcpyDeviceToHost, st));
-  std::vector<double> hist;
-  if (o.resid_history && maxit > 0) {
-    hist.resize((size_t)n_items * LAT_HIST_CAP);
-    CK(cudaMemcpyAsync(hist.data(), ws + wl.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  g.scal.resize((size_t)g.n_items * kScalBytes);
+  CK(cudaMemcpyAsync(g.scal.data(), g.ws + g.wl.scal, g.scal.size(), cudaMemcpyDeviceToHost, st));
+  if (g.want_hist) {
+    g.hist.resize((size_t)g.n_items * LAT_HIST_CAP);
+    CK(cudaMemcpyAsync(g.hist.data(), g.ws + g.wl.hist, g.hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
-  CK(cudaStreamSynchronize(st));
+  return LAT_OK;
+}
+
+int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, int* iters, double* resid) {
+  const lat_plan* P = g.P;
+  const int n_c = g.n_c, maxit = g.maxit;
+  const double tol = g.tol;
   int status = LAT_OK;
-  for (int i = 0; i < n_items; ++i) {
-    const ItemScal* sc = (const ItemScal*)(scal.data() + (size_t)i * kScalBytes);
+  for (int i = 0; i < g.n_items; ++i) {
+    const ItemScal* sc = (const ItemScal*)(g.scal.data() + (size_t)i * kScalBytes);
     int it = sc->iter;
     double r = sc->last_r;
     if (P->nax == 0) {  // m = 1: every iterate equals E, r_n = 0; stop at the first r_n < tol
@@ -419,11 +421,11 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
     if (resid) resid[i] = r;
     if (sigma_bar)
       for (int c = 0; c < n_c; ++c) sigma_bar[i * n_c + c] = sc->sigma_bar[c];
-    if (o.resid_history && maxit > 0) {
+    if (g.want_hist) {
       if (P->nax == 0)
         for (int k = 0; k < it; ++k) o.resid_history[(size_t)i * maxit + k] = 0.0;
       for (int k = 0; k < std::min(it, std::min(maxit, LAT_HIST_CAP)) && P->nax > 0; ++k)
-        o.resid_history[(size_t)i * maxit + k] = hist[(size_t)i * LAT_HIST_CAP + k];
+        o.resid_history[(size_t)i * maxit + k] = g.hist[(size_t)i * LAT_HIST_CAP + k];
     }
     int s = LAT_OK;
     if (!isfinite(r) && maxit > 0) s = LAT_DIVERGED;
@@ -433,12 +435,80 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
   return status;
 }
 
+int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st) {
+  bool any_loop = false;
+  for (const GroupRun& g : groups) any_loop |= g.loop;
+  if (any_loop && use_graph) {
+    // one graph, one WHILE node per group as parallel roots: the groups iterate concurrently
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    for (const GroupRun& g : groups) {
+      int rc = group_add_loop(g, top);
+      if (rc != LAT_OK) {
+        cudaGraphDestroy(top);
+        return rc;
+      }
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ce = cudaGraphInstantiate(&exec, top, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, st);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(top);
+    if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+  } else if (any_loop) {
+    // plain launches: every group still active takes one iteration, then the host reads the flags
+    int maxit = 0;
+    for (const GroupRun& g : groups) maxit = std::max(maxit, g.loop ? g.maxit : 0);
+    std::vector<char> live(groups.size());
+    for (size_t k = 0; k < groups.size(); ++k) live[k] = groups[k].loop;
+    std::vector<int> active(groups.size(), 0);
+    for (int n = 0; n < maxit; ++n) {
+      bool any = false;
+      for (size_t k = 0; k < groups.size(); ++k) {
+        if (!live[k]) continue;
+        int rc = group_plain_iteration(groups[k], st);
+        if (rc != LAT_OK) return rc;
+        CK(cudaMemcpyAsync(&active[k], group_active_flag(groups[k]), sizeof(int), cudaMemcpyDeviceToHost, st));
+        any = true;
+      }
+      if (!any) break;
+      CK(cudaStreamSynchronize(st));
+      for (size_t k = 0; k < groups.size(); ++k)
+        if (live[k] && active[k] == 0) live[k] = 0;
+    }
+  }
+  for (GroupRun& g : groups) {
+    int rc = group_finish(g, st);
+    if (rc != LAT_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(st));
+  return LAT_OK;
+}
+
+int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
+              const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws, const Work& wl,
+              const LatDev& dv, bool use_graph, double* sigma_bar, int* iters, double* resid, cudaStream_t st) {
+  std::vector<GroupRun> groups(1);
+  int rc = group_prepare(P, items, stiff, nph, tol, maxit, o, ws, wl, dv, groups[0], st);
+  if (rc != LAT_OK) return rc;
+  if ((rc = run_groups(groups, use_graph, st)) != LAT_OK) return rc;
+  return group_decode(groups[0], o, sigma_bar, iters, resid);
+}
+
 int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts& o) {
   if (maxit < 0 || !(tol >= 0)) return lat_fail(LAT_ERR_ARG, "bad maxit/tol");
   if (o.precision != LAT_FP64 && o.precision != LAT_MIXED) return lat_fail(LAT_ERR_ARG, "bad precision");
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
-  (void)P;
-  return LAT_OK;
+  return check_geometry(P, o.precision);
+}
+
+// the shared-memory limits bind at the smallest launch shape (one row per block, one column per
+// tile), which does not depend on the number of items
+int check_geometry(const lat_plan* P, int precision) {
+  if (P->nax == 0) return LAT_OK;
+  Geometry geo;
+  memset(&geo, 0, sizeof(geo));
+  return geometry(P, P->d * (P->d + 1) / 2, precision == LAT_MIXED ? 8 : 16, P->Rh, true, geo, 1);
 }
 
 int check_c0(const double* C0) {
@@ -470,12 +540,12 @@ using namespace latms_detail;
 void lat_graph_cache_free(lat_plan* P) { (void)P; }
 
 extern "C" size_t lattice_workspace_bytes(const lat_plan* P, int n_loads, int precision) {
-  if (!P || n_loads <= 0) return 0;
+  if (!P || n_loads <= 0 || check_geometry(P, precision) != LAT_OK) return 0;
   return layout(P, n_loads, precision, kMaxPhases, 1).total;
 }
 
 extern "C" size_t lattice_batch_workspace_bytes(const lat_plan* P, int n_items, int precision) {
-  if (!P || n_items <= 0) return 0;
+  if (!P || n_items <= 0 || check_geometry(P, precision) != LAT_OK) return 0;
   return layout(P, n_items, precision, LAT_BATCH_MAX_PHASES, n_items).total;
 }
 
@@ -548,6 +618,122 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
   const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
   return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar, iters, resid,
                    (cudaStream_t)stream);
+}
+
+namespace {
+
+// items of basic_scheme_solve_multi grouped by plan (order of first appearance)
+struct MultiGroup {
+  const lat_plan* P;
+  std::vector<int> inst;   // indices into the caller's items
+  int n_loads;             // load cases over the group = batch items
+};
+
+int multi_groups(const lat_multi_item* items, int n, std::vector<MultiGroup>& groups) {
+  groups.clear();
+  for (int i = 0; i < n; ++i) {
+    const lat_multi_item& b = items[i];
+    if (!b.plan || !b.phase || !b.stiffness || !b.E || !b.eps)
+      return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: NULL item field");
+    if (b.n_phases < 1 || b.n_phases > LAT_BATCH_MAX_PHASES)
+      return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: item n_phases not in 1..LAT_BATCH_MAX_PHASES");
+    if (b.n_loads < 1) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: item n_loads < 1");
+    size_t k = 0;
+    while (k < groups.size() && groups[k].P != b.plan) ++k;
+    if (k == groups.size()) groups.push_back(MultiGroup{b.plan, {}, 0});
+    groups[k].inst.push_back(i);
+    groups[k].n_loads += b.n_loads;
+  }
+  return LAT_OK;
+}
+
+}  // namespace
+
+extern "C" size_t lattice_multi_workspace_bytes(const lat_multi_item* items, int n_items, int precision) {
+  if (!items || n_items < 1) return 0;
+  std::vector<MultiGroup> groups;
+  if (multi_groups(items, n_items, groups) != LAT_OK) return 0;
+  size_t total = 0;
+  for (const MultiGroup& g : groups) {
+    if (check_geometry(g.P, precision) != LAT_OK) return 0;
+    total += align256(layout(g.P, g.n_loads, precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size()).total);
+  }
+  return total;
+}
+
+extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items, double tol, int maxit,
+                                        const lat_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                                        void* stream) {
+  if (!items || n_items < 1 || !workspace) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: bad argument");
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.resid_history) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: residual histories are not kept");
+  std::vector<MultiGroup> mg;
+  if (int rc = multi_groups(items, n_items, mg)) return rc;
+  if (workspace_bytes < lattice_multi_workspace_bytes(items, n_items, o.precision))
+    return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  for (int i = 0; i < n_items; ++i) {
+    if (int rc = check_c0(items[i].C0)) return rc;
+    if (((uintptr_t)items[i].eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+  }
+  for (const MultiGroup& g : mg) {
+    if (int rc = check_common(g.P, tol, maxit, o)) return rc;
+    if (int rc = lat_ensure_tables(const_cast<lat_plan*>(g.P))) return rc;
+  }
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<GroupRun> runs(mg.size());
+  char* ws = (char*)workspace;
+  size_t off = 0;
+  for (size_t k = 0; k < mg.size(); ++k) {
+    const MultiGroup& g = mg[k];
+    const int n_c = g.P->d * (g.P->d + 1) / 2;
+    std::vector<ItemHost> its;
+    std::vector<const double*> stiff;
+    std::vector<int> nph;
+    for (size_t t = 0; t < g.inst.size(); ++t) {
+      const lat_multi_item& b = items[g.inst[t]];
+      for (int lc = 0; lc < b.n_loads; ++lc) {
+        ItemHost it;
+        it.phase = b.phase;
+        it.table = (int)t;
+        it.C0[0] = b.C0[0];
+        it.C0[1] = b.C0[1];
+        for (int c = 0; c < 6; ++c) it.E[c] = c < n_c ? b.E[(size_t)lc * n_c + c] : 0.0;
+        it.eps = b.eps + (size_t)lc * n_c * g.P->m;
+        it.sigma = b.sigma ? b.sigma + (size_t)lc * n_c * g.P->m : nullptr;
+        its.push_back(it);
+      }
+      stiff.push_back(b.stiffness);
+      nph.push_back(b.n_phases);
+    }
+    const Work wl = layout(g.P, g.n_loads, o.precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size());
+    const LatDev dv = make_dev(g.P, o.precision == LAT_MIXED);
+    if (int rc = group_prepare(g.P, its, stiff, nph, tol, maxit, o, ws + off, wl, dv, runs[k], st)) return rc;
+    off += align256(wl.total);
+  }
+  if (int rc = run_groups(runs, o.plain_launches == 0, st)) return rc;
+  int status = LAT_OK;
+  for (size_t k = 0; k < mg.size(); ++k) {
+    const MultiGroup& g = mg[k];
+    const int n_c = g.P->d * (g.P->d + 1) / 2;
+    std::vector<double> sb((size_t)g.n_loads * n_c);
+    std::vector<int> it(g.n_loads);
+    std::vector<double> r(g.n_loads);
+    status = std::max(status, group_decode(runs[k], o, sb.data(), it.data(), r.data()));
+    int j = 0;
+    for (int idx : g.inst) {
+      const lat_multi_item& b = items[idx];
+      for (int lc = 0; lc < b.n_loads; ++lc, ++j) {
+        if (b.sigma_bar)
+          for (int c = 0; c < n_c; ++c) b.sigma_bar[lc * n_c + c] = sb[(size_t)j * n_c + c];
+        if (b.iters) b.iters[lc] = it[j];
+        if (b.resid) b.resid[lc] = r[j];
+      }
+    }
+  }
+  return status;
 }
 
 extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,

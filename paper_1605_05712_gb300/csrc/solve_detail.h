@@ -50,9 +50,40 @@ template <typename Real>
 void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,
                      cudaStream_t st);
 int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts& o);
+int check_geometry(const lat_plan* P, int precision);
 int check_c0(const double* C0);
 void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, const double* E, int n_loads,
                      double* eps, double* sigma, std::vector<ItemHost>& items);
+// one batch of items on one plan, prepared for a loop that may run beside other batches
+struct GroupRun {
+  const lat_plan* P;
+  int n_items, n_c, maxit;
+  double tol;
+  bool fp32, loop, want_hist;
+  LatDev dv;
+  Geometry geo;
+  RowArgs full;
+  ColArgs cl;
+  EffArgs ea;
+  int eff_blocks;
+  char* ws;
+  Work wl;
+  GlobScal glob0;
+  std::vector<double> tabs;     // host staging, alive until the stream is synchronized
+  std::vector<float> tabs_f;
+  std::vector<ItemDev> hdev;
+  std::vector<char> scal;       // host copy of the item scalars after the solve
+  std::vector<double> hist;
+};
+// uploads tables and items, fills eps^(0) = E (cold start) and enqueues the prologue on `st`
+int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
+                  const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws,
+                  const Work& wl, const LatDev& dv, GroupRun& g, cudaStream_t st);
+// the loops of all groups (one CUDA graph with a WHILE node per group, or plain launches), then the
+// effective stress and the scalars of every group; returns after synchronizing `st`
+int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st);
+// outputs of a finished group; returns its worst status
+int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, int* iters, double* resid);
 // runs a batch on workspace `ws` laid out by `wl`; dv carries the twiddle-table pointers;
 // use_graph: CUDA-graph WHILE loop, else plain launches with a host check per iteration
 int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,

@@ -213,3 +213,62 @@ def hashin_workload(seed=BASE_SEED, c=(0.1, 0.15, 0.2), total_fraction=0.25, cor
     lams, mus = zip(*[iso_projection(V) for V in stiff])
     return dict(c=c, rho_c=rho_c, rho_e=rho_e, R=R, stiffness=stiff, eps0=eps0, ceff_eps0=ceff_eps0,
                 C0=c0_mean_extremes(lams, mus))
+
+
+# ------------------------------------------------------------------ serving sweep (uneven batch)
+def _unimodular(rng, d, n_shears=3, amp=2):
+    """Product of n_shears random elementary shears I + s e_i e_j^T (i != j, s in [-amp, amp])."""
+    U = np.eye(d, dtype=np.int64)
+    for _ in range(n_shears):
+        i, j = rng.choice(d, size=2, replace=False)
+        S = np.eye(d, dtype=np.int64)
+        S[i, j] = int(rng.integers(-amp, amp + 1))
+        U = U @ S
+    return U
+
+
+def sweep_matrix(rng, d, U_exp, kind):
+    """Integer M with |det M| = 2^U_exp of the given kind:
+    'rank1'  divisors (1, .., 1, m): M = [[m, 0(, 0)], [-z2, 1(, 0)](, [-z3, 0, 1])], z random;
+    'rank2'  divisors (e1, m / e1) in 2-D or (1, e2, m / e2) in 3-D, e = 2^a, a in [1, U_exp / 2],
+             wrapped in random unimodular shears: M = U1 diag(e) V1;
+    'diag'   the tensor grid diag(2^a_1, .., 2^a_d), exponents a random composition of U_exp (each >= 1)."""
+    m = 1 << U_exp
+    if kind == "rank1":
+        M = np.eye(d, dtype=np.int64)
+        M[0, 0] = m
+        for i in range(1, d):
+            M[i, 0] = -int(rng.integers(1, m))
+        return M.tolist()
+    if kind == "rank2":
+        a = int(rng.integers(1, U_exp // 2 + 1))
+        e = [1 << a, m >> a] if d == 2 else [1, 1 << a, m >> a]
+        return (_unimodular(rng, d) @ np.diag(e).astype(np.int64) @ _unimodular(rng, d)).tolist()
+    cuts = np.sort(rng.choice(np.arange(1, U_exp), size=d - 1, replace=False))
+    a = np.diff(np.concatenate([[0], cuts, [U_exp]]))
+    return np.diag([1 << int(x) for x in a]).astype(np.int64).tolist()
+
+
+def serving_sweep(n=256, seed=BASE_SEED, m_exp=(12, 21), contrast_log10=(-2.0, 2.0)):
+    """Seeded uneven batch of independent problems (one dict per instance, seed + i):
+    d in {2, 3}; m = 2^U, U uniform in m_exp (inclusive); kind uniform in rank1 / rank2 / diag; 1-8
+    periodic ellipsoidal inclusions (ellipses in 2-D) at volume fraction U(0.05, 0.4); matrix (1, 1) and
+    inclusion lam = mu = 10^U(contrast_log10); C0 the mean of the extremes; the n_c unit load cases."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        d = int(rng.integers(2, 4))
+        U_exp = int(rng.integers(m_exp[0], m_exp[1] + 1))
+        kind = ["rank1", "rank2", "diag"][int(rng.integers(0, 3))]
+        M = sweep_matrix(rng, d, U_exp, kind)
+        n_incl = int(rng.integers(1, 9))
+        incl = random_inclusions(int(rng.integers(1 << 30)), d, n_incl, float(rng.uniform(0.05, 0.4)))
+        k = float(10.0 ** rng.uniform(*contrast_log10))
+        n_c = d * (d + 1) // 2
+        E = np.zeros((n_c, n_c))
+        for a in range(n_c):
+            E[a, a] = 1.0 if a < d else 0.5
+        out.append(dict(d=d, M=M, kind=kind, m=1 << U_exp, incl=incl, contrast=k,
+                        stiffness=[iso_voigt(1.0, 1.0), iso_voigt(k, k)], C0=c0_mean_extremes([1.0, k], [1.0, k]),
+                        E=E))
+    return out
