@@ -130,6 +130,11 @@ typedef struct lat_solve_opts {
   int mixed_increment;  /* LAT_MIXED only: 1 = binary32 kernels carry the increment
                            eps^(n+1) - eps^(n) (accumulated into the binary64 strain), 0 = they
                            carry the strain itself */
+  int mixed_restart;    /* LAT_MIXED increment form: 0 (default) = one binary64 iteration restarts
+                           the increment recurrence when an item's residual first falls below
+                           sqrt(tol) (binary32 rounding otherwise stays in the fixed point as an
+                           offset of up to 1/(1 - rate) times the accumulated rounding);
+                           negative = no restart.  The restart counts as an iteration. */
   int plain_launches;   /* 0: the iteration is a CUDA-graph WHILE loop (one replay per solve);
                            nonzero: plain kernel launches with a host read of the convergence
                            state after every iteration, same results (for profilers that do not

@@ -36,7 +36,8 @@ class LatticeError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("resid_history", ctypes.POINTER(ctypes.c_double)),
-                ("mixed_increment", ctypes.c_int), ("plain_launches", ctypes.c_int)]
+                ("mixed_increment", ctypes.c_int), ("mixed_restart", ctypes.c_int),
+                ("plain_launches", ctypes.c_int)]
 
 
 def lib():
@@ -156,7 +157,8 @@ def lattice_fft(plan, x, inverse=False, stream=None):
 
 def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
                        boundary="average", eps0=None, want_sigma=False, history=False, workspace=None,
-                       eps_out=None, stream=None, mixed_increment=True, plain_launches=False):
+                       eps_out=None, stream=None, mixed_increment=True, plain_launches=False,
+                       mixed_restart=True):
     """Algorithm 1 on the GPU.  Returns a dict of torch/numpy results.
 
     phase      uint8 CUDA tensor (m,), plan order
@@ -194,7 +196,7 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     hist = np.zeros((n_loads, max(maxit, 1))) if history else None
     opts = _Opts(prec, bnd, 1 if eps0 is not None else 0,
                  hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
-                 1 if mixed_increment else 0, 1 if plain_launches else 0)
+                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0)
     rc = lib().basic_scheme_solve(
         plan.handle, ctypes.c_void_p(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
         ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
@@ -257,7 +259,7 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
     resid = np.zeros(n_loads)
-    opts = _Opts(prec, bnd, 0, None, 1, 1)
+    opts = _Opts(prec, bnd, 0, None, 1, 0, 1)
     L = lib()
     f = L.basic_scheme_solve_noalloc
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3 + \
@@ -282,7 +284,7 @@ class _BatchItem(ctypes.Structure):
 
 def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit=1000, precision="fp64",
                              boundary="average", want_sigma=False, history=False, workspace=None, eps_out=None,
-                             stream=None, mixed_increment=True, plain_launches=False):
+                             stream=None, mixed_increment=True, plain_launches=False, mixed_restart=True):
     """Algorithm 1 for a batch of independent microstructures on one lattice, in one set of launches.
 
     phases       list of uint8 CUDA tensors (m,)
@@ -325,7 +327,7 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     resid = np.zeros(n)
     hist = np.zeros((n, max(maxit, 1))) if history else None
     opts = _Opts(prec, bnd, 0, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
-                 1 if mixed_increment else 0, 1 if plain_launches else 0)
+                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0)
     f = L.basic_scheme_solve_batch
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(_BatchItem), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                   ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -352,7 +354,7 @@ class _MultiItem(ctypes.Structure):
 
 def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", boundary="average",
                              want_sigma=False, workspace=None, stream=None, mixed_increment=True,
-                             plain_launches=False, warm_start=False):
+                             plain_launches=False, warm_start=False, mixed_restart=True):
     """Algorithm 1 for independent problems on different lattices in one call (one CUDA graph).
 
     problems  list of dicts: plan (LatticePlan), phase (uint8 CUDA tensor (m,)), stiffness
@@ -406,7 +408,8 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
         raise LatticeError(LAT_ERR_ARG, "lattice_multi_workspace_bytes: invalid items")
     dev = problems[0]["phase"].device
     ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
-    opts = _Opts(prec, bnd, 1 if warm_start else 0, None, 1 if mixed_increment else 0, 1 if plain_launches else 0)
+    opts = _Opts(prec, bnd, 1 if warm_start else 0, None, 1 if mixed_increment else 0, 0 if mixed_restart else -1,
+                 1 if plain_launches else 0)
     f = L.basic_scheme_solve_multi
     f.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts),
                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]

@@ -264,7 +264,11 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const ItemDev* item = a.items + item_i;
   ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
   const bool update = (a.flags & ROW_UPDATE) != 0;
-  if (update && *(volatile const int*)&isc->done) return;  // this item finished earlier
+  if (a.flags & ROW_ONLY_PAUSED) {
+    if (*(volatile const int*)&isc->done != ITEM_PAUSED) return;
+  } else if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) {
+    return;  // this item finished (or paused) earlier
+  }
   C* buf = (C*)smem_raw;
   C* nyq = buf + (size_t)nlines * Rh;
   double* red = (double*)(nyq + nlines);
@@ -328,10 +332,11 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 
   // pointwise: update, residual, polarization
   double dsum = 0.0;
-  // increment form: T carries delta^(n-1) once the first update is done (iteration counter > 0);
-  // the polarization is always taken of the increment
-  const bool tau_of_delta = update && (a.flags & ROW_INCREMENT) != 0;
-  const bool incr = tau_of_delta && (*(volatile const int*)&isc->iter > 0);
+  // increment form: T carries delta^(n-1) once the first update is done (iteration counter > 0), or
+  // from the start after a cold-start prologue; the polarization is always taken of the increment
+  const bool tau_of_delta = update && (a.flags & (ROW_INCREMENT | ROW_TAU_DELTA)) != 0;
+  const bool incr = update && (a.flags & ROW_INCREMENT) != 0 &&
+                    ((a.flags & ROW_INCR_FIRST) != 0 || *(volatile const int*)&isc->iter > 0);
   DF dfs = {0.f, 0.f}, dfs_shear = {0.f, 0.f};  // m <= 2^28: in-item offsets stay below 2^31
   for (int idx = tid; idx < rpc * Rh; idx += nthr) {
     const int row = idx >> lgRh, n = idx & (Rh - 1);
@@ -479,7 +484,9 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
       isc->last_r = r;
       const bool cont = isfinite(r) && !(r < a.it.tol) && n < a.it.maxit;
       isc->counter = 0u;
-      if (!cont) isc->done = 1;
+      if (!cont) isc->done = ITEM_DONE;
+      else if (a.it.pause_tol > 0 && r < a.it.pause_tol) isc->done = ITEM_PAUSED;
+      else isc->done = ITEM_ACTIVE;
       __threadfence();
       GlobScal* gs = a.it.glob;
       const unsigned arrived = atomicAdd(&gs->arrivals, 1u);
@@ -500,7 +507,10 @@ template <typename Real, int NC>
 __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   typedef typename cplx_of<Real>::type C;
   const int item_i = blockIdx.y;
-  if (a.scal && *(volatile const int*)&((const ItemScal*)((const char*)a.scal + (size_t)item_i * 256))->done) return;
+  if (a.scal) {
+    const int st = *(volatile const int*)&((const ItemScal*)((const char*)a.scal + (size_t)item_i * 256))->done;
+    if (a.only_paused ? st != ITEM_PAUSED : st != ITEM_ACTIVE) return;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = (C*)smem_raw;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -745,6 +755,56 @@ void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, in
   const int64_t nb = dv.nrows / rpc;
   row_complex_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, in, out, n_f, inverse, scale, rpc);
 }
+__global__ void prep_restart_kernel(ItemScal* scal, GlobScal* glob, int n_items) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int n = 0;
+  for (int i = 0; i < n_items; ++i)
+    n += ((const ItemScal*)((const char*)scal + (size_t)i * 256))->done == ITEM_PAUSED;
+  glob->active = n;
+  glob->arrivals = 0u;
+}
+
+__global__ void set_cond_kernel(const GlobScal* glob, unsigned long long cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, glob->active > 0 ? 1u : 0u);
+}
+
+// grid (blocks, items); t_elems / tn_elems complex values per item in T / TN
+__global__ void spectrum_to_f32_kernel(const double2* T64, const double2* TN64, float2* T32, float2* TN32,
+                                       int64_t t_elems, int64_t tn_elems, int64_t t_stride, int64_t tn_stride,
+                                       const ItemScal* scal) {
+  const int item_i = blockIdx.y;
+  if (((const ItemScal*)((const char*)scal + (size_t)item_i * 256))->done != ITEM_ACTIVE) return;
+  const double2* a = T64 + item_i * t_stride;
+  float2* b = T32 + item_i * t_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < t_elems; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = a[i];
+    b[i] = make_float2((float)v.x, (float)v.y);
+  }
+  const double2* an = TN64 + item_i * tn_stride;
+  float2* bn = TN32 + item_i * tn_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tn_elems; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = an[i];
+    bn[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void launch_prep_restart(ItemScal* scal, GlobScal* glob, int n_items, cudaStream_t st) {
+  prep_restart_kernel<<<1, 32, 0, st>>>(scal, glob, n_items);
+}
+void launch_set_cond(const GlobScal* glob, unsigned long long cond, cudaStream_t st) {
+  set_cond_kernel<<<1, 32, 0, st>>>(glob, cond);
+}
+void launch_spectrum_to_f32(const void* T64, const void* TN64, void* T32, void* TN32, int64_t t_elems,
+                            int64_t tn_elems, int64_t t_stride, int64_t tn_stride, const ItemScal* scal,
+                            int n_items, cudaStream_t st) {
+  int64_t nb = (t_elems + 255) / 256;
+  if (nb > 1216) nb = 1216;
+  spectrum_to_f32_kernel<<<dim3((unsigned)nb, n_items), 256, 0, st>>>(
+      (const double2*)T64, (const double2*)TN64, (float2*)T32, (float2*)TN32, t_elems, tn_elems, t_stride, tn_stride,
+      scal);
+}
+
 void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st) {
   int64_t nb = (m + 255) / 256;
   if (nb > 2048) nb = 2048;

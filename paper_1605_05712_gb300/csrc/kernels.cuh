@@ -7,6 +7,15 @@
 #define ROW_UPDATE 2     // inverse-transform T into eps^(n+1), residual, write eps
 #define ROW_GAMMA 4      // no column axes: apply Gamma0 on the row spectrum (d_M = 1, short)
 #define ROW_INCREMENT 8  // mixed precision: T carries the increment delta, eps += delta
+#define ROW_INCR_FIRST 16  // with ROW_INCREMENT: T carries an increment from the first iteration on (cold
+                           // start: the prologue mapped k = 0 to 0, so T holds G(E) - E)
+#define ROW_ONLY_PAUSED 32 // restart passes: only items in state ITEM_PAUSED take part
+#define ROW_TAU_DELTA 64   // with ROW_UPDATE: the polarization is taken of the increment eps^(n+1) - eps^(n)
+
+// ItemScal::done
+#define ITEM_ACTIVE 0
+#define ITEM_DONE 1        // converged, maxit, or non-finite residual
+#define ITEM_PAUSED 2      // residual fell below the restart level: waits for the binary64 restart
 
 // Column pass modes
 #define COL_FWD 0
@@ -30,7 +39,7 @@ struct ItemDev {
 // Device scalars of one item (the first bytes of its 256-byte slot)
 struct ItemScal {
   unsigned counter;      // last-block-done counter of the row pass (reset by the last block)
-  int done;              // item finished (converged, maxit, or non-finite residual)
+  int done;              // ITEM_ACTIVE, ITEM_DONE or ITEM_PAUSED
   int iter;              // iterations performed
   unsigned eff_counter;  // last-block counter of the effective-stress kernel
   double last_r;         // last residual
@@ -56,6 +65,7 @@ struct IterArgs {
   GlobScal* glob;
   double* hist;          // per item residual history, stride LAT_HIST_CAP
   double tol;
+  double pause_tol;      // > 0: an item whose residual falls below it (but not below tol) pauses
   int maxit;
   int n_items;
   unsigned long long cond;  // cudaGraphConditionalHandle of the enclosing WHILE node (0: none)
@@ -91,7 +101,8 @@ struct ColArgs {
   double scale;          // multiply on store (1/m for the last forward pass of lattice_fft), 1 = none
   const ItemDev* items;  // solver: E and Green constants per item
   MatArgs mat;
-  const ItemScal* scal;  // NULL or per-item scalars (skip finished items)
+  const ItemScal* scal;  // NULL or per-item scalars (skip items not ITEM_ACTIVE)
+  int only_paused;       // with scal: process ITEM_PAUSED items only (restart passes)
 };
 
 struct EffArgs {
@@ -112,3 +123,11 @@ template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
                         int rpc, int nthreads, size_t smem, cudaStream_t st);
 int lat_kernel_attrs(size_t max_smem);
+// restart of the increment form: glob->active = number of paused items, arrivals = 0
+void launch_prep_restart(ItemScal* scal, GlobScal* glob, int n_items, cudaStream_t st);
+// sets a WHILE node's condition to (glob->active > 0) from inside the graph
+void launch_set_cond(const GlobScal* glob, unsigned long long cond, cudaStream_t st);
+// binary64 -> binary32 copy of the spectrum (T and Nyquist planes) of every ITEM_ACTIVE item
+void launch_spectrum_to_f32(const void* T64, const void* TN64, void* T32, void* TN32, int64_t t_elems,
+                            int64_t tn_elems, int64_t t_stride, int64_t tn_stride, const ItemScal* scal,
+                            int n_items, cudaStream_t st);

@@ -132,6 +132,13 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   off = align256(off + (size_t)n_items * kScalBytes + kScalBytes);
   w.hist = off;
   off = align256(off + (size_t)n_items * LAT_HIST_CAP * sizeof(double));
+  w.T64 = w.TN64 = off;
+  if (precision == LAT_MIXED) {
+    w.T64 = off;
+    off = align256(off + (size_t)n_items * n_c * (P->m / 2) * 16);
+    w.TN64 = off;
+    off = align256(off + (size_t)n_items * n_c * P->nrows * 16);
+  }
   w.total = off;
   return w;
 }
@@ -181,25 +188,23 @@ template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geome
 
 namespace {
 
-// adds the WHILE loop of one group to `top` as a root node: body = row pass (update, residual,
+// adds a WHILE node to `top` after `dep` (or as a root): body = row pass (update, residual,
 // convergence; its last block sets the node's condition) + column passes
 template <typename Real>
-int add_loop_node(const GroupRun& g, cudaGraph_t top) {
-  cudaGraphConditionalHandle handle;
-  CK(cudaGraphConditionalHandleCreate(&handle, top, 1, cudaGraphCondAssignDefault));
+int add_loop_node(const GroupRun& g, const RowArgs& body_row, cudaGraph_t top, const cudaGraphNode_t* dep,
+                  cudaGraphConditionalHandle handle, cudaGraphNode_t* node_out) {
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &cp));
+  CK(cudaGraphAddNode(node_out, top, dep, nullptr, dep ? 1 : 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStream_t cap = nullptr;
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (ce == cudaSuccess) {
-    RowArgs full = g.full;
+    RowArgs full = body_row;
     full.it.cond = (unsigned long long)handle;
     launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, cap);
     enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, cap);
@@ -213,13 +218,64 @@ int add_loop_node(const GroupRun& g, cudaGraph_t top) {
 
 // one iteration of one group with plain launches (no graph condition)
 template <typename Real>
-int plain_iteration(const GroupRun& g, cudaStream_t st) {
-  RowArgs full = g.full;
+int plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream_t st) {
+  RowArgs full = body_row;
   full.it.cond = 0;
   launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
   enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
   CK(cudaGetLastError());
   return LAT_OK;
+}
+
+// the binary64 restart of the paused items (mixed precision only); cond2 != 0 sets the condition of
+// the loop that follows from the number of resumed items
+int enqueue_restart(const GroupRun& g, unsigned long long cond2, cudaStream_t st) {
+  const Work& wl = g.wl;
+  ItemScal* scal = (ItemScal*)(g.ws + wl.scal);
+  launch_prep_restart(scal, g.full.it.glob, g.n_items, st);
+  launch_row_pass<double>(g.dv64, g.r_pro, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
+  enqueue_columns<double>(g.dv64, g.P, g.geo64, g.c64, g.n_items, st);
+  launch_row_pass<double>(g.dv64, g.r_upd, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
+  const int64_t te = (int64_t)g.n_c * (g.P->m / 2), tne = (int64_t)g.n_c * g.P->nrows;
+  launch_spectrum_to_f32(g.ws + wl.T64, g.ws + wl.TN64, g.ws + wl.T, g.ws + wl.TN, te, tne, g.full.t_stride,
+                         g.full.tn_stride, scal, g.n_items, st);
+  if (g.P->nax > 1) enqueue_columns<float>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
+  if (cond2) launch_set_cond(g.full.it.glob, cond2, st);
+  CK(cudaGetLastError());
+  return LAT_OK;
+}
+
+// the loops of one group in `top`: WHILE (with pause) [-> restart chain -> WHILE]
+int add_group_loops(const GroupRun& g, cudaGraph_t top) {
+  cudaGraphConditionalHandle h1;
+  CK(cudaGraphConditionalHandleCreate(&h1, top, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t n1;
+  int rc = g.fp32 ? add_loop_node<float>(g, g.full, top, nullptr, h1, &n1)
+                  : add_loop_node<double>(g, g.full, top, nullptr, h1, &n1);
+  if (rc != LAT_OK || !g.restart) return rc;
+  cudaGraphConditionalHandle h2;
+  CK(cudaGraphConditionalHandleCreate(&h2, top, 0, cudaGraphCondAssignDefault));
+  cudaStream_t cap = nullptr;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraphNode_t leaf = nullptr;
+  cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, top, &n1, nullptr, 1, cudaStreamCaptureModeRelaxed);
+  if (ce == cudaSuccess) {
+    rc = enqueue_restart(g, (unsigned long long)h2, cap);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t ie = cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    if (ie == cudaSuccess && nd == 1) leaf = deps[0];
+    cudaGraph_t captured = nullptr;
+    ce = cudaStreamEndCapture(cap, &captured);
+    if (ce == cudaSuccess && ie != cudaSuccess) ce = ie;
+  }
+  cudaStreamDestroy(cap);
+  if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("restart capture: ") + cudaGetErrorString(ce));
+  if (rc != LAT_OK) return rc;
+  if (!leaf) return lat_fail(LAT_ERR_CUDA, "restart capture: no single leaf node");
+  cudaGraphNode_t n2;
+  return add_loop_node<float>(g, g.full2, top, &leaf, h2, &n2);
 }
 
 }  // namespace
@@ -241,6 +297,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   g.ws = ws;
   g.wl = wl;
   g.loop = false;
+  g.restart = false;
   g.want_hist = o.resid_history != nullptr && maxit > 0;
   // material tables: per table, D = C - C0 (binary64 and binary32) and C, in tensor-component form;
   // the reference medium is the table's (items sharing a table share C0)
@@ -347,15 +404,19 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ca.mat = ra.mat;
     const bool incr = fp32 && o.mixed_increment;
     const bool gamma_in_row = (P->nax == 1);
-    // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns
+    // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns.  In the
+    // increment form from a cold start (eps^(0) = E everywhere) k = 0 maps to 0 instead, so that T
+    // holds the first increment G(E) - E and the binary32 rounding is relative to it, not to E
+    const bool incr_first = incr && !o.warm_start;
     RowArgs first = ra;
     first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
-    first.mat.increment = 0;
+    first.mat.increment = incr_first ? 1 : 0;
     ColArgs c0 = ca;
     c0.scal = nullptr;
-    c0.mat.increment = 0;
+    c0.mat.increment = incr_first ? 1 : 0;
     g.full = ra;
-    g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0);
+    g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) |
+                   (incr_first ? ROW_INCR_FIRST : 0);
     g.full.mat.increment = incr ? 1 : 0;
     g.cl = ca;
     g.cl.scal = ra.it.scal;
@@ -369,6 +430,37 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     }
     CK(cudaGetLastError());
     g.loop = true;
+    // one binary64 restart when an item's residual first falls below sqrt(tol): the increment
+    // recurrence accumulates binary32 rounding as a standing offset of the fixed point (it never
+    // re-evaluates G(eps)); the restart recomputes the increment exactly, and the iterations after it
+    // contract the offset
+    const double pause = sqrt(tol);
+    g.restart = incr && o.mixed_restart >= 0 && tol > 0 && pause > tol && maxit > 1;
+    if (g.restart) {
+      g.full.it.pause_tol = pause;
+      g.dv64 = make_dev(P, false);
+      memset(&g.geo64, 0, sizeof(g.geo64));
+      if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items)) != LAT_OK) return rc;
+      RowArgs r64 = ra;
+      r64.rpc = g.geo64.rpc;
+      r64.T = ws + wl.T64;
+      r64.TN = ws + wl.TN64;
+      r64.it.pause_tol = 0.0;
+      g.r_pro = r64;
+      g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | (gamma_in_row ? ROW_GAMMA : 0);
+      g.r_pro.mat.increment = 0;
+      g.r_upd = r64;
+      g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | (gamma_in_row ? ROW_GAMMA : 0);
+      g.r_upd.mat.increment = 1;
+      g.c64 = ca;
+      g.c64.T = r64.T;
+      g.c64.TN = r64.TN;
+      g.c64.scal = ra.it.scal;
+      g.c64.only_paused = 1;
+      g.c64.mat.increment = 0;
+      g.full2 = g.full;
+      g.full2.it.pause_tol = 0.0;
+    }
   }
   g.ea.items = ditems;
   g.ea.partials = (double*)(ws + wl.partials);
@@ -378,14 +470,9 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   return LAT_OK;
 }
 
-int group_add_loop(const GroupRun& g, cudaGraph_t top) {
+int group_plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream_t st) {
   if (!g.loop) return LAT_OK;
-  return g.fp32 ? add_loop_node<float>(g, top) : add_loop_node<double>(g, top);
-}
-
-int group_plain_iteration(const GroupRun& g, cudaStream_t st) {
-  if (!g.loop) return LAT_OK;
-  return g.fp32 ? plain_iteration<float>(g, st) : plain_iteration<double>(g, st);
+  return g.fp32 ? plain_iteration<float>(g, body_row, st) : plain_iteration<double>(g, body_row, st);
 }
 
 const int* group_active_flag(const GroupRun& g) { return &g.full.it.glob->active; }
@@ -435,15 +522,46 @@ int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, 
   return status;
 }
 
+namespace {
+
+// plain launches: every group still active takes one iteration of its current loop, then the host
+// reads the active counts; phase 0 = first loop, 1 = second loop after the restart
+int plain_loops(std::vector<GroupRun>& groups, int phase, cudaStream_t st) {
+  int maxit = 0;
+  for (const GroupRun& g : groups) maxit = std::max(maxit, g.loop ? g.maxit : 0);
+  std::vector<char> live(groups.size());
+  for (size_t k = 0; k < groups.size(); ++k) live[k] = groups[k].loop && (phase == 0 || groups[k].restart);
+  std::vector<int> active(groups.size(), 0);
+  for (int n = 0; n < maxit; ++n) {
+    bool any = false;
+    for (size_t k = 0; k < groups.size(); ++k) {
+      if (!live[k]) continue;
+      int rc = group_plain_iteration(groups[k], phase == 0 ? groups[k].full : groups[k].full2, st);
+      if (rc != LAT_OK) return rc;
+      CK(cudaMemcpyAsync(&active[k], group_active_flag(groups[k]), sizeof(int), cudaMemcpyDeviceToHost, st));
+      any = true;
+    }
+    if (!any) break;
+    CK(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < groups.size(); ++k)
+      if (live[k] && active[k] == 0) live[k] = 0;
+  }
+  return LAT_OK;
+}
+
+}  // namespace
+
 int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st) {
   bool any_loop = false;
   for (const GroupRun& g : groups) any_loop |= g.loop;
   if (any_loop && use_graph) {
-    // one graph, one WHILE node per group as parallel roots: the groups iterate concurrently
+    // one graph: per group a WHILE node (plus its restart chain and second WHILE node); the groups
+    // are parallel branches and iterate concurrently
     cudaGraph_t top = nullptr;
     CK(cudaGraphCreate(&top, 0));
     for (const GroupRun& g : groups) {
-      int rc = group_add_loop(g, top);
+      if (!g.loop) continue;
+      int rc = add_group_loops(g, top);
       if (rc != LAT_OK) {
         cudaGraphDestroy(top);
         return rc;
@@ -456,26 +574,15 @@ int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st) {
     cudaGraphDestroy(top);
     if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
   } else if (any_loop) {
-    // plain launches: every group still active takes one iteration, then the host reads the flags
-    int maxit = 0;
-    for (const GroupRun& g : groups) maxit = std::max(maxit, g.loop ? g.maxit : 0);
-    std::vector<char> live(groups.size());
-    for (size_t k = 0; k < groups.size(); ++k) live[k] = groups[k].loop;
-    std::vector<int> active(groups.size(), 0);
-    for (int n = 0; n < maxit; ++n) {
-      bool any = false;
-      for (size_t k = 0; k < groups.size(); ++k) {
-        if (!live[k]) continue;
-        int rc = group_plain_iteration(groups[k], st);
-        if (rc != LAT_OK) return rc;
-        CK(cudaMemcpyAsync(&active[k], group_active_flag(groups[k]), sizeof(int), cudaMemcpyDeviceToHost, st));
-        any = true;
+    int rc = plain_loops(groups, 0, st);
+    if (rc != LAT_OK) return rc;
+    bool any_restart = false;
+    for (const GroupRun& g : groups)
+      if (g.loop && g.restart) {
+        if ((rc = enqueue_restart(g, 0, st)) != LAT_OK) return rc;
+        any_restart = true;
       }
-      if (!any) break;
-      CK(cudaStreamSynchronize(st));
-      for (size_t k = 0; k < groups.size(); ++k)
-        if (live[k] && active[k] == 0) live[k] = 0;
-    }
+    if (any_restart && (rc = plain_loops(groups, 1, st)) != LAT_OK) return rc;
   }
   for (GroupRun& g : groups) {
     int rc = group_finish(g, st);
@@ -508,7 +615,8 @@ int check_geometry(const lat_plan* P, int precision) {
   if (P->nax == 0) return LAT_OK;
   Geometry geo;
   memset(&geo, 0, sizeof(geo));
-  return geometry(P, P->d * (P->d + 1) / 2, precision == LAT_MIXED ? 8 : 16, P->Rh, true, geo, 1);
+  // the mixed path also runs binary64 passes (its restart)
+  return geometry(P, P->d * (P->d + 1) / 2, 16, P->Rh, true, geo, 1);
 }
 
 int check_c0(const double* C0) {

@@ -27,6 +27,7 @@ struct Geometry {
 // byte offsets of the workspace regions of a batched solve
 struct Work {
   size_t T, TN, items, tables, tables_f, partials, scal, hist, total;
+  size_t T64, TN64;   // mixed precision: binary64 spectrum of the restart (0 bytes otherwise)
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
 };
@@ -62,8 +63,16 @@ struct GroupRun {
   bool fp32, loop, want_hist;
   LatDev dv;
   Geometry geo;
-  RowArgs full;
+  RowArgs full;       // loop body row pass (with the pause level when a restart follows)
   ColArgs cl;
+  // binary64 restart of the increment form: prologue of the paused items (r_pro, c64), binary64
+  // update whose polarization is of the exact increment (r_upd), cast of the spectrum, binary32
+  // columns (cl), then the second loop (full2)
+  bool restart;
+  LatDev dv64;
+  Geometry geo64;
+  RowArgs r_pro, r_upd, full2;
+  ColArgs c64;
   EffArgs ea;
   int eff_blocks;
   char* ws;
