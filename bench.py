@@ -214,7 +214,7 @@ def bench_gpu(args):
     E = load_cases()
     work = setup(dev)
     m = work[0]["plan"].m
-    ws = torch.empty(max(w["plan"].workspace_bytes(3) for w in work), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1)), dtype=torch.uint8, device=dev)
     eps = torch.empty((3, 3, m), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
@@ -427,6 +427,73 @@ def bench_warmstart(args):
                       "totals": tot, "judge_max_sigma_bar_rel_diff_vs_fp64_cold": judge, "per_seed": per_seed}))
 
 
+def bench_sweep(args):
+    """Uneven serving sweep: 256 seeded independent problems (2-D and 3-D, m = 2^12 .. 2^21, rank-1 /
+    rank-2 / diagonal lattices, 1-8 inclusions, contrast 1e-2 .. 1e2, all unit load cases), mixed
+    precision to a 1e-6 residual in one basic_scheme_solve_multi call (one CUDA graph, a WHILE loop per
+    lattice), against the same problems solved one call each; sampled problems judged against binary64."""
+    import torch
+    from paper_1605_05712_gb300 import (basic_scheme_solve, basic_scheme_solve_multi, lattice_plan,
+                                        multi_workspace_bytes, synth)
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    sweep = synth.serving_sweep()
+    probs = []
+    for s_ in sweep:
+        P = lattice_plan(s_["M"])
+        ph = torch.from_numpy(synth.inclusions_phase(P.points(), P.m, s_["incl"])).to(dev)
+        probs.append(dict(plan=P, phase=ph, stiffness=s_["stiffness"], C0=s_["C0"], E=s_["E"],
+                          eps=torch.empty((len(s_["E"]), P.n_c, P.m), dtype=torch.float64, device=dev)))
+    t_setup = time.perf_counter() - t0
+    ws = torch.empty(multi_workspace_bytes(probs, "mixed"), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+
+    def run_multi():
+        return basic_scheme_solve_multi(probs, tol=1e-6, maxit=5000, precision="mixed", workspace=ws)
+
+    def run_each():
+        out = []
+        for p_ in probs:
+            out.append(basic_scheme_solve(p_["plan"], p_["phase"], p_["stiffness"], p_["C0"], p_["E"], tol=1e-6,
+                                          maxit=5000, precision="mixed", eps_out=p_["eps"]))
+        return out
+    for name, fn in (("multi", run_multi), ("one_call_each", run_each)):
+        fn()
+        times = []
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        outs = out[1] if name == "multi" else out
+        pit = sum(p_["plan"].m * int(np.sum(o["iters"])) for p_, o in zip(probs, outs))
+        its = np.concatenate([np.asarray(o["iters"]) for o in outs])
+        res[name] = {"s": round(float(np.median(times)), 3), "point_iterations": pit,
+                     "value": round(pit / float(np.median(times)), 1),
+                     "iterations_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())]}
+    # judge a sample against binary64: extremes of contrast and the largest problems
+    order = np.argsort([s_["contrast"] for s_ in sweep])
+    sizes = np.argsort([s_["m"] for s_ in sweep])
+    pick = sorted(set(list(order[:2]) + list(order[-2:]) + list(sizes[-2:])))
+    _, outs = run_multi()
+    worst = {"strain": 0.0, "sigma_bar": 0.0}
+    for i in pick:
+        p_, o = probs[i], outs[i]
+        ref = basic_scheme_solve(p_["plan"], p_["phase"], p_["stiffness"], p_["C0"], p_["E"], tol=1e-6, maxit=5000)
+        worst["strain"] = max(worst["strain"], float((o["eps"] - ref["eps"]).abs().max() / ref["eps"].abs().max()))
+        worst["sigma_bar"] = max(worst["sigma_bar"], float(np.abs(o["sigma_bar"] - ref["sigma_bar"]).max()
+                                                           / np.abs(ref["sigma_bar"]).max()))
+    print(json.dumps({"workload": "sweep (config 4): 256 problems, m = 2^12..2^21 (sum %d points), 2-D and 3-D, "
+                                  "rank-1/rank-2/diagonal, contrast 1e-2..1e2, all unit load cases, mixed, tol 1e-6"
+                                  % sum(p_["plan"].m for p_ in probs),
+                      "metric": METRIC, "unit": "point-iterations/s", "setup_s": round(t_setup, 1), "results": res,
+                      "judged_problems": [int(i) for i in pick], "max_rel_err_vs_fp64": worst,
+                      "l2": "flushed between timed steps"}))
+
+
 def profile_case(args):
     """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
     import torch
@@ -511,7 +578,7 @@ def main():
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
     ap.add_argument("--plain-launches", action="store_true",
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
-    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart"])
+    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep"])
     ap.add_argument("--ws-samples", type=int, default=2000)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)
@@ -525,6 +592,8 @@ def main():
         bench_hashin(args)
     elif args.workload == "warmstart":
         bench_warmstart(args)
+    elif args.workload == "sweep":
+        bench_sweep(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

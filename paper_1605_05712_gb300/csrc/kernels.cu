@@ -212,6 +212,27 @@ __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, co
 struct DF {
   float hi, lo;
 };
+// strain held as a double-float pair (hi, lo) in the 8 bytes of its binary64 slot during a mixed solve
+// (binary32 arithmetic only: GB300 issues binary64 at 1/58 of the binary32 rate)
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float x) {  // (hi, lo) += x
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);  // TwoSum error
+  const float l = lo + e;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+__device__ __forceinline__ float df_diff(float x, float hi, float lo) {  // x - (hi + lo), rounded once
+  const float s = x - hi;
+  const float bb = s - x;
+  const float e = (x - (s - bb)) - (hi + bb);  // TwoDiff error of x - hi
+  return s + (e - lo);
+}
+__device__ __forceinline__ float2 df_of(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
 __device__ __forceinline__ void df_add_sq(DF& acc, float x) {
   const float p = x * x;
   const float pe = fmaf(x, x, -p);           // x*x = p + pe exactly
@@ -288,11 +309,18 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const int npl = Rh / 2 + 1;
 
   if (a.flags & ROW_LOAD_EPS) {
+    const bool eps_df = (sizeof(Real) == 4) || (a.flags & ROW_EPS_DF);
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, n = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
-      const double2 v = *(const double2*)(eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 2u * n));
-      buf[idx] = cmake<C>(v.x, v.y);
+      const double* pe = eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 2u * n);
+      if (eps_df) {
+        const float4 v = *(const float4*)pe;
+        buf[idx] = cmake<C>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      } else {
+        const double2 v = *(const double2*)pe;
+        buf[idx] = cmake<C>(v.x, v.y);
+      }
     }
     __syncthreads();
   } else {
@@ -351,38 +379,64 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     if (update) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
-        double2* pe = (double2*)(eps + (uint32_t)(c * m32) + (uint32_t)g);
-        const double2 old = *pe;
+        double* pe = eps + (uint32_t)(c * m32) + (uint32_t)g;
         if constexpr (sizeof(Real) == 4) {
-          if (incr) {  // T carried the binary32 increment itself: no round trip, residual in double-float
-            *pe = make_double2(old.x + (double)e0[c], old.y + (double)e1[c]);
-            if (c >= D) {
-              df_add_sq(dfs_shear, e0[c]);
-              df_add_sq(dfs_shear, e1[c]);
-            } else {
-              df_add_sq(dfs, e0[c]);
-              df_add_sq(dfs, e1[c]);
-            }
-            continue;
+          // binary32 kernels: the strain is a double-float pair; no binary64 arithmetic
+          float4 o = *(float4*)pe;
+          float d0, d1;
+          if (incr) {  // T carried the increment itself
+            d0 = e0[c];
+            d1 = e1[c];
+            df_acc(o.x, o.y, d0);
+            df_acc(o.z, o.w, d1);
+          } else {     // T carried the new strain
+            d0 = df_diff(e0[c], o.x, o.y);
+            d1 = df_diff(e1[c], o.z, o.w);
+            o = make_float4(e0[c], 0.f, e1[c], 0.f);
           }
-        }
-        double n0 = (double)e0[c], n1 = (double)e1[c];
-        double d0, d1;
-        if (incr) {
-          d0 = n0;
-          d1 = n1;
-          n0 += old.x;
-          n1 += old.y;
+          *(float4*)pe = o;
+          if (c >= D) {
+            df_add_sq(dfs_shear, d0);
+            df_add_sq(dfs_shear, d1);
+          } else {
+            df_add_sq(dfs, d0);
+            df_add_sq(dfs, d1);
+          }
+          if (tau_of_delta) {
+            e0[c] = d0;
+            e1[c] = d1;
+          }
         } else {
-          d0 = n0 - old.x;
-          d1 = n1 - old.y;
-        }
-        const double wgt = (c >= D) ? 2.0 : 1.0;
-        dsum += wgt * (d0 * d0 + d1 * d1);
-        *pe = make_double2(n0, n1);
-        if (tau_of_delta) {
-          e0[c] = (Real)d0;
-          e1[c] = (Real)d1;
+          double2 old;
+          if (a.flags & ROW_EPS_DF) {
+            const float4 o = *(const float4*)pe;
+            old = make_double2((double)o.x + (double)o.y, (double)o.z + (double)o.w);
+          } else {
+            old = *(const double2*)pe;
+          }
+          double n0 = (double)e0[c], n1 = (double)e1[c];
+          double d0, d1;
+          if (incr) {
+            d0 = n0;
+            d1 = n1;
+            n0 += old.x;
+            n1 += old.y;
+          } else {
+            d0 = n0 - old.x;
+            d1 = n1 - old.y;
+          }
+          const double wgt = (c >= D) ? 2.0 : 1.0;
+          dsum += wgt * (d0 * d0 + d1 * d1);
+          if (a.flags & ROW_EPS_DF) {
+            const float2 h0 = df_of(n0), h1 = df_of(n1);
+            *(float4*)pe = make_float4(h0.x, h0.y, h1.x, h1.y);
+          } else {
+            *(double2*)pe = make_double2(n0, n1);
+          }
+          if (tau_of_delta) {
+            e0[c] = (Real)d0;
+            e1[c] = (Real)d1;
+          }
         }
       }
     }
@@ -755,6 +809,21 @@ void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, in
   const int64_t nb = dv.nrows / rpc;
   row_complex_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, in, out, n_f, inverse, scale, rpc);
 }
+// in place: binary64 strain <-> double-float pairs (to_df = 1: before a mixed solve's prologue)
+__global__ void eps_df_kernel(const ItemDev* items, int n_c, int64_t m, int to_df) {
+  double* eps = items[blockIdx.y].eps;
+  const int64_t n = (int64_t)n_c * m;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (to_df) {
+      const double v = eps[i];
+      *(float2*)(eps + i) = df_of(v);
+    } else {
+      const float2 p = *(const float2*)(eps + i);
+      eps[i] = (double)p.x + (double)p.y;
+    }
+  }
+}
+
 __global__ void prep_restart_kernel(ItemScal* scal, GlobScal* glob, int n_items) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int n = 0;
@@ -789,6 +858,11 @@ __global__ void spectrum_to_f32_kernel(const double2* T64, const double2* TN64, 
   }
 }
 
+void launch_eps_df(const ItemDev* items, int n_items, int n_c, int64_t m, int to_df, cudaStream_t st) {
+  int64_t nb = ((int64_t)n_c * m + 255) / 256;
+  if (nb > 2432) nb = 2432;
+  eps_df_kernel<<<dim3((unsigned)nb, n_items), 256, 0, st>>>(items, n_c, m, to_df);
+}
 void launch_prep_restart(ItemScal* scal, GlobScal* glob, int n_items, cudaStream_t st) {
   prep_restart_kernel<<<1, 32, 0, st>>>(scal, glob, n_items);
 }

@@ -11,6 +11,8 @@
                            // start: the prologue mapped k = 0 to 0, so T holds G(E) - E)
 #define ROW_ONLY_PAUSED 32 // restart passes: only items in state ITEM_PAUSED take part
 #define ROW_TAU_DELTA 64   // with ROW_UPDATE: the polarization is taken of the increment eps^(n+1) - eps^(n)
+#define ROW_EPS_DF 128     // binary64 kernels: the strain buffer holds double-float pairs (mixed solve);
+                           // the binary32 kernels always read and write it so
 
 // ItemScal::done
 #define ITEM_ACTIVE 0
@@ -123,6 +125,8 @@ template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
                         int rpc, int nthreads, size_t smem, cudaStream_t st);
 int lat_kernel_attrs(size_t max_smem);
+// in place: binary64 strain -> double-float pairs (to_df = 1) or back (0), all items
+void launch_eps_df(const ItemDev* items, int n_items, int n_c, int64_t m, int to_df, cudaStream_t st);
 // restart of the increment form: glob->active = number of paused items, arrivals = 0
 void launch_prep_restart(ItemScal* scal, GlobScal* glob, int n_items, cudaStream_t st);
 // sets a WHILE node's condition to (glob->active > 0) from inside the graph

@@ -366,6 +366,8 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   CK(cudaMemcpyAsync(glob, &g.glob0, sizeof(GlobScal), cudaMemcpyHostToDevice, st));
   const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
   if (!o.warm_start) launch_fill(ditems, n_items, n_c, m, st);
+  // mixed precision: the strain is held as double-float pairs in its own buffer during the solve
+  if (fp32) launch_eps_df(ditems, n_items, n_c, m, 1, st);
   CK(cudaGetLastError());
   if (P->nax > 0 && maxit > 0) {
     Geometry& geo = g.geo;
@@ -447,10 +449,10 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       r64.TN = ws + wl.TN64;
       r64.it.pause_tol = 0.0;
       g.r_pro = r64;
-      g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | (gamma_in_row ? ROW_GAMMA : 0);
+      g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
       g.r_pro.mat.increment = 0;
       g.r_upd = r64;
-      g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | (gamma_in_row ? ROW_GAMMA : 0);
+      g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
       g.r_upd.mat.increment = 1;
       g.c64 = ca;
       g.c64.T = r64.T;
@@ -478,6 +480,7 @@ int group_plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream
 const int* group_active_flag(const GroupRun& g) { return &g.full.it.glob->active; }
 
 int group_finish(GroupRun& g, cudaStream_t st) {
+  if (g.fp32) launch_eps_df(g.ea.items, g.n_items, g.n_c, g.P->m, 0, st);
   launch_eff(g.dv, g.ea, g.eff_blocks, g.n_items, st);
   CK(cudaGetLastError());
   g.scal.resize((size_t)g.n_items * kScalBytes);
@@ -870,7 +873,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   CK(cudaMemsetAsync(ws + wl.scal, 0, 2 * kScalBytes, st));
   RowArgs ra;
   memset(&ra, 0, sizeof(ra));
-  ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0);
+  ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0) | (fp32 ? ROW_INCREMENT | ROW_INCR_FIRST : 0);
   ra.rpc = geo.rpc;
   ra.items = (const ItemDev*)(ws + wl.items);
   ra.T = ws + wl.T;
@@ -903,6 +906,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   std::vector<cudaEvent_t> ev(2 * nk);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   std::vector<double> acc(nk, 0.0);
+  if (fp32) launch_eps_df(ra.items, 1, n_c, P->m, 1, st);   // as inside a mixed solve
   for (int rep = 0; rep < n_reps; ++rep) {
     int k = 0;
     CK(cudaEventRecord(ev[2 * k], st));
@@ -941,6 +945,8 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
       acc[j] += ms;
     }
   }
+  if (fp32) launch_eps_df(ra.items, 1, n_c, P->m, 0, st);
+  CK(cudaStreamSynchronize(st));
   for (auto& e : ev) cudaEventDestroy(e);
   for (int j = 0; j < 8; ++j) ms_out[j] = j < nk ? (float)(acc[j] / n_reps) : 0.0f;
   if (n_out) *n_out = nk;
