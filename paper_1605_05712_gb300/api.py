@@ -17,7 +17,7 @@ from ._build import LIB
 
 LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
 LAT_ERR_ARG = -1
-LAT_FP64, LAT_MIXED = 0, 1
+LAT_FP64, LAT_MIXED, LAT_DF64 = 0, 1, 2
 LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
 HIST_CAP = 4096
 BATCH_MAX_PHASES = 16
@@ -174,7 +174,7 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
     n_loads = E.shape[0]
     Ea, Ep = _f64(E)
-    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
@@ -217,7 +217,7 @@ def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=2
     stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
     C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
     Ea, Ep = _f64(np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)[0])
-    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     eps = torch.empty((plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
     ws = torch.empty(plan.workspace_bytes(1, prec), dtype=torch.uint8, device=phase.device)
     ms = (ctypes.c_float * 8)()
@@ -249,7 +249,7 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
     n_loads = E.shape[0]
     Ea, Ep = _f64(E)
-    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
@@ -299,7 +299,7 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     dev = phases[0].device
     eps = eps_out if eps_out is not None else torch.empty((n, plan.n_c, plan.m), dtype=torch.float64, device=dev)
     sigma = torch.empty_like(eps) if want_sigma else None
-    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     keep = []
     items = (_BatchItem * n)()
@@ -365,7 +365,7 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     """
     import torch
     n = len(problems)
-    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     items = (_MultiItem * n)()
     keep, outs = [], []
@@ -435,4 +435,4 @@ def multi_workspace_bytes(problems, precision="fp64"):
     L = lib()
     L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
     L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
-    return int(L.lattice_multi_workspace_bytes(items, n, {"fp64": LAT_FP64, "mixed": LAT_MIXED}[precision]))
+    return int(L.lattice_multi_workspace_bytes(items, n, {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]))

@@ -22,13 +22,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 template <typename R> struct cplx_of;
 template <> struct cplx_of<double> { typedef double2 type; };
 template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<dfloat> { typedef dcplx type; };
 
 template <typename C> __device__ __forceinline__ C cmake(double x, double y);
 template <> __device__ __forceinline__ double2 cmake<double2>(double x, double y) { return make_double2(x, y); }
 template <> __device__ __forceinline__ float2 cmake<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+template <> __device__ __forceinline__ dcplx cmake<dcplx>(double x, double y) {
+  dcplx r;
+  r.x = dfloat(x);
+  r.y = dfloat(y);
+  return r;
+}
+// complex from two reals of the kernel's precision (no round trip through binary64)
+template <typename C, typename R> __device__ __forceinline__ C cpair(R x, R y) { C r; r.x = x; r.y = y; return r; }
+
+// read-only loads of complex table entries
+template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
+template <> __device__ __forceinline__ dcplx ldg_c<dcplx>(const dcplx* p) { return ldg_dc(p); }
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -51,7 +66,7 @@ __device__ __forceinline__ uint32_t bitrev(uint32_t p, int log2L) {
 // twiddle W_L^j = exp(-2 pi i j / L) from the table of W_N^t, N = 2^tw_log2 >= L
 template <typename C>
 __device__ __forceinline__ C twid(const C* __restrict__ tw, int tw_log2, int log2L, uint32_t j) {
-  return __ldg(&tw[j << (tw_log2 - log2L)]);
+  return ldg_c(&tw[j << (tw_log2 - log2L)]);
 }
 
 // Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.

@@ -54,6 +54,8 @@ struct lat_plan {
   float2* d_twf;
   double2* d_stw;    // split twiddles: [hi (e >> s) | lo (2^s)]
   float2* d_stwf;
+  float4* d_twdf;     // double-float copies (re hi, re lo, im hi, im lo)
+  float4* d_stwdf;
   int64_t stw_hi_n, stw_lo_n;
   int device;
   // cached solver graph

@@ -14,8 +14,17 @@
 // decides convergence and sets the CUDA-graph WHILE condition.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft_smem.cuh"
 #include "kernels.cuh"
+
+// kernel precisions: binary64, binary32 (mixed), double-float pairs on the binary32 pipes
+template <typename R> constexpr bool is_f32 = std::is_same<R, float>::value;
+template <typename R> constexpr bool is_df = std::is_same<R, dfloat>::value;
+
+template <typename R> __device__ __forceinline__ R ldg_r(const R* p) { return __ldg(p); }
+template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) { return ldg_df(p); }
 
 // ------------------------------------------------------------------ Green operator (Sec. 3.1)
 // Gamma0(h) : tau for isotropic C0 (closed form of grad (grad^H C0 grad)^{-1} grad^H):
@@ -78,14 +87,14 @@ struct GreenK {
 template <typename Real>
 __device__ __forceinline__ GreenK<Real> green_consts(const ItemDev* item, const MatArgs& mt) {
   GreenK<Real> g;
-  if constexpr (sizeof(Real) == 4) {
+  if constexpr (is_f32<Real>) {
     g.c1 = item->c1f;
     g.c2 = item->c2f;
   } else {
-    g.c1 = item->c1;
-    g.c2 = item->c2;
+    g.c1 = Real(item->c1);
+    g.c2 = Real(item->c2);
   }
-  g.sc = (Real)mt.gscale;
+  g.sc = Real(mt.gscale);
   return g;
 }
 
@@ -215,18 +224,16 @@ struct DF {
 // strain held as a double-float pair (hi, lo) in the 8 bytes of its binary64 slot during a mixed solve
 // (binary32 arithmetic only: GB300 issues binary64 at 1/58 of the binary32 rate)
 __device__ __forceinline__ void df_acc(float& hi, float& lo, float x) {  // (hi, lo) += x
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float e = (hi - (s - bb)) + (x - bb);  // TwoSum error
-  const float l = lo + e;
-  hi = s + l;
-  lo = l - (hi - s);
+  float s, e, h, l;
+  two_sum(hi, x, s, e);
+  fast_two_sum(s, __fadd_rn(lo, e), h, l);
+  hi = h;
+  lo = l;
 }
 __device__ __forceinline__ float df_diff(float x, float hi, float lo) {  // x - (hi + lo), rounded once
-  const float s = x - hi;
-  const float bb = s - x;
-  const float e = (x - (s - bb)) - (hi + bb);  // TwoDiff error of x - hi
-  return s + (e - lo);
+  float s, e;
+  two_sum(x, -hi, s, e);
+  return __fadd_rn(s, __fsub_rn(e, lo));
 }
 __device__ __forceinline__ float2 df_of(double v) {
   const float hi = (float)v;
@@ -234,14 +241,11 @@ __device__ __forceinline__ float2 df_of(double v) {
 }
 
 __device__ __forceinline__ void df_add_sq(DF& acc, float x) {
-  const float p = x * x;
-  const float pe = fmaf(x, x, -p);           // x*x = p + pe exactly
-  const float s = acc.hi + p;
-  const float bb = s - acc.hi;
-  const float e = (acc.hi - (s - bb)) + (p - bb);  // TwoSum error of acc.hi + p
-  const float lo = acc.lo + pe + e;
-  acc.hi = s + lo;                           // renormalise
-  acc.lo = lo - (acc.hi - s);
+  const float p = __fmul_rn(x, x);
+  const float pe = __fmaf_rn(x, x, -p);      // x*x = p + pe exactly
+  float s, e;
+  two_sum(acc.hi, p, s, e);
+  fast_two_sum(s, __fadd_rn(__fadd_rn(acc.lo, pe), e), acc.hi, acc.lo);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -309,14 +313,16 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const int npl = Rh / 2 + 1;
 
   if (a.flags & ROW_LOAD_EPS) {
-    const bool eps_df = (sizeof(Real) == 4) || (a.flags & ROW_EPS_DF);
+    const bool eps_df = is_f32<Real> || is_df<Real> || (a.flags & ROW_EPS_DF);
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, n = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
       const double* pe = eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 2u * n);
       if (eps_df) {
         const float4 v = *(const float4*)pe;
-        buf[idx] = cmake<C>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        if constexpr (is_df<Real>) buf[idx] = cpair<C>(dfloat(v.x, v.y), dfloat(v.z, v.w));
+        else if constexpr (is_f32<Real>) buf[idx] = cpair<C>(v.x + v.y, v.z + v.w);
+        else buf[idx] = cmake<C>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
       } else {
         const double2 v = *(const double2*)pe;
         buf[idx] = cmake<C>(v.x, v.y);
@@ -366,6 +372,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   const bool incr = update && (a.flags & ROW_INCREMENT) != 0 &&
                     ((a.flags & ROW_INCR_FIRST) != 0 || *(volatile const int*)&isc->iter > 0);
   DF dfs = {0.f, 0.f}, dfs_shear = {0.f, 0.f};  // m <= 2^28: in-item offsets stay below 2^31
+  dfloat dd_acc(0.f, 0.f), dd_shear(0.f, 0.f);    // residual of the double-float kernels
   for (int idx = tid; idx < rpc * Rh; idx += nthr) {
     const int row = idx >> lgRh, n = idx & (Rh - 1);
     const uint32_t g = (uint32_t)(r0 + row) * (uint32_t)R + 2u * n;
@@ -380,7 +387,33 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         double* pe = eps + (uint32_t)(c * m32) + (uint32_t)g;
-        if constexpr (sizeof(Real) == 4) {
+        if constexpr (is_df<Real>) {
+          // double-float pairs: the strain buffer holds pairs during the solve, binary32 pipes only
+          const float4 o = *(const float4*)pe;
+          const dfloat o0(o.x, o.y), o1(o.z, o.w);
+          dfloat n0 = e0[c], n1 = e1[c], d0, d1;
+          if (incr) {
+            d0 = n0;
+            d1 = n1;
+            n0 = n0 + o0;
+            n1 = n1 + o1;
+          } else {
+            d0 = n0 - o0;
+            d1 = n1 - o1;
+          }
+          if (c >= D) {
+            df_acc_sq(dd_shear, d0);
+            df_acc_sq(dd_shear, d1);
+          } else {
+            df_acc_sq(dd_acc, d0);
+            df_acc_sq(dd_acc, d1);
+          }
+          *(float4*)pe = make_float4(n0.hi, n0.lo, n1.hi, n1.lo);
+          if (tau_of_delta) {
+            e0[c] = d0;
+            e1[c] = d1;
+          }
+        } else if constexpr (is_f32<Real>) {
           // binary32 kernels: the strain is a double-float pair; no binary64 arithmetic
           float4 o = *(float4*)pe;
           float d0, d1;
@@ -442,7 +475,8 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     }
     const uchar2 ph = *(const uchar2*)(phase + g);  // g even
     const Real* Dt;
-    if constexpr (sizeof(Real) == 4) Dt = (const Real*)Dtab_f;
+    if constexpr (is_f32<Real>) Dt = (const Real*)Dtab_f;
+    else if constexpr (is_df<Real>) Dt = (const Real*)item->Dtab_df;
     else Dt = (const Real*)Dtab;
     const Real* D0 = Dt + (int)ph.x * n_c * n_c;
     const Real* D1 = Dt + (int)ph.y * n_c * n_c;
@@ -451,10 +485,10 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
       Real t0 = 0, t1 = 0;
 #pragma unroll
       for (int q = 0; q < n_c; ++q) {
-        t0 += __ldg(D0 + c * n_c + q) * e0[q];
-        t1 += __ldg(D1 + c * n_c + q) * e1[q];
+        t0 += ldg_r(D0 + c * n_c + q) * e0[q];
+        t1 += ldg_r(D1 + c * n_c + q) * e1[q];
       }
-      buf[((size_t)c * rpc + row) * Rh + n] = cmake<C>(t0, t1);
+      buf[((size_t)c * rpc + row) * Rh + n] = cpair<C>(t0, t1);
     }
   }
   __syncthreads();
@@ -465,8 +499,8 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
     C* L = buf + (size_t)line * Rh;
     if (k == 0) {
       const C Z0 = L[0];
-      L[0] = cmake<C>((double)(Z0.x + Z0.y), 0.0);
-      nyq[line] = cmake<C>((double)(Z0.x - Z0.y), 0.0);
+      L[0] = cpair<C>(Z0.x + Z0.y, Real(0));
+      nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
     } else {
       const int kp = Rh - k;
       const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
@@ -518,6 +552,7 @@ __global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
   // convergence; the last item to arrive in this iteration sets the WHILE condition
   double* partials = a.it.partials + item_i * a.it.pstride;
   dsum += ((double)dfs.hi + (double)dfs.lo) + 2.0 * ((double)dfs_shear.hi + (double)dfs_shear.lo);
+  dsum += (double)dd_acc + 2.0 * (double)dd_shear;
   const double bs = block_sum(dsum, red);
   if (tid == 0) {
     partials[blockIdx.x] = bs;
@@ -622,8 +657,8 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   auto split_tw = [&](int64_t j) -> C {
     const C* st = (const C*)dv.stw;
     const int sh = dv.split_lo_log2;
-    const C hi = __ldg(st + (j >> sh));
-    const C lo = __ldg(st + dv.stw_hi_n + (j & ((int64_t(1) << sh) - 1)));
+    const C hi = ldg_c(st + (j >> sh));
+    const C lo = ldg_c(st + dv.stw_hi_n + (j & ((int64_t(1) << sh) - 1)));
     return cmul(hi, lo);
   };
   if (a.has_twiddle && a.mode != COL_INV) {
@@ -801,7 +836,7 @@ void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthrea
   const dim3 grid((unsigned)(a.outer * (a.tiles_main + a.tiles_nyq)), n_items);
   if (a.n_f == 6) col_pass_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
   else if (a.n_f == 3) col_pass_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
-  else col_pass_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
+  else if constexpr (!is_df<Real>) col_pass_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale, int rpc,
@@ -844,17 +879,18 @@ __global__ void spectrum_to_f32_kernel(const double2* T64, const double2* TN64, 
                                        const ItemScal* scal) {
   const int item_i = blockIdx.y;
   if (((const ItemScal*)((const char*)scal + (size_t)item_i * 256))->done != ITEM_ACTIVE) return;
-  const double2* a = T64 + item_i * t_stride;
+  // the restart spectrum holds double-float pairs (re hi, re lo, im hi, im lo)
+  const float4* a = (const float4*)T64 + item_i * t_stride;
   float2* b = T32 + item_i * t_stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < t_elems; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = a[i];
-    b[i] = make_float2((float)v.x, (float)v.y);
+    const float4 v = a[i];
+    b[i] = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
   }
-  const double2* an = TN64 + item_i * tn_stride;
+  const float4* an = (const float4*)TN64 + item_i * tn_stride;
   float2* bn = TN32 + item_i * tn_stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tn_elems; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = an[i];
-    bn[i] = make_float2((float)v.x, (float)v.y);
+    const float4 v = an[i];
+    bn[i] = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
   }
 }
 
@@ -890,8 +926,10 @@ void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cu
 
 template void launch_row_pass<double>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
 template void launch_row_pass<float>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_row_pass<dfloat>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
 template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
+template void launch_col_pass<dfloat>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_row_complex<double>(const LatDev&, const void*, void*, int, int, double, int, int, size_t,
                                          cudaStream_t);
 
@@ -917,6 +955,10 @@ int lat_kernel_attrs(size_t max_smem) {
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 6>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 6>, optin);
   if (e == cudaSuccess) e = set_smem(row_complex_kernel<double>, optin);
   return e == cudaSuccess ? 0 : (int)e;
 }

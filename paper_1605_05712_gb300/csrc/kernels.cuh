@@ -1,5 +1,6 @@
 // kernels.cuh -- argument blocks shared by kernels.cu and the solve drivers.
 #pragma once
+#include "df64.cuh"
 #include "internal.h"
 
 // Row pass flags
@@ -31,6 +32,7 @@ struct ItemDev {
   const uint8_t* phase;  // m phase ids
   const double* Dtab;    // n_phases x n_c x n_c: (C_p - C0) on tensor components
   const float* Dtab_f;   // the same in binary32 (for the binary32 kernels)
+  const dfloat* Dtab_df; // the same as double-float pairs (for the double-float kernels)
   const double* Ctab;    // n_phases x n_c x n_c: C_p on tensor components
   double E[6];           // macroscopic strain, tensor components
   double c1, c2;         // Green operator constants of this item's C0

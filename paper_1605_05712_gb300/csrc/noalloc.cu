@@ -77,8 +77,8 @@ extern "C" int basic_scheme_solve_noalloc(const lat_plan* P, const uint8_t* phas
   // scratch layout: [solve workspace | twiddle table | split twiddle table]
   const Work wl = layout(P, n_loads, o.precision, n_phases, 1);
   int64_t n_tw = 0, n_stw = 0;
-  if (P->nax > 0) lat_host_twiddles(P, fp32, nullptr, nullptr, &n_tw, &n_stw);
-  const size_t es = fp32 ? sizeof(float2) : sizeof(double2);
+  if (P->nax > 0) lat_host_twiddles(P, o.precision, nullptr, nullptr, &n_tw, &n_stw);
+  const size_t es = fp32 ? sizeof(float2) : o.precision == LAT_DF64 ? sizeof(float4) : sizeof(double2);
   const size_t off_tw = up256(wl.total), off_stw = up256(off_tw + n_tw * es);
   const size_t need = up256(off_stw + n_stw * es);
   if (need > (size_t)LAT_NOALLOC_SCRATCH_BYTES)
@@ -93,11 +93,11 @@ extern "C" int basic_scheme_solve_noalloc(const lat_plan* P, const uint8_t* phas
   // this plan's twiddles go into the scratch too (the plan's own device tables are not needed)
   std::vector<char> htw(n_tw * es), hstw(n_stw * es);
   if (P->nax > 0) {
-    lat_host_twiddles(P, fp32, htw.data(), hstw.data(), nullptr, nullptr);
+    lat_host_twiddles(P, o.precision, htw.data(), hstw.data(), nullptr, nullptr);
     CK_NA(cudaMemcpyAsync(ws + off_tw, htw.data(), htw.size(), cudaMemcpyHostToDevice, st));
     if (n_stw) CK_NA(cudaMemcpyAsync(ws + off_stw, hstw.data(), hstw.size(), cudaMemcpyHostToDevice, st));
   }
-  LatDev dv = make_dev(P, fp32);
+  LatDev dv = make_dev(P, o.precision);
   dv.tw = ws + off_tw;
   dv.stw = ws + off_stw;
   std::vector<ItemHost> items;

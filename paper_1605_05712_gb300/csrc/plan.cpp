@@ -303,51 +303,37 @@ static int choose_layout(lat_plan* P) {
   return LAT_OK;
 }
 
+int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t* n_tw, int64_t* n_stw);
+
 int lat_ensure_tables(lat_plan* P) {
   if (P->nax == 0 || P->d_tw) return LAT_OK;
   cudaGetDevice(&P->device);
   int lg = 1;
   for (int i = 0; i < P->nax; ++i) lg = std::max(lg, P->ax[i].log2len);
   P->tw_log2 = lg;
-  const int64_t N = int64_t(1) << lg;
-  std::vector<double2> tw(N);
-  std::vector<float2> twf(N);
-  for (int64_t t = 0; t < N; ++t) {
-    double re, im;
-    twiddle(t, N, &re, &im);
-    tw[t] = make_double2(re, im);
-    twf[t] = make_float2((float)re, (float)im);
-  }
-  cudaError_t err;
-  if ((err = cudaMalloc(&P->d_tw, N * sizeof(double2))) != cudaSuccess ||
-      (err = cudaMalloc(&P->d_twf, N * sizeof(float2))) != cudaSuccess ||
-      (err = cudaMemcpy(P->d_tw, tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(P->d_twf, twf.data(), N * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
-    return lat_fail(LAT_ERR_CUDA, std::string("twiddle upload: ") + cudaGetErrorString(err));
+  int64_t n_tw = 0, n_stw = 0;
+  lat_host_twiddles(P, 0, nullptr, nullptr, &n_tw, &n_stw);
   if (P->split) {
-    const int64_t e = P->split_e;
-    const int s = P->split_lo_log2;
-    P->stw_lo_n = int64_t(1) << s;
-    P->stw_hi_n = e >> s;
-    std::vector<double2> st(P->stw_hi_n + P->stw_lo_n);
-    std::vector<float2> stf(st.size());
-    for (int64_t j = 0; j < P->stw_hi_n; ++j) {
-      double re, im;
-      twiddle(j << s, e, &re, &im);
-      st[j] = make_double2(re, im);
+    P->stw_lo_n = int64_t(1) << P->split_lo_log2;
+    P->stw_hi_n = P->split_e >> P->split_lo_log2;
+  }
+  // binary64, binary32 and double-float copies of both tables
+  void** dst_tw[3] = {(void**)&P->d_tw, (void**)&P->d_twf, (void**)&P->d_twdf};
+  void** dst_stw[3] = {(void**)&P->d_stw, (void**)&P->d_stwf, (void**)&P->d_stwdf};
+  const size_t es[3] = {sizeof(double2), sizeof(float2), sizeof(float4)};
+  for (int k = 0; k < 3; ++k) {
+    std::vector<char> htw(n_tw * es[k]), hstw(std::max<int64_t>(n_stw, 1) * es[k]);
+    lat_host_twiddles(P, k, htw.data(), P->split ? hstw.data() : nullptr, nullptr, nullptr);
+    cudaError_t err;
+    if ((err = cudaMalloc(dst_tw[k], htw.size())) != cudaSuccess ||
+        (err = cudaMemcpy(*dst_tw[k], htw.data(), htw.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return lat_fail(LAT_ERR_CUDA, std::string("twiddle upload: ") + cudaGetErrorString(err));
+    if (P->split && n_stw > 0) {
+      const size_t nb = n_stw * es[k];
+      if ((err = cudaMalloc(dst_stw[k], nb)) != cudaSuccess ||
+          (err = cudaMemcpy(*dst_stw[k], hstw.data(), nb, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return lat_fail(LAT_ERR_CUDA, std::string("split twiddle upload: ") + cudaGetErrorString(err));
     }
-    for (int64_t j = 0; j < P->stw_lo_n; ++j) {
-      double re, im;
-      twiddle(j, e, &re, &im);
-      st[P->stw_hi_n + j] = make_double2(re, im);
-    }
-    for (size_t j = 0; j < st.size(); ++j) stf[j] = make_float2((float)st[j].x, (float)st[j].y);
-    size_t nb = st.size();
-    if ((err = cudaMalloc(&P->d_stw, nb * sizeof(double2))) != cudaSuccess ||
-        (err = cudaMalloc(&P->d_stwf, nb * sizeof(float2))) != cudaSuccess ||
-        (err = cudaMemcpy(P->d_stw, st.data(), nb * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (err = cudaMemcpy(P->d_stwf, stf.data(), nb * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
-      return lat_fail(LAT_ERR_CUDA, std::string("split twiddle upload: ") + cudaGetErrorString(err));
   }
   return LAT_OK;
 }
@@ -411,9 +397,17 @@ int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t*
   }
   if (n_tw) *n_tw = N;
   if (n_stw) *n_stw = hi_n + lo_n;
+  // kind (the fp32 argument): 0 binary64 (double2), 1 binary32 (float2), 2 double-float pairs
+  // (float4: re hi, re lo, im hi, im lo)
   auto put = [&](void* dst, int64_t i, double re, double im) {
-    if (fp32) ((float2*)dst)[i] = make_float2((float)re, (float)im);
-    else ((double2*)dst)[i] = make_double2(re, im);
+    if (fp32 == 1) {
+      ((float2*)dst)[i] = make_float2((float)re, (float)im);
+    } else if (fp32 == 2) {
+      const float rh = (float)re, ih = (float)im;
+      ((float4*)dst)[i] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+    } else {
+      ((double2*)dst)[i] = make_double2(re, im);
+    }
   };
   if (tw)
     for (int64_t t = 0; t < N; ++t) {
@@ -445,6 +439,8 @@ extern "C" void lattice_plan_destroy(lat_plan* P) {
   if (P->d_twf) cudaFree(P->d_twf);
   if (P->d_stw) cudaFree(P->d_stw);
   if (P->d_stwf) cudaFree(P->d_stwf);
+  if (P->d_twdf) cudaFree(P->d_twdf);
+  if (P->d_stwdf) cudaFree(P->d_stwdf);
   delete P;
 }
 

@@ -36,7 +36,7 @@ int ensure_attrs() {
   return rc;
 }
 
-LatDev make_dev(const lat_plan* P, bool fp32) {
+LatDev make_dev(const lat_plan* P, int kind) {
   LatDev dv;
   memset(&dv, 0, sizeof(dv));
   dv.d = P->d;
@@ -71,8 +71,8 @@ LatDev make_dev(const lat_plan* P, bool fp32) {
   dv.split_e = P->split_e;
   dv.stw_hi_n = P->stw_hi_n;
   dv.tw_log2 = P->tw_log2;
-  dv.tw = fp32 ? (const void*)P->d_twf : (const void*)P->d_tw;
-  dv.stw = fp32 ? (const void*)P->d_stwf : (const void*)P->d_stw;
+  dv.tw = kind == LAT_MIXED ? (const void*)P->d_twf : kind == LAT_DF64 ? (const void*)P->d_twdf : (const void*)P->d_tw;
+  dv.stw = kind == LAT_MIXED ? (const void*)P->d_stwf : kind == LAT_DF64 ? (const void*)P->d_stwdf : (const void*)P->d_stw;
   return dv;
 }
 
@@ -126,6 +126,8 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   off = align256(off + (size_t)n_tables * 2 * w.table_bytes);
   w.tables_f = off;
   off = align256(off + (size_t)n_tables * w.table_bytes / 2);
+  w.tables_df = off;   // (C - C0) as double-float pairs: 8 bytes per entry like binary64
+  off = align256(off + (precision != LAT_FP64 ? (size_t)n_tables * w.table_bytes : 0));  // mixed: its restart
   w.partials = off;
   off = align256(off + (size_t)n_items * w.pstride * sizeof(double));
   w.scal = off;
@@ -185,6 +187,7 @@ void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, Col
 }
 template void enqueue_columns<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
 template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
+template void enqueue_columns<dfloat>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
 
 namespace {
 
@@ -227,15 +230,16 @@ int plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream_t st)
   return LAT_OK;
 }
 
-// the binary64 restart of the paused items (mixed precision only); cond2 != 0 sets the condition of
+// the binary64-accurate restart of the paused items (mixed precision only, double-float kernels);
+// cond2 != 0 sets the condition of
 // the loop that follows from the number of resumed items
 int enqueue_restart(const GroupRun& g, unsigned long long cond2, cudaStream_t st) {
   const Work& wl = g.wl;
   ItemScal* scal = (ItemScal*)(g.ws + wl.scal);
   launch_prep_restart(scal, g.full.it.glob, g.n_items, st);
-  launch_row_pass<double>(g.dv64, g.r_pro, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
-  enqueue_columns<double>(g.dv64, g.P, g.geo64, g.c64, g.n_items, st);
-  launch_row_pass<double>(g.dv64, g.r_upd, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
+  launch_row_pass<dfloat>(g.dv64, g.r_pro, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
+  enqueue_columns<dfloat>(g.dv64, g.P, g.geo64, g.c64, g.n_items, st);
+  launch_row_pass<dfloat>(g.dv64, g.r_upd, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
   const int64_t te = (int64_t)g.n_c * (g.P->m / 2), tne = (int64_t)g.n_c * g.P->nrows;
   launch_spectrum_to_f32(g.ws + wl.T64, g.ws + wl.TN64, g.ws + wl.T, g.ws + wl.TN, te, tne, g.full.t_stride,
                          g.full.tn_stride, scal, g.n_items, st);
@@ -250,8 +254,9 @@ int add_group_loops(const GroupRun& g, cudaGraph_t top) {
   cudaGraphConditionalHandle h1;
   CK(cudaGraphConditionalHandleCreate(&h1, top, 1, cudaGraphCondAssignDefault));
   cudaGraphNode_t n1;
-  int rc = g.fp32 ? add_loop_node<float>(g, g.full, top, nullptr, h1, &n1)
-                  : add_loop_node<double>(g, g.full, top, nullptr, h1, &n1);
+  int rc = by_kind(g.kind, [&](auto tag) {
+    return add_loop_node<decltype(tag)>(g, g.full, top, nullptr, h1, &n1);
+  });
   if (rc != LAT_OK || !g.restart) return rc;
   cudaGraphConditionalHandle h2;
   CK(cudaGraphConditionalHandleCreate(&h2, top, 0, cudaGraphCondAssignDefault));
@@ -287,6 +292,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   const int d = P->d, n_c = d * (d + 1) / 2;
   const int64_t m = P->m;
   const bool fp32 = (o.precision == LAT_MIXED);
+  g.kind = o.precision;
   g.P = P;
   g.n_items = n_items;
   g.n_c = n_c;
@@ -339,6 +345,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     v.Ctab = (const double*)(ws + wl.tables + (size_t)(2 * it.table + 1) * wl.table_bytes);
     v.Dtab = (const double*)(ws + wl.tables + (size_t)(2 * it.table) * wl.table_bytes);
     v.Dtab_f = (const float*)(ws + wl.tables_f + (size_t)it.table * wl.table_bytes / 2);
+    v.Dtab_df = (const dfloat*)(ws + wl.tables_df + (size_t)it.table * wl.table_bytes);
     const double lam0 = it.C0[0], mu0 = it.C0[1];
     v.c1 = 0.5 / mu0;
     v.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
@@ -353,12 +360,23 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   g.tabs_f.assign((size_t)n_tables * tstride, 0.0f);
   for (int t = 0; t < n_tables; ++t)
     for (size_t k = 0; k < tstride; ++k) g.tabs_f[(size_t)t * tstride + k] = (float)g.tabs[(size_t)(2 * t) * tstride + k];
+  if (g.kind != LAT_FP64) {
+    g.tabs_df.assign((size_t)n_tables * tstride, make_float2(0.f, 0.f));
+    for (int t = 0; t < n_tables; ++t)
+      for (size_t k = 0; k < tstride; ++k) {
+        const double v = g.tabs[(size_t)(2 * t) * tstride + k];
+        const float hi = (float)v;
+        g.tabs_df[(size_t)t * tstride + k] = make_float2(hi, (float)(v - (double)hi));
+      }
+  }
   g.hdev.swap(hdev);
   g.glob0.arrivals = 0;
   g.glob0.active = n_items;
   // host buffers stay alive in g until the caller synchronizes
   CK(cudaMemcpyAsync(ws + wl.tables, g.tabs.data(), g.tabs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ws + wl.tables_f, g.tabs_f.data(), g.tabs_f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  if (g.kind != LAT_FP64)
+    CK(cudaMemcpyAsync(ws + wl.tables_df, g.tabs_df.data(), g.tabs_df.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ws + wl.items, g.hdev.data(), g.hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
   // device scalars start from zero; the batch starts with every item active
   CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_items * kScalBytes + kScalBytes, st));
@@ -367,7 +385,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
   if (!o.warm_start) launch_fill(ditems, n_items, n_c, m, st);
   // mixed precision: the strain is held as double-float pairs in its own buffer during the solve
-  if (fp32) launch_eps_df(ditems, n_items, n_c, m, 1, st);
+  if (g.kind != LAT_FP64) launch_eps_df(ditems, n_items, n_c, m, 1, st);
   CK(cudaGetLastError());
   if (P->nax > 0 && maxit > 0) {
     Geometry& geo = g.geo;
@@ -423,24 +441,22 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     g.cl = ca;
     g.cl.scal = ra.it.scal;
     g.cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
-    if (fp32) {
-      launch_row_pass<float>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
-      enqueue_columns<float>(dv, P, geo, c0, n_items, st);
-    } else {
-      launch_row_pass<double>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
-      enqueue_columns<double>(dv, P, geo, c0, n_items, st);
-    }
+    by_kind(g.kind, [&](auto tag) {
+      launch_row_pass<decltype(tag)>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+      enqueue_columns<decltype(tag)>(dv, P, geo, c0, n_items, st);
+      return 0;
+    });
     CK(cudaGetLastError());
     g.loop = true;
-    // one binary64 restart when an item's residual first falls below sqrt(tol): the increment
-    // recurrence accumulates binary32 rounding as a standing offset of the fixed point (it never
-    // re-evaluates G(eps)); the restart recomputes the increment exactly, and the iterations after it
-    // contract the offset
+    // one binary64-accurate restart (double-float kernels) when an item's residual first falls below
+    // sqrt(tol): the increment recurrence accumulates binary32 rounding as a standing offset of the
+    // fixed point (it never re-evaluates G(eps)); the restart recomputes the increment exactly, and
+    // the iterations after it contract the offset
     const double pause = sqrt(tol);
     g.restart = incr && o.mixed_restart >= 0 && tol > 0 && pause > tol && maxit > 1;
     if (g.restart) {
       g.full.it.pause_tol = pause;
-      g.dv64 = make_dev(P, false);
+      g.dv64 = make_dev(P, LAT_DF64);   // the restart runs on double-float pairs
       memset(&g.geo64, 0, sizeof(g.geo64));
       if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items)) != LAT_OK) return rc;
       RowArgs r64 = ra;
@@ -474,13 +490,13 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
 
 int group_plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream_t st) {
   if (!g.loop) return LAT_OK;
-  return g.fp32 ? plain_iteration<float>(g, body_row, st) : plain_iteration<double>(g, body_row, st);
+  return by_kind(g.kind, [&](auto tag) { return plain_iteration<decltype(tag)>(g, body_row, st); });
 }
 
 const int* group_active_flag(const GroupRun& g) { return &g.full.it.glob->active; }
 
 int group_finish(GroupRun& g, cudaStream_t st) {
-  if (g.fp32) launch_eps_df(g.ea.items, g.n_items, g.n_c, g.P->m, 0, st);
+  if (g.kind != LAT_FP64) launch_eps_df(g.ea.items, g.n_items, g.n_c, g.P->m, 0, st);
   launch_eff(g.dv, g.ea, g.eff_blocks, g.n_items, st);
   CK(cudaGetLastError());
   g.scal.resize((size_t)g.n_items * kScalBytes);
@@ -607,7 +623,8 @@ int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::
 
 int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts& o) {
   if (maxit < 0 || !(tol >= 0)) return lat_fail(LAT_ERR_ARG, "bad maxit/tol");
-  if (o.precision != LAT_FP64 && o.precision != LAT_MIXED) return lat_fail(LAT_ERR_ARG, "bad precision");
+  if (o.precision != LAT_FP64 && o.precision != LAT_MIXED && o.precision != LAT_DF64)
+    return lat_fail(LAT_ERR_ARG, "bad precision");
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
   return check_geometry(P, o.precision);
 }
@@ -687,7 +704,7 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   std::vector<ItemHost> items;
   load_case_items(P, phase, C0, E, n_loads, eps, sigma, items);
-  const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
+  const LatDev dv = make_dev(P, o.precision);
   return run_batch(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar,
                    iters, resid, (cudaStream_t)stream);
 }
@@ -726,7 +743,7 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
-  const LatDev dv = make_dev(P, o.precision == LAT_MIXED);
+  const LatDev dv = make_dev(P, o.precision);
   return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar, iters, resid,
                    (cudaStream_t)stream);
 }
@@ -820,7 +837,7 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
       nph.push_back(b.n_phases);
     }
     const Work wl = layout(g.P, g.n_loads, o.precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size());
-    const LatDev dv = make_dev(g.P, o.precision == LAT_MIXED);
+    const LatDev dv = make_dev(g.P, o.precision);
     if (int rc = group_prepare(g.P, its, stiff, nph, tol, maxit, o, ws + off, wl, dv, runs[k], st)) return rc;
     off += align256(wl.total);
   }
@@ -865,7 +882,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   const Work wl = layout(P, 1, precision, kMaxPhases, 1);
   char* ws = (char*)workspace;
   const bool fp32 = (precision == LAT_MIXED);
-  const LatDev dv = make_dev(P, fp32);
+  const LatDev dv = make_dev(P, precision);
   Geometry geo;
   memset(&geo, 0, sizeof(geo));
   if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, 1)) != LAT_OK) return rc;
@@ -906,12 +923,14 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   std::vector<cudaEvent_t> ev(2 * nk);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   std::vector<double> acc(nk, 0.0);
-  if (fp32) launch_eps_df(ra.items, 1, n_c, P->m, 1, st);   // as inside a mixed solve
+  if (precision != LAT_FP64) launch_eps_df(ra.items, 1, n_c, P->m, 1, st);   // as inside the solve
   for (int rep = 0; rep < n_reps; ++rep) {
     int k = 0;
     CK(cudaEventRecord(ev[2 * k], st));
-    if (fp32) launch_row_pass<float>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
-    else launch_row_pass<double>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
+    by_kind(precision, [&](auto tag) {
+      launch_row_pass<decltype(tag)>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
+      return 0;
+    });
     CK(cudaEventRecord(ev[2 * k + 1], st));
     ++k;
     auto one = [&](int gi, int mode) {
@@ -930,8 +949,10 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
       c.tiles_main = geo.tiles_main[gi];
       c.tiles_nyq = geo.tiles_nyq[gi];
       cudaEventRecord(ev[2 * k], st);
-      if (fp32) launch_col_pass<float>(dv, c, 1, kThreads, geo.col_smem[gi], st);
-      else launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[gi], st);
+      by_kind(precision, [&](auto tag) {
+        launch_col_pass<decltype(tag)>(dv, c, 1, kThreads, geo.col_smem[gi], st);
+        return 0;
+      });
       cudaEventRecord(ev[2 * k + 1], st);
       ++k;
     };
@@ -945,7 +966,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
       acc[j] += ms;
     }
   }
-  if (fp32) launch_eps_df(ra.items, 1, n_c, P->m, 0, st);
+  if (precision != LAT_FP64) launch_eps_df(ra.items, 1, n_c, P->m, 0, st);
   CK(cudaStreamSynchronize(st));
   for (auto& e : ev) cudaEventDestroy(e);
   for (int j = 0; j < 8; ++j) ms_out[j] = j < nk ? (float)(acc[j] / n_reps) : 0.0f;
@@ -967,7 +988,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
   }
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
-  const LatDev dv = make_dev(P, false);
+  const LatDev dv = make_dev(P, LAT_FP64);
   Geometry geo;
   int rc = geometry(P, 1, 16, P->Rlen, false, geo, 1);
   if (rc != LAT_OK) return rc;

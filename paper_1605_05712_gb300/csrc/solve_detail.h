@@ -26,7 +26,7 @@ struct Geometry {
 
 // byte offsets of the workspace regions of a batched solve
 struct Work {
-  size_t T, TN, items, tables, tables_f, partials, scal, hist, total;
+  size_t T, TN, items, tables, tables_f, tables_df, partials, scal, hist, total;
   size_t T64, TN64;   // mixed precision: binary64 spectrum of the restart (0 bytes otherwise)
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
@@ -43,7 +43,15 @@ struct ItemHost {
 };
 
 int ensure_attrs();
-LatDev make_dev(const lat_plan* P, bool fp32);
+// kind = the precision: LAT_FP64, LAT_MIXED (binary32 kernels) or LAT_DF64 (double-float kernels)
+LatDev make_dev(const lat_plan* P, int kind);
+// calls f(Real{}) with the kernel type of a precision
+template <typename F>
+int by_kind(int kind, F f) {
+  if (kind == LAT_MIXED) return f(float{});
+  if (kind == LAT_DF64) return f(dfloat{});
+  return f(double{});
+}
 int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items);
 Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables);
 void voigt_to_tc(const double* V, int d, double* out);
@@ -60,14 +68,15 @@ struct GroupRun {
   const lat_plan* P;
   int n_items, n_c, maxit;
   double tol;
+  int kind;           // LAT_FP64, LAT_MIXED or LAT_DF64
   bool fp32, loop, want_hist;
   LatDev dv;
   Geometry geo;
   RowArgs full;       // loop body row pass (with the pause level when a restart follows)
   ColArgs cl;
-  // binary64 restart of the increment form: prologue of the paused items (r_pro, c64), binary64
-  // update whose polarization is of the exact increment (r_upd), cast of the spectrum, binary32
-  // columns (cl), then the second loop (full2)
+  // restart of the increment form on double-float pairs (binary64-accurate): prologue of the paused
+  // items (r_pro, c64), update whose polarization is of the exact increment (r_upd), cast of the
+  // spectrum to binary32, binary32 columns (cl), then the second loop (full2)
   bool restart;
   LatDev dv64;
   Geometry geo64;
@@ -80,6 +89,7 @@ struct GroupRun {
   GlobScal glob0;
   std::vector<double> tabs;     // host staging, alive until the stream is synchronized
   std::vector<float> tabs_f;
+  std::vector<float2> tabs_df;
   std::vector<ItemDev> hdev;
   std::vector<char> scal;       // host copy of the item scalars after the solve
   std::vector<double> hist;
