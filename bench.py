@@ -134,21 +134,23 @@ PLAIN_LAUNCHES = False   # --plain-launches: iterate with plain launches instead
 
 def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
     """One pass of the workload.  fp64_separate: each load case its own solve (the configured
-    form); fp64_batched / mixed_batched: the three load cases of a lattice in one batched solve."""
+    form); *_batched: the three load cases of a lattice in one batched solve; df64 = the binary64-accurate
+    double-float kernels."""
     from paper_1605_05712_gb300 import basic_scheme_solve
     tot = 0
     iters = []
     for w in work:
-        if mode == "fp64_separate":
+        prec = mode.split("_")[0]                       # fp64, df64 or mixed
+        if mode.endswith("_separate"):
             its = []
             for lc in range(E.shape[0]):
                 g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E[lc:lc + 1], tol=tol, maxit=MAXIT,
-                                       workspace=ws, eps_out=eps[lc:lc + 1], plain_launches=PLAIN_LAUNCHES)
+                                       workspace=ws, eps_out=eps[lc:lc + 1], precision=prec,
+                                       plain_launches=PLAIN_LAUNCHES)
                 its.append(int(g["iters"][0]))
         else:
             g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
-                                   eps_out=eps, precision="mixed" if mode.startswith("mixed") else "fp64",
-                                   plain_launches=PLAIN_LAUNCHES)
+                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES)
             its = [int(x) for x in g["iters"]]
         iters.append(its)
         tot += w["plan"].m * int(np.sum(its))
@@ -214,7 +216,7 @@ def bench_gpu(args):
     E = load_cases()
     work = setup(dev)
     m = work[0]["plan"].m
-    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1)), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1, 2)), dtype=torch.uint8, device=dev)
     eps = torch.empty((3, 3, m), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
@@ -247,12 +249,12 @@ def bench_gpu(args):
     # variants on the same inputs: batched load cases (binary64, mixed) and time to a 1e-6 residual
     variants = {}
     if not args.no_variants:
-        for mode in ("fp64_batched", "mixed_batched"):
+        for mode in ("df64_separate", "fp64_batched", "df64_batched", "mixed_batched"):
             run_step(work, stiff, C0, E, ws, eps, mode)
             ms_v, u_v, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode), args.steps, flush, st)
             variants[mode] = {"value": round(u_v / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 4), "iterations": it_v}
         ttt = {}
-        for mode in ("fp64_separate", "fp64_batched", "mixed_batched"):
+        for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched"):
             run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6)
             ms_v, _, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6), args.steps, flush, st)
             ttt[mode] = {"ms": round(ms_v, 4), "iterations": it_v}
@@ -262,6 +264,7 @@ def bench_gpu(args):
     w = work[2]
     P = w["plan"]
     pt = lattice_pass_times(P, w["phase"], stiff, C0, E[0], n_reps=50)
+    pt_df = lattice_pass_times(P, w["phase"], stiff, C0, E[0], precision="df64", n_reps=50)
     model = {"m": P.m, "R": 512, "Rh": 256, "groups": [512]}   # the planner's decomposition of all three lattices
     bytes_row, bytes_col = algorithmic_bytes(model)
     flops_row, flops_col = row_col_flops(model)
@@ -278,7 +281,9 @@ def bench_gpu(args):
                            "FMA-loop probe measured 1.19)",
             "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
             "hbm_achieved_gbs": round(by / (ms_dom * 1e-3) / 1e9, 1),
-            "hbm_peak_gbs": pk.get("hbm_gbs"), "per_kernel_ms": [round(x, 5) for x in pt]}
+            "hbm_peak_gbs": pk.get("hbm_gbs"), "per_kernel_ms": [round(x, 5) for x in pt],
+            "df64_per_kernel_ms": [round(x, 5) for x in pt_df],
+            "df64_achieved_fp64_equiv_tflops": round(fl / (pt_df[dom] * 1e-3) / 1e12, 4)}
     gpu_launches = 0
     for it in iters:
         for n in it:   # per solve: fill, prologue (row + column), n loop iterations, effective stress
@@ -334,8 +339,9 @@ def bench_hashin(args):
                                                             R=w["R"])).to(dev)
         eps = torch.empty((6, 6, P.m), dtype=torch.float64, device=dev)
         res = {}
-        for prec in ("mixed", "fp64"):
-            ws = torch.empty(P.workspace_bytes(6, 1 if prec == "mixed" else 0), dtype=torch.uint8, device=dev)
+        for prec in ("mixed", "df64", "fp64"):
+            ws = torch.empty(P.workspace_bytes(6, {"fp64": 0, "mixed": 1, "df64": 2}[prec]), dtype=torch.uint8,
+                             device=dev)
             run = lambda: basic_scheme_solve(P, ph, w["stiffness"], w["C0"], E, tol=1e-6, maxit=2000,
                                              precision=prec, workspace=ws, eps_out=eps)
             for _ in range(args.warmup if prec == "mixed" else 1):
@@ -357,7 +363,8 @@ def bench_hashin(args):
             del ws
         sb_m, sb_d = np.array(res["mixed"]["sigma_bar"]), np.array(res["fp64"]["sigma_bar"])
         res["mixed_vs_fp64_ceff_rel"] = float(np.abs(sb_m - sb_d).max() / np.abs(sb_d).max())
-        for prec in ("mixed", "fp64"):
+        res["df64_vs_fp64_ceff_rel"] = float(np.abs(np.array(res["df64"]["sigma_bar"]) - sb_d).max() / np.abs(sb_d).max())
+        for prec in ("mixed", "df64", "fp64"):
             res[prec].pop("sigma_bar")
         out[name] = res
     print(json.dumps({"workload": "hashin3d (config 3): coated ellipsoid c=(0.1,0.15,0.2), fraction 0.25, "

@@ -361,6 +361,25 @@ int lattice_start_filter(double* out, const double* eps_g2, const double* eps0, 
                          void* stream);
 
 /*
+ * lattice_autotune -- pick the launch shapes of a solve on this plan by timing them on the device
+ * (not in the paper): the rows per block of the row pass and the tile width of every column pass,
+ * one kernel at a time, each candidate over 5 iterations of a homogeneous test problem with n_items
+ * items (load cases x problems).  The fastest are kept in the plan for solves of this precision
+ * whose item count falls in the same power-of-two bucket (1, 2-3, 4-7, ..., >= 128); they change
+ * how lines are grouped into blocks, never the arithmetic of a line, so the fields are the same.
+ *   workspace  device, >= lattice_autotune_workspace_bytes(plan, n_items, precision)
+ * Synchronizes `stream`.  Not thread-safe with solves on the same plan.
+ */
+size_t lattice_autotune_workspace_bytes(const lat_plan* plan, int n_items, int precision);
+int lattice_autotune(lat_plan* plan, int n_items, int precision, void* workspace, size_t workspace_bytes,
+                     void* stream);
+/* the tuned shapes of a bucket: returns 1 and fills rpc, w[n_groups] and ms[1 + n_groups] (device
+ * times of the row pass and of each column group) if the bucket is tuned, else 0; n_groups is always
+ * set (w and ms need 3 and 4 entries: a plan has at most 3 column groups) */
+int lattice_tune_info(const lat_plan* plan, int n_items, int precision, int* rpc, int* w, float* ms,
+                      int* n_groups);
+
+/*
  * lattice_pass_times -- profiling helper: average device time of each kernel
  * of one Basic Scheme iteration (no counterpart in the paper; it measures
  * the passes the solve above runs inside its CUDA graph).  Runs the

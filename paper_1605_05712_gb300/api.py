@@ -137,6 +137,41 @@ class LatticePlan:
     def workspace_bytes(self, n_loads=1, precision=LAT_FP64):
         return int(lib().lattice_workspace_bytes(self._h, n_loads, precision))
 
+    def autotune(self, n_items=1, precision="fp64", stream=None):
+        """Time the launch shapes of a solve with n_items items and keep the fastest in the plan
+        (lattice_autotune).  Returns tune_info(n_items, precision)."""
+        import torch
+        prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+        L = lib()
+        L.lattice_autotune_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.lattice_autotune_workspace_bytes.restype = ctypes.c_size_t
+        nb = int(L.lattice_autotune_workspace_bytes(self._h, n_items, prec))
+        if nb == 0:
+            raise LatticeError(LAT_ERR_ARG, "lattice_autotune_workspace_bytes: unsupported plan or arguments")
+        ws = torch.empty(nb, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+        L.lattice_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_void_p]
+        L.lattice_autotune.restype = ctypes.c_int
+        _check(L.lattice_autotune(self._h, n_items, prec, ctypes.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+        return self.tune_info(n_items, precision)
+
+    def tune_info(self, n_items=1, precision="fp64"):
+        """dict(rpc, w, ms) of the tuned bucket, or None if it is not tuned."""
+        prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+        rpc = ctypes.c_int(0)
+        ng = ctypes.c_int(0)
+        w = (ctypes.c_int * 3)()
+        ms = (ctypes.c_float * 4)()
+        L = lib()
+        L.lattice_tune_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int)]
+        L.lattice_tune_info.restype = ctypes.c_int
+        r = _check(L.lattice_tune_info(self._h, n_items, prec, ctypes.byref(rpc), w, ms, ctypes.byref(ng)))
+        if r == 0:
+            return None
+        return dict(rpc=rpc.value, w=[w[k] for k in range(ng.value)], ms=[ms[k] for k in range(1 + ng.value)])
+
 
 def lattice_plan(M):
     return LatticePlan(M)

@@ -58,6 +58,13 @@ struct lat_plan {
   float4* d_stwdf;
   int64_t stw_hi_n, stw_lo_n;
   int device;
+  // launch shapes picked by lattice_autotune, per precision and power-of-two bucket of the item count
+  struct Tune {
+    int valid;
+    int rpc;                     // rows per block of the row pass
+    int w[LAT_MAX_GROUPS];       // tile width (columns) of each column pass
+    float ms[1 + LAT_MAX_GROUPS];  // their measured device times (ms)
+  } tune[3][8];
   // cached solver graph
   void* graph_cache;
 };

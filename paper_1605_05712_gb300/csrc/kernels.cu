@@ -278,8 +278,15 @@ __device__ double ordered_sum(const double* p, int n) {
 
 // ------------------------------------------------------------------ row pass
 // grid: (row blocks, items); one block = rpc rows x n_c components of one item
+// resident blocks of 256 threads per SM the register budget is cut for: binary32 4 (64 registers;
+// the pass is latency-bound and ran 18 % faster at 128^3 than with 80 registers and 3 blocks); the
+// others keep the budgets the compiler picks on its own (binary64 2-D 64, pairs 2-D 80, 3-D 128)
 template <typename Real, int NC>
-__global__ void __launch_bounds__(256) row_pass_kernel(LatDev dv, RowArgs a) {
+constexpr int row_min_blocks() {
+  return is_f32<Real> ? 4 : (NC == 6 ? 2 : (is_df<Real> ? 3 : 4));
+}
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_kernel(LatDev dv, RowArgs a) {
   typedef typename cplx_of<Real>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;

@@ -76,33 +76,68 @@ LatDev make_dev(const lat_plan* P, int kind) {
   return dv;
 }
 
-// row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile; n_items blocks in grid.y
-int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items) {
+int tune_bucket(int n_items) {
+  int b = 0;
+  while (b < 7 && (2 << b) <= n_items) ++b;
+  return b;
+}
+
+size_t row_smem_bytes(const lat_plan* P, int n_f, size_t cs, bool nyq, int rpc) {
+  const int row_len = nyq ? P->Rh : P->Rlen;
+  return ((size_t)n_f * rpc * row_len + (nyq ? (size_t)n_f * rpc : 0)) * cs + 32 * sizeof(double);
+}
+size_t col_smem_bytes(const lat_plan* P, int n_f, size_t cs, int k, int64_t w) {
+  return (size_t)n_f * P->grp[k].G * w * cs;
+}
+
+int geometry_set_rpc(const lat_plan* P, int n_f, size_t cs, bool nyq, int rpc, Geometry& g) {
+  if (rpc < 1 || P->nrows % rpc != 0) return lat_fail(LAT_ERR_ARG, "rows per block must divide the row count");
+  const size_t sm = row_smem_bytes(P, n_f, cs, nyq, rpc);
+  if (sm > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
+  g.rpc = rpc;
+  g.row_blocks = (int)(P->nrows / rpc);
+  g.row_smem = sm;
+  return LAT_OK;
+}
+int geometry_set_w(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, int k, int64_t w, Geometry& g) {
+  const LatGroup& G = P->grp[k];
+  const int64_t ic = G.inner * row_slots;
+  if (w < 1 || (w & (w - 1)) != 0 || w > ic) return lat_fail(LAT_ERR_ARG, "tile width must be a power of two <= the columns");
+  if (col_smem_bytes(P, n_f, cs, k, w) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column group does not fit in shared memory");
+  const int64_t wN = std::min<int64_t>(w, G.inner);
+  g.w[k] = (int)w;
+  g.wN[k] = (int)wN;
+  g.tiles_main[k] = ic / w;
+  g.tiles_nyq[k] = nyq ? G.inner / wN : 0;
+  g.col_smem[k] = col_smem_bytes(P, n_f, cs, k, w);
+  return LAT_OK;
+}
+
+// row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile; n_items blocks in grid.y;
+// kind >= 0: a solve of that precision, which takes the plan's autotuned shapes when it has them
+int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items, int kind) {
   const int nsm = num_sms();
   const int64_t nrows = P->nrows;
-  const int row_len = nyq ? P->Rh : P->Rlen;
-  auto rsm = [&](int rpc) {
-    return ((size_t)n_f * rpc * row_len + (nyq ? (size_t)n_f * rpc : 0)) * cs + 32 * sizeof(double);
-  };
   int rpc = 1;
-  while (nrows % (2 * rpc) == 0 && rsm(2 * rpc) <= kRowSmemTarget && n_items * (nrows / (2 * rpc)) >= 2 * nsm) rpc *= 2;
-  g.rpc = rpc;
-  g.row_blocks = (int)(nrows / rpc);
-  g.row_smem = rsm(rpc);
-  if (g.row_smem > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
+  while (nrows % (2 * rpc) == 0 && row_smem_bytes(P, n_f, cs, nyq, 2 * rpc) <= kRowSmemTarget &&
+         n_items * (nrows / (2 * rpc)) >= 2 * nsm)
+    rpc *= 2;
+  if (int rc = geometry_set_rpc(P, n_f, cs, nyq, rpc, g)) return rc;
   for (int k = 0; k < P->ngroups; ++k) {
     const LatGroup& G = P->grp[k];
     const int64_t ic = G.inner * row_slots;
     int64_t w = std::min<int64_t>(32, ic);
-    auto csm = [&](int64_t ww) { return (size_t)n_f * G.G * ww * cs; };
-    while (w > 1 && (csm(w) > kColSmemMax || n_items * G.outer * (ic / w) < 2 * nsm)) w /= 2;
-    if (csm(w) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column group does not fit in shared memory");
-    const int64_t wN = std::min<int64_t>(w, G.inner);
-    g.w[k] = (int)w;
-    g.wN[k] = (int)wN;
-    g.tiles_main[k] = ic / w;
-    g.tiles_nyq[k] = nyq ? G.inner / wN : 0;
-    g.col_smem[k] = csm(w);
+    while (w > 1 && (col_smem_bytes(P, n_f, cs, k, w) > kColSmemMax || n_items * G.outer * (ic / w) < 2 * nsm)) w /= 2;
+    if (int rc = geometry_set_w(P, n_f, cs, row_slots, nyq, k, w, g)) return rc;
+  }
+  if (kind >= 0 && kind < 3 && nyq) {
+    const lat_plan::Tune& t = P->tune[kind][tune_bucket(n_items)];
+    if (t.valid) {
+      Geometry tg = g;
+      bool ok = geometry_set_rpc(P, n_f, cs, nyq, t.rpc, tg) == LAT_OK;
+      for (int k = 0; ok && k < P->ngroups; ++k) ok = geometry_set_w(P, n_f, cs, row_slots, nyq, k, t.w[k], tg) == LAT_OK;
+      if (ok) g = tg;
+    }
   }
   return LAT_OK;
 }
@@ -162,32 +197,37 @@ void voigt_to_tc(const double* V, int d, double* out) {
   } while (0)
 
 template <typename Real>
+void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs c, int k, int mode,
+                       int n_items, cudaStream_t st) {
+  const LatGroup& G = P->grp[k];
+  c.mode = mode;
+  c.gidx = k;
+  c.a0 = G.a0;
+  c.a1 = G.a1;
+  c.G = G.G;
+  c.outer = G.outer;
+  c.inner = G.inner;
+  c.has_twiddle = G.has_twiddle;
+  c.w = g.w[k];
+  c.wN = g.wN[k];
+  c.tiles_main = g.tiles_main[k];
+  c.tiles_nyq = g.tiles_nyq[k];
+  launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
+}
+
+template <typename Real>
 void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,
                      cudaStream_t st) {
   // forward over mid groups (innermost first), Gamma group, inverse mid groups
-  auto one = [&](int k, int mode) {
-    ColArgs c = base;
-    const LatGroup& G = P->grp[k];
-    c.mode = mode;
-    c.gidx = k;
-    c.a0 = G.a0;
-    c.a1 = G.a1;
-    c.G = G.G;
-    c.outer = G.outer;
-    c.inner = G.inner;
-    c.has_twiddle = G.has_twiddle;
-    c.w = g.w[k];
-    c.wN = g.wN[k];
-    c.tiles_main = g.tiles_main[k];
-    c.tiles_nyq = g.tiles_nyq[k];
-    launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
-  };
-  for (int k = P->ngroups - 1; k >= 0; --k) one(k, k == 0 ? COL_GAMMA : COL_FWD);
-  for (int k = 1; k < P->ngroups; ++k) one(k, COL_INV);
+  for (int k = P->ngroups - 1; k >= 0; --k) enqueue_col_group<Real>(dv, P, g, base, k, k == 0 ? COL_GAMMA : COL_FWD, n_items, st);
+  for (int k = 1; k < P->ngroups; ++k) enqueue_col_group<Real>(dv, P, g, base, k, COL_INV, n_items, st);
 }
 template void enqueue_columns<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
 template void enqueue_columns<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
 template void enqueue_columns<dfloat>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, cudaStream_t);
+template void enqueue_col_group<double>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, int, int, cudaStream_t);
+template void enqueue_col_group<float>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, int, int, cudaStream_t);
+template void enqueue_col_group<dfloat>(const LatDev&, const lat_plan*, const Geometry&, ColArgs, int, int, int, cudaStream_t);
 
 namespace {
 
@@ -390,7 +430,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   if (P->nax > 0 && maxit > 0) {
     Geometry& geo = g.geo;
     memset(&geo, 0, sizeof(geo));
-    int rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, n_items);
+    int rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, n_items, g.kind);
     if (rc != LAT_OK) return rc;
     RowArgs ra;
     memset(&ra, 0, sizeof(ra));
@@ -458,7 +498,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       g.full.it.pause_tol = pause;
       g.dv64 = make_dev(P, LAT_DF64);   // the restart runs on double-float pairs
       memset(&g.geo64, 0, sizeof(g.geo64));
-      if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items)) != LAT_OK) return rc;
+      if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items, LAT_DF64)) != LAT_OK) return rc;
       RowArgs r64 = ra;
       r64.rpc = g.geo64.rpc;
       r64.T = ws + wl.T64;
@@ -885,7 +925,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   const LatDev dv = make_dev(P, precision);
   Geometry geo;
   memset(&geo, 0, sizeof(geo));
-  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, 1)) != LAT_OK) return rc;
+  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, 1, precision)) != LAT_OK) return rc;
   // keep the item active for every timed launch: maxit far away, tol 0
   CK(cudaMemsetAsync(ws + wl.scal, 0, 2 * kScalBytes, st));
   RowArgs ra;

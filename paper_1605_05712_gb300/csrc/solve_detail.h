@@ -52,7 +52,14 @@ int by_kind(int kind, F f) {
   if (kind == LAT_DF64) return f(dfloat{});
   return f(double{});
 }
-int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items);
+int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items, int kind = -1);
+int geometry_set_rpc(const lat_plan* P, int n_f, size_t cs, bool nyq, int rpc, Geometry& g);
+int geometry_set_w(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, int k, int64_t w, Geometry& g);
+int tune_bucket(int n_items);
+size_t align256(size_t x);
+template <typename Real>
+void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs c, int k, int mode,
+                       int n_items, cudaStream_t st);
 Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables);
 void voigt_to_tc(const double* V, int d, double* out);
 template <typename Real>

@@ -405,3 +405,24 @@ def test_plain_launches_equal_graph_loop(cuda):
         assert np.array_equal(a["iters"], b["iters"])
         assert torch.equal(a["eps"], b["eps"])
         assert np.array_equal(a["sigma_bar"], b["sigma_bar"])
+
+
+@pytest.mark.parametrize("M,prec", [([[512, 16], [0, 512]], "fp64"), ([[512, 16], [0, 512]], "df64"),
+                                    ([[64, 0, 0], [0, 64, 0], [0, 0, 64]], "mixed"),
+                                    ([[128, 1, 0], [0, 128, 1], [0, 0, 64]], "mixed")])
+def test_autotuned_shapes_give_the_same_fields(cuda, M, prec):
+    # the tuner regroups lines into blocks; every line's arithmetic is unchanged, so the fields are equal
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan(M)
+    d = len(M)
+    ph = torch.from_numpy(inclusions(3, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+    E = np.eye(P.n_c)[:2]
+    a = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=6, precision=prec)
+    assert P.tune_info(2, prec) is None
+    info = P.autotune(2, prec)
+    assert info is not None and info["rpc"] >= 1 and len(info["w"]) == len(info["ms"]) - 1
+    b = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=6, precision=prec)
+    assert torch.equal(a["eps"], b["eps"])
+    c = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec)
+    assert c["status"] == 0
