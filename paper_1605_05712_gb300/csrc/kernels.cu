@@ -248,6 +248,22 @@ __device__ __forceinline__ void df_add_sq(DF& acc, float x) {
   fast_two_sum(s, __fadd_rn(__fadd_rn(acc.lo, pe), e), acc.hi, acc.lo);
 }
 
+// ------------------------------------------------------------------ asynchronous tile loads
+// global -> shared copies that bypass registers (cp.async, sm_80 and later), so that a thread has all
+// its tile elements in flight at once; cp.async.wait_all then waits for this thread's copies, and a
+// __syncthreads() after it publishes the tile.  Both addresses are aligned to the element size.
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* dst, const C* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+  } else {
+    static_assert(sizeof(C) == 8, "complex element of 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -340,12 +356,13 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, pos = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
-      buf[idx] = T[(uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos];
+      cp_async_elem(buf + idx, T + ((uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos));
     }
     for (int idx = tid; idx < nlines; idx += nthr) {
       const int c = idx >> lgrpc, row = idx & (rpc - 1);
-      nyq[idx] = TN[c * nrows + r0 + row];
+      cp_async_elem(nyq + idx, TN + (c * nrows + r0 + row));
     }
+    cp_async_wait_all();
     __syncthreads();
     // half spectrum X[0..Rh] -> Z = E + i O (inverse of the R2C post-processing), in place
     for (int idx = tid; idx < nlines * npl; idx += nthr) {
@@ -645,8 +662,10 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     const int col = idx & (w - 1);
     const int g = (idx >> lgw) & (G - 1);
     const int f = idx >> (lgw + lgG);
-    s[idx] = (col < wv) ? src[(uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col] : cmake<C>(0.0, 0.0);
+    if (col < wv) cp_async_elem(s + idx, src + ((uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col));
+    else s[idx] = cmake<C>(0.0, 0.0);
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // four-step twiddle W_e^{n1 k2} (k2 = row frequency of this column)
