@@ -200,6 +200,20 @@ def profiled_traffic(kernel_tag):
     return None
 
 
+def aggregate_ranks(ms_list, units_list, world, device):
+    """Replicas: every rank ran the same workload on its own GPU.  The job's time is the slowest rank's
+    (all-reduce MAX of each time), its throughput all ranks' units over that time.  Returns
+    (times_ms, values)."""
+    import torch
+    import torch.distributed as dist
+    ms = [float(x) for x in ms_list]
+    if world > 1:
+        t = torch.tensor(ms, dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = [float(x) for x in t.tolist()]
+    return ms, [world * u / (m / 1e3) for u, m in zip(units_list, ms)]
+
+
 def bench_gpu(args):
     import torch
     import torch.distributed as dist
@@ -239,12 +253,7 @@ def bench_gpu(args):
         return u, it
     ms_e2e, e2e_units, _ = timed(e2e_step, args.steps, flush, st)
     clocks = clk.stop()
-    if world > 1:
-        t = torch.tensor([ms_step, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_e2e = float(t[0]), float(t[1])
-    value = world * units / (ms_step / 1e3)
-    e2e_value = world * e2e_units / (ms_e2e / 1e3)
+    (ms_step, ms_e2e), (value, e2e_value) = aggregate_ranks([ms_step, ms_e2e], [units, e2e_units], world, dev)
 
     # variants on the same inputs: batched load cases (binary64, mixed) and time to a 1e-6 residual
     variants = {}
