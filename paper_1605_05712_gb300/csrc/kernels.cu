@@ -294,6 +294,20 @@ __device__ double ordered_sum(const double* p, int n) {
 
 // ------------------------------------------------------------------ row pass
 // grid: (row blocks, items); one block = rpc rows x n_c components of one item
+// index -> (line, k) for the R2C pre/post-processing without a division: first k in [0, Rh/2) for
+// every line (Rh/2 a power of two), then the middle frequency k = Rh/2 (its own partner) of each line
+__device__ __forceinline__ void kpair_index(int idx, int nlines, int lgRh, int& line, int& k) {
+  const int lgq = lgRh > 0 ? lgRh - 1 : 0;
+  const int n_lo = nlines << lgq;
+  if (idx < n_lo) {
+    line = idx >> lgq;
+    k = idx & ((1 << lgq) - 1);
+  } else {
+    line = idx - n_lo;
+    k = 1 << lgq;
+  }
+}
+
 // resident blocks of 256 threads per SM the register budget is cut for: binary32 4 (64 registers;
 // the pass is latency-bound and ran 18 % faster at 128^3 than with 80 registers and 3 blocks); the
 // others keep the budgets the compiler picks on its own (binary64 2-D 64, pairs 2-D 80, 3-D 128)
@@ -333,7 +347,8 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   const float* Dtab_f = item->Dtab_f;
   const C* tw = (const C*)dv.tw;
   const int tw_log2 = dv.tw_log2, lgR = lgRh + 1;
-  const int npl = Rh / 2 + 1;
+  // (line, k) pairs of the R2C pre/post-processing, k in [0, Rh/2]
+  const int npl_total = (nlines << (lgRh > 0 ? lgRh - 1 : 0)) + (Rh >= 2 ? nlines : 0);
 
   if (a.flags & ROW_LOAD_EPS) {
     const bool eps_df = is_f32<Real> || is_df<Real> || (a.flags & ROW_EPS_DF);
@@ -365,8 +380,9 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     cp_async_wait_all();
     __syncthreads();
     // half spectrum X[0..Rh] -> Z = E + i O (inverse of the R2C post-processing), in place
-    for (int idx = tid; idx < nlines * npl; idx += nthr) {
-      const int line = idx / npl, k = idx - line * npl;
+    for (int idx = tid; idx < npl_total; idx += nthr) {
+      int line, k;
+      kpair_index(idx, nlines, lgRh, line, k);
       C* L = buf + (size_t)line * Rh;
       if (k == 0) {
         const Real X0 = L[0].x, XN = nyq[line].x;
@@ -518,8 +534,9 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   __syncthreads();
   fft_dif(buf, lgRh, 0, nlines, tw, tw_log2);
   // R2C post-processing: X[k] = 1/2 (A - i W_R^k B), A = Z_k + conj Z_{Rh-k}, B = Z_k - conj Z_{Rh-k}
-  for (int idx = tid; idx < nlines * npl; idx += nthr) {
-    const int line = idx / npl, k = idx - line * npl;
+  for (int idx = tid; idx < npl_total; idx += nthr) {
+    int line, k;
+    kpair_index(idx, nlines, lgRh, line, k);
     C* L = buf + (size_t)line * Rh;
     if (k == 0) {
       const C Z0 = L[0];
@@ -543,7 +560,10 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
     const GreenK<Real> gk = green_consts<Real>(item, a.mat);
     for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
-      const int row = idx / (Rh + 1), k = idx - row * (Rh + 1);
+      // k in [0, Rh) of every row first (shifts), then the Nyquist frequency k = Rh of each row
+      const int n_lo = rpc << lgRh;
+      const int row = idx < n_lo ? idx >> lgRh : idx - n_lo;
+      const int k = idx < n_lo ? (idx & (Rh - 1)) : Rh;
       C val[NC];
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
@@ -669,16 +689,16 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   __syncthreads();
 
   // four-step twiddle W_e^{n1 k2} (k2 = row frequency of this column)
-  int64_t after_n1 = 1;
+  int lg_after_n1 = 0;
   int len_n1 = 1;
   if (a.has_twiddle) {
-    for (int x = dv.split_n1 + 1; x < a.a1; ++x) after_n1 *= dv.ax_len[x];
+    for (int x = dv.split_n1 + 1; x < a.a1; ++x) lg_after_n1 += dv.ax_log2[x];
     len_n1 = dv.ax_len[dv.split_n1];
   }
   auto col_krow = [&](int col) -> int64_t {
     const int64_t ii = i0 + col;
     if (nyqt) return (int64_t)dv.Rh;
-    return (int64_t)bitrev((uint32_t)(ii % a.row_slots), lg_slots);
+    return (int64_t)bitrev((uint32_t)(ii & (a.row_slots - 1)), lg_slots);   // row_slots is a power of two
   };
   auto split_tw = [&](int64_t j) -> C {
     const C* st = (const C*)dv.stw;
@@ -690,7 +710,7 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   if (a.has_twiddle && a.mode != COL_INV) {
     for (int idx = tid; idx < G * w; idx += nthr) {
       const int col = idx & (w - 1), g = idx >> lgw;
-      const int64_t n1 = (g / after_n1) % len_n1;
+      const int64_t n1 = (g >> lg_after_n1) & (len_n1 - 1);
       const C W = split_tw(n1 * col_krow(col));
 #pragma unroll
       for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmul(s[(size_t)f * G * w + idx], W);
@@ -748,7 +768,7 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
     if (a.has_twiddle) {
       for (int idx = tid; idx < G * w; idx += nthr) {
         const int col = idx & (w - 1), g = idx >> lgw;
-        const int64_t n1 = (g / after_n1) % len_n1;
+        const int64_t n1 = (g >> lg_after_n1) & (len_n1 - 1);
         const C W = split_tw(n1 * col_krow(col));
 #pragma unroll
         for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmulc(s[(size_t)f * G * w + idx], W);
