@@ -91,6 +91,18 @@ int lattice_plan(const int64_t* M, int d, lat_plan** out);
 void lattice_plan_destroy(lat_plan* plan);
 
 /*
+ * lattice_plan_set_cell -- the transformed pattern P_L(M) = L Lambda(M) cap L [-1/2, 1/2)^d of
+ * Sec. 3.3 (Def. 3.3): the microstructure lives in the cell L [-1/2, 1/2)^d, the pattern point y of
+ * lattice_points sits at x = L y, and the Fourier index h stands for the physical frequency L^{-T} h,
+ * where the Green operator is evaluated (the transform over the index sets is unchanged).  Phase
+ * fields are to be sampled at x = L y.  Strains and stresses are Cartesian components in the x frame.
+ *   L  host, d*d row-major, regular; NULL restores the unit cube.
+ * Returns LAT_ERR_ARG for non-finite entries, LAT_ERR_SINGULAR for a singular L.  Applies to solves
+ * started after the call (not to lattice_fft, which has no Green operator).
+ */
+int lattice_plan_set_cell(lat_plan* plan, const double* L);
+
+/*
  * lattice_plan_info -- m = |det M|, d_M = #{e_j > 1} and the d elementary
  * divisors e_1 | e_2 | ... (Sec. 2.2).  Any output pointer may be NULL.
  */

@@ -65,7 +65,7 @@ def boundary_mask(lat):
 
 
 def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
-                 transform='auto', boundary='literal'):
+                 transform='auto', boundary='literal', L=None, C0_tensor=None):
     """Run Algorithm 1.
 
     M        integer matrix (d x d) or an ``oracle.lattice.Lattice``
@@ -75,17 +75,29 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
     E        (d, d) macroscopic strain (tensor components)
     tol      Cauchy threshold; maxit caps the iteration count
     eps0     optional (m, d, d) warm start
+    L        optional regular real (d x d) cell matrix: the transformed pattern P_L(M) = L Lambda(M) cap
+             L [-1/2, 1/2)^d of Sec. 3.3 (Def. 3.3).  The point y of P(M) sits at x = L y in the cell
+             L [-1/2, 1/2)^d, whose dual lattice is L^{-T} Z^d, so the Fourier index h stands for the
+             physical frequency L^{-T} h: Gamma0 is evaluated there.  The DFT over the index sets is
+             unchanged.  None = the unit cube (L = I).
+    C0_tensor  optional (d, d, d, d) general reference medium (replaces C0); Gamma0 then comes from
+             the acoustic tensor K(xi) = C0 xi xi (the operator form of Sec. 3.1)
     Returns dict(eps, sigma, sigma_bar, iters, history).
     """
     lat = M if isinstance(M, Lattice) else Lattice(M)
     d, m = lat.d, lat.m
     phase = np.asarray(phase, dtype=np.int64)
     stiff = np.asarray(stiff, dtype=np.float64)
-    lam0, mu0 = C0
     E = np.asarray(E, dtype=np.float64)
-    C0t = el.iso_tensor(lam0, mu0, d)
+    if C0_tensor is None:
+        lam0, mu0 = C0
+        C0t = el.iso_tensor(lam0, mu0, d)
+    else:
+        C0t = np.asarray(C0_tensor, dtype=np.float64)
     dC = stiff - C0t                                   # (C_p - C0)
     h = lat.h.astype(np.float64)
+    if L is not None:
+        h = h @ np.linalg.inv(np.asarray(L, dtype=np.float64))      # rows: (L^{-T} h)^T = h^T L^{-1}
     nz = np.any(lat.h != 0, axis=1)
     assert nz.sum() == m - 1 and not nz[0], "h = 0 must be exactly k = 0"
     bmask = boundary_mask(lat) if boundary == 'zero' else None
@@ -99,7 +111,10 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
         tau = _phase_ddot(dC, phase, eps)                              # polarization
         tau_hat = _transform(lat, tau, False, transform)               # F(M) tau
         eps_hat = np.zeros_like(tau_hat)
-        eps_hat[nz] = -el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
+        if C0_tensor is None:
+            eps_hat[nz] = -el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
+        else:
+            eps_hat[nz] = -el.gamma_general_apply(C0t, h[nz], tau_hat[nz])
         if bmask is not None:
             eps_hat[bmask] = 0.0
         eps_hat[~nz] = E                                               # mean strain

@@ -134,6 +134,18 @@ class LatticePlan:
         _check(lib().lattice_freqs(self._h, h.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return h
 
+    def set_cell(self, L=None):
+        """Transformed pattern P_L(M) (Sec. 3.3): the cell is L [-1/2, 1/2)^d, the point y sits at
+        x = L y and the Green operator is evaluated at L^{-T} h (lattice_plan_set_cell); None resets."""
+        f = lib().lattice_plan_set_cell
+        f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        f.restype = ctypes.c_int
+        if L is None:
+            _check(f(self._h, None))
+            return
+        a, ap = _f64(np.asarray(L, dtype=np.float64).reshape(self.d, self.d))
+        _check(f(self._h, ap))
+
     def workspace_bytes(self, n_loads=1, precision=LAT_FP64):
         return int(lib().lattice_workspace_bytes(self._h, n_loads, precision))
 

@@ -58,6 +58,9 @@ struct lat_plan {
   float4* d_stwdf;
   int64_t stw_hi_n, stw_lo_n;
   int device;
+  // transformed pattern (lattice_plan_set_cell): has_cell and L^{-T}
+  int has_cell;
+  double cell_LinvT[3][3];
   // launch shapes picked by lattice_autotune, per precision and power-of-two bucket of the item count
   struct Tune {
     int valid;
@@ -85,6 +88,10 @@ struct LatDev {
   int tw_log2;
   const void* tw;             // twiddle table (double2 or float2, per precision)
   const void* stw;            // split twiddles [hi | lo]
+  // transformed pattern P_L(M) (Sec. 3.3): Gamma0 at L^{-T} h; binary64, binary32 and pair copies
+  int cell;
+  double cellT[3][3];
+  float cellT_f[3][3], cellT_lo[3][3];
 };
 
 void lat_set_error(const std::string& s);

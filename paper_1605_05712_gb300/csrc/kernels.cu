@@ -155,6 +155,27 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
   }
 }
 
+// h <- L^{-T} h in the kernel's precision (the matrix comes in all three forms, no binary64 conversion)
+template <typename Real>
+__device__ __forceinline__ Real cell_entry(const LatDev& dv, int i, int j) {
+  if constexpr (is_f32<Real>) return dv.cellT_f[i][j];
+  else if constexpr (is_df<Real>) return dfloat(dv.cellT_f[i][j], dv.cellT_lo[i][j]);
+  else return dv.cellT[i][j];
+}
+template <typename Real, int D>
+__device__ __forceinline__ void cell_map(const LatDev& dv, Real* h) {
+  Real t[3];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += cell_entry<Real>(dv, i, j) * h[j];
+    t[i] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) h[i] = t[i];
+}
+
 // frequency from the per-axis spectral indices: kk[x] for the logical axes (row last)
 template <typename Real, int NC>
 __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
@@ -210,6 +231,11 @@ __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, co
         for (int i = 0; i < d; ++i) h2[i] = (Real)hi[i];
       }
     }
+  }
+  if (dv.cell && !zero) {
+    // transformed pattern P_L(M) (Sec. 3.3, Def. 3.3): the index h is the frequency L^{-T} h
+    cell_map<Real, d>(dv, h);
+    if (boundary) cell_map<Real, d>(dv, h2);
   }
   green_point_h<Real, NC>(dv, mt, item, gk, zero, boundary, h, h2, val);
 }

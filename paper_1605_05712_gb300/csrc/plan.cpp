@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "internal.h"
@@ -442,6 +443,36 @@ extern "C" void lattice_plan_destroy(lat_plan* P) {
   if (P->d_twdf) cudaFree(P->d_twdf);
   if (P->d_stwdf) cudaFree(P->d_stwdf);
   delete P;
+}
+
+extern "C" int lattice_plan_set_cell(lat_plan* P, const double* L) {
+  if (!P) return lat_fail(LAT_ERR_ARG, "lattice_plan_set_cell: NULL plan");
+  if (!L) {
+    P->has_cell = 0;
+    return LAT_OK;
+  }
+  const int d = P->d;
+  double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double scale = 0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      if (!std::isfinite(L[i * d + j])) return lat_fail(LAT_ERR_ARG, "lattice_plan_set_cell: L not finite");
+      A[i][j] = L[i * d + j];
+      scale = std::max(scale, std::fabs(A[i][j]));
+    }
+  // inverse by cofactors (d <= 3); L^{-T}_ij = cof_ij / det
+  const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                     A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  if (!(std::fabs(det) > 1e-12 * scale * scale * scale))
+    return lat_fail(LAT_ERR_SINGULAR, "lattice_plan_set_cell: L is singular");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      P->cell_LinvT[i][j] = (A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1]) / det;
+    }
+  P->has_cell = 1;
+  return LAT_OK;
 }
 
 extern "C" int lattice_plan_info(const lat_plan* P, int64_t* m, int* d_M, int64_t* divisors) {

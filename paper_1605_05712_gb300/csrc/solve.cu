@@ -71,6 +71,14 @@ LatDev make_dev(const lat_plan* P, int kind) {
   dv.split_e = P->split_e;
   dv.stw_hi_n = P->stw_hi_n;
   dv.tw_log2 = P->tw_log2;
+  dv.cell = P->has_cell;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double v = P->has_cell ? P->cell_LinvT[i][j] : (i == j ? 1.0 : 0.0);
+      dv.cellT[i][j] = v;
+      dv.cellT_f[i][j] = (float)v;
+      dv.cellT_lo[i][j] = (float)(v - (double)(float)v);
+    }
   dv.tw = kind == LAT_MIXED ? (const void*)P->d_twf : kind == LAT_DF64 ? (const void*)P->d_twdf : (const void*)P->d_tw;
   dv.stw = kind == LAT_MIXED ? (const void*)P->d_stwf : kind == LAT_DF64 ? (const void*)P->d_stwdf : (const void*)P->d_stw;
   return dv;

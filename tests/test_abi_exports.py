@@ -1,4 +1,5 @@
 """liblatms.so builds, loads without a GPU and exports every function include/*.h declares."""
+import pytest
 import ctypes
 import glob
 import os
@@ -45,3 +46,14 @@ def test_host_side_plan_without_gpu():
             raise AssertionError("expected an error")
         except LatticeError as e:
             assert e.code == code
+
+
+def test_set_cell_validates_on_the_host():
+    from paper_1605_05712_gb300 import LatticeError, lattice_plan
+    P = lattice_plan([[16, 4], [0, 8]])
+    P.set_cell([[1.3, 0.4], [-0.2, 0.9]])
+    P.set_cell(None)
+    with pytest.raises(LatticeError):
+        P.set_cell([[1.0, 2.0], [0.5, 1.0]])            # singular
+    with pytest.raises(LatticeError):
+        P.set_cell([[float("nan"), 0.0], [0.0, 1.0]])

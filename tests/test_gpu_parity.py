@@ -69,10 +69,13 @@ def test_lattice_fft_matches_oracle(cuda, M):
     assert relerr(back, x) < 1e-12
 
 
-def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=None, cuda=None, precision="fp64"):
+def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=None, cuda=None, precision="fp64",
+             cell=None):
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
     P = lattice_plan(M)
+    if cell is not None:
+        P.set_cell(cell)
     L = Lattice(M)
     d = L.d
     ph_plan = phase_fn(P.points(), P.m)
@@ -94,7 +97,8 @@ def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=No
         if warm is not None:
             w0 = np.empty((L.m, d, d))
             w0[perm] = comps_to_tensor(warm[lc], d)
-        o = basic_scheme(L, ph_or, S, C0, Et, tol=tol, maxit=maxit, eps0=w0, boundary=("zero" if boundary == "zero" else "literal"))
+        o = basic_scheme(L, ph_or, S, C0, Et, tol=tol, maxit=maxit, eps0=w0,
+                         boundary=("zero" if boundary == "zero" else "literal"), L=cell)
         outs.append(o)
     return P, L, perm, g, outs
 
@@ -426,3 +430,55 @@ def test_autotuned_shapes_give_the_same_fields(cuda, M, prec):
     assert torch.equal(a["eps"], b["eps"])
     c = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec)
     assert c["status"] == 0
+
+
+# ---------------------------------------------------------------- transformed pattern P_L(M) (Sec. 3.3)
+CELL2 = [[1.3, 0.4], [-0.2, 0.9]]
+CELL3 = [[1.1, 0.3, -0.2], [0.0, 0.8, 0.25], [0.15, -0.1, 1.2]]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", [[[16, 4], [0, 8]], [[512, 16], [0, 512]], [[64, 1], [0, 64]],
+                               [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]]])
+def test_transformed_cell_fixed_iterations(cuda, M, prec):
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    out = run_pair(M, inclusions(6, d, 3, 0.3), LAM2, (5.5, 5.5), E, tol=0.0, maxit=5, cuda=cuda, precision=prec,
+                   cell=CELL2 if d == 2 else CELL3)
+    check_pair(*out, d=d)
+
+
+@pytest.mark.parametrize("M", [[[256, 0], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+def test_transformed_cell_mixed_within_stated_tolerance(cuda, M):
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    P.set_cell(CELL2 if d == 2 else CELL3)
+    ph = torch.from_numpy(inclusions(7, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+    E = np.eye(P.n_c)[:2]
+    a = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=2000, precision="mixed")
+    b = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=2000)
+    assert a["status"] == b["status"] == 0
+    assert float((a["eps"] - b["eps"]).abs().max() / b["eps"].abs().max()) <= MIXED_STRAIN_RTOL
+    assert np.abs(a["sigma_bar"] - b["sigma_bar"]).max() <= MIXED_CEFF_RTOL * np.abs(b["sigma_bar"]).max()
+
+
+def test_transformed_aligned_laminate_is_analytic(cuda):
+    # all frequencies of M = [[4096, 12288], [0, 1]] are parallel to (1, 3); in the cell L the laminate
+    # is the analytic one with the physical normal L^{-T} (1, 3)
+    import torch
+    from oracle import analytic as an
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan([[4096, 12288], [0, 1]])
+    P.set_cell(CELL2)
+    ph = synth.laminate_phase(P.points(), P.m, [1, 3])
+    E = np.array([[0.6, 0.0, 0.25]])
+    g = basic_scheme_solve(P, torch.from_numpy(ph).to(cuda), LAM2, (5.5, 5.5), E, tol=1e-14, maxit=500)
+    S = stiff_tensors(LAM2, 2)
+    n_phys = np.linalg.inv(np.array(CELL2)).T @ np.array([1.0, 3.0])
+    e1, e2, sb = an.laminate_fields(S[0], S[1], 0.5, n_phys, el.comps_to_sym(E[0], 2))
+    ex = np.where(ph[:, None, None] == 0, e1, e2)
+    eg = comps_to_tensor(g["eps"][0].cpu().numpy(), 2)
+    assert relerr(eg, ex) < 1e-10
+    assert relerr(el.comps_to_sym(g["sigma_bar"][0], 2), sb) < 1e-10
