@@ -510,6 +510,35 @@ def bench_sweep(args):
                       "l2": "flushed between timed steps"}))
 
 
+def bench_gather(args):
+    """Subsampling (Sec. 2.1 / 5.2): three binary64 field planes on the 2048 x 2048 grid gathered onto its
+    rank-2 subpattern N = [[2048,1024],[0,1024]] (m = 2^21) through lattice_gather; HBM GB/s of the
+    gather (algorithmic bytes: the planes read at the mapped points and written, plus the map)."""
+    import torch
+    from paper_1605_05712_gb300 import gather, gather_map, lattice_plan
+    dev = torch.device("cuda", 0)
+    src, dst = lattice_plan([[2048, 0], [0, 2048]]), lattice_plan([[2048, 1024], [0, 1024]])
+    t0 = time.perf_counter()
+    mp = torch.from_numpy(gather_map(src, dst)).to(dev)
+    t_map = time.perf_counter() - t0
+    x = torch.randn((3, src.m), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        gather(x, mp)
+    def step():
+        gather(x, mp)
+        return dst.m, None
+    ms, _, _ = timed(step, args.steps, flush, st)
+    nbytes = 3 * dst.m * 8 * 2 + dst.m * 4
+    pk = peaks()
+    print(json.dumps({"workload": "gather: 3 binary64 planes, 2048^2 grid -> subpattern [[2048,1024],[0,1024]] "
+                                  "(m = 2^21)", "map_host_s": round(t_map, 3), "ms": round(ms, 4),
+                      "algorithmic_bytes": nbytes, "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                      "hbm_peak_gbs": pk.get("hbm_gbs"),
+                      "frac": round(nbytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], 3) if pk.get("hbm_gbs") else None}))
+
+
 def profile_case(args):
     """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
     import torch
@@ -594,7 +623,7 @@ def main():
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
     ap.add_argument("--plain-launches", action="store_true",
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
-    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep"])
+    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep", "gather"])
     ap.add_argument("--ws-samples", type=int, default=2000)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)
@@ -610,6 +639,8 @@ def main():
         bench_warmstart(args)
     elif args.workload == "sweep":
         bench_sweep(args)
+    elif args.workload == "gather":
+        bench_gather(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

@@ -103,6 +103,28 @@ void lattice_plan_destroy(lat_plan* plan);
 int lattice_plan_set_cell(lat_plan* plan, const double* L);
 
 /*
+ * lattice_gather_map -- subsampling and rearrangement between patterns.  For M = J N (J integral),
+ * Lambda(N) is a sublattice of Lambda(M) and P(N) a subpattern of P(M) (Sec. 2.1); for
+ * pattern-congruent matrices (P(M1) = P(M2), e.g. M2 = Q M1 with Q unimodular, Sec. 2.2) the two
+ * point sets coincide and only the order differs.  map (host, to->m int32) receives, for every point
+ * of `to` in its plan order, the plan-order slot of the same point in `from`.  Host computation
+ * (exact integer matching of the point numerators); O(from->m) memory.
+ * Returns LAT_ERR_ARG if a point of P(to) is not in P(from) (or the dimensions differ),
+ * LAT_ERR_SIZE if from->m >= 2^31.
+ */
+int lattice_gather_map(const lat_plan* from, const lat_plan* to, int32_t* map);
+
+/*
+ * lattice_gather -- out[f][s] = in[f][map[s]] for s < n_out and f < n_fields (device): samples
+ * fields given on P(from) onto P(to) with a map of lattice_gather_map (copied to the device by the
+ * caller).  elem_bytes 1 (phase ids), 2, 4, 8 (binary64) or 16; in_plane / out_plane are the plane
+ * strides in elements.  Buffers aligned to the element size; in and out must not overlap.
+ * Asynchronous on `stream`.
+ */
+int lattice_gather(const void* in, void* out, const int32_t* map, int64_t n_out, int elem_bytes,
+                   int n_fields, int64_t in_plane, int64_t out_plane, void* stream);
+
+/*
  * lattice_plan_info -- m = |det M|, d_M = #{e_j > 1} and the d elementary
  * divisors e_1 | e_2 | ... (Sec. 2.2).  Any output pointer may be NULL.
  */

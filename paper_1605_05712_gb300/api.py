@@ -483,3 +483,34 @@ def multi_workspace_bytes(problems, precision="fp64"):
     L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
     L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
     return int(L.lattice_multi_workspace_bytes(items, n, {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]))
+
+
+def gather_map(src_plan, dst_plan):
+    """For every point of P(dst) in its plan order, the plan-order slot of the same point in P(src)
+    (lattice_gather_map): dst a subpattern of src (M_src = J M_dst, Sec. 2.1) or pattern-congruent
+    to it (Sec. 2.2).  Host numpy int32 array of dst.m entries; raises if P(dst) is not in P(src)."""
+    out = np.empty(dst_plan.m, dtype=np.int32)
+    f = lib().lattice_gather_map
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    _check(f(src_plan.handle, dst_plan.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
+
+
+def gather(x, index_map, stream=None):
+    """out[..., s] = x[..., index_map[s]] on the GPU (lattice_gather): fields (..., m_src) on P(src)
+    sampled onto P(dst).  x a contiguous CUDA tensor, index_map a CUDA int32 tensor from gather_map."""
+    import torch
+    if not (x.is_cuda and index_map.is_cuda and index_map.dtype == torch.int32 and x.is_contiguous()):
+        raise TypeError("gather: x must be a contiguous CUDA tensor and index_map a CUDA int32 tensor")
+    lead = tuple(x.shape[:-1])
+    n_f = int(np.prod(lead)) if lead else 1
+    n = index_map.numel()
+    out = torch.empty(lead + (n,), dtype=x.dtype, device=x.device)
+    f = lib().lattice_gather
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(index_map.data_ptr()),
+             n, x.element_size(), n_f, x.shape[-1], n, _stream(stream)))
+    return out

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -511,6 +512,50 @@ extern "C" int lattice_points(const lat_plan* P, int64_t* p) {
       if (2 * r >= m) r -= m;
       p[s * d + i] = (int64_t)r;
     }
+  }
+  return LAT_OK;
+}
+
+namespace {
+struct PointKey {
+  int64_t c[3];
+  bool operator==(const PointKey& o) const { return c[0] == o.c[0] && c[1] == o.c[1] && c[2] == o.c[2]; }
+};
+struct PointHash {
+  size_t operator()(const PointKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < 3; ++i) h = (h ^ (uint64_t)k.c[i]) * 1099511628211ull;
+    return (size_t)(h ^ (h >> 29));
+  }
+};
+}  // namespace
+
+extern "C" int lattice_gather_map(const lat_plan* from, const lat_plan* to, int32_t* map) {
+  if (!from || !to || !map) return lat_fail(LAT_ERR_ARG, "lattice_gather_map: NULL argument");
+  if (from->d != to->d) return lat_fail(LAT_ERR_ARG, "lattice_gather_map: plans of different dimension");
+  if (from->m >= (int64_t(1) << 31)) return lat_fail(LAT_ERR_SIZE, "lattice_gather_map: m of the source >= 2^31");
+  if (from->m % to->m != 0)
+    return lat_fail(LAT_ERR_ARG, "lattice_gather_map: |det| of the target does not divide the source's: not a subpattern");
+  const int d = from->d;
+  std::vector<int64_t> pf((size_t)from->m * d), pt((size_t)to->m * d);
+  lattice_points(from, pf.data());
+  lattice_points(to, pt.data());
+  // y = p_from / m_from = p_to / m_to: both in [-1/2, 1/2)^d, so equal points have equal scaled numerators
+  const int64_t scale = from->m / to->m;
+  std::unordered_map<PointKey, int32_t, PointHash> where;
+  where.reserve((size_t)from->m * 2);
+  for (int64_t s = 0; s < from->m; ++s) {
+    PointKey k = {{0, 0, 0}};
+    for (int i = 0; i < d; ++i) k.c[i] = pf[(size_t)s * d + i];
+    where.emplace(k, (int32_t)s);
+  }
+  for (int64_t s = 0; s < to->m; ++s) {
+    PointKey k = {{0, 0, 0}};
+    for (int i = 0; i < d; ++i) k.c[i] = pt[(size_t)s * d + i] * scale;
+    auto it = where.find(k);
+    if (it == where.end())
+      return lat_fail(LAT_ERR_ARG, "lattice_gather_map: a point of the target pattern is not in the source pattern");
+    map[s] = it->second;
   }
   return LAT_OK;
 }
