@@ -539,6 +539,52 @@ def bench_gather(args):
                       "frac": round(nbytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], 3) if pk.get("hbm_gbs") else None}))
 
 
+def bench_shear_sweep(args):
+    """Sec. 5.1 shear sweep: Example 4.1's coated ellipse (one point along x3) on the 393 pattern matrices
+    M_{j,k,alpha}, M~_j (m = 2^14 / 2^13), the analytic load case eps0, all in one
+    basic_scheme_solve_multi call per precision, tol 1e-8; e_eff of the Table-1 matrices against the
+    analytic C^eff eps0."""
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve_multi, lattice_plan, multi_workspace_bytes, synth
+    dev = torch.device("cuda", 0)
+    w = synth.hashin2d_workload()
+    E = np.array([[w["eps0"][0, 0], w["eps0"][1, 1], w["eps0"][2, 2], w["eps0"][1, 2], w["eps0"][0, 2],
+                   w["eps0"][0, 1]]])
+    probs = []
+    for name, M in synth.shear_sweep_matrices():
+        P = lattice_plan(M)
+        ph = synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+        probs.append(dict(name=name, plan=P, phase=torch.from_numpy(ph).to(dev), stiffness=w["stiffness"],
+                          C0=w["C0"], E=E, eps=torch.empty((1, 6, P.m), dtype=torch.float64, device=dev)))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    ref = np.linalg.norm(w["ceff_eps0"])
+    res = {}
+    for prec in ("fp64", "df64", "mixed"):
+        ws = torch.empty(multi_workspace_bytes(probs, prec), dtype=torch.uint8, device=dev)
+        last = {}
+
+        def step():
+            rc, outs = basic_scheme_solve_multi(probs, tol=1e-8, maxit=3000, precision=prec, workspace=ws)
+            last["outs"] = outs
+            return sum(p_["plan"].m * int(o["iters"][0]) for p_, o in zip(probs, outs)), None
+        step()
+        ms, units, _ = timed(step, max(1, args.steps), flush, st)
+        eff = {}
+        for p_, o in zip(probs, last["outs"]):
+            sb = o["sigma_bar"][0]
+            S = np.array([[sb[0], sb[5], sb[4]], [sb[5], sb[1], sb[3]], [sb[4], sb[3], sb[2]]])
+            eff[p_["name"]] = float(np.linalg.norm(S - w["ceff_eps0"]) / ref)
+        res[prec] = {"ms": round(ms, 2), "value": round(units / (ms / 1e3), 1),
+                     "e_eff_table1": {k: round(eff[k], 5) for k in ("M_7,0,0", "M~_7", "M_8,16,0", "M_9,-496,0",
+                                                                   "M_9,16,0", "M_7,272,1")},
+                     "e_eff_min": [min(eff, key=eff.get), round(min(eff.values()), 5)]}
+        del ws
+    print(json.dumps({"workload": "shear sweep (Sec. 5.1): 393 matrices M_{j,k,alpha}, M~_j, coated ellipse of "
+                                  "Example 4.1, eps0 load case, tol 1e-8", "metric": METRIC,
+                      "unit": "point-iterations/s", "results": res}))
+
+
 def profile_case(args):
     """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
     import torch
@@ -623,7 +669,7 @@ def main():
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
     ap.add_argument("--plain-launches", action="store_true",
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
-    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep", "gather"])
+    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep", "gather", "shear_sweep"])
     ap.add_argument("--ws-samples", type=int, default=2000)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)
@@ -641,6 +687,8 @@ def main():
         bench_sweep(args)
     elif args.workload == "gather":
         bench_gather(args)
+    elif args.workload == "shear_sweep":
+        bench_shear_sweep(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

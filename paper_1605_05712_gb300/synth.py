@@ -177,7 +177,7 @@ def iso_projection(V):
 
 
 def hashin_workload(seed=BASE_SEED, c=(0.1, 0.15, 0.2), total_fraction=0.25, core=(10.0, 10.0),
-                    coating=(1.0, 1.0), matrix_base=(1.0, 1.0)):
+                    coating=(1.0, 1.0), matrix_base=(1.0, 1.0), rho_e=None, R=None):
     """Coated ellipsoid of the generalized Hashin structure (Sec. 4.2) as a benchmark input.
 
     Core semi-axes c (rho_c = 0), a confocal coating to the given total inclusion volume fraction,
@@ -190,14 +190,16 @@ def hashin_workload(seed=BASE_SEED, c=(0.1, 0.15, 0.2), total_fraction=0.25, cor
     from scipy.optimize import brentq
     c = np.asarray(c, dtype=np.float64)
     rng = np.random.default_rng(seed)
-    R = euler_zyz(*rng.uniform(0, 2 * np.pi, 3))
-    vol = lambda r: 4.0 / 3.0 * np.pi * np.prod(np.sqrt(c ** 2 + r)) - total_fraction
-    rho_e = brentq(vol, 0.0, 1.0, xtol=1e-15)
+    if R is None:
+        R = euler_zyz(*rng.uniform(0, 2 * np.pi, 3))
+    if rho_e is None:
+        vol = lambda r: 4.0 / 3.0 * np.pi * np.prod(np.sqrt(c ** 2 + r)) - total_fraction
+        rho_e = brentq(vol, 0.0, 1.0, xtol=1e-15)
     rho_c = 0.0
     lc, mc = core
     le, me = coating
     kc, ke = lc + 2 * mc / 3, le + 2 * me / 3
-    g = lambda r: np.prod(c ** 2 + r)
+    g = lambda r: np.prod([ci ** 2 + r for ci in c if np.isfinite(ci)])
     f = lambda r: np.sqrt(g(rho_c) / g(r))
     Dc = np.diag(_depol_carlson(c, rho_c))
     fe = f(rho_e)
@@ -271,4 +273,31 @@ def serving_sweep(n=256, seed=BASE_SEED, m_exp=(12, 21), contrast_log10=(-2.0, 2
         out.append(dict(d=d, M=M, kind=kind, m=1 << U_exp, incl=incl, contrast=k,
                         stiffness=[iso_voigt(1.0, 1.0), iso_voigt(k, k)], C0=c0_mean_extremes([1.0, k], [1.0, k]),
                         E=E))
+    return out
+
+
+# ------------------------------------------------------------------ Sec. 5.1 shear sweep (Table 1)
+def hashin2d_workload():
+    """Example 4.1 as a two-dimensional problem (one point along x3): the coated ellipse c = (0.05,
+    0.35, inf), rho_c = 0, rho_e = 0.09, rotated by 60 degrees about x3 (n = (1/2, sqrt(3)/2, 0), the
+    reading of the printed n = (1/2, 1, 0)); core (10, 10), coating (1, 1), the neutral matrix
+    (the Lame constants of the paper's experiment are not printed)."""
+    t = np.pi / 3.0
+    R = np.array([[np.cos(t), -np.sin(t), 0.0], [np.sin(t), np.cos(t), 0.0], [0.0, 0.0, 1.0]])
+    return hashin_workload(c=(0.05, 0.35, np.inf), rho_e=0.09, R=R)
+
+
+def shear_sweep_matrices():
+    """The pattern matrices of Sec. 5.1 as (name, 3 x 3 list): M_{j,k,alpha} = [[2^j, alpha k, 0],
+    [(1 - alpha) k, 2^(14-j), 0], [0, 0, 1]] for j in {7, 8, 9}, alpha in {0, 1}, k in 16 {-32, ..., 32}
+    (390 matrices, det 2^14), and M~_j = 1/2 [[1, 1, 0], [-1, 1, 0], [0, 0, 2]] diag(2^j, 2^(14-j), 1)
+    for j in {7, 8, 9} (det 2^13)."""
+    out = []
+    for j in (7, 8, 9):
+        for alpha in (0, 1):
+            for k in range(-32 * 16, 32 * 16 + 1, 16):
+                out.append(("M_%d,%d,%d" % (j, k, alpha),
+                            [[2 ** j, alpha * k, 0], [(1 - alpha) * k, 2 ** (14 - j), 0], [0, 0, 1]]))
+    for j in (7, 8, 9):
+        out.append(("M~_%d" % j, [[2 ** (j - 1), 2 ** (13 - j), 0], [-2 ** (j - 1), 2 ** (13 - j), 0], [0, 0, 1]]))
     return out

@@ -39,3 +39,18 @@ def test_sweep_geometry_fits():
     for prec in ("fp64", "mixed"):
         assert all(multi_workspace_bytes([p], prec) > 0 for p in probs)
         assert multi_workspace_bytes(probs, prec) >= sum(multi_workspace_bytes([p], prec) for p in probs)
+
+
+def test_shear_sweep_matrices_and_workload():
+    from oracle.lattice import smith_normal_form
+    mats = synth.shear_sweep_matrices()
+    assert len(mats) == 393
+    for name, M in mats:
+        det = abs(round(np.linalg.det(np.array(M, float))))
+        assert det == (2 ** 13 if name.startswith("M~") else 2 ** 14)
+        _, e, _ = smith_normal_form(M)
+        assert int(e[0]) == 1                                  # one point along x3
+        assert multi_workspace_bytes([dict(plan=lattice_plan(M), stiffness=[np.eye(6)], E=np.zeros((1, 6)))]) > 0
+    w = synth.hashin2d_workload()
+    assert w["rho_e"] == 0.09 and np.isinf(w["c"][2])
+    assert np.linalg.eigvalsh(w["stiffness"][2]).min() > 0      # the neutral matrix is positive definite
