@@ -65,7 +65,7 @@ def boundary_mask(lat):
 
 
 def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
-                 transform='auto', boundary='literal', L=None, C0_tensor=None):
+                 transform='auto', boundary='literal', L=None, C0_tensor=None, scheme='basic'):
     """Run Algorithm 1.
 
     M        integer matrix (d x d) or an ``oracle.lattice.Lattice``
@@ -82,6 +82,14 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
              unchanged.  None = the unit cube (L = I).
     C0_tensor  optional (d, d, d, d) general reference medium (replaces C0); Gamma0 then comes from
              the acoustic tensor K(xi) = C0 xi xi (the operator form of Sec. 3.1)
+    scheme   'basic' (Algorithm 1) or 'eyre_milton', an accelerated scheme of the kind the paper names
+             as carrying over to patterns (Sec. 6), written from the projector identities: with
+             u = (C + C0) eps, v = (C - C0) eps and Pi = C0 Gamma0 (the projector onto C0 times
+             compatible fields), compatibility of eps and equilibrium of C eps read u = (I - 2 Pi) v at
+             h != 0 and <u> = <v> + 2 C0 E; the iteration u <- (I - 2 Pi) v(u) contracts at
+             max |c - c0| / (c + c0).  Each step: v = (C - C0) eps, u_hat = v_hat - 2 C0 Gamma0 v_hat
+             (h != 0), u_hat_0 = v_hat_0 + 2 C0 E, u = Re F^{-1} u_hat, eps <- (C + C0)^{-1} u.  Its
+             fixed point is Algorithm 1's.
     Returns dict(eps, sigma, sigma_bar, iters, history).
     """
     lat = M if isinstance(M, Lattice) else Lattice(M)
@@ -107,18 +115,35 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
     norm0 = np.sqrt(m) * nE if nE > 0 else 1.0
     history = []
     it = 0
+    if scheme == 'eyre_milton':
+        # (C_p + C0)^{-1} per phase, as the inverse of the linear map on symmetric tensors
+        Wp = np.array([_inverse_on_sym(stiff[q] + C0t) for q in range(len(stiff))])
+        if boundary == 'zero':
+            # zeroing eps_hat at the boundary frequencies has no counterpart in the u iteration
+            raise ValueError("the Eyre-Milton scheme takes the literal (averaged) boundary treatment")
+    elif scheme != 'basic':
+        raise ValueError("scheme must be 'basic' or 'eyre_milton'")
     while it < maxit:
-        tau = _phase_ddot(dC, phase, eps)                              # polarization
+        tau = _phase_ddot(dC, phase, eps)                              # polarization (v for Eyre-Milton)
         tau_hat = _transform(lat, tau, False, transform)               # F(M) tau
         eps_hat = np.zeros_like(tau_hat)
         if C0_tensor is None:
-            eps_hat[nz] = -el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
+            g = el.gamma_iso_apply(h[nz], tau_hat[nz], lam0, mu0)
         else:
-            eps_hat[nz] = -el.gamma_general_apply(C0t, h[nz], tau_hat[nz])
-        if bmask is not None:
-            eps_hat[bmask] = 0.0
-        eps_hat[~nz] = E                                               # mean strain
-        eps_new = _transform(lat, eps_hat, True, transform).real       # F(M)^{-1}
+            g = el.gamma_general_apply(C0t, h[nz], tau_hat[nz])
+        if scheme == 'basic':
+            eps_hat[nz] = -g
+            if bmask is not None:
+                eps_hat[bmask] = 0.0
+            eps_hat[~nz] = E                                           # mean strain
+            eps_new = _transform(lat, eps_hat, True, transform).real   # F(M)^{-1}
+        else:
+            eps_hat[nz] = tau_hat[nz] - 2.0 * el.ddot(C0t, g)         # u_hat = (I - 2 C0 Gamma0) v_hat
+            if bmask is not None:
+                eps_hat[bmask] = 0.0
+            eps_hat[~nz] = tau_hat[~nz] + 2.0 * el.ddot(C0t, E)       # <u> = <v> + 2 C0 E
+            u = _transform(lat, eps_hat, True, transform).real
+            eps_new = _phase_ddot(Wp, phase, u)                        # eps = (C + C0)^{-1} u
         r = np.sqrt(el.frob2(eps_new - eps).sum()) / norm0
         eps = eps_new
         it += 1
@@ -127,6 +152,24 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
             break
     sigma = _phase_ddot(stiff, phase, eps)
     return dict(eps=eps, sigma=sigma, sigma_bar=sigma.mean(axis=0), iters=it, history=history)
+
+
+def _inverse_on_sym(C):
+    """Inverse of the linear map eps -> C : eps on symmetric d x d tensors, as a (d, d, d, d) tensor
+    with the minor symmetries (via the orthonormal Mandel basis)."""
+    d = C.shape[0]
+    pairs = [(i, i) for i in range(d)] + [(i, j) for i in range(d) for j in range(i + 1, d)]
+    B = []
+    for (i, j) in pairs:
+        e = np.zeros((d, d))
+        if i == j:
+            e[i, i] = 1.0
+        else:
+            e[i, j] = e[j, i] = np.sqrt(0.5)
+        B.append(e)
+    A = np.array([[np.einsum('ij,ijkl,kl', a, C, b) for b in B] for a in B])
+    Ai = np.linalg.inv(A)
+    return np.einsum('pq,pij,qkl->ijkl', Ai, np.array(B), np.array(B))
 
 
 def filtered_start(M, phase, stiff, C0, E, eps0, rho, **kw):
