@@ -132,6 +132,9 @@ def setup(dev):
 PLAIN_LAUNCHES = False   # --plain-launches: iterate with plain launches instead of the CUDA-graph loop
 
 
+C0_EM = (np.sqrt(1.0 * 10.0), np.sqrt(1.0 * 10.0))   # geometric mean of the laminate's extremes
+
+
 def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
     """One pass of the workload.  fp64_separate: each load case its own solve (the configured
     form); *_batched: the three load cases of a lattice in one batched solve; df64 = the binary64-accurate
@@ -141,7 +144,12 @@ def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
     iters = []
     for w in work:
         prec = mode.split("_")[0]                       # fp64, df64 or mixed
-        if mode.endswith("_separate"):
+        em = mode.endswith("_em")                       # Eyre-Milton at the geometric-mean reference
+        if em:
+            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0_EM, E, tol=tol, maxit=MAXIT, workspace=ws,
+                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES, scheme="eyre_milton")
+            its = [int(x) for x in g["iters"]]
+        elif mode.endswith("_separate"):
             its = []
             for lc in range(E.shape[0]):
                 g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E[lc:lc + 1], tol=tol, maxit=MAXIT,
@@ -263,7 +271,8 @@ def bench_gpu(args):
             ms_v, u_v, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode), args.steps, flush, st)
             variants[mode] = {"value": round(u_v / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 4), "iterations": it_v}
         ttt = {}
-        for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched"):
+        for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched", "fp64_batched_em",
+                     "mixed_batched_em"):
             run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6)
             ms_v, _, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6), args.steps, flush, st)
             ttt[mode] = {"ms": round(ms_v, 4), "iterations": it_v}
@@ -474,7 +483,14 @@ def bench_sweep(args):
             out.append(basic_scheme_solve(p_["plan"], p_["phase"], p_["stiffness"], p_["C0"], p_["E"], tol=1e-6,
                                           maxit=5000, precision="mixed", eps_out=p_["eps"]))
         return out
-    for name, fn in (("multi", run_multi), ("one_call_each", run_each)):
+    probs_em = [dict(p_, C0=(np.sqrt(s_["stiffness"][0][0, 1] * s_["stiffness"][1][0, 1]),) * 2)
+                for p_, s_ in zip(probs, sweep)]
+
+    def run_multi_em():
+        return basic_scheme_solve_multi(probs_em, tol=1e-6, maxit=5000, precision="mixed", workspace=ws,
+                                        scheme="eyre_milton")
+
+    for name, fn in (("multi", run_multi), ("one_call_each", run_each), ("multi_eyre_milton", run_multi_em)):
         fn()
         times = []
         for _ in range(max(1, args.steps)):
@@ -484,7 +500,7 @@ def bench_sweep(args):
             out = fn()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t1)
-        outs = out[1] if name == "multi" else out
+        outs = out[1] if name.startswith("multi") else out
         pit = sum(p_["plan"].m * int(np.sum(o["iters"])) for p_, o in zip(probs, outs))
         its = np.concatenate([np.asarray(o["iters"]) for o in outs])
         res[name] = {"s": round(float(np.median(times)), 3), "point_iterations": pit,

@@ -65,6 +65,10 @@ extern "C" {
                           convergence test in binary64.  Agrees with LAT_FP64 to ~1e-13; faster
                           where binary64 issues at a small fraction of the binary32 rate */
 
+/* iteration (lat_solve_opts.scheme) */
+#define LAT_SCHEME_BASIC 0
+#define LAT_SCHEME_EYRE_MILTON 1
+
 /* treatment of boundary frequencies of the symmetric cell (k with h(-k) != -h(k)) */
 #define LAT_BOUNDARY_AVERAGE 0  /* Gamma0 averaged over h(k) and -h(-k): the real part of the
                                    paper's complex update (default) */
@@ -178,6 +182,13 @@ typedef struct lat_solve_opts {
                            nonzero: plain kernel launches with a host read of the convergence
                            state after every iteration, same results (for profilers that do not
                            trace kernels inside graphs with conditional nodes) */
+  int scheme;           /* LAT_SCHEME_BASIC (0, Algorithm 1) or LAT_SCHEME_EYRE_MILTON (1):
+                           the accelerated iteration u = (C + C0) eps <- (I - 2 C0 Gamma0)
+                           (C - C0) eps, <u> = <(C - C0) eps> + 2 C0 E (Sec. 6 notes that such
+                           schemes carry over to patterns).  Same discrete solution as Algorithm 1
+                           at the same C0, converging for any positive C0, fastest at the
+                           geometric mean of the phase extremes (rate (sqrt(k)-1)/(sqrt(k)+1)
+                           against (k-1)/(k+1)).  Not with LAT_BOUNDARY_ZERO. */
 } lat_solve_opts;
 
 /*

@@ -17,6 +17,8 @@ from ._build import LIB
 
 LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
 LAT_ERR_ARG = -1
+LAT_SCHEME_BASIC, LAT_SCHEME_EYRE_MILTON = 0, 1
+_SCHEMES = {"basic": LAT_SCHEME_BASIC, "eyre_milton": LAT_SCHEME_EYRE_MILTON}
 LAT_FP64, LAT_MIXED, LAT_DF64 = 0, 1, 2
 LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
 HIST_CAP = 4096
@@ -37,7 +39,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("resid_history", ctypes.POINTER(ctypes.c_double)),
                 ("mixed_increment", ctypes.c_int), ("mixed_restart", ctypes.c_int),
-                ("plain_launches", ctypes.c_int)]
+                ("plain_launches", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 def lib():
@@ -205,8 +207,8 @@ def lattice_fft(plan, x, inverse=False, stream=None):
 def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
                        boundary="average", eps0=None, want_sigma=False, history=False, workspace=None,
                        eps_out=None, stream=None, mixed_increment=True, plain_launches=False,
-                       mixed_restart=True):
-    """Algorithm 1 on the GPU.  Returns a dict of torch/numpy results.
+                       mixed_restart=True, scheme="basic"):
+    """Algorithm 1 on the GPU (scheme="eyre_milton": the accelerated iteration, same discrete solution).  Returns a dict of torch/numpy results.
 
     phase      uint8 CUDA tensor (m,), plan order
     stiffness  (n_phases, 6, 6) Voigt matrices (host)
@@ -243,7 +245,8 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     hist = np.zeros((n_loads, max(maxit, 1))) if history else None
     opts = _Opts(prec, bnd, 1 if eps0 is not None else 0,
                  hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
-                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0)
+                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0,
+                 _SCHEMES[scheme])
     rc = lib().basic_scheme_solve(
         plan.handle, ctypes.c_void_p(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
         ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
@@ -331,7 +334,8 @@ class _BatchItem(ctypes.Structure):
 
 def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit=1000, precision="fp64",
                              boundary="average", want_sigma=False, history=False, workspace=None, eps_out=None,
-                             stream=None, mixed_increment=True, plain_launches=False, mixed_restart=True):
+                             stream=None, mixed_increment=True, plain_launches=False, mixed_restart=True,
+                             scheme="basic"):
     """Algorithm 1 for a batch of independent microstructures on one lattice, in one set of launches.
 
     phases       list of uint8 CUDA tensors (m,)
@@ -374,7 +378,8 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     resid = np.zeros(n)
     hist = np.zeros((n, max(maxit, 1))) if history else None
     opts = _Opts(prec, bnd, 0, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
-                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0)
+                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0,
+                 _SCHEMES[scheme])
     f = L.basic_scheme_solve_batch
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(_BatchItem), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                   ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -401,7 +406,7 @@ class _MultiItem(ctypes.Structure):
 
 def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", boundary="average",
                              want_sigma=False, workspace=None, stream=None, mixed_increment=True,
-                             plain_launches=False, warm_start=False, mixed_restart=True):
+                             plain_launches=False, warm_start=False, mixed_restart=True, scheme="basic"):
     """Algorithm 1 for independent problems on different lattices in one call (one CUDA graph).
 
     problems  list of dicts: plan (LatticePlan), phase (uint8 CUDA tensor (m,)), stiffness
@@ -456,7 +461,7 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     dev = problems[0]["phase"].device
     ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
     opts = _Opts(prec, bnd, 1 if warm_start else 0, None, 1 if mixed_increment else 0, 0 if mixed_restart else -1,
-                 1 if plain_launches else 0)
+                 1 if plain_launches else 0, _SCHEMES[scheme])
     f = L.basic_scheme_solve_multi
     f.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts),
                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]

@@ -83,6 +83,7 @@ __device__ __forceinline__ void v_to_h(const LatDev& dv, const int64_t* v, int64
 template <typename Real>
 struct GreenK {
   Real c1, c2, sc;
+  Real lam0, mu0;  // Eyre-Milton: C0 applied after Gamma0
 };
 template <typename Real>
 __device__ __forceinline__ GreenK<Real> green_consts(const ItemDev* item, const MatArgs& mt) {
@@ -90,9 +91,13 @@ __device__ __forceinline__ GreenK<Real> green_consts(const ItemDev* item, const 
   if constexpr (is_f32<Real>) {
     g.c1 = item->c1f;
     g.c2 = item->c2f;
+    g.lam0 = item->lam0f;
+    g.mu0 = item->mu0f;
   } else {
     g.c1 = Real(item->c1);
     g.c2 = Real(item->c2);
+    g.lam0 = Real(item->lam0);
+    g.mu0 = Real(item->mu0);
   }
   g.sc = Real(mt.gscale);
   return g;
@@ -124,8 +129,18 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
   typedef typename cplx_of<Real>::type C;
   constexpr int d = (NC == 6) ? 3 : 2, n_c = NC;
   if (zero) {
+    if (mt.scheme == LAT_SCHEME_EYRE_MILTON) {
+      // <u> = <v> + 2 C0 : E (the forward transform is unnormalized: -sc = 1/m); an increment keeps <v>
 #pragma unroll
-    for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(item->E[c], 0.0);
+      for (int c = 0; c < n_c; ++c) {
+        val[c].x = -gk.sc * val[c].x;
+        val[c].y = -gk.sc * val[c].y;
+        if (!mt.increment) val[c].x += Real(item->twoC0E[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) val[c] = mt.increment ? cmake<C>(0.0, 0.0) : cmake<C>(item->E[c], 0.0);
+    }
     return;
   }
   if (boundary && mt.boundary_zero) {
@@ -147,6 +162,23 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
     gamma_apply<Real>(d, h2, a2, gk.c1, gk.c2, ti, gi2);
 #pragma unroll
     for (int c = 0; c < n_c; ++c) gr[c] = Real(0.5) * (gr[c] + gr2[c]), gi[c] = Real(0.5) * (gi[c] + gi2[c]);
+  }
+  if (mt.scheme == LAT_SCHEME_EYRE_MILTON) {
+    // u_hat = v_hat / m - 2 C0 : Gamma0 : v_hat / m = -sc v_hat + 2 C0 : (sc Gamma0 : v_hat)
+    Real trr = Real(0), tri = Real(0);
+#pragma unroll
+    for (int c = 0; c < d; ++c) trr += gr[c], tri += gi[c];
+    trr = gk.sc * trr;
+    tri = gk.sc * tri;
+    const Real two = Real(2);
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) {
+      Real cr = two * gk.mu0 * (gk.sc * gr[c]), ci = two * gk.mu0 * (gk.sc * gi[c]);
+      if (c < d) cr += gk.lam0 * trr, ci += gk.lam0 * tri;
+      val[c].x = two * cr - gk.sc * tr[c];
+      val[c].y = two * ci - gk.sc * ti[c];
+    }
+    return;
   }
 #pragma unroll
   for (int c = 0; c < n_c; ++c) {
@@ -449,6 +481,29 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
       e0[c] = z.x;
       e1[c] = z.y;
     }
+    const uchar2 ph = *(const uchar2*)(phase + g);  // g even
+    if (update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
+      // the transform returned u = (C + C0) eps (or its increment): eps = (C_p + C0)^{-1} u per point
+      const Real* Wt;
+      if constexpr (is_f32<Real>) Wt = (const Real*)item->Wtab_f;
+      else if constexpr (is_df<Real>) Wt = (const Real*)item->Wtab_df;
+      else Wt = (const Real*)item->Wtab;
+      const Real* W0 = Wt + (int)ph.x * n_c * n_c;
+      const Real* W1 = Wt + (int)ph.y * n_c * n_c;
+      // u is still in shared memory: read it from there (no register copies on the common path)
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        Real t0 = Real(0), t1 = Real(0);
+#pragma unroll
+        for (int q = 0; q < n_c; ++q) {
+          const C z = buf[((size_t)q * rpc + row) * Rh + n];
+          t0 += ldg_r(W0 + c * n_c + q) * z.x;
+          t1 += ldg_r(W1 + c * n_c + q) * z.y;
+        }
+        e0[c] = t0;
+        e1[c] = t1;
+      }
+    }
     if (update) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
@@ -539,7 +594,6 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
         }
       }
     }
-    const uchar2 ph = *(const uchar2*)(phase + g);  // g even
     const Real* Dt;
     if constexpr (is_f32<Real>) Dt = (const Real*)Dtab_f;
     else if constexpr (is_df<Real>) Dt = (const Real*)item->Dtab_df;

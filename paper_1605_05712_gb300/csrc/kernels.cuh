@@ -37,6 +37,14 @@ struct ItemDev {
   double E[6];           // macroscopic strain, tensor components
   double c1, c2;         // Green operator constants of this item's C0
   float c1f, c2f;
+  // Eyre-Milton iteration: (C_p + C0)^{-1} on tensor components (maps the stress-like u to the strain),
+  // the reference medium's Lame constants and 2 C0 : E (tensor components)
+  const double* Wtab;
+  const float* Wtab_f;
+  const dfloat* Wtab_df;
+  double lam0, mu0;
+  float lam0f, mu0f;
+  double twoC0E[6];
   double norm0;          // sqrt(m) ||E||_F (1 if E = 0)
 };
 
@@ -60,6 +68,7 @@ struct MatArgs {
   double gscale;         // -1/m: the forward 1/m of F(M) and the minus sign of the update
   int boundary_zero;
   int increment;         // 1: spectrum carries an increment, k = 0 gets 0 instead of E
+  int scheme;            // LAT_SCHEME_BASIC (Algorithm 1) or LAT_SCHEME_EYRE_MILTON
 };
 
 struct IterArgs {

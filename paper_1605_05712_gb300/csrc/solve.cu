@@ -171,6 +171,13 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   off = align256(off + (size_t)n_tables * w.table_bytes / 2);
   w.tables_df = off;   // (C - C0) as double-float pairs: 8 bytes per entry like binary64
   off = align256(off + (precision != LAT_FP64 ? (size_t)n_tables * w.table_bytes : 0));  // mixed: its restart
+  // (C + C0)^{-1} of the Eyre-Milton iteration: binary64, binary32, pairs
+  w.tables_w = off;
+  off = align256(off + (size_t)n_tables * w.table_bytes);
+  w.tables_wf = off;
+  off = align256(off + (size_t)n_tables * w.table_bytes / 2);
+  w.tables_wdf = off;
+  off = align256(off + (size_t)n_tables * w.table_bytes);
   w.partials = off;
   off = align256(off + (size_t)n_items * w.pstride * sizeof(double));
   w.scal = off;
@@ -186,6 +193,33 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   }
   w.total = off;
   return w;
+}
+
+// inverse of an n x n matrix (n <= 6) by Gauss-Jordan with partial pivoting; false if singular
+bool invert_small(const double* A, int n, double* out) {
+  double M[6][12];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  double scale = 0;
+  for (int i = 0; i < n * n; ++i) scale = std::max(scale, fabs(A[i]));
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (!(fabs(M[piv][c]) > 1e-14 * scale)) return false;
+    if (piv != c)
+      for (int j = 0; j < 2 * n; ++j) std::swap(M[c][j], M[piv][j]);
+    const double inv = 1.0 / M[c][c];
+    for (int j = 0; j < 2 * n; ++j) M[c][j] *= inv;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+        for (int j = 0; j < 2 * n; ++j) M[r][j] -= f * M[c][j];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) out[i * n + j] = M[i][n + j];
+  return true;
 }
 
 // tensor-component form of a 6x6 Voigt matrix: out[I][J] = V[vi][vj] * (J shear ? 2 : 1)
@@ -358,6 +392,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   const int n_tables = (int)stiff.size();
   const size_t tstride = wl.table_bytes / sizeof(double);
   std::vector<double> tabs((size_t)n_tables * 2 * tstride, 0.0);
+  std::vector<double> tabs_w((size_t)n_tables * tstride, 0.0);
   for (int t = 0; t < n_tables; ++t) {
     int owner = -1;
     for (int i = 0; i < n_items && owner < 0; ++i)
@@ -380,6 +415,12 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       double* Cp = &tabs[(size_t)(2 * t + 1) * tstride + (size_t)p * n_c * n_c];
       voigt_to_tc(stiff[t] + 36 * p, d, Cp);
       for (int k = 0; k < n_c * n_c; ++k) Dp[k] = Cp[k] - c0tc[k];
+      if (o.scheme == LAT_SCHEME_EYRE_MILTON) {
+        double S[36];
+        for (int k = 0; k < n_c * n_c; ++k) S[k] = Cp[k] + c0tc[k];
+        if (!invert_small(S, n_c, &tabs_w[(size_t)t * tstride + (size_t)p * n_c * n_c]))
+          return lat_fail(LAT_ERR_ARG, "Eyre-Milton: C_p + C0 is singular");
+      }
     }
   }
   std::vector<ItemDev> hdev(n_items);
@@ -394,7 +435,29 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     v.Dtab = (const double*)(ws + wl.tables + (size_t)(2 * it.table) * wl.table_bytes);
     v.Dtab_f = (const float*)(ws + wl.tables_f + (size_t)it.table * wl.table_bytes / 2);
     v.Dtab_df = (const dfloat*)(ws + wl.tables_df + (size_t)it.table * wl.table_bytes);
+    v.Wtab = (const double*)(ws + wl.tables_w + (size_t)it.table * wl.table_bytes);
+    v.Wtab_f = (const float*)(ws + wl.tables_wf + (size_t)it.table * wl.table_bytes / 2);
+    v.Wtab_df = (const dfloat*)(ws + wl.tables_wdf + (size_t)it.table * wl.table_bytes);
     const double lam0 = it.C0[0], mu0 = it.C0[1];
+    v.lam0 = lam0;
+    v.mu0 = mu0;
+    v.lam0f = (float)lam0;
+    v.mu0f = (float)mu0;
+    {  // 2 C0 : E on tensor components
+      double C0v[36], c0e[36];
+      memset(C0v, 0, sizeof(C0v));
+      for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) C0v[a * 6 + b] = lam0;
+        C0v[a * 6 + a] = lam0 + 2 * mu0;
+        C0v[(a + 3) * 6 + (a + 3)] = mu0;
+      }
+      voigt_to_tc(C0v, d, c0e);
+      for (int c = 0; c < 6; ++c) {
+        double acc = 0;
+        for (int q = 0; c < n_c && q < n_c; ++q) acc += c0e[c * n_c + q] * it.E[q];
+        v.twoC0E[c] = 2.0 * acc;
+      }
+    }
     v.c1 = 0.5 / mu0;
     v.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
     v.c1f = (float)v.c1;
@@ -417,6 +480,14 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
         g.tabs_df[(size_t)t * tstride + k] = make_float2(hi, (float)(v - (double)hi));
       }
   }
+  g.tabs_w.swap(tabs_w);
+  g.tabs_wf.assign(g.tabs_w.size(), 0.f);
+  g.tabs_wdf.assign(g.tabs_w.size(), make_float2(0.f, 0.f));
+  for (size_t k = 0; k < g.tabs_w.size(); ++k) {
+    const double v = g.tabs_w[k];
+    g.tabs_wf[k] = (float)v;
+    g.tabs_wdf[k] = make_float2((float)v, (float)(v - (double)(float)v));
+  }
   g.hdev.swap(hdev);
   g.glob0.arrivals = 0;
   g.glob0.active = n_items;
@@ -425,6 +496,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   CK(cudaMemcpyAsync(ws + wl.tables_f, g.tabs_f.data(), g.tabs_f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   if (g.kind != LAT_FP64)
     CK(cudaMemcpyAsync(ws + wl.tables_df, g.tabs_df.data(), g.tabs_df.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+  if (o.scheme == LAT_SCHEME_EYRE_MILTON) {
+    CK(cudaMemcpyAsync(ws + wl.tables_w, g.tabs_w.data(), g.tabs_w.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws + wl.tables_wf, g.tabs_wf.data(), g.tabs_wf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws + wl.tables_wdf, g.tabs_wdf.data(), g.tabs_wdf.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+  }
   CK(cudaMemcpyAsync(ws + wl.items, g.hdev.data(), g.hdev.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st));
   // device scalars start from zero; the batch starts with every item active
   CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)n_items * kScalBytes + kScalBytes, st));
@@ -450,6 +526,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ra.tn_stride = (int64_t)(wl.tn_per_lc / (fp32 ? 8 : 16));
     ra.mat.gscale = -1.0 / (double)m;
     ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
+    ra.mat.scheme = o.scheme;
     ra.it.partials = (double*)(ws + wl.partials);
     ra.it.pstride = wl.pstride;
     ra.it.scal = (ItemScal*)(ws + wl.scal);
@@ -475,7 +552,8 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns.  In the
     // increment form from a cold start (eps^(0) = E everywhere) k = 0 maps to 0 instead, so that T
     // holds the first increment G(E) - E and the binary32 rounding is relative to it, not to E
-    const bool incr_first = incr && !o.warm_start;
+    // (the Eyre-Milton cold start u = (C + C0) E varies in space, so its first step is taken in full)
+    const bool incr_first = incr && !o.warm_start && o.scheme == LAT_SCHEME_BASIC;
     RowArgs first = ra;
     first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
     first.mat.increment = incr_first ? 1 : 0;
@@ -674,6 +752,9 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.precision != LAT_FP64 && o.precision != LAT_MIXED && o.precision != LAT_DF64)
     return lat_fail(LAT_ERR_ARG, "bad precision");
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
+  if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON) return lat_fail(LAT_ERR_ARG, "bad scheme");
+  if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)
+    return lat_fail(LAT_ERR_ARG, "the Eyre-Milton scheme takes the averaged boundary treatment");
   return check_geometry(P, o.precision);
 }
 

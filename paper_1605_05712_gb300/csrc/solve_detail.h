@@ -26,7 +26,7 @@ struct Geometry {
 
 // byte offsets of the workspace regions of a batched solve
 struct Work {
-  size_t T, TN, items, tables, tables_f, tables_df, partials, scal, hist, total;
+  size_t T, TN, items, tables, tables_f, tables_df, tables_w, tables_wf, tables_wdf, partials, scal, hist, total;
   size_t T64, TN64;   // mixed precision: binary64 spectrum of the restart (0 bytes otherwise)
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
@@ -97,6 +97,9 @@ struct GroupRun {
   std::vector<double> tabs;     // host staging, alive until the stream is synchronized
   std::vector<float> tabs_f;
   std::vector<float2> tabs_df;
+  std::vector<double> tabs_w;   // (C + C0)^{-1} (Eyre-Milton)
+  std::vector<float> tabs_wf;
+  std::vector<float2> tabs_wdf;
   std::vector<ItemDev> hdev;
   std::vector<char> scal;       // host copy of the item scalars after the solve
   std::vector<double> hist;

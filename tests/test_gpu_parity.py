@@ -70,7 +70,7 @@ def test_lattice_fft_matches_oracle(cuda, M):
 
 
 def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=None, cuda=None, precision="fp64",
-             cell=None):
+             cell=None, scheme="basic"):
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
     P = lattice_plan(M)
@@ -87,7 +87,8 @@ def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=No
     if warm is not None:
         eps0 = torch.from_numpy(np.ascontiguousarray(warm)).to(cuda)
     g = basic_scheme_solve(P, torch.from_numpy(ph_plan).to(cuda), voigts, C0, E, tol=tol, maxit=maxit,
-                           boundary=boundary, history=True, want_sigma=True, eps0=eps0, precision=precision)
+                           boundary=boundary, history=True, want_sigma=True, eps0=eps0, precision=precision,
+                           scheme=scheme)
     g["precision"] = precision
     S = stiff_tensors(voigts, d)
     outs = []
@@ -98,7 +99,8 @@ def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=No
             w0 = np.empty((L.m, d, d))
             w0[perm] = comps_to_tensor(warm[lc], d)
         o = basic_scheme(L, ph_or, S, C0, Et, tol=tol, maxit=maxit, eps0=w0,
-                         boundary=("zero" if boundary == "zero" else "literal"), L=cell)
+                         boundary=("zero" if boundary == "zero" else "literal"), L=cell,
+                         scheme="eyre_milton" if scheme == "eyre_milton" else "basic")
         outs.append(o)
     return P, L, perm, g, outs
 
@@ -482,3 +484,46 @@ def test_transformed_aligned_laminate_is_analytic(cuda):
     eg = comps_to_tensor(g["eps"][0].cpu().numpy(), 2)
     assert relerr(eg, ex) < 1e-10
     assert relerr(el.comps_to_sym(g["sigma_bar"][0], 2), sb) < 1e-10
+
+
+# ---------------------------------------------------------------- Eyre-Milton iteration (scheme option)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", [[[16, 4], [0, 8]], [[512, 16], [0, 512]], [[64, 1], [0, 64]],
+                               [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]]])
+def test_eyre_milton_fixed_iterations(cuda, M, prec):
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    g = np.sqrt(10.0)
+    out = run_pair(M, inclusions(6, d, 3, 0.3), LAM2, (g, g), E, tol=0.0, maxit=5, cuda=cuda, precision=prec,
+                   scheme="eyre_milton")
+    check_pair(*out, d=d)
+
+
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+def test_eyre_milton_solution_and_iterations(cuda, M):
+    import torch
+    from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    ph = torch.from_numpy(inclusions(7, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+    k = 100.0
+    S = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(k, k)]
+    E = np.eye(P.n_c)[:2]
+    # same reference medium: the same discrete solution as Algorithm 1
+    b = basic_scheme_solve(P, ph, S, ((1 + k) / 2, (1 + k) / 2), E, tol=1e-11, maxit=20000)
+    e = basic_scheme_solve(P, ph, S, ((1 + k) / 2, (1 + k) / 2), E, tol=1e-11, maxit=20000, scheme="eyre_milton")
+    assert b["status"] == e["status"] == 0
+    assert float((b["eps"] - e["eps"]).abs().max() / b["eps"].abs().max()) < 1e-7
+    # at its own reference (geometric mean) it converges in a fraction of the iterations
+    b6 = basic_scheme_solve(P, ph, S, ((1 + k) / 2, (1 + k) / 2), E, tol=1e-6, maxit=20000)
+    e6 = basic_scheme_solve(P, ph, S, (np.sqrt(k), np.sqrt(k)), E, tol=1e-6, maxit=20000, scheme="eyre_milton")
+    assert int(e6["iters"].max()) < int(b6["iters"].max()) / 3
+    # mixed precision within the stated tolerances of its binary64 counterpart
+    m6 = basic_scheme_solve(P, ph, S, (np.sqrt(k), np.sqrt(k)), E, tol=1e-6, maxit=20000, scheme="eyre_milton",
+                            precision="mixed")
+    assert m6["status"] == 0
+    assert float((m6["eps"] - e6["eps"]).abs().max() / e6["eps"].abs().max()) <= MIXED_STRAIN_RTOL
+    assert np.abs(m6["sigma_bar"] - e6["sigma_bar"]).max() <= MIXED_CEFF_RTOL * np.abs(e6["sigma_bar"]).max()
+    with pytest.raises(LatticeError):
+        basic_scheme_solve(P, ph, S, (np.sqrt(k), np.sqrt(k)), E, tol=1e-6, maxit=10, scheme="eyre_milton",
+                           boundary="zero")
