@@ -12,7 +12,8 @@ Modules
 lattice     Smith normal form, pattern P(M), generating set G(M^T)  (Sec. 2.1-2.2)
 transform   Fourier matrix F(M): naive definition and separable FFT (Eq. Fouriermatrix)
 elasticity  isotropic stiffness, double contraction, Green operator  (Sec. 3.1)
-scheme      Algorithm 1, the fixed-point scheme on patterns          (Sec. 3.2)
+scheme      Algorithm 1, the fixed-point scheme on patterns          (Sec. 3.2),
+            and the accelerated schemes of Sec. 6 (Eyre-Milton, conjugate gradients)
 analytic    laminate and generalized Hashin closed forms            (Sec. 4)
 classic     independent Moulinec-Suquet scheme on a tensor grid     (Sec. 3.2, M diagonal)
 

@@ -90,6 +90,7 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
              max |c - c0| / (c + c0).  Each step: v = (C - C0) eps, u_hat = v_hat - 2 C0 Gamma0 v_hat
              (h != 0), u_hat_0 = v_hat_0 + 2 C0 E, u = Re F^{-1} u_hat, eps <- (C + C0)^{-1} u.  Its
              fixed point is Algorithm 1's.
+             'cg': conjugate gradients on the same discrete equation (``conjugate_gradient``).
     Returns dict(eps, sigma, sigma_bar, iters, history).
     """
     lat = M if isinstance(M, Lattice) else Lattice(M)
@@ -121,8 +122,11 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
         if boundary == 'zero':
             # zeroing eps_hat at the boundary frequencies has no counterpart in the u iteration
             raise ValueError("the Eyre-Milton scheme takes the literal (averaged) boundary treatment")
+    elif scheme == 'cg':
+        return conjugate_gradient(lat, phase, stiff, C0, E, tol, maxit, eps0=eps0, transform=transform,
+                                  boundary=boundary, L=L, C0_tensor=C0_tensor)
     elif scheme != 'basic':
-        raise ValueError("scheme must be 'basic' or 'eyre_milton'")
+        raise ValueError("scheme must be 'basic', 'eyre_milton' or 'cg'")
     while it < maxit:
         tau = _phase_ddot(dC, phase, eps)                              # polarization (v for Eyre-Milton)
         tau_hat = _transform(lat, tau, False, transform)               # F(M) tau
@@ -152,6 +156,89 @@ def basic_scheme(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None,
             break
     sigma = _phase_ddot(stiff, phase, eps)
     return dict(eps=eps, sigma=sigma, sigma_bar=sigma.mean(axis=0), iters=it, history=history)
+
+
+def conjugate_gradient(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None, transform='auto',
+                       boundary='literal', L=None, C0_tensor=None):
+    """Conjugate gradients on the discrete Lippmann-Schwinger equation (an accelerated scheme of the
+    kind Sec. 6 says carries over to patterns; the paper cites Zeman et al. 2010 for it).
+
+    With eps = E + e and e compatible with zero mean, Algorithm 1's fixed point solves
+    A e = b,  A = Gamma0 C,  b = -Gamma0 C E.
+    On the compatible zero-mean fields Gamma0 C0 is the identity, so <C0 A a, c> = <C a, c>: A is
+    self-adjoint and positive in the inner product <a, c>_C0 = sum_y a_y : C0 : c_y, and plain
+    (Hestenes-Stiefel) conjugate gradients apply in that inner product:
+        x = E, r = -Gamma0 C x, p = r
+        repeat: q = A p, alpha = <r, r>_C0 / <p, q>_C0, x += alpha p, r' = r - alpha q,
+                beta = <r', r'>_C0 / <r, r>_C0, p = r' + beta p, r = r'
+    r = -Gamma0 : sigma(x) is Algorithm 1's increment at x, so the stopping test takes Algorithm 1's
+    measure ||r|| / ||eps^(0)|| (l2 over the pattern of the Frobenius norm).  Every application of A
+    (one forward and one inverse transform) counts as one iteration; history[k] is the measure of the
+    k-th iterate, reached after k + 1 transforms.
+
+    Gamma0 C0 must be a projector at every frequency: ``boundary='zero'``, or 'literal' on a lattice
+    without boundary frequencies (every divisor odd).  A warm start is refused: the iterates stay in
+    eps^(0) + the compatible fields, so an incompatible part of eps^(0) would never be removed.
+    """
+    lat = M if isinstance(M, Lattice) else Lattice(M)
+    d, m = lat.d, lat.m
+    phase = np.asarray(phase, dtype=np.int64)
+    stiff = np.asarray(stiff, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    if eps0 is not None:
+        raise ValueError("the conjugate-gradient scheme starts from eps = E")
+    if C0_tensor is None:
+        lam0, mu0 = C0
+        C0t = el.iso_tensor(lam0, mu0, d)
+    else:
+        C0t = np.asarray(C0_tensor, dtype=np.float64)
+    h = lat.h.astype(np.float64)
+    if L is not None:
+        h = h @ np.linalg.inv(np.asarray(L, dtype=np.float64))
+    nz = np.any(lat.h != 0, axis=1)
+    bmask = boundary_mask(lat)
+    if boundary != 'zero' and bmask.any():
+        raise ValueError("the conjugate-gradient scheme needs boundary='zero' on lattices with boundary frequencies")
+
+    def apply_A(v):
+        """Gamma0 : (C : v) with the mean and the boundary frequencies set to zero."""
+        t_hat = _transform(lat, _phase_ddot(stiff, phase, v), False, transform)
+        out = np.zeros_like(t_hat)
+        if C0_tensor is None:
+            out[nz] = el.gamma_iso_apply(h[nz], t_hat[nz], lam0, mu0)
+        else:
+            out[nz] = el.gamma_general_apply(C0t, h[nz], t_hat[nz])
+        out[bmask] = 0.0
+        return _transform(lat, out, True, transform).real
+
+    def dot_c0(a, c):
+        return float(np.einsum('yij,ijkl,ykl->', a, C0t, c))
+
+    nE = np.sqrt(el.frob2(E))
+    norm0 = np.sqrt(m) * nE if nE > 0 else 1.0
+    x = np.broadcast_to(E, (m, d, d)).copy()
+    history = []
+    it = 0
+    if maxit > 0:
+        r = -apply_A(x)
+        it = 1
+        history.append(float(np.sqrt(el.frob2(r).sum()) / norm0))
+        p = r.copy()
+        gamma = dot_c0(r, r)
+        while not history[-1] < tol and it < maxit:
+            q = apply_A(p)
+            it += 1
+            delta = dot_c0(p, q)
+            alpha = gamma / delta if delta != 0 else 0.0
+            x = x + alpha * p
+            r = r - alpha * q
+            history.append(float(np.sqrt(el.frob2(r).sum()) / norm0))
+            gamma_new = dot_c0(r, r)
+            beta = gamma_new / gamma if gamma != 0 else 0.0
+            p = r + beta * p
+            gamma = gamma_new
+    sigma = _phase_ddot(stiff, phase, x)
+    return dict(eps=x, sigma=sigma, sigma_bar=sigma.mean(axis=0), iters=it, history=history)
 
 
 def _inverse_on_sym(C):
