@@ -145,7 +145,12 @@ def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
     for w in work:
         prec = mode.split("_")[0]                       # fp64, df64 or mixed
         em = mode.endswith("_em")                       # Eyre-Milton at the geometric-mean reference
-        if em:
+        if mode.endswith("_cg"):                        # conjugate gradients (boundary frequencies zeroed)
+            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
+                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES, scheme="cg",
+                                   boundary="zero")
+            its = [int(x) for x in g["iters"]]
+        elif em:
             g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0_EM, E, tol=tol, maxit=MAXIT, workspace=ws,
                                    eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES, scheme="eyre_milton")
             its = [int(x) for x in g["iters"]]
@@ -226,6 +231,7 @@ def bench_gpu(args):
     import torch
     import torch.distributed as dist
     from paper_1605_05712_gb300 import lattice_pass_times, synth
+    from paper_1605_05712_gb300.api import LAT_WS_CG
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -238,7 +244,8 @@ def bench_gpu(args):
     E = load_cases()
     work = setup(dev)
     m = work[0]["plan"].m
-    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1, 2)), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1, 2, 0 | LAT_WS_CG, 2 | LAT_WS_CG)),
+                     dtype=torch.uint8, device=dev)
     eps = torch.empty((3, 3, m), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
@@ -272,7 +279,7 @@ def bench_gpu(args):
             variants[mode] = {"value": round(u_v / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 4), "iterations": it_v}
         ttt = {}
         for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched", "fp64_batched_em",
-                     "mixed_batched_em"):
+                     "mixed_batched_em", "fp64_batched_cg", "df64_batched_cg"):
             run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6)
             ms_v, _, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6), args.steps, flush, st)
             ttt[mode] = {"ms": round(ms_v, 4), "iterations": it_v}
@@ -470,7 +477,8 @@ def bench_sweep(args):
         probs.append(dict(plan=P, phase=ph, stiffness=s_["stiffness"], C0=s_["C0"], E=s_["E"],
                           eps=torch.empty((len(s_["E"]), P.n_c, P.m), dtype=torch.float64, device=dev)))
     t_setup = time.perf_counter() - t0
-    ws = torch.empty(multi_workspace_bytes(probs, "mixed"), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(multi_workspace_bytes(probs, "mixed"), multi_workspace_bytes(probs, "df64", scheme="cg")),
+                     dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     res = {}
 
@@ -490,7 +498,12 @@ def bench_sweep(args):
         return basic_scheme_solve_multi(probs_em, tol=1e-6, maxit=5000, precision="mixed", workspace=ws,
                                         scheme="eyre_milton")
 
-    for name, fn in (("multi", run_multi), ("one_call_each", run_each), ("multi_eyre_milton", run_multi_em)):
+    def run_multi_cg():
+        return basic_scheme_solve_multi(probs, tol=1e-6, maxit=5000, precision="df64", workspace=ws, scheme="cg",
+                                        boundary="zero")
+
+    for name, fn in (("multi", run_multi), ("one_call_each", run_each), ("multi_eyre_milton", run_multi_em),
+                     ("multi_cg_df64", run_multi_cg)):
         fn()
         times = []
         for _ in range(max(1, args.steps)):

@@ -68,6 +68,11 @@ extern "C" {
 /* iteration (lat_solve_opts.scheme) */
 #define LAT_SCHEME_BASIC 0
 #define LAT_SCHEME_EYRE_MILTON 1
+#define LAT_SCHEME_CG 2
+/* OR into the precision argument of lattice_workspace_bytes, lattice_batch_workspace_bytes and
+   lattice_multi_workspace_bytes to size the workspace of a LAT_SCHEME_CG solve (four more
+   strain-sized vectors per load case) */
+#define LAT_WS_CG 256
 
 /* treatment of boundary frequencies of the symmetric cell (k with h(-k) != -h(k)) */
 #define LAT_BOUNDARY_AVERAGE 0  /* Gamma0 averaged over h(k) and -h(-k): the real part of the
@@ -165,7 +170,7 @@ int lattice_fft(const lat_plan* plan, const double* in, double* out, int n_field
                 int inverse, void* workspace, size_t workspace_bytes, void* stream);
 
 typedef struct lat_solve_opts {
-  int precision;        /* LAT_FP64 or LAT_MIXED */
+  int precision;        /* LAT_FP64, LAT_MIXED or LAT_DF64 */
   int boundary;         /* LAT_BOUNDARY_AVERAGE or LAT_BOUNDARY_ZERO */
   int warm_start;       /* 0: eps^(0) = E (Algorithm 1); 1: eps holds eps^(0) on entry */
   double* resid_history;/* host or NULL: n_loads * maxit residuals r_0, r_1, ... (rest untouched) */
@@ -188,7 +193,18 @@ typedef struct lat_solve_opts {
                            schemes carry over to patterns).  Same discrete solution as Algorithm 1
                            at the same C0, converging for any positive C0, fastest at the
                            geometric mean of the phase extremes (rate (sqrt(k)-1)/(sqrt(k)+1)
-                           against (k-1)/(k+1)).  Not with LAT_BOUNDARY_ZERO. */
+                           against (k-1)/(k+1)).  Not with LAT_BOUNDARY_ZERO.
+                           LAT_SCHEME_CG (2): conjugate gradients on the same discrete equation
+                           (Sec. 6; the paper cites Zeman et al. 2010) in the inner product
+                           sum_y a : C0 : c, where Gamma0 C is self-adjoint and positive on the
+                           compatible zero-mean fields.  Its residual r = -Gamma0 : sigma(eps) is
+                           Algorithm 1's increment, so tol means the same; one iteration is one
+                           forward and one inverse transform.  The solution does not depend on C0;
+                           iterations grow with the square root of the contrast.  LAT_FP64 or
+                           LAT_DF64 only, cold start only, and LAT_BOUNDARY_ZERO on lattices with an
+                           even largest divisor (there Gamma0 C0 is a projector only with the
+                           boundary frequencies zeroed); LAT_ERR_ARG otherwise.  The workspace
+                           query takes LAT_WS_CG. */
 } lat_solve_opts;
 
 /*

@@ -176,6 +176,11 @@ def conjugate_gradient(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None, 
     (one forward and one inverse transform) counts as one iteration; history[k] is the measure of the
     k-th iterate, reached after k + 1 transforms.
 
+    Rounding leaves every update a part outside the compatible fields of relative size ~u (the unit
+    roundoff); A annihilates that part, so once the residual is at the rounding level of the first one
+    the step lengths are undefined.  The iteration therefore also stops when ||r_k|| <= 1024 u ||r_0||
+    (u = 2^-53), which includes r_0 = 0 (E is then the exact discrete solution).
+
     Gamma0 C0 must be a projector at every frequency: ``boundary='zero'``, or 'literal' on a lattice
     without boundary frequencies (every divisor odd).  A warm start is refused: the iterates stay in
     eps^(0) + the compatible fields, so an incompatible part of eps^(0) would never be removed.
@@ -225,7 +230,8 @@ def conjugate_gradient(M, phase, stiff, C0, E, tol=1e-8, maxit=1000, eps0=None, 
         history.append(float(np.sqrt(el.frob2(r).sum()) / norm0))
         p = r.copy()
         gamma = dot_c0(r, r)
-        while not history[-1] < tol and it < maxit:
+        floor = 1024 * 2.0 ** -53 * history[0]
+        while not history[-1] < tol and it < maxit and not history[-1] <= floor:
             q = apply_A(p)
             it += 1
             delta = dot_c0(p, q)

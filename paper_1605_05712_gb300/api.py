@@ -17,8 +17,9 @@ from ._build import LIB
 
 LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED = 0, 1, 2
 LAT_ERR_ARG = -1
-LAT_SCHEME_BASIC, LAT_SCHEME_EYRE_MILTON = 0, 1
-_SCHEMES = {"basic": LAT_SCHEME_BASIC, "eyre_milton": LAT_SCHEME_EYRE_MILTON}
+LAT_SCHEME_BASIC, LAT_SCHEME_EYRE_MILTON, LAT_SCHEME_CG = 0, 1, 2
+_SCHEMES = {"basic": LAT_SCHEME_BASIC, "eyre_milton": LAT_SCHEME_EYRE_MILTON, "cg": LAT_SCHEME_CG}
+LAT_WS_CG = 256   # OR into the precision of a workspace query: room for the conjugate-gradient vectors
 LAT_FP64, LAT_MIXED, LAT_DF64 = 0, 1, 2
 LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO = 0, 1
 HIST_CAP = 4096
@@ -208,7 +209,11 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
                        boundary="average", eps0=None, want_sigma=False, history=False, workspace=None,
                        eps_out=None, stream=None, mixed_increment=True, plain_launches=False,
                        mixed_restart=True, scheme="basic"):
-    """Algorithm 1 on the GPU (scheme="eyre_milton": the accelerated iteration, same discrete solution).  Returns a dict of torch/numpy results.
+    """Algorithm 1 on the GPU.  Returns a dict of torch/numpy results.
+
+    scheme     "basic" (Algorithm 1), "eyre_milton" (accelerated fixed point, same discrete solution at
+               the same C0) or "cg" (conjugate gradients; fp64/df64, cold start, boundary "zero" on
+               lattices with an even largest divisor)
 
     phase      uint8 CUDA tensor (m,), plan order
     stiffness  (n_phases, 6, 6) Voigt matrices (host)
@@ -237,7 +242,7 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     if eps0 is not None and eps_out is not None:
         eps.copy_(eps0)
     sigma = torch.empty_like(eps) if want_sigma else None
-    wsb = plan.workspace_bytes(n_loads, prec)
+    wsb = plan.workspace_bytes(n_loads, prec | (LAT_WS_CG if scheme == "cg" else 0))
     ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
@@ -371,7 +376,7 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     L = lib()
     L.lattice_batch_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.lattice_batch_workspace_bytes.restype = ctypes.c_size_t
-    wsb = int(L.lattice_batch_workspace_bytes(plan.handle, n, prec))
+    wsb = int(L.lattice_batch_workspace_bytes(plan.handle, n, prec | (LAT_WS_CG if scheme == "cg" else 0)))
     ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
     sbar = np.zeros((n, plan.n_c))
     iters = np.zeros(n, dtype=np.int32)
@@ -455,7 +460,7 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     L = lib()
     L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
     L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
-    wsb = int(L.lattice_multi_workspace_bytes(items, n, prec))
+    wsb = int(L.lattice_multi_workspace_bytes(items, n, prec | (LAT_WS_CG if scheme == "cg" else 0)))
     if wsb == 0:
         raise LatticeError(LAT_ERR_ARG, "lattice_multi_workspace_bytes: invalid items")
     dev = problems[0]["phase"].device
@@ -472,7 +477,7 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     return rc, outs
 
 
-def multi_workspace_bytes(problems, precision="fp64"):
+def multi_workspace_bytes(problems, precision="fp64", scheme="basic"):
     """Workspace bytes basic_scheme_solve_multi needs for these problems."""
     n = len(problems)
     items = (_MultiItem * n)()
@@ -487,7 +492,8 @@ def multi_workspace_bytes(problems, precision="fp64"):
     L = lib()
     L.lattice_multi_workspace_bytes.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_int]
     L.lattice_multi_workspace_bytes.restype = ctypes.c_size_t
-    return int(L.lattice_multi_workspace_bytes(items, n, {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]))
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+    return int(L.lattice_multi_workspace_bytes(items, n, prec | (LAT_WS_CG if scheme == "cg" else 0)))
 
 
 def gather_map(src_plan, dst_plan):

@@ -366,6 +366,215 @@ __device__ __forceinline__ void kpair_index(int idx, int nlines, int lgRh, int& 
   }
 }
 
+// One row-pass block: rpc rows x n_c components of one item in shared memory, as complex slots (two
+// neighbouring real points per slot, bit-reversed after the forward FFT) plus the Nyquist value of
+// each line; T / TN are the item's spectrum planes.
+template <typename Real>
+struct RowTile {
+  typedef typename cplx_of<Real>::type C;
+  C* buf;
+  C* nyq;
+  C* T;
+  C* TN;
+  const C* tw;
+  int Rh, lgRh, lgR, rpc, lgrpc, nlines, npl_total, tw_log2;
+  int64_t r0, nrows;
+  uint32_t hm32;
+};
+
+template <typename Real>
+__device__ __forceinline__ RowTile<Real> make_row_tile(const LatDev& dv, const RowArgs& a, unsigned char* smem,
+                                                       int item_i, int n_c) {
+  typedef typename cplx_of<Real>::type C;
+  RowTile<Real> t;
+  t.Rh = dv.Rh;
+  t.lgRh = dv.log2Rh;
+  t.lgR = t.lgRh + 1;
+  t.rpc = a.rpc;
+  t.lgrpc = __ffs(a.rpc) - 1;
+  t.nlines = n_c * t.rpc;
+  // (line, k) pairs of the R2C pre/post-processing, k in [0, Rh/2]
+  t.npl_total = (t.nlines << (t.lgRh > 0 ? t.lgRh - 1 : 0)) + (t.Rh >= 2 ? t.nlines : 0);
+  t.tw_log2 = dv.tw_log2;
+  t.r0 = (int64_t)blockIdx.x * t.rpc;
+  t.nrows = dv.nrows;
+  t.hm32 = (uint32_t)(dv.m / 2);
+  t.buf = (C*)smem;
+  t.nyq = t.buf + (size_t)t.nlines * t.Rh;
+  t.T = (C*)a.T + item_i * a.t_stride;
+  t.TN = (C*)a.TN + item_i * a.tn_stride;
+  t.tw = (const C*)dv.tw;
+  return t;
+}
+
+// the block's rows of the half spectrum -> real rows: tile loads, inverse of the R2C post-processing
+// (X[0..Rh] -> Z = E + i O), inverse FFT
+template <typename Real>
+__device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
+  typedef typename cplx_of<Real>::type C;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Rh = t.Rh, lgRh = t.lgRh, rpc = t.rpc, lgrpc = t.lgrpc, nlines = t.nlines;
+  C* buf = t.buf;
+  C* nyq = t.nyq;
+  for (int idx = tid; idx < nlines * Rh; idx += nthr) {
+    const int line = idx >> lgRh, pos = idx & (Rh - 1);
+    const int c = line >> lgrpc, row = line & (rpc - 1);
+    cp_async_elem(buf + idx, t.T + ((uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos));
+  }
+  for (int idx = tid; idx < nlines; idx += nthr) {
+    const int c = idx >> lgrpc, row = idx & (rpc - 1);
+    cp_async_elem(nyq + idx, t.TN + (c * t.nrows + t.r0 + row));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int idx = tid; idx < t.npl_total; idx += nthr) {
+    int line, k;
+    kpair_index(idx, nlines, lgRh, line, k);
+    C* L = buf + (size_t)line * Rh;
+    if (k == 0) {
+      const Real X0 = L[0].x, XN = nyq[line].x;
+      L[0].x = X0 + XN;
+      L[0].y = X0 - XN;
+    } else {
+      const int kp = Rh - k;
+      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+      const C Xk = L[pk], Xkp = L[pkp];
+      const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
+      L[pk] = cadd(cadd(Xk, cconj(Xkp)), cmuli(cmulc(csub(Xk, cconj(Xkp)), wk)));
+      if (kp != k) {
+        const C wkp = twid(t.tw, t.tw_log2, t.lgR, kp);
+        L[pkp] = cadd(cadd(Xkp, cconj(Xk)), cmuli(cmulc(csub(Xkp, cconj(Xk)), wkp)));
+      }
+    }
+  }
+  __syncthreads();
+  fft_dit_inv(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+}
+
+// real rows (written by every thread before the call) -> forward FFT, R2C post-processing
+// X[k] = 1/2 (A - i W_R^k B), A = Z_k + conj Z_{Rh-k}, B = Z_k - conj Z_{Rh-k}, Gamma0 when the row is
+// the only logical axis (ROW_GAMMA), stores of the half spectrum and the Nyquist column
+template <typename Real, int NC>
+__device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const LatDev& dv, const RowArgs& a,
+                                                 const ItemDev* item) {
+  typedef typename cplx_of<Real>::type C;
+  constexpr int n_c = NC;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Rh = t.Rh, lgRh = t.lgRh, rpc = t.rpc, lgrpc = t.lgrpc, nlines = t.nlines;
+  C* buf = t.buf;
+  C* nyq = t.nyq;
+  __syncthreads();
+  fft_dif(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+  for (int idx = tid; idx < t.npl_total; idx += nthr) {
+    int line, k;
+    kpair_index(idx, nlines, lgRh, line, k);
+    C* L = buf + (size_t)line * Rh;
+    if (k == 0) {
+      const C Z0 = L[0];
+      L[0] = cpair<C>(Z0.x + Z0.y, Real(0));
+      nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
+    } else {
+      const int kp = Rh - k;
+      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+      const C Zk = L[pk], Zkp = L[pkp];
+      const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
+      const C A1 = cadd(Zk, cconj(Zkp)), B1 = csub(Zk, cconj(Zkp));
+      L[pk] = cscale(csub(A1, cmuli(cmul(B1, wk))), Real(0.5));
+      if (kp != k) {
+        const C wkp = twid(t.tw, t.tw_log2, t.lgR, kp);
+        const C A2 = cadd(Zkp, cconj(Zk)), B2 = csub(Zkp, cconj(Zk));
+        L[pkp] = cscale(csub(A2, cmuli(cmul(B2, wkp))), Real(0.5));
+      }
+    }
+  }
+  __syncthreads();
+  if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
+    const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+    for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
+      // k in [0, Rh) of every row first (shifts), then the Nyquist frequency k = Rh of each row
+      const int n_lo = rpc << lgRh;
+      const int row = idx < n_lo ? idx >> lgRh : idx - n_lo;
+      const int k = idx < n_lo ? (idx & (Rh - 1)) : Rh;
+      C val[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        const int line = c * rpc + row;
+        val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
+      }
+      int kk[LAT_MAX_AX] = {0};
+      kk[dv.nax - 1] = k;
+      green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        const int line = c * rpc + row;
+        if (k == Rh) nyq[line] = val[c];
+        else buf[(size_t)line * Rh + bitrev(k, lgRh)] = val[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nlines * Rh; idx += nthr) {
+    const int line = idx >> lgRh, pos = idx & (Rh - 1);
+    const int c = line >> lgrpc, row = line & (rpc - 1);
+    t.T[(uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos] = buf[idx];
+  }
+  for (int idx = tid; idx < nlines; idx += nthr) {
+    const int c = idx >> lgrpc, row = idx & (rpc - 1);
+    t.TN[c * t.nrows + t.r0 + row] = nyq[idx];
+  }
+}
+
+// per-item reduction of NV values over the blocks of grid.x: block sums go to
+// partials[v * gridDim.x + blockIdx.x]; the item's last block to arrive returns true on warp 0, with
+// the totals (summed in block order) in tot on lane 0; every other thread returns false
+template <int NV>
+__device__ __forceinline__ bool item_reduce(const double* v, double* partials, ItemScal* isc, double* red,
+                                            int* s_last, double* tot) {
+  double bs[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) bs[k] = block_sum(v[k], red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = bs[k];
+    __threadfence();
+    const unsigned t = atomicAdd(&isc->counter, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last || threadIdx.x >= 32) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = ordered_sum(partials + k * gridDim.x, gridDim.x);
+  return true;
+}
+
+// thread 0 of an item's last block: record residual r, decide the item's state (stop: end the
+// iteration whatever r is); the last item to report in this iteration recounts the active items and
+// sets the WHILE condition
+__device__ __forceinline__ void item_report(double r, ItemScal* isc, int item_i, const IterArgs& it,
+                                            bool stop = false) {
+  const int n = isc->iter + 1;
+  isc->iter = n;
+  if (n - 1 < LAT_HIST_CAP) it.hist[(size_t)item_i * LAT_HIST_CAP + n - 1] = r;
+  isc->last_r = r;
+  const bool cont = isfinite(r) && !(r < it.tol) && n < it.maxit && !stop;
+  isc->counter = 0u;
+  if (!cont) isc->done = ITEM_DONE;
+  else if (it.pause_tol > 0 && r < it.pause_tol) isc->done = ITEM_PAUSED;
+  else isc->done = ITEM_ACTIVE;
+  __threadfence();
+  GlobScal* gs = it.glob;
+  const unsigned arrived = atomicAdd(&gs->arrivals, 1u);
+  if ((int)arrived == *(volatile int*)&gs->active - 1) {  // every active item has reported
+    int active = 0;
+    for (int i = 0; i < it.n_items; ++i)
+      active += !*(volatile const int*)&((const ItemScal*)((const char*)it.scal + (size_t)i * 256))->done;
+    gs->active = active;
+    gs->arrivals = 0u;
+    if (it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)it.cond, active > 0 ? 1u : 0u);
+  }
+}
+
 // resident blocks of 256 threads per SM the register budget is cut for: binary32 4 (64 registers;
 // the pass is latency-bound and ran 18 % faster at 128^3 than with 80 registers and 3 blocks); the
 // others keep the budgets the compiler picks on its own (binary64 2-D 64, pairs 2-D 80, 3-D 128)
@@ -389,24 +598,18 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   } else if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) {
     return;  // this item finished (or paused) earlier
   }
-  C* buf = (C*)smem_raw;
-  C* nyq = buf + (size_t)nlines * Rh;
-  double* red = (double*)(nyq + nlines);
+  const RowTile<Real> tile = make_row_tile<Real>(dv, a, smem_raw, item_i, n_c);
+  C* buf = tile.buf;
+  double* red = (double*)(tile.nyq + nlines);
   __shared__ int s_last;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int64_t m = dv.m, R = dv.Rlen, half_m = m / 2, nrows = dv.nrows;
-  const int64_t r0 = (int64_t)blockIdx.x * rpc;
-  const uint32_t m32 = (uint32_t)m, hm32 = (uint32_t)half_m;
-  C* T = (C*)a.T + item_i * a.t_stride;
-  C* TN = (C*)a.TN + item_i * a.tn_stride;
+  const int64_t m = dv.m, R = dv.Rlen;
+  const int64_t r0 = tile.r0;
+  const uint32_t m32 = (uint32_t)m;
   double* eps = item->eps;
   const uint8_t* phase = item->phase;
   const double* Dtab = item->Dtab;
   const float* Dtab_f = item->Dtab_f;
-  const C* tw = (const C*)dv.tw;
-  const int tw_log2 = dv.tw_log2, lgR = lgRh + 1;
-  // (line, k) pairs of the R2C pre/post-processing, k in [0, Rh/2]
-  const int npl_total = (nlines << (lgRh > 0 ? lgRh - 1 : 0)) + (Rh >= 2 ? nlines : 0);
 
   if (a.flags & ROW_LOAD_EPS) {
     const bool eps_df = is_f32<Real> || is_df<Real> || (a.flags & ROW_EPS_DF);
@@ -426,40 +629,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     }
     __syncthreads();
   } else {
-    for (int idx = tid; idx < nlines * Rh; idx += nthr) {
-      const int line = idx >> lgRh, pos = idx & (Rh - 1);
-      const int c = line >> lgrpc, row = line & (rpc - 1);
-      cp_async_elem(buf + idx, T + ((uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos));
-    }
-    for (int idx = tid; idx < nlines; idx += nthr) {
-      const int c = idx >> lgrpc, row = idx & (rpc - 1);
-      cp_async_elem(nyq + idx, TN + (c * nrows + r0 + row));
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // half spectrum X[0..Rh] -> Z = E + i O (inverse of the R2C post-processing), in place
-    for (int idx = tid; idx < npl_total; idx += nthr) {
-      int line, k;
-      kpair_index(idx, nlines, lgRh, line, k);
-      C* L = buf + (size_t)line * Rh;
-      if (k == 0) {
-        const Real X0 = L[0].x, XN = nyq[line].x;
-        L[0].x = X0 + XN;
-        L[0].y = X0 - XN;
-      } else {
-        const int kp = Rh - k;
-        const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
-        const C Xk = L[pk], Xkp = L[pkp];
-        const C wk = twid(tw, tw_log2, lgR, k);
-        L[pk] = cadd(cadd(Xk, cconj(Xkp)), cmuli(cmulc(csub(Xk, cconj(Xkp)), wk)));
-        if (kp != k) {
-          const C wkp = twid(tw, tw_log2, lgR, kp);
-          L[pkp] = cadd(cadd(Xkp, cconj(Xk)), cmuli(cmulc(csub(Xkp, cconj(Xk)), wkp)));
-        }
-      }
-    }
-    __syncthreads();
-    fft_dit_inv(buf, lgRh, 0, nlines, tw, tw_log2);
+    row_tile_inverse<Real>(tile);
   }
 
   // pointwise: update, residual, polarization
@@ -611,106 +781,220 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
       buf[((size_t)c * rpc + row) * Rh + n] = cpair<C>(t0, t1);
     }
   }
-  __syncthreads();
-  fft_dif(buf, lgRh, 0, nlines, tw, tw_log2);
-  // R2C post-processing: X[k] = 1/2 (A - i W_R^k B), A = Z_k + conj Z_{Rh-k}, B = Z_k - conj Z_{Rh-k}
-  for (int idx = tid; idx < npl_total; idx += nthr) {
-    int line, k;
-    kpair_index(idx, nlines, lgRh, line, k);
-    C* L = buf + (size_t)line * Rh;
-    if (k == 0) {
-      const C Z0 = L[0];
-      L[0] = cpair<C>(Z0.x + Z0.y, Real(0));
-      nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
-    } else {
-      const int kp = Rh - k;
-      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
-      const C Zk = L[pk], Zkp = L[pkp];
-      const C wk = twid(tw, tw_log2, lgR, k);
-      const C A1 = cadd(Zk, cconj(Zkp)), B1 = csub(Zk, cconj(Zkp));
-      L[pk] = cscale(csub(A1, cmuli(cmul(B1, wk))), Real(0.5));
-      if (kp != k) {
-        const C wkp = twid(tw, tw_log2, lgR, kp);
-        const C A2 = cadd(Zkp, cconj(Zk)), B2 = csub(Zkp, cconj(Zk));
-        L[pkp] = cscale(csub(A2, cmuli(cmul(B2, wkp))), Real(0.5));
-      }
-    }
-  }
-  __syncthreads();
-  if (a.flags & ROW_GAMMA) {  // single logical axis: the row spectrum is the whole spectrum
-    const GreenK<Real> gk = green_consts<Real>(item, a.mat);
-    for (int idx = tid; idx < rpc * (Rh + 1); idx += nthr) {
-      // k in [0, Rh) of every row first (shifts), then the Nyquist frequency k = Rh of each row
-      const int n_lo = rpc << lgRh;
-      const int row = idx < n_lo ? idx >> lgRh : idx - n_lo;
-      const int k = idx < n_lo ? (idx & (Rh - 1)) : Rh;
-      C val[NC];
-#pragma unroll
-      for (int c = 0; c < n_c; ++c) {
-        const int line = c * rpc + row;
-        val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
-      }
-      int kk[LAT_MAX_AX] = {0};
-      kk[dv.nax - 1] = k;
-      green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
-#pragma unroll
-      for (int c = 0; c < n_c; ++c) {
-        const int line = c * rpc + row;
-        if (k == Rh) nyq[line] = val[c];
-        else buf[(size_t)line * Rh + bitrev(k, lgRh)] = val[c];
-      }
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < nlines * Rh; idx += nthr) {
-    const int line = idx >> lgRh, pos = idx & (Rh - 1);
-    const int c = line >> lgrpc, row = line & (rpc - 1);
-    T[(uint32_t)c * hm32 + (uint32_t)(r0 + row) * (uint32_t)Rh + (uint32_t)pos] = buf[idx];
-  }
-  for (int idx = tid; idx < nlines; idx += nthr) {
-    const int c = idx >> lgrpc, row = idx & (rpc - 1);
-    TN[c * nrows + r0 + row] = nyq[idx];
-  }
+  row_tile_forward<Real, NC>(tile, dv, a, item);
   if (!update) return;
   // residual: block partial -> the item's last block sums in block order and decides its
   // convergence; the last item to arrive in this iteration sets the WHILE condition
   double* partials = a.it.partials + item_i * a.it.pstride;
   dsum += ((double)dfs.hi + (double)dfs.lo) + 2.0 * ((double)dfs_shear.hi + (double)dfs_shear.lo);
   dsum += (double)dd_acc + 2.0 * (double)dd_shear;
-  const double bs = block_sum(dsum, red);
-  if (tid == 0) {
-    partials[blockIdx.x] = bs;
-    __threadfence();
-    const unsigned t = atomicAdd(&isc->counter, 1u);
-    s_last = (t == gridDim.x - 1);
+  double tot;
+  if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
+  if (tid == 0) item_report(sqrt(tot) / item->norm0, isc, item_i, a.it);
+}
+
+// ------------------------------------------------------------------ conjugate gradients
+// Conjugate gradients on the discrete Lippmann-Schwinger equation A e = -Gamma0 C E, A = Gamma0 C, for
+// the compatible zero-mean part e of the strain (one of the accelerated schemes Sec. 6 says carry over to
+// patterns).  On those fields Gamma0 C0 is the identity, so A is self-adjoint and positive in the inner
+// product <a, c>_C0 = sum_y a_y : C0 : c_y; the recurrences are the Chronopoulos-Gear form of CG, whose
+// two inner products come from one pass, so an iteration needs one reduction instead of two:
+//   p = r + beta p,  q = w + beta q,  x += alpha p,  r -= alpha q,  w = A r,
+//   gamma = <r, r>_C0, delta = <w, r>_C0, beta = gamma / gamma_prev,
+//   alpha = gamma / (delta - beta gamma / alpha_prev)        (first step: beta = 0, alpha = gamma / delta)
+// with q = A p carried by recurrence.  Rounding leaves each update a residual part outside the compatible
+// fields of relative size ~u (unit roundoff); A annihilates it, so once ||r|| falls to the rounding
+// level of ||r_0|| the step lengths are meaningless and the iteration stops: at ||r|| <= 1024 u ||r_0||
+// (u = 2^-53 in binary64, 2^-48 for the pairs), or at once when r_0 = 0 (E is the exact solution).
+// The transform maps a field v to -Gamma0 : (C : v) (the Green step
+// of Algorithm 1 with k = 0 mapped to 0), so r = -Gamma0 : sigma(x) is Algorithm 1's increment at x and
+// the stopping test takes its measure ||r|| / ||eps^(0)||.  The material tables hold C (not C - C0).
+// The vectors are held like the strain: binary64, or double-float pairs in the pair kernels.
+template <typename Real>
+__device__ __forceinline__ void fld_ld2(const double* p, Real& v0, Real& v1) {
+  if constexpr (is_df<Real>) {
+    const float4 o = *(const float4*)p;
+    v0 = dfloat(o.x, o.y);
+    v1 = dfloat(o.z, o.w);
+  } else {
+    const double2 o = *(const double2*)p;
+    v0 = (Real)o.x;
+    v1 = (Real)o.y;
   }
-  __syncthreads();
-  if (!s_last) return;
-  if (tid < 32) {
-    __threadfence();
-    const double s = ordered_sum(partials, gridDim.x);
-    if (tid == 0) {
-      const double r = sqrt(s) / item->norm0;
-      const int n = isc->iter + 1;
-      isc->iter = n;
-      if (n - 1 < LAT_HIST_CAP) a.it.hist[(size_t)item_i * LAT_HIST_CAP + n - 1] = r;
-      isc->last_r = r;
-      const bool cont = isfinite(r) && !(r < a.it.tol) && n < a.it.maxit;
-      isc->counter = 0u;
-      if (!cont) isc->done = ITEM_DONE;
-      else if (a.it.pause_tol > 0 && r < a.it.pause_tol) isc->done = ITEM_PAUSED;
-      else isc->done = ITEM_ACTIVE;
-      __threadfence();
-      GlobScal* gs = a.it.glob;
-      const unsigned arrived = atomicAdd(&gs->arrivals, 1u);
-      if ((int)arrived == *(volatile int*)&gs->active - 1) {  // every active item has reported
-        int active = 0;
-        for (int i = 0; i < a.it.n_items; ++i)
-          active += !*(volatile const int*)&((const ItemScal*)((const char*)a.it.scal + (size_t)i * 256))->done;
-        gs->active = active;
-        gs->arrivals = 0u;
-        if (a.it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.it.cond, active > 0 ? 1u : 0u);
+}
+template <typename Real>
+__device__ __forceinline__ void fld_st2(double* p, Real v0, Real v1) {
+  if constexpr (is_df<Real>) *(float4*)p = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+  else *(double2*)p = make_double2((double)v0, (double)v1);
+}
+// a : C0 : c for isotropic C0 on tensor components (shear components stored once, counted twice)
+template <typename Real, int NC>
+__device__ __forceinline__ Real c0_dot(const Real* a, const Real* c, Real lam0, Real two_mu0) {
+  constexpr int D = (NC == 6) ? 3 : 2;
+  Real ta = Real(0), tc = Real(0), s = Real(0), sh = Real(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ta += a[k];
+    tc += c[k];
+    s += a[k] * c[k];
+  }
+#pragma unroll
+  for (int k = D; k < NC; ++k) sh += a[k] * c[k];
+  return lam0 * (ta * tc) + two_mu0 * (s + (sh + sh));
+}
+template <typename Real, int NC>
+__device__ __forceinline__ Real frob2(const Real* a) {
+  constexpr int D = (NC == 6) ? 3 : 2;
+  Real s = Real(0), sh = Real(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += a[k] * a[k];
+#pragma unroll
+  for (int k = D; k < NC; ++k) sh += a[k] * a[k];
+  return s + (sh + sh);
+}
+
+// the update stage keeps five vectors of a point pair live: 3 blocks of 256 threads per SM (85 registers)
+// for 2-D, the row pass's budget for 3-D
+template <typename Real, int NC>
+constexpr int cg_min_blocks() {
+  return NC == 6 ? 2 : 3;
+}
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kernel(LatDev dv, RowArgs a, CgArgs cg) {
+  typedef typename cplx_of<Real>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int n_c = NC;
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
+  const int stage = cg.stage;
+  if (stage != CG_FWD_X && *(volatile const int*)&isc->done != ITEM_ACTIVE) return;
+  const RowTile<Real> tile = make_row_tile<Real>(dv, a, smem_raw, item_i, n_c);
+  const int Rh = tile.Rh, lgRh = tile.lgRh, rpc = tile.rpc;
+  C* buf = tile.buf;
+  double* red = (double*)(tile.nyq + tile.nlines);
+  __shared__ int s_last;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t m32 = (uint32_t)dv.m, R = (uint32_t)dv.Rlen;
+  const size_t voff = (size_t)item_i * cg.vstride;
+  double* x = item->eps;
+  double* r = cg.r + voff;
+  double* p = cg.p + voff;
+  double* q = cg.q + voff;
+  double* w = cg.w + voff;
+  const bool from_spectrum = (stage == CG_FULL0 || stage == CG_A);
+  if (from_spectrum) row_tile_inverse<Real>(tile);
+  Real alpha = Real(0), beta = Real(0);
+  if (stage == CG_B) {
+    alpha = Real(isc->cg_alpha);
+    beta = Real(isc->cg_beta);
+  }
+  const Real lam0 = Real(item->lam0), two_mu0 = Real(2.0 * item->mu0);
+  const Real* Ct;
+  if constexpr (is_df<Real>) Ct = (const Real*)item->Dtab_df;
+  else Ct = (const Real*)item->Dtab;
+  Real acc0 = Real(0), acc1 = Real(0);  // <r, r>_C0 (or <w, r>_C0) and ||r||^2
+  for (int idx = tid; idx < rpc * Rh; idx += nthr) {
+    const int row = idx >> lgRh, n = idx & (Rh - 1);
+    const uint32_t g = (uint32_t)(tile.r0 + row) * R + 2u * n;
+    Real v0[NC], v1[NC];
+    if (from_spectrum) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        const C z = buf[((size_t)c * rpc + row) * Rh + n];
+        v0[c] = z.x;
+        v1[c] = z.y;
       }
+    }
+    if (stage == CG_FWD_X) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) fld_ld2<Real>(x + (uint32_t)(c * m32) + g, v0[c], v1[c]);
+    } else if (stage == CG_FULL0) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) fld_st2<Real>(r + (uint32_t)(c * m32) + g, v0[c], v1[c]);
+      acc0 += c0_dot<Real, NC>(v0, v0, lam0, two_mu0) + c0_dot<Real, NC>(v1, v1, lam0, two_mu0);
+      acc1 += frob2<Real, NC>(v0) + frob2<Real, NC>(v1);
+    } else if (stage == CG_A) {
+      Real s0[NC], s1[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        v0[c] = -v0[c];
+        v1[c] = -v1[c];
+        fld_st2<Real>(w + (uint32_t)(c * m32) + g, v0[c], v1[c]);
+        fld_ld2<Real>(r + (uint32_t)(c * m32) + g, s0[c], s1[c]);
+      }
+      acc0 += c0_dot<Real, NC>(v0, s0, lam0, two_mu0) + c0_dot<Real, NC>(v1, s1, lam0, two_mu0);
+      continue;  // no polarization: the next stage starts from the updated vectors
+    } else {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        const uint32_t o = (uint32_t)(c * m32) + g;
+        Real r0, r1, p0, p1, q0, q1, w0, w1, x0, x1;
+        fld_ld2<Real>(r + o, r0, r1);
+        fld_ld2<Real>(p + o, p0, p1);
+        fld_ld2<Real>(q + o, q0, q1);
+        fld_ld2<Real>(w + o, w0, w1);
+        fld_ld2<Real>(x + o, x0, x1);
+        p0 = r0 + beta * p0;
+        p1 = r1 + beta * p1;
+        q0 = w0 + beta * q0;
+        q1 = w1 + beta * q1;
+        x0 = x0 + alpha * p0;
+        x1 = x1 + alpha * p1;
+        r0 = r0 - alpha * q0;
+        r1 = r1 - alpha * q1;
+        fld_st2<Real>(p + o, p0, p1);
+        fld_st2<Real>(q + o, q0, q1);
+        fld_st2<Real>(x + o, x0, x1);
+        fld_st2<Real>(r + o, r0, r1);
+        v0[c] = r0;
+        v1[c] = r1;
+      }
+      acc0 += c0_dot<Real, NC>(v0, v0, lam0, two_mu0) + c0_dot<Real, NC>(v1, v1, lam0, two_mu0);
+      acc1 += frob2<Real, NC>(v0) + frob2<Real, NC>(v1);
+    }
+    // tau = C : v for the next transform
+    const uchar2 ph = *(const uchar2*)(item->phase + g);  // g even
+    const Real* C0p = Ct + (int)ph.x * n_c * n_c;
+    const Real* C1p = Ct + (int)ph.y * n_c * n_c;
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) {
+      Real t0 = Real(0), t1 = Real(0);
+#pragma unroll
+      for (int k = 0; k < n_c; ++k) {
+        t0 += ldg_r(C0p + c * n_c + k) * v0[k];
+        t1 += ldg_r(C1p + c * n_c + k) * v1[k];
+      }
+      buf[((size_t)c * rpc + row) * Rh + n] = cpair<C>(t0, t1);
+    }
+  }
+  if (stage != CG_A) row_tile_forward<Real, NC>(tile, dv, a, item);
+  if (stage == CG_FWD_X) return;
+  double* partials = a.it.partials + item_i * a.it.pstride;
+  const double v[2] = {(double)acc0, (double)acc1};
+  double tot[2];
+  if (stage == CG_A) {
+    if (!item_reduce<1>(v, partials, isc, red, &s_last, tot)) return;
+    if (tid == 0) {
+      const double gam = isc->cg_gamma, delta = tot[0];
+      const bool first = (isc->iter == 1) || isc->cg_alpha_prev == 0.0 || isc->cg_gamma_prev == 0.0;
+      const double bet = first ? 0.0 : gam / isc->cg_gamma_prev;
+      const double den = first ? delta : delta - bet * gam / isc->cg_alpha_prev;
+      const double alp = (gam != 0.0 && den != 0.0) ? gam / den : 0.0;
+      isc->cg_alpha = alp;
+      isc->cg_beta = bet;
+      isc->cg_gamma_prev = gam;
+      isc->cg_alpha_prev = alp;
+      isc->counter = 0u;
+    }
+  } else {
+    if (!item_reduce<2>(v, partials, isc, red, &s_last, tot)) return;
+    if (tid == 0) {
+      const double rr = sqrt(tot[1]) / item->norm0;
+      const double floor_rel = is_df<Real> ? 0x1p-38 : 0x1p-43;  // 1024 u
+      if (stage == CG_FULL0) isc->cg_r0 = rr;
+      isc->cg_gamma = tot[0];
+      item_report(rr, isc, item_i, a.it, rr <= floor_rel * isc->cg_r0);
     }
   }
 }
@@ -958,6 +1242,17 @@ void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_item
   else row_pass_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
+void launch_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, int nthreads,
+                   size_t smem, cudaStream_t st) {
+  if constexpr (is_f32<Real>) {
+    return;  // the conjugate-gradient scheme runs in binary64 or on double-float pairs (checked on entry)
+  } else {
+    const dim3 grid(nblocks, n_items);
+    if (dv.n_c == 6) cg_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a, cg);
+    else cg_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a, cg);
+  }
+}
+template <typename Real>
 void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st) {
   const dim3 grid((unsigned)(a.outer * (a.tiles_main + a.tiles_nyq)), n_items);
   if (a.n_f == 6) col_pass_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
@@ -1053,6 +1348,9 @@ void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cu
 template void launch_row_pass<double>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
 template void launch_row_pass<float>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
 template void launch_row_pass<dfloat>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_cg_row<double>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_cg_row<float>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_cg_row<dfloat>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t, cudaStream_t);
 template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_col_pass<dfloat>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
@@ -1086,5 +1384,9 @@ int lat_kernel_attrs(size_t max_smem) {
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 6>, optin);
   if (e == cudaSuccess) e = set_smem(row_complex_kernel<double>, optin);
+  if (e == cudaSuccess) e = set_smem(cg_row_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(cg_row_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(cg_row_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = set_smem(cg_row_kernel<dfloat, 6>, optin);
   return e == cudaSuccess ? 0 : (int)e;
 }

@@ -56,6 +56,9 @@ struct ItemScal {
   unsigned eff_counter;  // last-block counter of the effective-stress kernel
   double last_r;         // last residual
   double sigma_bar[6];   // mean stress
+  // conjugate gradients: step lengths and <r, r>_C0 of the current and the previous iteration
+  double cg_alpha, cg_beta, cg_gamma, cg_gamma_prev, cg_alpha_prev;
+  double cg_r0;          // first residual (the rounding floor of the iteration is relative to it)
 };
 
 // Batch-wide device scalars
@@ -68,7 +71,7 @@ struct MatArgs {
   double gscale;         // -1/m: the forward 1/m of F(M) and the minus sign of the update
   int boundary_zero;
   int increment;         // 1: spectrum carries an increment, k = 0 gets 0 instead of E
-  int scheme;            // LAT_SCHEME_BASIC (Algorithm 1) or LAT_SCHEME_EYRE_MILTON
+  int scheme;            // Green step of LAT_SCHEME_BASIC (also conjugate gradients) or LAT_SCHEME_EYRE_MILTON
 };
 
 struct IterArgs {
@@ -118,6 +121,21 @@ struct ColArgs {
   int only_paused;       // with scal: process ITEM_PAUSED items only (restart passes)
 };
 
+// Conjugate-gradient row kernel stages
+#define CG_FWD_X 0   // tau = C : x, forward transform                                   (prologue)
+#define CG_FULL0 1   // r = -A x from the spectrum, <r, r>_C0, ||r||; tau = C : r, forward (prologue)
+#define CG_A 2       // w = A r from the spectrum, <w, r>_C0; step lengths alpha, beta
+#define CG_B 3       // p, q, x, r updates, <r, r>_C0, ||r||, convergence; tau = C : r, forward
+
+struct CgArgs {
+  double* r;             // per item (stride vstride): n_c planes of m, in the strain's storage
+  double* p;             // (binary64, or double-float pairs for the double-float kernels)
+  double* q;             // q = A p by recurrence
+  double* w;             // w = A r
+  int64_t vstride;       // doubles per item
+  int stage;             // CG_*
+};
+
 struct EffArgs {
   const ItemDev* items;
   double* partials;      // per item: blocks x n_c
@@ -128,6 +146,9 @@ struct EffArgs {
 template <typename Real>
 void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
                      cudaStream_t st);
+template <typename Real>
+void launch_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, int nthreads,
+                   size_t smem, cudaStream_t st);
 template <typename Real>
 void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st);
 void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st);

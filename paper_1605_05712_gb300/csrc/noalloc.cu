@@ -75,7 +75,7 @@ extern "C" int basic_scheme_solve_noalloc(const lat_plan* P, const uint8_t* phas
   if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
   const bool fp32 = (o.precision == LAT_MIXED);
   // scratch layout: [solve workspace | twiddle table | split twiddle table]
-  const Work wl = layout(P, n_loads, o.precision, n_phases, 1);
+  const Work wl = layout(P, n_loads, o.precision, n_phases, 1, o.scheme);
   int64_t n_tw = 0, n_stw = 0;
   if (P->nax > 0) lat_host_twiddles(P, o.precision, nullptr, nullptr, &n_tw, &n_stw);
   const size_t es = fp32 ? sizeof(float2) : o.precision == LAT_DF64 ? sizeof(float4) : sizeof(double2);

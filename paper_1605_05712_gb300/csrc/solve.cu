@@ -150,13 +150,14 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
   return LAT_OK;
 }
 
-Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables) {
+Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables, int scheme) {
   const int n_c = P->d * (P->d + 1) / 2;
   const size_t cs = (precision == LAT_MIXED) ? 8 : 16;
   Work w;
   w.t_per_lc = (size_t)n_c * (P->m / 2) * cs;
   w.tn_per_lc = (size_t)n_c * P->nrows * cs;
-  w.pstride = std::max<int64_t>(P->nrows, (int64_t)kEffBlocksMax * 6);
+  // two values per row block (conjugate gradients), n_c per block of the effective stress
+  w.pstride = std::max<int64_t>(2 * P->nrows, (int64_t)kEffBlocksMax * 6);
   w.table_bytes = (size_t)phases_per_table * n_c * n_c * sizeof(double);
   size_t off = 0;
   w.T = off;
@@ -191,6 +192,9 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
     w.TN64 = off;
     off = align256(off + (size_t)n_items * n_c * P->nrows * 16);
   }
+  w.cgv = off;
+  w.cg_stride = (int64_t)n_c * P->m;
+  if (scheme == LAT_SCHEME_CG) off = align256(off + (size_t)n_items * 4 * w.cg_stride * sizeof(double));
   w.total = off;
   return w;
 }
@@ -273,8 +277,25 @@ template void enqueue_col_group<dfloat>(const LatDev&, const lat_plan*, const Ge
 
 namespace {
 
-// adds a WHILE node to `top` after `dep` (or as a root): body = row pass (update, residual,
-// convergence; its last block sets the node's condition) + column passes
+// one iteration of a group: row pass (update, residual, convergence) + column passes; conjugate
+// gradients: update stage, column passes, the stage that forms w = A r and the step lengths
+template <typename Real>
+void enqueue_body(const GroupRun& g, const RowArgs& full, cudaStream_t st) {
+  if (g.cg) {
+    CgArgs cb = g.cga;
+    cb.stage = CG_B;
+    launch_cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+    enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
+    cb.stage = CG_A;
+    launch_cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+    return;
+  }
+  launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+  enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
+}
+
+// adds a WHILE node to `top` after `dep` (or as a root): body = one iteration (enqueue_body); the
+// last block of the convergence test sets the node's condition
 template <typename Real>
 int add_loop_node(const GroupRun& g, const RowArgs& body_row, cudaGraph_t top, const cudaGraphNode_t* dep,
                   cudaGraphConditionalHandle handle, cudaGraphNode_t* node_out) {
@@ -291,8 +312,7 @@ int add_loop_node(const GroupRun& g, const RowArgs& body_row, cudaGraph_t top, c
   if (ce == cudaSuccess) {
     RowArgs full = body_row;
     full.it.cond = (unsigned long long)handle;
-    launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, cap);
-    enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, cap);
+    enqueue_body<Real>(g, full, cap);
     cudaGraph_t captured = nullptr;
     ce = cudaStreamEndCapture(cap, &captured);
   }
@@ -306,8 +326,7 @@ template <typename Real>
 int plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream_t st) {
   RowArgs full = body_row;
   full.it.cond = 0;
-  launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
-  enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
+  enqueue_body<Real>(g, full, st);
   CK(cudaGetLastError());
   return LAT_OK;
 }
@@ -334,9 +353,34 @@ int enqueue_restart(const GroupRun& g, unsigned long long cond2, cudaStream_t st
 // the loops of one group in `top`: WHILE (with pause) [-> restart chain -> WHILE]
 int add_group_loops(const GroupRun& g, cudaGraph_t top) {
   cudaGraphConditionalHandle h1;
-  CK(cudaGraphConditionalHandleCreate(&h1, top, 1, cudaGraphCondAssignDefault));
   cudaGraphNode_t n1;
-  int rc = by_kind(g.kind, [&](auto tag) {
+  int rc = LAT_OK;
+  if (g.cg) {
+    // the conjugate-gradient prologue may already have stopped every item (a homogeneous medium, or
+    // maxit = 1): the loop's condition starts from the active count, set by a node before the loop
+    CK(cudaGraphConditionalHandleCreate(&h1, top, 0, cudaGraphCondAssignDefault));
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraphNode_t leaf = nullptr;
+    cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+      launch_set_cond(g.full.it.glob, (unsigned long long)h1, cap);
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaError_t ie = cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+      if (ie == cudaSuccess && nd == 1) leaf = deps[0];
+      cudaGraph_t captured = nullptr;
+      ce = cudaStreamEndCapture(cap, &captured);
+      if (ce == cudaSuccess && ie != cudaSuccess) ce = ie;
+    }
+    cudaStreamDestroy(cap);
+    if (ce != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("loop condition capture: ") + cudaGetErrorString(ce));
+    if (!leaf) return lat_fail(LAT_ERR_CUDA, "loop condition capture: no single leaf node");
+    return by_kind(g.kind, [&](auto tag) { return add_loop_node<decltype(tag)>(g, g.full, top, &leaf, h1, &n1); });
+  }
+  CK(cudaGraphConditionalHandleCreate(&h1, top, 1, cudaGraphCondAssignDefault));
+  rc = by_kind(g.kind, [&](auto tag) {
     return add_loop_node<decltype(tag)>(g, g.full, top, nullptr, h1, &n1);
   });
   if (rc != LAT_OK || !g.restart) return rc;
@@ -387,6 +431,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   g.loop = false;
   g.restart = false;
   g.want_hist = o.resid_history != nullptr && maxit > 0;
+  g.cg = (o.scheme == LAT_SCHEME_CG);
   // material tables: per table, D = C - C0 (binary64 and binary32) and C, in tensor-component form;
   // the reference medium is the table's (items sharing a table share C0)
   const int n_tables = (int)stiff.size();
@@ -414,7 +459,8 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       double* Dp = &tabs[(size_t)(2 * t) * tstride + (size_t)p * n_c * n_c];
       double* Cp = &tabs[(size_t)(2 * t + 1) * tstride + (size_t)p * n_c * n_c];
       voigt_to_tc(stiff[t] + 36 * p, d, Cp);
-      for (int k = 0; k < n_c * n_c; ++k) Dp[k] = Cp[k] - c0tc[k];
+      // conjugate gradients transform C : v, not the polarization (C - C0) : eps
+      for (int k = 0; k < n_c * n_c; ++k) Dp[k] = o.scheme == LAT_SCHEME_CG ? Cp[k] : Cp[k] - c0tc[k];
       if (o.scheme == LAT_SCHEME_EYRE_MILTON) {
         double S[36];
         for (int k = 0; k < n_c * n_c; ++k) S[k] = Cp[k] + c0tc[k];
@@ -526,7 +572,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ra.tn_stride = (int64_t)(wl.tn_per_lc / (fp32 ? 8 : 16));
     ra.mat.gscale = -1.0 / (double)m;
     ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
-    ra.mat.scheme = o.scheme;
+    ra.mat.scheme = o.scheme == LAT_SCHEME_EYRE_MILTON ? LAT_SCHEME_EYRE_MILTON : LAT_SCHEME_BASIC;
     ra.it.partials = (double*)(ws + wl.partials);
     ra.it.pstride = wl.pstride;
     ra.it.scal = (ItemScal*)(ws + wl.scal);
@@ -547,63 +593,101 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ca.scale = 1.0;
     ca.items = ditems;
     ca.mat = ra.mat;
-    const bool incr = fp32 && o.mixed_increment;
     const bool gamma_in_row = (P->nax == 1);
-    // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns.  In the
-    // increment form from a cold start (eps^(0) = E everywhere) k = 0 maps to 0 instead, so that T
-    // holds the first increment G(E) - E and the binary32 rounding is relative to it, not to E
-    // (the Eyre-Milton cold start u = (C + C0) E varies in space, so its first step is taken in full)
-    const bool incr_first = incr && !o.warm_start && o.scheme == LAT_SCHEME_BASIC;
-    RowArgs first = ra;
-    first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
-    first.mat.increment = incr_first ? 1 : 0;
-    ColArgs c0 = ca;
-    c0.scal = nullptr;
-    c0.mat.increment = incr_first ? 1 : 0;
-    g.full = ra;
-    g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) |
-                   (incr_first ? ROW_INCR_FIRST : 0);
-    g.full.mat.increment = incr ? 1 : 0;
-    g.cl = ca;
-    g.cl.scal = ra.it.scal;
-    g.cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
-    by_kind(g.kind, [&](auto tag) {
-      launch_row_pass<decltype(tag)>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
-      enqueue_columns<decltype(tag)>(dv, P, geo, c0, n_items, st);
-      return 0;
-    });
-    CK(cudaGetLastError());
-    g.loop = true;
-    // one binary64-accurate restart (double-float kernels) when an item's residual first falls below
-    // sqrt(tol): the increment recurrence accumulates binary32 rounding as a standing offset of the
-    // fixed point (it never re-evaluates G(eps)); the restart recomputes the increment exactly, and
-    // the iterations after it contract the offset
-    const double pause = sqrt(tol);
-    g.restart = incr && o.mixed_restart >= 0 && tol > 0 && pause > tol && maxit > 1;
-    if (g.restart) {
-      g.full.it.pause_tol = pause;
-      g.dv64 = make_dev(P, LAT_DF64);   // the restart runs on double-float pairs
-      memset(&g.geo64, 0, sizeof(g.geo64));
-      if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items, LAT_DF64)) != LAT_OK) return rc;
-      RowArgs r64 = ra;
-      r64.rpc = g.geo64.rpc;
-      r64.T = ws + wl.T64;
-      r64.TN = ws + wl.TN64;
-      r64.it.pause_tol = 0.0;
-      g.r_pro = r64;
-      g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
-      g.r_pro.mat.increment = 0;
-      g.r_upd = r64;
-      g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
-      g.r_upd.mat.increment = 1;
-      g.c64 = ca;
-      g.c64.T = r64.T;
-      g.c64.TN = r64.TN;
-      g.c64.scal = ra.it.scal;
-      g.c64.only_paused = 1;
-      g.c64.mat.increment = 0;
-      g.full2 = g.full;
-      g.full2.it.pause_tol = 0.0;
+    if (g.cg) {
+      // conjugate gradients (binary64 or double-float pairs): every transform maps v to
+      // -Gamma0 : (C : v) with k = 0 -> 0.  Prologue: r = -A x (x = E), then w = A r and the first
+      // step lengths; p and q start at 0 (the first update multiplies them by beta = 0)
+      ra.flags = gamma_in_row ? ROW_GAMMA : 0;
+      ra.mat.increment = 1;
+      ca.mat = ra.mat;
+      g.full = ra;
+      g.cl = ca;
+      g.cl.scal = ra.it.scal;
+      CgArgs cg;
+      memset(&cg, 0, sizeof(cg));
+      cg.vstride = wl.cg_stride;
+      cg.r = (double*)(ws + wl.cgv);
+      cg.p = cg.r + (size_t)n_items * wl.cg_stride;
+      cg.q = cg.p + (size_t)n_items * wl.cg_stride;
+      cg.w = cg.q + (size_t)n_items * wl.cg_stride;
+      g.cga = cg;
+      CK(cudaMemsetAsync(cg.p, 0, (size_t)2 * n_items * wl.cg_stride * sizeof(double), st));
+      ColArgs c0 = ca;
+      c0.scal = nullptr;
+      by_kind(g.kind, [&](auto tag) {
+        typedef decltype(tag) Real;
+        CgArgs cs = cg;
+        cs.stage = CG_FWD_X;
+        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        enqueue_columns<Real>(dv, P, geo, c0, n_items, st);
+        cs.stage = CG_FULL0;
+        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        enqueue_columns<Real>(dv, P, geo, g.cl, n_items, st);
+        cs.stage = CG_A;
+        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        return 0;
+      });
+      CK(cudaGetLastError());
+      g.loop = true;
+    } else {
+      const bool incr = fp32 && o.mixed_increment;
+      // prologue: tau^(0) from eps^(0), forward transform, Gamma (k = 0 -> E), inverse columns.  In the
+      // increment form from a cold start (eps^(0) = E everywhere) k = 0 maps to 0 instead, so that T
+      // holds the first increment G(E) - E and the binary32 rounding is relative to it, not to E
+      // (the Eyre-Milton cold start u = (C + C0) E varies in space, so its first step is taken in full)
+      const bool incr_first = incr && !o.warm_start && o.scheme == LAT_SCHEME_BASIC;
+      RowArgs first = ra;
+      first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
+      first.mat.increment = incr_first ? 1 : 0;
+      ColArgs c0 = ca;
+      c0.scal = nullptr;
+      c0.mat.increment = incr_first ? 1 : 0;
+      g.full = ra;
+      g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) |
+                     (incr_first ? ROW_INCR_FIRST : 0);
+      g.full.mat.increment = incr ? 1 : 0;
+      g.cl = ca;
+      g.cl.scal = ra.it.scal;
+      g.cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
+      by_kind(g.kind, [&](auto tag) {
+        launch_row_pass<decltype(tag)>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        enqueue_columns<decltype(tag)>(dv, P, geo, c0, n_items, st);
+        return 0;
+      });
+      CK(cudaGetLastError());
+      g.loop = true;
+      // one binary64-accurate restart (double-float kernels) when an item's residual first falls below
+      // sqrt(tol): the increment recurrence accumulates binary32 rounding as a standing offset of the
+      // fixed point (it never re-evaluates G(eps)); the restart recomputes the increment exactly, and
+      // the iterations after it contract the offset
+      const double pause = sqrt(tol);
+      g.restart = incr && o.mixed_restart >= 0 && tol > 0 && pause > tol && maxit > 1;
+      if (g.restart) {
+        g.full.it.pause_tol = pause;
+        g.dv64 = make_dev(P, LAT_DF64);   // the restart runs on double-float pairs
+        memset(&g.geo64, 0, sizeof(g.geo64));
+        if ((rc = geometry(P, n_c, 16, P->Rh, true, g.geo64, n_items, LAT_DF64)) != LAT_OK) return rc;
+        RowArgs r64 = ra;
+        r64.rpc = g.geo64.rpc;
+        r64.T = ws + wl.T64;
+        r64.TN = ws + wl.TN64;
+        r64.it.pause_tol = 0.0;
+        g.r_pro = r64;
+        g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
+        g.r_pro.mat.increment = 0;
+        g.r_upd = r64;
+        g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
+        g.r_upd.mat.increment = 1;
+        g.c64 = ca;
+        g.c64.T = r64.T;
+        g.c64.TN = r64.TN;
+        g.c64.scal = ra.it.scal;
+        g.c64.only_paused = 1;
+        g.c64.mat.increment = 0;
+        g.full2 = g.full;
+        g.full2.it.pause_tol = 0.0;
+      }
     }
   }
   g.ea.items = ditems;
@@ -752,9 +836,20 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.precision != LAT_FP64 && o.precision != LAT_MIXED && o.precision != LAT_DF64)
     return lat_fail(LAT_ERR_ARG, "bad precision");
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
-  if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON) return lat_fail(LAT_ERR_ARG, "bad scheme");
+  if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON && o.scheme != LAT_SCHEME_CG)
+    return lat_fail(LAT_ERR_ARG, "bad scheme");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)
     return lat_fail(LAT_ERR_ARG, "the Eyre-Milton scheme takes the averaged boundary treatment");
+  if (o.scheme == LAT_SCHEME_CG) {
+    if (o.precision == LAT_MIXED)
+      return lat_fail(LAT_ERR_ARG, "the conjugate-gradient scheme runs in LAT_FP64 or LAT_DF64");
+    if (o.warm_start) return lat_fail(LAT_ERR_ARG, "the conjugate-gradient scheme starts from eps = E");
+    // an even largest divisor means boundary frequencies, where the averaged Green operator is not a
+    // projector and the iteration operator is not self-adjoint
+    if (o.boundary == LAT_BOUNDARY_AVERAGE && P && P->ed % 2 == 0)
+      return lat_fail(LAT_ERR_ARG, "the conjugate-gradient scheme needs LAT_BOUNDARY_ZERO on lattices with an "
+                                   "even largest divisor (boundary frequencies)");
+  }
   return check_geometry(P, o.precision);
 }
 
@@ -796,14 +891,20 @@ using namespace latms_detail;
 
 void lat_graph_cache_free(lat_plan* P) { (void)P; }
 
+// the precision argument of the workspace queries: a precision, plus LAT_WS_CG for conjugate gradients
+static int ws_scheme(int precision) { return (precision & LAT_WS_CG) ? LAT_SCHEME_CG : LAT_SCHEME_BASIC; }
+static int ws_precision(int precision) { return precision & ~LAT_WS_CG; }
+
 extern "C" size_t lattice_workspace_bytes(const lat_plan* P, int n_loads, int precision) {
-  if (!P || n_loads <= 0 || check_geometry(P, precision) != LAT_OK) return 0;
-  return layout(P, n_loads, precision, kMaxPhases, 1).total;
+  const int prec = ws_precision(precision);
+  if (!P || n_loads <= 0 || check_geometry(P, prec) != LAT_OK) return 0;
+  return layout(P, n_loads, prec, kMaxPhases, 1, ws_scheme(precision)).total;
 }
 
 extern "C" size_t lattice_batch_workspace_bytes(const lat_plan* P, int n_items, int precision) {
-  if (!P || n_items <= 0 || check_geometry(P, precision) != LAT_OK) return 0;
-  return layout(P, n_items, precision, LAT_BATCH_MAX_PHASES, n_items).total;
+  const int prec = ws_precision(precision);
+  if (!P || n_items <= 0 || check_geometry(P, prec) != LAT_OK) return 0;
+  return layout(P, n_items, prec, LAT_BATCH_MAX_PHASES, n_items, ws_scheme(precision)).total;
 }
 
 extern "C" size_t lattice_fft_workspace_bytes(const lat_plan* P, int n_fields) {
@@ -826,7 +927,7 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   if (opts) o = *opts;
   if (int rc = check_common(P, tol, maxit, o)) return rc;
   if (int rc = check_c0(C0)) return rc;
-  const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1);
+  const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1, o.scheme);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
   if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
@@ -868,7 +969,7 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
     stiff[i] = b.stiffness;
     nph[i] = b.n_phases;
   }
-  const Work wl = layout(P, n_items, o.precision, LAT_BATCH_MAX_PHASES, n_items);
+  const Work wl = layout(P, n_items, o.precision, LAT_BATCH_MAX_PHASES, n_items, o.scheme);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
@@ -911,9 +1012,10 @@ extern "C" size_t lattice_multi_workspace_bytes(const lat_multi_item* items, int
   std::vector<MultiGroup> groups;
   if (multi_groups(items, n_items, groups) != LAT_OK) return 0;
   size_t total = 0;
+  const int prec = ws_precision(precision), scheme = ws_scheme(precision);
   for (const MultiGroup& g : groups) {
-    if (check_geometry(g.P, precision) != LAT_OK) return 0;
-    total += align256(layout(g.P, g.n_loads, precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size()).total);
+    if (check_geometry(g.P, prec) != LAT_OK) return 0;
+    total += align256(layout(g.P, g.n_loads, prec, LAT_BATCH_MAX_PHASES, (int)g.inst.size(), scheme).total);
   }
   return total;
 }
@@ -928,7 +1030,8 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
   if (o.resid_history) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_multi: residual histories are not kept");
   std::vector<MultiGroup> mg;
   if (int rc = multi_groups(items, n_items, mg)) return rc;
-  if (workspace_bytes < lattice_multi_workspace_bytes(items, n_items, o.precision))
+  if (workspace_bytes <
+      lattice_multi_workspace_bytes(items, n_items, o.precision | (o.scheme == LAT_SCHEME_CG ? LAT_WS_CG : 0)))
     return lat_fail(LAT_ERR_SIZE, "workspace too small");
   for (int i = 0; i < n_items; ++i) {
     if (int rc = check_c0(items[i].C0)) return rc;
@@ -965,7 +1068,7 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
       stiff.push_back(b.stiffness);
       nph.push_back(b.n_phases);
     }
-    const Work wl = layout(g.P, g.n_loads, o.precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size());
+    const Work wl = layout(g.P, g.n_loads, o.precision, LAT_BATCH_MAX_PHASES, (int)g.inst.size(), o.scheme);
     const LatDev dv = make_dev(g.P, o.precision);
     if (int rc = group_prepare(g.P, its, stiff, nph, tol, maxit, o, ws + off, wl, dv, runs[k], st)) return rc;
     off += align256(wl.total);

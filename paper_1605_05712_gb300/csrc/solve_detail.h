@@ -28,6 +28,8 @@ struct Geometry {
 struct Work {
   size_t T, TN, items, tables, tables_f, tables_df, tables_w, tables_wf, tables_wdf, partials, scal, hist, total;
   size_t T64, TN64;   // mixed precision: binary64 spectrum of the restart (0 bytes otherwise)
+  size_t cgv;         // conjugate gradients: r, p, q, w per item (0 bytes otherwise)
+  int64_t cg_stride;  // doubles per vector and item (n_c m)
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
 };
@@ -60,7 +62,9 @@ size_t align256(size_t x);
 template <typename Real>
 void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs c, int k, int mode,
                        int n_items, cudaStream_t st);
-Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables);
+// scheme = LAT_SCHEME_CG adds the four vectors of the conjugate-gradient iteration
+Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables,
+            int scheme = LAT_SCHEME_BASIC);
 void voigt_to_tc(const double* V, int d, double* out);
 template <typename Real>
 void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,
@@ -80,6 +84,8 @@ struct GroupRun {
   LatDev dv;
   Geometry geo;
   RowArgs full;       // loop body row pass (with the pause level when a restart follows)
+  bool cg;            // conjugate gradients: the loop body is cg_row(B), columns, cg_row(A)
+  CgArgs cga;
   ColArgs cl;
   // restart of the increment form on double-float pairs (binary64-accurate): prologue of the paused
   // items (r_pro, c64), update whose polarization is of the exact increment (r_upd), cast of the

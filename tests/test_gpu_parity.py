@@ -5,6 +5,8 @@ Tolerances: the binary64 path must agree with the oracle to 1e-10 relative
 iteration count of a converged solve must match exactly unless the oracle's
 residual at the stopping iteration lies within 1e-6 relative of tol.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -100,12 +102,12 @@ def run_pair(M, phase_fn, voigts, C0, E, tol, maxit, boundary="average", warm=No
             w0[perm] = comps_to_tensor(warm[lc], d)
         o = basic_scheme(L, ph_or, S, C0, Et, tol=tol, maxit=maxit, eps0=w0,
                          boundary=("zero" if boundary == "zero" else "literal"), L=cell,
-                         scheme="eyre_milton" if scheme == "eyre_milton" else "basic")
+                         scheme=scheme)
         outs.append(o)
     return P, L, perm, g, outs
 
 
-def check_pair(P, L, perm, g, outs, d, rtol=RTOL, check_iters=True, tol=0.0):
+def check_pair(P, L, perm, g, outs, d, rtol=RTOL, check_iters=True, tol=0.0, hist_atol=None):
     for lc, o in enumerate(outs):
         eg = comps_to_tensor(g["eps"][lc].cpu().numpy(), d)
         assert relerr(eg, o["eps"][perm]) < rtol, "strain field"
@@ -122,6 +124,8 @@ def check_pair(P, L, perm, g, outs, d, rtol=RTOL, check_iters=True, tol=0.0):
         # absolute floor: the strain's rounding, relative to the normalisation sqrt(m) |E| of r -- 2^-53 in
         # binary64, 2^-48 for double-float pairs (seen once the increments are ~1e-8 of the strain)
         atol = 1e-13 if g.get("precision") == "df64" else 1e-15
+        if hist_atol is not None:
+            atol = hist_atol
         assert np.all(np.abs(hg - ho) <= 1e-9 * np.maximum(ho, 1e-14) + atol), "residual history"
 
 
@@ -527,3 +531,112 @@ def test_eyre_milton_solution_and_iterations(cuda, M):
     with pytest.raises(LatticeError):
         basic_scheme_solve(P, ph, S, (np.sqrt(k), np.sqrt(k)), E, tol=1e-6, maxit=10, scheme="eyre_milton",
                            boundary="zero")
+
+
+# ---------------------------------------------------------------- conjugate gradients (scheme option)
+# the rank-1 lattices with one point along x2 sample a line that misses the inclusions: a laminate there,
+# with f1 = 3/10 (at f1 = 1/2 the square wave excites only odd harmonics, the boundary frequencies of
+# these lattices, which are zeroed)
+CG_MATS = [[[16, 4], [0, 8]], [[256, 16], [0, 256]], [[64, 32], [0, 1]], [[4096, 12288], [0, 1]],
+           [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]], [[2, 0], [0, 1]]]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", CG_MATS)
+def test_cg_fixed_iterations(cuda, M, prec):
+    # the oracle runs Hestenes-Stiefel CG, the kernels the Chronopoulos-Gear recurrences: equal iterates
+    # up to rounding; [[2,0],[0,1]] converges at once and stops at the rounding floor on both sides
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    ph = ((lambda p, m: synth.laminate_phase(p, m, [1, 3], Fraction(3, 10))) if d == 2 and M[1][1] == 1
+          else inclusions(6, d, 3, 0.3))
+    out = run_pair(M, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=6, cuda=cuda, precision=prec,
+                   scheme="cg", boundary="zero")
+    # a residual at the rounding floor (<= 1024 u r_0) is rounding noise on both sides
+    check_pair(*out, d=d, hist_atol=1e-13)
+
+
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+def test_cg_solution_and_iterations(cuda, M):
+    import torch
+    from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    ph = torch.from_numpy(inclusions(7, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+    k = 100.0
+    S = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(k, k)]
+    E = np.eye(P.n_c)[:2]
+    C0 = ((1 + k) / 2, (1 + k) / 2)
+    # Algorithm 1's discrete solution (boundary frequencies zeroed, where it does not depend on C0)
+    b = basic_scheme_solve(P, ph, S, C0, E, tol=1e-11, maxit=20000, boundary="zero")
+    c = basic_scheme_solve(P, ph, S, C0, E, tol=1e-11, maxit=2000, boundary="zero", scheme="cg")
+    c2 = basic_scheme_solve(P, ph, S, (1.0, 3.0), E, tol=1e-11, maxit=2000, boundary="zero", scheme="cg")
+    cd = basic_scheme_solve(P, ph, S, C0, E, tol=1e-11, maxit=2000, boundary="zero", scheme="cg", precision="df64")
+    assert b["status"] == c["status"] == c2["status"] == cd["status"] == 0
+    scale = float(b["eps"].abs().max())
+    assert float((b["eps"] - c["eps"]).abs().max()) / scale < 1e-7
+    assert float((c2["eps"] - c["eps"]).abs().max()) / scale < 1e-7
+    assert float((cd["eps"] - c["eps"]).abs().max()) / scale < 1e-9
+    assert np.abs(c["sigma_bar"] - b["sigma_bar"]).max() < 1e-7 * np.abs(b["sigma_bar"]).max()
+    # far fewer transforms to the same tolerance
+    b6 = basic_scheme_solve(P, ph, S, C0, E, tol=1e-6, maxit=20000, boundary="zero")
+    c6 = basic_scheme_solve(P, ph, S, C0, E, tol=1e-6, maxit=2000, boundary="zero", scheme="cg")
+    assert int(c6["iters"].max()) < int(b6["iters"].max()) / 4
+    for kw in (dict(precision="mixed", boundary="zero"), dict(boundary="average"),
+               dict(boundary="zero", eps0=c6["eps"].clone())):
+        with pytest.raises(LatticeError):
+            basic_scheme_solve(P, ph, S, C0, E, tol=1e-6, maxit=10, scheme="cg", **kw)
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_cg_stops_in_the_prologue(cuda, plain):
+    # a homogeneous medium has r = 0 after the first transform: one iteration, eps = E, and the loop that
+    # follows the prologue must not run (its condition starts from the active count)
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan([[64, 8], [0, 32]])
+    E = np.array([[0.3, -0.2, 0.1], [1.0, 0.0, 0.0]])
+    zero = torch.zeros(P.m, dtype=torch.uint8, device=cuda)
+    g = basic_scheme_solve(P, zero, [synth.iso_voigt(3.0, 2.0)], (1.0, 0.5), E, tol=1e-12, maxit=50,
+                           boundary="zero", scheme="cg", plain_launches=plain, history=True)
+    assert g["status"] == 0 and np.all(g["iters"] == 1)
+    for lc in range(2):
+        assert float((g["eps"][lc] - torch.tensor(E[lc], device=cuda)[:, None]).abs().max()) < 1e-14
+    # maxit = 1 stops after the prologue too
+    ph = torch.from_numpy(inclusions(2, 2, 3, 0.3)(P.points(), P.m)).to(cuda)
+    g1 = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-12, maxit=1, boundary="zero", scheme="cg",
+                            plain_launches=plain)
+    assert g1["status"] == 1 and np.all(g1["iters"] == 1)
+
+
+def test_cg_batch_and_multi(cuda):
+    # a batch where one item stops in the prologue and the others iterate; a multi call over two plans
+    # equals its single solves bitwise, with the graph loop and with plain launches
+    import torch
+    from paper_1605_05712_gb300 import (basic_scheme_solve, basic_scheme_solve_batch, basic_scheme_solve_multi,
+                                        lattice_plan)
+    P = lattice_plan([[128, 8], [0, 64]])
+    phs = [torch.from_numpy(inclusions(s, 2, 3, 0.3)(P.points(), P.m)).to(cuda) for s in (1, 2)]
+    phs.append(torch.zeros(P.m, dtype=torch.uint8, device=cuda))
+    Es = np.array([[1.0, 0.0, 0.0], [0.2, 0.5, -0.3], [0.4, 0.1, 0.2]])
+    bt = basic_scheme_solve_batch(P, phs, [LAM2] * 3, [(5.5, 5.5)] * 3, Es, tol=1e-9, maxit=500, boundary="zero",
+                                  scheme="cg")
+    assert bt["status"] == 0 and bt["iters"][2] == 1 and bt["iters"][0] > 5
+    for i in range(3):
+        s = basic_scheme_solve(P, phs[i], LAM2, (5.5, 5.5), Es[i:i + 1], tol=1e-9, maxit=500, boundary="zero",
+                               scheme="cg")
+        assert int(s["iters"][0]) == int(bt["iters"][i])
+        assert float((s["eps"][0] - bt["eps"][i]).abs().max()) <= 1e-12 * float(s["eps"].abs().max())
+    P2 = lattice_plan([[8, 1, 0], [0, 8, 1], [0, 0, 16]])
+    ph2 = torch.from_numpy(inclusions(4, 3, 2, 0.25)(P2.points(), P2.m)).to(cuda)
+    probs = [dict(plan=P, phase=phs[0], stiffness=LAM2, C0=(5.5, 5.5), E=Es[:2]),
+             dict(plan=P2, phase=ph2, stiffness=LAM2, C0=(2.0, 3.0), E=np.eye(6)[:2])]
+    rc, outs = basic_scheme_solve_multi(probs, tol=1e-9, maxit=500, boundary="zero", scheme="cg")
+    rc_p, outs_p = basic_scheme_solve_multi(probs, tol=1e-9, maxit=500, boundary="zero", scheme="cg",
+                                            plain_launches=True)
+    assert rc == rc_p == 0
+    for pb, o, op in zip(probs, outs, outs_p):
+        single = basic_scheme_solve(pb["plan"], pb["phase"], pb["stiffness"], pb["C0"], pb["E"], tol=1e-9,
+                                    maxit=500, boundary="zero", scheme="cg")
+        assert np.array_equal(o["iters"], single["iters"]) and np.array_equal(o["iters"], op["iters"])
+        assert torch.equal(o["eps"], single["eps"]) and torch.equal(o["eps"], op["eps"])

@@ -10,7 +10,8 @@ product), against Algorithm 1 and against properties fixed by the mathematics of
 - the strain energy 1/2 <C x, x> falls monotonically (the iterates minimise it over growing Krylov
   spaces);
 - homogeneous media need one transform; the aligned laminate is exact; high contrast needs far fewer
-  iterations than Algorithm 1.
+  iterations than Algorithm 1;
+- the iteration stops at the rounding floor instead of amplifying rounding noise.
 """
 import numpy as np
 import pytest
@@ -137,3 +138,15 @@ def test_refusals():
     with pytest.raises(ValueError):
         conjugate_gradient(L, ph, S, (5.5, 5.5), E, boundary='zero', eps0=np.zeros((L.m, 2, 2)))
     assert basic_scheme(L, ph, S, (5.5, 5.5), E, tol=1e-6, scheme='cg', boundary='zero')["iters"] > 1
+
+
+def test_stops_at_the_rounding_floor():
+    # homogeneous medium, tol = 0: r_0 is rounding noise.  Past the floor the step lengths divide noise
+    # by noise (A annihilates the incompatible rounding in r) and the iterate drifts by O(1); the
+    # iteration must stop there and keep eps = E to rounding
+    L = Lattice([[16, 4], [0, 8]])
+    E = np.array([[1.1, 0.1], [0.1, 0.1]])
+    S = np.array([el.iso_tensor(1, 1, 2), el.iso_tensor(10, 10, 2)])
+    c = conjugate_gradient(L, np.zeros(L.m, int), S, (5.5, 5.5), E, tol=0.0, maxit=20, boundary='zero')
+    assert c["iters"] <= 2
+    assert np.abs(c["eps"] - E).max() < 1e-14
