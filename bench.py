@@ -347,6 +347,7 @@ def bench_hashin(args):
     the plain binary64 form on the same inputs; C^eff eps0 against the analytic value."""
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan, synth
+    from paper_1605_05712_gb300.api import LAT_WS_CG
     dev = torch.device("cuda", 0)
     w = synth.hashin_workload()
     E = np.eye(6)
@@ -364,14 +365,21 @@ def bench_hashin(args):
                                                             R=w["R"])).to(dev)
         eps = torch.empty((6, 6, P.m), dtype=torch.float64, device=dev)
         res = {}
-        for prec in ("mixed", "df64", "fp64"):
-            ws = torch.empty(P.workspace_bytes(6, {"fp64": 0, "mixed": 1, "df64": 2}[prec]), dtype=torch.uint8,
-                             device=dev)
-            run = lambda: basic_scheme_solve(P, ph, w["stiffness"], w["C0"], E, tol=1e-6, maxit=2000,
-                                             precision=prec, workspace=ws, eps_out=eps)
+        # forms: Algorithm 1 in each precision; the accelerated schemes (Eyre-Milton at the geometric mean
+        # of the core and coating moduli, conjugate gradients with the boundary frequencies zeroed)
+        g_mean = float(np.sqrt(10.0 * 1.0))
+        forms = {"mixed": ("mixed", w["C0"], {}), "df64": ("df64", w["C0"], {}), "fp64": ("fp64", w["C0"], {}),
+                 "eyre_milton_mixed": ("mixed", (g_mean, g_mean), {"scheme": "eyre_milton"}),
+                 "cg_df64": ("df64", w["C0"], {"scheme": "cg", "boundary": "zero"})}
+        for form, (prec, C0f, kw) in forms.items():
+            flag = LAT_WS_CG if kw.get("scheme") == "cg" else 0
+            ws = torch.empty(P.workspace_bytes(6, {"fp64": 0, "mixed": 1, "df64": 2}[prec] | flag),
+                             dtype=torch.uint8, device=dev)
+            run = lambda: basic_scheme_solve(P, ph, w["stiffness"], C0f, E, tol=1e-6, maxit=2000,
+                                             precision=prec, workspace=ws, eps_out=eps, **kw)
             for _ in range(args.warmup if prec == "mixed" else 1):
                 g = run()
-            steps = args.steps if prec == "mixed" else 1
+            steps = args.steps if form == "mixed" else 1
             last = {}
 
             def step():
@@ -381,16 +389,17 @@ def bench_hashin(args):
             ms, units, _ = timed(step, steps, flush, st)
             g = last["g"]
             ce = (g["sigma_bar"].T @ e0)
-            res[prec] = {"ms": round(ms, 3), "value": round(units / (ms / 1e3), 1),
+            res[form] = {"ms": round(ms, 3), "value": round(units / (ms / 1e3), 1),
                          "iterations": [int(x) for x in g["iters"]],
                          "ceff_eps0_rel_err_vs_analytic": float(np.linalg.norm(ce - ce_ref) / np.linalg.norm(ce_ref)),
                          "sigma_bar": g["sigma_bar"].tolist()}
             del ws
-        sb_m, sb_d = np.array(res["mixed"]["sigma_bar"]), np.array(res["fp64"]["sigma_bar"])
-        res["mixed_vs_fp64_ceff_rel"] = float(np.abs(sb_m - sb_d).max() / np.abs(sb_d).max())
-        res["df64_vs_fp64_ceff_rel"] = float(np.abs(np.array(res["df64"]["sigma_bar"]) - sb_d).max() / np.abs(sb_d).max())
-        for prec in ("mixed", "df64", "fp64"):
-            res[prec].pop("sigma_bar")
+        sb_d = np.array(res["fp64"]["sigma_bar"])
+        for form in ("mixed", "df64", "eyre_milton_mixed", "cg_df64"):
+            res[form + "_vs_fp64_ceff_rel"] = float(np.abs(np.array(res[form]["sigma_bar"]) - sb_d).max()
+                                                    / np.abs(sb_d).max())
+        for form in forms:
+            res[form].pop("sigma_bar")
         out[name] = res
     print(json.dumps({"workload": "hashin3d (config 3): coated ellipsoid c=(0.1,0.15,0.2), fraction 0.25, "
                                   "core/coating/matrix 10/1/1+rank-one, m=2^21, 6 load cases batched, tol 1e-6",
@@ -624,6 +633,17 @@ def profile_case(args):
     st = [synth.iso_voigt(*l) for l in LAMES]
     E = np.zeros(P.n_c)
     E[0] = 1.0
+    if args.profile_scheme == "cg":
+        # a conjugate-gradient solve with plain launches (ncu sees each kernel): prologue stages
+        # FWD_X, FULL0, A, then per iteration B, the column passes, A
+        from paper_1605_05712_gb300 import basic_scheme_solve
+        t0 = time.perf_counter()
+        g = basic_scheme_solve(P, ph, st, (5.5, 5.5), E, tol=0.0, maxit=args.steps, precision=prec, scheme="cg",
+                               boundary="zero", plain_launches=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": M, "precision": prec, "scheme": "cg", "m": P.m,
+                          "iterations": int(g["iters"][0]), "s": round(time.perf_counter() - t0, 3)}))
+        return
     ms = lattice_pass_times(P, ph, st, (5.5, 5.5), E, precision=prec, n_reps=args.steps)
     print(json.dumps({"profile_case": M, "precision": prec, "m": P.m, "ms_per_kernel": ms}))
 
@@ -696,6 +716,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
+    ap.add_argument("--profile-scheme", default="basic", choices=["basic", "cg"],
+                    help="with --profile-case: cg runs a conjugate-gradient solve of --steps iterations")
     ap.add_argument("--plain-launches", action="store_true",
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
     ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep", "gather", "shear_sweep"])

@@ -93,13 +93,20 @@ __device__ __forceinline__ GreenK<Real> green_consts(const ItemDev* item, const 
     g.c2 = item->c2f;
     g.lam0 = item->lam0f;
     g.mu0 = item->mu0f;
+    g.sc = mt.gscale_f;
+  } else if constexpr (is_df<Real>) {  // host-made pairs: no binary64 conversions per thread
+    g.c1 = item->c1_df;
+    g.c2 = item->c2_df;
+    g.lam0 = item->lam0_df;
+    g.mu0 = item->mu0_df;
+    g.sc = mt.gscale_df;
   } else {
-    g.c1 = Real(item->c1);
-    g.c2 = Real(item->c2);
-    g.lam0 = Real(item->lam0);
-    g.mu0 = Real(item->mu0);
+    g.c1 = item->c1;
+    g.c2 = item->c2;
+    g.lam0 = item->lam0;
+    g.mu0 = item->mu0;
+    g.sc = mt.gscale;
   }
-  g.sc = Real(mt.gscale);
   return g;
 }
 
@@ -343,6 +350,23 @@ __device__ double block_sum(double x, double* red) {
   return t;
 }
 
+// block sum of a double-float pair into a binary64 value (valid on thread 0): the warps add pairs (binary32
+// pipes) and convert once per warp, so the pair kernels issue no binary64 arithmetic per thread
+__device__ double block_sum(dfloat x, double* red) {
+  for (int o = 16; o > 0; o >>= 1)
+    x = x + dfloat(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = (double)x;
+  __syncthreads();
+  double t = 0;
+  if (wid == 0) {
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
 // ordered sum of n values written by other blocks (bypasses L1), result on every lane of warp 0
 __device__ double ordered_sum(const double* p, int n) {
   double t = 0;
@@ -524,11 +548,12 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   }
 }
 
-// per-item reduction of NV values over the blocks of grid.x: block sums go to
+// per-item reduction of NV values (binary64, or pairs in the pair kernels) over the blocks of grid.x: block
+// sums go to
 // partials[v * gridDim.x + blockIdx.x]; the item's last block to arrive returns true on warp 0, with
 // the totals (summed in block order) in tot on lane 0; every other thread returns false
-template <int NV>
-__device__ __forceinline__ bool item_reduce(const double* v, double* partials, ItemScal* isc, double* red,
+template <int NV, typename V>
+__device__ __forceinline__ bool item_reduce(const V* v, double* partials, ItemScal* isc, double* red,
                                             int* s_last, double* tot) {
   double bs[NV];
 #pragma unroll
@@ -786,10 +811,16 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   // residual: block partial -> the item's last block sums in block order and decides its
   // convergence; the last item to arrive in this iteration sets the WHILE condition
   double* partials = a.it.partials + item_i * a.it.pstride;
-  dsum += ((double)dfs.hi + (double)dfs.lo) + 2.0 * ((double)dfs_shear.hi + (double)dfs_shear.lo);
-  dsum += (double)dd_acc + 2.0 * (double)dd_shear;
   double tot;
-  if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
+  if constexpr (is_f32<Real> || is_df<Real>) {
+    // the pair kernels keep the partial a pair (shear terms counted twice, exactly) down to the warp sums
+    dfloat pr;
+    if constexpr (is_f32<Real>) pr = dfloat(dfs.hi, dfs.lo) + dfloat(2.f * dfs_shear.hi, 2.f * dfs_shear.lo);
+    else pr = dd_acc + (dd_shear + dd_shear);
+    if (!item_reduce<1>(&pr, partials, isc, red, &s_last, &tot)) return;
+  } else {
+    if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
+  }
   if (tid == 0) item_report(sqrt(tot) / item->norm0, isc, item_i, a.it);
 }
 
@@ -884,12 +915,22 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
   double* w = cg.w + voff;
   const bool from_spectrum = (stage == CG_FULL0 || stage == CG_A);
   if (from_spectrum) row_tile_inverse<Real>(tile);
-  Real alpha = Real(0), beta = Real(0);
-  if (stage == CG_B) {
-    alpha = Real(isc->cg_alpha);
-    beta = Real(isc->cg_beta);
+  Real alpha = Real(0), beta = Real(0), lam0, two_mu0;
+  if constexpr (is_df<Real>) {  // host- or last-block-made pairs: no binary64 conversions per thread
+    if (stage == CG_B) {
+      alpha = isc->cg_alpha_df;
+      beta = isc->cg_beta_df;
+    }
+    lam0 = item->lam0_df;
+    two_mu0 = item->mu0_df + item->mu0_df;
+  } else {
+    if (stage == CG_B) {
+      alpha = Real(isc->cg_alpha);
+      beta = Real(isc->cg_beta);
+    }
+    lam0 = Real(item->lam0);
+    two_mu0 = Real(2.0 * item->mu0);
   }
-  const Real lam0 = Real(item->lam0), two_mu0 = Real(2.0 * item->mu0);
   const Real* Ct;
   if constexpr (is_df<Real>) Ct = (const Real*)item->Dtab_df;
   else Ct = (const Real*)item->Dtab;
@@ -971,7 +1012,7 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
   if (stage != CG_A) row_tile_forward<Real, NC>(tile, dv, a, item);
   if (stage == CG_FWD_X) return;
   double* partials = a.it.partials + item_i * a.it.pstride;
-  const double v[2] = {(double)acc0, (double)acc1};
+  const Real v[2] = {acc0, acc1};
   double tot[2];
   if (stage == CG_A) {
     if (!item_reduce<1>(v, partials, isc, red, &s_last, tot)) return;
@@ -983,6 +1024,8 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
       const double alp = (gam != 0.0 && den != 0.0) ? gam / den : 0.0;
       isc->cg_alpha = alp;
       isc->cg_beta = bet;
+      isc->cg_alpha_df = dfloat(alp);
+      isc->cg_beta_df = dfloat(bet);
       isc->cg_gamma_prev = gam;
       isc->cg_alpha_prev = alp;
       isc->counter = 0u;
@@ -1013,20 +1056,23 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   constexpr int n_f = NC, D = (NC == 6) ? 3 : 2;
   const int G = a.G;
-  int64_t b = blockIdx.x;
-  const int64_t main_blocks = a.outer * a.tiles_main;
+  // block -> (outer index, tile) in 32-bit arithmetic: a 64-bit division runs on the binary64 pipe
+  uint32_t b = blockIdx.x;
+  const uint32_t main_blocks = (uint32_t)(a.outer * a.tiles_main);   // < gridDim.x
   const bool nyqt = b >= main_blocks;
   int64_t o, t, inner_count;
   int w;
   if (!nyqt) {
-    o = b / a.tiles_main;
-    t = b - o * a.tiles_main;
+    const uint32_t tm = (uint32_t)a.tiles_main, oo = b / tm;
+    o = oo;
+    t = b - oo * tm;
     w = a.w;
     inner_count = a.inner * a.row_slots;
   } else {
     b -= main_blocks;
-    o = b / a.tiles_nyq;
-    t = b - o * a.tiles_nyq;
+    const uint32_t tn = (uint32_t)a.tiles_nyq, oo = b / tn;
+    o = oo;
+    t = b - oo * tn;
     w = a.wN;
     inner_count = a.inner;
   }
@@ -1140,8 +1186,9 @@ __global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
       __syncthreads();
     }
   }
-  const Real sc = (Real)a.scale;
-  const bool do_scale = a.scale != 1.0;
+  const bool do_scale = a.do_scale != 0;
+  Real sc = Real(1);
+  if (do_scale) sc = (Real)a.scale;
   for (int idx = tid; idx < n_f * G * w; idx += nthr) {
     const int col = idx & (w - 1);
     if (col >= wv) continue;

@@ -37,6 +37,9 @@ struct ItemDev {
   double E[6];           // macroscopic strain, tensor components
   double c1, c2;         // Green operator constants of this item's C0
   float c1f, c2f;
+  // the same constants (and C0's Lame constants) as double-float pairs: the pair kernels read them
+  // instead of converting binary64 values, which runs on the binary64 pipe at 1/64 of the binary32 rate
+  dfloat c1_df, c2_df, lam0_df, mu0_df;
   // Eyre-Milton iteration: (C_p + C0)^{-1} on tensor components (maps the stress-like u to the strain),
   // the reference medium's Lame constants and 2 C0 : E (tensor components)
   const double* Wtab;
@@ -59,6 +62,7 @@ struct ItemScal {
   // conjugate gradients: step lengths and <r, r>_C0 of the current and the previous iteration
   double cg_alpha, cg_beta, cg_gamma, cg_gamma_prev, cg_alpha_prev;
   double cg_r0;          // first residual (the rounding floor of the iteration is relative to it)
+  dfloat cg_alpha_df, cg_beta_df;  // the step lengths as pairs (for the double-float kernels)
 };
 
 // Batch-wide device scalars
@@ -69,6 +73,8 @@ struct GlobScal {
 
 struct MatArgs {
   double gscale;         // -1/m: the forward 1/m of F(M) and the minus sign of the update
+  float gscale_f;        // the same in binary32 and as a pair (set with mat_set_gscale)
+  dfloat gscale_df;
   int boundary_zero;
   int increment;         // 1: spectrum carries an increment, k = 0 gets 0 instead of E
   int scheme;            // Green step of LAT_SCHEME_BASIC (also conjugate gradients) or LAT_SCHEME_EYRE_MILTON
@@ -115,11 +121,18 @@ struct ColArgs {
   int64_t t_stride, tn_stride;  // per item (blockIdx.y)
   const void* Tin;       // first pass of the complex transform reads here (else = T)
   double scale;          // multiply on store (1/m for the last forward pass of lattice_fft), 1 = none
+  int do_scale;          // scale != 1 (decided on the host)
   const ItemDev* items;  // solver: E and Green constants per item
   MatArgs mat;
   const ItemScal* scal;  // NULL or per-item scalars (skip items not ITEM_ACTIVE)
   int only_paused;       // with scal: process ITEM_PAUSED items only (restart passes)
 };
+
+inline void mat_set_gscale(MatArgs& m, double g) {
+  m.gscale = g;
+  m.gscale_f = (float)g;
+  m.gscale_df = dfloat(g);
+}
 
 // Conjugate-gradient row kernel stages
 #define CG_FWD_X 0   // tau = C : x, forward transform                                   (prologue)

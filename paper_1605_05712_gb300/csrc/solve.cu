@@ -508,6 +508,10 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     v.c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
     v.c1f = (float)v.c1;
     v.c2f = (float)v.c2;
+    v.c1_df = dfloat(v.c1);
+    v.c2_df = dfloat(v.c2);
+    v.lam0_df = dfloat(lam0);
+    v.mu0_df = dfloat(mu0);
     double nE2 = 0;
     for (int c = 0; c < 6; ++c) v.E[c] = c < n_c ? it.E[c] : 0.0;
     for (int c = 0; c < n_c; ++c) nE2 += (c >= d ? 2.0 : 1.0) * it.E[c] * it.E[c];
@@ -570,7 +574,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ra.TN = ws + wl.TN;
     ra.t_stride = (int64_t)(wl.t_per_lc / (fp32 ? 8 : 16));
     ra.tn_stride = (int64_t)(wl.tn_per_lc / (fp32 ? 8 : 16));
-    ra.mat.gscale = -1.0 / (double)m;
+    mat_set_gscale(ra.mat, -1.0 / (double)m);
     ra.mat.boundary_zero = o.boundary == LAT_BOUNDARY_ZERO;
     ra.mat.scheme = o.scheme == LAT_SCHEME_EYRE_MILTON ? LAT_SCHEME_EYRE_MILTON : LAT_SCHEME_BASIC;
     ra.it.partials = (double*)(ws + wl.partials);
@@ -1127,7 +1131,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ra.items = (const ItemDev*)(ws + wl.items);
   ra.T = ws + wl.T;
   ra.TN = ws + wl.TN;
-  ra.mat.gscale = -1.0 / (double)P->m;
+  mat_set_gscale(ra.mat, -1.0 / (double)P->m);
   ra.it.partials = (double*)(ws + wl.partials);
   ra.it.pstride = wl.pstride;
   ra.it.scal = (ItemScal*)(ws + wl.scal);
@@ -1253,6 +1257,7 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       c.tiles_nyq = 0;
       c.Tin = tin;
       c.scale = scale;
+      c.do_scale = scale != 1.0;
       launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[k], st);
     };
     if (!inverse) {

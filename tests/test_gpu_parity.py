@@ -556,6 +556,17 @@ def test_cg_fixed_iterations(cuda, M, prec):
     check_pair(*out, d=d, hist_atol=1e-13)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", [[[16, 4], [0, 8]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]]])
+def test_cg_transformed_cell_fixed_iterations(cuda, M, prec):
+    # conjugate gradients on P_L(M): the Green operator at L^{-T} h, as in Algorithm 1
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    out = run_pair(M, inclusions(6, d, 3, 0.3), LAM2, (5.5, 5.5), E, tol=0.0, maxit=5, cuda=cuda, precision=prec,
+                   cell=CELL2 if d == 2 else CELL3, scheme="cg", boundary="zero")
+    check_pair(*out, d=d, hist_atol=1e-13)
+
+
 @pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
 def test_cg_solution_and_iterations(cuda, M):
     import torch
