@@ -253,6 +253,28 @@ def test_aligned_laminate_config1_matches_analytic(cuda):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_aligned_laminate_262144_matches_analytic(cuda, prec):
+    # the aligned rank-1 lattice of the m = 262144 laminate, M = [[262144, 786432], [0, 1]]: every frequency
+    # is parallel to (1,3), so the converged discrete solution is the analytic laminate point by point -- a
+    # full-size check without an oracle run; three unit load cases in one solve
+    import torch
+    from oracle import analytic as an
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    P = lattice_plan([[262144, 786432], [0, 1]])
+    ph = synth.laminate_phase(P.points(), P.m, [1, 3])
+    E = np.eye(3)
+    E[2, 2] = 0.5
+    g = basic_scheme_solve(P, torch.from_numpy(ph).to(cuda), LAM2, (5.5, 5.5), E, tol=1e-14, maxit=300,
+                           precision=prec)
+    S = stiff_tensors(LAM2, 2)
+    for lc in range(3):
+        e1, e2, sb = an.laminate_fields(S[0], S[1], 0.5, np.array([1.0, 3.0]), el.comps_to_sym(E[lc], 2))
+        ex = np.where(ph[:, None, None] == 0, e1, e2)
+        assert relerr(comps_to_tensor(g["eps"][lc].cpu().numpy(), 2), ex) < (1e-12 if prec == "fp64" else 1e-11)
+        assert relerr(el.comps_to_sym(g["sigma_bar"][lc], 2), sb) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("name", ["grid512", "rank1_262144", "rank2_262144"])
 def test_full_size_262144_fixed_iterations(cuda, name, prec):
     # the benchmark workload: laminate n = (1,3), m = 262144, three unit load cases, compared field-wise
