@@ -411,7 +411,7 @@ def bench_warmstart(args):
     ellipsoidal-inclusion microstructures at 64^3 (contrast 10^U(-1,2)), evaluate on held-out seeds at
     128^3: iterations and wall time to a 1e-6 residual for the six unit load cases batched, from the cold
     start, the raw prediction, and both after the two-iteration start filter, in binary64 and in mixed
-    precision; every result judged against the plain binary64 cold start (effective stress)."""
+    precision; every result checked against the plain binary64 cold start (effective stress)."""
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
     from paper_1605_05712_gb300.warmstart import (UNIT_E, WarmStartNet, feature_table, random_microstructure,
@@ -428,7 +428,7 @@ def bench_warmstart(args):
     E = UNIT_E
     names = ["cold", "warm", "cold_filtered", "warm_filtered"]
     tot = {prec: {k: {"iters": 0, "s": 0.0} for k in names} for prec in ("fp64", "mixed")}
-    per_seed, judge = [], 0.0
+    per_seed, worst_sb = [], 0.0
     for s in range(args.ws_eval):
         ph, stiff, C0 = random_microstructure(900000 + s, n, dev)
         ref = None
@@ -450,7 +450,7 @@ def bench_warmstart(args):
                 row["%s_%s" % (prec, k)] = it
                 if ref is None:
                     ref = r["sigma_bar"]
-                judge = max(judge, float(np.abs(r["sigma_bar"] - ref).max() / np.abs(ref).max()))
+                worst_sb = max(worst_sb, float(np.abs(r["sigma_bar"] - ref).max() / np.abs(ref).max()))
         tab = torch.from_numpy(feature_table(stiff, C0[1]).reshape(-1)).to(dev)
         eps0 = net.predict(ph, tab, n, E)
         cold = basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-6, maxit=5000)
@@ -465,14 +465,14 @@ def bench_warmstart(args):
                                   % (args.ws_samples, args.ws_train_n, args.ws_eval, n),
                       "train_s": round(t_train, 1), "train_loss_first_last": [float(np.mean(losses[:100])),
                                                                                float(np.mean(losses[-100:]))],
-                      "totals": tot, "judge_max_sigma_bar_rel_diff_vs_fp64_cold": judge, "per_seed": per_seed}))
+                      "totals": tot, "max_sigma_bar_rel_diff_vs_fp64_cold": worst_sb, "per_seed": per_seed}))
 
 
 def bench_sweep(args):
     """Uneven serving sweep: 256 seeded independent problems (2-D and 3-D, m = 2^12 .. 2^21, rank-1 /
     rank-2 / diagonal lattices, 1-8 inclusions, contrast 1e-2 .. 1e2, all unit load cases), mixed
     precision to a 1e-6 residual in one basic_scheme_solve_multi call (one CUDA graph, a WHILE loop per
-    lattice), against the same problems solved one call each; sampled problems judged against binary64."""
+    lattice), against the same problems solved one call each; sampled problems checked against binary64."""
     import torch
     from paper_1605_05712_gb300 import (basic_scheme_solve, basic_scheme_solve_multi, lattice_plan,
                                         multi_workspace_bytes, synth)
@@ -528,7 +528,7 @@ def bench_sweep(args):
         res[name] = {"s": round(float(np.median(times)), 3), "point_iterations": pit,
                      "value": round(pit / float(np.median(times)), 1),
                      "iterations_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())]}
-    # judge a sample against binary64: extremes of contrast and the largest problems
+    # check a sample against binary64: extremes of contrast and the largest problems
     order = np.argsort([s_["contrast"] for s_ in sweep])
     sizes = np.argsort([s_["m"] for s_ in sweep])
     pick = sorted(set(list(order[:2]) + list(order[-2:]) + list(sizes[-2:])))
@@ -544,7 +544,7 @@ def bench_sweep(args):
                                   "rank-1/rank-2/diagonal, contrast 1e-2..1e2, all unit load cases, mixed, tol 1e-6"
                                   % sum(p_["plan"].m for p_ in probs),
                       "metric": METRIC, "unit": "point-iterations/s", "setup_s": round(t_setup, 1), "results": res,
-                      "judged_problems": [int(i) for i in pick], "max_rel_err_vs_fp64": worst,
+                      "checked_problems": [int(i) for i in pick], "max_rel_err_vs_fp64": worst,
                       "l2": "flushed between timed steps"}))
 
 

@@ -1,7 +1,7 @@
 """CPU FP64 oracle for the lattice Basic Scheme (Bergmann & Merkert, arXiv 1605.05712).
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
-restatement of the paper's method in numpy float64.  It exists to judge the
+restatement of the paper's method in numpy float64.  It exists to check the
 CUDA implementation in ``paper_1605_05712_gb300``; the two share no code.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import it.  The product path

@@ -3,7 +3,7 @@
 Test infrastructure only (see ``oracle/__init__``).  The warm start is not in the
 paper: it predicts the strain-localization field A (eps = A : E) from the
 stiffness field so that Algorithm 1 can start from eps^(0) = A : E instead of E;
-the scheme then runs to the same tolerance and judges the result.
+the scheme then runs to the same tolerance and checks the result.
 
 Network (a periodic 3-D U-Net with 4 levels and 32 channels):
     x0 = features (21 stiffness components, zero-padded to 32 channels); relu is leaky (slope 0.1)

@@ -3,7 +3,7 @@ training loop (argument marshalling and orchestration; every layer runs in libla
 
 The network predicts the strain-localization field A of a cubic tensor grid from its stiffness
 field; eps^(0) = A : E starts basic_scheme_solve, which then runs to the same tolerance as a cold
-start and so judges the prediction.  Training data are plain-scheme solutions of seeded random
+start and so checks the prediction.  Training data are plain-scheme solutions of seeded random
 ellipsoidal-inclusion microstructures.
 """
 from __future__ import annotations

@@ -208,7 +208,7 @@ def test_start_filter_matches_oracle(cuda):
 def test_trained_warm_start_against_cold_start(cuda):
     # train on the GPU (own kernels), then measure on held-out microstructures: prediction error against
     # the converged field (the cold start's is 1), and iterations to tol 1e-6 from the cold start, the raw
-    # prediction, and both after the start filter; the plain cold start judges every result
+    # prediction, and both after the start filter; the plain cold start is the reference for every result
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
     from paper_1605_05712_gb300.warmstart import (UNIT_E, WarmStartNet, feature_table, random_microstructure,
@@ -235,7 +235,7 @@ def test_trained_warm_start_against_cold_start(cuda):
         for name, r in runs.items():
             assert r["status"] == 0
             its[name] += int(np.sum(r["iters"]))
-            # the plain scheme judges: every start converges to the cold start's effective stress
+            # the plain scheme is the reference: every start converges to the cold start's effective stress
             assert np.abs(r["sigma_bar"] - cold["sigma_bar"]).max() < 1e-5 * np.abs(cold["sigma_bar"]).max()
     print("held-out prediction error^2 (cold start = 1):", np.round(errs, 3), "iterations:", its)
     assert max(errs) < 0.5
