@@ -290,7 +290,7 @@ def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=2
 
 
 def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
-                               boundary="average", eps_out=None, want_sigma=False, stream=None):
+                               boundary="average", eps_out=None, want_sigma=False, stream=None, scheme="basic"):
     """basic_scheme_solve through the no-allocation entry point of the C ABI.
 
     For callers that cannot allocate device memory inside the call: the library uses its own
@@ -314,7 +314,7 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
     resid = np.zeros(n_loads)
-    opts = _Opts(prec, bnd, 0, None, 1, 0, 1)
+    opts = _Opts(prec, bnd, 0, None, 1, 0, 1, _SCHEMES[scheme])
     L = lib()
     f = L.basic_scheme_solve_noalloc
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3 + \

@@ -47,3 +47,23 @@ def test_noalloc_matches_workspace_entry_point_twice(cuda):
     with pytest.raises(LatticeError) as ei:
         basic_scheme_solve_noalloc(Pb, phb, stiff[:1], (5.5, 5.5), np.eye(6)[:1], tol=1e-8, maxit=2)
     assert ei.value.code == -4
+
+
+@pytest.mark.parametrize("scheme,C0,boundary", [("eyre_milton", (np.sqrt(10.0), np.sqrt(10.0)), "average"),
+                                                ("cg", (5.5, 5.5), "zero")])
+def test_noalloc_accelerated_schemes(cuda, scheme, C0, boundary):
+    # the accelerated schemes through the no-allocation entry point (plain launches on the static scratch;
+    # conjugate gradients need four more strain-sized vectors there) equal the workspace entry point
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    from paper_1605_05712_gb300.api import basic_scheme_solve_noalloc
+    P = lattice_plan([[128, 16], [0, 256]])   # m = 32768: the vectors fit the 16 MiB scratch
+    ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 3])).to(cuda)
+    stiff = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(10.0, 10.0)]
+    E = np.array([[1.0, 0.0, 0.0], [0.2, -0.4, 0.3]])
+    ref = basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-9, maxit=500, boundary=boundary, scheme=scheme)
+    g = basic_scheme_solve_noalloc(P, ph, stiff, C0, E, tol=1e-9, maxit=500, boundary=boundary, scheme=scheme)
+    assert g["status"] == ref["status"] == 0
+    assert np.array_equal(g["iters"], ref["iters"])
+    assert _rel(g["eps"].cpu().numpy(), ref["eps"].cpu().numpy()) < RTOL
+    assert _rel(g["sigma_bar"], ref["sigma_bar"]) < RTOL
