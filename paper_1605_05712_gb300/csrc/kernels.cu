@@ -460,15 +460,15 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
       L[0].x = X0 + XN;
       L[0].y = X0 - XN;
     } else {
+      // Z_k = A + i B conj(W^k), A = X_k + conj X_{Rh-k}, B = X_k - conj X_{Rh-k}; the partner reuses
+      // both: W_R^{Rh-k} = -conj(W_R^k), so Z_{Rh-k} = conj(A) + i conj(B conj(W^k))
       const int kp = Rh - k;
       const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
       const C Xk = L[pk], Xkp = L[pkp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
-      L[pk] = cadd(cadd(Xk, cconj(Xkp)), cmuli(cmulc(csub(Xk, cconj(Xkp)), wk)));
-      if (kp != k) {
-        const C wkp = twid(t.tw, t.tw_log2, t.lgR, kp);
-        L[pkp] = cadd(cadd(Xkp, cconj(Xk)), cmuli(cmulc(csub(Xkp, cconj(Xk)), wkp)));
-      }
+      const C A = cadd(Xk, cconj(Xkp)), Pw = cmulc(csub(Xk, cconj(Xkp)), wk);
+      L[pk] = cadd(A, cmuli(Pw));
+      if (kp != k) L[pkp] = cadd(cconj(A), cmuli(cconj(Pw)));
     }
   }
   __syncthreads();
@@ -498,17 +498,15 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
       L[0] = cpair<C>(Z0.x + Z0.y, Real(0));
       nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
     } else {
+      // the partner reuses A and W^k B: X_{Rh-k} = 1/2 (conj(A) - i conj(W^k B)), since
+      // W_R^{Rh-k} = -conj(W_R^k) and Z_{Rh-k} - conj Z_k = -conj(B)
       const int kp = Rh - k;
       const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
       const C Zk = L[pk], Zkp = L[pkp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
-      const C A1 = cadd(Zk, cconj(Zkp)), B1 = csub(Zk, cconj(Zkp));
-      L[pk] = cscale(csub(A1, cmuli(cmul(B1, wk))), Real(0.5));
-      if (kp != k) {
-        const C wkp = twid(t.tw, t.tw_log2, t.lgR, kp);
-        const C A2 = cadd(Zkp, cconj(Zk)), B2 = csub(Zkp, cconj(Zk));
-        L[pkp] = cscale(csub(A2, cmuli(cmul(B2, wkp))), Real(0.5));
-      }
+      const C A1 = cadd(Zk, cconj(Zkp)), Q = cmul(csub(Zk, cconj(Zkp)), wk);
+      L[pk] = cscale(csub(A1, cmuli(Q)), Real(0.5));
+      if (kp != k) L[pkp] = cscale(csub(cconj(A1), cmuli(cconj(Q))), Real(0.5));
     }
   }
   __syncthreads();
