@@ -27,35 +27,50 @@ template <typename R> __device__ __forceinline__ R ldg_r(const R* p) { return __
 template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) { return ldg_df(p); }
 
 // ------------------------------------------------------------------ Green operator (Sec. 3.1)
-// Gamma0(h) : tau for isotropic C0 (closed form of grad (grad^H C0 grad)^{-1} grad^H):
-//   (Gamma0 : tau)_ij = [c1 (h_i w_j + h_j w_i) - c2 s h_i h_j / |h|^2] / |h|^2,
-//   w = tau h, s = h . w, c1 = 1/(2 mu0), c2 = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)).
-template <typename Real>
-__device__ __forceinline__ void gamma_apply(int d, const Real* h, Real a, Real c1, Real c2, const Real* t, Real* out) {
-  Real A[3][3];
-  if (d == 2) {
-    A[0][0] = t[0]; A[1][1] = t[1]; A[0][1] = A[1][0] = t[2];
-    A[2][2] = A[0][2] = A[2][0] = A[1][2] = A[2][1] = 0;
-  } else {
-    A[0][0] = t[0]; A[1][1] = t[1]; A[2][2] = t[2];
-    A[1][2] = A[2][1] = t[3]; A[0][2] = A[2][0] = t[4]; A[0][1] = A[1][0] = t[5];
-  }
-  Real w[3], s = 0;
-  for (int i = 0; i < d; ++i) {
-    Real acc = 0;
-    for (int j = 0; j < d; ++j) acc += A[i][j] * h[j];
-    w[i] = acc;
-    s += h[i] * acc;
-  }
-  const Real q = c2 * a * s;
-#define GAM(i, j) (a * (c1 * (h[i] * w[j] + h[j] * w[i]) - q * h[i] * h[j]))
-  if (d == 2) {
-    out[0] = GAM(0, 0); out[1] = GAM(1, 1); out[2] = GAM(0, 1);
-  } else {
-    out[0] = GAM(0, 0); out[1] = GAM(1, 1); out[2] = GAM(2, 2);
-    out[3] = GAM(1, 2); out[4] = GAM(0, 2); out[5] = GAM(0, 1);
-  }
-#undef GAM
+// sc Gamma0(h) : tau for isotropic C0 (closed form of grad (grad^H C0 grad)^{-1} grad^H), applied to the
+// real and imaginary parts of tau_hat at once so that the products of h and the constants are shared:
+//   (Gamma0 : tau)_ij = [c1 (h_i w_j + h_j w_i) - q h_i h_j] / |h|^2,  q = c2 (h . w) / |h|^2,
+//   w = tau h, c1 = 1/(2 mu0), c2 = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)).
+// The factors are grouped so that no intermediate leaves the binary32 range for |h| < 2^31.
+template <typename Real, int D>
+__device__ __forceinline__ void gamma_apply2(const Real* h, Real c1, Real c2, Real sc, const Real* tr,
+                                             const Real* ti, Real* gr, Real* gi) {
+  Real n2 = h[0] * h[0] + h[1] * h[1];
+  if constexpr (D == 3) n2 = n2 + h[2] * h[2];
+  const Real a = Real(1) / n2;
+  const Real ka = sc * a, c2a = c2 * a, c1x2 = c1 + c1;
+  // one part at a time (the products of h are recomputed rather than held, to keep registers low)
+  auto one = [&](const Real* t, Real* out) {
+    Real A[3][3];
+    if constexpr (D == 2) {
+      A[0][0] = t[0]; A[1][1] = t[1]; A[0][1] = A[1][0] = t[2];
+    } else {
+      A[0][0] = t[0]; A[1][1] = t[1]; A[2][2] = t[2];
+      A[1][2] = A[2][1] = t[3]; A[0][2] = A[2][0] = t[4]; A[0][1] = A[1][0] = t[5];
+    }
+    Real w[3], s = Real(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      Real acc = A[i][0] * h[0];
+#pragma unroll
+      for (int j = 1; j < D; ++j) acc += A[i][j] * h[j];
+      w[i] = acc;
+      s += h[i] * acc;
+    }
+    const Real q = c2a * s;
+#define GAMD(i) (ka * (c1x2 * (h[i] * w[i]) - (q * h[i]) * h[i]))
+#define GAMO(i, j) (ka * (c1 * (h[i] * w[j] + h[j] * w[i]) - (q * h[i]) * h[j]))
+    if constexpr (D == 2) {
+      out[0] = GAMD(0); out[1] = GAMD(1); out[2] = GAMO(0, 1);
+    } else {
+      out[0] = GAMD(0); out[1] = GAMD(1); out[2] = GAMD(2);
+      out[3] = GAMO(1, 2); out[4] = GAMO(0, 2); out[5] = GAMO(0, 1);
+    }
+#undef GAMD
+#undef GAMO
+  };
+  one(tr, gr);
+  one(ti, gi);
 }
 
 __device__ __forceinline__ int64_t mod_ed(const LatDev& dv, int64_t v) {
@@ -155,18 +170,14 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
     for (int c = 0; c < n_c; ++c) val[c] = cmake<C>(0.0, 0.0);
     return;
   }
-  Real tr[NC], ti[NC], gr[NC], gi[NC];
+  Real tr[NC], ti[NC], gr[NC], gi[NC];   // gr, gi = sc Gamma0 : tau_hat
 #pragma unroll
   for (int c = 0; c < n_c; ++c) tr[c] = val[c].x, ti[c] = val[c].y;
-  const Real a = Real(1) / (h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-  gamma_apply<Real>(d, h, a, gk.c1, gk.c2, tr, gr);
-  gamma_apply<Real>(d, h, a, gk.c1, gk.c2, ti, gi);
+  gamma_apply2<Real, d>(h, gk.c1, gk.c2, gk.sc, tr, ti, gr, gi);
   if (boundary) {
     // average with -h(-k): Gamma0 is even in h, so evaluate at h(-k) directly
-    const Real a2 = Real(1) / (h2[0] * h2[0] + h2[1] * h2[1] + h2[2] * h2[2]);
     Real gr2[NC], gi2[NC];
-    gamma_apply<Real>(d, h2, a2, gk.c1, gk.c2, tr, gr2);
-    gamma_apply<Real>(d, h2, a2, gk.c1, gk.c2, ti, gi2);
+    gamma_apply2<Real, d>(h2, gk.c1, gk.c2, gk.sc, tr, ti, gr2, gi2);
 #pragma unroll
     for (int c = 0; c < n_c; ++c) gr[c] = Real(0.5) * (gr[c] + gr2[c]), gi[c] = Real(0.5) * (gi[c] + gi2[c]);
   }
@@ -175,12 +186,10 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
     Real trr = Real(0), tri = Real(0);
 #pragma unroll
     for (int c = 0; c < d; ++c) trr += gr[c], tri += gi[c];
-    trr = gk.sc * trr;
-    tri = gk.sc * tri;
     const Real two = Real(2);
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
-      Real cr = two * gk.mu0 * (gk.sc * gr[c]), ci = two * gk.mu0 * (gk.sc * gi[c]);
+      Real cr = two * gk.mu0 * gr[c], ci = two * gk.mu0 * gi[c];
       if (c < d) cr += gk.lam0 * trr, ci += gk.lam0 * tri;
       val[c].x = two * cr - gk.sc * tr[c];
       val[c].y = two * ci - gk.sc * ti[c];
@@ -189,8 +198,8 @@ __device__ __forceinline__ void green_point_h(const LatDev& dv, const MatArgs& m
   }
 #pragma unroll
   for (int c = 0; c < n_c; ++c) {
-    val[c].x = gk.sc * gr[c];
-    val[c].y = gk.sc * gi[c];
+    val[c].x = gr[c];
+    val[c].y = gi[c];
   }
 }
 
@@ -1041,8 +1050,14 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
 }
 
 // ------------------------------------------------------------------ column pass
+// resident blocks of 256 threads per SM the column pass's register budget is cut for (the compiler's own
+// choice spilled the binary32 3-D pass): 85 registers for 2-D, 128 for the 3-D binary64 and pair passes
 template <typename Real, int NC>
-__global__ void __launch_bounds__(256) col_pass_kernel(LatDev dv, ColArgs a) {
+constexpr int col_min_blocks() {
+  return NC == 6 ? (is_f32<Real> ? 3 : 2) : (NC == 3 ? 3 : 4);
+}
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_kernel(LatDev dv, ColArgs a) {
   typedef typename cplx_of<Real>::type C;
   const int item_i = blockIdx.y;
   if (a.scal) {
