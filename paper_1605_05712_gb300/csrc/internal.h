@@ -68,8 +68,6 @@ struct lat_plan {
     int w[LAT_MAX_GROUPS];       // tile width (columns) of each column pass
     float ms[1 + LAT_MAX_GROUPS];  // their measured device times (ms)
   } tune[3][8];
-  // cached solver graph
-  void* graph_cache;
 };
 
 // Parameters shared by the solver kernels (passed by value).

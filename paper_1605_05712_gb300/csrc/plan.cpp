@@ -432,11 +432,8 @@ int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t*
   return LAT_OK;
 }
 
-void lat_graph_cache_free(lat_plan* P);
-
 extern "C" void lattice_plan_destroy(lat_plan* P) {
   if (!P) return;
-  lat_graph_cache_free(P);
   if (P->d_tw) cudaFree(P->d_tw);
   if (P->d_twf) cudaFree(P->d_twf);
   if (P->d_stw) cudaFree(P->d_stw);

@@ -893,8 +893,6 @@ void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, 
 
 using namespace latms_detail;
 
-void lat_graph_cache_free(lat_plan* P) { (void)P; }
-
 // the precision argument of the workspace queries: a precision, plus LAT_WS_CG for conjugate gradients
 static int ws_scheme(int precision) { return (precision & LAT_WS_CG) ? LAT_SCHEME_CG : LAT_SCHEME_BASIC; }
 static int ws_precision(int precision) { return precision & ~LAT_WS_CG; }
