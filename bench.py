@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 LATS = ["grid512", "rank1_262144", "rank2_262144"]
+WORKLOAD = ("2-D laminate n=(1,3), m=262144 on diag(512,512), rank-1 [[512,1],[0,512]] and rank-2 "
+            "[[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64")
 LAMES = [(1.0, 1.0), (10.0, 10.0)]
 N_INT = [1, 3]
 TOL = 1e-8
@@ -318,9 +320,7 @@ def bench_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded laminate phases generated on the host)",
-        "config": {"workload": "2-D laminate n=(1,3), m=262144 on diag(512,512), rank-1 [[512,1],[0,512]] and "
-                               "rank-2 [[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64",
-                   "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
+        "config": {"workload": WORKLOAD, "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
                    "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "launch": "plain launches, host convergence check per iteration" if PLAIN_LAUNCHES
                              else "one CUDA-graph WHILE loop per solve"},
@@ -696,8 +696,9 @@ def bench_reference(args):
     res = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "point-iterations/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "ms_per_step": round(1e3 * tt / max(args.steps, 1), 2), "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "2-D laminate n=(1,3), m=262144, rank-2 [[512,16],[0,512]], load case 11, "
-                                  "bounded sample of oracle iterations per step"},
+           "config": {"workload": WORKLOAD, "lattices": LATS, "load_cases": 3, "tol": TOL,
+                      "sample": "each step a bounded sample of the workload: oracle iterations on the rank-2 "
+                                "lattice [[512,16],[0,512]], unit load case 11, point-iterations counted"},
            "cpu_baseline": {"value": round(v, 1), "unit": "point-iterations/s", "cores": 1, "kind": "oracle",
                             "sample": "2-iteration oracle solves repeated for ~%.0f s per step" %
                                       max(2.0, args.cpu_seconds / max(args.steps, 1))},
