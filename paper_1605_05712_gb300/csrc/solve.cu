@@ -6,6 +6,11 @@
 // microstructures on one lattice): each kernel launch covers all items (grid.y), each item keeps
 // its own strain, spectrum, material tables, reference medium and convergence state, and blocks of
 // finished items return at once.  The loop runs until every item has stopped.
+//
+// The same drivers run the accelerated schemes of lat_solve_opts.scheme: the Eyre-Milton iteration
+// (the same passes with another Green step and per-phase (C + C0)^{-1} tables) and conjugate
+// gradients (the two cg_row_kernel stages around the column passes, with its own prologue and a loop
+// condition that starts from the active count).
 #include <math.h>
 #include <string.h>
 
