@@ -14,9 +14,12 @@
  *    a negative LAT_ERR_* code on error.  lattice_last_error() returns a
  *    thread-local message for the last failing call.
  *  - Ownership: the library allocates device memory only inside
- *    lattice_plan() (index constants and twiddle tables, freed by
- *    lattice_plan_destroy()).  Every field buffer and the workspace belong to
- *    the caller; solves never allocate.
+ *    lattice_plan() (twiddle tables on the device current at that call, freed
+ *    by lattice_plan_destroy()).  Every field buffer and the workspace belong
+ *    to the caller; solves never allocate.  A plan's solves must run with its
+ *    device current (LAT_ERR_ARG otherwise); a plan made on a machine without
+ *    a CUDA device is host-only (points, frequencies, gather maps) and its
+ *    solves return LAT_ERR_CUDA.
  *  - "device" pointers are CUDA global-memory pointers on the current device;
  *    "host" pointers are ordinary host memory.  `stream` is a cudaStream_t
  *    passed as void* (NULL = the legacy default stream).
@@ -47,7 +50,10 @@ extern "C" {
 /* outcomes (>= 0) */
 #define LAT_OK               0
 #define LAT_NOT_CONVERGED    1   /* maxit reached with r >= tol; outputs hold the last iterate */
-#define LAT_DIVERGED         2   /* the residual became non-finite; outputs hold the last iterate */
+#define LAT_DIVERGED         2   /* the residual became non-finite, or grew for LAT_DIVERGE_STEPS
+                                    consecutive iterations to above 1 (the increment larger than the
+                                    start strain itself); outputs hold the last iterate */
+#define LAT_DIVERGE_STEPS   16
 /* errors (< 0) */
 #define LAT_ERR_ARG         -1   /* NULL pointer, bad count, bad option */
 #define LAT_ERR_SINGULAR    -2   /* det M == 0 */
@@ -88,7 +94,8 @@ typedef struct lat_plan lat_plan;
  *   out  receives the plan (caller frees with lattice_plan_destroy).
  * Computes the Smith normal form M = Q E R (Sec. 2.2), the pattern
  * dimension d_M, the FFT decomposition over the elementary divisors and
- * uploads twiddle tables to the current device.
+ * uploads twiddle tables to the current device (the plan's device; without a
+ * CUDA device the plan is host-only).
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
  * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (an elementary divisor
  * with an odd factor > 1, or one that needs more than one four-step split),
@@ -328,26 +335,29 @@ int basic_scheme_solve_multi(const lat_multi_item* items, int n_items, double to
 /*
  * basic_scheme_solve_noalloc -- basic_scheme_solve for callers that cannot
  * allocate device memory (the paper has no counterpart: this is a property of
- * the library, not of the method).  Code that runs while a stream is being
- * captured into a CUDA graph, a serving loop with a fixed memory budget, or a
- * runtime whose allocator owns all device memory cannot call cudaMalloc for
- * the workspace basic_scheme_solve wants.  This variant takes no workspace and
- * allocates nothing: its scratch is one static device array of
- * LAT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library
- * holds until the process exits.  The caller still owns and passes the inputs
- * and outputs, with the meaning they have for basic_scheme_solve.
+ * the library, not of the method).  A serving loop with a fixed device-memory
+ * budget, a runtime whose own allocator owns all device memory, or code that
+ * must not allocate while it sets up work around a later stream capture cannot
+ * call cudaMalloc for the workspace basic_scheme_solve wants.  This variant
+ * takes no workspace and allocates nothing: its scratch is one static device
+ * array of LAT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the
+ * library holds until the process exits.  The caller still owns and passes the
+ * inputs and outputs, with the meaning they have for basic_scheme_solve; the
+ * twiddle tables are the plan's (lattice_plan made them).
  *  - Limit: returns LAT_ERR_SIZE (message gives the bytes needed) when the
- *    solve's workspace plus the plan's twiddle tables exceed the array, e.g.
- *    binary64 m = 262144 in 2-D fits two load cases.
+ *    solve's workspace exceeds the array, e.g. binary64 m = 262144 in 2-D fits
+ *    two load cases, not three.
  *  - The first call on a device looks up the array's device address (with
- *    that device current) and keeps it; make that first call before any
- *    stream capture.
+ *    that device current) and keeps it; concurrent first calls from several
+ *    host threads are serialized.
  *  - Every call shares the one array; each call clears what it reads before
  *    use, but calls that overlap on the GPU (other streams or host threads)
  *    race on it.
  *  - The iteration uses plain kernel launches and reads the convergence flag
- *    back after every iteration instead of a CUDA-graph loop; the results
- *    equal basic_scheme_solve's.
+ *    back after every iteration (a stream synchronization) instead of a
+ *    CUDA-graph loop; the results equal basic_scheme_solve's.  It must
+ *    therefore not be called on a stream that is being captured: that returns
+ *    LAT_ERR_ARG before anything is enqueued.
  */
 #define LAT_NOALLOC_SCRATCH_BYTES (16u << 20)
 int basic_scheme_solve_noalloc(const lat_plan* plan, const uint8_t* phase, int n_phases,

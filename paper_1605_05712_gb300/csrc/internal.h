@@ -57,7 +57,7 @@ struct lat_plan {
   float4* d_twdf;     // double-float copies (re hi, re lo, im hi, im lo)
   float4* d_stwdf;
   int64_t stw_hi_n, stw_lo_n;
-  int device;
+  int device;        // device holding the tables (-1: created without a CUDA device, host-only)
   // transformed pattern (lattice_plan_set_cell): has_cell and L^{-T}
   int has_cell;
   double cell_LinvT[3][3];
@@ -93,6 +93,7 @@ struct LatDev {
 };
 
 void lat_set_error(const std::string& s);
-// upload twiddle tables to the current device on first use (plans are host-only until then)
-int lat_ensure_tables(lat_plan* P);
+// LAT_OK if the plan's device tables exist on the current device (lattice_plan uploads them to the device
+// current at creation); LAT_ERR_CUDA for a host-only plan, LAT_ERR_ARG for another device
+int lat_plan_device_check(const lat_plan* P);
 int lat_fail(int code, const std::string& s);

@@ -588,8 +588,14 @@ __device__ __forceinline__ void item_report(double r, ItemScal* isc, int item_i,
   const int n = isc->iter + 1;
   isc->iter = n;
   if (n - 1 < LAT_HIST_CAP) it.hist[(size_t)item_i * LAT_HIST_CAP + n - 1] = r;
+  // divergence: a residual that grew for LAT_DIVERGE_STEPS iterations in a row to above 1 (an increment
+  // larger than the start strain) belongs to an iteration that does not contract (e.g. C0 too soft)
+  const int grow = (n > 1 && r > isc->last_r) ? isc->grow + 1 : 0;
+  isc->grow = grow;
+  const bool diverging = grow >= LAT_DIVERGE_STEPS && r > 1.0;
+  if (diverging) isc->diverged = 1;
   isc->last_r = r;
-  const bool cont = isfinite(r) && !(r < it.tol) && n < it.maxit && !stop;
+  const bool cont = isfinite(r) && !(r < it.tol) && n < it.maxit && !stop && !diverging;
   isc->counter = 0u;
   if (!cont) isc->done = ITEM_DONE;
   else if (it.pause_tol > 0 && r < it.pause_tol) isc->done = ITEM_PAUSED;

@@ -63,6 +63,8 @@ struct ItemScal {
   double cg_alpha, cg_beta, cg_gamma, cg_gamma_prev, cg_alpha_prev;
   double cg_r0;          // first residual (the rounding floor of the iteration is relative to it)
   dfloat cg_alpha_df, cg_beta_df;  // the step lengths as pairs (for the double-float kernels)
+  int grow;              // consecutive iterations whose residual exceeded the previous one
+  int diverged;          // 1: stopped by the divergence rule (LAT_DIVERGED)
 };
 
 // Batch-wide device scalars
@@ -180,3 +182,5 @@ void launch_set_cond(const GlobScal* glob, unsigned long long cond, cudaStream_t
 void launch_spectrum_to_f32(const void* T64, const void* TN64, void* T32, void* TN32, int64_t t_elems,
                             int64_t tn_elems, int64_t t_stride, int64_t tn_stride, const ItemScal* scal,
                             int n_items, cudaStream_t st);
+
+static_assert(sizeof(ItemScal) <= 256, "the device scalars of an item fill one 256-byte slot");

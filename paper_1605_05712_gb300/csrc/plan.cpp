@@ -307,19 +307,22 @@ static int choose_layout(lat_plan* P) {
 
 int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t* n_tw, int64_t* n_stw);
 
-int lat_ensure_tables(lat_plan* P) {
-  if (P->nax == 0 || P->d_tw) return LAT_OK;
-  cudaGetDevice(&P->device);
+// Host part of the twiddle tables: their sizes (the device copies are made by lat_upload_tables).
+static void set_table_sizes(lat_plan* P) {
   int lg = 1;
   for (int i = 0; i < P->nax; ++i) lg = std::max(lg, P->ax[i].log2len);
   P->tw_log2 = lg;
-  int64_t n_tw = 0, n_stw = 0;
-  lat_host_twiddles(P, 0, nullptr, nullptr, &n_tw, &n_stw);
   if (P->split) {
     P->stw_lo_n = int64_t(1) << P->split_lo_log2;
     P->stw_hi_n = P->split_e >> P->split_lo_log2;
   }
-  // binary64, binary32 and double-float copies of both tables
+}
+
+// binary64, binary32 and double-float copies of both twiddle tables on the current device
+static int lat_upload_tables(lat_plan* P) {
+  if (P->nax == 0) return LAT_OK;
+  int64_t n_tw = 0, n_stw = 0;
+  lat_host_twiddles(P, 0, nullptr, nullptr, &n_tw, &n_stw);
   void** dst_tw[3] = {(void**)&P->d_tw, (void**)&P->d_twf, (void**)&P->d_twdf};
   void** dst_stw[3] = {(void**)&P->d_stw, (void**)&P->d_stwf, (void**)&P->d_stwdf};
   const size_t es[3] = {sizeof(double2), sizeof(float2), sizeof(float4)};
@@ -337,6 +340,20 @@ int lat_ensure_tables(lat_plan* P) {
         return lat_fail(LAT_ERR_CUDA, std::string("split twiddle upload: ") + cudaGetErrorString(err));
     }
   }
+  return LAT_OK;
+}
+
+int lat_plan_device_check(const lat_plan* P) {
+  if (P->nax == 0) return LAT_OK;   // m = 1: no transform, no tables
+  if (P->device < 0)
+    return lat_fail(LAT_ERR_CUDA, "the plan was created without a CUDA device (host-only plan: points, "
+                                  "frequencies and gather maps only)");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != P->device)
+    return lat_fail(LAT_ERR_ARG, "the plan's tables live on device " + std::to_string(P->device) +
+                                     " but the current device is " + std::to_string(dev));
   return LAT_OK;
 }
 
@@ -381,6 +398,19 @@ extern "C" int lattice_plan(const int64_t* Min, int d, lat_plan** out) {
   for (int j = d; j < 3; ++j) P->e[j] = 1;
   int rc = choose_layout(P);
   if (rc != LAT_OK) {
+    lattice_plan_destroy(P);
+    return rc;
+  }
+  set_table_sizes(P);
+  // the twiddle tables go to the current device now, so that no solve allocates; without a CUDA device
+  // the plan stays host-only (points, frequencies, gather maps) and solves report LAT_ERR_CUDA
+  P->device = -1;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) == cudaSuccess && n_dev > 0) {
+    if (cudaGetDevice(&P->device) != cudaSuccess) P->device = -1;
+  }
+  cudaGetLastError();   // a machine without a device leaves a (non-sticky) error behind
+  if (P->device >= 0 && (rc = lat_upload_tables(P)) != LAT_OK) {
     lattice_plan_destroy(P);
     return rc;
   }

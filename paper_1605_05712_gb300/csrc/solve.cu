@@ -753,7 +753,7 @@ int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, 
         o.resid_history[(size_t)i * maxit + k] = g.hist[(size_t)i * LAT_HIST_CAP + k];
     }
     int s = LAT_OK;
-    if (!isfinite(r) && maxit > 0) s = LAT_DIVERGED;
+    if ((!isfinite(r) || sc->diverged) && maxit > 0) s = LAT_DIVERGED;
     else if (!(r < tol)) s = LAT_NOT_CONVERGED;
     status = std::max(status, s);
   }
@@ -937,8 +937,8 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1, o.scheme);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
   if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+  if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
-  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   std::vector<ItemHost> items;
   load_case_items(P, phase, C0, E, n_loads, eps, sigma, items);
   const LatDev dv = make_dev(P, o.precision);
@@ -978,8 +978,8 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
   }
   const Work wl = layout(P, n_items, o.precision, LAT_BATCH_MAX_PHASES, n_items, o.scheme);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
-  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   const LatDev dv = make_dev(P, o.precision);
   return run_batch(P, items, stiff, nph, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar, iters, resid,
                    (cudaStream_t)stream);
@@ -1046,7 +1046,7 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
   }
   for (const MultiGroup& g : mg) {
     if (int rc = check_common(g.P, tol, maxit, o)) return rc;
-    if (int rc = lat_ensure_tables(const_cast<lat_plan*>(g.P))) return rc;
+    if (int rc = lat_plan_device_check(g.P)) return rc;
   }
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1225,8 +1225,8 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
     CK(cudaMemcpyAsync(out, in, (size_t)n_fields * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return LAT_OK;
   }
+  if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
-  if (int rc = lat_ensure_tables(const_cast<lat_plan*>(P))) return rc;
   const LatDev dv = make_dev(P, LAT_FP64);
   Geometry geo;
   int rc = geometry(P, 1, 16, P->Rlen, false, geo, 1);

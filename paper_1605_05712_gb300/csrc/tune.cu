@@ -158,8 +158,8 @@ extern "C" int lattice_autotune(lat_plan* P, int n_items, int precision, void* w
   const TuneWs tw = tune_layout(P, n_items, precision);
   if (workspace_bytes < tw.total) return lat_fail(LAT_ERR_SIZE, "lattice_autotune: workspace too small");
   if (P->nax == 0) return LAT_OK;
+  if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
-  if (int rc = lat_ensure_tables(P)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   const int n_c = P->d * (P->d + 1) / 2;
