@@ -1,20 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the lattice Basic Scheme (Algorithm 1, arXiv 1605.05712) on GB300.
 
-Workload (one "step"): the 2-D two-phase laminate (normal (1,3)/sqrt(10),
-volume fraction 1/2, isotropic phases (lam, mu) = (1,1) and (10,10), plane
-strain, C0 = mean of the phase extremes) on three lattices of m = 262,144
-points -- the tensor grid diag(512,512), the rank-1 lattice [[512,1],[0,512]]
-and the sheared rank-2 lattice [[512,16],[0,512]] -- with the three unit
-load cases solved one after another to a Cauchy residual of 1e-8, binary64
-throughout.  Metric: lattice-point iterations per second
-(sum over lattices and load cases of m x iterations / step time).
+Workload (one "step"): the 3-D generalized Hashin structure of Sec. 4.2 -- a coated ellipsoid (core
+semi-axes (0.1, 0.15, 0.2), total inclusion fraction 0.25, seeded rotation; core (lam, mu) = (10, 10),
+confocal coating (1, 1), matrix (1, 1) plus the rank-one correction that makes the coated inclusion
+neutral for eps0) -- on three lattices of m = 2^21 points: the tensor grid diag(128,128,128), the rank-1
+lattice [[128,1,0],[0,128,1],[0,0,128]] and the sheared full-rank lattice [[128,16,0],[0,128,16],[0,0,128]].
+Per lattice one solve of the six unit load cases batched (one launch set for all six), to a Cauchy
+residual of 1e-6, binary64 throughout (the paper's precision).  Metric: lattice-point iterations per
+second (sum over lattices and load cases of m x iterations / step time).
 
-Legs: device-timed steps with inputs resident in HBM (value), the same through
-the C ABI with the phase field copied host->device and the strain field
-copied back every step (e2e), per-kernel CUDA-event timing of one iteration
-(roofline), and the CPU oracle on a bounded sample (cpu_baseline).
-``--impl reference`` times the oracle alone.
+Legs: device-timed steps with inputs resident in HBM (value); the same through the C ABI with the phase
+fields copied host->device and all six strain fields of every lattice copied back every step (e2e);
+per-kernel CUDA-event timing of one batched iteration on each lattice, in binary64 (ALU roofline) and in
+mixed precision (HBM roofline); variants (mixed, double-float pairs, Eyre-Milton, conjugate gradients,
+time to r < 1e-6 against binary64, and the 2-D m = 262144 laminate); the CPU oracle on a bounded sample
+on the host cores (cpu_baseline).  ``--impl reference`` times the oracle alone.
 """
 import argparse
 import json
@@ -29,16 +30,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-LATS = ["grid512", "rank1_262144", "rank2_262144"]
-WORKLOAD = ("2-D laminate n=(1,3), m=262144 on diag(512,512), rank-1 [[512,1],[0,512]] and rank-2 "
-            "[[512,16],[0,512]]; 3 unit load cases solved separately; tol 1e-8; FP64")
+LATS = ["grid128", "rank1_2097152", "sheared128"]
+WORKLOAD = ("3-D generalized Hashin structure (coated ellipsoid, fraction 0.25, core/coating/matrix 10/1/1 + "
+            "rank-one neutrality correction), m=2^21 on diag(128,128,128), rank-1 [[128,1,0],[0,128,1],[0,0,128]] "
+            "and sheared [[128,16,0],[0,128,16],[0,0,128]]; 6 unit load cases batched per solve; tol 1e-6; FP64")
+TOL = 1e-6
+MAXIT = 2000
+N_LC = 6
+METRIC = "lattice-point iterations/s"
+N_SM = 152
+FP64_FMA_PER_SM_CLK = 2      # GB300 binary64 pipe: 2 FMA per SM per clock (1.25 TFLOP/s nominal near 2 GHz)
+L2_FLUSH_BYTES = 512 << 20
+# 2-D laminate of m = 262144 (a variant): normal (1,3), fraction 1/2, phases (1,1) and (10,10)
+LATS2 = ["grid512", "rank1_262144", "rank2_262144"]
 LAMES = [(1.0, 1.0), (10.0, 10.0)]
 N_INT = [1, 3]
-TOL = 1e-8
-MAXIT = 2000
-METRIC = "lattice-point iterations/s"
-FP64_PEAK_TFLOPS = 1.25
-L2_FLUSH_BYTES = 512 << 20
 
 
 def peaks():
@@ -48,10 +54,16 @@ def peaks():
         return {}
 
 
-def load_cases(n_c=3):
-    E = np.zeros((n_c, n_c))
-    for a in range(n_c):
-        E[a, a] = 1.0 if a < 2 else 0.5     # unit load cases, tensor components (eps_12 = 1/2)
+def fp64_peak_tflops(pk):
+    """Binary64 ALU peak from unit counts and the maximum SM clock: 152 SMs x 2 FMA x 2 flops x f_max."""
+    f = pk.get("sm_max_mhz") or 2070.0
+    return N_SM * FP64_FMA_PER_SM_CLK * 2 * f * 1e6 / 1e12
+
+
+def unit_loads(n_c):
+    E = np.eye(n_c)
+    d = 3 if n_c == 6 else 2
+    E[d:, d:] *= 0.5              # unit load cases in tensor components (eps_ij = eps_ji = 1/2)
     return E
 
 
@@ -94,81 +106,100 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def row_col_flops(P, n_c=3):
-    """Algorithmic flops of one iteration split by kernel (5 N log2 N per complex FFT of N points)."""
+# ------------------------------------------------------------------ cost model from the plan's decomposition
+def kernel_models(P, n_items, prec):
+    """Algorithmic flops and HBM bytes of every kernel of one batched iteration, in launch order (row pass,
+    then the column passes: forward groups innermost first, the Green group, inverse groups), from the
+    plan's FFT decomposition (lattice_plan_layout).  5 N log2 N flops per complex FFT of N points; ~10 flops
+    per complex value for each R2C pre/post-processing; 2 n_c^2 per point for the polarization and 3 n_c for
+    the update and residual; ~90 per complex frequency value for the Green operator; 6 per complex value for
+    each four-step twiddle.  Bytes: every HBM-resident word read and written once (spectrum slots of s bytes
+    per complex value, the strain as 8-byte words, one phase byte per point)."""
     import math
-    m, Rh = P["m"], P["Rh"]
-    # row pass: inverse + forward half-length complex FFT of every row and component, R2C pre/post
-    # processing (~10 flops per complex point each way), polarization (n_c^2 FMA), residual (3 n_c)
-    row = n_c * (2 * 5 * (m // 2) * math.log2(Rh) + 2 * 10 * (m // 2)) + m * (2 * n_c * n_c + 3 * n_c)
-    col = []
-    for G in P["groups"]:
-        f = n_c * 2 * 5 * (m // 2 + m // P["R"]) * math.log2(G)
-        col.append(f)
-    col[0] += (m // 2 + m // P["R"]) * 2 * 45       # Green operator, ~45 flops per real part
-    return row, col
+    lay = P.layout()
+    n_c, m = P.n_c, P.m
+    ax = lay["ax_len"]
+    R = ax[-1]
+    Rh = R // 2
+    spec = m // 2 + m // R                     # complex values per component: half spectrum + Nyquist plane
+    s = 8 if prec == "mixed" else 16
+    row_f = n_c * (m // R) * 2 * (5 * Rh * math.log2(max(Rh, 1)) + 10 * Rh) + m * (2 * n_c * n_c + 3 * n_c)
+    if len(ax) == 1:
+        row_f += 90 * spec
+    row_b = 2 * n_c * spec * s + 2 * n_c * m * 8 + m
+    out = [dict(kernel="row_pass", flops=n_items * row_f, bytes=n_items * row_b)]
+    groups = lay["groups"]
+    order = [(k, "gamma" if k == 0 else "fwd") for k in range(len(groups) - 1, -1, -1)] + \
+            [(k, "inv") for k in range(1, len(groups))]
+    for k, mode in order:
+        a0, a1 = groups[k]
+        G = int(np.prod(ax[a0:a1]))
+        dirs = 2 if mode == "gamma" else 1
+        f = n_c * dirs * 5 * spec * math.log2(G)
+        if mode == "gamma":
+            f += 90 * spec
+        if lay["split"]:
+            f += n_c * dirs * 6 * spec
+        out.append(dict(kernel="col_pass_%s_g%d" % (mode, k), flops=n_items * f, bytes=n_items * 2 * n_c * spec * s))
+    return out
 
 
-def algorithmic_bytes(P, n_c=3, s=8):
-    """HBM bytes of one iteration by kernel: row pass reads T + eps + phase, writes eps + T;
-    a column pass reads and writes T (half spectrum + Nyquist plane)."""
-    m = P["m"]
-    spec = n_c * (m // 2 + m // P["R"]) * 2 * s
-    row = spec + n_c * m * s + m + n_c * m * s + spec
-    col = [2 * spec for _ in P["groups"]]
-    return row, col
+def launches_per_solve(P, iters, prec):
+    """Kernels one batched solve launches: fill, (pair conversion), prologue, the loop body once per
+    iteration of the slowest item, (pair conversion back), effective stress."""
+    nk = 1 + max(0, 2 * len(P.layout()["groups"]) - 1)
+    return 1 + (2 if prec != "fp64" else 0) + nk + int(max(iters)) * nk + 1
 
 
-def setup(dev):
+# ------------------------------------------------------------------ workload
+def setup(dev, want_host=True):
     import torch
     from paper_1605_05712_gb300 import lattice_plan, synth
+    w = synth.hashin_workload()
     out = []
     for name in LATS:
         P = lattice_plan(synth.LATTICES[name])
-        ph = synth.laminate_phase(P.points(), P.m, N_INT)
-        out.append(dict(name=name, plan=P, phase_host=torch.from_numpy(ph).pin_memory(),
-                        phase=torch.from_numpy(ph).to(dev)))
-    return out
+        ph = synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+        item = dict(name=name, plan=P, phase=torch.from_numpy(ph).to(dev),
+                    eps=torch.empty((N_LC, 6, P.m), dtype=torch.float64, device=dev))
+        if want_host:
+            item["phase_host"] = torch.from_numpy(ph).pin_memory()
+            item["eps_host"] = torch.empty((N_LC, 6, P.m), dtype=torch.float64).pin_memory()
+        out.append(item)
+    return w, out
 
 
 PLAIN_LAUNCHES = False   # --plain-launches: iterate with plain launches instead of the CUDA-graph loop
 
+FORMS = {
+    # name: (precision, scheme options, reference medium: "mean" of the extremes or "geo" geometric mean)
+    "fp64": ("fp64", {}, "mean"),
+    "mixed": ("mixed", {}, "mean"),
+    "df64": ("df64", {}, "mean"),
+    "fp64_eyre_milton": ("fp64", {"scheme": "eyre_milton"}, "geo"),
+    "mixed_eyre_milton": ("mixed", {"scheme": "eyre_milton"}, "geo"),
+    "fp64_cg": ("fp64", {"scheme": "cg", "boundary": "zero"}, "mean"),
+    "df64_cg": ("df64", {"scheme": "cg", "boundary": "zero"}, "mean"),
+}
 
-C0_EM = (np.sqrt(1.0 * 10.0), np.sqrt(1.0 * 10.0))   # geometric mean of the laminate's extremes
 
-
-def run_step(work, stiff, C0, E, ws, eps, mode="fp64_separate", tol=TOL):
-    """One pass of the workload.  fp64_separate: each load case its own solve (the configured
-    form); *_batched: the three load cases of a lattice in one batched solve; df64 = the binary64-accurate
-    double-float kernels."""
+def run_step(w, work, ws, form="fp64", tol=TOL, to_host=False):
+    """One pass of the workload: per lattice one batched solve of the six unit load cases."""
     from paper_1605_05712_gb300 import basic_scheme_solve
-    tot = 0
-    iters = []
-    for w in work:
-        prec = mode.split("_")[0]                       # fp64, df64 or mixed
-        em = mode.endswith("_em")                       # Eyre-Milton at the geometric-mean reference
-        if mode.endswith("_cg"):                        # conjugate gradients (boundary frequencies zeroed)
-            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
-                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES, scheme="cg",
-                                   boundary="zero")
-            its = [int(x) for x in g["iters"]]
-        elif em:
-            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0_EM, E, tol=tol, maxit=MAXIT, workspace=ws,
-                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES, scheme="eyre_milton")
-            its = [int(x) for x in g["iters"]]
-        elif mode.endswith("_separate"):
-            its = []
-            for lc in range(E.shape[0]):
-                g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E[lc:lc + 1], tol=tol, maxit=MAXIT,
-                                       workspace=ws, eps_out=eps[lc:lc + 1], precision=prec,
-                                       plain_launches=PLAIN_LAUNCHES)
-                its.append(int(g["iters"][0]))
-        else:
-            g = basic_scheme_solve(w["plan"], w["phase"], stiff, C0, E, tol=tol, maxit=MAXIT, workspace=ws,
-                                   eps_out=eps, precision=prec, plain_launches=PLAIN_LAUNCHES)
-            its = [int(x) for x in g["iters"]]
+    prec, kw, c0 = FORMS[form]
+    C0 = w["C0"] if c0 == "mean" else (float(np.sqrt(10.0)),) * 2   # geometric mean of core and coating
+    E = unit_loads(6)
+    tot, iters = 0, []
+    for it in work:
+        if to_host:
+            it["phase"].copy_(it["phase_host"], non_blocking=True)
+        g = basic_scheme_solve(it["plan"], it["phase"], w["stiffness"], C0, E, tol=tol, maxit=MAXIT, workspace=ws,
+                               eps_out=it["eps"], precision=prec, plain_launches=PLAIN_LAUNCHES, **kw)
+        if to_host:
+            it["eps_host"].copy_(it["eps"], non_blocking=True)
+        its = [int(x) for x in g["iters"]]
         iters.append(its)
-        tot += w["plan"].m * int(np.sum(its))
+        tot += it["plan"].m * int(np.sum(its))
     return tot, iters
 
 
@@ -229,115 +260,163 @@ def aggregate_ranks(ms_list, units_list, world, device):
     return ms, [world * u / (m / 1e3) for u, m in zip(units_list, ms)]
 
 
+def roofline_of(w, work, prec, iters, pk, bound):
+    """Per-kernel CUDA-event times of one batched iteration (all six load cases, as the solve launches
+    them) on every lattice; the dominant kernel is the one with the largest share of the step (time per
+    launch x iterations of its lattice); achieved = its algorithmic flops or bytes per launch / its time."""
+    from paper_1605_05712_gb300 import lattice_pass_times
+    E = unit_loads(6)
+    rows, best = [], None
+    for it, its in zip(work, iters):
+        P = it["plan"]
+        ms = lattice_pass_times(P, it["phase"], w["stiffness"], w["C0"], E, precision=prec, n_reps=10)
+        models = kernel_models(P, N_LC, prec)
+        for k, (t, mo) in enumerate(zip(ms, models)):
+            share = t * max(its)
+            rec = dict(lattice=it["name"], kernel=mo["kernel"], ms=round(t, 5), flops=mo["flops"], bytes=mo["bytes"],
+                       share_ms_per_step=round(share, 3))
+            rows.append(rec)
+            if best is None or share > best["share_ms_per_step"]:
+                best = rec
+    t = best["ms"] * 1e-3
+    kname = best["kernel"].split("_")[0] + "_pass"
+    real = {"fp64": "double", "mixed": "float", "df64": "dfloat"}[prec]
+    tag = "%s<%s,6>/%s/%s" % (kname, real, best["kernel"], best["lattice"])
+    if bound == "alu":
+        peak = fp64_peak_tflops(pk)
+        ach = best["flops"] / t / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4),
+                "peak_source": "derived from unit counts and clocks: 152 SMs x 2 binary64 FMA/clk x 2 flops x "
+                               "%.0f MHz (sm_max_mhz of the measured peaks)" % (pk.get("sm_max_mhz") or 2070.0)}
+    else:
+        peak = pk.get("hbm_gbs")
+        ach = best["bytes"] / t / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4) if peak else None,
+                "peak_source": "hbm_gbs of MEASURED_PEAKS.json (of measured)" if peak else "no measured peak"}
+    roof.update({"traffic": profiled_traffic(tag), "kernel": tag, "algorithmic_flops_per_launch": best["flops"],
+                 "algorithmic_bytes_per_launch": best["bytes"], "ms_per_launch": best["ms"],
+                 "hbm_achieved_gbs": round(best["bytes"] / t / 1e9, 1),
+                 "per_kernel": rows})
+    return roof
+
+
 def bench_gpu(args):
     import torch
     import torch.distributed as dist
-    from paper_1605_05712_gb300 import lattice_pass_times, synth
     from paper_1605_05712_gb300.api import LAT_WS_CG
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)     # worker processes spawned before this process uses the GPU
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stiff = [synth.iso_voigt(*l) for l in LAMES]
-    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
-    E = load_cases()
-    work = setup(dev)
-    m = work[0]["plan"].m
-    ws = torch.empty(max(w["plan"].workspace_bytes(3, p) for w in work for p in (0, 1, 2, 0 | LAT_WS_CG, 2 | LAT_WS_CG)),
+    w, work = setup(dev)
+    ws = torch.empty(max(it["plan"].workspace_bytes(N_LC, p) for it in work for p in (0, 1, 2, 0 | LAT_WS_CG, 2 | LAT_WS_CG)),
                      dtype=torch.uint8, device=dev)
-    eps = torch.empty((3, 3, m), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        run_step(work, stiff, C0, E, ws, eps)
+        run_step(w, work, ws)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = Clocks(local)
-    ms_step, units, iters = timed(lambda: run_step(work, stiff, C0, E, ws, eps), args.steps, flush, st)
-    # end-to-end: host phase -> device, solves, strain -> host, every step
-    eps_host = torch.empty((3, 3, m), dtype=torch.float64).pin_memory()
-
-    def e2e_step():
-        for w in work:
-            w["phase"].copy_(w["phase_host"], non_blocking=True)
-        u, it = run_step(work, stiff, C0, E, ws, eps)
-        eps_host.copy_(eps, non_blocking=True)
-        return u, it
-    ms_e2e, e2e_units, _ = timed(e2e_step, args.steps, flush, st)
+    ms_step, units, iters = timed(lambda: run_step(w, work, ws), args.steps, flush, st)
+    # end-to-end: host phase fields -> device, solves, all six strain fields of every lattice -> host
+    ms_e2e, e2e_units, _ = timed(lambda: run_step(w, work, ws, to_host=True), args.steps, flush, st)
     clocks = clk.stop()
     (ms_step, ms_e2e), (value, e2e_value) = aggregate_ranks([ms_step, ms_e2e], [units, e2e_units], world, dev)
+    pk = peaks()
+    roof = roofline_of(w, work, "fp64", iters, pk, "alu")
 
-    # variants on the same inputs: batched load cases (binary64, mixed) and time to a 1e-6 residual
     variants = {}
     if not args.no_variants:
-        for mode in ("df64_separate", "fp64_batched", "df64_batched", "mixed_batched"):
-            run_step(work, stiff, C0, E, ws, eps, mode)
-            ms_v, u_v, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode), args.steps, flush, st)
-            variants[mode] = {"value": round(u_v / (ms_v / 1e3), 1), "ms_per_step": round(ms_v, 4), "iterations": it_v}
         ttt = {}
-        for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched", "fp64_batched_em",
-                     "mixed_batched_em", "fp64_batched_cg", "df64_batched_cg"):
-            run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6)
-            ms_v, _, it_v = timed(lambda: run_step(work, stiff, C0, E, ws, eps, mode, tol=1e-6), args.steps, flush, st)
-            ttt[mode] = {"ms": round(ms_v, 4), "iterations": it_v}
+        for form in ("mixed", "df64", "mixed_eyre_milton", "fp64_eyre_milton", "df64_cg", "fp64_cg"):
+            run_step(w, work, ws, form)
+            ms_v, u_v, it_v = timed(lambda: run_step(w, work, ws, form), max(1, min(args.steps, 3)), flush, st)
+            ttt[form] = {"ms": round(ms_v, 3), "value": round(u_v / (ms_v / 1e3), 1), "iterations": it_v,
+                         "speedup_vs_fp64": round(ms_step / ms_v, 2)}
+        ttt["fp64"] = {"ms": round(ms_step, 3), "value": round(value, 1), "iterations": iters}
         variants["time_to_resid_1e-6_ms"] = ttt
+        run_step(w, work, ws, "mixed")
+        variants["mixed_roofline"] = roofline_of(w, work, "mixed", ttt["mixed"]["iterations"], pk, "hbm")
+        variants["laminate2d_262144"] = bench_laminate2d(dev, args, flush, st)
 
-    # per-kernel timing of one iteration on the rank-2 lattice (dominant kernel -> roofline)
-    w = work[2]
-    P = w["plan"]
-    pt = lattice_pass_times(P, w["phase"], stiff, C0, E[0], n_reps=50)
-    pt_df = lattice_pass_times(P, w["phase"], stiff, C0, E[0], precision="df64", n_reps=50)
-    model = {"m": P.m, "R": 512, "Rh": 256, "groups": [512]}   # the planner's decomposition of all three lattices
-    bytes_row, bytes_col = algorithmic_bytes(model)
-    flops_row, flops_col = row_col_flops(model)
-    dom = int(np.argmax(pt[:2]))
-    ms_dom = pt[dom]
-    pk = peaks()
-    fl, by = (flops_row, bytes_row) if dom == 0 else (flops_col[0], bytes_col[0])
-    tag = ("row_pass" if dom == 0 else "col_pass") + "<double,3>/rank2_262144"
-    fp64_peak = FP64_PEAK_TFLOPS
-    roof = {"bound": "alu", "achieved": round(fl / (ms_dom * 1e-3) / 1e12, 4), "peak": fp64_peak,
-            "unit": "TFLOP/s", "frac": round(fl / (ms_dom * 1e-3) / 1e12 / fp64_peak, 4),
-            "traffic": profiled_traffic(tag), "kernel": tag,
-            "peak_source": "nominal GB300 binary64 rate 1.25 TFLOP/s (no FP64 entry in the measured peaks; an "
-                           "FMA-loop probe measured 1.19)",
-            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
-            "hbm_achieved_gbs": round(by / (ms_dom * 1e-3) / 1e9, 1),
-            "hbm_peak_gbs": pk.get("hbm_gbs"), "per_kernel_ms": [round(x, 5) for x in pt],
-            "df64_per_kernel_ms": [round(x, 5) for x in pt_df],
-            "df64_achieved_fp64_equiv_tflops": round(fl / (pt_df[dom] * 1e-3) / 1e12, 4)}
-    gpu_launches = 0
-    for it in iters:
-        for n in it:   # per solve: fill, prologue (row + column), n loop iterations, effective stress
-            gpu_launches += 1 + 2 + 2 * n + 1
+    gpu_launches = sum(launches_per_solve(it["plan"], its, "fp64") for it, its in zip(work, iters))
+    m_total = sum(it["plan"].m for it in work)
     res = {
         "metric": METRIC, "value": round(value, 1), "unit": "point-iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded laminate phases generated on the host)",
-        "config": {"workload": WORKLOAD, "lattices": LATS, "load_cases": 3, "tol": TOL, "iterations": iters,
-                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU",
+        "data": "synthetic (seeded coated-ellipsoid phases generated on the host)",
+        "config": {"workload": WORKLOAD, "lattices": LATS, "m": work[0]["plan"].m, "load_cases": N_LC, "tol": TOL,
+                   "iterations": iters,
+                   "l2": "inputs larger than L2 (strain 604 MB per lattice) and a 512 MiB write between timed steps",
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "launch": "plain launches, host convergence check per iteration" if PLAIN_LAUNCHES
                              else "one CUDA-graph WHILE loop per solve"},
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 1), "unit": "point-iterations/s",
-                "h2d_bytes_per_step": int(sum(w_["plan"].m for w_ in work)),
-                "d2h_bytes_per_step": int(eps.numel() * 8)},
+                "h2d_bytes_per_step": int(m_total),
+                "d2h_bytes_per_step": int(sum(it["eps"].numel() * 8 for it in work))},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "variants": variants,
     }
-    if rank == 0 and world == 1 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if cpu is not None:
+        res["cpu_baseline"] = cpu
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res))
+
+
+def bench_laminate2d(dev, args, flush, st):
+    """The 2-D laminate at m = 262144 on three lattices, the three unit load cases solved one after another
+    to tol 1e-8 in binary64 (and batched, and in the other precisions)."""
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan, synth
+    stiff = [synth.iso_voigt(*l) for l in LAMES]
+    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
+    E = unit_loads(3)
+    work = []
+    for name in LATS2:
+        P = lattice_plan(synth.LATTICES[name])
+        work.append((P, torch.from_numpy(synth.laminate_phase(P.points(), P.m, N_INT)).to(dev)))
+    ws = torch.empty(max(P.workspace_bytes(3, p) for P, _ in work for p in (0, 1, 2)), dtype=torch.uint8, device=dev)
+    eps = torch.empty((3, 3, work[0][0].m), dtype=torch.float64, device=dev)
+    out = {}
+    for mode in ("fp64_separate", "fp64_batched", "df64_batched", "mixed_batched"):
+        prec = mode.split("_")[0]
+
+        def step():
+            tot, its_all = 0, []
+            for P, ph in work:
+                if mode.endswith("separate"):
+                    its = []
+                    for lc in range(3):
+                        g = basic_scheme_solve(P, ph, stiff, C0, E[lc:lc + 1], tol=1e-8, maxit=MAXIT, workspace=ws,
+                                               eps_out=eps[lc:lc + 1], precision=prec)
+                        its.append(int(g["iters"][0]))
+                else:
+                    g = basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-8, maxit=MAXIT, workspace=ws, eps_out=eps,
+                                           precision=prec)
+                    its = [int(x) for x in g["iters"]]
+                its_all.append(its)
+                tot += P.m * sum(its)
+            return tot, its_all
+        step()
+        ms, u, its = timed(step, max(1, min(args.steps, 3)), flush, st)
+        out[mode] = {"value": round(u / (ms / 1e3), 1), "ms_per_step": round(ms, 3), "iterations": its}
+    return out
 
 
 def bench_hashin(args):
@@ -648,60 +727,97 @@ def profile_case(args):
     print(json.dumps({"profile_case": M, "precision": prec, "m": P.m, "ms_per_kernel": ms}))
 
 
-def oracle_sample(seconds, names=("rank2_262144",)):
-    """Time the CPU oracle on a bounded sample: a few iterations of the workload's solves."""
+def _oracle_proc(name, lc, iters, barrier, q):
+    """Spawned worker: build the lattice and phases of one config-3 problem, wait for the others at the
+    barrier, then run `iters` oracle iterations of unit load case lc (numpy float64, one thread)."""
+    sys.path.insert(0, ROOT)
     from oracle import elasticity as el
     from oracle.lattice import Lattice
     from oracle.scheme import basic_scheme
     from paper_1605_05712_gb300 import synth
-    S = np.array([el.voigt6_to_tensor(synth.iso_voigt(*l), 2) for l in LAMES])
-    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
-    units, t_total, n_it = 0, 0.0, 0
-    lats = {}
-    for nm in names:
-        L = Lattice(synth.LATTICES[nm])
-        lats[nm] = (L, synth.laminate_phase(L.p, L.m, N_INT))
-    E = el.comps_to_sym(load_cases()[0], 2)
-    while t_total < seconds:
-        for nm in names:
-            L, ph = lats[nm]
-            t0 = time.perf_counter()
-            r = basic_scheme(L, ph, S, C0, E, tol=0.0, maxit=2)
-            t_total += time.perf_counter() - t0
-            units += L.m * r["iters"]
-            n_it += r["iters"]
-    return units / t_total, t_total, n_it
+    w = synth.hashin_workload()
+    L = Lattice(synth.LATTICES[name])
+    ph = synth.coated_ellipsoid_phase(L.p, L.m, w["c"], w["rho_c"], w["rho_e"], R=w["R"])
+    S = np.array([el.voigt6_to_tensor(V, 3) for V in w["stiffness"]])
+    E = el.comps_to_sym(unit_loads(6)[lc], 3)
+    barrier.wait()
+    t0 = time.time()
+    r = basic_scheme(L, ph, S, w["C0"], E, tol=0.0, maxit=iters)
+    q.put((L.m * r["iters"], t0, time.time()))
+
+
+def _mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return 16 << 30
+
+
+ORACLE_BYTES = 3.5e9     # peak memory of one oracle solve at m = 2^21 (measured ~3.0 GB)
+
+
+def oracle_sample(n_proc, iters):
+    """n_proc spawned processes, each running `iters` oracle iterations of its own (lattice, load case) of
+    the config-3 workload at the same time; returns (point-iterations/s over the common wall time, wall
+    seconds).  Spawned, so no worker inherits a CUDA context."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(n_proc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_proc, args=(LATS[i % 3], i % 6, iters, barrier, q)) for i in range(n_proc)]
+    for p_ in procs:
+        p_.start()
+    res = [q.get() for _ in range(n_proc)]
+    for p_ in procs:
+        p_.join()
+    units = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / wall, wall
+
+
+def oracle_procs():
+    """Worker count: every host core, capped at 16 and at a quarter of the available memory."""
+    ncpu = os.cpu_count() or 1
+    return max(1, min(ncpu, 16, int(_mem_available() / 4 / ORACLE_BYTES)))
 
 
 def cpu_baseline(seconds):
-    v, t, n = oracle_sample(seconds)
-    return {"value": round(v, 1), "unit": "point-iterations/s", "cores": 1, "kind": "oracle",
-            "sample": "%d iterations of the oracle (numpy float64, single thread) on the rank-2 m=262144 "
-                      "laminate, unit load case 11, %.1f s" % (n, t)}
+    n = oracle_procs()
+    v1, t1 = oracle_sample(1, 1)
+    iters = max(1, int(round(seconds / max(t1, 1e-3))))
+    vn, tn = oracle_sample(n, iters)
+    return {"value": round(vn, 1), "unit": "point-iterations/s", "cores": n, "kind": "oracle",
+            "single_process_value": round(v1, 1),
+            "host_cpus": os.cpu_count(),
+            "sample": "%d processes, each %d oracle iteration(s) (numpy float64, one thread each) of one unit load "
+                      "case on one m=2^21 config-3 lattice, started together, %.1f s wall; single process: 1 "
+                      "iteration in %.1f s" % (n, iters, tn, t1)}
 
 
 def bench_reference(args):
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
-    vals = []
+    n = oracle_procs()
     for _ in range(args.warmup):
-        oracle_sample(1.0)
-    tt = 0
+        oracle_sample(1, 1)
+    vals, tt = [], 0.0
     for _ in range(args.steps):
-        v, t, n = oracle_sample(max(2.0, args.cpu_seconds / max(args.steps, 1)))
+        v, t = oracle_sample(n, 1)
         vals.append(v)
         tt += t
     v = float(np.mean(vals))
     res = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "point-iterations/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "ms_per_step": round(1e3 * tt / max(args.steps, 1), 2), "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "lattices": LATS, "load_cases": 3, "tol": TOL,
-                      "sample": "each step a bounded sample of the workload: oracle iterations on the rank-2 "
-                                "lattice [[512,16],[0,512]], unit load case 11, point-iterations counted"},
-           "cpu_baseline": {"value": round(v, 1), "unit": "point-iterations/s", "cores": 1, "kind": "oracle",
-                            "sample": "2-iteration oracle solves repeated for ~%.0f s per step" %
-                                      max(2.0, args.cpu_seconds / max(args.steps, 1))},
+           "config": {"workload": WORKLOAD, "lattices": LATS, "load_cases": N_LC, "tol": TOL,
+                      "sample": "each step a bounded sample of the workload: one oracle iteration in each of %d "
+                                "processes (lattice i mod 3, unit load case i mod 6), point-iterations counted" % n},
+           "cpu_baseline": {"value": round(v, 1), "unit": "point-iterations/s", "cores": n, "kind": "oracle",
+                            "host_cpus": os.cpu_count(),
+                            "sample": "%d concurrent single-thread oracle processes, 1 iteration each per step" % n},
            "e2e": {"value": round(v, 1), "unit": "point-iterations/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -721,7 +837,8 @@ def main():
                     help="with --profile-case: cg runs a conjugate-gradient solve of --steps iterations")
     ap.add_argument("--plain-launches", action="store_true",
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
-    ap.add_argument("--workload", default="laminate2d", choices=["laminate2d", "hashin3d", "warmstart", "sweep", "gather", "shear_sweep"])
+    ap.add_argument("--workload", default="default", choices=["default", "hashin3d", "warmstart", "sweep", "gather",
+                                                               "shear_sweep"])
     ap.add_argument("--ws-samples", type=int, default=2000)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)

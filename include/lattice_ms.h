@@ -454,19 +454,37 @@ int lattice_tune_info(const lat_plan* plan, int n_items, int precision, int* rpc
  * lattice_pass_times -- profiling helper: average device time of each kernel
  * of one Basic Scheme iteration (no counterpart in the paper; it measures
  * the passes the solve above runs inside its CUDA graph).  Runs the
- * prologue once and then n_reps iterations of load case 0 with plain
- * launches, a CUDA event pair around every launch on `stream`.  Arguments
- * as for basic_scheme_solve (eps is overwritten).
+ * prologue once and then n_reps iterations of the n_loads load cases as one
+ * batch (the launches basic_scheme_solve makes: every kernel covers all load
+ * cases) with plain launches, a CUDA event pair around every launch on
+ * `stream`.  Arguments as for basic_scheme_solve (E holds n_loads x n_c
+ * values; eps, n_loads x n_c x m, is overwritten).
  *   ms_out  host, >= 8 floats: [0] row pass, [1..] column passes in
  *           launch order (forward mid groups, Gamma group, inverse mid groups),
  *           unused entries set to 0.
  *   n_out   receives the number of kernels per iteration.
  */
 int lattice_pass_times(const lat_plan* plan, const uint8_t* phase, int n_phases,
-                       const double* stiffness, const double* C0, const double* E,
+                       const double* stiffness, const double* C0, const double* E, int n_loads,
                        int precision, int n_reps, double* eps,
                        void* workspace, size_t workspace_bytes, void* stream,
                        float* ms_out, int* n_out);
+
+/*
+ * lattice_plan_layout -- the FFT decomposition a plan chose for the pattern
+ * DFT of Sec. 2.2 (its d_M-dimensional DFT over the elementary divisors),
+ * for cost models and profiling (no counterpart in the paper).
+ *   nax        number of logical axes in storage order; the last one is the
+ *              contiguous row (a divisor axis may be split four-step into
+ *              two logical axes).
+ *   ax_len     host, >= 6 ints: their lengths.
+ *   ngroups    column passes per transform direction: group g covers the
+ *              logical axes [grp[2g], grp[2g+1]) (host, >= 6 ints); group 0
+ *              also applies the Green operator.
+ *   split      1 if the largest divisor is split four-step.
+ * Any output pointer may be NULL.
+ */
+int lattice_plan_layout(const lat_plan* plan, int* nax, int* ax_len, int* ngroups, int* grp, int* split);
 
 #ifdef __cplusplus
 }

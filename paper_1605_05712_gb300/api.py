@@ -149,6 +149,20 @@ class LatticePlan:
         a, ap = _f64(np.asarray(L, dtype=np.float64).reshape(self.d, self.d))
         _check(f(self._h, ap))
 
+    def layout(self):
+        """The FFT decomposition of the plan (lattice_plan_layout): dict(ax_len, groups, split); the last
+        logical axis is the contiguous row, group g covers logical axes [a0, a1) and group 0 applies
+        the Green operator."""
+        f = lib().lattice_plan_layout
+        f.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 5
+        f.restype = ctypes.c_int
+        nax, ng, split = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ax = (ctypes.c_int * 6)()
+        grp = (ctypes.c_int * 6)()
+        _check(f(self._h, ctypes.byref(nax), ax, ctypes.byref(ng), grp, ctypes.byref(split)))
+        return dict(ax_len=[ax[i] for i in range(nax.value)],
+                    groups=[(grp[2 * g], grp[2 * g + 1]) for g in range(ng.value)], split=split.value)
+
     def workspace_bytes(self, n_loads=1, precision=LAT_FP64):
         return int(lib().lattice_workspace_bytes(self._h, n_loads, precision))
 
@@ -267,25 +281,27 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
 
 
 def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=20, stream=None):
-    """Average device milliseconds per launch of each kernel of one iteration (profiling helper)."""
+    """Average device milliseconds per launch of each kernel of one iteration (profiling helper); E is
+    (n_c,) or (n_loads, n_c): the load cases run as one batch, as in basic_scheme_solve."""
     import torch
     stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
     C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
-    Ea, Ep = _f64(np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)[0])
+    Ea, Ep = _f64(np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c))
+    n_loads = Ea.shape[0]
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
-    eps = torch.empty((plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
-    ws = torch.empty(plan.workspace_bytes(1, prec), dtype=torch.uint8, device=phase.device)
+    eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
+    ws = torch.empty(plan.workspace_bytes(n_loads, prec), dtype=torch.uint8, device=phase.device)
     ms = (ctypes.c_float * 8)()
     n = ctypes.c_int()
     L = lib()
     L.lattice_pass_times.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + \
-        [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                                 ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
-                                                 ctypes.POINTER(ctypes.c_int)]
+        [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
     L.lattice_pass_times.restype = ctypes.c_int
     _check(L.lattice_pass_times(plan.handle, ctypes.c_void_p(phase.data_ptr()), stiff.shape[0], stiff_p, C0p, Ep,
-                                prec, int(n_reps), ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
-                                ws.numel(), _stream(stream), ms, ctypes.byref(n)))
+                                n_loads, prec, int(n_reps), ctypes.c_void_p(eps.data_ptr()),
+                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream), ms, ctypes.byref(n)))
     return [ms[i] for i in range(n.value)]
 
 

@@ -9,11 +9,12 @@
 
 #define LAT_MAX_AX 6
 #define LAT_MAX_GROUPS 3
+#define LAT_MAX_RADIX 16  // stages of a mixed-radix axis transform
 #define LAT_HIST_CAP 4096  // residuals kept per item in the workspace
 
 // One logical FFT axis in storage order (row-major, last = contiguous row).
 struct LatAxis {
-  int len;         // length (power of two)
+  int len;         // length (a power of two, or any length on a general plan)
   int log2len;
   int snf;         // elementary-divisor axis j this axis belongs to
   int64_t mult;    // k_j += mult * (spectral index on this axis)
@@ -61,6 +62,13 @@ struct lat_plan {
   // transformed pattern (lattice_plan_set_cell): has_cell and L^{-T}
   int has_cell;
   double cell_LinvT[3][3];
+  // general plans (an elementary divisor that is not a power of two): mixed-radix natural-order transforms,
+  // one logical axis per column pass, full complex spectrum; radices of each logical axis and the offset
+  // of its table of W_len^t in the twiddle table (the tables of all axes concatenated)
+  int general;
+  int ax_nrad[LAT_MAX_AX];
+  uint16_t ax_rad[LAT_MAX_AX][LAT_MAX_RADIX];
+  int ax_twoff[LAT_MAX_AX];
   // launch shapes picked by lattice_autotune, per precision and power-of-two bucket of the item count
   struct Tune {
     int valid;
@@ -86,6 +94,11 @@ struct LatDev {
   int tw_log2;
   const void* tw;             // twiddle table (double2 or float2, per precision)
   const void* stw;            // split twiddles [hi | lo]
+  // general plan: mixed-radix axes (see lat_plan)
+  int general;
+  int ax_nrad[LAT_MAX_AX];
+  uint16_t ax_rad[LAT_MAX_AX][LAT_MAX_RADIX];
+  int ax_twoff[LAT_MAX_AX];
   // transformed pattern P_L(M) (Sec. 3.3): Gamma0 at L^{-T} h; binary64, binary32 and pair copies
   int cell;
   double cellT[3][3];

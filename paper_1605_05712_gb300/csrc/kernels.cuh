@@ -172,6 +172,16 @@ template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
                         int rpc, int nthreads, size_t smem, cudaStream_t st);
 int lat_kernel_attrs(size_t max_smem);
+// mixed-radix kernels of general plans (kernels_gen.cu): binary64 and double-float pairs; the binary32
+// instantiations launch nothing (binary32 solves are refused on general plans)
+template <typename Real>
+void launch_gen_row(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
+                    cudaStream_t st);
+template <typename Real>
+void launch_gen_col(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st);
+void launch_gen_row_complex(const LatDev& dv, const void* in, void* out, int inverse, double scale, int rpc,
+                            int nthreads, size_t smem, cudaStream_t st);
+int lat_gen_kernel_attrs(int optin);
 // in place: binary64 strain -> double-float pairs (to_df = 1) or back (0), all items
 void launch_eps_df(const ItemDev* items, int n_items, int n_c, int64_t m, int to_df, cudaStream_t st);
 // restart of the increment form: glob->active = number of paused items, arrivals = 0

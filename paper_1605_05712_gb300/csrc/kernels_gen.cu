@@ -1,0 +1,337 @@
+// kernels_gen.cu -- the Basic Scheme iteration on lattices whose elementary divisors are not all powers of
+// two (Sec. 2.2: the pattern DFT is the d_M-dimensional DFT over the divisors e_j, for every regular M).
+//
+// Same pass structure as kernels.cu, with mixed-radix transforms (fft_mixed.cuh) in natural order and
+// the full complex spectrum (no real-to-complex packing: a row of odd length has no half-length
+// complex form).  Per item the spectrum T holds n_c planes of m complex values in spectral order, the
+// row axis last.  One iteration of Algorithm 1 (Sec. 3.2):
+//   gen_row_kernel : inverse FFT of the previous spectrum along the row -> eps^(n+1) (its real part),
+//                    Cauchy residual (Sec. 5.2) against eps^(n), eps written, polarization
+//                    tau = (C_y - C0) : eps, forward FFT along the row (Green operator here when the row
+//                    is the only axis);
+//   gen_col_kernel : one logical axis per launch on tiles of columns: four-step twiddle, forward FFT,
+//                    the Green operator (axis 0), inverse FFT, inverse twiddle.
+// Binary64 and double-float pairs only (the binary32 increment form needs the power-of-two kernels).
+#include <math.h>
+
+#include "fft_mixed.cuh"
+#include "kernels_dev.cuh"
+
+// strain slot of one point: binary64, or a double-float pair (hi, lo) during a pair solve
+template <typename Real>
+__device__ __forceinline__ Real eps_ld1(const double* p) {
+  if constexpr (is_df<Real>) {
+    const float2 o = *(const float2*)p;
+    return dfloat(o.x, o.y);
+  } else {
+    return *p;
+  }
+}
+template <typename Real>
+__device__ __forceinline__ void eps_st1(double* p, Real v) {
+  if constexpr (is_df<Real>) *(float2*)p = make_float2(v.hi, v.lo);
+  else *p = v;
+}
+
+// the two-level table of W_e^j of the four-step split: W_e^{(j >> s) << s} W_e^{j & (2^s - 1)}
+template <typename C>
+__device__ __forceinline__ C gen_split_tw(const LatDev& dv, int64_t j) {
+  const C* st = (const C*)dv.stw;
+  const int sh = dv.split_lo_log2;
+  return cmul(ldg_c(st + (j >> sh)), ldg_c(st + dv.stw_hi_n + (j & ((int64_t(1) << sh) - 1))));
+}
+
+// ------------------------------------------------------------------ row pass
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
+  typedef typename cplx_of<Real>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;
+  const int R = dv.Rlen, rpc = a.rpc, nlines = n_c * rpc;
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
+  const bool update = (a.flags & ROW_UPDATE) != 0;
+  if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) return;   // finished earlier
+  C* buf0 = (C*)smem_raw;
+  C* buf1 = buf0 + (size_t)nlines * R;
+  double* red = (double*)(buf1 + (size_t)nlines * R);
+  __shared__ int s_last;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t m = dv.m, r0 = (int64_t)blockIdx.x * rpc;
+  C* T = (C*)a.T + item_i * a.t_stride;
+  const int ra = dv.nax - 1;
+  const C* tw = (const C*)dv.tw + dv.ax_twoff[ra];
+  double* eps = item->eps;
+  const uint8_t* phase = item->phase;
+  C* cur = buf0;
+  if (a.flags & ROW_LOAD_EPS) {
+    for (int idx = tid; idx < nlines * R; idx += nthr) {
+      const int line = idx / R, n = idx - line * R;
+      const int c = line / rpc, row = line - c * rpc;
+      buf0[idx] = cpair<C>(eps_ld1<Real>(eps + (c * m + (r0 + row) * R + n)), Real(0));
+    }
+    __syncthreads();
+  } else {
+    for (int idx = tid; idx < nlines * R; idx += nthr) {
+      const int line = idx / R, n = idx - line * R;
+      const int c = line / rpc, row = line - c * rpc;
+      cp_async_elem(buf0 + idx, T + (c * m + (r0 + row) * R + n));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    cur = fft_mixed<C, true>(buf0, buf1, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, nlines, tw);
+  }
+  C* other = (cur == buf0) ? buf1 : buf0;
+  // pointwise: update, residual, polarization (the inverse transform's real part is eps^(n+1))
+  double dsum = 0.0;
+  dfloat dd_acc(0.f, 0.f), dd_shear(0.f, 0.f);
+  for (int idx = tid; idx < rpc * R; idx += nthr) {
+    const int row = idx / R, n = idx - row * R;
+    const int64_t g = (r0 + row) * R + n;
+    Real e[NC];
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) e[c] = cur[((size_t)c * rpc + row) * R + n].x;
+    const int ph = phase[g];
+    if (update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
+      // the transform returned u = (C + C0) eps: eps = (C_p + C0)^{-1} u
+      const Real* W = (is_df<Real> ? (const Real*)item->Wtab_df : (const Real*)item->Wtab) + ph * n_c * n_c;
+      Real u[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) u[c] = e[c];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        Real t = Real(0);
+#pragma unroll
+        for (int q = 0; q < n_c; ++q) t += ldg_r(W + c * n_c + q) * u[q];
+        e[c] = t;
+      }
+    }
+    if (update) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        double* pe = eps + (c * m + g);
+        const Real d = e[c] - eps_ld1<Real>(pe);
+        if constexpr (is_df<Real>) {
+          if (c >= D) df_acc_sq(dd_shear, d);
+          else df_acc_sq(dd_acc, d);
+        } else {
+          dsum += (c >= D ? 2.0 : 1.0) * (d * d);
+        }
+        eps_st1<Real>(pe, e[c]);
+      }
+    }
+    const Real* Dt = (is_df<Real> ? (const Real*)item->Dtab_df : (const Real*)item->Dtab) + ph * n_c * n_c;
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) {
+      Real t = Real(0);
+#pragma unroll
+      for (int q = 0; q < n_c; ++q) t += ldg_r(Dt + c * n_c + q) * e[q];
+      cur[((size_t)c * rpc + row) * R + n] = cpair<C>(t, Real(0));
+    }
+  }
+  __syncthreads();
+  C* out = fft_mixed<C, false>(cur, other, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, nlines, tw);
+  if (a.flags & ROW_GAMMA) {  // the row is the only logical axis: its spectrum is the whole spectrum
+    const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+    for (int idx = tid; idx < rpc * R; idx += nthr) {
+      const int row = idx / R, k = idx - row * R;
+      C val[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) val[c] = out[((size_t)c * rpc + row) * R + k];
+      int kk[LAT_MAX_AX] = {0};
+      kk[ra] = k;
+      green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) out[((size_t)c * rpc + row) * R + k] = val[c];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nlines * R; idx += nthr) {
+    const int line = idx / R, n = idx - line * R;
+    const int c = line / rpc, row = line - c * rpc;
+    T[c * m + (r0 + row) * R + n] = out[idx];
+  }
+  if (!update) return;
+  double* partials = a.it.partials + item_i * a.it.pstride;
+  double tot;
+  if constexpr (is_df<Real>) {
+    const dfloat pr = dd_acc + (dd_shear + dd_shear);
+    if (!item_reduce<1>(&pr, partials, isc, red, &s_last, &tot)) return;
+  } else {
+    if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
+  }
+  if (tid == 0) item_report(sqrt(tot) / item->norm0, isc, item_i, a.it);
+}
+
+// ------------------------------------------------------------------ column pass (one logical axis)
+// grid: (outer x tiles, items); a tile is w (a power of two) neighbouring columns of the axis a.a0 with
+// all n_f planes; columns are the indices of the axes after a0 (row axis included), tiles_main per outer
+template <typename Real, int NF>
+__global__ void __launch_bounds__(256) gen_col_kernel(LatDev dv, ColArgs a) {
+  typedef typename cplx_of<Real>::type C;
+  const int item_i = blockIdx.y;
+  if (a.scal) {
+    const int st = *(volatile const int*)&((const ItemScal*)((const char*)a.scal + (size_t)item_i * 256))->done;
+    if (st != ITEM_ACTIVE) return;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.G, x = a.a0, w = a.w, lgw = __ffs(w) - 1;
+  C* s0 = (C*)smem_raw;
+  C* s1 = s0 + (size_t)NF * L * w;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t tiles = a.tiles_main;
+  const int64_t o = blockIdx.x / tiles, t = blockIdx.x - o * tiles;
+  const int64_t ic = a.inner * a.row_slots;          // columns per outer index
+  const int64_t i0 = t * w;
+  const int wv = (int)min((int64_t)w, ic - i0);
+  const int64_t plane = a.outer * (int64_t)L * ic;
+  C* dst = (C*)a.T + item_i * a.t_stride;
+  const C* src = a.Tin ? (const C*)a.Tin : dst;
+  const int64_t base = o * L * ic + i0;
+  for (int idx = tid; idx < NF * L * w; idx += nthr) {
+    const int col = idx & (w - 1), g = (idx >> lgw) % L, f = (idx >> lgw) / L;
+    if (col < wv) cp_async_elem(s0 + idx, src + (f * plane + base + (int64_t)g * ic + col));
+    else s0[idx] = cmake<C>(0.0, 0.0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const C* tw = (const C*)dv.tw + dv.ax_twoff[x];
+  // four-step twiddle W_e^{n1 k2}: the split's n1 axis is the one before the row, so k2 = column index
+  if (a.has_twiddle && a.mode != COL_INV) {
+    for (int idx = tid; idx < L * w; idx += nthr) {
+      const int col = idx & (w - 1), g = idx >> lgw;
+      const C W = gen_split_tw<C>(dv, (int64_t)g * ((i0 + col) % dv.Rlen));
+#pragma unroll
+      for (int f = 0; f < NF; ++f) s0[(size_t)f * L * w + idx] = cmul(s0[(size_t)f * L * w + idx], W);
+    }
+    __syncthreads();
+  }
+  C* cur = s0;
+  if (a.mode != COL_INV) cur = fft_mixed<C, false>(s0, s1, L, dv.ax_rad[x], dv.ax_nrad[x], lgw, NF, tw);
+  if constexpr (NF >= 3) {
+    if (a.mode == COL_GAMMA) {
+      const ItemDev* item = a.items + item_i;
+      const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+      for (int idx = tid; idx < L * w; idx += nthr) {
+        const int col = idx & (w - 1), g = idx >> lgw;
+        int kk[LAT_MAX_AX] = {0};
+        kk[x] = g;
+        int64_t i = i0 + col;
+        for (int y = dv.nax - 1; y > x; --y) {
+          kk[y] = (int)(i % dv.ax_len[y]);
+          i /= dv.ax_len[y];
+        }
+        C val[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) val[f] = cur[(size_t)f * L * w + idx];
+        green_at<Real, NF>(dv, a.mat, item, gk, kk, val);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cur[(size_t)f * L * w + idx] = val[f];
+      }
+      __syncthreads();
+    }
+  }
+  if (a.mode != COL_FWD) {
+    C* other = (cur == s0) ? s1 : s0;
+    cur = fft_mixed<C, true>(cur, other, L, dv.ax_rad[x], dv.ax_nrad[x], lgw, NF, tw);
+    if (a.has_twiddle) {
+      for (int idx = tid; idx < L * w; idx += nthr) {
+        const int col = idx & (w - 1), g = idx >> lgw;
+        const C W = gen_split_tw<C>(dv, (int64_t)g * ((i0 + col) % dv.Rlen));
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cur[(size_t)f * L * w + idx] = cmulc(cur[(size_t)f * L * w + idx], W);
+      }
+      __syncthreads();
+    }
+  }
+  const bool do_scale = a.do_scale != 0;
+  const Real sc = do_scale ? (Real)a.scale : Real(1);
+  for (int idx = tid; idx < NF * L * w; idx += nthr) {
+    const int col = idx & (w - 1);
+    if (col >= wv) continue;
+    const int g = (idx >> lgw) % L, f = (idx >> lgw) / L;
+    C v = cur[idx];
+    if (do_scale) v = cscale(v, sc);
+    dst[f * plane + base + (int64_t)g * ic + col] = v;
+  }
+}
+
+// ------------------------------------------------------------------ complex row transform (lattice_fft)
+__global__ void __launch_bounds__(256) gen_row_complex_kernel(LatDev dv, const double2* in, double2* out,
+                                                              int inverse, double scale, int rpc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int R = dv.Rlen, ra = dv.nax - 1;
+  double2* b0 = (double2*)smem_raw;
+  double2* b1 = b0 + (size_t)rpc * R;
+  const int64_t off = (int64_t)blockIdx.x * rpc * R;
+  for (int idx = threadIdx.x; idx < rpc * R; idx += blockDim.x) b0[idx] = in[off + idx];
+  __syncthreads();
+  const double2* tw = (const double2*)dv.tw + dv.ax_twoff[ra];
+  double2* r = inverse ? fft_mixed<double2, true>(b0, b1, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, rpc, tw)
+                       : fft_mixed<double2, false>(b0, b1, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, rpc, tw);
+  for (int idx = threadIdx.x; idx < rpc * R; idx += blockDim.x) {
+    double2 v = r[idx];
+    if (scale != 1.0) v = cscale(v, scale);
+    out[off + idx] = v;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename Real>
+void launch_gen_row(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
+                    cudaStream_t st) {
+  if constexpr (is_f32<Real>) {
+    return;   // binary32 solves take the power-of-two kernels only (refused on entry for other plans)
+  } else {
+    const dim3 grid(nblocks, n_items);
+    if (dv.n_c == 6) gen_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+    else gen_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
+  }
+}
+template <typename Real>
+void launch_gen_col(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st) {
+  if constexpr (is_f32<Real>) {
+    return;
+  } else {
+    const dim3 grid((unsigned)(a.outer * a.tiles_main), n_items);
+    if (a.n_f == 6) gen_col_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+    else if (a.n_f == 3) gen_col_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
+    else if constexpr (!is_df<Real>) gen_col_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
+  }
+}
+void launch_gen_row_complex(const LatDev& dv, const void* in, void* out, int inverse, double scale, int rpc,
+                            int nthreads, size_t smem, cudaStream_t st) {
+  const int64_t nb = dv.nrows / rpc;
+  gen_row_complex_kernel<<<(unsigned)nb, nthreads, smem, st>>>(dv, (const double2*)in, (double2*)out, inverse, scale,
+                                                              rpc);
+}
+
+template void launch_gen_row<double>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_gen_row<float>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_gen_row<dfloat>(const LatDev&, const RowArgs&, int, int, int, size_t, cudaStream_t);
+template void launch_gen_col<double>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
+template void launch_gen_col<float>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
+template void launch_gen_col<dfloat>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
+
+template <typename K>
+static cudaError_t gen_set_smem(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+int lat_gen_kernel_attrs(int optin) {
+  cudaError_t e = gen_set_smem(gen_row_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 1>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_complex_kernel, optin);
+  return e == cudaSuccess ? 0 : (int)e;
+}

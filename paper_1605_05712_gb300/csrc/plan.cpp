@@ -184,6 +184,107 @@ void twiddle(int64_t t, int64_t N, double* re, double* im) {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// radices of a mixed-radix transform of length L: 4s, a 2, then the odd primes ascending
+static int factor_radices(int64_t L, uint16_t* rad) {
+  int n = 0;
+  while (L % 4 == 0 && n < LAT_MAX_RADIX) rad[n++] = 4, L /= 4;
+  while (L % 2 == 0 && n < LAT_MAX_RADIX) rad[n++] = 2, L /= 2;
+  for (int64_t p = 3; L > 1 && n < LAT_MAX_RADIX; p += 2)
+    while (L % p == 0 && n < LAT_MAX_RADIX) rad[n++] = (uint16_t)p, L /= p;
+  return L == 1 ? n : -1;
+}
+
+static void set_cv(lat_plan* P) {
+  for (int t = 0; t < P->nax; ++t) {
+    LatAxis& a = P->ax[t];
+    int j = a.snf;
+    for (int r = 0; r < P->d; ++r) {
+      i128 c = (i128)(P->ed / P->e[j]) * P->P[r][j];
+      a.cv[r] = (int64_t)mod((i128)a.mult * mod(c, P->ed), P->ed);
+    }
+  }
+}
+
+// Layout of a general plan (some divisor is not a power of two): every divisor axis is one logical axis
+// transformed in one pass; the last one (the contiguous row) is split four-step as A B when longer than
+// a line may be.  A line of every logical axis, all n_c planes, twice (ping-pong), must fit in shared
+// memory: 2 x n_c x L x 16 B <= 196 KB.
+static int choose_layout_general(lat_plan* P, const std::vector<int>& paxes) {
+  const int d = P->d, n_c = d * (d + 1) / 2;
+  const int64_t LMAX = (n_c == 3) ? 2048 : 1024;
+  P->general = 1;
+  for (size_t i = 0; i + 1 < paxes.size(); ++i)
+    if (P->e[paxes[i]] > LMAX)
+      return lat_fail(LAT_ERR_UNSUPPORTED, "elementary divisor " + std::to_string((long long)P->e[paxes[i]]) +
+                                               " is longer than one mixed-radix pass (" + std::to_string((long long)LMAX) +
+                                               " points) and not the largest");
+  const int jL = paxes.back();
+  const int64_t eL = P->e[jL];
+  int64_t B = eL;
+  if (eL > LMAX) {   // four-step: B (row) and A = eL / B both <= LMAX, B nearest sqrt(eL), the larger on the row
+    B = -1;
+    double best = 1e300;
+    for (int64_t b = 2; b <= LMAX; ++b)
+      if (eL % b == 0 && eL / b <= LMAX && b >= eL / b) {
+        const double dist = fabs(log((double)b) - 0.5 * log((double)eL));
+        if (dist < best) best = dist, B = b;
+      }
+    if (B < 0)
+      return lat_fail(LAT_ERR_UNSUPPORTED, "elementary divisor " + std::to_string((long long)eL) +
+                                               " needs more than one four-step split");
+  }
+  int na = 0;
+  for (size_t i = 0; i + 1 < paxes.size(); ++i) {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)P->e[paxes[i]];
+    a.snf = paxes[i];
+    a.mult = 1;
+  }
+  P->split = (B != eL);
+  if (P->split) {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)(eL / B);
+    a.snf = jL;
+    a.mult = B;  // k = k2 + B k1
+    P->split_n1 = na - 1;
+    P->split_e = eL;
+    P->split_lo_log2 = (ilog2(eL) + 1) / 2;
+  }
+  {
+    LatAxis& a = P->ax[na++];
+    a.len = (int)B;
+    a.snf = jL;
+    a.mult = 1;
+  }
+  P->nax = na;
+  int off = 0;
+  for (int i = 0; i < na; ++i) {
+    P->ax[i].log2len = ilog2(P->ax[i].len);
+    P->ax_nrad[i] = factor_radices(P->ax[i].len, P->ax_rad[i]);
+    if (P->ax_nrad[i] < 0) return lat_fail(LAT_ERR_UNSUPPORTED, "axis length with too many prime factors");
+    P->ax_twoff[i] = off;
+    off += P->ax[i].len;
+  }
+  P->Rlen = (int)B;
+  P->Rh = (int)(B / 2);
+  P->log2Rh = ilog2(std::max<int64_t>(P->Rh, 1));
+  P->nrows = P->m / B;
+  P->ngroups = na - 1;
+  for (int k = 0; k < na - 1; ++k) {
+    LatGroup& G = P->grp[k];
+    G.a0 = k;
+    G.a1 = k + 1;
+    G.G = P->ax[k].len;
+    G.outer = 1;
+    for (int t = 0; t < k; ++t) G.outer *= P->ax[t].len;
+    G.inner = 1;
+    for (int t = k + 1; t < na - 1; ++t) G.inner *= P->ax[t].len;
+    G.has_twiddle = P->split && k == P->split_n1;
+  }
+  set_cv(P);
+  return LAT_OK;
+}
+
 static int choose_layout(lat_plan* P) {
   const int d = P->d;
   std::vector<int> paxes;
@@ -191,10 +292,7 @@ static int choose_layout(lat_plan* P) {
     if (P->e[j] > 1) paxes.push_back(j);
   P->dM = (int)paxes.size();
   for (int j : paxes)
-    if (!is_pow2(P->e[j]))
-      return lat_fail(LAT_ERR_UNSUPPORTED,
-                      "elementary divisor " + std::to_string((long long)P->e[j]) +
-                          " is not a power of two (mixed-radix pattern FFT not built)");
+    if (!is_pow2(P->e[j])) return choose_layout_general(P, paxes);
   if (P->dM == 0) {  // m == 1
     P->nax = 0;
     P->ngroups = 0;
@@ -293,15 +391,7 @@ static int choose_layout(lat_plan* P) {
     G.has_twiddle = P->split && (P->split_n1 >= i && P->split_n1 < j);
     i = j;
   }
-  // v contributions
-  for (int t = 0; t < na; ++t) {
-    LatAxis& a = P->ax[t];
-    int j = a.snf;
-    for (int r = 0; r < d; ++r) {
-      i128 c = (i128)(P->ed / P->e[j]) * P->P[r][j];
-      a.cv[r] = (int64_t)mod((i128)a.mult * mod(c, P->ed), P->ed);
-    }
-  }
+  set_cv(P);   // v contributions
   return LAT_OK;
 }
 
@@ -314,7 +404,7 @@ static void set_table_sizes(lat_plan* P) {
   P->tw_log2 = lg;
   if (P->split) {
     P->stw_lo_n = int64_t(1) << P->split_lo_log2;
-    P->stw_hi_n = P->split_e >> P->split_lo_log2;
+    P->stw_hi_n = ((P->split_e - 1) >> P->split_lo_log2) + 1;
   }
 }
 
@@ -421,11 +511,17 @@ extern "C" int lattice_plan(const int64_t* Min, int d, lat_plan** out) {
 int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t* n_tw, int64_t* n_stw) {
   int lg = 1;
   for (int i = 0; i < P->nax; ++i) lg = std::max(lg, P->ax[i].log2len);
-  const int64_t N = int64_t(1) << lg;
+  // power-of-two plans: one table of W_N^t, N = 2^lg; general plans: the tables of W_len^t of every
+  // logical axis, concatenated
+  int64_t N = int64_t(1) << lg;
+  if (P->general) {
+    N = 0;
+    for (int i = 0; i < P->nax; ++i) N += P->ax[i].len;
+  }
   int64_t lo_n = 0, hi_n = 0;
   if (P->split) {
     lo_n = int64_t(1) << P->split_lo_log2;
-    hi_n = P->split_e >> P->split_lo_log2;
+    hi_n = ((P->split_e - 1) >> P->split_lo_log2) + 1;
   }
   if (n_tw) *n_tw = N;
   if (n_stw) *n_stw = hi_n + lo_n;
@@ -441,12 +537,19 @@ int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t*
       ((double2*)dst)[i] = make_double2(re, im);
     }
   };
-  if (tw)
+  if (tw && !P->general)
     for (int64_t t = 0; t < N; ++t) {
       double re, im;
       twiddle(t, N, &re, &im);
       put(tw, t, re, im);
     }
+  if (tw && P->general)
+    for (int i = 0; i < P->nax; ++i)
+      for (int64_t t = 0; t < P->ax[i].len; ++t) {
+        double re, im;
+        twiddle(t, P->ax[i].len, &re, &im);
+        put(tw, P->ax_twoff[i] + t, re, im);
+      }
   if (stw && P->split) {
     for (int64_t j = 0; j < hi_n; ++j) {
       double re, im;
@@ -500,6 +603,21 @@ extern "C" int lattice_plan_set_cell(lat_plan* P, const double* L) {
       P->cell_LinvT[i][j] = (A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1]) / det;
     }
   P->has_cell = 1;
+  return LAT_OK;
+}
+
+extern "C" int lattice_plan_layout(const lat_plan* P, int* nax, int* ax_len, int* ngroups, int* grp, int* split) {
+  if (!P) return lat_fail(LAT_ERR_ARG, "lattice_plan_layout: NULL plan");
+  if (nax) *nax = P->nax;
+  if (ax_len)
+    for (int a = 0; a < LAT_MAX_AX; ++a) ax_len[a] = a < P->nax ? P->ax[a].len : 0;
+  if (ngroups) *ngroups = P->ngroups;
+  if (grp)
+    for (int g = 0; g < LAT_MAX_GROUPS; ++g) {
+      grp[2 * g] = g < P->ngroups ? P->grp[g].a0 : 0;
+      grp[2 * g + 1] = g < P->ngroups ? P->grp[g].a1 : 0;
+    }
+  if (split) *split = P->split;
   return LAT_OK;
 }
 
@@ -587,7 +705,8 @@ extern "C" int lattice_gather_map(const lat_plan* from, const lat_plan* to, int3
   return LAT_OK;
 }
 
-// spectral slot of the complex transform (bit-reversed positions on every axis) -> k
+// spectral slot of the complex transform (bit-reversed positions on every axis of a power-of-two plan,
+// natural positions on a general plan) -> k
 static void slot_k(const lat_plan* P, int64_t slot, int64_t k[3]) {
   k[0] = k[1] = k[2] = 0;
   int64_t rest = slot;
@@ -596,8 +715,12 @@ static void slot_k(const lat_plan* P, int64_t slot, int64_t k[3]) {
     rest /= P->ax[a].len;
     int lg = P->ax[a].log2len;
     int64_t kk = 0;
-    for (int b = 0; b < lg; ++b)
-      if (pos & (int64_t(1) << b)) kk |= int64_t(1) << (lg - 1 - b);
+    if (P->general) {
+      kk = pos;   // mixed-radix transforms keep natural order
+    } else {
+      for (int b = 0; b < lg; ++b)
+        if (pos & (int64_t(1) << b)) kk |= int64_t(1) << (lg - 1 - b);
+    }
     k[P->ax[a].snf] += P->ax[a].mult * kk;
   }
 }

@@ -70,6 +70,12 @@ LatDev make_dev(const lat_plan* P, int kind) {
     dv.ax_log2[a] = P->ax[a].log2len;
     for (int r = 0; r < 3; ++r) dv.ax_cv[a][r] = P->ax[a].cv[r];
   }
+  dv.general = P->general;
+  for (int a = 0; a < LAT_MAX_AX; ++a) {
+    dv.ax_nrad[a] = P->ax_nrad[a];
+    dv.ax_twoff[a] = P->ax_twoff[a];
+    for (int r = 0; r < LAT_MAX_RADIX; ++r) dv.ax_rad[a][r] = P->ax_rad[a][r];
+  }
   dv.split = P->split;
   dv.split_n1 = P->split_n1;
   dv.split_lo_log2 = P->split_lo_log2;
@@ -128,7 +134,38 @@ int geometry_set_w(const lat_plan* P, int n_f, size_t cs, int row_slots, bool ny
 
 // row_slots = Rh (solver) or Rlen (complex transform); n_f planes per tile; n_items blocks in grid.y;
 // kind >= 0: a solve of that precision, which takes the plan's autotuned shapes when it has them
+// launch shapes of a general plan's mixed-radix kernels: two tile buffers (ping-pong) of n_f planes; rows
+// per block a power of two dividing the row count, column tiles of a power-of-two width (the last tile
+// of an axis may be ragged)
+static int geometry_general(const lat_plan* P, int n_f, size_t cs, Geometry& g, int n_items) {
+  const int nsm = num_sms();
+  const int64_t nrows = P->nrows, R = P->Rlen;
+  auto row_smem = [&](int rpc) { return 2 * (size_t)n_f * rpc * R * cs + 32 * sizeof(double); };
+  if (row_smem(1) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
+  int rpc = 1;
+  while (nrows % (2 * rpc) == 0 && row_smem(2 * rpc) <= kRowSmemTarget && n_items * (nrows / (2 * rpc)) >= 2 * nsm)
+    rpc *= 2;
+  g.rpc = rpc;
+  g.row_blocks = (int)(nrows / rpc);
+  g.row_smem = row_smem(rpc);
+  for (int k = 0; k < P->ngroups; ++k) {
+    const LatGroup& G = P->grp[k];
+    const int64_t ic = G.inner * R;
+    auto smem = [&](int64_t w) { return 2 * (size_t)n_f * G.G * w * cs; };
+    if (smem(1) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "column does not fit in shared memory");
+    int64_t w = 32;
+    while (w > 1 && (w / 2 >= ic || smem(w) > kColSmemMax || n_items * G.outer * ((ic + w - 1) / w) < 2 * nsm)) w /= 2;
+    g.w[k] = (int)w;
+    g.wN[k] = 0;
+    g.tiles_main[k] = (ic + w - 1) / w;
+    g.tiles_nyq[k] = 0;
+    g.col_smem[k] = smem(w);
+  }
+  return LAT_OK;
+}
+
 int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geometry& g, int n_items, int kind) {
+  if (P->general) return geometry_general(P, n_f, cs, g, n_items);
   const int nsm = num_sms();
   const int64_t nrows = P->nrows;
   int rpc = 1;
@@ -159,8 +196,9 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   const int n_c = P->d * (P->d + 1) / 2;
   const size_t cs = (precision == LAT_MIXED) ? 8 : 16;
   Work w;
-  w.t_per_lc = (size_t)n_c * (P->m / 2) * cs;
-  w.tn_per_lc = (size_t)n_c * P->nrows * cs;
+  // half spectrum + Nyquist plane (power-of-two plans), or the full complex spectrum (general plans)
+  w.t_per_lc = P->general ? (size_t)n_c * P->m * cs : (size_t)n_c * (P->m / 2) * cs;
+  w.tn_per_lc = P->general ? 0 : (size_t)n_c * P->nrows * cs;
   // two values per row block (conjugate gradients), n_c per block of the effective stress
   w.pstride = std::max<int64_t>(2 * P->nrows, (int64_t)kEffBlocksMax * 6);
   w.table_bytes = (size_t)phases_per_table * n_c * n_c * sizeof(double);
@@ -263,7 +301,15 @@ void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, C
   c.wN = g.wN[k];
   c.tiles_main = g.tiles_main[k];
   c.tiles_nyq = g.tiles_nyq[k];
-  launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
+  if (dv.general) launch_gen_col<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
+  else launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
+}
+
+// the row pass of a plan: power-of-two kernels or the mixed-radix kernels of a general plan
+template <typename Real>
+void launch_row(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, size_t smem, cudaStream_t st) {
+  if (dv.general) launch_gen_row<Real>(dv, a, nblocks, n_items, kThreads, smem, st);
+  else launch_row_pass<Real>(dv, a, nblocks, n_items, kThreads, smem, st);
 }
 
 template <typename Real>
@@ -295,7 +341,7 @@ void enqueue_body(const GroupRun& g, const RowArgs& full, cudaStream_t st) {
     launch_cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
     return;
   }
-  launch_row_pass<Real>(g.dv, full, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+  launch_row<Real>(g.dv, full, g.geo.row_blocks, g.n_items, g.geo.row_smem, st);
   enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
 }
 
@@ -592,8 +638,8 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     ra.it.n_items = n_items;
     ColArgs ca;
     memset(&ca, 0, sizeof(ca));
-    ca.row_slots = P->Rh;
-    ca.has_nyq = 1;
+    ca.row_slots = P->general ? P->Rlen : P->Rh;
+    ca.has_nyq = P->general ? 0 : 1;
     ca.n_f = n_c;
     ca.T = ra.T;
     ca.TN = ra.TN;
@@ -660,7 +706,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       g.cl.scal = ra.it.scal;
       g.cl.mat.increment = incr ? 1 : 0;   // the loop's spectra carry increments: k = 0 gets 0
       by_kind(g.kind, [&](auto tag) {
-        launch_row_pass<decltype(tag)>(dv, first, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        launch_row<decltype(tag)>(dv, first, geo.row_blocks, n_items, geo.row_smem, st);
         enqueue_columns<decltype(tag)>(dv, P, geo, c0, n_items, st);
         return 0;
       });
@@ -847,6 +893,9 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
   if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON && o.scheme != LAT_SCHEME_CG)
     return lat_fail(LAT_ERR_ARG, "bad scheme");
+  if (P && P->general && (o.precision == LAT_MIXED || o.scheme == LAT_SCHEME_CG))
+    return lat_fail(LAT_ERR_UNSUPPORTED, "lattices with an elementary divisor that is not a power of two run "
+                                         "Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 or LAT_DF64");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)
     return lat_fail(LAT_ERR_ARG, "the Eyre-Milton scheme takes the averaged boundary treatment");
   if (o.scheme == LAT_SCHEME_CG) {
@@ -1104,29 +1153,32 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
 }
 
 extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,
-                                  const double* C0, const double* E, int precision, int n_reps, double* eps,
-                                  void* workspace, size_t workspace_bytes, void* stream, float* ms_out, int* n_out) {
-  if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace || !ms_out || n_reps < 1)
+                                  const double* C0, const double* E, int n_loads, int precision, int n_reps,
+                                  double* eps, void* workspace, size_t workspace_bytes, void* stream, float* ms_out,
+                                  int* n_out) {
+  if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace || !ms_out || n_reps < 1 || n_loads < 1)
     return lat_fail(LAT_ERR_ARG, "lattice_pass_times: bad argument");
   if (P->nax == 0) return lat_fail(LAT_ERR_ARG, "lattice_pass_times: m = 1 has no passes");
+  if (P->general) return lat_fail(LAT_ERR_UNSUPPORTED, "lattice_pass_times: power-of-two plans only");
   // one solve with maxit = 1 sets up tables, workspace and the spectrum; then time plain launches
   lat_solve_opts o;
   memset(&o, 0, sizeof(o));
   o.precision = precision;
-  int rc = basic_scheme_solve(P, phase, n_phases, stiffness, C0, E, 1, 0.0, 1, &o, eps, nullptr, nullptr, nullptr,
-                              nullptr, workspace, workspace_bytes, stream);
+  int rc = basic_scheme_solve(P, phase, n_phases, stiffness, C0, E, n_loads, 0.0, 1, &o, eps, nullptr, nullptr,
+                              nullptr, nullptr, workspace, workspace_bytes, stream);
   if (rc < 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int d = P->d, n_c = d * (d + 1) / 2;
-  const Work wl = layout(P, 1, precision, kMaxPhases, 1);
+  const int ni = n_loads;
+  const Work wl = layout(P, ni, precision, kMaxPhases, 1);
   char* ws = (char*)workspace;
   const bool fp32 = (precision == LAT_MIXED);
   const LatDev dv = make_dev(P, precision);
   Geometry geo;
   memset(&geo, 0, sizeof(geo));
-  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, 1, precision)) != LAT_OK) return rc;
+  if ((rc = geometry(P, n_c, fp32 ? 8 : 16, P->Rh, true, geo, ni, precision)) != LAT_OK) return rc;
   // keep the item active for every timed launch: maxit far away, tol 0
-  CK(cudaMemsetAsync(ws + wl.scal, 0, 2 * kScalBytes, st));
+  CK(cudaMemsetAsync(ws + wl.scal, 0, (size_t)(ni + 1) * kScalBytes, st));
   RowArgs ra;
   memset(&ra, 0, sizeof(ra));
   ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0) | (fp32 ? ROW_INCREMENT | ROW_INCR_FIRST : 0);
@@ -1134,19 +1186,21 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ra.items = (const ItemDev*)(ws + wl.items);
   ra.T = ws + wl.T;
   ra.TN = ws + wl.TN;
+  ra.t_stride = (int64_t)(wl.t_per_lc / (fp32 ? 8 : 16));
+  ra.tn_stride = (int64_t)(wl.tn_per_lc / (fp32 ? 8 : 16));
   mat_set_gscale(ra.mat, -1.0 / (double)P->m);
   ra.it.partials = (double*)(ws + wl.partials);
   ra.it.pstride = wl.pstride;
   ra.it.scal = (ItemScal*)(ws + wl.scal);
-  ra.it.glob = (GlobScal*)(ws + wl.scal + kScalBytes);
+  ra.it.glob = (GlobScal*)(ws + wl.scal + (size_t)ni * kScalBytes);
   ra.it.hist = (double*)(ws + wl.hist);
   ra.it.tol = 0.0;
   ra.it.maxit = 1 << 30;
-  ra.it.n_items = 1;
+  ra.it.n_items = ni;
   ra.it.cond = 0;
   GlobScal g0;
   g0.arrivals = 0;
-  g0.active = 1;
+  g0.active = ni;
   CK(cudaMemcpyAsync(ra.it.glob, &g0, sizeof(g0), cudaMemcpyHostToDevice, st));
   ColArgs ca;
   memset(&ca, 0, sizeof(ca));
@@ -1155,6 +1209,8 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   ca.n_f = n_c;
   ca.T = ra.T;
   ca.TN = ra.TN;
+  ca.t_stride = ra.t_stride;
+  ca.tn_stride = ra.tn_stride;
   ca.scale = 1.0;
   ca.items = ra.items;
   ca.mat = ra.mat;
@@ -1162,12 +1218,12 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   std::vector<cudaEvent_t> ev(2 * nk);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   std::vector<double> acc(nk, 0.0);
-  if (precision != LAT_FP64) launch_eps_df(ra.items, 1, n_c, P->m, 1, st);   // as inside the solve
+  if (precision != LAT_FP64) launch_eps_df(ra.items, ni, n_c, P->m, 1, st);   // as inside the solve
   for (int rep = 0; rep < n_reps; ++rep) {
     int k = 0;
     CK(cudaEventRecord(ev[2 * k], st));
     by_kind(precision, [&](auto tag) {
-      launch_row_pass<decltype(tag)>(dv, ra, geo.row_blocks, 1, kThreads, geo.row_smem, st);
+      launch_row_pass<decltype(tag)>(dv, ra, geo.row_blocks, ni, kThreads, geo.row_smem, st);
       return 0;
     });
     CK(cudaEventRecord(ev[2 * k + 1], st));
@@ -1189,7 +1245,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
       c.tiles_nyq = geo.tiles_nyq[gi];
       cudaEventRecord(ev[2 * k], st);
       by_kind(precision, [&](auto tag) {
-        launch_col_pass<decltype(tag)>(dv, c, 1, kThreads, geo.col_smem[gi], st);
+        launch_col_pass<decltype(tag)>(dv, c, ni, kThreads, geo.col_smem[gi], st);
         return 0;
       });
       cudaEventRecord(ev[2 * k + 1], st);
@@ -1205,7 +1261,7 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
       acc[j] += ms;
     }
   }
-  if (precision != LAT_FP64) launch_eps_df(ra.items, 1, n_c, P->m, 0, st);
+  if (precision != LAT_FP64) launch_eps_df(ra.items, ni, n_c, P->m, 0, st);
   CK(cudaStreamSynchronize(st));
   for (auto& e : ev) cudaEventDestroy(e);
   for (int j = 0; j < 8; ++j) ms_out[j] = j < nk ? (float)(acc[j] / n_reps) : 0.0f;
@@ -1261,16 +1317,19 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       c.Tin = tin;
       c.scale = scale;
       c.do_scale = scale != 1.0;
-      launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[k], st);
+      if (P->general) launch_gen_col<double>(dv, c, 1, kThreads, geo.col_smem[k], st);
+      else launch_col_pass<double>(dv, c, 1, kThreads, geo.col_smem[k], st);
+    };
+    auto row = [&](const void* rin, int inv, double scale) {
+      if (P->general) launch_gen_row_complex(dv, rin, fout, inv, scale, geo.rpc, kThreads, geo.row_smem, st);
+      else launch_row_complex<double>(dv, rin, fout, 1, inv, scale, geo.rpc, kThreads, geo.row_smem, st);
     };
     if (!inverse) {
-      launch_row_complex<double>(dv, fin, fout, 1, 0, P->ngroups == 0 ? inv_m : 1.0, geo.rpc, kThreads,
-                                 geo.row_smem, st);
+      row(fin, 0, P->ngroups == 0 ? inv_m : 1.0);
       for (int k = P->ngroups - 1; k >= 0; --k) col(k, COL_FWD, nullptr, k == 0 ? inv_m : 1.0);
     } else {
       for (int k = 0; k < P->ngroups; ++k) col(k, COL_INV, k == 0 ? (const void*)fin : nullptr, 1.0);
-      launch_row_complex<double>(dv, P->ngroups == 0 ? (const void*)fin : (const void*)fout, fout, 1, 1, 1.0,
-                                 geo.rpc, kThreads, geo.row_smem, st);
+      row(P->ngroups == 0 ? (const void*)fin : (const void*)fout, 1, 1.0);
     }
     CK(cudaGetLastError());
   }

@@ -158,6 +158,7 @@ extern "C" int lattice_autotune(lat_plan* P, int n_items, int precision, void* w
   const TuneWs tw = tune_layout(P, n_items, precision);
   if (workspace_bytes < tw.total) return lat_fail(LAT_ERR_SIZE, "lattice_autotune: workspace too small");
   if (P->nax == 0) return LAT_OK;
+  if (P->general) return lat_fail(LAT_ERR_UNSUPPORTED, "lattice_autotune: power-of-two plans only");
   if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   cudaStream_t st = (cudaStream_t)stream;

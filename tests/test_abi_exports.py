@@ -34,13 +34,16 @@ def test_host_side_plan_without_gpu():
     import numpy as np
     from oracle.lattice import Lattice
     from paper_1605_05712_gb300 import LatticeError, lattice_plan
-    for M in ([[8, -4], [2, 7]], [[512, 16], [0, 512]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]]):
+    for M in ([[8, -4], [2, 7]], [[512, 16], [0, 512]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]],
+              [[3, 0], [0, 5]], [[6, 2], [0, 10]], [[3072, 0], [0, 1]], [[1, 0, 0], [0, 3, 0], [0, 0, 45]]):
         P = lattice_plan(M)
         L = Lattice(M)
         assert P.m == L.m and P.divisors == L.e
         assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
         assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
-    for bad, code in (([[2, 4], [1, 2]], -2), ([[3, 0], [0, 5]], -5)):
+    # singular; a divisor longer than one mixed-radix pass that is not the largest; one whose four-step
+    # split would need a factor above the pass length (a prime beyond it)
+    for bad, code in (([[2, 4], [1, 2]], -2), ([[3000, 0], [0, 3000]], -5), ([[4099, 0], [0, 1]], -5)):
         try:
             lattice_plan(bad)
             raise AssertionError("expected an error")

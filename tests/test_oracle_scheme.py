@@ -93,7 +93,7 @@ def test_laminate_closed_forms_agree_with_milton():
             assert np.abs(el.ddot(Ce, E) - sb).max() < 1e-11
 
 
-@pytest.mark.parametrize("N", [(8, 8), (6, 10), (3, 4), (4, 4, 4), (2, 6, 4)])
+@pytest.mark.parametrize("N", [(8, 8), (6, 10), (3, 4), (5, 7), (4, 4, 4), (2, 6, 4), (3, 5, 9)])
 def test_diagonal_lattice_equals_classic_grid_scheme(N):
     d = len(N)
     M = np.diag(N).tolist()
