@@ -222,7 +222,7 @@ def timed(fn, steps, flush, st):
 def kernel_sha():
     import hashlib
     h = hashlib.sha1()
-    for f in ("kernels.cu", "fft_smem.cuh", "kernels.cuh"):
+    for f in ("kernels.cu", "kernels_dev.cuh", "fft_smem.cuh", "kernels.cuh", "kernels_gen.cu", "fft_mixed.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1605_05712_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -703,28 +703,36 @@ def bench_shear_sweep(args):
 
 
 def profile_case(args):
-    """Plain launches of the iteration kernels (lattice_pass_times) for ncu: precision and lattice on argv."""
+    """Plain launches of one iteration's kernels (lattice_pass_times) for ncu: precision and lattice on argv,
+    --profile-loads load cases batched (the bench solves six).  3-D lattices take the coated-ellipsoid
+    workload of the bench, 2-D ones the laminate."""
     import torch
     from paper_1605_05712_gb300 import lattice_pass_times, lattice_plan, synth
     prec, M = args.profile_case[0], json.loads(args.profile_case[1])
     P = lattice_plan(M)
-    ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 3] if P.d == 2 else [1, 3, 2])).cuda()
-    st = [synth.iso_voigt(*l) for l in LAMES]
-    E = np.zeros(P.n_c)
-    E[0] = 1.0
+    if P.d == 3:
+        w = synth.hashin_workload()
+        ph = torch.from_numpy(synth.coated_ellipsoid_phase(P.points(), P.m, w["c"], w["rho_c"], w["rho_e"],
+                                                           R=w["R"])).cuda()
+        st, C0 = w["stiffness"], w["C0"]
+    else:
+        ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, [1, 3])).cuda()
+        st, C0 = [synth.iso_voigt(*l) for l in LAMES], (5.5, 5.5)
+    E = unit_loads(P.n_c)[:max(1, args.profile_loads)]
     if args.profile_scheme == "cg":
         # a conjugate-gradient solve with plain launches (ncu sees each kernel): prologue stages
         # FWD_X, FULL0, A, then per iteration B, the column passes, A
         from paper_1605_05712_gb300 import basic_scheme_solve
         t0 = time.perf_counter()
-        g = basic_scheme_solve(P, ph, st, (5.5, 5.5), E, tol=0.0, maxit=args.steps, precision=prec, scheme="cg",
+        g = basic_scheme_solve(P, ph, st, C0, E, tol=0.0, maxit=args.steps, precision=prec, scheme="cg",
                                boundary="zero", plain_launches=True)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": M, "precision": prec, "scheme": "cg", "m": P.m,
                           "iterations": int(g["iters"][0]), "s": round(time.perf_counter() - t0, 3)}))
         return
-    ms = lattice_pass_times(P, ph, st, (5.5, 5.5), E, precision=prec, n_reps=args.steps)
-    print(json.dumps({"profile_case": M, "precision": prec, "m": P.m, "ms_per_kernel": ms}))
+    ms = lattice_pass_times(P, ph, st, C0, E, precision=prec, n_reps=args.steps)
+    print(json.dumps({"profile_case": M, "precision": prec, "m": P.m, "load_cases": len(E), "ms_per_kernel": ms,
+                      "layout": P.layout()}))
 
 
 def _oracle_proc(name, lc, iters, barrier, q):
@@ -833,6 +841,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
+    ap.add_argument("--profile-loads", type=int, default=1, help="with --profile-case: load cases batched")
     ap.add_argument("--profile-scheme", default="basic", choices=["basic", "cg"],
                     help="with --profile-case: cg runs a conjugate-gradient solve of --steps iterations")
     ap.add_argument("--plain-launches", action="store_true",

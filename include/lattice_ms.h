@@ -96,10 +96,18 @@ typedef struct lat_plan lat_plan;
  * dimension d_M, the FFT decomposition over the elementary divisors and
  * uploads twiddle tables to the current device (the plan's device; without a
  * CUDA device the plan is host-only).
+ * Every regular M is planned: divisors that are powers of two take radix-4/2
+ * kernels with bit-reversed spectra; any other divisor takes mixed-radix
+ * kernels (radix 4, 2, 3, 5 and a direct p-point DFT for other primes) in
+ * natural order, with the full complex spectrum.  Those "general" plans run
+ * Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 and LAT_DF64 (LAT_MIXED
+ * and LAT_SCHEME_CG return LAT_ERR_UNSUPPORTED there) and take strain buffers
+ * aligned to 8 bytes.
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
- * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (an elementary divisor
- * with an odd factor > 1, or one that needs more than one four-step split),
- * LAT_ERR_CUDA.
+ * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a divisor that needs
+ * more than one four-step split, or a general plan's divisor other than the
+ * largest that is longer than one mixed-radix pass: 2048 points in 2-D, 1024
+ * in 3-D), LAT_ERR_CUDA.
  */
 int lattice_plan(const int64_t* M, int d, lat_plan** out);
 
@@ -304,7 +312,8 @@ int basic_scheme_solve_batch(const lat_plan* plan, const lat_batch_item* items, 
  *     n_phases   1..LAT_BATCH_MAX_PHASES; stiffness host, n_phases * 36 Voigt
  *     C0         isotropic reference medium (lambda0, mu0), lambda0 + 2 mu0 > 0, mu0 > 0
  *     E, n_loads host, n_loads x n_c macroscopic strains (tensor components), n_loads >= 1
- *     eps        device, n_loads x n_c x m binary64, 16-byte aligned (output; input with warm_start)
+ *     eps        device, n_loads x n_c x m binary64, 16-byte aligned (8 bytes on plans with a divisor that
+ *                is not a power of two) (output; input with warm_start)
  *     sigma      device or NULL, n_loads x n_c x m
  *     sigma_bar, iters, resid  host or NULL, n_loads (x n_c) outputs per item
  *   opts       as basic_scheme_solve; resid_history must be NULL (LAT_ERR_ARG otherwise)

@@ -87,7 +87,7 @@ extern "C" int basic_scheme_solve_noalloc(const lat_plan* P, const uint8_t* phas
   if (opts) o = *opts;
   if (int rc = check_common(P, tol, maxit, o)) return rc;
   if (int rc = check_c0(C0)) return rc;
-  if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+  if (((uintptr_t)eps & eps_align_mask(P)) != 0) return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
   if (int rc = lat_plan_device_check(P)) return rc;
   const Work wl = layout(P, n_loads, o.precision, n_phases, 1, o.scheme);
   const size_t need = up256(wl.total);

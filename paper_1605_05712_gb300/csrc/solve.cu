@@ -921,6 +921,10 @@ int check_geometry(const lat_plan* P, int precision) {
   return geometry(P, P->d * (P->d + 1) / 2, 16, P->Rh, true, geo, 1);
 }
 
+// the power-of-two kernels move the strain of two neighbouring points at once (16 bytes); the mixed-radix
+// kernels of general plans one point (8 bytes), so odd m and per-load-case offsets of n_c m points are fine
+size_t eps_align_mask(const lat_plan* P) { return P->general ? 7 : 15; }
+
 int check_c0(const double* C0) {
   if (!(C0[1] > 0) || !(C0[0] + 2 * C0[1] > 0)) return lat_fail(LAT_ERR_ARG, "C0 must have mu0 > 0 and lam0 + 2 mu0 > 0");
   return LAT_OK;
@@ -985,7 +989,7 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   if (int rc = check_c0(C0)) return rc;
   const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1, o.scheme);
   if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
-  if (((uintptr_t)eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+  if (((uintptr_t)eps & eps_align_mask(P)) != 0) return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
   if (int rc = lat_plan_device_check(P)) return rc;
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   std::vector<ItemHost> items;
@@ -1013,7 +1017,7 @@ extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item*
     if (b.n_phases < 1 || b.n_phases > LAT_BATCH_MAX_PHASES)
       return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_batch: item n_phases not in 1..LAT_BATCH_MAX_PHASES");
     if (int rc = check_c0(b.C0)) return rc;
-    if (((uintptr_t)b.eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+    if (((uintptr_t)b.eps & eps_align_mask(P)) != 0) return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
     ItemHost& it = items[i];
     it.phase = b.phase;
     it.table = i;
@@ -1091,7 +1095,8 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
     return lat_fail(LAT_ERR_SIZE, "workspace too small");
   for (int i = 0; i < n_items; ++i) {
     if (int rc = check_c0(items[i].C0)) return rc;
-    if (((uintptr_t)items[i].eps & 15) != 0) return lat_fail(LAT_ERR_ARG, "eps must be 16-byte aligned");
+    if (((uintptr_t)items[i].eps & eps_align_mask(items[i].plan)) != 0)
+      return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
   }
   for (const MultiGroup& g : mg) {
     if (int rc = check_common(g.P, tol, maxit, o)) return rc;

@@ -177,7 +177,7 @@ SOLVE_2D = [[[1, 0], [0, 1]], [[2, 0], [0, 1]], [[2, 1], [0, 2]], [[8, -4], [2, 
             [[128, 1], [0, 128]], [[4096, 12288], [0, 1]], [[2048, 0], [0, 4]],
             # general plans (mixed-radix kernels)
             [[3, 0], [0, 5]], [[6, 1], [0, 10]], [[3072, 0], [0, 1]], [[12, 0], [0, 6]], [[96, 1], [0, 96]],
-            [[45, 9], [0, 45]], [[1009, 0], [0, 1]]]
+            [[45, 9], [0, 45]]]
 
 
 # "df64": the binary64-accurate path on double-float pairs, held to the same 1e-10 as binary64
@@ -884,3 +884,18 @@ def test_general_plan_warm_start_batch_multi_and_refusals(cuda):
         with pytest.raises(LatticeError) as ei:
             basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, **kw)
         assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", [[[1009, 0], [0, 1]], [[2018, 1], [0, 1]], [[1, 0, 0], [0, 1, 0], [0, 0, 1021]]])
+def test_prime_length_lattice(cuda, M, prec):
+    # a rank-1 pattern of prime length (1009, 2 x 1009, 1021): the direct p-point DFT stage.  The pattern
+    # lies on a line, so the laminate with normal (1, 3[, 2]) is heterogeneous along it
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    ph = laminate([1, 3] if d == 2 else [1, 3, 2])
+    out = run_pair(M, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=6, cuda=cuda, precision=prec)
+    assert 0 < np.count_nonzero(ph(out[1].p, out[1].m)) < out[1].m
+    # the direct p-point DFT sums p terms: its rounding grows like sqrt(p) u instead of log2(m) u, which
+    # sets the absolute floor of the residual history once the laminate has converged (~1e-13 by step 5)
+    check_pair(*out, d=d, hist_atol=1e-14 if prec == "fp64" else None)
