@@ -269,6 +269,26 @@ int basic_scheme_solve(const lat_plan* plan, const uint8_t* phase, int n_phases,
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * basic_scheme_solve_async -- basic_scheme_solve (Algorithm 1, Sec. 3.2) without the final host
+ * synchronization: everything is enqueued on `stream` (the iteration is the CUDA-graph loop) and the
+ * call returns at once; the scalar results are written to device memory at the end of the solve.
+ *   sigma_bar_d  device or NULL, n_loads x n_c binary64: mean stress per load case
+ *   iters_d      device or NULL, n_loads int32: iterations performed
+ *   resid_d      device or NULL, n_loads binary64: last Cauchy residual
+ *   status_d     device or NULL, n_loads int32: LAT_OK, LAT_NOT_CONVERGED or LAT_DIVERGED per load case
+ * Other arguments as for basic_scheme_solve; opts->resid_history must be NULL and plain_launches 0
+ * (LAT_ERR_ARG otherwise).  phase, eps, sigma, the workspace and the result arrays must stay valid
+ * until the stream has passed the solve.  Host-side argument errors are returned before anything is
+ * enqueued; the return value is LAT_OK once the solve is enqueued (its outcome is in status_d).
+ */
+int basic_scheme_solve_async(const lat_plan* plan, const uint8_t* phase, int n_phases,
+                             const double* stiffness, const double* C0,
+                             const double* E, int n_loads, double tol, int maxit,
+                             const lat_solve_opts* opts, double* eps, double* sigma,
+                             double* sigma_bar_d, int* iters_d, double* resid_d, int* status_d,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Batches of independent microstructures on one lattice (shared plan): each
  * item has its own phase field, material, reference medium, macroscopic
  * strain and outputs, and stops on its own residual.  All items run in the

@@ -280,6 +280,52 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     return out
 
 
+def basic_scheme_solve_async(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
+                             boundary="average", eps0=None, want_sigma=False, workspace=None, eps_out=None,
+                             stream=None, mixed_increment=True, mixed_restart=True, scheme="basic"):
+    """Algorithm 1 enqueued on the stream without a host synchronization (basic_scheme_solve_async): returns
+    at once with device tensors sigma_bar (n_loads, n_c), iters, resid and status (n_loads) that are valid
+    once the stream has passed the solve (e.g. after torch.cuda.synchronize())."""
+    import torch
+    stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
+    n_ph = stiff.shape[0]
+    C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
+    E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
+    n_loads = E.shape[0]
+    Ea, Ep = _f64(E)
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+        raise TypeError("phase must be a uint8 CUDA tensor with m entries")
+    dev = phase.device
+    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
+                                                          device=dev)
+    if eps0 is not None:
+        eps.copy_(eps0)
+    sigma = torch.empty_like(eps) if want_sigma else None
+    wsb = plan.workspace_bytes(n_loads, prec | (LAT_WS_CG if scheme == "cg" else 0))
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sbar = torch.empty((n_loads, plan.n_c), dtype=torch.float64, device=dev)
+    iters = torch.empty(n_loads, dtype=torch.int32, device=dev)
+    resid = torch.empty(n_loads, dtype=torch.float64, device=dev)
+    status = torch.empty(n_loads, dtype=torch.int32, device=dev)
+    opts = _Opts(prec, bnd, 1 if eps0 is not None else 0, None, 1 if mixed_increment else 0,
+                 0 if mixed_restart else -1, 0, _SCHEMES[scheme])
+    f = lib().basic_scheme_solve_async
+    vp = ctypes.c_void_p
+    f.argtypes = [vp, vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3 + \
+        [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp,
+         ctypes.c_size_t, vp]
+    f.restype = ctypes.c_int
+    rc = f(plan.handle, vp(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
+           ctypes.byref(opts), vp(eps.data_ptr()), vp(sigma.data_ptr()) if sigma is not None else None,
+           vp(sbar.data_ptr()), vp(iters.data_ptr()), vp(resid.data_ptr()), vp(status.data_ptr()),
+           vp(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(rc)
+    # the tensors the enqueued work reads or writes are returned so that they outlive it
+    return dict(eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid, status=status, workspace=ws)
+
+
 def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=20, stream=None):
     """Average device milliseconds per launch of each kernel of one iteration (profiling helper); E is
     (n_c,) or (n_loads, n_c): the load cases run as one batch, as in basic_scheme_solve."""

@@ -69,6 +69,23 @@ __device__ __forceinline__ C twid(const C* __restrict__ tw, int tw_log2, int log
   return ldg_c(&tw[j << (tw_log2 - log2L)]);
 }
 
+// the three twiddles W_L^j, W_L^{2j}, W_L^{3j} of a radix-4 butterfly.  Binary32 kernels load W_L^j and
+// form the powers by complex multiplication (two products instead of two table loads, whose latency the
+// binary32 passes wait on; about one rounding more, inside the mixed-precision tolerance); binary64 and
+// pair kernels load all three (their arithmetic pipes, not the loads, bound them)
+template <typename C>
+__device__ __forceinline__ void twid3(const C* __restrict__ tw, int tw_log2, int log2L, uint32_t j, C& w1, C& w2,
+                                      C& w3) {
+  w1 = twid(tw, tw_log2, log2L, j);
+  if constexpr (sizeof(C) == 8) {   // float2
+    w2 = cmul(w1, w1);
+    w3 = cmul(w1, w2);
+  } else {
+    w2 = twid(tw, tw_log2, log2L, 2 * j);
+    w3 = twid(tw, tw_log2, log2L, 3 * j);
+  }
+}
+
 // Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.
 // Output in bit-reversed order.  Must be called by all threads of the block.
 template <typename C>
@@ -112,9 +129,11 @@ __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict
         p0[2 * q] = csub(d02, id13);
         p0[3 * q] = cadd(d02, id13);
       } else {
-        p0[q] = cmul(csub(s02, s13), twid(tw, tw_log2, lg, 2 * j));
-        p0[2 * q] = cmul(csub(d02, id13), twid(tw, tw_log2, lg, j));
-        p0[3 * q] = cmul(cadd(d02, id13), twid(tw, tw_log2, lg, 3 * j));
+        C w1, w2, w3;
+        twid3(tw, tw_log2, lg, j, w1, w2, w3);
+        p0[q] = cmul(csub(s02, s13), w2);
+        p0[2 * q] = cmul(csub(d02, id13), w1);
+        p0[3 * q] = cmul(cadd(d02, id13), w3);
       }
     }
     __syncthreads();
@@ -143,9 +162,11 @@ __device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __rest
       const C c0 = p0[0];
       C p1 = p0[q], p2 = p0[2 * q], p3 = p0[3 * q];
       if (j != 0) {  // conj twiddles u^2, u^1, u^3 with u = conj(W_N^j)
-        p1 = cmulc(p1, twid(tw, tw_log2, lg, 2 * j));
-        p2 = cmulc(p2, twid(tw, tw_log2, lg, j));
-        p3 = cmulc(p3, twid(tw, tw_log2, lg, 3 * j));
+        C w1, w2, w3;
+        twid3(tw, tw_log2, lg, j, w1, w2, w3);
+        p1 = cmulc(p1, w2);
+        p2 = cmulc(p2, w1);
+        p3 = cmulc(p3, w3);
       }
       const C a = cadd(c0, p1), bb = csub(c0, p1), sp = cadd(p2, p3), dp = cmuli(csub(p2, p3));
       p0[0] = cadd(a, sp);

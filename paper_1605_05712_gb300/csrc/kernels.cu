@@ -13,6 +13,7 @@
 // The residual reduction ends in the last block of the row pass, which also
 // decides convergence and sets the CUDA-graph WHILE condition.
 #include <math.h>
+#include <math_constants.h>
 
 #include <type_traits>
 
@@ -22,17 +23,20 @@
 
 // ------------------------------------------------------------------ row pass
 // grid: (row blocks, items); one block = rpc rows x n_c components of one item
-// index -> (line, k) for the R2C pre/post-processing without a division: first k in [0, Rh/2) for
-// every line (Rh/2 a power of two), then the middle frequency k = Rh/2 (its own partner) of each line
-__device__ __forceinline__ void kpair_index(int idx, int nlines, int lgRh, int& line, int& k) {
+// index -> (line, slot) for the R2C pre/post-processing without a division.  The pairs (k, Rh - k) are
+// walked in slot order: the spectrum is bit-reversed, so k < Rh/2 exactly when its slot bitrev(k) is
+// even; first the even slots 2i (i < Rh/2) of every line, then slot 1 (k = Rh/2, its own partner) of each
+// line.  Neighbouring threads then touch slots 2 apart, not the bit-reversed slots of neighbouring k
+// (which share one shared-memory bank: a 32-way conflict on 1024-point half rows).
+__device__ __forceinline__ void kslot_index(int idx, int nlines, int lgRh, int& line, int& slot) {
   const int lgq = lgRh > 0 ? lgRh - 1 : 0;
   const int n_lo = nlines << lgq;
   if (idx < n_lo) {
     line = idx >> lgq;
-    k = idx & ((1 << lgq) - 1);
+    slot = (idx & ((1 << lgq) - 1)) << 1;
   } else {
     line = idx - n_lo;
-    k = 1 << lgq;
+    slot = 1;
   }
 }
 
@@ -98,8 +102,9 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
   cp_async_wait_all();
   __syncthreads();
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
-    int line, k;
-    kpair_index(idx, nlines, lgRh, line, k);
+    int line, slot;
+    kslot_index(idx, nlines, lgRh, line, slot);
+    const int k = (int)bitrev((uint32_t)slot, lgRh);
     C* L = buf + (size_t)line * Rh;
     if (k == 0) {
       const Real X0 = L[0].x, XN = nyq[line].x;
@@ -109,7 +114,7 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
       // Z_k = A + i B conj(W^k), A = X_k + conj X_{Rh-k}, B = X_k - conj X_{Rh-k}; the partner reuses
       // both: W_R^{Rh-k} = -conj(W_R^k), so Z_{Rh-k} = conj(A) + i conj(B conj(W^k))
       const int kp = Rh - k;
-      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+      const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
       const C Xk = L[pk], Xkp = L[pkp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
       const C A = cadd(Xk, cconj(Xkp)), Pw = cmulc(csub(Xk, cconj(Xkp)), wk);
@@ -136,8 +141,9 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   __syncthreads();
   fft_dif(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
-    int line, k;
-    kpair_index(idx, nlines, lgRh, line, k);
+    int line, slot;
+    kslot_index(idx, nlines, lgRh, line, slot);
+    const int k = (int)bitrev((uint32_t)slot, lgRh);
     C* L = buf + (size_t)line * Rh;
     if (k == 0) {
       const C Z0 = L[0];
@@ -147,7 +153,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
       // the partner reuses A and W^k B: X_{Rh-k} = 1/2 (conj(A) - i conj(W^k B)), since
       // W_R^{Rh-k} = -conj(W_R^k) and Z_{Rh-k} - conj Z_k = -conj(B)
       const int kp = Rh - k;
-      const uint32_t pk = bitrev(k, lgRh), pkp = bitrev(kp, lgRh);
+      const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
       const C Zk = L[pk], Zkp = L[pkp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
       const C A1 = cadd(Zk, cconj(Zkp)), Q = cmul(csub(Zk, cconj(Zkp)), wk);
@@ -979,6 +985,39 @@ void launch_spectrum_to_f32(const void* T64, const void* TN64, void* T32, void* 
   spectrum_to_f32_kernel<<<dim3((unsigned)nb, n_items), 256, 0, st>>>(
       (const double2*)T64, (const double2*)TN64, (float2*)T32, (float2*)TN32, t_elems, tn_elems, t_stride, tn_stride,
       scal);
+}
+
+// the host decode of a finished solve, on the device: m = 1 (trivial) iterates to E at once (r = 0 after one
+// iteration when tol > 0); maxit = 0 reports no residual; non-finite or diverging residuals are LAT_DIVERGED
+__global__ void scalars_out_kernel(const ItemScal* scal, int n_items, int n_c, double tol, int maxit, int trivial,
+                                   double* sigma_bar, int* iters, double* resid, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  const ItemScal* sc = (const ItemScal*)((const char*)scal + (size_t)i * 256);
+  int it = sc->iter;
+  double r = sc->last_r;
+  if (trivial) {
+    it = (maxit > 0 && tol > 0) ? 1 : maxit;
+    r = maxit > 0 ? 0.0 : CUDART_NAN;
+  } else if (maxit == 0) {
+    r = CUDART_NAN;
+  }
+  if (iters) iters[i] = it;
+  if (resid) resid[i] = r;
+  if (sigma_bar)
+    for (int c = 0; c < n_c; ++c) sigma_bar[i * n_c + c] = sc->sigma_bar[c];
+  if (status) {
+    int s = LAT_OK;
+    if ((!isfinite(r) || sc->diverged) && maxit > 0) s = LAT_DIVERGED;
+    else if (!(r < tol)) s = LAT_NOT_CONVERGED;
+    status[i] = s;
+  }
+}
+
+void launch_scalars_out(const ItemScal* scal, int n_items, int n_c, double tol, int maxit, bool trivial,
+                        double* sigma_bar, int* iters, double* resid, int* status, cudaStream_t st) {
+  scalars_out_kernel<<<(n_items + 127) / 128, 128, 0, st>>>(scal, n_items, n_c, tol, maxit, trivial ? 1 : 0,
+                                                            sigma_bar, iters, resid, status);
 }
 
 void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st) {

@@ -167,6 +167,10 @@ void launch_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nbl
 template <typename Real>
 void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st);
 void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st);
+// the per-item results of a solve to device memory (asynchronous solves): mean stress, iterations, last
+// residual and the outcome (LAT_OK, LAT_NOT_CONVERGED, LAT_DIVERGED); trivial = the plan has m = 1
+void launch_scalars_out(const ItemScal* scal, int n_items, int n_c, double tol, int maxit, bool trivial,
+                        double* sigma_bar, int* iters, double* resid, int* status, cudaStream_t st);
 void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cudaStream_t st);
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,

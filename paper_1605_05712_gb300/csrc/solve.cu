@@ -760,10 +760,16 @@ int group_plain_iteration(const GroupRun& g, const RowArgs& body_row, cudaStream
 
 const int* group_active_flag(const GroupRun& g) { return &g.full.it.glob->active; }
 
-int group_finish(GroupRun& g, cudaStream_t st) {
+int group_finish(GroupRun& g, cudaStream_t st, const AsyncOut* aout) {
   if (g.kind != LAT_FP64) launch_eps_df(g.ea.items, g.n_items, g.n_c, g.P->m, 0, st);
   launch_eff(g.dv, g.ea, g.eff_blocks, g.n_items, st);
   CK(cudaGetLastError());
+  if (aout) {   // scalars to device memory, no host copy
+    launch_scalars_out((const ItemScal*)(g.ws + g.wl.scal), g.n_items, g.n_c, g.tol, g.maxit, g.P->nax == 0,
+                       aout->sigma_bar, aout->iters, aout->resid, aout->status, st);
+    CK(cudaGetLastError());
+    return LAT_OK;
+  }
   g.scal.resize((size_t)g.n_items * kScalBytes);
   CK(cudaMemcpyAsync(g.scal.data(), g.ws + g.wl.scal, g.scal.size(), cudaMemcpyDeviceToHost, st));
   if (g.want_hist) {
@@ -835,7 +841,7 @@ int plain_loops(std::vector<GroupRun>& groups, int phase, cudaStream_t st) {
 
 }  // namespace
 
-int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st) {
+int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st, const AsyncOut* aout) {
   bool any_loop = false;
   for (const GroupRun& g : groups) any_loop |= g.loop;
   if (any_loop && use_graph) {
@@ -869,10 +875,10 @@ int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st) {
     if (any_restart && (rc = plain_loops(groups, 1, st)) != LAT_OK) return rc;
   }
   for (GroupRun& g : groups) {
-    int rc = group_finish(g, st);
+    int rc = group_finish(g, st, aout);
     if (rc != LAT_OK) return rc;
   }
-  CK(cudaStreamSynchronize(st));
+  if (!aout) CK(cudaStreamSynchronize(st));
   return LAT_OK;
 }
 
@@ -997,6 +1003,40 @@ extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n
   const LatDev dv = make_dev(P, o.precision);
   return run_batch(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar,
                    iters, resid, (cudaStream_t)stream);
+}
+
+extern "C" int basic_scheme_solve_async(const lat_plan* P, const uint8_t* phase, int n_phases,
+                                        const double* stiffness, const double* C0, const double* E, int n_loads,
+                                        double tol, int maxit, const lat_solve_opts* opts, double* eps, double* sigma,
+                                        double* sigma_bar_d, int* iters_d, double* resid_d, int* status_d,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (!P || !phase || !stiffness || !C0 || !E || !eps || !workspace)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_async: NULL argument");
+  if (n_phases < 1 || n_phases > kMaxPhases)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_async: n_phases not in 1..256");
+  if (n_loads < 1) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_async: n_loads < 1");
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.resid_history || o.plain_launches)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_async: no residual history and no plain launches (both need "
+                                 "the host during the solve)");
+  if (int rc = check_common(P, tol, maxit, o)) return rc;
+  if (int rc = check_c0(C0)) return rc;
+  const Work wl = layout(P, n_loads, o.precision, kMaxPhases, 1, o.scheme);
+  if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  if (((uintptr_t)eps & eps_align_mask(P)) != 0) return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
+  if (int rc = lat_plan_device_check(P)) return rc;
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  std::vector<ItemHost> items;
+  load_case_items(P, phase, C0, E, n_loads, eps, sigma, items);
+  const LatDev dv = make_dev(P, o.precision);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<GroupRun> groups(1);
+  if (int rc = group_prepare(P, items, {stiffness}, {n_phases}, tol, maxit, o, (char*)workspace, wl, dv, groups[0], st))
+    return rc;
+  const AsyncOut aout = {sigma_bar_d, iters_d, resid_d, status_d};
+  return run_groups(groups, true, st, &aout);
 }
 
 extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item* bitems, int n_items, double tol,

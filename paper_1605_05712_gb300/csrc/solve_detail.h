@@ -117,9 +117,17 @@ struct GroupRun {
 int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
                   const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws,
                   const Work& wl, const LatDev& dv, GroupRun& g, cudaStream_t st);
+// device destinations of the scalar results of an asynchronous solve (any may be NULL)
+struct AsyncOut {
+  double* sigma_bar;
+  int* iters;
+  double* resid;
+  int* status;
+};
 // the loops of all groups (one CUDA graph with a WHILE node per group, or plain launches), then the
-// effective stress and the scalars of every group; returns after synchronizing `st`
-int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st);
+// effective stress and the scalars of every group; returns after synchronizing `st`, or, with aout (one
+// group, graph loop), as soon as everything is enqueued, the scalars going to device memory
+int run_groups(std::vector<GroupRun>& groups, bool use_graph, cudaStream_t st, const AsyncOut* aout = nullptr);
 // outputs of a finished group; returns its worst status
 int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, int* iters, double* resid);
 // runs a batch on workspace `ws` laid out by `wl`; dv carries the twiddle-table pointers;

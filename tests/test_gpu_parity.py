@@ -899,3 +899,37 @@ def test_prime_length_lattice(cuda, M, prec):
     # the direct p-point DFT sums p terms: its rounding grows like sqrt(p) u instead of log2(m) u, which
     # sets the absolute floor of the residual history once the laminate has converged (~1e-13 by step 5)
     check_pair(*out, d=d, hist_atol=1e-14 if prec == "fp64" else None)
+
+
+# ---------------------------------------------------------------- asynchronous entry point
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_async_solve_matches_synchronous(cuda, prec):
+    # basic_scheme_solve_async returns before the solve ends; after a synchronization its device results
+    # equal basic_scheme_solve's bitwise (same kernels, same graph); a non-converged and a diverged item
+    # report their outcome in the status array
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, basic_scheme_solve_async, lattice_plan
+    for M in ([[256, 16], [0, 256]], [[32, 4, 0], [0, 32, 4], [0, 0, 32]], [[45, 9], [0, 45]]):
+        if prec == "mixed" and M == [[45, 9], [0, 45]]:
+            continue
+        P = lattice_plan(M)
+        d = len(M)
+        ph = torch.from_numpy(inclusions(3, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+        E = np.eye(P.n_c)[:2]
+        ref = basic_scheme_solve(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec)
+        a = basic_scheme_solve_async(P, ph, LAM2, (5.5, 5.5), E, tol=1e-7, maxit=500, precision=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(a["eps"], ref["eps"])
+        assert np.array_equal(a["iters"].cpu().numpy(), ref["iters"])
+        assert np.array_equal(a["sigma_bar"].cpu().numpy(), ref["sigma_bar"])
+        assert np.array_equal(a["resid"].cpu().numpy(), ref["resid"])
+        assert np.all(a["status"].cpu().numpy() == 0)
+    P = lattice_plan([[64, 8], [0, 32]])
+    ph = torch.from_numpy(inclusions(3, 2, 3, 0.3)(P.points(), P.m)).to(cuda)
+    a = basic_scheme_solve_async(P, ph, LAM2, (5.5, 5.5), np.eye(3)[:1], tol=1e-12, maxit=3, precision=prec)
+    stiff = [LAM2[0], LAM2[1].copy()]
+    stiff[1][0, 0] = np.nan
+    b = basic_scheme_solve_async(P, ph, stiff, (5.5, 5.5), np.eye(3)[:1], tol=1e-8, maxit=50, precision=prec)
+    torch.cuda.synchronize()
+    assert int(a["status"][0]) == 1 and int(a["iters"][0]) == 3
+    assert int(b["status"][0]) == 2
