@@ -74,7 +74,7 @@ __device__ __forceinline__ RowTile<Real> make_row_tile(const LatDev& dv, const R
   t.nrows = dv.nrows;
   t.hm32 = (uint32_t)(dv.m / 2);
   t.buf = (C*)smem;
-  t.nyq = t.buf + (size_t)t.nlines * t.Rh;
+  t.nyq = t.buf + tile_span((int64_t)t.nlines * t.Rh, sizeof(C));
   t.T = (C*)a.T + item_i * a.t_stride;
   t.TN = (C*)a.TN + item_i * a.tn_stride;
   t.tw = (const C*)dv.tw;
@@ -93,7 +93,7 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
   for (int idx = tid; idx < nlines * Rh; idx += nthr) {
     const int line = idx >> lgRh, pos = idx & (Rh - 1);
     const int c = line >> lgrpc, row = line & (rpc - 1);
-    cp_async_elem(buf + idx, t.T + ((uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos));
+    cp_async_elem(buf + tpos<C>(idx), t.T + ((uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos));
   }
   for (int idx = tid; idx < nlines; idx += nthr) {
     const int c = idx >> lgrpc, row = idx & (rpc - 1);
@@ -105,21 +105,23 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
     const int k = (int)bitrev((uint32_t)slot, lgRh);
-    C* L = buf + (size_t)line * Rh;
+    const int lb = line * Rh;
     if (k == 0) {
-      const Real X0 = L[0].x, XN = nyq[line].x;
-      L[0].x = X0 + XN;
-      L[0].y = X0 - XN;
+      C& L0 = buf[tpos<C>(lb)];
+      const Real X0 = L0.x, XN = nyq[line].x;
+      L0.x = X0 + XN;
+      L0.y = X0 - XN;
     } else {
       // Z_k = A + i B conj(W^k), A = X_k + conj X_{Rh-k}, B = X_k - conj X_{Rh-k}; the partner reuses
       // both: W_R^{Rh-k} = -conj(W_R^k), so Z_{Rh-k} = conj(A) + i conj(B conj(W^k))
       const int kp = Rh - k;
       const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
-      const C Xk = L[pk], Xkp = L[pkp];
+      const int ik = tpos<C>(lb + (int)pk), ikp = tpos<C>(lb + (int)pkp);
+      const C Xk = buf[ik], Xkp = buf[ikp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
       const C A = cadd(Xk, cconj(Xkp)), Pw = cmulc(csub(Xk, cconj(Xkp)), wk);
-      L[pk] = cadd(A, cmuli(Pw));
-      if (kp != k) L[pkp] = cadd(cconj(A), cmuli(cconj(Pw)));
+      buf[ik] = cadd(A, cmuli(Pw));
+      if (kp != k) buf[ikp] = cadd(cconj(A), cmuli(cconj(Pw)));
     }
   }
   __syncthreads();
@@ -144,21 +146,22 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
     const int k = (int)bitrev((uint32_t)slot, lgRh);
-    C* L = buf + (size_t)line * Rh;
+    const int lb = line * Rh;
     if (k == 0) {
-      const C Z0 = L[0];
-      L[0] = cpair<C>(Z0.x + Z0.y, Real(0));
+      const C Z0 = buf[tpos<C>(lb)];
+      buf[tpos<C>(lb)] = cpair<C>(Z0.x + Z0.y, Real(0));
       nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
     } else {
       // the partner reuses A and W^k B: X_{Rh-k} = 1/2 (conj(A) - i conj(W^k B)), since
       // W_R^{Rh-k} = -conj(W_R^k) and Z_{Rh-k} - conj Z_k = -conj(B)
       const int kp = Rh - k;
       const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
-      const C Zk = L[pk], Zkp = L[pkp];
+      const int ik = tpos<C>(lb + (int)pk), ikp = tpos<C>(lb + (int)pkp);
+      const C Zk = buf[ik], Zkp = buf[ikp];
       const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
       const C A1 = cadd(Zk, cconj(Zkp)), Q = cmul(csub(Zk, cconj(Zkp)), wk);
-      L[pk] = cscale(csub(A1, cmuli(Q)), Real(0.5));
-      if (kp != k) L[pkp] = cscale(csub(cconj(A1), cmuli(cconj(Q))), Real(0.5));
+      buf[ik] = cscale(csub(A1, cmuli(Q)), Real(0.5));
+      if (kp != k) buf[ikp] = cscale(csub(cconj(A1), cmuli(cconj(Q))), Real(0.5));
     }
   }
   __syncthreads();
@@ -173,7 +176,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
-        val[c] = (k == Rh) ? nyq[line] : buf[(size_t)line * Rh + bitrev(k, lgRh)];
+        val[c] = (k == Rh) ? nyq[line] : buf[tpos<C>(line * Rh + (int)bitrev(k, lgRh))];
       }
       int kk[LAT_MAX_AX] = {0};
       kk[dv.nax - 1] = k;
@@ -182,7 +185,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
       for (int c = 0; c < n_c; ++c) {
         const int line = c * rpc + row;
         if (k == Rh) nyq[line] = val[c];
-        else buf[(size_t)line * Rh + bitrev(k, lgRh)] = val[c];
+        else buf[tpos<C>(line * Rh + (int)bitrev(k, lgRh))] = val[c];
       }
     }
     __syncthreads();
@@ -190,7 +193,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   for (int idx = tid; idx < nlines * Rh; idx += nthr) {
     const int line = idx >> lgRh, pos = idx & (Rh - 1);
     const int c = line >> lgrpc, row = line & (rpc - 1);
-    t.T[(uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos] = buf[idx];
+    t.T[(uint32_t)c * t.hm32 + (uint32_t)(t.r0 + row) * (uint32_t)Rh + (uint32_t)pos] = buf[tpos<C>(idx)];
   }
   for (int idx = tid; idx < nlines; idx += nthr) {
     const int c = idx >> lgrpc, row = idx & (rpc - 1);
@@ -242,12 +245,12 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
       const double* pe = eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 2u * n);
       if (eps_df) {
         const float4 v = *(const float4*)pe;
-        if constexpr (is_df<Real>) buf[idx] = cpair<C>(dfloat(v.x, v.y), dfloat(v.z, v.w));
-        else if constexpr (is_f32<Real>) buf[idx] = cpair<C>(v.x + v.y, v.z + v.w);
-        else buf[idx] = cmake<C>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        if constexpr (is_df<Real>) buf[tpos<C>(idx)] = cpair<C>(dfloat(v.x, v.y), dfloat(v.z, v.w));
+        else if constexpr (is_f32<Real>) buf[tpos<C>(idx)] = cpair<C>(v.x + v.y, v.z + v.w);
+        else buf[tpos<C>(idx)] = cmake<C>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
       } else {
         const double2 v = *(const double2*)pe;
-        buf[idx] = cmake<C>(v.x, v.y);
+        buf[tpos<C>(idx)] = cmake<C>(v.x, v.y);
       }
     }
     __syncthreads();
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     Real e0[NC], e1[NC];
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
-      const C z = buf[((size_t)c * rpc + row) * Rh + n];
+      const C z = buf[tpos<C>((c * rpc + row) * Rh + n)];
       e0[c] = z.x;
       e1[c] = z.y;
     }
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
         Real t0 = Real(0), t1 = Real(0);
 #pragma unroll
         for (int q = 0; q < n_c; ++q) {
-          const C z = buf[((size_t)q * rpc + row) * Rh + n];
+          const C z = buf[tpos<C>((q * rpc + row) * Rh + n)];
           t0 += ldg_r(W0 + c * n_c + q) * z.x;
           t1 += ldg_r(W1 + c * n_c + q) * z.y;
         }
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
         t0 += ldg_r(D0 + c * n_c + q) * e0[q];
         t1 += ldg_r(D1 + c * n_c + q) * e1[q];
       }
-      buf[((size_t)c * rpc + row) * Rh + n] = cpair<C>(t0, t1);
+      buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
     }
   }
   row_tile_forward<Real, NC>(tile, dv, a, item);
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
     if (from_spectrum) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
-        const C z = buf[((size_t)c * rpc + row) * Rh + n];
+        const C z = buf[tpos<C>((c * rpc + row) * Rh + n)];
         v0[c] = z.x;
         v1[c] = z.y;
       }
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
         t0 += ldg_r(C0p + c * n_c + k) * v0[k];
         t1 += ldg_r(C1p + c * n_c + k) * v1[k];
       }
-      buf[((size_t)c * rpc + row) * Rh + n] = cpair<C>(t0, t1);
+      buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
     }
   }
   if (stage != CG_A) row_tile_forward<Real, NC>(tile, dv, a, item);
@@ -696,8 +699,8 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
     const int col = idx & (w - 1);
     const int g = (idx >> lgw) & (G - 1);
     const int f = idx >> (lgw + lgG);
-    if (col < wv) cp_async_elem(s + idx, src + ((uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col));
-    else s[idx] = cmake<C>(0.0, 0.0);
+    if (col < wv) cp_async_elem(s + tpos<C>(idx), src + ((uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col));
+    else s[tpos<C>(idx)] = cmake<C>(0.0, 0.0);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -727,7 +730,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       const int64_t n1 = (g >> lg_after_n1) & (len_n1 - 1);
       const C W = split_tw(n1 * col_krow(col));
 #pragma unroll
-      for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmul(s[(size_t)f * G * w + idx], W);
+      for (int f = 0; f < n_f; ++f) s[tpos<C>(f * G * w + idx)] = cmul(s[tpos<C>(f * G * w + idx)], W);
     }
     __syncthreads();
   }
@@ -764,10 +767,10 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       kk[dv.nax - 1] = (int)col_krow(col);
       C val[NC];
 #pragma unroll
-      for (int f = 0; f < n_f; ++f) val[f] = s[(size_t)f * G * w + idx];
+      for (int f = 0; f < n_f; ++f) val[f] = s[tpos<C>(f * G * w + idx)];
       if constexpr (NC >= 3) green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
 #pragma unroll
-      for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = val[f];
+      for (int f = 0; f < n_f; ++f) s[tpos<C>(f * G * w + idx)] = val[f];
     }
     __syncthreads();
   }
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
         const int64_t n1 = (g >> lg_after_n1) & (len_n1 - 1);
         const C W = split_tw(n1 * col_krow(col));
 #pragma unroll
-        for (int f = 0; f < n_f; ++f) s[(size_t)f * G * w + idx] = cmulc(s[(size_t)f * G * w + idx], W);
+        for (int f = 0; f < n_f; ++f) s[tpos<C>(f * G * w + idx)] = cmulc(s[tpos<C>(f * G * w + idx)], W);
       }
       __syncthreads();
     }
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
     if (col >= wv) continue;
     const int g = (idx >> lgw) & (G - 1);
     const int f = idx >> (lgw + lgG);
-    C val = s[idx];
+    C val = s[tpos<C>(idx)];
     if (do_scale) val = cscale(val, sc);
     dst[(uint32_t)f * plane32 + base32 + (uint32_t)g * ic32 + (uint32_t)col] = val;
   }
@@ -818,7 +821,7 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
   for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
     const int line = idx / R, pos = idx - line * R;
     const int f = line / rpc, row = line - f * rpc;
-    buf[idx] = src[f * m + (r0 + row) * R + pos];
+    buf[tpos<C>(idx)] = src[f * m + (r0 + row) * R + pos];
   }
   __syncthreads();
   if (inverse) fft_dit_inv(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2);
@@ -827,7 +830,7 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
   for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
     const int line = idx / R, pos = idx - line * R;
     const int f = line / rpc, row = line - f * rpc;
-    C v = buf[idx];
+    C v = buf[tpos<C>(idx)];
     if (scale != 1.0) v = cscale(v, sc);
     dst[f * m + (r0 + row) * R + pos] = v;
   }

@@ -3,6 +3,12 @@
 #include "df64.cuh"
 #include "internal.h"
 
+// Shared-memory tiles of the power-of-two kernels are padded by one complex value after every 128 bytes
+// (16 binary32 complex values, 8 binary64 or double-float ones): values a multiple of 128 bytes apart --
+// the strided butterflies of the short FFT stages, the same slot of neighbouring lines -- then fall into
+// different banks.  tile_span(n, cs) is the number of complex slots a tile of n values occupies.
+__host__ __device__ inline int64_t tile_span(int64_t n, size_t cs) { return n + n / (cs == 8 ? 16 : 8) + 1; }
+
 // Row pass flags
 #define ROW_LOAD_EPS 1   // take eps^(n) from the strain buffer (first iteration / warm start)
 #define ROW_UPDATE 2     // inverse-transform T into eps^(n+1), residual, write eps

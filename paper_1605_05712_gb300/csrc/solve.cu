@@ -103,10 +103,12 @@ int tune_bucket(int n_items) {
 
 size_t row_smem_bytes(const lat_plan* P, int n_f, size_t cs, bool nyq, int rpc) {
   const int row_len = nyq ? P->Rh : P->Rlen;
-  return ((size_t)n_f * rpc * row_len + (nyq ? (size_t)n_f * rpc : 0)) * cs + 32 * sizeof(double);
+  // the padded tile of the rows, the Nyquist values of each line, 32 doubles for block reductions
+  return ((size_t)tile_span((int64_t)n_f * rpc * row_len, cs) + (nyq ? (size_t)n_f * rpc : 0)) * cs +
+         32 * sizeof(double);
 }
 size_t col_smem_bytes(const lat_plan* P, int n_f, size_t cs, int k, int64_t w) {
-  return (size_t)n_f * P->grp[k].G * w * cs;
+  return (size_t)tile_span((int64_t)n_f * P->grp[k].G * w, cs) * cs;
 }
 
 int geometry_set_rpc(const lat_plan* P, int n_f, size_t cs, bool nyq, int rpc, Geometry& g) {
