@@ -746,29 +746,37 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
   if (NC >= 3 && a.mode == COL_GAMMA) {
     const ItemDev* item = a.items + item_i;
     const GreenK<Real> gk = green_consts<Real>(item, a.mat);
-    for (int idx = tid; idx < G * w; idx += nthr) {
-      const int col = idx & (w - 1), g = idx >> lgw;
-      int kk[LAT_MAX_AX] = {0};
-      // group axes (bit-reversed after the DIF)
-      int rem = g;
-      for (int x = a.a1 - 1; x >= a.a0; --x) {
-        const int pos = rem & (dv.ax_len[x] - 1);
-        rem >>= dv.ax_log2[x];
-        kk[x] = (int)bitrev(pos, dv.ax_log2[x]);
-      }
-      // axes between the group and the row (transformed by the mid passes, bit-reversed)
+    // the frequency's coordinates v = sum_x k_x cv[x] split into the column's share (the axes between the
+    // group and the row, transformed by the mid passes, and the row; a thread keeps its column, since the
+    // block size is a multiple of w) and the group's share, which varies with g
+    uint32_t vc32[3] = {0u, 0u, 0u};
+    int64_t vc64[3] = {0, 0, 0};
+    {
+      const int col = tid & (w - 1);
       const int64_t ii = i0 + col;
       int64_t mid = nyqt ? ii : (ii >> lg_slots);
       for (int x = dv.nax - 2; x >= a.a1; --x) {
         const int pos = (int)(mid & (dv.ax_len[x] - 1));
         mid >>= dv.ax_log2[x];
-        kk[x] = (int)bitrev(pos, dv.ax_log2[x]);
+        v_add<D>(dv, x, (int)bitrev(pos, dv.ax_log2[x]), vc32, vc64);
       }
-      kk[dv.nax - 1] = (int)col_krow(col);
+      v_add<D>(dv, dv.nax - 1, (int)col_krow(col), vc32, vc64);
+    }
+    for (int idx = tid; idx < G * w; idx += nthr) {
+      const int g = idx >> lgw;
+      uint32_t v32[3] = {vc32[0], vc32[1], vc32[2]};
+      int64_t v64[3] = {vc64[0], vc64[1], vc64[2]};
+      // group axes (bit-reversed after the DIF)
+      int rem = g;
+      for (int x = a.a1 - 1; x >= a.a0; --x) {
+        const int pos = rem & (dv.ax_len[x] - 1);
+        rem >>= dv.ax_log2[x];
+        v_add<D>(dv, x, (int)bitrev(pos, dv.ax_log2[x]), v32, v64);
+      }
       C val[NC];
 #pragma unroll
       for (int f = 0; f < n_f; ++f) val[f] = s[tpos<C>(f * G * w + idx)];
-      if constexpr (NC >= 3) green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
+      if constexpr (NC >= 3) green_from_v<Real, NC>(dv, a.mat, item, gk, v32, v64, val);
 #pragma unroll
       for (int f = 0; f < n_f; ++f) s[tpos<C>(f * G * w + idx)] = val[f];
     }

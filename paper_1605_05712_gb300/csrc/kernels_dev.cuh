@@ -216,22 +216,21 @@ __device__ __forceinline__ void cell_map(const LatDev& dv, Real* h) {
 }
 
 // frequency from the per-axis spectral indices: kk[x] for the logical axes (row last)
+// the Green step at the frequency whose fractional coordinates are v / e_d: v32 are the per-component
+// sums of kk[x] cv[x] in wrapping 32-bit arithmetic (used when dv.h32), v64 the same sums in int64
 template <typename Real, int NC>
-__device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
-                                         const GreenK<Real>& gk, const int* kk,
-                                         typename cplx_of<Real>::type* val) {
+__device__ __forceinline__ void green_from_v(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
+                                             const GreenK<Real>& gk, const uint32_t* v32, const int64_t* v64,
+                                             typename cplx_of<Real>::type* val) {
   constexpr int d = (NC == 6) ? 3 : 2;
   Real h[3] = {0, 0, 0}, h2[3] = {0, 0, 0};
   bool zero = true, boundary = false;
   if (dv.h32) {
-    uint32_t v[3] = {0u, 0u, 0u}, vn[3];
-    for (int x = 0; x < dv.nax; ++x)
-#pragma unroll
-      for (int r = 0; r < d; ++r) v[r] += (uint32_t)kk[x] * (uint32_t)dv.ax_cv[x][r];  // exact mod 2^32
+    uint32_t v[3], vn[3];
     const uint32_t mask = (uint32_t)dv.ed_mask;
 #pragma unroll
     for (int r = 0; r < d; ++r) {
-      v[r] &= mask;
+      v[r] = v32[r] & mask;   // exact mod 2^32, hence mod e_d
       zero = zero && (v[r] == 0u);
       boundary = boundary || (2u * v[r] == (uint32_t)dv.ed);  // v' = -e_d/2: -v has the same representative
       vn[r] = (0u - v[r]) & mask;
@@ -249,12 +248,9 @@ __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, co
     }
   } else {
     int64_t v[3] = {0, 0, 0}, vn[3] = {0, 0, 0};
-    for (int x = 0; x < dv.nax; ++x)
-#pragma unroll
-      for (int r = 0; r < d; ++r) v[r] += (int64_t)kk[x] * dv.ax_cv[x][r];
 #pragma unroll
     for (int r = 0; r < d; ++r) {
-      v[r] = mod_ed(dv, v[r]);
+      v[r] = mod_ed(dv, v64[r]);
       zero = zero && (v[r] == 0);
       boundary = boundary || (2 * v[r] == dv.ed);
       vn[r] = mod_ed(dv, dv.ed - v[r]);
@@ -277,6 +273,28 @@ __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, co
     if (boundary) cell_map<Real, d>(dv, h2);
   }
   green_point_h<Real, NC>(dv, mt, item, gk, zero, boundary, h, h2, val);
+}
+
+// adds the contribution k cv[x] of spectral index k on logical axis x to the sums of green_from_v
+template <int D>
+__device__ __forceinline__ void v_add(const LatDev& dv, int x, int k, uint32_t* v32, int64_t* v64) {
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    v32[r] += (uint32_t)k * (uint32_t)dv.ax_cv[x][r];
+    v64[r] += (int64_t)k * dv.ax_cv[x][r];
+  }
+}
+
+// frequency from the per-axis spectral indices: kk[x] for the logical axes (row last)
+template <typename Real, int NC>
+__device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, const ItemDev* item,
+                                         const GreenK<Real>& gk, const int* kk,
+                                         typename cplx_of<Real>::type* val) {
+  constexpr int d = (NC == 6) ? 3 : 2;
+  uint32_t v32[3] = {0u, 0u, 0u};
+  int64_t v64[3] = {0, 0, 0};
+  for (int x = 0; x < dv.nax; ++x) v_add<d>(dv, x, kk[x], v32, v64);
+  green_from_v<Real, NC>(dv, mt, item, gk, v32, v64, val);
 }
 
 // ------------------------------------------------------------------ double-float accumulation
