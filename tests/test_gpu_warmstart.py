@@ -237,6 +237,14 @@ def test_trained_warm_start_against_cold_start(cuda):
             its[name] += int(np.sum(r["iters"]))
             # the plain scheme is the reference: every start converges to the cold start's effective stress
             assert np.abs(r["sigma_bar"] - cold["sigma_bar"]).max() < 1e-5 * np.abs(cold["sigma_bar"]).max()
-    print("held-out prediction error^2 (cold start = 1):", np.round(errs, 3), "iterations:", its)
+    # the network against the same method without it: the raw prediction against the cold start, the filtered
+    # prediction against the filtered cold start.  The filter's own gain is the filtered cold start against
+    # the cold start.  (Measured: the prediction is 3-15x closer to the solution than E, yet needs about as
+    # many iterations as the filtered cold start: its remaining error lies on the slow interface modes.)
+    gain_raw = its["cold"] - its["warm"]
+    gain_filtered = its["cold_filtered"] - its["warm_filtered"]
+    print("held-out prediction error^2 (cold start = 1):", np.round(errs, 3), "iterations:", its,
+          "network gain without filter: %d, with filter: %d, filter's own gain: %d"
+          % (gain_raw, gain_filtered, its["cold"] - its["cold_filtered"]))
     assert max(errs) < 0.5
-    assert its["warm_filtered"] < its["cold"]
+    assert its["cold_filtered"] < its["cold"]           # the filter's gain, measured without the network
