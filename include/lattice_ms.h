@@ -289,6 +289,27 @@ int basic_scheme_solve_async(const lat_plan* plan, const uint8_t* phase, int n_p
                              void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * basic_scheme_solve_field -- Algorithm 1 (Sec. 3.2) with a per-point stiffness field C(y) instead of
+ * phases (Sec. 3.1: the Lippmann-Schwinger equation holds for any field C(x); the polarization is
+ * tau_y = C_y : eps_y - C0 : eps_y):
+ *   voigt   device, 21 x m binary64, 16-byte aligned: plane p holds entry p of the row-major upper
+ *           triangle of each point's 6x6 Voigt matrix ((0,0), (0,1), ..., (0,5), (1,1), ..., (5,5);
+ *           Voigt order 11, 22, 33, 23, 13, 12 on engineering strain) in plan order; d = 2 reads the
+ *           plane-strain block (11, 22, 12).  Read-only; shared by all load cases.
+ *   workspace  device, >= lattice_field_workspace_bytes(plan, n_loads, precision) (it also holds the
+ *           binary32 / pair copies of the field the LAT_MIXED and LAT_DF64 kernels read)
+ * Other arguments and outputs as for basic_scheme_solve.  Algorithm 1 only (opts->scheme must be
+ * LAT_SCHEME_BASIC: LAT_ERR_ARG otherwise).  Per iteration the kernels read the field (168 bytes per
+ * point in binary64, 84 in binary32) where the phase form reads one byte.
+ */
+size_t lattice_field_workspace_bytes(const lat_plan* plan, int n_loads, int precision);
+int basic_scheme_solve_field(const lat_plan* plan, const double* voigt, const double* C0,
+                             const double* E, int n_loads, double tol, int maxit,
+                             const lat_solve_opts* opts, double* eps, double* sigma,
+                             double* sigma_bar, int* iters, double* resid,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Batches of independent microstructures on one lattice (shared plan): each
  * item has its own phase field, material, reference medium, macroscopic
  * strain and outputs, and stops on its own residual.  All items run in the

@@ -9,10 +9,11 @@ hand-written CUDA for sm_103a behind the C ABI of ``include/lattice_ms.h``.
 """
 from .api import (LAT_BOUNDARY_AVERAGE, LAT_BOUNDARY_ZERO, LAT_DIVERGED, LAT_FP64, LAT_MIXED,
                   LAT_NOT_CONVERGED, LAT_OK, LatticeError, LatticePlan, basic_scheme_solve,
-                  basic_scheme_solve_async, basic_scheme_solve_batch, basic_scheme_solve_multi, lattice_fft, lattice_pass_times,
+                  basic_scheme_solve_async, basic_scheme_solve_batch, basic_scheme_solve_field, voigt_field, basic_scheme_solve_multi, lattice_fft, lattice_pass_times,
                   lattice_plan, lib, multi_workspace_bytes, gather, gather_map)
 
-__all__ = ["lattice_plan", "lattice_pass_times", "basic_scheme_solve_async", "basic_scheme_solve_batch", "basic_scheme_solve_multi",
+__all__ = ["lattice_plan", "lattice_pass_times", "basic_scheme_solve_async", "basic_scheme_solve_batch",
+           "basic_scheme_solve_field", "voigt_field", "basic_scheme_solve_multi",
            "multi_workspace_bytes", "gather", "gather_map", "LatticePlan", "lattice_fft", "basic_scheme_solve", "lib", "LatticeError",
            "LAT_OK", "LAT_NOT_CONVERGED", "LAT_DIVERGED", "LAT_FP64", "LAT_MIXED",
            "LAT_BOUNDARY_AVERAGE", "LAT_BOUNDARY_ZERO"]

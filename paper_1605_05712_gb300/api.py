@@ -280,6 +280,71 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     return out
 
 
+VOIGT_TRIU = [(i, j) for i in range(6) for j in range(i, 6)]   # plane order of a stiffness field
+
+
+def voigt_field(voigts):
+    """(m, 6, 6) per-point Voigt matrices -> the (21, m) plane layout of basic_scheme_solve_field."""
+    v = np.asarray(voigts, dtype=np.float64)
+    return np.ascontiguousarray(np.stack([v[:, i, j] for i, j in VOIGT_TRIU]))
+
+
+def basic_scheme_solve_field(plan, field, C0, E, tol=1e-8, maxit=1000, precision="fp64", boundary="average",
+                             eps0=None, want_sigma=False, history=False, workspace=None, eps_out=None, stream=None,
+                             mixed_increment=True, mixed_restart=True, plain_launches=False):
+    """Algorithm 1 with a per-point stiffness field (basic_scheme_solve_field).
+
+    field  float64 CUDA tensor (21, m): plane p = upper-triangle entry p of each point's 6x6 Voigt matrix
+           in plan order (voigt_field builds it from (m, 6, 6) matrices)
+    Other arguments and the returned dict as for basic_scheme_solve.
+    """
+    import torch
+    if field.dtype != torch.float64 or not field.is_cuda or tuple(field.shape) != (21, plan.m):
+        raise TypeError("field must be a float64 CUDA tensor of shape (21, m)")
+    field = field.contiguous()
+    C0a, C0p = _f64(np.asarray(C0, dtype=np.float64).reshape(2))
+    E = np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c)
+    n_loads = E.shape[0]
+    Ea, Ep = _f64(E)
+    prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+    bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
+    dev = field.device
+    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
+                                                          device=dev)
+    if eps0 is not None:
+        eps.copy_(eps0)
+    sigma = torch.empty_like(eps) if want_sigma else None
+    L = lib()
+    L.lattice_field_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    L.lattice_field_workspace_bytes.restype = ctypes.c_size_t
+    wsb = int(L.lattice_field_workspace_bytes(plan.handle, n_loads, prec))
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sbar = np.zeros((n_loads, plan.n_c))
+    iters = np.zeros(n_loads, dtype=np.int32)
+    resid = np.zeros(n_loads)
+    hist = np.zeros((n_loads, max(maxit, 1))) if history else None
+    opts = _Opts(prec, bnd, 1 if eps0 is not None else 0,
+                 hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
+                 1 if mixed_increment else 0, 0 if mixed_restart else -1, 1 if plain_launches else 0,
+                 LAT_SCHEME_BASIC)
+    f = L.basic_scheme_solve_field
+    vp = ctypes.c_void_p
+    f.argtypes = [vp, vp] + [ctypes.POINTER(ctypes.c_double)] * 2 + \
+        [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts), vp, vp,
+         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp,
+         ctypes.c_size_t, vp]
+    f.restype = ctypes.c_int
+    rc = f(plan.handle, vp(field.data_ptr()), C0p, Ep, n_loads, float(tol), int(maxit), ctypes.byref(opts),
+           vp(eps.data_ptr()), vp(sigma.data_ptr()) if sigma is not None else None,
+           sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), vp(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check(rc)
+    out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
+    if history:
+        out["history"] = [hist[i, :min(int(iters[i]), maxit, HIST_CAP)] for i in range(n_loads)]
+    return out
+
+
 def basic_scheme_solve_async(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, precision="fp64",
                              boundary="average", eps0=None, want_sigma=False, workspace=None, eps_out=None,
                              stream=None, mixed_increment=True, mixed_restart=True, scheme="basic"):

@@ -208,7 +208,9 @@ template <typename Real, int NC>
 constexpr int row_min_blocks() {
   return is_f32<Real> ? 4 : (NC == 6 ? 2 : (is_df<Real> ? 3 : 4));
 }
-template <typename Real, int NC>
+// FIELD: the material is a per-point stiffness field (basic_scheme_solve_field, Algorithm 1 only) instead
+// of phase ids and per-phase tables
+template <typename Real, int NC, bool FIELD>
 __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_kernel(LatDev dv, RowArgs a) {
   typedef typename cplx_of<Real>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -277,8 +279,9 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
       e0[c] = z.x;
       e1[c] = z.y;
     }
-    const uchar2 ph = *(const uchar2*)(phase + g);  // g even
-    if (update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
+    uchar2 ph = make_uchar2(0, 0);
+    if constexpr (!FIELD) ph = *(const uchar2*)(phase + g);  // g even
+    if (!FIELD && update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
       // the transform returned u = (C + C0) eps (or its increment): eps = (C_p + C0)^{-1} u per point
       const Real* Wt;
       if constexpr (is_f32<Real>) Wt = (const Real*)item->Wtab_f;
@@ -390,21 +393,35 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
         }
       }
     }
-    const Real* Dt;
-    if constexpr (is_f32<Real>) Dt = (const Real*)Dtab_f;
-    else if constexpr (is_df<Real>) Dt = (const Real*)item->Dtab_df;
-    else Dt = (const Real*)Dtab;
-    const Real* D0 = Dt + (int)ph.x * n_c * n_c;
-    const Real* D1 = Dt + (int)ph.y * n_c * n_c;
+    if constexpr (FIELD) {
+      const Real* F;
+      if constexpr (is_f32<Real>) F = (const Real*)item->fld_f;
+      else if constexpr (is_df<Real>) F = (const Real*)item->fld_df;
+      else F = (const Real*)item->fld;
+      const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+      const Real two_mu0 = gk.mu0 + gk.mu0;
+      Real t0[NC], t1[NC];
+      field_polarize<Real, NC>(F, m, g, gk.lam0, two_mu0, e0, t0);
+      field_polarize<Real, NC>(F, m, g + 1, gk.lam0, two_mu0, e1, t1);
 #pragma unroll
-    for (int c = 0; c < n_c; ++c) {
-      Real t0 = 0, t1 = 0;
+      for (int c = 0; c < n_c; ++c) buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0[c], t1[c]);
+    } else {
+      const Real* Dt;
+      if constexpr (is_f32<Real>) Dt = (const Real*)Dtab_f;
+      else if constexpr (is_df<Real>) Dt = (const Real*)item->Dtab_df;
+      else Dt = (const Real*)Dtab;
+      const Real* D0 = Dt + (int)ph.x * n_c * n_c;
+      const Real* D1 = Dt + (int)ph.y * n_c * n_c;
 #pragma unroll
-      for (int q = 0; q < n_c; ++q) {
-        t0 += ldg_r(D0 + c * n_c + q) * e0[q];
-        t1 += ldg_r(D1 + c * n_c + q) * e1[q];
+      for (int c = 0; c < n_c; ++c) {
+        Real t0 = 0, t1 = 0;
+#pragma unroll
+        for (int q = 0; q < n_c; ++q) {
+          t0 += ldg_r(D0 + c * n_c + q) * e0[q];
+          t1 += ldg_r(D1 + c * n_c + q) * e1[q];
+        }
+        buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
       }
-      buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
     }
   }
   row_tile_forward<Real, NC>(tile, dv, a, item);
@@ -863,9 +880,19 @@ __global__ void __launch_bounds__(256) eff_kernel(LatDev dv, EffArgs a) {
   const int64_t m = dv.m, stride = (int64_t)gridDim.x * blockDim.x;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const double* Cp = it->Ctab + (int)it->phase[i] * n_c * n_c;
     double e[6];
     for (int c = 0; c < n_c; ++c) e[c] = it->eps[c * m + i];
+    if (it->fld) {   // per-point stiffness field: sigma = C_y : eps (tau + C0 : eps with C0 = 0)
+      double sg[6];
+      if (n_c == 6) field_polarize<double, 6>(it->fld, m, i, 0.0, 0.0, e, sg);
+      else field_polarize<double, 3>(it->fld, m, i, 0.0, 0.0, e, sg);
+      for (int c = 0; c < n_c; ++c) {
+        if (it->sigma) it->sigma[c * m + i] = sg[c];
+        acc[c] += sg[c];
+      }
+      continue;
+    }
+    const double* Cp = it->Ctab + (int)it->phase[i] * n_c * n_c;
     for (int c = 0; c < n_c; ++c) {
       double sgm = 0;
       for (int q = 0; q < n_c; ++q) sgm += __ldg(Cp + c * n_c + q) * e[q];
@@ -900,8 +927,13 @@ template <typename Real>
 void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
                      cudaStream_t st) {
   const dim3 grid(nblocks, n_items);
-  if (dv.n_c == 6) row_pass_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
-  else row_pass_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
+  if (a.flags & ROW_FIELD) {
+    if (dv.n_c == 6) row_pass_kernel<Real, 6, true><<<grid, nthreads, smem, st>>>(dv, a);
+    else row_pass_kernel<Real, 3, true><<<grid, nthreads, smem, st>>>(dv, a);
+  } else {
+    if (dv.n_c == 6) row_pass_kernel<Real, 6, false><<<grid, nthreads, smem, st>>>(dv, a);
+    else row_pass_kernel<Real, 3, false><<<grid, nthreads, smem, st>>>(dv, a);
+  }
 }
 template <typename Real>
 void launch_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, int nthreads,
@@ -1031,6 +1063,23 @@ void launch_scalars_out(const ItemScal* scal, int n_items, int n_c, double tol, 
                                                             sigma_bar, iters, resid, status);
 }
 
+__global__ void field_copies_kernel(const double* fld, float* fld_f, dfloat* fld_df, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fld[i];
+    if (fld_f) fld_f[i] = (float)v;
+    if (fld_df) {
+      const float2 p = df_of(v);
+      fld_df[i] = dfloat(p.x, p.y);
+    }
+  }
+}
+
+void launch_field_copies(const double* fld, float* fld_f, dfloat* fld_df, int64_t n, cudaStream_t st) {
+  int64_t nb = (n + 255) / 256;
+  if (nb > 4864) nb = 4864;
+  field_copies_kernel<<<(unsigned)nb, 256, 0, st>>>(fld, fld_f, fld_df, n);
+}
+
 void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStream_t st) {
   int64_t nb = (m + 255) / 256;
   if (nb > 2048) nb = 2048;
@@ -1065,17 +1114,23 @@ int lat_kernel_attrs(size_t max_smem) {
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
     optin = (int)max_smem;
-  cudaError_t e = set_smem(row_pass_kernel<double, 3>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6>, optin);
+  cudaError_t e = set_smem(row_pass_kernel<double, 3, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 3, true>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, true>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, true>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, true>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, true>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, true>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 1>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 6>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 6>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, false>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 6>, optin);
   if (e == cudaSuccess) e = set_smem(row_complex_kernel<double>, optin);

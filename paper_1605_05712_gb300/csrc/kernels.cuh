@@ -20,6 +20,7 @@ __host__ __device__ inline int64_t tile_span(int64_t n, size_t cs) { return n + 
 #define ROW_TAU_DELTA 64   // with ROW_UPDATE: the polarization is taken of the increment eps^(n+1) - eps^(n)
 #define ROW_EPS_DF 128     // binary64 kernels: the strain buffer holds double-float pairs (mixed solve);
                            // the binary32 kernels always read and write it so
+#define ROW_FIELD 256      // the material is a per-point stiffness field (ItemDev::fld*), not phase tables
 
 // ItemScal::done
 #define ITEM_ACTIVE 0
@@ -55,6 +56,11 @@ struct ItemDev {
   float lam0f, mu0f;
   double twoC0E[6];
   double norm0;          // sqrt(m) ||E||_F (1 if E = 0)
+  // per-point stiffness field (basic_scheme_solve_field; NULL otherwise): 21 planes of m values, plane p the
+  // upper-triangle entry p of each point's 6x6 Voigt matrix; binary64 (the caller's), binary32 and pair copies
+  const double* fld;
+  const float* fld_f;
+  const dfloat* fld_df;
 };
 
 // Device scalars of one item (the first bytes of its 256-byte slot)
@@ -178,6 +184,8 @@ void launch_fill(const ItemDev* items, int n_items, int n_c, int64_t m, cudaStre
 void launch_scalars_out(const ItemScal* scal, int n_items, int n_c, double tol, int maxit, bool trivial,
                         double* sigma_bar, int* iters, double* resid, int* status, cudaStream_t st);
 void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cudaStream_t st);
+// binary32 and pair copies of a 21 x m binary64 stiffness field (either destination may be NULL)
+void launch_field_copies(const double* fld, float* fld_f, dfloat* fld_df, int64_t n, cudaStream_t st);
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
                         int rpc, int nthreads, size_t smem, cudaStream_t st);

@@ -297,6 +297,42 @@ __device__ __forceinline__ void green_at(const LatDev& dv, const MatArgs& mt, co
   green_from_v<Real, NC>(dv, mt, item, gk, v32, v64, val);
 }
 
+// ------------------------------------------------------------------ per-point stiffness field
+// Voigt index (11, 22, 33, 23, 13, 12 -> 0..5) of tensor component c; 2-D (plane strain) takes 11, 22, 12
+template <int NC>
+__device__ __forceinline__ constexpr int fld_vidx(int c) { return NC == 6 ? c : (c == 2 ? 5 : c); }
+// position of entry (i, j), i <= j, of a symmetric 6x6 matrix in its row-major upper triangle
+__device__ __forceinline__ constexpr int fld_tri(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
+
+// tau = C_y : e - C0 : e at one point, from the 21 upper-triangle Voigt entries of C_y (6x6 on engineering
+// strain; plane p of fld at stride fs holds entry p); e and tau tensor components.  C_y : e is the
+// symmetric product on the engineering strain, each stored entry read once.
+template <typename Real, int NC>
+__device__ __forceinline__ void field_polarize(const Real* fld, int64_t fs, int64_t g, Real lam0, Real two_mu0,
+                                               const Real* e, Real* tau) {
+  constexpr int D = (NC == 6) ? 3 : 2;
+  Real ev[NC], s[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    ev[c] = c < D ? e[c] : e[c] + e[c];
+    s[c] = Real(0);
+  }
+#pragma unroll
+  for (int a = 0; a < NC; ++a)
+#pragma unroll
+    for (int b = a; b < NC; ++b) {
+      const int va = fld_vidx<NC>(a), vb = fld_vidx<NC>(b);
+      const Real cab = ldg_r(fld + fld_tri(va < vb ? va : vb, va < vb ? vb : va) * fs + g);
+      s[a] += cab * ev[b];
+      if (b != a) s[b] += cab * ev[a];
+    }
+  Real tr = e[0];
+#pragma unroll
+  for (int c = 1; c < D; ++c) tr += e[c];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) tau[c] = c < D ? s[c] - (lam0 * tr + two_mu0 * e[c]) : s[c] - two_mu0 * e[c];
+}
+
 // ------------------------------------------------------------------ double-float accumulation
 // Sum of squares carried as an unevaluated pair of binary32 values (hi + lo), with Knuth's TwoSum
 // for the addition and the FMA-based exact product (Dekker) for the square: about 2^-48 relative,

@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
     Real e[NC];
 #pragma unroll
     for (int c = 0; c < n_c; ++c) e[c] = cur[((size_t)c * rpc + row) * R + n].x;
-    const int ph = phase[g];
-    if (update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
+    const bool field = (a.flags & ROW_FIELD) != 0;
+    const int ph = field ? 0 : phase[g];
+    if (!field && update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
       // the transform returned u = (C + C0) eps: eps = (C_p + C0)^{-1} u
       const Real* W = (is_df<Real> ? (const Real*)item->Wtab_df : (const Real*)item->Wtab) + ph * n_c * n_c;
       Real u[NC];
@@ -120,6 +121,15 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
         }
         eps_st1<Real>(pe, e[c]);
       }
+    }
+    if (field) {   // per-point stiffness field: tau = C_y : eps - C0 : eps
+      const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+      Real t[NC];
+      field_polarize<Real, NC>(is_df<Real> ? (const Real*)item->fld_df : (const Real*)item->fld, m, g, gk.lam0,
+                               gk.mu0 + gk.mu0, e, t);
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) cur[((size_t)c * rpc + row) * R + n] = cpair<C>(t[c], Real(0));
+      continue;
     }
     const Real* Dt = (is_df<Real> ? (const Real*)item->Dtab_df : (const Real*)item->Dtab) + ph * n_c * n_c;
 #pragma unroll

@@ -194,7 +194,8 @@ int geometry(const lat_plan* P, int n_f, size_t cs, int row_slots, bool nyq, Geo
   return LAT_OK;
 }
 
-Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables, int scheme) {
+Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables, int scheme,
+            bool field) {
   const int n_c = P->d * (P->d + 1) / 2;
   const size_t cs = (precision == LAT_MIXED) ? 8 : 16;
   Work w;
@@ -240,6 +241,11 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   w.cgv = off;
   w.cg_stride = (int64_t)n_c * P->m;
   if (scheme == LAT_SCHEME_CG) off = align256(off + (size_t)n_items * 4 * w.cg_stride * sizeof(double));
+  // the stiffness field in the kernels' types: binary32 (mixed) and pairs (df64, and the mixed restart)
+  w.fld_f = off;
+  if (field && precision == LAT_MIXED) off = align256(off + (size_t)21 * P->m * sizeof(float));
+  w.fld_df = off;
+  if (field && precision != LAT_FP64) off = align256(off + (size_t)21 * P->m * sizeof(dfloat));
   w.total = off;
   return w;
 }
@@ -530,6 +536,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
     v.eps = it.eps;
     v.sigma = it.sigma;
     v.phase = it.phase;
+    if (it.field) {
+      v.fld = it.field;
+      v.fld_f = o.precision == LAT_MIXED ? (const float*)(ws + wl.fld_f) : nullptr;
+      v.fld_df = o.precision != LAT_FP64 ? (const dfloat*)(ws + wl.fld_df) : nullptr;
+    }
     v.Ctab = (const double*)(ws + wl.tables + (size_t)(2 * it.table + 1) * wl.table_bytes);
     v.Dtab = (const double*)(ws + wl.tables + (size_t)(2 * it.table) * wl.table_bytes);
     v.Dtab_f = (const float*)(ws + wl.tables_f + (size_t)it.table * wl.table_bytes / 2);
@@ -610,6 +621,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   GlobScal* glob = (GlobScal*)(ws + wl.scal + (size_t)n_items * kScalBytes);
   CK(cudaMemcpyAsync(glob, &g.glob0, sizeof(GlobScal), cudaMemcpyHostToDevice, st));
   const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
+  const bool field = n_items > 0 && items[0].field != nullptr;   // a field solve: all items share the field
+  const int fieldflag = field ? ROW_FIELD : 0;
+  if (field && o.precision != LAT_FP64)
+    launch_field_copies(items[0].field, o.precision == LAT_MIXED ? (float*)(ws + wl.fld_f) : nullptr,
+                        (dfloat*)(ws + wl.fld_df), (int64_t)21 * m, st);
   if (!o.warm_start) launch_fill(ditems, n_items, n_c, m, st);
   // mixed precision: the strain is held as double-float pairs in its own buffer during the solve
   if (g.kind != LAT_FP64) launch_eps_df(ditems, n_items, n_c, m, 1, st);
@@ -695,13 +711,13 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       // (the Eyre-Milton cold start u = (C + C0) E varies in space, so its first step is taken in full)
       const bool incr_first = incr && !o.warm_start && o.scheme == LAT_SCHEME_BASIC;
       RowArgs first = ra;
-      first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0);
+      first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
       first.mat.increment = incr_first ? 1 : 0;
       ColArgs c0 = ca;
       c0.scal = nullptr;
       c0.mat.increment = incr_first ? 1 : 0;
       g.full = ra;
-      g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) |
+      g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) | fieldflag |
                      (incr_first ? ROW_INCR_FIRST : 0);
       g.full.mat.increment = incr ? 1 : 0;
       g.cl = ca;
@@ -731,10 +747,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
         r64.TN = ws + wl.TN64;
         r64.it.pause_tol = 0.0;
         g.r_pro = r64;
-        g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
+        g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
         g.r_pro.mat.increment = 0;
         g.r_upd = r64;
-        g.r_upd.flags = ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0);
+        g.r_upd.flags =
+            ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
         g.r_upd.mat.increment = 1;
         g.c64 = ca;
         g.c64.T = r64.T;
@@ -945,6 +962,7 @@ void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, 
   items.resize(n_loads);
   for (int lc = 0; lc < n_loads; ++lc) {
     ItemHost& it = items[lc];
+    it.field = nullptr;
     it.phase = phase;
     it.table = 0;
     it.C0[0] = C0[0];
@@ -1039,6 +1057,48 @@ extern "C" int basic_scheme_solve_async(const lat_plan* P, const uint8_t* phase,
     return rc;
   const AsyncOut aout = {sigma_bar_d, iters_d, resid_d, status_d};
   return run_groups(groups, true, st, &aout);
+}
+
+extern "C" size_t lattice_field_workspace_bytes(const lat_plan* P, int n_loads, int precision) {
+  if (!P || n_loads <= 0 || check_geometry(P, precision) != LAT_OK) return 0;
+  return layout(P, n_loads, precision, 1, 1, LAT_SCHEME_BASIC, true).total;
+}
+
+extern "C" int basic_scheme_solve_field(const lat_plan* P, const double* voigt, const double* C0, const double* E,
+                                        int n_loads, double tol, int maxit, const lat_solve_opts* opts, double* eps,
+                                        double* sigma, double* sigma_bar, int* iters, double* resid,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (!P || !voigt || !C0 || !E || !eps || !workspace)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_field: NULL argument");
+  if (n_loads < 1) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_field: n_loads < 1");
+  if (((uintptr_t)voigt & 15) != 0) return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_field: field not 16-byte aligned");
+  lat_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.scheme != LAT_SCHEME_BASIC)
+    return lat_fail(LAT_ERR_ARG, "basic_scheme_solve_field: Algorithm 1 only (the accelerated schemes need "
+                                 "per-phase tables)");
+  if (int rc = check_common(P, tol, maxit, o)) return rc;
+  if (int rc = check_c0(C0)) return rc;
+  const Work wl = layout(P, n_loads, o.precision, 1, 1, LAT_SCHEME_BASIC, true);
+  if (workspace_bytes < wl.total) return lat_fail(LAT_ERR_SIZE, "workspace too small");
+  if (((uintptr_t)eps & eps_align_mask(P)) != 0) return lat_fail(LAT_ERR_ARG, "eps misaligned (16 bytes; 8 on general plans)");
+  if (int rc = lat_plan_device_check(P)) return rc;
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  std::vector<ItemHost> items;
+  load_case_items(P, nullptr, C0, E, n_loads, eps, sigma, items);
+  for (ItemHost& it : items) it.field = voigt;
+  // the per-phase tables are not read; one placeholder phase (the reference medium) keeps their layout
+  double ref[36];
+  memset(ref, 0, sizeof(ref));
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) ref[a * 6 + b] = C0[0];
+    ref[a * 6 + a] = C0[0] + 2 * C0[1];
+    ref[(a + 3) * 6 + (a + 3)] = C0[1];
+  }
+  const LatDev dv = make_dev(P, o.precision);
+  return run_batch(P, items, {ref}, {1}, tol, maxit, o, (char*)workspace, wl, dv, o.plain_launches == 0, sigma_bar,
+                   iters, resid, (cudaStream_t)stream);
 }
 
 extern "C" int basic_scheme_solve_batch(const lat_plan* P, const lat_batch_item* bitems, int n_items, double tol,
@@ -1158,7 +1218,7 @@ extern "C" int basic_scheme_solve_multi(const lat_multi_item* items, int n_items
     for (size_t t = 0; t < g.inst.size(); ++t) {
       const lat_multi_item& b = items[g.inst[t]];
       for (int lc = 0; lc < b.n_loads; ++lc) {
-        ItemHost it;
+        ItemHost it{};
         it.phase = b.phase;
         it.table = (int)t;
         it.C0[0] = b.C0[0];

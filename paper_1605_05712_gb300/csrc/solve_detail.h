@@ -31,6 +31,7 @@ struct Work {
   size_t T, TN, items, tables, tables_f, tables_df, tables_w, tables_wf, tables_wdf, partials, scal, hist, total;
   size_t T64, TN64;   // mixed precision: binary64 spectrum of the restart (0 bytes otherwise)
   size_t cgv;         // conjugate gradients: r, p, q, w per item (0 bytes otherwise)
+  size_t fld_f, fld_df;  // stiffness-field solves: binary32 and pair copies of the field (0 bytes otherwise)
   int64_t cg_stride;  // doubles per vector and item (n_c m)
   size_t t_per_lc, tn_per_lc, table_bytes;
   int64_t pstride;  // doubles of reduction partials per item
@@ -38,6 +39,7 @@ struct Work {
 
 // host description of one item of a batch
 struct ItemHost {
+  const double* field;  // device 21 x m Voigt stiffness field (basic_scheme_solve_field), else NULL
   const uint8_t* phase;
   int table;        // index of its material table
   double C0[2];
@@ -65,8 +67,9 @@ template <typename Real>
 void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs c, int k, int mode,
                        int n_items, cudaStream_t st);
 // scheme = LAT_SCHEME_CG adds the four vectors of the conjugate-gradient iteration
+// field: a per-point stiffness field (basic_scheme_solve_field) adds its binary32 / pair copies
 Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table, int n_tables,
-            int scheme = LAT_SCHEME_BASIC);
+            int scheme = LAT_SCHEME_BASIC, bool field = false);
 void voigt_to_tc(const double* V, int d, double* out);
 template <typename Real>
 void enqueue_columns(const LatDev& dv, const lat_plan* P, const Geometry& g, ColArgs base, int n_items,

@@ -933,3 +933,69 @@ def test_async_solve_matches_synchronous(cuda, prec):
     torch.cuda.synchronize()
     assert int(a["status"][0]) == 1 and int(a["iters"][0]) == 3
     assert int(b["status"][0]) == 2
+
+
+# ---------------------------------------------------------------- per-point stiffness field
+def _random_spd_voigts(rng, m):
+    """m seeded anisotropic stiffness matrices: isotropic (lam, mu) per point plus a random positive
+    semidefinite perturbation (Voigt form, engineering shear)."""
+    out = np.empty((m, 6, 6))
+    for i in range(m):
+        lam, mu = 10 ** rng.uniform(-0.5, 1.0), 10 ** rng.uniform(-0.5, 1.0)
+        A = rng.standard_normal((6, 6))
+        out[i] = synth.iso_voigt(lam, mu) + 0.05 * mu * (A @ A.T) / 6
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("M", [[[16, 4], [0, 8]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[6, 1], [0, 10]],
+                               [[3, 0, 0], [0, 3, 0], [0, 0, 15]]])
+def test_field_solve_matches_oracle(cuda, M, prec):
+    # a genuinely per-point anisotropic field: the oracle gives every point its own phase
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve_field, lattice_plan, voigt_field
+    P, L = lattice_plan(M), Lattice(M)
+    d = L.d
+    perm = to_oracle_order(P.points(), L)
+    rng = np.random.default_rng(21)
+    V_or = _random_spd_voigts(rng, L.m)                     # oracle order
+    V_plan = V_or[perm]
+    field = torch.from_numpy(voigt_field(V_plan)).to(cuda)
+    E = np.eye(P.n_c)[:2] + 0.1
+    C0 = (5.0, 4.0)
+    g = basic_scheme_solve_field(P, field, C0, E, tol=0.0, maxit=5, precision=prec, want_sigma=True, history=True)
+    S = np.array([el.voigt6_to_tensor(v, d) for v in V_or])
+    for lc in range(2):
+        o = basic_scheme(L, np.arange(L.m), S, C0, el.comps_to_sym(E[lc], d), tol=0.0, maxit=5)
+        assert relerr(comps_to_tensor(g["eps"][lc].cpu().numpy(), d), o["eps"][perm]) < RTOL
+        assert relerr(comps_to_tensor(g["sigma"][lc].cpu().numpy(), d), o["sigma"][perm]) < RTOL
+        assert relerr(el.comps_to_sym(g["sigma_bar"][lc], d), o["sigma_bar"]) < RTOL
+        ho = np.array(o["history"])
+        atol = 1e-13 if prec == "df64" else 1e-15
+        assert np.all(np.abs(np.array(g["history"][lc]) - ho) <= 1e-9 * ho + atol)
+
+
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+def test_field_solve_equals_phase_solve(cuda, M):
+    # the field built from a phase field and its table solves the same problem as the phase form: binary64
+    # and df64 to rounding, mixed within its stated bounds against binary64
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, basic_scheme_solve_field, lattice_plan, voigt_field
+    P = lattice_plan(M)
+    d = len(M)
+    ph = inclusions(3, d, 4, 0.3)(P.points(), P.m)
+    V = np.array(LAM2)[ph]
+    field = torch.from_numpy(voigt_field(V)).to(cuda)
+    phd = torch.from_numpy(ph).to(cuda)
+    E = np.eye(P.n_c)[:2]
+    ref = basic_scheme_solve(P, phd, LAM2, (5.5, 5.5), E, tol=1e-8, maxit=2000)
+    for prec in ("fp64", "df64"):
+        f = basic_scheme_solve_field(P, field, (5.5, 5.5), E, tol=1e-8, maxit=2000, precision=prec)
+        assert f["status"] == 0 and np.array_equal(f["iters"], ref["iters"])
+        assert float((f["eps"] - ref["eps"]).abs().max() / ref["eps"].abs().max()) < 1e-11
+        assert np.abs(f["sigma_bar"] - ref["sigma_bar"]).max() < 1e-11 * np.abs(ref["sigma_bar"]).max()
+    r6 = basic_scheme_solve(P, phd, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=2000)
+    fm = basic_scheme_solve_field(P, field, (5.5, 5.5), E, tol=1e-6, maxit=2000, precision="mixed")
+    assert fm["status"] == 0
+    assert float((fm["eps"] - r6["eps"]).abs().max() / r6["eps"].abs().max()) <= MIXED_STRAIN_RTOL
+    assert np.abs(fm["sigma_bar"] - r6["sigma_bar"]).max() <= MIXED_CEFF_RTOL * np.abs(r6["sigma_bar"]).max()
