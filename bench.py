@@ -499,7 +499,7 @@ def bench_warmstart(args):
     net = WarmStartNet(dev, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = train(net, args.ws_train_n, args.ws_samples, 2, 3e-4, seed0=5000)
+    losses = train(net, args.ws_train_n, args.ws_samples, args.ws_steps, args.ws_lr, seed0=5000)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     n = args.ws_eval_n
@@ -539,9 +539,9 @@ def bench_warmstart(args):
     for prec in tot:
         for k in names:
             tot[prec][k]["s"] = round(tot[prec][k]["s"], 3)
-    print(json.dumps({"workload": "warmstart (config 5): train %d samples x 2 Adam steps at %d^3, evaluate %d "
-                                  "held-out seeds at %d^3, 6 unit load cases batched, tol 1e-6"
-                                  % (args.ws_samples, args.ws_train_n, args.ws_eval, n),
+    print(json.dumps({"workload": "warmstart (config 5): train %d samples x %d Adam steps (lr %g) at %d^3, evaluate "
+                                  "%d held-out seeds at %d^3, 6 unit load cases batched, tol 1e-6"
+                                  % (args.ws_samples, args.ws_steps, args.ws_lr, args.ws_train_n, args.ws_eval, n),
                       "train_s": round(t_train, 1), "train_loss_first_last": [float(np.mean(losses[:100])),
                                                                                float(np.mean(losses[-100:]))],
                       "totals": tot, "max_sigma_bar_rel_diff_vs_fp64_cold": worst_sb, "per_seed": per_seed}))
@@ -848,7 +848,9 @@ def main():
                     help="iterate with plain kernel launches (same results) so that ncu lists every kernel")
     ap.add_argument("--workload", default="default", choices=["default", "hashin3d", "warmstart", "sweep", "gather",
                                                                "shear_sweep"])
-    ap.add_argument("--ws-samples", type=int, default=2000)
+    ap.add_argument("--ws-samples", type=int, default=10000)
+    ap.add_argument("--ws-steps", type=int, default=2, help="Adam steps per training sample")
+    ap.add_argument("--ws-lr", type=float, default=3e-4)
     ap.add_argument("--ws-train-n", type=int, default=64)
     ap.add_argument("--ws-eval-n", type=int, default=128)
     ap.add_argument("--ws-eval", type=int, default=4)

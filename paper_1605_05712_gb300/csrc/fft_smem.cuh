@@ -170,7 +170,9 @@ __device__ void r16_stage(C* s, int log2L, int lgnlo, int nhi, int lg, const C* 
 
 // Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.
 // Output in bit-reversed order.  Must be called by all threads of the block.
-template <typename C>
+// FUSE: run pairs of radix-4 stages in registers (r16_stage); binary32 kernels always, the 16-byte types
+// where the kernel's register budget holds 16 complex values (the six-component passes, 128 registers)
+template <typename C, bool FUSE = (sizeof(C) == 8)>
 __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
   if (log2L == 0) return;
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
@@ -190,9 +192,8 @@ __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict
     __syncthreads();
     lg -= 1;
   }
-  // binary32: pairs of radix-4 stages fused in registers while at least two remain (16 complex values per
-  // thread; the 16-byte types keep single stages within their register budgets)
-  if constexpr (sizeof(C) == 8)
+  // pairs of radix-4 stages fused in registers while at least two remain (16 complex values per thread)
+  if constexpr (FUSE)
     for (; lg >= 4; lg -= 4) r16_stage<C, false>(s, log2L, lgnlo, nhi, lg, tw, tw_log2);
   const int lgq_line = log2L - 2;  // radix-4 butterflies per line = L/4
   for (; lg >= 2; lg -= 2) {
@@ -227,7 +228,7 @@ __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict
 
 // Inverse DIT FFT (sign +1, unnormalized): the adjoint of fft_dif.
 // Input in bit-reversed order, output natural.  All threads must call.
-template <typename C>
+template <typename C, bool FUSE = (sizeof(C) == 8)>
 __device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
   if (log2L == 0) return;
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
@@ -235,7 +236,7 @@ __device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __rest
   // the DIF ran its radix-4 stages on block sizes 2^(log2L - (log2L&1)) ... 4; mirror them: a lone
   // smallest stage when their number is odd, then pairs fused in registers (adjoint order inside a pair)
   const int lgmax = log2L - (log2L & 1);
-  const int lone = sizeof(C) == 8 ? (((lgmax / 2) & 1) ? 2 : 0) : lgmax;
+  const int lone = FUSE ? (((lgmax / 2) & 1) ? 2 : 0) : lgmax;
   for (int lg = 2; lg <= lone; lg += 2) {
     const int lgq = lg - 2;
     const unsigned total = (unsigned)nhi << (lgnlo + lgq_line);
@@ -263,7 +264,7 @@ __device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __rest
     }
     __syncthreads();
   }
-  if constexpr (sizeof(C) == 8)
+  if constexpr (FUSE)
     for (int lg = lone + 4; lg <= lgmax; lg += 4) r16_stage<C, true>(s, log2L, lgnlo, nhi, lg, tw, tw_log2);
   if (log2L & 1) {   // adjoint of the leading radix-2 stage, applied last
     const int lgh = log2L - 1;

@@ -83,7 +83,15 @@ __device__ __forceinline__ RowTile<Real> make_row_tile(const LatDev& dv, const R
 
 // the block's rows of the half spectrum -> real rows: tile loads, inverse of the R2C post-processing
 // (X[0..Rh] -> Z = E + i O), inverse FFT
-template <typename Real>
+// fused radix-4 stage pairs: binary32 always; binary64 in the six-component passes, whose 128-register
+// budget holds the 16 values of a group (2.5-5 % faster at 2^21; the 2-D budgets of 64-85 registers do
+// not hold them, and the double-float pair kernels ran 12-23 % slower fused)
+template <typename Real, int NC>
+constexpr bool fuse16() {
+  return is_f32<Real> || (NC == 6 && !is_df<Real>);
+}
+
+template <typename Real, int NC>
 __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
   typedef typename cplx_of<Real>::type C;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -125,7 +133,7 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
     }
   }
   __syncthreads();
-  fft_dit_inv(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+  fft_dit_inv<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
 }
 
 // real rows (written by every thread before the call) -> forward FFT, R2C post-processing
@@ -141,7 +149,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   C* buf = t.buf;
   C* nyq = t.nyq;
   __syncthreads();
-  fft_dif(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+  fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     }
     __syncthreads();
   } else {
-    row_tile_inverse<Real>(tile);
+    row_tile_inverse<Real, NC>(tile);
   }
 
   // pointwise: update, residual, polarization
@@ -532,7 +540,7 @@ __global__ void __launch_bounds__(256, (cg_min_blocks<Real, NC>())) cg_row_kerne
   double* q = cg.q + voff;
   double* w = cg.w + voff;
   const bool from_spectrum = (stage == CG_FULL0 || stage == CG_A);
-  if (from_spectrum) row_tile_inverse<Real>(tile);
+  if (from_spectrum) row_tile_inverse<Real, NC>(tile);
   Real alpha = Real(0), beta = Real(0), lam0, two_mu0;
   if constexpr (is_df<Real>) {  // host- or last-block-made pairs: no binary64 conversions per thread
     if (stage == CG_B) {
@@ -756,7 +764,8 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
     for (int x = a.a1 - 1; x >= a.a0; --x) {
       int64_t before = 1;
       for (int y = a.a0; y < x; ++y) before *= dv.ax_len[y];
-      fft_dif(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw, dv.tw_log2);
+      fft_dif<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
+                                     dv.tw_log2);
       after *= dv.ax_len[x];
     }
   }
@@ -804,7 +813,8 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
     for (int x = a.a0; x < a.a1; ++x) {
       int64_t after = 1;
       for (int y = x + 1; y < a.a1; ++y) after *= dv.ax_len[y];
-      fft_dit_inv(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw, dv.tw_log2);
+      fft_dit_inv<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
+                                         dv.tw_log2);
       before *= dv.ax_len[x];
     }
     if (a.has_twiddle) {
