@@ -423,10 +423,23 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         Real t0 = 0, t1 = 0;
+        if constexpr (NC == 6) {   // rows of 6 entries: pairs of entries in one load (rows 16-byte aligned)
 #pragma unroll
-        for (int q = 0; q < n_c; ++q) {
-          t0 += ldg_r(D0 + c * n_c + q) * e0[q];
-          t1 += ldg_r(D1 + c * n_c + q) * e1[q];
+          for (int q = 0; q < n_c; q += 2) {
+            Real a0, b0, a1, b1;
+            ldg_r2(D0 + c * n_c + q, a0, b0);
+            ldg_r2(D1 + c * n_c + q, a1, b1);
+            t0 += a0 * e0[q];
+            t0 += b0 * e0[q + 1];
+            t1 += a1 * e1[q];
+            t1 += b1 * e1[q + 1];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < n_c; ++q) {
+            t0 += ldg_r(D0 + c * n_c + q) * e0[q];
+            t1 += ldg_r(D1 + c * n_c + q) * e1[q];
+          }
         }
         buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
       }

@@ -16,6 +16,22 @@ template <typename R> constexpr bool is_df = std::is_same<R, dfloat>::value;
 
 template <typename R> __device__ __forceinline__ R ldg_r(const R* p) { return __ldg(p); }
 template <> __device__ __forceinline__ dfloat ldg_r<dfloat>(const dfloat* p) { return ldg_df(p); }
+// two consecutive table entries in one read-only load (p aligned to twice the entry size)
+__device__ __forceinline__ void ldg_r2(const double* p, double& a, double& b) {
+  const double2 v = __ldg((const double2*)p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ldg_r2(const float* p, float& a, float& b) {
+  const float2 v = __ldg((const float2*)p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ldg_r2(const dfloat* p, dfloat& a, dfloat& b) {
+  const float4 v = __ldg((const float4*)p);
+  a = dfloat(v.x, v.y);
+  b = dfloat(v.z, v.w);
+}
 
 // ------------------------------------------------------------------ Green operator (Sec. 3.1)
 // sc Gamma0(h) : tau for isotropic C0 (closed form of grad (grad^H C0 grad)^{-1} grad^H), applied to the
