@@ -2,16 +2,19 @@
 //
 // The pattern FFT of Sec. 2.2 is an ordinary d_M-dimensional DFT over the
 // elementary divisors; every 1-D piece of it runs here on lines held in
-// shared memory.  Forward transforms are decimation-in-frequency (Sande-Tukey)
-// and leave the spectrum in bit-reversed order; inverse transforms are the
-// exact adjoint (decimation-in-time) and take bit-reversed input to natural
-// output.  Forward -> pointwise Green operator -> inverse therefore needs no
-// permutation pass: the pointwise step decodes each frequency with __brev.
+// shared memory.  Forward transforms leave the spectrum in bit-reversed order
+// and inverse transforms take bit-reversed input to natural output, so
+// forward -> pointwise Green operator -> inverse needs no permutation pass: the
+// pointwise step decodes each frequency with __brev.
 //
-// Radix-4 stages are two radix-2 DIF stages fused (so the order stays plain
-// bit reversal); an odd log2 length adds one radix-2 stage.  Butterflies are
-// in place, a thread keeps only the 4 values of the butterfly it is working
-// on, and stages are separated by __syncthreads().
+// Binary32 and double-float kernels: the forward transform is decimation in
+// frequency (Sande-Tukey), the inverse its exact adjoint (decimation in time);
+// radix-4 stages are two radix-2 stages fused (so the order stays plain bit
+// reversal), an odd log2 length adds one radix-2 stage.  Binary64 kernels run
+// decimation in time both ways with fused multiply-add butterflies (fft_fwd_fma,
+// fft_inv_fma below).  Butterflies are in place, a thread keeps only the
+// values of the butterflies it is working on, and stages are separated by
+// __syncthreads().
 //
 // Line addressing: a line l = l_hi * nlo + l_lo (nlo a power of two) has its element idx at
 //   l_hi * L * nlo + idx * nlo + l_lo,
@@ -22,6 +25,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "df64.cuh"
 
@@ -168,12 +173,214 @@ __device__ void r16_stage(C* s, int log2L, int lgnlo, int nhi, int lg, const C* 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- binary64: fused multiply-add butterflies
+// The binary64 passes are bound by the binary64 arithmetic pipe, so their cost is the number of binary64
+// instructions.  A twiddled radix-4 butterfly written as three complex products and sixteen additions takes
+// 28 of them.  Taking the real (or imaginary) part of each twiddle out of its product as a common factor
+// (Linzer and Feig's method, in the radix-4 arrangement Goedecker gave it) turns every product into the
+// multiplier of a fused multiply-add: 22 instructions.  With b' = (b.x - tau b.y, b.y + tau b.x):
+//   form A (Re w != 0): tau = Im w / Re w,   w b = Re w (b'.x, b'.y)
+//   form B (Im w != 0): tau = -Re w / Im w,  w b = (-Im w b'.y, Im w b'.x)
+// The butterfly's twiddles are w1 = W_N^j, w2 = w1^2, w3 = w1^3 with 0 <= j < N/4, so w1 and w3 are always
+// in form A (their angles stay off pi/2 and 3 pi/2 for power-of-two N); w2 takes whichever form has the
+// larger divisor.  Table entry t (N = 2^tw_log2, t < N/4), eight binary64 words:
+//   t1 = tau(w1), t3 = tau(w3), tau2 = tau(w2), s1 = Re w1, sx2, sy2 (the two scales of w2 b), r = Re w3 / Re w1,
+//   and a word whose bits are nonzero when w2 is in form B.
+// Then w1 a + w3 b = s1 (a' + r b'), and every sum of a value and a scaled product is one fused multiply-add.
+// Entry 0 holds the identity twiddles (tau = 0, scales and r = 1), which reproduce the plain additions
+// exactly, so no lane needs a branch of its own.
+struct FmaTw {
+  double t1, t3, tau2, s1, sx2, sy2, r;
+  bool swap;
+};
+__device__ __forceinline__ FmaTw fma_tw(const double* __restrict__ lf, int tw_log2, int lg, uint32_t j) {
+  const double2* p = (const double2*)lf + 4 * (size_t)(j << (tw_log2 - lg));
+  const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+  FmaTw w;
+  w.t1 = a.x;
+  w.t3 = a.y;
+  w.tau2 = b.x;
+  w.s1 = b.y;
+  w.sx2 = c.x;
+  w.sy2 = c.y;
+  w.r = d.x;
+  w.swap = __double_as_longlong(d.y) != 0;
+  return w;
+}
+
+// radix-4 decimation-in-time butterfly: a0..a3 at block positions j, j + N/4, j + N/2, j + 3N/4 of a block of
+// N = 2^lg, twiddles w2, w1, w3 on a1, a2, a3 (INV: their conjugates, the inverse transform)
+template <bool INV>
+__device__ __forceinline__ void r4_plain(double2& a0, double2& a1, double2& a2, double2& a3) {
+  const double2 A = cadd(a0, a1), B = csub(a0, a1), sp = cadd(a2, a3), dm = csub(a2, a3);
+  a0 = cadd(A, sp);
+  a2 = csub(A, sp);
+  // forward: B -/+ i dm; inverse: B +/- i dm
+  if (!INV) {
+    a1 = make_double2(B.x + dm.y, B.y - dm.x);
+    a3 = make_double2(B.x - dm.y, B.y + dm.x);
+  } else {
+    a1 = make_double2(B.x - dm.y, B.y + dm.x);
+    a3 = make_double2(B.x + dm.y, B.y - dm.x);
+  }
+}
+template <bool INV>
+__device__ __forceinline__ void r4_fma(double2& a0, double2& a1, double2& a2, double2& a3, const FmaTw& w) {
+  double Ax, Ay, Bx, By, X2, Y2, X3, Y3;
+  if (!INV) {
+    // w2 a1 = (sx2 P, sy2 Q)
+    const double bx = fma(-w.tau2, a1.y, a1.x), by = fma(w.tau2, a1.x, a1.y);
+    const double P = w.swap ? by : bx, Q = w.swap ? bx : by;
+    Ax = fma(w.sx2, P, a0.x);
+    Ay = fma(w.sy2, Q, a0.y);
+    Bx = fma(-w.sx2, P, a0.x);
+    By = fma(-w.sy2, Q, a0.y);
+    X2 = fma(-w.t1, a2.y, a2.x);
+    Y2 = fma(w.t1, a2.x, a2.y);
+    X3 = fma(-w.t3, a3.y, a3.x);
+    Y3 = fma(w.t3, a3.x, a3.y);
+  } else {
+    // conj(w2) a1 = conj(w2 conj(a1)) = (sx2 P, -sy2 Q)
+    const double bx = fma(w.tau2, a1.y, a1.x), by = fma(w.tau2, a1.x, -a1.y);
+    const double P = w.swap ? by : bx, Q = w.swap ? bx : by;
+    Ax = fma(w.sx2, P, a0.x);
+    Ay = fma(-w.sy2, Q, a0.y);
+    Bx = fma(-w.sx2, P, a0.x);
+    By = fma(w.sy2, Q, a0.y);
+    X2 = fma(w.t1, a2.y, a2.x);
+    Y2 = fma(-w.t1, a2.x, a2.y);
+    X3 = fma(w.t3, a3.y, a3.x);
+    Y3 = fma(-w.t3, a3.x, a3.y);
+  }
+  // w1 a2 +/- w3 a3 = s1 (SP or DM)
+  const double SPx = fma(w.r, X3, X2), SPy = fma(w.r, Y3, Y2);
+  const double DMx = fma(-w.r, X3, X2), DMy = fma(-w.r, Y3, Y2);
+  a0 = make_double2(fma(w.s1, SPx, Ax), fma(w.s1, SPy, Ay));
+  a2 = make_double2(fma(-w.s1, SPx, Ax), fma(-w.s1, SPy, Ay));
+  if (!INV) {   // B -/+ i s1 DM
+    a1 = make_double2(fma(w.s1, DMy, Bx), fma(-w.s1, DMx, By));
+    a3 = make_double2(fma(-w.s1, DMy, Bx), fma(w.s1, DMx, By));
+  } else {      // B +/- i s1 DM
+    a1 = make_double2(fma(-w.s1, DMy, Bx), fma(w.s1, DMx, By));
+    a3 = make_double2(fma(w.s1, DMy, Bx), fma(-w.s1, DMx, By));
+  }
+}
+// the butterfly of position j in a block of 2^lg: blocks of 4 have no twiddles; where every lane of a warp
+// has the same j (uniform), j = 0 takes the plain additions
+template <bool INV>
+__device__ __forceinline__ void r4_at(double2& a0, double2& a1, double2& a2, double2& a3, uint32_t j, int lg,
+                                      bool uniform, const double* __restrict__ lf, int tw_log2) {
+  if (lg == 2 || (uniform && j == 0)) r4_plain<INV>(a0, a1, a2, a3);
+  else r4_fma<INV>(a0, a1, a2, a3, fma_tw(lf, tw_log2, lg, j));
+}
+
+// Stage plan shared by both binary64 transforms: an odd log2 length first takes one twiddle-free radix-2
+// stage (span 1 of the bit-reversed-input algorithm), then radix-4 stages on blocks of 2^lg, lg = lg0 + 2,
+// lg0 + 4, ..., log2L, one shared-memory round trip each.
+//
+// The inverse (bit-reversed in, natural out) is the decimation-in-time algorithm as it stands.  The forward
+// transform (natural in, bit-reversed out) is the same algorithm with every memory position p relabelled
+// bitrev(p): a butterfly of block 2^lg at (block b, position j) moves to group G = bitrev(j) and offset
+// i = bitrev(b) of span H = 2^(log2L - lg), its four values at G 4H + v H + i with v = bitrev2(u), and its
+// twiddles stay those of j.  So both run twiddle-before-butterfly (decimation in time), the order the
+// fused multiply-adds need, and the forward output is the bit-reversed spectrum the decimation-in-frequency
+// kernels produce.
+static __device__ void fft_fwd_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2) {
+  if (log2L == 0) return;
+  const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
+  const int lg0 = log2L & 1;
+  if (lg0) {   // span L/2, no twiddles
+    const int lgh = log2L - 1;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgh);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned k = rest & ((1u << lgh) - 1u), l_hi = rest >> lgh;
+      const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + (k << lgnlo));
+      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + (int)((1u << lgh) << lgnlo));
+      const double2 a = s[i0], c = s[i1];
+      s[i0] = cadd(a, c);
+      s[i1] = csub(a, c);
+    }
+    __syncthreads();
+  }
+  int lg = lg0 + 2;
+  for (; lg <= log2L; lg += 2) {
+    // block 2^lg relabelled: groups G of 4H values, H = 2^(log2L - lg); value u at G 4H + bitrev2(u) H + i
+    const int lgH = log2L - lg, lgg = lg - 2;
+    const unsigned total = (unsigned)nhi << (lgnlo + log2L - 2);
+    const bool uni = lgH + lgnlo >= 5;
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned i = rest & ((1u << lgH) - 1u), G = (rest >> lgH) & ((1u << lgg) - 1u);
+      const unsigned l_hi = rest >> (log2L - 2);
+      const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + (((G << (lgH + 2)) | i) << lgnlo));
+      const int h = 1 << (lgH + lgnlo);
+      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + 2 * h), i2 = tpos<double2>(e0 + h),
+                i3 = tpos<double2>(e0 + 3 * h);
+      double2 a0 = s[i0], a1 = s[i1], a2 = s[i2], a3 = s[i3];
+      r4_at<false>(a0, a1, a2, a3, bitrev(G, lgg), lg, uni, lf, tw_log2);
+      s[i0] = a0;
+      s[i1] = a1;
+      s[i2] = a2;
+      s[i3] = a3;
+    }
+    __syncthreads();
+  }
+}
+
+static __device__ void fft_inv_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2) {
+  if (log2L == 0) return;
+  const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
+  const int lg0 = log2L & 1;
+  const bool uni = lgnlo >= 5;   // neighbouring lanes differ in the line, not in the block position
+  if (lg0) {   // span 1, no twiddles
+    const int lgh = log2L - 1;
+    const unsigned total = (unsigned)nhi << (lgnlo + lgh);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned k = rest & ((1u << lgh) - 1u), l_hi = rest >> lgh;
+      const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + ((2u * k) << lgnlo));
+      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + (1 << lgnlo));
+      const double2 a = s[i0], c = s[i1];
+      s[i0] = cadd(a, c);
+      s[i1] = csub(a, c);
+    }
+    __syncthreads();
+  }
+  int lg = lg0 + 2;
+  for (; lg <= log2L; lg += 2) {
+    const int lgq = lg - 2;
+    const unsigned total = (unsigned)nhi << (lgnlo + log2L - 2);
+    for (unsigned b = threadIdx.x; b < total; b += nthr) {
+      const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
+      const unsigned j = rest & ((1u << lgq) - 1u), blk = (rest >> lgq) & ((1u << (log2L - lg)) - 1u);
+      const unsigned l_hi = rest >> (log2L - 2);
+      const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + ((((blk << lg) | j)) << lgnlo));
+      const int q = 1 << (lgq + lgnlo);
+      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + q), i2 = tpos<double2>(e0 + 2 * q),
+                i3 = tpos<double2>(e0 + 3 * q);
+      double2 a0 = s[i0], a1 = s[i1], a2 = s[i2], a3 = s[i3];
+      r4_at<true>(a0, a1, a2, a3, j, lg, uni, lf, tw_log2);
+      s[i0] = a0;
+      s[i1] = a1;
+      s[i2] = a2;
+      s[i3] = a3;
+    }
+    __syncthreads();
+  }
+}
+
 // Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.
 // Output in bit-reversed order.  Must be called by all threads of the block.
-// FUSE: run pairs of radix-4 stages in registers (r16_stage); binary32 kernels always, the 16-byte types
-// where the kernel's register budget holds 16 complex values (the six-component passes, 128 registers)
+// FUSE: run pairs of radix-4 stages in registers (r16_stage), as the binary32 kernels do.
+// Binary64 (C = double2) runs fft_fwd_fma with the fused multiply-add table lf instead (FUSE unused).
 template <typename C, bool FUSE = (sizeof(C) == 8)>
-__device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
+__device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2,
+                        const double* __restrict__ lf) {
+  if constexpr (std::is_same<C, double2>::value) {
+    fft_fwd_fma(s, log2L, lgnlo, nhi, lf, tw_log2);
+    return;
+  }
   if (log2L == 0) return;
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
   int lg = log2L;  // log2 of current block size N
@@ -228,8 +435,14 @@ __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict
 
 // Inverse DIT FFT (sign +1, unnormalized): the adjoint of fft_dif.
 // Input in bit-reversed order, output natural.  All threads must call.
+// Binary64 runs fft_inv_fma (same result up to rounding).
 template <typename C, bool FUSE = (sizeof(C) == 8)>
-__device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2) {
+__device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2,
+                            const double* __restrict__ lf) {
+  if constexpr (std::is_same<C, double2>::value) {
+    fft_inv_fma(s, log2L, lgnlo, nhi, lf, tw_log2);
+    return;
+  }
   if (log2L == 0) return;
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
   const int lgq_line = log2L - 2;

@@ -57,6 +57,8 @@ struct lat_plan {
   float2* d_stwf;
   float4* d_twdf;     // double-float copies (re hi, re lo, im hi, im lo)
   float4* d_stwdf;
+  double* d_lf;       // fused multiply-add butterfly table of the binary64 kernels (power-of-two plans)
+  double* d_rc;       // fused multiply-add table of their real-row pre/post-processing
   int64_t stw_hi_n, stw_lo_n;
   int device;        // device holding the tables (-1: created without a CUDA device, host-only)
   // transformed pattern (lattice_plan_set_cell): has_cell and L^{-T}
@@ -94,6 +96,8 @@ struct LatDev {
   int tw_log2;
   const void* tw;             // twiddle table (double2 or float2, per precision)
   const void* stw;            // split twiddles [hi | lo]
+  const double* lf;           // binary64 butterfly table (fft_smem.cuh, FmaTw): 8 words per t < 2^tw_log2 / 4
+  const double* rc;           // binary64 real-transform table: (Re w / Im w, Im w, Im w / 2, 0), w = W_N^t, t <= N/4
   // general plan: mixed-radix axes (see lat_plan)
   int general;
   int ax_nrad[LAT_MAX_AX];

@@ -51,6 +51,8 @@ struct RowTile {
   C* T;
   C* TN;
   const C* tw;
+  const double* lf;
+  const double* rc;
   int Rh, lgRh, lgR, rpc, lgrpc, nlines, npl_total, tw_log2;
   int64_t r0, nrows;
   uint32_t hm32;
@@ -78,17 +80,19 @@ __device__ __forceinline__ RowTile<Real> make_row_tile(const LatDev& dv, const R
   t.T = (C*)a.T + item_i * a.t_stride;
   t.TN = (C*)a.TN + item_i * a.tn_stride;
   t.tw = (const C*)dv.tw;
+  t.lf = dv.lf;
+  t.rc = dv.rc;
   return t;
 }
 
 // the block's rows of the half spectrum -> real rows: tile loads, inverse of the R2C post-processing
 // (X[0..Rh] -> Z = E + i O), inverse FFT
-// fused radix-4 stage pairs: binary32 always; binary64 in the six-component passes, whose 128-register
-// budget holds the 16 values of a group (2.5-5 % faster at 2^21; the 2-D budgets of 64-85 registers do
-// not hold them, and the double-float pair kernels ran 12-23 % slower fused)
+// fused radix-4 stage pairs (16 complex values per thread): binary32 only.  The double-float pair kernels
+// ran 12-23 % slower fused; the binary64 fused multiply-add stages ran ~1 % slower fused at 2^21 (six
+// components), with three times the register spills
 template <typename Real, int NC>
 constexpr bool fuse16() {
-  return is_f32<Real> || (NC == 6 && !is_df<Real>);
+  return is_f32<Real>;
 }
 
 template <typename Real, int NC>
@@ -126,14 +130,24 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
       const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
       const int ik = tpos<C>(lb + (int)pk), ikp = tpos<C>(lb + (int)pkp);
       const C Xk = buf[ik], Xkp = buf[ikp];
-      const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
-      const C A = cadd(Xk, cconj(Xkp)), Pw = cmulc(csub(Xk, cconj(Xkp)), wk);
-      buf[ik] = cadd(A, cmuli(Pw));
-      if (kp != k) buf[ikp] = cadd(cconj(A), cmuli(cconj(Pw)));
+      if constexpr (std::is_same<C, double2>::value) {
+        // conj(W^k) B = s (c B.x + B.y, c B.y - B.x), W^k = W_R^k, s = Im W^k, c = Re W^k / Im W^k: the
+        // products fold into fused multiply-adds (10 operations for the pair instead of 12)
+        const double2 e = __ldg((const double2*)t.rc + 2 * (k << (t.tw_log2 - t.lgR)));
+        const double Ax = Xk.x + Xkp.x, Ay = Xk.y - Xkp.y, Bx = Xk.x - Xkp.x, By = Xk.y + Xkp.y;
+        const double P = fma(e.x, Bx, By), Q = fma(e.x, By, -Bx);
+        buf[ik] = make_double2(fma(-e.y, Q, Ax), fma(e.y, P, Ay));
+        if (kp != k) buf[ikp] = make_double2(fma(e.y, Q, Ax), fma(e.y, P, -Ay));
+      } else {
+        const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
+        const C A = cadd(Xk, cconj(Xkp)), Pw = cmulc(csub(Xk, cconj(Xkp)), wk);
+        buf[ik] = cadd(A, cmuli(Pw));
+        if (kp != k) buf[ikp] = cadd(cconj(A), cmuli(cconj(Pw)));
+      }
     }
   }
   __syncthreads();
-  fft_dit_inv<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+  fft_dit_inv<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf);
 }
 
 // real rows (written by every thread before the call) -> forward FFT, R2C post-processing
@@ -149,7 +163,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   C* buf = t.buf;
   C* nyq = t.nyq;
   __syncthreads();
-  fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2);
+  fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf);
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
@@ -166,10 +180,22 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
       const uint32_t pk = (uint32_t)slot, pkp = bitrev(kp, lgRh);
       const int ik = tpos<C>(lb + (int)pk), ikp = tpos<C>(lb + (int)pkp);
       const C Zk = buf[ik], Zkp = buf[ikp];
-      const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
-      const C A1 = cadd(Zk, cconj(Zkp)), Q = cmul(csub(Zk, cconj(Zkp)), wk);
-      buf[ik] = cscale(csub(A1, cmuli(Q)), Real(0.5));
-      if (kp != k) buf[ikp] = cscale(csub(cconj(A1), cmuli(cconj(Q))), Real(0.5));
+      if constexpr (std::is_same<C, double2>::value) {
+        // W^k B = s (c B.x - B.y, c B.y + B.x) with the table's c and h = s / 2 (12 operations for the pair
+        // instead of 16)
+        const double2* e = (const double2*)t.rc + 2 * (k << (t.tw_log2 - t.lgR));
+        const double c = __ldg(&e->x), h = __ldg(&e[1].x);
+        const double Bx = Zk.x - Zkp.x, By = Zk.y + Zkp.y;
+        const double P = fma(c, Bx, -By), Q = fma(c, By, Bx);
+        const double Hx = 0.5 * (Zk.x + Zkp.x), Hy = 0.5 * (Zk.y - Zkp.y);
+        buf[ik] = make_double2(fma(h, Q, Hx), fma(-h, P, Hy));
+        if (kp != k) buf[ikp] = make_double2(fma(-h, Q, Hx), fma(-h, P, -Hy));
+      } else {
+        const C wk = twid(t.tw, t.tw_log2, t.lgR, k);
+        const C A1 = cadd(Zk, cconj(Zkp)), Q = cmul(csub(Zk, cconj(Zkp)), wk);
+        buf[ik] = cscale(csub(A1, cmuli(Q)), Real(0.5));
+        if (kp != k) buf[ikp] = cscale(csub(cconj(A1), cmuli(cconj(Q))), Real(0.5));
+      }
     }
   }
   __syncthreads();
@@ -246,6 +272,21 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   const uint8_t* phase = item->phase;
   const double* Dtab = item->Dtab;
   const float* Dtab_f = item->Dtab_f;
+
+  if (update && !(a.flags & ROW_LOAD_EPS) && R >= 16) {
+    // the block's strain rows (and phase ids) are read only after the inverse transform: send them towards
+    // L2 now, so that the pointwise step finds them there instead of waiting on HBM
+    const int lg_lpr = lgRh - 3;   // 128-byte lines per row of one component: R * 8 / 128
+    const int n_pf = nlines << lg_lpr;
+    for (int i = tid; i < n_pf; i += nthr) {
+      const int line = i >> lg_lpr, k = i & ((1 << lg_lpr) - 1);
+      const int c = line >> lgrpc, row = line & (rpc - 1);
+      prefetch_l2(eps + ((uint32_t)c * m32 + (uint32_t)(r0 + row) * (uint32_t)R + 16u * (uint32_t)k));
+    }
+    if (!FIELD && R >= 128)
+      for (int i = tid; i < (rpc << (lgRh - 6)); i += nthr)
+        prefetch_l2(phase + ((uint32_t)(r0 + (i >> (lgRh - 6))) * (uint32_t)R + 128u * (uint32_t)(i & ((1 << (lgRh - 6)) - 1))));
+  }
 
   if (a.flags & ROW_LOAD_EPS) {
     const bool eps_df = is_f32<Real> || is_df<Real> || (a.flags & ROW_EPS_DF);
@@ -778,7 +819,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       int64_t before = 1;
       for (int y = a.a0; y < x; ++y) before *= dv.ax_len[y];
       fft_dif<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
-                                     dv.tw_log2);
+                                     dv.tw_log2, dv.lf);
       after *= dv.ax_len[x];
     }
   }
@@ -827,7 +868,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       int64_t after = 1;
       for (int y = x + 1; y < a.a1; ++y) after *= dv.ax_len[y];
       fft_dit_inv<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
-                                         dv.tw_log2);
+                                         dv.tw_log2, dv.lf);
       before *= dv.ax_len[x];
     }
     if (a.has_twiddle) {
@@ -872,8 +913,8 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
     buf[tpos<C>(idx)] = src[f * m + (r0 + row) * R + pos];
   }
   __syncthreads();
-  if (inverse) fft_dit_inv(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2);
-  else fft_dif(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2);
+  if (inverse) fft_dit_inv(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2, dv.lf);
+  else fft_dif(buf, lgR, 0, nlines, (const C*)dv.tw, dv.tw_log2, dv.lf);
   const Real sc = (Real)scale;
   for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
     const int line = idx / R, pos = idx - line * R;

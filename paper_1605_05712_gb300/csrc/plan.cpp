@@ -430,6 +430,52 @@ static int lat_upload_tables(lat_plan* P) {
         return lat_fail(LAT_ERR_CUDA, std::string("split twiddle upload: ") + cudaGetErrorString(err));
     }
   }
+  if (!P->general) {   // butterfly table of the binary64 kernels (FmaTw in fft_smem.cuh)
+    const int64_t N = int64_t(1) << P->tw_log2, n = std::max<int64_t>(N / 4, 1);
+    std::vector<double> lf((size_t)n * 8, 0.0);
+    for (int64_t t = 0; t < n; ++t) {
+      double* e = &lf[(size_t)t * 8];
+      if (t == 0) {   // identity twiddles: the plain additions, exactly
+        e[3] = e[4] = e[5] = e[6] = 1.0;
+        continue;
+      }
+      double r1, i1, r2, i2, r3, i3;
+      twiddle(t, N, &r1, &i1);
+      twiddle(2 * t, N, &r2, &i2);
+      twiddle(3 * t, N, &r3, &i3);
+      e[0] = i1 / r1;   // 0 < t < N/4: cos of t, 3t (of 2 pi / N) are nonzero
+      e[1] = i3 / r3;
+      e[3] = r1;
+      e[6] = r3 / r1;
+      int64_t swap = 0;
+      if (std::fabs(r2) >= std::fabs(i2)) {
+        e[2] = i2 / r2;
+        e[4] = e[5] = r2;
+      } else {
+        e[2] = -r2 / i2;
+        e[4] = -i2;
+        e[5] = i2;
+        swap = 1;
+      }
+      memcpy(&e[7], &swap, sizeof(swap));
+    }
+    // table of the real-row pre/post-processing (kernels.cu): for w = W_N^t, 0 < t <= N/4 (where Im w != 0),
+    // c = Re w / Im w, Im w and Im w / 2, so that w b = Im w (c b.x - b.y, c b.y + b.x)
+    std::vector<double> rc((size_t)(N / 4 + 1) * 4, 0.0);
+    for (int64_t t = 1; t <= N / 4; ++t) {
+      double re, im;
+      twiddle(t, N, &re, &im);
+      rc[(size_t)t * 4] = re / im;
+      rc[(size_t)t * 4 + 1] = im;
+      rc[(size_t)t * 4 + 2] = 0.5 * im;
+    }
+    cudaError_t err;
+    if ((err = cudaMalloc((void**)&P->d_lf, lf.size() * sizeof(double))) != cudaSuccess ||
+        (err = cudaMemcpy(P->d_lf, lf.data(), lf.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMalloc((void**)&P->d_rc, rc.size() * sizeof(double))) != cudaSuccess ||
+        (err = cudaMemcpy(P->d_rc, rc.data(), rc.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return lat_fail(LAT_ERR_CUDA, std::string("butterfly table upload: ") + cudaGetErrorString(err));
+  }
   return LAT_OK;
 }
 
@@ -573,6 +619,8 @@ extern "C" void lattice_plan_destroy(lat_plan* P) {
   if (P->d_stwf) cudaFree(P->d_stwf);
   if (P->d_twdf) cudaFree(P->d_twdf);
   if (P->d_stwdf) cudaFree(P->d_stwdf);
+  if (P->d_lf) cudaFree(P->d_lf);
+  if (P->d_rc) cudaFree(P->d_rc);
   delete P;
 }
 

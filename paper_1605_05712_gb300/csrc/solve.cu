@@ -92,6 +92,8 @@ LatDev make_dev(const lat_plan* P, int kind) {
     }
   dv.tw = kind == LAT_MIXED ? (const void*)P->d_twf : kind == LAT_DF64 ? (const void*)P->d_twdf : (const void*)P->d_tw;
   dv.stw = kind == LAT_MIXED ? (const void*)P->d_stwf : kind == LAT_DF64 ? (const void*)P->d_stwdf : (const void*)P->d_stw;
+  dv.lf = P->d_lf;
+  dv.rc = P->d_rc;
   return dv;
 }
 

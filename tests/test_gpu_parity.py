@@ -211,6 +211,63 @@ def test_solve_fp64_fixed_iterations_3d(cuda, M, prec):
     check_pair(*out, d=3)
 
 
+def _orthotropic_voigts(rng, n):
+    """n seeded axis-aligned orthotropic stiffness matrices (Voigt form): a random positive definite normal
+    block and a positive shear diagonal, no normal-shear coupling."""
+    out = np.zeros((n, 6, 6))
+    for i in range(n):
+        A = rng.standard_normal((3, 3))
+        out[i, :3, :3] = 2.0 * np.eye(3) + A @ A.T
+        out[i, 3:, 3:] = np.diag(10 ** rng.uniform(-0.3, 0.8, 3))
+    return out
+
+
+# phase tables beyond the isotropic ones: axis-aligned orthotropic and fully anisotropic stiffness (every
+# entry of the tensor-component matrix in play)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("kind", ["orthotropic", "anisotropic"])
+@pytest.mark.parametrize("M", [[[16, 4], [0, 8]], [[64, 32], [0, 1]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]],
+                               [[4096, 0, 0], [0, 1, 0], [0, 0, 1]], [[6, 1], [0, 10]]])
+def test_solve_fixed_iterations_anisotropic_tables(cuda, M, kind, prec):
+    d = len(M)
+    n_c = d * (d + 1) // 2
+    rng = np.random.default_rng(31)
+    voigts = list(_orthotropic_voigts(rng, 3) if kind == "orthotropic" else _random_spd_voigts(rng, 3))
+    E = np.ones((2, n_c)) * 0.2
+    E[0, 0] = 1.0
+
+    def ph(p, m):
+        a = inclusions(5, d, 2, 0.2)(p, m)
+        b = inclusions(9, d, 1, 0.1)(p, m)
+        return np.where(b == 1, 2, a).astype(np.uint8)
+    out = run_pair(M, ph, voigts, (5.0, 4.0), E, tol=0.0, maxit=5, cuda=cuda, precision=prec)
+    check_pair(*out, d=d)
+
+
+@pytest.mark.parametrize("kind", ["orthotropic", "anisotropic"])
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+def test_mixed_anisotropic_tables_against_fp64(cuda, M, kind):
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    d = len(M)
+    n_c = d * (d + 1) // 2
+    rng = np.random.default_rng(32)
+    voigts = list(_orthotropic_voigts(rng, 2) if kind == "orthotropic" else _random_spd_voigts(rng, 2))
+    # reference medium 2 mu0 = the mean of the extreme Mandel eigenvalues, lam0 = 0 (a contraction)
+    w = np.sqrt(2.0)
+    scale = np.outer([1, 1, 1, w, w, w], [1, 1, 1, w, w, w])
+    ev = np.concatenate([np.linalg.eigvalsh(v * scale) for v in voigts])
+    C0 = (0.0, 0.25 * (ev.min() + ev.max()))
+    P = lattice_plan(M)
+    phd = torch.from_numpy(inclusions(3, d, 4, 0.3)(P.points(), P.m)).to(cuda)
+    E = np.eye(n_c)[:2]
+    ref = basic_scheme_solve(P, phd, voigts, C0, E, tol=1e-6, maxit=3000)
+    mx = basic_scheme_solve(P, phd, voigts, C0, E, tol=1e-6, maxit=3000, precision="mixed")
+    assert ref["status"] == 0 and mx["status"] == 0
+    assert float((mx["eps"] - ref["eps"]).abs().max() / ref["eps"].abs().max()) <= MIXED_STRAIN_RTOL
+    assert np.abs(mx["sigma_bar"] - ref["sigma_bar"]).max() <= MIXED_CEFF_RTOL * np.abs(ref["sigma_bar"]).max()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("M", [[[64, 0], [0, 64]], [[512, 16], [0, 512]], [[8, 1, 0], [0, 8, 1], [0, 0, 8]],
                                [[60, 0], [0, 60]], [[45, 1], [0, 45]], [[12, 1, 0], [0, 12, 1], [0, 0, 12]]])
