@@ -242,11 +242,17 @@ template <typename Real, int NC>
 constexpr int row_min_blocks() {
   return is_f32<Real> ? 4 : (NC == 6 ? 2 : (is_df<Real> ? 3 : 4));
 }
-// FIELD: the material is a per-point stiffness field (basic_scheme_solve_field, Algorithm 1 only) instead
-// of phase ids and per-phase tables
-template <typename Real, int NC, bool FIELD>
+// MAT, the form of the material: MAT_TABLE phase ids and per-phase n_c x n_c tables; MAT_ORTHO the same
+// tables when they couple no normal and shear components and have a diagonal shear block (ROW_ORTHO: 12
+// instead of 36 products per point in 3-D); MAT_FIELD a per-point stiffness field (basic_scheme_solve_field,
+// Algorithm 1 only).  Separate instantiations, so that the general kernel keeps its own register allocation
+#define MAT_TABLE 0
+#define MAT_ORTHO 1
+#define MAT_FIELD 2
+template <typename Real, int NC, int MAT>
 __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_kernel(LatDev dv, RowArgs a) {
   typedef typename cplx_of<Real>::type C;
+  constexpr bool FIELD = (MAT == MAT_FIELD);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;
   const int Rh = dv.Rh, lgRh = dv.log2Rh, rpc = a.rpc, lgrpc = __ffs(a.rpc) - 1;
@@ -461,28 +467,47 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
       else Dt = (const Real*)Dtab;
       const Real* D0 = Dt + (int)ph.x * n_c * n_c;
       const Real* D1 = Dt + (int)ph.y * n_c * n_c;
+      if constexpr (MAT == MAT_ORTHO) {   // normal block D x D, shear diagonal
 #pragma unroll
-      for (int c = 0; c < n_c; ++c) {
-        Real t0 = 0, t1 = 0;
-        if constexpr (NC == 6) {   // rows of 6 entries: pairs of entries in one load (rows 16-byte aligned)
-#pragma unroll
-          for (int q = 0; q < n_c; q += 2) {
-            Real a0, b0, a1, b1;
-            ldg_r2(D0 + c * n_c + q, a0, b0);
-            ldg_r2(D1 + c * n_c + q, a1, b1);
-            t0 += a0 * e0[q];
-            t0 += b0 * e0[q + 1];
-            t1 += a1 * e1[q];
-            t1 += b1 * e1[q + 1];
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < n_c; ++q) {
-            t0 += ldg_r(D0 + c * n_c + q) * e0[q];
-            t1 += ldg_r(D1 + c * n_c + q) * e1[q];
-          }
+        for (int c = 0; c < D; ++c) {
+          Real a0, b0, a1, b1;
+          ldg_r2(D0 + c * n_c, a0, b0);   // NC == 6: rows 16-byte aligned
+          ldg_r2(D1 + c * n_c, a1, b1);
+          Real t0 = a0 * e0[0], t1 = a1 * e1[0];
+          t0 += b0 * e0[1];
+          t1 += b1 * e1[1];
+          t0 += ldg_r(D0 + c * n_c + 2) * e0[2];
+          t1 += ldg_r(D1 + c * n_c + 2) * e1[2];
+          buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
         }
-        buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
+#pragma unroll
+        for (int c = D; c < n_c; ++c)
+          buf[tpos<C>((c * rpc + row) * Rh + n)] =
+              cpair<C>(ldg_r(D0 + c * (n_c + 1)) * e0[c], ldg_r(D1 + c * (n_c + 1)) * e1[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < n_c; ++c) {
+          Real t0 = 0, t1 = 0;
+          if constexpr (NC == 6) {   // rows of 6 entries: pairs of entries in one load (rows 16-byte aligned)
+#pragma unroll
+            for (int q = 0; q < n_c; q += 2) {
+              Real a0, b0, a1, b1;
+              ldg_r2(D0 + c * n_c + q, a0, b0);
+              ldg_r2(D1 + c * n_c + q, a1, b1);
+              t0 += a0 * e0[q];
+              t0 += b0 * e0[q + 1];
+              t1 += a1 * e1[q];
+              t1 += b1 * e1[q + 1];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < n_c; ++q) {
+              t0 += ldg_r(D0 + c * n_c + q) * e0[q];
+              t1 += ldg_r(D1 + c * n_c + q) * e1[q];
+            }
+          }
+          buf[tpos<C>((c * rpc + row) * Rh + n)] = cpair<C>(t0, t1);
+        }
       }
     }
   }
@@ -992,11 +1017,13 @@ void launch_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_item
                      cudaStream_t st) {
   const dim3 grid(nblocks, n_items);
   if (a.flags & ROW_FIELD) {
-    if (dv.n_c == 6) row_pass_kernel<Real, 6, true><<<grid, nthreads, smem, st>>>(dv, a);
-    else row_pass_kernel<Real, 3, true><<<grid, nthreads, smem, st>>>(dv, a);
+    if (dv.n_c == 6) row_pass_kernel<Real, 6, MAT_FIELD><<<grid, nthreads, smem, st>>>(dv, a);
+    else row_pass_kernel<Real, 3, MAT_FIELD><<<grid, nthreads, smem, st>>>(dv, a);
+  } else if (dv.n_c == 6) {
+    if (a.flags & ROW_ORTHO) row_pass_kernel<Real, 6, MAT_ORTHO><<<grid, nthreads, smem, st>>>(dv, a);
+    else row_pass_kernel<Real, 6, MAT_TABLE><<<grid, nthreads, smem, st>>>(dv, a);
   } else {
-    if (dv.n_c == 6) row_pass_kernel<Real, 6, false><<<grid, nthreads, smem, st>>>(dv, a);
-    else row_pass_kernel<Real, 3, false><<<grid, nthreads, smem, st>>>(dv, a);
+    row_pass_kernel<Real, 3, MAT_TABLE><<<grid, nthreads, smem, st>>>(dv, a);
   }
 }
 template <typename Real>
@@ -1178,23 +1205,26 @@ int lat_kernel_attrs(size_t max_smem) {
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
     optin = (int)max_smem;
-  cudaError_t e = set_smem(row_pass_kernel<double, 3, false>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, false>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, false>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, false>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 3, true>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, true>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, true>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, true>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, true>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, true>, optin);
+  cudaError_t e = set_smem(row_pass_kernel<double, 3, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 3, MAT_FIELD>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, MAT_FIELD>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 3, MAT_FIELD>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, MAT_FIELD>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, MAT_FIELD>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, MAT_FIELD>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 1>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<double, 6>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<float, 6>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, false>, optin);
-  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, false>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 3, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, MAT_TABLE>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<double, 6, MAT_ORTHO>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<float, 6, MAT_ORTHO>, optin);
+  if (e == cudaSuccess) e = set_smem(row_pass_kernel<dfloat, 6, MAT_ORTHO>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 3>, optin);
   if (e == cudaSuccess) e = set_smem(col_pass_kernel<dfloat, 6>, optin);
   if (e == cudaSuccess) e = set_smem(row_complex_kernel<double>, optin);

@@ -21,6 +21,9 @@ __host__ __device__ inline int64_t tile_span(int64_t n, size_t cs) { return n + 
 #define ROW_EPS_DF 128     // binary64 kernels: the strain buffer holds double-float pairs (mixed solve);
                            // the binary32 kernels always read and write it so
 #define ROW_FIELD 256      // the material is a per-point stiffness field (ItemDev::fld*), not phase tables
+#define ROW_ORTHO 512      // every phase table of the batch couples no normal and shear components and has a
+                           // diagonal shear block (isotropic, cubic, axis-aligned orthotropic phases): the
+                           // six-component row pass reads the normal block and the shear diagonal only
 
 // ItemScal::done
 #define ITEM_ACTIVE 0

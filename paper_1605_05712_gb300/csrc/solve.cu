@@ -289,6 +289,15 @@ void voigt_to_tc(const double* V, int d, double* out) {
     for (int J = 0; J < n_c; ++J) out[I * n_c + J] = V[vi[I] * 6 + vi[J]] * (J >= d ? 2.0 : 1.0);
 }
 
+// true when the tensor-component matrix T (n_c x n_c) couples no normal and shear components and has a
+// diagonal shear block (exact zeros): the polarization needs the normal block and the shear diagonal only
+bool tc_ortho(const double* T, int n_c, int d) {
+  for (int I = 0; I < n_c; ++I)
+    for (int J = 0; J < n_c; ++J)
+      if (I != J && (I >= d || J >= d) && T[I * n_c + J] != 0.0) return false;
+  return true;
+}
+
 #define CK(x)                                                                                  \
   do {                                                                                         \
     cudaError_t e_ = (x);                                                                      \
@@ -530,6 +539,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       }
     }
   }
+  // the isotropic reference medium has the structure, so D = C - C0 has it exactly when C has
+  bool ortho = true;
+  for (int t = 0; t < n_tables; ++t)
+    for (int p = 0; p < nph[t]; ++p)
+      ortho = ortho && tc_ortho(&tabs[(size_t)(2 * t + 1) * tstride + (size_t)p * n_c * n_c], n_c, d);
   std::vector<ItemDev> hdev(n_items);
   for (int i = 0; i < n_items; ++i) {
     const ItemHost& it = items[i];
@@ -624,7 +638,7 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
   CK(cudaMemcpyAsync(glob, &g.glob0, sizeof(GlobScal), cudaMemcpyHostToDevice, st));
   const ItemDev* ditems = (const ItemDev*)(ws + wl.items);
   const bool field = n_items > 0 && items[0].field != nullptr;   // a field solve: all items share the field
-  const int fieldflag = field ? ROW_FIELD : 0;
+  const int matflag = field ? ROW_FIELD : (ortho ? ROW_ORTHO : 0);   // the material's form
   if (field && o.precision != LAT_FP64)
     launch_field_copies(items[0].field, o.precision == LAT_MIXED ? (float*)(ws + wl.fld_f) : nullptr,
                         (dfloat*)(ws + wl.fld_df), (int64_t)21 * m, st);
@@ -713,13 +727,13 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
       // (the Eyre-Milton cold start u = (C + C0) E varies in space, so its first step is taken in full)
       const bool incr_first = incr && !o.warm_start && o.scheme == LAT_SCHEME_BASIC;
       RowArgs first = ra;
-      first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
+      first.flags = ROW_LOAD_EPS | (gamma_in_row ? ROW_GAMMA : 0) | matflag;
       first.mat.increment = incr_first ? 1 : 0;
       ColArgs c0 = ca;
       c0.scal = nullptr;
       c0.mat.increment = incr_first ? 1 : 0;
       g.full = ra;
-      g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) | fieldflag |
+      g.full.flags = ROW_UPDATE | (gamma_in_row ? ROW_GAMMA : 0) | (incr ? ROW_INCREMENT : 0) | matflag |
                      (incr_first ? ROW_INCR_FIRST : 0);
       g.full.mat.increment = incr ? 1 : 0;
       g.cl = ca;
@@ -749,11 +763,11 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
         r64.TN = ws + wl.TN64;
         r64.it.pause_tol = 0.0;
         g.r_pro = r64;
-        g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
+        g.r_pro.flags = ROW_LOAD_EPS | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | matflag;
         g.r_pro.mat.increment = 0;
         g.r_upd = r64;
         g.r_upd.flags =
-            ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | fieldflag;
+            ROW_UPDATE | ROW_TAU_DELTA | ROW_ONLY_PAUSED | ROW_EPS_DF | (gamma_in_row ? ROW_GAMMA : 0) | matflag;
         g.r_upd.mat.increment = 1;
         g.c64 = ca;
         g.c64.T = r64.T;
@@ -1291,6 +1305,15 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
   RowArgs ra;
   memset(&ra, 0, sizeof(ra));
   ra.flags = ROW_UPDATE | (P->nax == 1 ? ROW_GAMMA : 0) | (fp32 ? ROW_INCREMENT | ROW_INCR_FIRST : 0);
+  {  // the same material form as the solve
+    bool ortho = true;
+    double T[36];
+    for (int p = 0; p < n_phases; ++p) {
+      voigt_to_tc(stiffness + 36 * p, d, T);
+      ortho = ortho && tc_ortho(T, n_c, d);
+    }
+    if (ortho) ra.flags |= ROW_ORTHO;
+  }
   ra.rpc = geo.rpc;
   ra.items = (const ItemDev*)(ws + wl.items);
   ra.T = ws + wl.T;

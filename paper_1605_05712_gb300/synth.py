@@ -211,7 +211,13 @@ def hashin_workload(seed=BASE_SEED, c=(0.1, 0.15, 0.2), total_fraction=0.25, cor
     Cb = iso_tensor3(*matrix_base)
     u = ceff_eps0 - np.einsum('ijkl,kl->ij', Cb, eps0)
     Cm = Cb + np.einsum('ij,kl->ijkl', u, u) / np.einsum('ij,ij', u, eps0)
-    stiff = [iso_voigt(*core), iso_voigt(*coating), tensor_to_voigt(Cm)]
+    Vm = tensor_to_voigt(Cm)
+    Vi = iso_voigt(*iso_projection(Vm))
+    if np.abs(Vm - Vi).max() <= 1e-12 * np.abs(Vm).max():
+        # u is a multiple of the identity when the coating and base shear moduli agree (the Se terms of u
+        # cancel), so the matrix is isotropic: take its exact form, without the rotation's rounding
+        Vm = Vi
+    stiff = [iso_voigt(*core), iso_voigt(*coating), Vm]
     lams, mus = zip(*[iso_projection(V) for V in stiff])
     return dict(c=c, rho_c=rho_c, rho_e=rho_e, R=R, stiffness=stiff, eps0=eps0, ceff_eps0=ceff_eps0,
                 C0=c0_mean_extremes(lams, mus))
