@@ -107,23 +107,39 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ cost model from the plan's decomposition
-def kernel_models(P, n_items, prec):
+def tables_orthotropic(stiffness, d):
+    """True when every Voigt table couples no normal and shear components and has a diagonal shear block
+    (exact zeros): the row pass then polarizes with the normal block and the shear diagonal only."""
+    vi = [0, 1, 2, 3, 4, 5] if d == 3 else [0, 1, 5]
+    n_c = len(vi)
+    for V in stiffness:
+        V = np.asarray(V)
+        for I in range(n_c):
+            for J in range(n_c):
+                if I != J and (I >= d or J >= d) and V[vi[I], vi[J]] != 0.0:
+                    return False
+    return True
+
+
+def kernel_models(P, n_items, prec, ortho=False):
     """Algorithmic flops and HBM bytes of every kernel of one batched iteration, in launch order (row pass,
     then the column passes: forward groups innermost first, the Green group, inverse groups), from the
     plan's FFT decomposition (lattice_plan_layout).  5 N log2 N flops per complex FFT of N points; ~10 flops
-    per complex value for each R2C pre/post-processing; 2 n_c^2 per point for the polarization and 3 n_c for
-    the update and residual; ~90 per complex frequency value for the Green operator; 6 per complex value for
-    each four-step twiddle.  Bytes: every HBM-resident word read and written once (spectrum slots of s bytes
-    per complex value, the strain as 8-byte words, one phase byte per point)."""
+    per complex value for each R2C pre/post-processing; 2 n_c^2 per point for the polarization (orthotropic
+    tables: 2 (d^2 + n_c - d), the products that are not structurally zero) and 3 n_c for the update and
+    residual; ~90 per complex frequency value for the Green operator; 6 per complex value for each four-step
+    twiddle.  Bytes: every HBM-resident word read and written once (spectrum slots of s bytes per complex
+    value, the strain as 8-byte words, one phase byte per point)."""
     import math
     lay = P.layout()
     n_c, m = P.n_c, P.m
+    n_pol = (P.d * P.d + n_c - P.d) if ortho else n_c * n_c
     ax = lay["ax_len"]
     R = ax[-1]
     Rh = R // 2
     spec = m // 2 + m // R                     # complex values per component: half spectrum + Nyquist plane
     s = 8 if prec == "mixed" else 16
-    row_f = n_c * (m // R) * 2 * (5 * Rh * math.log2(max(Rh, 1)) + 10 * Rh) + m * (2 * n_c * n_c + 3 * n_c)
+    row_f = n_c * (m // R) * 2 * (5 * Rh * math.log2(max(Rh, 1)) + 10 * Rh) + m * (2 * n_pol + 3 * n_c)
     if len(ax) == 1:
         row_f += 90 * spec
     row_b = 2 * n_c * spec * s + 2 * n_c * m * 8 + m
@@ -270,7 +286,7 @@ def roofline_of(w, work, prec, iters, pk, bound):
     for it, its in zip(work, iters):
         P = it["plan"]
         ms = lattice_pass_times(P, it["phase"], w["stiffness"], w["C0"], E, precision=prec, n_reps=10)
-        models = kernel_models(P, N_LC, prec)
+        models = kernel_models(P, N_LC, prec, ortho=tables_orthotropic(w["stiffness"], P.d))
         for k, (t, mo) in enumerate(zip(ms, models)):
             share = t * max(its)
             rec = dict(lattice=it["name"], kernel=mo["kernel"], ms=round(t, 5), flops=mo["flops"], bytes=mo["bytes"],
@@ -349,6 +365,7 @@ def bench_gpu(args):
         run_step(w, work, ws, "mixed")
         variants["mixed_roofline"] = roofline_of(w, work, "mixed", ttt["mixed"]["iterations"], pk, "hbm")
         variants["laminate2d_262144"] = bench_laminate2d(dev, args, flush, st)
+        variants["laminate4096_latency"] = bench_laminate4096(dev, args, flush, st)
 
     gpu_launches = sum(launches_per_solve(it["plan"], its, "fp64") for it, its in zip(work, iters))
     m_total = sum(it["plan"].m for it in work)
@@ -416,6 +433,40 @@ def bench_laminate2d(dev, args, flush, st):
         step()
         ms, u, its = timed(step, max(1, min(args.steps, 3)), flush, st)
         out[mode] = {"value": round(u / (ms / 1e3), 1), "ms_per_step": round(ms, 3), "iterations": its}
+    return out
+
+
+def bench_laminate4096(dev, args, flush, st):
+    """Config 1, the latency case: the 2-D laminate (layer normal (1,3), phases (1,1) / (10,10), C0 the mean
+    of the extremes) at m = 4096, E = (1,0,0), one binary64 solve to tol 1e-8 per lattice: the aligned
+    rank-1 lattice of config 1, the spread rank-1 lattice [[64,1],[0,64]] and the tensor grid diag(64,64)
+    the paper times (94 iterations, 41.2 s in its Matlab code).  Wall time per solve through the C ABI
+    (device inputs, results left on the device), median of the timed repeats."""
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan, synth
+    stiff = [synth.iso_voigt(*l) for l in LAMES]
+    C0 = synth.c0_mean_extremes([l[0] for l in LAMES], [l[1] for l in LAMES])
+    E = unit_loads(3)[:1]
+    out = {}
+    for name, M in (("laminate4096_aligned", synth.LATTICES["laminate4096_aligned"]),
+                    ("laminate4096_rank1", synth.LATTICES["laminate4096_rank1"]), ("grid64", [[64, 0], [0, 64]])):
+        P = lattice_plan(M)
+        ph = torch.from_numpy(synth.laminate_phase(P.points(), P.m, N_INT)).to(dev)
+        ws = torch.empty(P.workspace_bytes(1, 0), dtype=torch.uint8, device=dev)
+        eps = torch.empty((1, 3, P.m), dtype=torch.float64, device=dev)
+        solve = lambda: basic_scheme_solve(P, ph, stiff, C0, E, tol=1e-8, maxit=MAXIT, workspace=ws, eps_out=eps)
+        for _ in range(3):
+            g = solve()
+        times = []
+        for _ in range(max(5, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = solve()
+            times.append((time.perf_counter() - t0) * 1e3)
+        ms = float(np.median(times))
+        out[name] = {"M": M, "m": P.m, "iterations": int(g["iters"][0]), "ms_per_solve": round(ms, 3),
+                     "point_iterations_per_s": round(P.m * int(g["iters"][0]) / (ms / 1e3), 1),
+                     "sigma_bar": [float(x) for x in np.asarray(g["sigma_bar"][0])]}
     return out
 
 

@@ -183,30 +183,33 @@ __device__ void r16_stage(C* s, int log2L, int lgnlo, int nhi, int lg, const C* 
 //   form B (Im w != 0): tau = -Re w / Im w,  w b = (-Im w b'.y, Im w b'.x)
 // The butterfly's twiddles are w1 = W_N^j, w2 = w1^2, w3 = w1^3 with 0 <= j < N/4, so w1 and w3 are always
 // in form A (their angles stay off pi/2 and 3 pi/2 for power-of-two N); w2 takes whichever form has the
-// larger divisor.  Table entry t (N = 2^tw_log2, t < N/4), eight binary64 words:
-//   t1 = tau(w1), t3 = tau(w3), tau2 = tau(w2), s1 = Re w1, sx2, sy2 (the two scales of w2 b), r = Re w3 / Re w1,
-//   and a word whose bits are nonzero when w2 is in form B.
+// larger divisor.  Per twiddle index t (N = 2^tw_log2, t < N/4): t1 = tau(w1), t3 = tau(w3), tau2 = tau(w2),
+// s1 = Re w1, sx2 (the first scale of w2 b; the second is sy2 = sx2 in form A, -sx2 in form B) and
+// r = Re w3 / Re w1 with its lowest mantissa bit replaced by the form of w2 (1: form B; <= 1 ulp of r).
 // Then w1 a + w3 b = s1 (a' + r b'), and every sum of a value and a scaled product is one fused multiply-add.
-// Entry 0 holds the identity twiddles (tau = 0, scales and r = 1), which reproduce the plain additions
+// Index 0 holds the identity twiddles (tau = 0, scales and r = 1), which reproduce the plain additions
 // exactly, so no lane needs a branch of its own.
+// Layout (lf): two copies of six arrays of n = max(N/4, 1) words, [t1 | t3 | tau2 | s1 | sx2 | r]; the first
+// copy in natural order of t, the second in bit-reversed order (position u holds t = bitrev(u) over log2 n
+// bits), so that lanes with neighbouring indices read neighbouring words in both transforms.
 struct FmaTw {
   double t1, t3, tau2, s1, sx2, sy2, r;
   bool swap;
 };
-__device__ __forceinline__ FmaTw fma_tw(const double* __restrict__ lf, int tw_log2, int lg, uint32_t j) {
-  const double2* p = (const double2*)lf + 4 * (size_t)(j << (tw_log2 - lg));
-  const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+__device__ __forceinline__ FmaTw fma_tw(const double* __restrict__ base, int n, uint32_t e) {
   FmaTw w;
-  w.t1 = a.x;
-  w.t3 = a.y;
-  w.tau2 = b.x;
-  w.s1 = b.y;
-  w.sx2 = c.x;
-  w.sy2 = c.y;
-  w.r = d.x;
-  w.swap = __double_as_longlong(d.y) != 0;
+  w.t1 = __ldg(base + e);
+  w.t3 = __ldg(base + n + e);
+  w.tau2 = __ldg(base + 2 * n + e);
+  w.s1 = __ldg(base + 3 * n + e);
+  w.sx2 = __ldg(base + 4 * n + e);
+  w.r = __ldg(base + 5 * n + e);
+  w.swap = (__double_as_longlong(w.r) & 1) != 0;
+  // sy2 = -sx2 in form B: a sign flip by integer operations (no binary64 instruction)
+  w.sy2 = __longlong_as_double(__double_as_longlong(w.sx2) ^ ((long long)w.swap << 63));
   return w;
 }
+__device__ __forceinline__ int fma_tw_n(int tw_log2) { return tw_log2 >= 2 ? 1 << (tw_log2 - 2) : 1; }
 
 // radix-4 decimation-in-time butterfly: a0..a3 at block positions j, j + N/4, j + N/2, j + 3N/4 of a block of
 // N = 2^lg, twiddles w2, w1, w3 on a1, a2, a3 (INV: their conjugates, the inverse transform)
@@ -265,18 +268,24 @@ __device__ __forceinline__ void r4_fma(double2& a0, double2& a1, double2& a2, do
     a3 = make_double2(fma(w.s1, DMy, Bx), fma(-w.s1, DMx, By));
   }
 }
-// the butterfly of position j in a block of 2^lg: blocks of 4 have no twiddles; where every lane of a warp
-// has the same j (uniform), j = 0 takes the plain additions
+// the butterfly at slots i0..i3 of the tile: plain additions (blocks of 4, or twiddle index 0 where every
+// lane of the warp has the same index), else the fused multiply-add form with twiddles w
 template <bool INV>
-__device__ __forceinline__ void r4_at(double2& a0, double2& a1, double2& a2, double2& a3, uint32_t j, int lg,
-                                      bool uniform, const double* __restrict__ lf, int tw_log2) {
-  if (lg == 2 || (uniform && j == 0)) r4_plain<INV>(a0, a1, a2, a3);
-  else r4_fma<INV>(a0, a1, a2, a3, fma_tw(lf, tw_log2, lg, j));
+__device__ __forceinline__ void r4_slots(double2* s, int i0, int i1, int i2, int i3, bool plain, const FmaTw& w) {
+  double2 a0 = s[i0], a1 = s[i1], a2 = s[i2], a3 = s[i3];
+  if (plain) r4_plain<INV>(a0, a1, a2, a3);
+  else r4_fma<INV>(a0, a1, a2, a3, w);
+  s[i0] = a0;
+  s[i1] = a1;
+  s[i2] = a2;
+  s[i3] = a3;
 }
 
 // Stage plan shared by both binary64 transforms: an odd log2 length first takes one twiddle-free radix-2
 // stage (span 1 of the bit-reversed-input algorithm), then radix-4 stages on blocks of 2^lg, lg = lg0 + 2,
-// lg0 + 4, ..., log2L, one shared-memory round trip each.
+// lg0 + 4, ..., log2L, one shared-memory round trip each.  The nhi line groups are nrep equal sets (the
+// tensor components, outermost) with the same twiddles: a thread loads a butterfly's twiddles once and
+// applies them in every set (nrep times fewer table loads).
 //
 // The inverse (bit-reversed in, natural out) is the decimation-in-time algorithm as it stands.  The forward
 // transform (natural in, bit-reversed out) is the same algorithm with every memory position p relabelled
@@ -285,8 +294,11 @@ __device__ __forceinline__ void r4_at(double2& a0, double2& a1, double2& a2, dou
 // twiddles stay those of j.  So both run twiddle-before-butterfly (decimation in time), the order the
 // fused multiply-adds need, and the forward output is the bit-reversed spectrum the decimation-in-frequency
 // kernels produce.
-static __device__ void fft_fwd_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2) {
+static __device__ void fft_fwd_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2,
+                                   int nrep) {
   if (log2L == 0) return;
+  const int n = fma_tw_n(tw_log2);
+  const int nh1 = nhi / nrep, rep_off = nh1 << (log2L + lgnlo);
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
   const int lg0 = log2L & 1;
   if (lg0) {   // span L/2, no twiddles
@@ -305,9 +317,11 @@ static __device__ void fft_fwd_fma(double2* s, int log2L, int lgnlo, int nhi, co
   }
   int lg = lg0 + 2;
   for (; lg <= log2L; lg += 2) {
-    // block 2^lg relabelled: groups G of 4H values, H = 2^(log2L - lg); value u at G 4H + bitrev2(u) H + i
+    // block 2^lg relabelled: groups G of 4H values, H = 2^(log2L - lg); value u at G 4H + bitrev2(u) H + i.
+    // Its twiddle index bitrev(G) over lg - 2 bits, shifted to the table's N, is bitrev(G) over log2 n bits:
+    // position G of the bit-reversed table copy, the same at every stage
     const int lgH = log2L - lg, lgg = lg - 2;
-    const unsigned total = (unsigned)nhi << (lgnlo + log2L - 2);
+    const unsigned total = (unsigned)nh1 << (lgnlo + log2L - 2);
     const bool uni = lgH + lgnlo >= 5;
     for (unsigned b = threadIdx.x; b < total; b += nthr) {
       const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
@@ -315,21 +329,24 @@ static __device__ void fft_fwd_fma(double2* s, int log2L, int lgnlo, int nhi, co
       const unsigned l_hi = rest >> (log2L - 2);
       const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + (((G << (lgH + 2)) | i) << lgnlo));
       const int h = 1 << (lgH + lgnlo);
-      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + 2 * h), i2 = tpos<double2>(e0 + h),
-                i3 = tpos<double2>(e0 + 3 * h);
-      double2 a0 = s[i0], a1 = s[i1], a2 = s[i2], a3 = s[i3];
-      r4_at<false>(a0, a1, a2, a3, bitrev(G, lgg), lg, uni, lf, tw_log2);
-      s[i0] = a0;
-      s[i1] = a1;
-      s[i2] = a2;
-      s[i3] = a3;
+      const bool plain = lg == 2 || (uni && G == 0);
+      FmaTw w = {};
+      if (!plain) w = fma_tw(lf + 6 * n, n, G);
+      for (int c = 0; c < nrep; ++c) {
+        const int ec = e0 + c * rep_off;
+        r4_slots<false>(s, tpos<double2>(ec), tpos<double2>(ec + 2 * h), tpos<double2>(ec + h),
+                        tpos<double2>(ec + 3 * h), plain, w);
+      }
     }
     __syncthreads();
   }
 }
 
-static __device__ void fft_inv_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2) {
+static __device__ void fft_inv_fma(double2* s, int log2L, int lgnlo, int nhi, const double* __restrict__ lf, int tw_log2,
+                                   int nrep) {
   if (log2L == 0) return;
+  const int n = fma_tw_n(tw_log2);
+  const int nh1 = nhi / nrep, rep_off = nh1 << (log2L + lgnlo);
   const unsigned nthr = blockDim.x, nlo_m = (1u << lgnlo) - 1u;
   const int lg0 = log2L & 1;
   const bool uni = lgnlo >= 5;   // neighbouring lanes differ in the line, not in the block position
@@ -350,21 +367,21 @@ static __device__ void fft_inv_fma(double2* s, int log2L, int lgnlo, int nhi, co
   int lg = lg0 + 2;
   for (; lg <= log2L; lg += 2) {
     const int lgq = lg - 2;
-    const unsigned total = (unsigned)nhi << (lgnlo + log2L - 2);
+    const unsigned total = (unsigned)nh1 << (lgnlo + log2L - 2);
     for (unsigned b = threadIdx.x; b < total; b += nthr) {
       const unsigned l_lo = b & nlo_m, rest = b >> lgnlo;
       const unsigned j = rest & ((1u << lgq) - 1u), blk = (rest >> lgq) & ((1u << (log2L - lg)) - 1u);
       const unsigned l_hi = rest >> (log2L - 2);
       const int e0 = (int)(((l_hi << (log2L + lgnlo)) | l_lo) + ((((blk << lg) | j)) << lgnlo));
       const int q = 1 << (lgq + lgnlo);
-      const int i0 = tpos<double2>(e0), i1 = tpos<double2>(e0 + q), i2 = tpos<double2>(e0 + 2 * q),
-                i3 = tpos<double2>(e0 + 3 * q);
-      double2 a0 = s[i0], a1 = s[i1], a2 = s[i2], a3 = s[i3];
-      r4_at<true>(a0, a1, a2, a3, j, lg, uni, lf, tw_log2);
-      s[i0] = a0;
-      s[i1] = a1;
-      s[i2] = a2;
-      s[i3] = a3;
+      const bool plain = lg == 2 || (uni && j == 0);
+      FmaTw w = {};
+      if (!plain) w = fma_tw(lf, n, j << (tw_log2 - lg));
+      for (int c = 0; c < nrep; ++c) {
+        const int ec = e0 + c * rep_off;
+        r4_slots<true>(s, tpos<double2>(ec), tpos<double2>(ec + q), tpos<double2>(ec + 2 * q),
+                       tpos<double2>(ec + 3 * q), plain, w);
+      }
     }
     __syncthreads();
   }
@@ -373,12 +390,13 @@ static __device__ void fft_inv_fma(double2* s, int log2L, int lgnlo, int nhi, co
 // Forward DIF FFT (sign -1, unnormalized) of nhi * nlo lines of length 2^log2L, nlo = 2^lgnlo.
 // Output in bit-reversed order.  Must be called by all threads of the block.
 // FUSE: run pairs of radix-4 stages in registers (r16_stage), as the binary32 kernels do.
+// nrep (binary64 only): the lines form nrep equal sets, outermost, that share their twiddles.
 // Binary64 (C = double2) runs fft_fwd_fma with the fused multiply-add table lf instead (FUSE unused).
 template <typename C, bool FUSE = (sizeof(C) == 8)>
 __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2,
-                        const double* __restrict__ lf) {
+                        const double* __restrict__ lf, int nrep = 1) {
   if constexpr (std::is_same<C, double2>::value) {
-    fft_fwd_fma(s, log2L, lgnlo, nhi, lf, tw_log2);
+    fft_fwd_fma(s, log2L, lgnlo, nhi, lf, tw_log2, nrep);
     return;
   }
   if (log2L == 0) return;
@@ -438,9 +456,9 @@ __device__ void fft_dif(C* s, int log2L, int lgnlo, int nhi, const C* __restrict
 // Binary64 runs fft_inv_fma (same result up to rounding).
 template <typename C, bool FUSE = (sizeof(C) == 8)>
 __device__ void fft_dit_inv(C* s, int log2L, int lgnlo, int nhi, const C* __restrict__ tw, int tw_log2,
-                            const double* __restrict__ lf) {
+                            const double* __restrict__ lf, int nrep = 1) {
   if constexpr (std::is_same<C, double2>::value) {
-    fft_inv_fma(s, log2L, lgnlo, nhi, lf, tw_log2);
+    fft_inv_fma(s, log2L, lgnlo, nhi, lf, tw_log2, nrep);
     return;
   }
   if (log2L == 0) return;

@@ -147,7 +147,7 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
     }
   }
   __syncthreads();
-  fft_dit_inv<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf);
+  fft_dit_inv<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf, NC);
 }
 
 // real rows (written by every thread before the call) -> forward FFT, R2C post-processing
@@ -163,7 +163,7 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   C* buf = t.buf;
   C* nyq = t.nyq;
   __syncthreads();
-  fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf);
+  fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf, NC);
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   }
 
   // pointwise: update, residual, polarization
-  double dsum = 0.0;
+  double dsum = 0.0, dsum_sh = 0.0;   // binary64 residual: normal and shear components (the latter counted twice)
   // increment form: T carries delta^(n-1) once the first update is done (iteration counter > 0), or
   // from the start after a cold-start prologue; the polarization is always taken of the increment
   const bool tau_of_delta = update && (a.flags & (ROW_INCREMENT | ROW_TAU_DELTA)) != 0;
@@ -433,8 +433,9 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
             d0 = n0 - old.x;
             d1 = n1 - old.y;
           }
-          const double wgt = (c >= D) ? 2.0 : 1.0;
-          dsum += wgt * (d0 * d0 + d1 * d1);
+          double& acc = (c >= D) ? dsum_sh : dsum;   // c is unrolled: a register, no select
+          acc = fma(d0, d0, acc);
+          acc = fma(d1, d1, acc);
           if (a.flags & ROW_EPS_DF) {
             const float2 h0 = df_of(n0), h1 = df_of(n1);
             *(float4*)pe = make_float4(h0.x, h0.y, h1.x, h1.y);
@@ -524,6 +525,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
     else pr = dd_acc + (dd_shear + dd_shear);
     if (!item_reduce<1>(&pr, partials, isc, red, &s_last, &tot)) return;
   } else {
+    dsum = fma(2.0, dsum_sh, dsum);
     if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
   }
   if (tid == 0) item_report(sqrt(tot) / item->norm0, isc, item_i, a.it);
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       int64_t before = 1;
       for (int y = a.a0; y < x; ++y) before *= dv.ax_len[y];
       fft_dif<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
-                                     dv.tw_log2, dv.lf);
+                                     dv.tw_log2, dv.lf, n_f);
       after *= dv.ax_len[x];
     }
   }
@@ -893,7 +895,7 @@ __global__ void __launch_bounds__(256, (col_min_blocks<Real, NC>())) col_pass_ke
       int64_t after = 1;
       for (int y = x + 1; y < a.a1; ++y) after *= dv.ax_len[y];
       fft_dit_inv<C, fuse16<Real, NC>()>(s, dv.ax_log2[x], lgw + (__ffsll(after) - 1), (int)(n_f * before), tw,
-                                         dv.tw_log2, dv.lf);
+                                         dv.tw_log2, dv.lf, n_f);
       before *= dv.ax_len[x];
     }
     if (a.has_twiddle) {

@@ -432,32 +432,43 @@ static int lat_upload_tables(lat_plan* P) {
   }
   if (!P->general) {   // butterfly table of the binary64 kernels (FmaTw in fft_smem.cuh)
     const int64_t N = int64_t(1) << P->tw_log2, n = std::max<int64_t>(N / 4, 1);
-    std::vector<double> lf((size_t)n * 8, 0.0);
+    int lgn = 0;
+    while ((int64_t(1) << lgn) < n) ++lgn;
+    std::vector<double> lf((size_t)n * 12, 0.0);
     for (int64_t t = 0; t < n; ++t) {
-      double* e = &lf[(size_t)t * 8];
-      if (t == 0) {   // identity twiddles: the plain additions, exactly
-        e[3] = e[4] = e[5] = e[6] = 1.0;
-        continue;
-      }
-      double r1, i1, r2, i2, r3, i3;
-      twiddle(t, N, &r1, &i1);
-      twiddle(2 * t, N, &r2, &i2);
-      twiddle(3 * t, N, &r3, &i3);
-      e[0] = i1 / r1;   // 0 < t < N/4: cos of t, 3t (of 2 pi / N) are nonzero
-      e[1] = i3 / r3;
-      e[3] = r1;
-      e[6] = r3 / r1;
+      double e[6];   // t1, t3, tau2, s1, sx2, r (with the form bit)
       int64_t swap = 0;
-      if (std::fabs(r2) >= std::fabs(i2)) {
-        e[2] = i2 / r2;
-        e[4] = e[5] = r2;
+      if (t == 0) {   // identity twiddles: the plain additions, exactly
+        e[0] = e[1] = e[2] = 0.0;
+        e[3] = e[4] = e[5] = 1.0;
       } else {
-        e[2] = -r2 / i2;
-        e[4] = -i2;
-        e[5] = i2;
-        swap = 1;
+        double r1, i1, r2, i2, r3, i3;
+        twiddle(t, N, &r1, &i1);
+        twiddle(2 * t, N, &r2, &i2);
+        twiddle(3 * t, N, &r3, &i3);
+        e[0] = i1 / r1;   // 0 < t < N/4: cos of t, 3t (of 2 pi / N) are nonzero
+        e[1] = i3 / r3;
+        e[3] = r1;
+        e[5] = r3 / r1;
+        if (std::fabs(r2) >= std::fabs(i2)) {
+          e[2] = i2 / r2;
+          e[4] = r2;
+        } else {
+          e[2] = -r2 / i2;
+          e[4] = -i2;
+          swap = 1;
+        }
       }
-      memcpy(&e[7], &swap, sizeof(swap));
+      uint64_t rb;
+      memcpy(&rb, &e[5], sizeof(rb));
+      rb = (rb & ~uint64_t(1)) | (uint64_t)swap;
+      memcpy(&e[5], &rb, sizeof(rb));
+      uint64_t u = 0;   // bit-reversed position of t over lgn bits
+      for (int k = 0; k < lgn; ++k) u |= (uint64_t)((t >> k) & 1) << (lgn - 1 - k);
+      for (int k = 0; k < 6; ++k) {
+        lf[(size_t)k * n + t] = e[k];
+        lf[(size_t)(6 + k) * n + u] = e[k];
+      }
     }
     // table of the real-row pre/post-processing (kernels.cu): for w = W_N^t, 0 < t <= N/4 (where Im w != 0),
     // c = Re w / Im w, Im w and Im w / 2, so that w b = Im w (c b.x - b.y, c b.y + b.x)
