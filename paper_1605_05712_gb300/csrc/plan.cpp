@@ -314,7 +314,10 @@ static int choose_layout(lat_plan* P) {
     int64_t B = int64_t(1) << lb;
     if (B <= 2 * RH_MAX && B >= 2) cands.push_back(B);
   }
-  if (eL <= 2 * RH_MAX) cands.push_back(eL);
+  // no split only where it leaves work for several blocks (at least 32 rows) or the rows are short: a
+  // single long row (a small rank-1 pattern, m <= 4096) would run as one block per item on one SM, where
+  // the split's two passes spread it over m / B blocks
+  if (eL <= 2 * RH_MAX && (P->m / eL >= 32 || eL <= 128)) cands.push_back(eL);
   for (int64_t B : cands) {
     std::vector<int64_t> lens;
     for (size_t i = 0; i + 1 < paxes.size(); ++i) lens.push_back(P->e[paxes[i]]);
