@@ -113,17 +113,20 @@ __device__ __forceinline__ void row_tile_inverse(const RowTile<Real>& t) {
   }
   cp_async_wait_all();
   __syncthreads();
+  // k = 0 (with the Nyquist value) in a loop of its own, so that its arithmetic never rides predicated
+  // along in the pairs' loop (it touches slot 0 and the Nyquist value only)
+  for (int line = tid; line < nlines; line += nthr) {
+    C& L0 = buf[tpos<C>(line * Rh)];
+    const Real X0 = L0.x, XN = nyq[line].x;
+    L0.x = X0 + XN;
+    L0.y = X0 - XN;
+  }
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
     const int k = (int)bitrev((uint32_t)slot, lgRh);
     const int lb = line * Rh;
-    if (k == 0) {
-      C& L0 = buf[tpos<C>(lb)];
-      const Real X0 = L0.x, XN = nyq[line].x;
-      L0.x = X0 + XN;
-      L0.y = X0 - XN;
-    } else {
+    if (k != 0) {
       // Z_k = A + i B conj(W^k), A = X_k + conj X_{Rh-k}, B = X_k - conj X_{Rh-k}; the partner reuses
       // both: W_R^{Rh-k} = -conj(W_R^k), so Z_{Rh-k} = conj(A) + i conj(B conj(W^k))
       const int kp = Rh - k;
@@ -164,16 +167,17 @@ __device__ __forceinline__ void row_tile_forward(const RowTile<Real>& t, const L
   C* nyq = t.nyq;
   __syncthreads();
   fft_dif<C, fuse16<Real, NC>()>(buf, lgRh, 0, nlines, t.tw, t.tw_log2, t.lf, NC);
+  for (int line = tid; line < nlines; line += nthr) {   // k = 0 and the Nyquist value, as in the inverse
+    const C Z0 = buf[tpos<C>(line * Rh)];
+    buf[tpos<C>(line * Rh)] = cpair<C>(Z0.x + Z0.y, Real(0));
+    nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
+  }
   for (int idx = tid; idx < t.npl_total; idx += nthr) {
     int line, slot;
     kslot_index(idx, nlines, lgRh, line, slot);
     const int k = (int)bitrev((uint32_t)slot, lgRh);
     const int lb = line * Rh;
-    if (k == 0) {
-      const C Z0 = buf[tpos<C>(lb)];
-      buf[tpos<C>(lb)] = cpair<C>(Z0.x + Z0.y, Real(0));
-      nyq[line] = cpair<C>(Z0.x - Z0.y, Real(0));
-    } else {
+    if (k != 0) {
       // the partner reuses A and W^k B: X_{Rh-k} = 1/2 (conj(A) - i conj(W^k B)), since
       // W_R^{Rh-k} = -conj(W_R^k) and Z_{Rh-k} - conj Z_k = -conj(B)
       const int kp = Rh - k;
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   }
 
   if (a.flags & ROW_LOAD_EPS) {
-    const bool eps_df = is_f32<Real> || is_df<Real> || (a.flags & ROW_EPS_DF);
+    const bool eps_df = is_f32<Real> || is_df<Real>;   // binary64 kernels: binary64 strain
     for (int idx = tid; idx < nlines * Rh; idx += nthr) {
       const int line = idx >> lgRh, n = idx & (Rh - 1);
       const int c = line >> lgrpc, row = line & (rpc - 1);
@@ -319,8 +323,12 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
   double dsum = 0.0, dsum_sh = 0.0;   // binary64 residual: normal and shear components (the latter counted twice)
   // increment form: T carries delta^(n-1) once the first update is done (iteration counter > 0), or
   // from the start after a cold-start prologue; the polarization is always taken of the increment
-  const bool tau_of_delta = update && (a.flags & (ROW_INCREMENT | ROW_TAU_DELTA)) != 0;
-  const bool incr = update && (a.flags & ROW_INCREMENT) != 0 &&
+  // (binary64 kernels never carry the increment: ROW_INCREMENT comes with the binary32 kernels only,
+  // ROW_TAU_DELTA and ROW_EPS_DF with the double-float restart; constant false there, so that no binary64
+  // instruction of those paths is issued predicated off)
+  constexpr bool DBL = std::is_same<Real, double>::value;
+  const bool tau_of_delta = !DBL && update && (a.flags & (ROW_INCREMENT | ROW_TAU_DELTA)) != 0;
+  const bool incr = !DBL && update && (a.flags & ROW_INCREMENT) != 0 &&
                     ((a.flags & ROW_INCR_FIRST) != 0 || *(volatile const int*)&isc->iter > 0);
   DF dfs = {0.f, 0.f}, dfs_shear = {0.f, 0.f};  // m <= 2^28: in-item offsets stay below 2^31
   dfloat dd_acc(0.f, 0.f), dd_shear(0.f, 0.f);    // residual of the double-float kernels
@@ -415,37 +423,14 @@ __global__ void __launch_bounds__(256, (row_min_blocks<Real, NC>())) row_pass_ke
             e1[c] = d1;
           }
         } else {
-          double2 old;
-          if (a.flags & ROW_EPS_DF) {
-            const float4 o = *(const float4*)pe;
-            old = make_double2((double)o.x + (double)o.y, (double)o.z + (double)o.w);
-          } else {
-            old = *(const double2*)pe;
-          }
-          double n0 = (double)e0[c], n1 = (double)e1[c];
-          double d0, d1;
-          if (incr) {
-            d0 = n0;
-            d1 = n1;
-            n0 += old.x;
-            n1 += old.y;
-          } else {
-            d0 = n0 - old.x;
-            d1 = n1 - old.y;
-          }
+          // binary64: T carried the new strain; the Cauchy increment is the difference to the stored one
+          const double2 old = *(const double2*)pe;
+          const double n0 = (double)e0[c], n1 = (double)e1[c];
+          const double d0 = n0 - old.x, d1 = n1 - old.y;
           double& acc = (c >= D) ? dsum_sh : dsum;   // c is unrolled: a register, no select
           acc = fma(d0, d0, acc);
           acc = fma(d1, d1, acc);
-          if (a.flags & ROW_EPS_DF) {
-            const float2 h0 = df_of(n0), h1 = df_of(n1);
-            *(float4*)pe = make_float4(h0.x, h0.y, h1.x, h1.y);
-          } else {
-            *(double2*)pe = make_double2(n0, n1);
-          }
-          if (tau_of_delta) {
-            e0[c] = (Real)d0;
-            e1[c] = (Real)d1;
-          }
+          *(double2*)pe = make_double2(n0, n1);
         }
       }
     }

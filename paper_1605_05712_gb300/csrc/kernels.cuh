@@ -13,13 +13,15 @@ __host__ __device__ inline int64_t tile_span(int64_t n, size_t cs) { return n + 
 #define ROW_LOAD_EPS 1   // take eps^(n) from the strain buffer (first iteration / warm start)
 #define ROW_UPDATE 2     // inverse-transform T into eps^(n+1), residual, write eps
 #define ROW_GAMMA 4      // no column axes: apply Gamma0 on the row spectrum (d_M = 1, short)
-#define ROW_INCREMENT 8  // mixed precision: T carries the increment delta, eps += delta
+#define ROW_INCREMENT 8  // mixed precision (binary32 kernels only): T carries the increment delta, eps += delta
 #define ROW_INCR_FIRST 16  // with ROW_INCREMENT: T carries an increment from the first iteration on (cold
                            // start: the prologue mapped k = 0 to 0, so T holds G(E) - E)
 #define ROW_ONLY_PAUSED 32 // restart passes: only items in state ITEM_PAUSED take part
-#define ROW_TAU_DELTA 64   // with ROW_UPDATE: the polarization is taken of the increment eps^(n+1) - eps^(n)
-#define ROW_EPS_DF 128     // binary64 kernels: the strain buffer holds double-float pairs (mixed solve);
-                           // the binary32 kernels always read and write it so
+#define ROW_TAU_DELTA 64   // with ROW_UPDATE (double-float restart): the polarization is taken of the increment
+                           // eps^(n+1) - eps^(n)
+#define ROW_EPS_DF 128     // the strain buffer holds double-float pairs (mixed solve): set on the double-float
+                           // restart passes; the binary32 and pair kernels always read and write it so, the
+                           // binary64 kernels never (none of these three flags reaches them)
 #define ROW_FIELD 256      // the material is a per-point stiffness field (ItemDev::fld*), not phase tables
 #define ROW_ORTHO 512      // every phase table of the batch couples no normal and shear components and has a
                            // diagonal shear block (isotropic, cubic, axis-aligned orthotropic phases): the
