@@ -753,6 +753,23 @@ def bench_shear_sweep(args):
                       "unit": "point-iterations/s", "results": res}))
 
 
+def profile_conv(args):
+    """Plain launches of the warm-start network for ncu: --steps forward passes at n^3 with seeded
+    parameters and a seeded three-phase feature field (the convolutions run on tcgen05 for rows of 16,
+    32, 64 and 128 voxels)."""
+    import torch
+    from paper_1605_05712_gb300.warmstart import WarmStartNet
+    dev = torch.device("cuda", 0)
+    n = args.profile_conv
+    net = WarmStartNet(dev, seed=5)
+    rng = np.random.default_rng(5)
+    phase = torch.from_numpy(rng.integers(0, 3, size=n ** 3).astype(np.uint8)).to(dev)
+    net.features(phase, rng.uniform(0.0, 2.0, size=(3, 21)).astype(np.float32), n)
+    for _ in range(max(1, args.steps)):
+        net.forward(n)
+    torch.cuda.synchronize()
+
+
 def profile_case(args):
     """Plain launches of one iteration's kernels (lattice_pass_times) for ncu: precision and lattice on argv,
     --profile-loads load cases batched (the bench solves six).  3-D lattices take the coated-ellipsoid
@@ -893,6 +910,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", nargs=2, metavar=("PRECISION", "M_JSON"))
     ap.add_argument("--profile-loads", type=int, default=1, help="with --profile-case: load cases batched")
+    ap.add_argument("--profile-conv", type=int, default=0, metavar="N",
+                    help="run --steps forward passes of the warm-start network at N^3 (for ncu)")
     ap.add_argument("--profile-scheme", default="basic", choices=["basic", "cg"],
                     help="with --profile-case: cg runs a conjugate-gradient solve of --steps iterations")
     ap.add_argument("--plain-launches", action="store_true",
@@ -910,6 +929,8 @@ def main():
     PLAIN_LAUNCHES = args.plain_launches
     if args.profile_case:
         profile_case(args)
+    elif args.profile_conv:
+        profile_conv(args)
     elif args.workload == "hashin3d":
         bench_hashin(args)
     elif args.workload == "warmstart":

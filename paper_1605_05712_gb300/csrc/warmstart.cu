@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "conv_tc05.cuh"
 #include "warmstart.h"
 
 using namespace nvcuda;
@@ -448,14 +449,44 @@ int set_attrs() {
   if (done) return 0;
   cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc05::conv3_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)std::max(std::max(tc05::smem_bytes(16), tc05::smem_bytes(32)),
+                                           std::max(tc05::smem_bytes(64), tc05::smem_bytes(128))));
+  if (e == cudaSuccess)   // the whole shared memory of an SM: two blocks of 128-voxel rows (2 x 105 KB)
+    e = cudaFuncSetAttribute(tc05::conv3_tc05_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(conv3_dw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess) done = true;
   return (int)e;
 }
 
+// tcgen05 path: rows of 16, 32, 64 or 128 voxels packed into 128-voxel tiles
+bool tc05_fits(int n0, int n1, int n2) {
+  return (n2 == 16 || n2 == 32 || n2 == 64 || n2 == 128) && n1 % (128 / n2) == 0 && ((int64_t)n0 * n1 * n2) % 128 == 0;
+}
+// persistent blocks: as many as are resident at once (by shared memory: one or two per SM), at most one
+// per tile
+unsigned tc05_grid(int n0, int n1, int n2) {
+  static int sms = 0, smem_sm = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || sms <= 0)
+      sms = 1, smem_sm = 0;
+  }
+  // blocks never wait on one another, so a count above what is resident only queues blocks
+  const int per_sm = std::max(1, smem_sm / (int)(tc05::smem_bytes(n2) + 1024));
+  const int64_t tiles = (int64_t)n0 * n1 * n2 / 128;
+  return (unsigned)std::min<int64_t>(tiles, (int64_t)per_sm * sms);
+}
+
 void conv3_forward(const void* in, const void* Wf, const void* Wb, const float* bias, void* out, int n0, int n1,
                    int n2, int out_mode, cudaStream_t st) {
-  if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
+  if (tc05_fits(n0, n1, n2))
+    tc05::conv3_tc05_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::smem_bytes(n2), st>>>(
+        (const bf16*)in, (const bf16*)Wf, bias, out, n0, n1, n2, out_mode, 0, kLeak);
+  else if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
     conv3_tc_kernel<<<n0 * n1, 128, conv3_smem(n2), st>>>((const bf16*)in, (const bf16*)Wf, bias, out, n0, n1, n2,
                                                           out_mode, 0);
   else
@@ -465,7 +496,10 @@ void conv3_forward(const void* in, const void* Wf, const void* Wb, const float* 
 
 void conv3_backward_data(const void* dpre, const void* Wb, float* out, int n0, int n1, int n2, cudaStream_t st) {
   // din[u, ci] = sum_t sum_co W[t][ci][co] dpre[u - off_t, co]: B operand (k = co, n = ci) col-major is Wb
-  if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
+  if (tc05_fits(n0, n1, n2))
+    tc05::conv3_tc05_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::smem_bytes(n2), st>>>(
+        (const bf16*)dpre, (const bf16*)Wb, nullptr, out, n0, n1, n2, 1, 1, kLeak);
+  else if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
     conv3_tc_kernel<<<n0 * n1, 128, conv3_smem(n2), st>>>((const bf16*)dpre, (const bf16*)Wb, nullptr, out, n0, n1,
                                                           n2, 1, 1);
   else
