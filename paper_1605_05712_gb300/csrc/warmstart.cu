@@ -450,9 +450,11 @@ int set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tc05::conv3_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)std::max(std::max(tc05::smem_bytes(16), tc05::smem_bytes(32)),
-                                           std::max(tc05::smem_bytes(64), tc05::smem_bytes(128))));
-  if (e == cudaSuccess)   // the whole shared memory of an SM: two blocks of 128-voxel rows (2 x 105 KB)
+                             (int)std::max(std::max(tc05::smem_bytes(16), tc05::smem_bytes(32)), tc05::smem_bytes(64)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc05::conv3_tc05_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc05::ring_smem_bytes(128));
+  if (e == cudaSuccess)   // the whole shared memory of an SM: two blocks of 86-105 KB
     e = cudaFuncSetAttribute(tc05::conv3_tc05_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
@@ -461,12 +463,13 @@ int set_attrs() {
   return (int)e;
 }
 
-// tcgen05 path: rows of 16, 32, 64 or 128 voxels packed into 128-voxel tiles
-bool tc05_fits(int n0, int n1, int n2) {
-  return (n2 == 16 || n2 == 32 || n2 == 64 || n2 == 128) && n1 % (128 / n2) == 0 && ((int64_t)n0 * n1 * n2) % 128 == 0;
+// tcgen05 paths: rows of 128 voxels with the sliding window, rows of 16, 32 or 64 packed into 128-voxel tiles
+bool tc05_fits(int n0, int n1, int n2) {   // the tile kernel
+  return (n2 == 16 || n2 == 32 || n2 == 64) && n1 % (128 / n2) == 0 && ((int64_t)n0 * n1 * n2) % 128 == 0;
 }
 // persistent blocks: as many as are resident at once (by shared memory: one or two per SM), at most one
 // per tile
+bool tc05_ring(int n1, int n2) { return n2 == 128 && n1 % std::min(n1, tc05::kRingRows) == 0; }   // the ring kernel
 unsigned tc05_grid(int n0, int n1, int n2) {
   static int sms = 0, smem_sm = 0;
   if (sms == 0) {
@@ -476,6 +479,11 @@ unsigned tc05_grid(int n0, int n1, int n2) {
       sms = 1, smem_sm = 0;
   }
   // blocks never wait on one another, so a count above what is resident only queues blocks
+  if (tc05_ring(n1, n2)) {   // work items of kRingRows rows
+    const int per_sm = std::max(1, smem_sm / (int)(tc05::ring_smem_bytes(n2) + 1024));
+    const int64_t items = (int64_t)n0 * (n1 / std::min(n1, tc05::kRingRows));
+    return (unsigned)std::min<int64_t>(items, (int64_t)per_sm * sms);
+  }
   const int per_sm = std::max(1, smem_sm / (int)(tc05::smem_bytes(n2) + 1024));
   const int64_t tiles = (int64_t)n0 * n1 * n2 / 128;
   return (unsigned)std::min<int64_t>(tiles, (int64_t)per_sm * sms);
@@ -483,7 +491,10 @@ unsigned tc05_grid(int n0, int n1, int n2) {
 
 void conv3_forward(const void* in, const void* Wf, const void* Wb, const float* bias, void* out, int n0, int n1,
                    int n2, int out_mode, cudaStream_t st) {
-  if (tc05_fits(n0, n1, n2))
+  if (tc05_ring(n1, n2))
+    tc05::conv3_tc05_ring_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::ring_smem_bytes(n2), st>>>(
+        (const bf16*)in, (const bf16*)Wf, bias, out, n0, n1, n2, out_mode, 0, kLeak);
+  else if (tc05_fits(n0, n1, n2))
     tc05::conv3_tc05_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::smem_bytes(n2), st>>>(
         (const bf16*)in, (const bf16*)Wf, bias, out, n0, n1, n2, out_mode, 0, kLeak);
   else if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
@@ -496,7 +507,10 @@ void conv3_forward(const void* in, const void* Wf, const void* Wb, const float* 
 
 void conv3_backward_data(const void* dpre, const void* Wb, float* out, int n0, int n1, int n2, cudaStream_t st) {
   // din[u, ci] = sum_t sum_co W[t][ci][co] dpre[u - off_t, co]: B operand (k = co, n = ci) col-major is Wb
-  if (tc05_fits(n0, n1, n2))
+  if (tc05_ring(n1, n2))
+    tc05::conv3_tc05_ring_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::ring_smem_bytes(n2), st>>>(
+        (const bf16*)dpre, (const bf16*)Wb, nullptr, out, n0, n1, n2, 1, 1, kLeak);
+  else if (tc05_fits(n0, n1, n2))
     tc05::conv3_tc05_kernel<<<tc05_grid(n0, n1, n2), 128, tc05::smem_bytes(n2), st>>>(
         (const bf16*)dpre, (const bf16*)Wb, nullptr, out, n0, n1, n2, 1, 1, kLeak);
   else if (n2 >= 16 && n2 % 16 == 0 && n2 <= 128)
