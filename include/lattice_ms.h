@@ -433,6 +433,11 @@ int basic_scheme_solve_noalloc(const lat_plan* plan, const uint8_t* phase, int n
  * (c0 c1 c2 c3 d2 d1 d0) W[27][32][32] (taps (dz,dy,dx) lexicographic, ci, co)
  * then b[32]; then the 1x1 head H[32][36] and hb[36].
  * Feature table: per phase 21 floats, the upper triangle of its Voigt matrix / mu0.
+ * Errors: LAT_ERR_SIZE / LAT_ERR_ARG for bad sizes or pointers, LAT_ERR_CUDA for
+ * a failed launch or copy.  The tensor-core convolutions bound their waits on
+ * their own products; one that ran out writes NaN outputs and raises a device
+ * flag, which the calls that synchronize (get_params, get_activation,
+ * train_step with loss_out) report as LAT_ERR_CUDA and clear.
  */
 size_t lat_wsnet_param_bytes(void);
 int64_t lat_wsnet_num_params(void);

@@ -684,6 +684,21 @@ extern "C" size_t lat_wsnet_work_bytes(int n) {
   return layout_acts(nullptr, n).total;
 }
 
+// a tcgen05 convolution whose mbarrier wait ran out wrote NaN outputs and set tc05::g_timeout: reported
+// (and cleared) by the entry points that synchronize
+static int tc05_check() {
+  int f = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&f, tc05::g_timeout, sizeof(int));
+  if (e != cudaSuccess) return lat_fail(LAT_ERR_CUDA, std::string("warm start: ") + cudaGetErrorString(e));
+  if (f) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(tc05::g_timeout, &zero, sizeof(int));
+    return lat_fail(LAT_ERR_CUDA, "warm start: a tensor-core convolution timed out waiting for its products "
+                                  "(its outputs are NaN)");
+  }
+  return LAT_OK;
+}
+
 extern "C" int lat_wsnet_set_params(void* params, const float* host_params, void* stream) {
   if (!params || !host_params) return lat_fail(LAT_ERR_ARG, "lat_wsnet_set_params: NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -702,7 +717,7 @@ extern "C" int lat_wsnet_get_params(const void* params, float* host_params, floa
   if (host_params) CKW(cudaMemcpyAsync(host_params, P.p, kNParams * sizeof(float), cudaMemcpyDeviceToHost, st));
   if (host_grads) CKW(cudaMemcpyAsync(host_grads, P.g, kNParams * sizeof(float), cudaMemcpyDeviceToHost, st));
   CKW(cudaStreamSynchronize(st));
-  return LAT_OK;
+  return tc05_check();
 }
 
 static int prepare(void* work, size_t work_bytes, int n, Acts& a) {
@@ -781,6 +796,7 @@ extern "C" int lat_wsnet_train_step(void* params, const uint8_t* phase, const fl
   if (loss_out) {
     CKW(cudaMemcpyAsync(loss_out, a.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     CKW(cudaStreamSynchronize(st));
+    return tc05_check();
   }
   return LAT_OK;
 }
@@ -807,6 +823,7 @@ extern "C" int lat_wsnet_get_activation(const void* work, size_t work_bytes, int
   cudaStream_t st = (cudaStream_t)stream;
   CKW(cudaMemcpyAsync(tmp.data(), src, cnt * 2, cudaMemcpyDeviceToHost, st));
   CKW(cudaStreamSynchronize(st));
+  if (int rc = tc05_check()) return rc;
   for (int64_t i = 0; i < cnt; ++i) {
     const uint32_t b = (uint32_t)tmp[i] << 16;
     float f;
