@@ -102,12 +102,15 @@ typedef struct lat_plan lat_plan;
  * natural order, with the full complex spectrum.  Those "general" plans run
  * Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 and LAT_DF64 (LAT_MIXED
  * and LAT_SCHEME_CG return LAT_ERR_UNSUPPORTED there) and take strain buffers
- * aligned to 8 bytes.
+ * aligned to 8 bytes.  A largest divisor longer than one mixed-radix pass
+ * (2048 points in 2-D, 1024 in 3-D) is split four-step into two passes; when
+ * no such split exists (a large prime factor) its rows are transformed by
+ * Bluestein's chirp-z convolution (lattice_plan_layout reports split = 2):
+ * LAT_FP64 only, and lattice_fft then needs lattice_fft_workspace_bytes.
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
- * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a divisor that needs
- * more than one four-step split, or a general plan's divisor other than the
- * largest that is longer than one mixed-radix pass: 2048 points in 2-D, 1024
- * in 3-D), LAT_ERR_CUDA.
+ * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a general plan's
+ * divisor other than the largest that is longer than one mixed-radix pass,
+ * or a chirp-z row longer than 2^22 points), LAT_ERR_CUDA.
  */
 int lattice_plan(const int64_t* M, int d, lat_plan** out);
 
@@ -536,7 +539,10 @@ int lattice_pass_times(const lat_plan* plan, const uint8_t* phase, int n_phases,
  *   ngroups    column passes per transform direction: group g covers the
  *              logical axes [grp[2g], grp[2g+1]) (host, >= 6 ints); group 0
  *              also applies the Green operator.
- *   split      1 if the largest divisor is split four-step.
+ *   split      1 if the largest divisor is split four-step; 2 if the row (the
+ *              largest divisor, not split) is transformed by Bluestein's
+ *              chirp-z convolution (general plans whose largest divisor has no
+ *              split into two lines of at most 2048 points in 2-D, 1024 in 3-D).
  * Any output pointer may be NULL.
  */
 int lattice_plan_layout(const lat_plan* plan, int* nax, int* ax_len, int* ngroups, int* grp, int* split);

@@ -214,8 +214,14 @@ def lattice_fft(plan, x, inverse=False, stream=None):
     x = x.contiguous()
     n_f = x.numel() // plan.m
     out = torch.empty_like(x)
-    _check(lib().lattice_fft(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n_f,
-                             1 if inverse else 0, None, 0, _stream(stream)))
+    L = lib()
+    L.lattice_fft_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.lattice_fft_workspace_bytes.restype = ctypes.c_size_t
+    nb = int(L.lattice_fft_workspace_bytes(plan.handle, n_f))
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=x.device) if nb else None
+    _check(L.lattice_fft(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n_f,
+                         1 if inverse else 0, ctypes.c_void_p(ws.data_ptr()) if ws is not None else None, nb,
+                         _stream(stream)))
     return out
 
 

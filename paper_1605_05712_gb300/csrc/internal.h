@@ -71,6 +71,17 @@ struct lat_plan {
   int ax_nrad[LAT_MAX_AX];
   uint16_t ax_rad[LAT_MAX_AX][LAT_MAX_RADIX];
   int ax_twoff[LAT_MAX_AX];
+  // general plans whose largest divisor p is longer than one line in shared memory and has no split
+  // into two lines that fit: the row axis (length p, not split) is transformed by Bluestein's chirp-z
+  // convolution, a cyclic convolution of power-of-two length blue_L >= 2p - 1 run by blue_sub (the
+  // power-of-two plan diag(1, blue_L)); d_chirp[n] = exp(-i pi n^2 / p) (n < p) and d_bh the
+  // unnormalized DFT of the wrapped conjugate chirp, in blue_sub's spectral order
+  int blue;
+  int64_t blue_L;
+  lat_plan* blue_sub;
+  int blue_lgA, blue_lgB;  // blue_sub's storage order: sample n at slot (n mod A) B + n / A, A B = blue_L
+  double2* d_chirp;
+  double2* d_bh;
   // launch shapes picked by lattice_autotune, per precision and power-of-two bucket of the item count
   struct Tune {
     int valid;
@@ -103,6 +114,13 @@ struct LatDev {
   int ax_nrad[LAT_MAX_AX];
   uint16_t ax_rad[LAT_MAX_AX][LAT_MAX_RADIX];
   int ax_twoff[LAT_MAX_AX];
+  // Bluestein row axis (see lat_plan): its tables, and the plan itself for the host-side launchers
+  int blue;
+  int64_t blue_L;
+  int blue_lgA, blue_lgB;     // the sub-plan stores sample n at slot (n mod A) B + n / A (L = A B)
+  const double2* blue_chirp;
+  const double2* blue_bh;
+  const void* blue_plan;      // host pointer (const lat_plan*), never read on the device
   // transformed pattern P_L(M) (Sec. 3.3): Gamma0 at L^{-T} h; binary64, binary32 and pair copies
   int cell;
   double cellT[3][3];

@@ -917,8 +917,8 @@ __global__ void __launch_bounds__(256) row_complex_kernel(LatDev dv, const void*
   C* buf = (C*)smem_raw;
   const int R = dv.Rlen, lgR = dv.log2Rh + 1, nlines = n_f * rpc;
   const int64_t m = dv.m, r0 = (int64_t)blockIdx.x * rpc;
-  const C* src = (const C*)in;
-  C* dst = (C*)out;
+  const C* src = (const C*)in + (int64_t)blockIdx.y * n_f * m;   // grid.y: groups of n_f fields
+  C* dst = (C*)out + (int64_t)blockIdx.y * n_f * m;
   for (int idx = threadIdx.x; idx < nlines * R; idx += blockDim.x) {
     const int line = idx / R, pos = idx - line * R;
     const int f = line / rpc, row = line - f * rpc;
@@ -1033,9 +1033,10 @@ void launch_col_pass(const LatDev& dv, const ColArgs& a, int n_items, int nthrea
 }
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale, int rpc,
-                        int nthreads, size_t smem, cudaStream_t st) {
+                        int nthreads, size_t smem, cudaStream_t st, int n_groups) {
   const int64_t nb = dv.nrows / rpc;
-  row_complex_kernel<Real><<<(unsigned)nb, nthreads, smem, st>>>(dv, in, out, n_f, inverse, scale, rpc);
+  row_complex_kernel<Real><<<dim3((unsigned)nb, (unsigned)n_groups), nthreads, smem, st>>>(dv, in, out, n_f, inverse,
+                                                                                          scale, rpc);
 }
 // in place: binary64 strain <-> double-float pairs (to_df = 1: before a mixed solve's prologue)
 __global__ void eps_df_kernel(const ItemDev* items, int n_c, int64_t m, int to_df) {
@@ -1177,7 +1178,7 @@ template void launch_col_pass<double>(const LatDev&, const ColArgs&, int, int, s
 template void launch_col_pass<float>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_col_pass<dfloat>(const LatDev&, const ColArgs&, int, int, size_t, cudaStream_t);
 template void launch_row_complex<double>(const LatDev&, const void*, void*, int, int, double, int, int, size_t,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 
 template <typename K>
 static cudaError_t set_smem(K kernel, int optin) {

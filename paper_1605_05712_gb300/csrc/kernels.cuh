@@ -191,9 +191,10 @@ void launch_scalars_out(const ItemScal* scal, int n_items, int n_c, double tol, 
 void launch_eff(const LatDev& dv, const EffArgs& a, int nblocks, int n_items, cudaStream_t st);
 // binary32 and pair copies of a 21 x m binary64 stiffness field (either destination may be NULL)
 void launch_field_copies(const double* fld, float* fld_f, dfloat* fld_df, int64_t n, cudaStream_t st);
+// n_groups (grid.y) groups of n_f fields, m apart
 template <typename Real>
 void launch_row_complex(const LatDev& dv, const void* in, void* out, int n_f, int inverse, double scale,
-                        int rpc, int nthreads, size_t smem, cudaStream_t st);
+                        int rpc, int nthreads, size_t smem, cudaStream_t st, int n_groups = 1);
 int lat_kernel_attrs(size_t max_smem);
 // mixed-radix kernels of general plans (kernels_gen.cu): binary64 and double-float pairs; the binary32
 // instantiations launch nothing (binary32 solves are refused on general plans)
@@ -205,6 +206,21 @@ void launch_gen_col(const LatDev& dv, const ColArgs& a, int n_items, int nthread
 void launch_gen_row_complex(const LatDev& dv, const void* in, void* out, int inverse, double scale, int rpc,
                             int nthreads, size_t smem, cudaStream_t st);
 int lat_gen_kernel_attrs(int optin);
+// chirp-z rows (kernels_gen.cu, binary64): line l0 + y (y < nl) of the batch is line j = l % lines_per_item
+// of item i = l / lines_per_item, p complex values at base + i stride + j p; Y holds nl lines of L in the
+// sub-plan's storage order, sample n at slot(n) = (n mod A) B + n / A (A = 2^lgA, B = 2^lgB).
+// pre: sample n of Y = x_n w_n (n < p; conjugated input for the inverse), 0 up to L; mul: Y[y][k] *= bh[k]
+// scale; post: out_k = w_k (sample k of Y) (conjugated for the inverse) times scale, k < p
+void launch_blue_pre(const double2* src, int64_t src_stride, int lines_per_item, int64_t p, int64_t L, int lgA,
+                     int lgB, const double2* chirp, double2* Y, int inverse, int64_t l0, int nl, cudaStream_t st);
+void launch_blue_mul(double2* Y, const double2* bh, int64_t L, int nl, double scale, cudaStream_t st);
+void launch_blue_post(const double2* Y, double2* dst, int64_t dst_stride, int lines_per_item, int64_t p, int64_t L,
+                      int lgA, int lgB, const double2* chirp, int inverse, double scale, int64_t l0, int nl,
+                      cudaStream_t st);
+// the pointwise step of a chirp-z plan's row pass (update, residual, polarization; grid nblocks x items)
+// and its Green operator when the row is the only logical axis
+void launch_blue_point(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, cudaStream_t st);
+void launch_blue_green(const LatDev& dv, const RowArgs& a, int n_items, cudaStream_t st);
 // in place: binary64 strain -> double-float pairs (to_df = 1) or back (0), all items
 void launch_eps_df(const ItemDev* items, int n_items, int n_c, int64_t m, int to_df, cudaStream_t st);
 // restart of the increment form: glob->active = number of paused items, arrivals = 0

@@ -14,6 +14,8 @@
 // Binary64 and double-float pairs only (the binary32 increment form needs the power-of-two kernels).
 #include <math.h>
 
+#include <algorithm>
+
 #include "fft_mixed.cuh"
 #include "kernels_dev.cuh"
 
@@ -285,6 +287,177 @@ __global__ void __launch_bounds__(256) gen_row_complex_kernel(LatDev dv, const d
     if (scale != 1.0) v = cscale(v, scale);
     out[off + idx] = v;
   }
+}
+
+// ------------------------------------------------------------------ chirp-z rows (Bluestein)
+// A largest divisor p with no split into two lines that fit in shared memory is transformed as
+// X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_n = exp(-i pi n^2 / p): the sum is a cyclic convolution of
+// power-of-two length L >= 2p - 1, taken by the transforms of the plan diag(1, L) between pre and post.
+// Y is in the storage order of the power-of-two sub-plan: slot s = n1 B + n2 holds sample n = n1 + A n2
+__global__ void __launch_bounds__(256) blue_pre_kernel(const double2* __restrict__ src, int64_t src_stride,
+                                                       int lines_per_item, int64_t p, int64_t L, int lgA, int lgB,
+                                                       const double2* __restrict__ chirp, double2* __restrict__ Y,
+                                                       int inverse, int64_t l0) {
+  const int64_t l = l0 + blockIdx.y;
+  const int64_t i = l / lines_per_item, j = l - i * lines_per_item;
+  const double2* x = src + i * src_stride + j * p;
+  double2* y = Y + (int64_t)blockIdx.y * L;
+  const int64_t Bm = (int64_t(1) << lgB) - 1;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < L; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = (s >> lgB) + ((s & Bm) << lgA);
+    double2 v = make_double2(0.0, 0.0);
+    if (n < p) {
+      v = x[n];
+      if (inverse) v.y = -v.y;   // inverse DFT = conj(DFT(conj x))
+      v = cmul(v, __ldg(chirp + n));
+    }
+    y[s] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) blue_mul_kernel(double2* __restrict__ Y, const double2* __restrict__ bh,
+                                                       int64_t L, double scale) {
+  double2* y = Y + (int64_t)blockIdx.y * L;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = cscale(cmul(y[k], __ldg(bh + k)), scale);
+}
+
+__global__ void __launch_bounds__(256) blue_post_kernel(const double2* __restrict__ Y, double2* __restrict__ dst,
+                                                        int64_t dst_stride, int lines_per_item, int64_t p, int64_t L,
+                                                        int lgA, int lgB, const double2* __restrict__ chirp,
+                                                        int inverse, double scale, int64_t l0) {
+  const int64_t l = l0 + blockIdx.y;
+  const int64_t i = l / lines_per_item, j = l - i * lines_per_item;
+  double2* out = dst + i * dst_stride + j * p;
+  const double2* y = Y + (int64_t)blockIdx.y * L;
+  const int64_t Am = (int64_t(1) << lgA) - 1;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = cmul(y[((k & Am) << lgB) + (k >> lgA)], __ldg(chirp + k));
+    if (inverse) v.y = -v.y;
+    out[k] = cscale(v, scale);
+  }
+}
+
+// the pointwise step of Algorithm 1 on a chirp-z plan (the row pass of gen_row_kernel without its row
+// transforms, which run as the launches above): eps^(n+1) = Re of the inverse transform held in T, the
+// Cauchy residual against eps^(n), tau = (C_y - C0) : eps^(n+1) back into T as a real signal
+template <int NC>
+__global__ void __launch_bounds__(256) blue_point_kernel(LatDev dv, RowArgs a) {
+  constexpr int n_c = NC, D = (NC == 6) ? 3 : 2;
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
+  const bool update = (a.flags & ROW_UPDATE) != 0;
+  if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) return;   // finished earlier
+  __shared__ double red[32];
+  __shared__ int s_last;
+  const int64_t m = dv.m;
+  double2* T = (double2*)a.T + item_i * a.t_stride;
+  double* eps = item->eps;
+  const uint8_t* phase = item->phase;
+  const bool load = (a.flags & ROW_LOAD_EPS) != 0, field = (a.flags & ROW_FIELD) != 0;
+  double dsum = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < m; g += (int64_t)gridDim.x * blockDim.x) {
+    double e[NC];
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) e[c] = load ? eps[c * m + g] : T[c * m + g].x;
+    const int ph = field ? 0 : phase[g];
+    if (!field && update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
+      // the transform returned u = (C + C0) eps: eps = (C_p + C0)^{-1} u
+      const double* W = item->Wtab + ph * n_c * n_c;
+      double u[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) u[c] = e[c];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < n_c; ++q) t += ldg_r(W + c * n_c + q) * u[q];
+        e[c] = t;
+      }
+    }
+    if (update) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        double* pe = eps + (c * m + g);
+        const double d = e[c] - *pe;
+        dsum += (c >= D ? 2.0 : 1.0) * (d * d);
+        *pe = e[c];
+      }
+    }
+    double t[NC];
+    if (field) {   // per-point stiffness field: tau = C_y : eps - C0 : eps
+      const GreenK<double> gk = green_consts<double>(item, a.mat);
+      field_polarize<double, NC>(item->fld, m, g, gk.lam0, gk.mu0 + gk.mu0, e, t);
+    } else {
+      const double* Dt = item->Dtab + ph * n_c * n_c;
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < n_c; ++q) s += ldg_r(Dt + c * n_c + q) * e[q];
+        t[c] = s;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) T[c * m + g] = make_double2(t[c], 0.0);
+  }
+  if (!update) return;
+  double* partials = a.it.partials + item_i * a.it.pstride;
+  double tot;
+  if (!item_reduce<1>(&dsum, partials, isc, red, &s_last, &tot)) return;
+  if (threadIdx.x == 0) item_report(sqrt(tot) / item->norm0, isc, item_i, a.it);
+}
+
+// the Green operator on the spectrum of a chirp-z plan whose row is its only logical axis (d_M = 1)
+template <int NC>
+__global__ void __launch_bounds__(256) blue_green_kernel(LatDev dv, RowArgs a) {
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  if (a.flags & ROW_UPDATE) {   // items that stopped in this iteration or earlier keep their spectrum
+    const ItemScal* isc = (const ItemScal*)((const char*)a.it.scal + (size_t)item_i * 256);
+    if (*(volatile const int*)&isc->done != ITEM_ACTIVE) return;
+  }
+  const GreenK<double> gk = green_consts<double>(item, a.mat);
+  const int64_t m = dv.m;
+  double2* T = (double2*)a.T + item_i * a.t_stride;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 val[NC];
+#pragma unroll
+    for (int f = 0; f < NC; ++f) val[f] = T[f * m + k];
+    int kk[LAT_MAX_AX] = {0};
+    kk[0] = (int)k;
+    green_at<double, NC>(dv, a.mat, item, gk, kk, val);
+#pragma unroll
+    for (int f = 0; f < NC; ++f) T[f * m + k] = val[f];
+  }
+}
+
+static unsigned blue_grid_x(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 1024)); }
+
+void launch_blue_pre(const double2* src, int64_t src_stride, int lines_per_item, int64_t p, int64_t L, int lgA,
+                     int lgB, const double2* chirp, double2* Y, int inverse, int64_t l0, int nl, cudaStream_t st) {
+  blue_pre_kernel<<<dim3(blue_grid_x(L), nl), 256, 0, st>>>(src, src_stride, lines_per_item, p, L, lgA, lgB, chirp, Y,
+                                                            inverse, l0);
+}
+void launch_blue_mul(double2* Y, const double2* bh, int64_t L, int nl, double scale, cudaStream_t st) {
+  blue_mul_kernel<<<dim3(blue_grid_x(L), nl), 256, 0, st>>>(Y, bh, L, scale);
+}
+void launch_blue_post(const double2* Y, double2* dst, int64_t dst_stride, int lines_per_item, int64_t p, int64_t L,
+                      int lgA, int lgB, const double2* chirp, int inverse, double scale, int64_t l0, int nl,
+                      cudaStream_t st) {
+  blue_post_kernel<<<dim3(blue_grid_x(p), nl), 256, 0, st>>>(Y, dst, dst_stride, lines_per_item, p, L, lgA, lgB, chirp,
+                                                             inverse, scale, l0);
+}
+void launch_blue_point(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, cudaStream_t st) {
+  const dim3 grid(nblocks, n_items);
+  if (dv.n_c == 6) blue_point_kernel<6><<<grid, 256, 0, st>>>(dv, a);
+  else blue_point_kernel<3><<<grid, 256, 0, st>>>(dv, a);
+}
+void launch_blue_green(const LatDev& dv, const RowArgs& a, int n_items, cudaStream_t st) {
+  const dim3 grid(blue_grid_x(dv.m), n_items);
+  if (dv.n_c == 6) blue_green_kernel<6><<<grid, 256, 0, st>>>(dv, a);
+  else blue_green_kernel<3><<<grid, 256, 0, st>>>(dv, a);
 }
 
 // ------------------------------------------------------------------ launchers

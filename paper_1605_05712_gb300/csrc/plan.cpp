@@ -208,7 +208,8 @@ static void set_cv(lat_plan* P) {
 // Layout of a general plan (some divisor is not a power of two): every divisor axis is one logical axis
 // transformed in one pass; the last one (the contiguous row) is split four-step as A B when longer than
 // a line may be.  A line of every logical axis, all n_c planes, twice (ping-pong), must fit in shared
-// memory: 2 x n_c x L x 16 B <= 196 KB.
+// memory: 2 x n_c x L x 16 B <= 196 KB.  A largest divisor with no such split (a large prime, or a
+// large prime times a small factor) stays one row transformed by Bluestein's chirp-z convolution.
 static int choose_layout_general(lat_plan* P, const std::vector<int>& paxes) {
   const int d = P->d, n_c = d * (d + 1) / 2;
   const int64_t LMAX = (n_c == 3) ? 2048 : 1024;
@@ -229,9 +230,7 @@ static int choose_layout_general(lat_plan* P, const std::vector<int>& paxes) {
         const double dist = fabs(log((double)b) - 0.5 * log((double)eL));
         if (dist < best) best = dist, B = b;
       }
-    if (B < 0)
-      return lat_fail(LAT_ERR_UNSUPPORTED, "elementary divisor " + std::to_string((long long)eL) +
-                                               " needs more than one four-step split");
+    if (B < 0) B = eL, P->blue = 1;   // no split into two lines that fit: Bluestein on the whole row
   }
   int na = 0;
   for (size_t i = 0; i + 1 < paxes.size(); ++i) {
@@ -260,10 +259,23 @@ static int choose_layout_general(lat_plan* P, const std::vector<int>& paxes) {
   int off = 0;
   for (int i = 0; i < na; ++i) {
     P->ax[i].log2len = ilog2(P->ax[i].len);
-    P->ax_nrad[i] = factor_radices(P->ax[i].len, P->ax_rad[i]);
+    const bool row = i == na - 1;
+    P->ax_nrad[i] = (row && P->blue) ? 0 : factor_radices(P->ax[i].len, P->ax_rad[i]);
+    if (P->ax_nrad[i] < 0 && row && !P->split) P->blue = 1, P->ax_nrad[i] = 0;   // more stages than a pass holds
     if (P->ax_nrad[i] < 0) return lat_fail(LAT_ERR_UNSUPPORTED, "axis length with too many prime factors");
     P->ax_twoff[i] = off;
-    off += P->ax[i].len;
+    if (!(row && P->blue)) off += P->ax[i].len;   // the Bluestein row has no table of W_p^t
+  }
+  if (P->blue) {
+    // Bluestein (chirp-z): X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_n = exp(-i pi n^2 / p), a cyclic
+    // convolution of length L >= 2p - 1 (power of two), transformed by the power-of-two plan diag(1, L)
+    int64_t L = 1;
+    while (L < 2 * eL - 1) L <<= 1;
+    if (L > (int64_t(1) << 23))
+      return lat_fail(LAT_ERR_UNSUPPORTED, "elementary divisor " + std::to_string((long long)eL) +
+                                               " has no split into two lines of at most " + std::to_string((long long)LMAX) +
+                                               " points and is longer than a chirp-z transform of 2^23 points allows");
+    P->blue_L = L;
   }
   P->Rlen = (int)B;
   P->Rh = (int)(B / 2);
@@ -493,6 +505,39 @@ static int lat_upload_tables(lat_plan* P) {
   return LAT_OK;
 }
 
+// Bluestein row (general plans, see lat_plan): the power-of-two plan diag(1, L), the chirp
+// w_n = exp(-i pi n^2 / p) (n^2 reduced mod 2p exactly) and the unnormalized DFT of the wrapped
+// conjugate chirp b (b_j = conj(w_|j|) at j mod L for |j| < p, 0 elsewhere), transformed on the device
+// by the sub-plan's own forward passes so that its spectral order is the one the solver multiplies in
+static int lat_blue_tables(lat_plan* P) {
+  const int64_t p = P->Rlen, L = P->blue_L;
+  const int64_t Msub[4] = {1, 0, 0, L};
+  if (int rc = lattice_plan(Msub, 2, &P->blue_sub)) return rc;
+  const lat_plan* S = P->blue_sub;
+  if (S->general || S->device != P->device || S->nax != (S->split ? 2 : 1))
+    return lat_fail(LAT_ERR_CUDA, "chirp-z sub-plan: unexpected layout or device");
+  // the sub-plan's storage order (lattice_points): a split row holds sample n = n1 + A n2 at n1 B + n2
+  const int64_t A = S->split ? S->ax[S->split_n1].len : 1;
+  P->blue_lgA = ilog2(A);
+  P->blue_lgB = ilog2(L / A);
+  auto slot = [&](int64_t n) { return ((n & (A - 1)) << P->blue_lgB) + (n >> P->blue_lgA); };
+  std::vector<double2> w(p), b(L, make_double2(0.0, 0.0));
+  for (int64_t n = 0; n < p; ++n) {
+    double re, im;
+    twiddle((int64_t)((i128)n * n % (2 * p)), 2 * p, &re, &im);
+    w[n] = make_double2(re, im);
+    b[slot(n)] = make_double2(re, -im);
+    if (n > 0) b[slot(L - n)] = make_double2(re, -im);
+  }
+  cudaError_t err;
+  if ((err = cudaMalloc((void**)&P->d_chirp, p * sizeof(double2))) != cudaSuccess ||
+      (err = cudaMemcpy(P->d_chirp, w.data(), p * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMalloc((void**)&P->d_bh, L * sizeof(double2))) != cudaSuccess ||
+      (err = cudaMemcpy(P->d_bh, b.data(), L * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return lat_fail(LAT_ERR_CUDA, std::string("chirp-z table upload: ") + cudaGetErrorString(err));
+  return lat_blue_transform_bh(P);
+}
+
 int lat_plan_device_check(const lat_plan* P) {
   if (P->nax == 0) return LAT_OK;   // m = 1: no transform, no tables
   if (P->device < 0)
@@ -560,7 +605,8 @@ extern "C" int lattice_plan(const int64_t* Min, int d, lat_plan** out) {
     if (cudaGetDevice(&P->device) != cudaSuccess) P->device = -1;
   }
   cudaGetLastError();   // a machine without a device leaves a (non-sticky) error behind
-  if (P->device >= 0 && (rc = lat_upload_tables(P)) != LAT_OK) {
+  if (P->device >= 0 && (rc = lat_upload_tables(P)) == LAT_OK && P->blue) rc = lat_blue_tables(P);
+  if (P->device >= 0 && rc != LAT_OK) {
     lattice_plan_destroy(P);
     return rc;
   }
@@ -576,7 +622,7 @@ int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t*
   int64_t N = int64_t(1) << lg;
   if (P->general) {
     N = 0;
-    for (int i = 0; i < P->nax; ++i) N += P->ax[i].len;
+    for (int i = 0; i < P->nax; ++i) N += (P->blue && i == P->nax - 1) ? 0 : P->ax[i].len;
   }
   int64_t lo_n = 0, hi_n = 0;
   if (P->split) {
@@ -605,7 +651,7 @@ int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t*
     }
   if (tw && P->general)
     for (int i = 0; i < P->nax; ++i)
-      for (int64_t t = 0; t < P->ax[i].len; ++t) {
+      for (int64_t t = 0; t < ((P->blue && i == P->nax - 1) ? 0 : P->ax[i].len); ++t) {
         double re, im;
         twiddle(t, P->ax[i].len, &re, &im);
         put(tw, P->ax_twoff[i] + t, re, im);
@@ -635,6 +681,9 @@ extern "C" void lattice_plan_destroy(lat_plan* P) {
   if (P->d_stwdf) cudaFree(P->d_stwdf);
   if (P->d_lf) cudaFree(P->d_lf);
   if (P->d_rc) cudaFree(P->d_rc);
+  if (P->d_chirp) cudaFree(P->d_chirp);
+  if (P->d_bh) cudaFree(P->d_bh);
+  if (P->blue_sub) lattice_plan_destroy(P->blue_sub);
   delete P;
 }
 
@@ -679,7 +728,7 @@ extern "C" int lattice_plan_layout(const lat_plan* P, int* nax, int* ax_len, int
       grp[2 * g] = g < P->ngroups ? P->grp[g].a0 : 0;
       grp[2 * g + 1] = g < P->ngroups ? P->grp[g].a1 : 0;
     }
-  if (split) *split = P->split;
+  if (split) *split = P->blue ? 2 : P->split;
   return LAT_OK;
 }
 

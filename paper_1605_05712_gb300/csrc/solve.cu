@@ -76,6 +76,13 @@ LatDev make_dev(const lat_plan* P, int kind) {
     dv.ax_twoff[a] = P->ax_twoff[a];
     for (int r = 0; r < LAT_MAX_RADIX; ++r) dv.ax_rad[a][r] = P->ax_rad[a][r];
   }
+  dv.blue = P->blue;
+  dv.blue_L = P->blue_L;
+  dv.blue_lgA = P->blue_lgA;
+  dv.blue_lgB = P->blue_lgB;
+  dv.blue_chirp = P->d_chirp;
+  dv.blue_bh = P->d_bh;
+  dv.blue_plan = P;
   dv.split = P->split;
   dv.split_n1 = P->split_n1;
   dv.split_lo_log2 = P->split_lo_log2;
@@ -145,13 +152,19 @@ static int geometry_general(const lat_plan* P, int n_f, size_t cs, Geometry& g, 
   const int nsm = num_sms();
   const int64_t nrows = P->nrows, R = P->Rlen;
   auto row_smem = [&](int rpc) { return 2 * (size_t)n_f * rpc * R * cs + 32 * sizeof(double); };
-  if (row_smem(1) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
-  int rpc = 1;
-  while (nrows % (2 * rpc) == 0 && row_smem(2 * rpc) <= kRowSmemTarget && n_items * (nrows / (2 * rpc)) >= 2 * nsm)
-    rpc *= 2;
-  g.rpc = rpc;
-  g.row_blocks = (int)(nrows / rpc);
-  g.row_smem = row_smem(rpc);
+  if (P->blue) {   // chirp-z rows: the pointwise step runs on its own, grid-stride over the points
+    g.rpc = 1;
+    g.row_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P->m + 1023) / 1024, 1024));
+    g.row_smem = 0;
+  } else {
+    if (row_smem(1) > kMaxSmem) return lat_fail(LAT_ERR_UNSUPPORTED, "row does not fit in shared memory");
+    int rpc = 1;
+    while (nrows % (2 * rpc) == 0 && row_smem(2 * rpc) <= kRowSmemTarget && n_items * (nrows / (2 * rpc)) >= 2 * nsm)
+      rpc *= 2;
+    g.rpc = rpc;
+    g.row_blocks = (int)(nrows / rpc);
+    g.row_smem = row_smem(rpc);
+  }
   for (int k = 0; k < P->ngroups; ++k) {
     const LatGroup& G = P->grp[k];
     const int64_t ic = G.inner * R;
@@ -203,7 +216,8 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   Work w;
   // half spectrum + Nyquist plane (power-of-two plans), or the full complex spectrum (general plans)
   w.t_per_lc = P->general ? (size_t)n_c * P->m * cs : (size_t)n_c * (P->m / 2) * cs;
-  w.tn_per_lc = P->general ? 0 : (size_t)n_c * P->nrows * cs;
+  // general plans: no Nyquist plane; a chirp-z row takes the convolution lines there (blue_L per row)
+  w.tn_per_lc = P->general ? (P->blue ? (size_t)n_c * P->nrows * P->blue_L * 16 : 0) : (size_t)n_c * P->nrows * cs;
   // two values per row block (conjugate gradients), n_c per block of the effective stress
   w.pstride = std::max<int64_t>(2 * P->nrows, (int64_t)kEffBlocksMax * 6);
   w.table_bytes = (size_t)phases_per_table * n_c * n_c * sizeof(double);
@@ -324,9 +338,106 @@ void enqueue_col_group(const LatDev& dv, const lat_plan* P, const Geometry& g, C
   else launch_col_pass<Real>(dv, c, n_items, kThreads, g.col_smem[k], st);
 }
 
+// the length-L transforms of a chirp-z row on nl lines of Y (L apart), in place: forward (unnormalized,
+// the sub-plan's spectral order) or its inverse (unnormalized), the passes of lattice_fft on the
+// power-of-two plan S = diag(1, L) with one line per item
+static void blue_sub_fft(const lat_plan* S, const LatDev& sdv, const Geometry& geo, double2* Y, int nl, int inverse,
+                         cudaStream_t st) {
+  ColArgs base;
+  memset(&base, 0, sizeof(base));
+  base.row_slots = S->Rlen;
+  base.n_f = 1;
+  base.T = Y;
+  base.t_stride = S->m;
+  base.scale = 1.0;
+  auto col = [&](int k, int mode) {
+    ColArgs c = base;
+    const LatGroup& G = S->grp[k];
+    c.mode = mode;
+    c.gidx = k;
+    c.a0 = G.a0;
+    c.a1 = G.a1;
+    c.G = G.G;
+    c.outer = G.outer;
+    c.inner = G.inner;
+    c.has_twiddle = G.has_twiddle;
+    c.w = geo.w[k];
+    c.wN = geo.wN[k];
+    c.tiles_main = geo.tiles_main[k];
+    launch_col_pass<double>(sdv, c, nl, kThreads, geo.col_smem[k], st);
+  };
+  if (!inverse) {
+    launch_row_complex<double>(sdv, Y, Y, 1, 0, 1.0, geo.rpc, kThreads, geo.row_smem, st, nl);
+    for (int k = S->ngroups - 1; k >= 0; --k) col(k, COL_FWD);
+  } else {
+    for (int k = 0; k < S->ngroups; ++k) col(k, COL_INV);
+    launch_row_complex<double>(sdv, Y, Y, 1, 1, 1.0, geo.rpc, kThreads, geo.row_smem, st, nl);
+  }
+}
+
+// Bluestein's chirp-z form of the DFT along a row of length p (Sec. 2.2's DFT over the largest divisor):
+// X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_n = exp(-i pi n^2 / p), the sum a cyclic convolution of
+// length L >= 2p - 1 taken by the sub-plan's transforms; the inverse is conj(DFT(conj x)).  Lines j <
+// lines_per_item of item i start at src + i src_stride + j p (complex binary64) and go to dst likewise;
+// Y holds y_lines lines of L; scale multiplies the result.
+void blue_rows(const LatDev& dv, const double2* src, int64_t src_stride, double2* dst, int64_t dst_stride,
+               int lines_per_item, int n_items, double2* Y, int64_t y_lines, int inverse, double scale,
+               cudaStream_t st) {
+  const lat_plan* P = (const lat_plan*)dv.blue_plan;
+  const lat_plan* S = P->blue_sub;
+  const int64_t p = dv.Rlen, L = dv.blue_L;
+  const int64_t total = (int64_t)lines_per_item * n_items;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(total, 65535), y_lines));
+  const LatDev sdv = make_dev(S, LAT_FP64);
+  Geometry geo;
+  memset(&geo, 0, sizeof(geo));
+  geometry(S, 1, 16, S->Rlen, false, geo, (int)chunk);   // a power-of-two plan of one field always fits
+  for (int64_t l0 = 0; l0 < total; l0 += chunk) {
+    const int nl = (int)std::min<int64_t>(chunk, total - l0);
+    launch_blue_pre(src, src_stride, lines_per_item, p, L, dv.blue_lgA, dv.blue_lgB, dv.blue_chirp, Y, inverse, l0,
+                    nl, st);
+    blue_sub_fft(S, sdv, geo, Y, nl, 0, st);
+    launch_blue_mul(Y, dv.blue_bh, L, nl, 1.0 / (double)L, st);
+    blue_sub_fft(S, sdv, geo, Y, nl, 1, st);
+    launch_blue_post(Y, dst, dst_stride, lines_per_item, p, L, dv.blue_lgA, dv.blue_lgB, dv.blue_chirp, inverse, scale,
+                     l0, nl, st);
+  }
+}
+
+// the row pass of a chirp-z plan: inverse row transforms of the spectrum (except on a pass that starts
+// from the strain), the pointwise step, forward row transforms, and the Green operator when the row is
+// the only logical axis.  The convolution lines live in the Nyquist slot of the workspace (RowArgs::TN).
+static void blue_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, cudaStream_t st) {
+  const int lines = (int)(dv.n_c * dv.nrows);
+  double2* T = (double2*)a.T;
+  double2* Y = (double2*)a.TN;
+  const int64_t y_lines = (int64_t)lines * n_items;
+  if (!(a.flags & ROW_LOAD_EPS)) blue_rows(dv, T, a.t_stride, T, a.t_stride, lines, n_items, Y, y_lines, 1, 1.0, st);
+  launch_blue_point(dv, a, nblocks, n_items, st);
+  blue_rows(dv, T, a.t_stride, T, a.t_stride, lines, n_items, Y, y_lines, 0, 1.0, st);
+  if (a.flags & ROW_GAMMA) launch_blue_green(dv, a, n_items, st);
+}
+
+int lat_blue_transform_bh_impl(lat_plan* P) {
+  if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
+  const lat_plan* S = P->blue_sub;
+  const LatDev sdv = make_dev(S, LAT_FP64);
+  Geometry geo;
+  memset(&geo, 0, sizeof(geo));
+  if (int rc = geometry(S, 1, 16, S->Rlen, false, geo, 1)) return rc;
+  blue_sub_fft(S, sdv, geo, P->d_bh, 1, 0, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(0));
+  return LAT_OK;
+}
+
 // the row pass of a plan: power-of-two kernels or the mixed-radix kernels of a general plan
 template <typename Real>
 void launch_row(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, size_t smem, cudaStream_t st) {
+  if (dv.blue) {   // binary64 only: other precisions are refused on entry for these plans
+    if constexpr (std::is_same<Real, double>::value) blue_row_pass(dv, a, nblocks, n_items, st);
+    return;
+  }
   if (dv.general) launch_gen_row<Real>(dv, a, nblocks, n_items, kThreads, smem, st);
   else launch_row_pass<Real>(dv, a, nblocks, n_items, kThreads, smem, st);
 }
@@ -937,6 +1048,8 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (P && P->general && (o.precision == LAT_MIXED || o.scheme == LAT_SCHEME_CG))
     return lat_fail(LAT_ERR_UNSUPPORTED, "lattices with an elementary divisor that is not a power of two run "
                                          "Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 or LAT_DF64");
+  if (P && P->blue && o.precision != LAT_FP64)
+    return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run in LAT_FP64");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)
     return lat_fail(LAT_ERR_ARG, "the Eyre-Milton scheme takes the averaged boundary treatment");
   if (o.scheme == LAT_SCHEME_CG) {
@@ -993,6 +1106,8 @@ void load_case_items(const lat_plan* P, const uint8_t* phase, const double* C0, 
 
 using namespace latms_detail;
 
+int lat_blue_transform_bh(lat_plan* P) { return lat_blue_transform_bh_impl(P); }
+
 // the precision argument of the workspace queries: a precision, plus LAT_WS_CG for conjugate gradients
 static int ws_scheme(int precision) { return (precision & LAT_WS_CG) ? LAT_SCHEME_CG : LAT_SCHEME_BASIC; }
 static int ws_precision(int precision) { return precision & ~LAT_WS_CG; }
@@ -1010,9 +1125,9 @@ extern "C" size_t lattice_batch_workspace_bytes(const lat_plan* P, int n_items, 
 }
 
 extern "C" size_t lattice_fft_workspace_bytes(const lat_plan* P, int n_fields) {
-  (void)P;
-  (void)n_fields;
-  return 0;
+  // the convolution lines of a chirp-z row (blue_L complex binary64 per row of every field); else none
+  if (!P || n_fields < 1 || !P->blue) return 0;
+  return (size_t)n_fields * P->nrows * P->blue_L * sizeof(double2);
 }
 
 extern "C" int basic_scheme_solve(const lat_plan* P, const uint8_t* phase, int n_phases, const double* stiffness,
@@ -1403,8 +1518,6 @@ extern "C" int lattice_pass_times(const lat_plan* P, const uint8_t* phase, int n
 
 extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int n_fields, int inverse,
                            void* workspace, size_t workspace_bytes, void* stream) {
-  (void)workspace;
-  (void)workspace_bytes;
   if (!P || !in || !out || n_fields < 1) return lat_fail(LAT_ERR_ARG, "lattice_fft: bad argument");
   if (in == out) return lat_fail(LAT_ERR_ARG, "lattice_fft: in and out must not overlap");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1420,6 +1533,14 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
   int rc = geometry(P, 1, 16, P->Rlen, false, geo, 1);
   if (rc != LAT_OK) return rc;
   const double inv_m = 1.0 / (double)m;
+  if (P->blue && (!workspace || workspace_bytes < lattice_fft_workspace_bytes(P, n_fields)))
+    return lat_fail(LAT_ERR_SIZE, "lattice_fft: the chirp-z row needs lattice_fft_workspace_bytes of workspace");
+  // chirp-z row (general plans): the row transforms of all fields at once, before the forward column
+  // passes and after the inverse ones
+  const int64_t y_lines = (int64_t)n_fields * P->nrows;
+  if (P->blue && !inverse)
+    blue_rows(dv, (const double2*)in, m, (double2*)out, m, (int)P->nrows, n_fields, (double2*)workspace, y_lines, 0,
+              P->ngroups == 0 ? inv_m : 1.0, st);
   for (int f = 0; f < n_fields; ++f) {
     const double2* fin = (const double2*)in + (size_t)f * m;
     double2* fout = (double2*)out + (size_t)f * m;
@@ -1457,13 +1578,17 @@ extern "C" int lattice_fft(const lat_plan* P, const double* in, double* out, int
       else launch_row_complex<double>(dv, rin, fout, 1, inv, scale, geo.rpc, kThreads, geo.row_smem, st);
     };
     if (!inverse) {
-      row(fin, 0, P->ngroups == 0 ? inv_m : 1.0);
+      if (!P->blue) row(fin, 0, P->ngroups == 0 ? inv_m : 1.0);
       for (int k = P->ngroups - 1; k >= 0; --k) col(k, COL_FWD, nullptr, k == 0 ? inv_m : 1.0);
     } else {
       for (int k = 0; k < P->ngroups; ++k) col(k, COL_INV, k == 0 ? (const void*)fin : nullptr, 1.0);
-      row(P->ngroups == 0 ? (const void*)fin : (const void*)fout, 1, 1.0);
+      if (!P->blue) row(P->ngroups == 0 ? (const void*)fin : (const void*)fout, 1, 1.0);
     }
     CK(cudaGetLastError());
   }
+  if (P->blue && inverse)
+    blue_rows(dv, (const double2*)(P->ngroups == 0 ? in : out), m, (double2*)out, m, (int)P->nrows, n_fields,
+              (double2*)workspace, y_lines, 1, 1.0, st);
+  CK(cudaGetLastError());
   return LAT_OK;
 }

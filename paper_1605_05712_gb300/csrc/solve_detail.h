@@ -138,9 +138,18 @@ int group_decode(const GroupRun& g, const lat_solve_opts& o, double* sigma_bar, 
 int run_batch(const lat_plan* P, const std::vector<ItemHost>& items, const std::vector<const double*>& stiff,
               const std::vector<int>& nph, double tol, int maxit, const lat_solve_opts& o, char* ws, const Work& wl,
               const LatDev& dv, bool use_graph, double* sigma_bar, int* iters, double* resid, cudaStream_t st);
+// chirp-z row transforms of a plan with lat_plan::blue (solve.cu): lines j < lines_per_item of item i at
+// src + i src_stride + j p -> dst likewise (complex binary64, in place allowed); Y holds y_lines lines of
+// blue_L; inverse: the unnormalized inverse DFT; scale multiplies the result
+void blue_rows(const LatDev& dv, const double2* src, int64_t src_stride, double2* dst, int64_t dst_stride,
+               int lines_per_item, int n_items, double2* Y, int64_t y_lines, int inverse, double scale,
+               cudaStream_t st);
+int lat_blue_transform_bh_impl(lat_plan* P);
 
 }  // namespace latms_detail
 
 // host copies of the plan's twiddle tables (W_N^t, N = 2^tw_log2, and the split table
 // [hi | lo]) in binary64 or binary32 pairs; returns the two table lengths in entries
 int lat_host_twiddles(const lat_plan* P, int fp32, void* tw, void* stw, int64_t* n_tw, int64_t* n_stw);
+// at plan creation: d_bh (the wrapped conjugate chirp) -> its DFT by the chirp-z sub-plan, on the device
+int lat_blue_transform_bh(lat_plan* P);

@@ -41,9 +41,20 @@ def test_host_side_plan_without_gpu():
         assert P.m == L.m and P.divisors == L.e
         assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
         assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
-    # singular; a divisor longer than one mixed-radix pass that is not the largest; one whose four-step
-    # split would need a factor above the pass length (a prime beyond it)
-    for bad, code in (([[2, 4], [1, 2]], -2), ([[3000, 0], [0, 3000]], -5), ([[4099, 0], [0, 1]], -5)):
+    # a largest divisor with no split into two passes (a prime beyond the pass length, or such a prime
+    # times a small factor) keeps its rows whole for the chirp-z transform: layout split = 2
+    for M in ([[4099, 0], [0, 1]], [[2053, 7], [0, 1]], [[2, 0], [0, 4106]], [[1031, 0, 0], [5, 1, 0], [7, 0, 1]],
+              [[3, 0, 0], [0, 1, 0], [0, 0, 3093]]):
+        P = lattice_plan(M)
+        L = Lattice(M)
+        lay = P.layout()
+        assert lay["split"] == 2 and lay["ax_len"][-1] == L.e[-1]
+        assert P.m == L.m and P.divisors == L.e
+        assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
+        assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
+    # singular; a divisor longer than one mixed-radix pass that is not the largest; a prime largest divisor
+    # beyond the longest chirp-z row (2^22 points)
+    for bad, code in (([[2, 4], [1, 2]], -2), ([[3000, 0], [0, 3000]], -5), ([[4194319, 0], [0, 1]], -5)):
         try:
             lattice_plan(bad)
             raise AssertionError("expected an error")

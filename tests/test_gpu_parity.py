@@ -79,7 +79,11 @@ GEN_MATS = [[[3, 0], [0, 5]], [[6, 1], [0, 10]], [[3072, 0], [0, 1]], [[5, 0], [
             [[6, 2], [0, 10]], [[96, 1], [0, 96]], [[1009, 0], [0, 1]], [[1, 0, 0], [0, 3, 0], [0, 0, 45]],
             [[3, 0, 0], [0, 3, 0], [0, 0, 15]], [[2, 1, 0], [0, 3, 1], [1, 0, 4]],
             [[45, 0, 0], [0, 45, 0], [0, 0, 45]]]
-FFT_MATS = FFT_MATS + GEN_MATS
+# largest divisors with no split into two passes (chirp-z rows): rank-1 primes 2053 (2-D) and 1031 (3-D),
+# (2, 2 x 2053), rank-1 2 x 4099, and 3-D (1, 3, 3 x 1031) whose chirp-z row meets a column pass
+BLUE_MATS = [[[2053, 7], [0, 1]], [[1031, 0, 0], [5, 1, 0], [7, 0, 1]], [[2, 0], [0, 4106]], [[8198, 3], [0, 1]],
+             [[3, 0, 0], [0, 1, 0], [0, 0, 3093]]]
+FFT_MATS = FFT_MATS + GEN_MATS + BLUE_MATS
 
 
 @pytest.mark.parametrize("M", FFT_MATS)
@@ -956,6 +960,31 @@ def test_prime_length_lattice(cuda, M, prec):
     # the direct p-point DFT sums p terms: its rounding grows like sqrt(p) u instead of log2(m) u, which
     # sets the absolute floor of the residual history once the laminate has converged (~1e-13 by step 5)
     check_pair(*out, d=d, hist_atol=1e-14 if prec == "fp64" else None)
+
+
+@pytest.mark.parametrize("M", BLUE_MATS)
+def test_chirp_z_lattice(cuda, M):
+    # the chirp-z rows (Bluestein) against the oracle: Algorithm 1 on a laminate (rank-1 patterns lie on a
+    # line, along which the laminate with normal (1, 3[, 2]) is heterogeneous) or on inclusions, then the
+    # Eyre-Milton scheme; binary64 only (the other precisions are refused)
+    from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
+    import torch
+    d = len(M)
+    E = np.eye(d * (d + 1) // 2)[:2] + 0.1
+    P = lattice_plan(M)
+    assert P.layout()["split"] == 2
+    rank1 = P.divisors[:-1] == [1] * (d - 1)
+    ph = laminate([1, 3] if d == 2 else [1, 3, 2]) if rank1 else inclusions(7, d, 2, 0.3)
+    out = run_pair(M, ph, LAM2, (5.5, 5.5), E, tol=0.0, maxit=5, cuda=cuda)
+    assert 0 < np.count_nonzero(ph(out[1].p, out[1].m)) < out[1].m
+    check_pair(*out, d=d, hist_atol=1e-14)
+    out = run_pair(M, ph, LAM2, (np.sqrt(10.0),) * 2, E, tol=0.0, maxit=4, cuda=cuda, scheme="eyre_milton")
+    check_pair(*out, d=d, hist_atol=1e-14)
+    php = torch.from_numpy(ph(P.points(), P.m)).to(cuda)
+    for prec in ("df64", "mixed"):
+        with pytest.raises(LatticeError) as ei:
+            basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, precision=prec)
+        assert ei.value.code == -5
 
 
 # ---------------------------------------------------------------- asynchronous entry point
