@@ -11,7 +11,8 @@
 //                    is the only axis);
 //   gen_col_kernel : one logical axis per launch on tiles of columns: four-step twiddle, forward FFT,
 //                    the Green operator (axis 0), inverse FFT, inverse twiddle.
-// Binary64 and double-float pairs only (the binary32 increment form needs the power-of-two kernels).
+// Binary64, double-float pairs and binary32 (the mixed path: increment form on a strain held as pairs, and
+// its binary64-accurate restart on pairs, as the power-of-two kernels do it).
 #include <math.h>
 
 #include <algorithm>
@@ -19,15 +20,25 @@
 #include "fft_mixed.cuh"
 #include "kernels_dev.cuh"
 
-// strain slot of one point: binary64, or a double-float pair (hi, lo) during a pair solve
+// strain slot of one point: binary64, or a double-float pair (hi, lo) during a pair or mixed solve
 template <typename Real>
 __device__ __forceinline__ Real eps_ld1(const double* p) {
   if constexpr (is_df<Real>) {
     const float2 o = *(const float2*)p;
     return dfloat(o.x, o.y);
+  } else if constexpr (is_f32<Real>) {
+    const float2 o = *(const float2*)p;
+    return o.x + o.y;
   } else {
     return *p;
   }
+}
+// per-precision copies of the item's tables: binary64, binary32 (mixed) or pairs
+template <typename Real>
+__device__ __forceinline__ const Real* tab_of(const double* d, const float* f, const dfloat* df) {
+  if constexpr (is_df<Real>) return (const Real*)df;
+  else if constexpr (is_f32<Real>) return (const Real*)f;
+  else return (const Real*)d;
 }
 template <typename Real>
 __device__ __forceinline__ void eps_st1(double* p, Real v) {
@@ -54,7 +65,11 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
   const ItemDev* item = a.items + item_i;
   ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
   const bool update = (a.flags & ROW_UPDATE) != 0;
-  if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) return;   // finished earlier
+  if (a.flags & ROW_ONLY_PAUSED) {   // the restart passes of a mixed solve (pairs)
+    if (*(volatile const int*)&isc->done != ITEM_PAUSED) return;
+  } else if (update && *(volatile const int*)&isc->done != ITEM_ACTIVE) {
+    return;   // finished (or paused) earlier
+  }
   C* buf0 = (C*)smem_raw;
   C* buf1 = buf0 + (size_t)nlines * R;
   double* red = (double*)(buf1 + (size_t)nlines * R);
@@ -85,9 +100,15 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
     cur = fft_mixed<C, true>(buf0, buf1, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, nlines, tw);
   }
   C* other = (cur == buf0) ? buf1 : buf0;
-  // pointwise: update, residual, polarization (the inverse transform's real part is eps^(n+1))
+  // pointwise: update, residual, polarization (the inverse transform's real part is eps^(n+1), or the
+  // increment eps^(n+1) - eps^(n) in the binary32 increment form)
+  constexpr bool DBL = std::is_same<Real, double>::value;
+  const bool tau_of_delta = !DBL && update && (a.flags & (ROW_INCREMENT | ROW_TAU_DELTA)) != 0;
+  const bool incr = !DBL && update && (a.flags & ROW_INCREMENT) != 0 &&
+                    ((a.flags & ROW_INCR_FIRST) != 0 || *(volatile const int*)&isc->iter > 0);
   double dsum = 0.0;
   dfloat dd_acc(0.f, 0.f), dd_shear(0.f, 0.f);
+  DF dfs = {0.f, 0.f}, dfs_shear = {0.f, 0.f};
   for (int idx = tid; idx < rpc * R; idx += nthr) {
     const int row = idx / R, n = idx - row * R;
     const int64_t g = (r0 + row) * R + n;
@@ -98,7 +119,7 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
     const int ph = field ? 0 : phase[g];
     if (!field && update && a.mat.scheme == LAT_SCHEME_EYRE_MILTON) {
       // the transform returned u = (C + C0) eps: eps = (C_p + C0)^{-1} u
-      const Real* W = (is_df<Real> ? (const Real*)item->Wtab_df : (const Real*)item->Wtab) + ph * n_c * n_c;
+      const Real* W = tab_of<Real>(item->Wtab, item->Wtab_f, item->Wtab_df) + ph * n_c * n_c;
       Real u[NC];
 #pragma unroll
       for (int c = 0; c < n_c; ++c) u[c] = e[c];
@@ -114,26 +135,44 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
 #pragma unroll
       for (int c = 0; c < n_c; ++c) {
         double* pe = eps + (c * m + g);
-        const Real d = e[c] - eps_ld1<Real>(pe);
-        if constexpr (is_df<Real>) {
-          if (c >= D) df_acc_sq(dd_shear, d);
-          else df_acc_sq(dd_acc, d);
+        if constexpr (is_f32<Real>) {
+          // binary32: the strain is a double-float pair; no binary64 arithmetic
+          float2 o = *(float2*)pe;
+          float d;
+          if (incr) {   // T carried the increment itself
+            d = e[c];
+            df_acc(o.x, o.y, d);
+          } else {      // T carried the new strain
+            d = df_diff(e[c], o.x, o.y);
+            o = make_float2(e[c], 0.f);
+          }
+          *(float2*)pe = o;
+          if (c >= D) df_add_sq(dfs_shear, d);
+          else df_add_sq(dfs, d);
+          if (tau_of_delta) e[c] = d;
         } else {
-          dsum += (c >= D ? 2.0 : 1.0) * (d * d);
+          const Real d = e[c] - eps_ld1<Real>(pe);
+          if constexpr (is_df<Real>) {
+            if (c >= D) df_acc_sq(dd_shear, d);
+            else df_acc_sq(dd_acc, d);
+          } else {
+            dsum += (c >= D ? 2.0 : 1.0) * (d * d);
+          }
+          eps_st1<Real>(pe, e[c]);
+          if (tau_of_delta) e[c] = d;   // the pair restart: polarization of the exact increment
         }
-        eps_st1<Real>(pe, e[c]);
       }
     }
     if (field) {   // per-point stiffness field: tau = C_y : eps - C0 : eps
       const GreenK<Real> gk = green_consts<Real>(item, a.mat);
       Real t[NC];
-      field_polarize<Real, NC>(is_df<Real> ? (const Real*)item->fld_df : (const Real*)item->fld, m, g, gk.lam0,
-                               gk.mu0 + gk.mu0, e, t);
+      field_polarize<Real, NC>(tab_of<Real>(item->fld, item->fld_f, item->fld_df), m, g, gk.lam0, gk.mu0 + gk.mu0,
+                               e, t);
 #pragma unroll
       for (int c = 0; c < n_c; ++c) cur[((size_t)c * rpc + row) * R + n] = cpair<C>(t[c], Real(0));
       continue;
     }
-    const Real* Dt = (is_df<Real> ? (const Real*)item->Dtab_df : (const Real*)item->Dtab) + ph * n_c * n_c;
+    const Real* Dt = tab_of<Real>(item->Dtab, item->Dtab_f, item->Dtab_df) + ph * n_c * n_c;
 #pragma unroll
     for (int c = 0; c < n_c; ++c) {
       Real t = Real(0);
@@ -167,7 +206,10 @@ __global__ void __launch_bounds__(256) gen_row_kernel(LatDev dv, RowArgs a) {
   if (!update) return;
   double* partials = a.it.partials + item_i * a.it.pstride;
   double tot;
-  if constexpr (is_df<Real>) {
+  if constexpr (is_f32<Real>) {
+    const dfloat pr = dfloat(dfs.hi, dfs.lo) + dfloat(2.f * dfs_shear.hi, 2.f * dfs_shear.lo);
+    if (!item_reduce<1>(&pr, partials, isc, red, &s_last, &tot)) return;
+  } else if constexpr (is_df<Real>) {
     const dfloat pr = dd_acc + (dd_shear + dd_shear);
     if (!item_reduce<1>(&pr, partials, isc, red, &s_last, &tot)) return;
   } else {
@@ -185,7 +227,7 @@ __global__ void __launch_bounds__(256) gen_col_kernel(LatDev dv, ColArgs a) {
   const int item_i = blockIdx.y;
   if (a.scal) {
     const int st = *(volatile const int*)&((const ItemScal*)((const char*)a.scal + (size_t)item_i * 256))->done;
-    if (st != ITEM_ACTIVE) return;
+    if (a.only_paused ? st != ITEM_PAUSED : st != ITEM_ACTIVE) return;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.G, x = a.a0, w = a.w, lgw = __ffs(w) - 1;
@@ -464,24 +506,16 @@ void launch_blue_green(const LatDev& dv, const RowArgs& a, int n_items, cudaStre
 template <typename Real>
 void launch_gen_row(const LatDev& dv, const RowArgs& a, int nblocks, int n_items, int nthreads, size_t smem,
                     cudaStream_t st) {
-  if constexpr (is_f32<Real>) {
-    return;   // binary32 solves take the power-of-two kernels only (refused on entry for other plans)
-  } else {
-    const dim3 grid(nblocks, n_items);
-    if (dv.n_c == 6) gen_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
-    else gen_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
-  }
+  const dim3 grid(nblocks, n_items);
+  if (dv.n_c == 6) gen_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+  else gen_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
 }
 template <typename Real>
 void launch_gen_col(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st) {
-  if constexpr (is_f32<Real>) {
-    return;
-  } else {
-    const dim3 grid((unsigned)(a.outer * a.tiles_main), n_items);
-    if (a.n_f == 6) gen_col_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
-    else if (a.n_f == 3) gen_col_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
-    else if constexpr (!is_df<Real>) gen_col_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
-  }
+  const dim3 grid((unsigned)(a.outer * a.tiles_main), n_items);
+  if (a.n_f == 6) gen_col_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a);
+  else if (a.n_f == 3) gen_col_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a);
+  else if constexpr (std::is_same<Real, double>::value) gen_col_kernel<Real, 1><<<grid, nthreads, smem, st>>>(dv, a);
 }
 void launch_gen_row_complex(const LatDev& dv, const void* in, void* out, int inverse, double scale, int rpc,
                             int nthreads, size_t smem, cudaStream_t st) {
@@ -510,6 +544,10 @@ int lat_gen_kernel_attrs(int optin) {
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<double, 6>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 3>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<float, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<float, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<float, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<float, 6>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 1>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 3>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<double, 6>, optin);

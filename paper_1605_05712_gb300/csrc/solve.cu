@@ -248,11 +248,11 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   w.hist = off;
   off = align256(off + (size_t)n_items * LAT_HIST_CAP * sizeof(double));
   w.T64 = w.TN64 = off;
-  if (precision == LAT_MIXED) {
+  if (precision == LAT_MIXED) {   // the restart's pair spectrum: as T (and TN) with 16-byte values
     w.T64 = off;
-    off = align256(off + (size_t)n_items * n_c * (P->m / 2) * 16);
+    off = align256(off + (size_t)n_items * n_c * (P->general ? P->m : P->m / 2) * 16);
     w.TN64 = off;
-    off = align256(off + (size_t)n_items * n_c * P->nrows * 16);
+    off = align256(off + (P->general ? 0 : (size_t)n_items * n_c * P->nrows * 16));
   }
   w.cgv = off;
   w.cg_stride = (int64_t)n_c * P->m;
@@ -519,10 +519,12 @@ int enqueue_restart(const GroupRun& g, unsigned long long cond2, cudaStream_t st
   const Work& wl = g.wl;
   ItemScal* scal = (ItemScal*)(g.ws + wl.scal);
   launch_prep_restart(scal, g.full.it.glob, g.n_items, st);
-  launch_row_pass<dfloat>(g.dv64, g.r_pro, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
+  launch_row<dfloat>(g.dv64, g.r_pro, g.geo64.row_blocks, g.n_items, g.geo64.row_smem, st);
   enqueue_columns<dfloat>(g.dv64, g.P, g.geo64, g.c64, g.n_items, st);
-  launch_row_pass<dfloat>(g.dv64, g.r_upd, g.geo64.row_blocks, g.n_items, kThreads, g.geo64.row_smem, st);
-  const int64_t te = (int64_t)g.n_c * (g.P->m / 2), tne = (int64_t)g.n_c * g.P->nrows;
+  launch_row<dfloat>(g.dv64, g.r_upd, g.geo64.row_blocks, g.n_items, g.geo64.row_smem, st);
+  // general plans: the full complex spectrum, no Nyquist plane
+  const int64_t te = (int64_t)g.n_c * (g.P->general ? g.P->m : g.P->m / 2);
+  const int64_t tne = g.P->general ? 0 : (int64_t)g.n_c * g.P->nrows;
   launch_spectrum_to_f32(g.ws + wl.T64, g.ws + wl.TN64, g.ws + wl.T, g.ws + wl.TN, te, tne, g.full.t_stride,
                          g.full.tn_stride, scal, g.n_items, st);
   if (g.P->nax > 1) enqueue_columns<float>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
@@ -1045,9 +1047,9 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
   if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON && o.scheme != LAT_SCHEME_CG)
     return lat_fail(LAT_ERR_ARG, "bad scheme");
-  if (P && P->general && (o.precision == LAT_MIXED || o.scheme == LAT_SCHEME_CG))
+  if (P && P->general && o.scheme == LAT_SCHEME_CG)
     return lat_fail(LAT_ERR_UNSUPPORTED, "lattices with an elementary divisor that is not a power of two run "
-                                         "Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 or LAT_DF64");
+                                         "Algorithm 1 and the Eyre-Milton scheme");
   if (P && P->blue && o.precision != LAT_FP64)
     return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run in LAT_FP64");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)

@@ -392,8 +392,12 @@ MIXED_STRAIN_RTOL = 1e-5     # max relative strain-field error against the binar
 MIXED_CEFF_RTOL = 1e-6       # relative error of the mean stress (a column of C^eff)
 
 
+# the last five are general plans (mixed-radix binary32 kernels and their pair restart): (45, 45) sheared,
+# rank-1 m = 9216 (four-step 96 x 96), (1, 3, 45), 24^3, and 3-D rank-1 m = 1728
 @pytest.mark.parametrize("M", [[[256, 0], [0, 256]], [[512, 16], [0, 512]], [[64, 1], [0, 64]],
-                               [[32, 0, 0], [0, 32, 0], [0, 0, 32]], [[64, 1, 0], [0, 64, 1], [0, 0, 64]]])
+                               [[32, 0, 0], [0, 32, 0], [0, 0, 32]], [[64, 1, 0], [0, 64, 1], [0, 0, 64]],
+                               [[45, 9], [0, 45]], [[96, 1], [0, 96]], [[1, 0, 0], [0, 3, 0], [0, 0, 45]],
+                               [[24, 0, 0], [0, 24, 0], [0, 0, 24]], [[12, 1, 0], [0, 12, 1], [0, 0, 12]]])
 def test_mixed_precision_within_stated_tolerance(cuda, M):
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
@@ -940,11 +944,41 @@ def test_general_plan_warm_start_batch_multi_and_refusals(cuda):
     assert torch.equal(s1["eps"], outs[0]["eps"])
     s2 = basic_scheme_solve(P2, ph2, LAM2, (5.5, 5.5), Es[:1], tol=1e-9, maxit=500)
     assert torch.equal(s2["eps"], outs[1]["eps"])
-    # binary32 solves and conjugate gradients need the power-of-two kernels
-    for kw in (dict(precision="mixed"), dict(scheme="cg", boundary="zero")):
-        with pytest.raises(LatticeError) as ei:
-            basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, **kw)
-        assert ei.value.code == -5
+    # conjugate gradients need the power-of-two kernels
+    with pytest.raises(LatticeError) as ei:
+        basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, scheme="cg", boundary="zero")
+    assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("M", [[[6, 1], [0, 10]], [[3, 0, 0], [0, 3, 0], [0, 0, 15]]])
+def test_general_plan_mixed_forms(cuda, M):
+    # binary32 on general plans: the Eyre-Milton scheme (whose first step is taken in full), the plain
+    # (non-increment) form and a contrast-100 composite (the pair restart removes the binary32 offset),
+    # within the stated bounds
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
+    d = len(M)
+    P = lattice_plan(M)
+    L = Lattice(M)
+    perm = to_oracle_order(P.points(), L)
+    incl = synth.random_inclusions(12, d, 3, 0.3)
+    ph_p = torch.from_numpy(synth.inclusions_phase(P.points(), P.m, incl)).to(cuda)
+    ph_o = synth.inclusions_phase(L.p, L.m, incl)
+    E = np.eye(P.n_c)[:2] + 0.1
+    for lam, kw, okw in (((10.0, 10.0), dict(scheme="eyre_milton"), dict(scheme="eyre_milton")),
+                         ((10.0, 10.0), dict(mixed_increment=False), {}),
+                         ((100.0, 100.0), {}, {})):
+        voigts = [synth.iso_voigt(1.0, 1.0), synth.iso_voigt(*lam)]
+        C0 = (np.sqrt(lam[0]),) * 2 if "scheme" in kw else synth.c0_mean_extremes([1, lam[0]], [1, lam[1]])
+        g = basic_scheme_solve(P, ph_p, voigts, C0, E, tol=1e-6, maxit=3000, precision="mixed", **kw)
+        assert g["status"] == 0
+        S = stiff_tensors(voigts, d)
+        for lc in range(2):
+            o = basic_scheme(L, ph_o, S, C0, el.comps_to_sym(E[lc], d), tol=1e-6, maxit=3000, **okw)
+            assert abs(int(g["iters"][lc]) - o["iters"]) <= 1
+            eg = comps_to_tensor(g["eps"][lc].cpu().numpy(), d)
+            assert relerr_global(eg, o["eps"][perm]) < MIXED_STRAIN_RTOL
+            assert relerr_global(el.comps_to_sym(g["sigma_bar"][lc], d), o["sigma_bar"]) < MIXED_CEFF_RTOL
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
@@ -996,8 +1030,6 @@ def test_async_solve_matches_synchronous(cuda, prec):
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, basic_scheme_solve_async, lattice_plan
     for M in ([[256, 16], [0, 256]], [[32, 4, 0], [0, 32, 4], [0, 0, 32]], [[45, 9], [0, 45]]):
-        if prec == "mixed" and M == [[45, 9], [0, 45]]:
-            continue
         P = lattice_plan(M)
         d = len(M)
         ph = torch.from_numpy(inclusions(3, d, 4, 0.3)(P.points(), P.m)).to(cuda)
