@@ -100,13 +100,13 @@ typedef struct lat_plan lat_plan;
  * kernels with bit-reversed spectra; any other divisor takes mixed-radix
  * kernels (radix 4, 2, 3, 5 and a direct p-point DFT for other primes) in
  * natural order, with the full complex spectrum.  Those "general" plans run
- * Algorithm 1 and the Eyre-Milton scheme in every precision (LAT_SCHEME_CG
- * returns LAT_ERR_UNSUPPORTED there) and take strain buffers aligned to 8
- * bytes.  A largest divisor longer than one mixed-radix pass
+ * every scheme and precision the power-of-two plans run and take strain
+ * buffers aligned to 8 bytes.  A largest divisor longer than one mixed-radix pass
  * (2048 points in 2-D, 1024 in 3-D) is split four-step into two passes; when
  * no such split exists (a large prime factor) its rows are transformed by
  * Bluestein's chirp-z convolution (lattice_plan_layout reports split = 2):
- * LAT_FP64 only, and lattice_fft then needs lattice_fft_workspace_bytes.
+ * Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 only, and lattice_fft
+ * then needs lattice_fft_workspace_bytes.
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
  * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a general plan's
  * divisor other than the largest that is longer than one mixed-radix pass,

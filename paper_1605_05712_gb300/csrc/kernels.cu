@@ -550,32 +550,6 @@ __device__ __forceinline__ void fld_st2(double* p, Real v0, Real v1) {
   if constexpr (is_df<Real>) *(float4*)p = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
   else *(double2*)p = make_double2((double)v0, (double)v1);
 }
-// a : C0 : c for isotropic C0 on tensor components (shear components stored once, counted twice)
-template <typename Real, int NC>
-__device__ __forceinline__ Real c0_dot(const Real* a, const Real* c, Real lam0, Real two_mu0) {
-  constexpr int D = (NC == 6) ? 3 : 2;
-  Real ta = Real(0), tc = Real(0), s = Real(0), sh = Real(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    ta += a[k];
-    tc += c[k];
-    s += a[k] * c[k];
-  }
-#pragma unroll
-  for (int k = D; k < NC; ++k) sh += a[k] * c[k];
-  return lam0 * (ta * tc) + two_mu0 * (s + (sh + sh));
-}
-template <typename Real, int NC>
-__device__ __forceinline__ Real frob2(const Real* a) {
-  constexpr int D = (NC == 6) ? 3 : 2;
-  Real s = Real(0), sh = Real(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) s += a[k] * a[k];
-#pragma unroll
-  for (int k = D; k < NC; ++k) sh += a[k] * a[k];
-  return s + (sh + sh);
-}
-
 // the update stage keeps five vectors of a point pair live: 3 blocks of 256 threads per SM (85 registers)
 // for 2-D, the row pass's budget for 3-D
 template <typename Real, int NC>
@@ -1019,6 +993,7 @@ void launch_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nbl
   if constexpr (is_f32<Real>) {
     return;  // the conjugate-gradient scheme runs in binary64 or on double-float pairs (checked on entry)
   } else {
+    if (dv.general) return launch_gen_cg_row<Real>(dv, a, cg, nblocks, n_items, nthreads, smem, st);
     const dim3 grid(nblocks, n_items);
     if (dv.n_c == 6) cg_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a, cg);
     else cg_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a, cg);

@@ -205,6 +205,10 @@ template <typename Real>
 void launch_gen_col(const LatDev& dv, const ColArgs& a, int n_items, int nthreads, size_t smem, cudaStream_t st);
 void launch_gen_row_complex(const LatDev& dv, const void* in, void* out, int inverse, double scale, int rpc,
                             int nthreads, size_t smem, cudaStream_t st);
+// the conjugate-gradient row stages (cg_row_kernel's) on a general plan: binary64 and pairs
+template <typename Real>
+void launch_gen_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, int nthreads,
+                       size_t smem, cudaStream_t st);
 int lat_gen_kernel_attrs(int optin);
 // chirp-z rows (kernels_gen.cu, binary64): line l0 + y (y < nl) of the batch is line j = l % lines_per_item
 // of item i = l / lines_per_item, p complex values at base + i stride + j p; Y holds nl lines of L in the

@@ -513,3 +513,30 @@ __device__ __forceinline__ void item_report(double r, ItemScal* isc, int item_i,
     if (it.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)it.cond, active > 0 ? 1u : 0u);
   }
 }
+
+// ------------------------------------------------------------------ conjugate-gradient inner products
+// a : C0 : c for isotropic C0 on tensor components (shear components stored once, counted twice)
+template <typename Real, int NC>
+__device__ __forceinline__ Real c0_dot(const Real* a, const Real* c, Real lam0, Real two_mu0) {
+  constexpr int D = (NC == 6) ? 3 : 2;
+  Real ta = Real(0), tc = Real(0), s = Real(0), sh = Real(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ta += a[k];
+    tc += c[k];
+    s += a[k] * c[k];
+  }
+#pragma unroll
+  for (int k = D; k < NC; ++k) sh += a[k] * c[k];
+  return lam0 * (ta * tc) + two_mu0 * (s + (sh + sh));
+}
+template <typename Real, int NC>
+__device__ __forceinline__ Real frob2(const Real* a) {
+  constexpr int D = (NC == 6) ? 3 : 2;
+  Real s = Real(0), sh = Real(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += a[k] * a[k];
+#pragma unroll
+  for (int k = D; k < NC; ++k) sh += a[k] * a[k];
+  return s + (sh + sh);
+}

@@ -331,6 +331,198 @@ __global__ void __launch_bounds__(256) gen_row_complex_kernel(LatDev dv, const d
   }
 }
 
+// ------------------------------------------------------------------ conjugate gradients
+// The stages of cg_row_kernel (kernels.cu: Chronopoulos-Gear conjugate gradients on the discrete
+// Lippmann-Schwinger equation, its transform v -> -Gamma0 : (C : v) with k = 0 -> 0, tables holding C) on a
+// general plan's rows: mixed-radix row transforms, one point per thread step.  The vectors x (the strain),
+// r, p, q = A p and w = A r are held like the strain (binary64, or pairs in the pair kernels).
+template <typename Real, int NC>
+__global__ void __launch_bounds__(256) gen_cg_row_kernel(LatDev dv, RowArgs a, CgArgs cg) {
+  typedef typename cplx_of<Real>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int n_c = NC;
+  const int R = dv.Rlen, rpc = a.rpc, nlines = n_c * rpc;
+  const int item_i = blockIdx.y;
+  const ItemDev* item = a.items + item_i;
+  ItemScal* isc = (ItemScal*)((char*)a.it.scal + (size_t)item_i * 256);
+  const int stage = cg.stage;
+  if (stage != CG_FWD_X && *(volatile const int*)&isc->done != ITEM_ACTIVE) return;
+  C* buf0 = (C*)smem_raw;
+  C* buf1 = buf0 + (size_t)nlines * R;
+  double* red = (double*)(buf1 + (size_t)nlines * R);
+  __shared__ int s_last;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t m = dv.m, r0 = (int64_t)blockIdx.x * rpc;
+  C* T = (C*)a.T + item_i * a.t_stride;
+  const int ra = dv.nax - 1;
+  const C* tw = (const C*)dv.tw + dv.ax_twoff[ra];
+  const size_t voff = (size_t)item_i * cg.vstride;
+  double* x = item->eps;
+  double* r = cg.r + voff;
+  double* p = cg.p + voff;
+  double* q = cg.q + voff;
+  double* w = cg.w + voff;
+  const bool from_spectrum = (stage == CG_FULL0 || stage == CG_A);
+  C* cur = buf0;
+  if (from_spectrum) {
+    for (int idx = tid; idx < nlines * R; idx += nthr) {
+      const int line = idx / R, n = idx - line * R;
+      const int c = line / rpc, row = line - c * rpc;
+      cp_async_elem(buf0 + idx, T + (c * m + (r0 + row) * R + n));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    cur = fft_mixed<C, true>(buf0, buf1, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, nlines, tw);
+  }
+  C* other = (cur == buf0) ? buf1 : buf0;
+  Real alpha = Real(0), beta = Real(0), lam0, two_mu0;
+  if constexpr (is_df<Real>) {
+    if (stage == CG_B) {
+      alpha = isc->cg_alpha_df;
+      beta = isc->cg_beta_df;
+    }
+    lam0 = item->lam0_df;
+    two_mu0 = item->mu0_df + item->mu0_df;
+  } else {
+    if (stage == CG_B) {
+      alpha = Real(isc->cg_alpha);
+      beta = Real(isc->cg_beta);
+    }
+    lam0 = Real(item->lam0);
+    two_mu0 = Real(2.0 * item->mu0);
+  }
+  const Real* Ct = tab_of<Real>(item->Dtab, item->Dtab_f, item->Dtab_df);
+  Real acc0 = Real(0), acc1 = Real(0);   // <r, r>_C0 (or <w, r>_C0) and ||r||^2
+  for (int idx = tid; idx < rpc * R; idx += nthr) {
+    const int row = idx / R, n = idx - row * R;
+    const int64_t g = (r0 + row) * R + n;
+    Real v[NC];
+    if (from_spectrum) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) v[c] = cur[((size_t)c * rpc + row) * R + n].x;
+    }
+    if (stage == CG_FWD_X) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) v[c] = eps_ld1<Real>(x + c * m + g);
+    } else if (stage == CG_FULL0) {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) eps_st1<Real>(r + c * m + g, v[c]);
+      acc0 += c0_dot<Real, NC>(v, v, lam0, two_mu0);
+      acc1 += frob2<Real, NC>(v);
+    } else if (stage == CG_A) {
+      Real s[NC];
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        v[c] = -v[c];
+        eps_st1<Real>(w + c * m + g, v[c]);
+        s[c] = eps_ld1<Real>(r + c * m + g);
+      }
+      acc0 += c0_dot<Real, NC>(v, s, lam0, two_mu0);
+      continue;   // no polarization: the next stage starts from the updated vectors
+    } else {
+#pragma unroll
+      for (int c = 0; c < n_c; ++c) {
+        const int64_t o = c * m + g;
+        Real rv = eps_ld1<Real>(r + o), pv = eps_ld1<Real>(p + o), qv = eps_ld1<Real>(q + o);
+        const Real wv = eps_ld1<Real>(w + o);
+        Real xv = eps_ld1<Real>(x + o);
+        pv = rv + beta * pv;
+        qv = wv + beta * qv;
+        xv = xv + alpha * pv;
+        rv = rv - alpha * qv;
+        eps_st1<Real>(p + o, pv);
+        eps_st1<Real>(q + o, qv);
+        eps_st1<Real>(x + o, xv);
+        eps_st1<Real>(r + o, rv);
+        v[c] = rv;
+      }
+      acc0 += c0_dot<Real, NC>(v, v, lam0, two_mu0);
+      acc1 += frob2<Real, NC>(v);
+    }
+    // tau = C : v for the next transform
+    const Real* Cp = Ct + (int)item->phase[g] * n_c * n_c;
+#pragma unroll
+    for (int c = 0; c < n_c; ++c) {
+      Real t = Real(0);
+#pragma unroll
+      for (int k = 0; k < n_c; ++k) t += ldg_r(Cp + c * n_c + k) * v[k];
+      cur[((size_t)c * rpc + row) * R + n] = cpair<C>(t, Real(0));
+    }
+  }
+  __syncthreads();
+  if (stage != CG_A) {
+    C* out = fft_mixed<C, false>(cur, other, R, dv.ax_rad[ra], dv.ax_nrad[ra], 0, nlines, tw);
+    if (a.flags & ROW_GAMMA) {   // the row is the only logical axis
+      const GreenK<Real> gk = green_consts<Real>(item, a.mat);
+      for (int idx = tid; idx < rpc * R; idx += nthr) {
+        const int row = idx / R, k = idx - row * R;
+        C val[NC];
+#pragma unroll
+        for (int c = 0; c < n_c; ++c) val[c] = out[((size_t)c * rpc + row) * R + k];
+        int kk[LAT_MAX_AX] = {0};
+        kk[ra] = k;
+        green_at<Real, NC>(dv, a.mat, item, gk, kk, val);
+#pragma unroll
+        for (int c = 0; c < n_c; ++c) out[((size_t)c * rpc + row) * R + k] = val[c];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nlines * R; idx += nthr) {
+      const int line = idx / R, n = idx - line * R;
+      const int c = line / rpc, row = line - c * rpc;
+      T[c * m + (r0 + row) * R + n] = out[idx];
+    }
+  }
+  if (stage == CG_FWD_X) return;
+  double* partials = a.it.partials + item_i * a.it.pstride;
+  const Real vv[2] = {acc0, acc1};
+  double tot[2];
+  if (stage == CG_A) {
+    if (!item_reduce<1>(vv, partials, isc, red, &s_last, tot)) return;
+    if (tid == 0) {
+      const double gam = isc->cg_gamma, delta = tot[0];
+      const bool first = (isc->iter == 1) || isc->cg_alpha_prev == 0.0 || isc->cg_gamma_prev == 0.0;
+      const double bet = first ? 0.0 : gam / isc->cg_gamma_prev;
+      const double den = first ? delta : delta - bet * gam / isc->cg_alpha_prev;
+      const double alp = (gam != 0.0 && den != 0.0) ? gam / den : 0.0;
+      isc->cg_alpha = alp;
+      isc->cg_beta = bet;
+      isc->cg_alpha_df = dfloat(alp);
+      isc->cg_beta_df = dfloat(bet);
+      isc->cg_gamma_prev = gam;
+      isc->cg_alpha_prev = alp;
+      isc->counter = 0u;
+    }
+  } else {
+    if (!item_reduce<2>(vv, partials, isc, red, &s_last, tot)) return;
+    if (tid == 0) {
+      const double rr = sqrt(tot[1]) / item->norm0;
+      const double floor_rel = is_df<Real> ? 0x1p-38 : 0x1p-43;   // 1024 u
+      if (stage == CG_FULL0) isc->cg_r0 = rr;
+      isc->cg_gamma = tot[0];
+      item_report(rr, isc, item_i, a.it, rr <= floor_rel * isc->cg_r0);
+    }
+  }
+}
+
+template <typename Real>
+void launch_gen_cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, int nthreads,
+                       size_t smem, cudaStream_t st) {
+  if constexpr (is_f32<Real>) {
+    return;   // conjugate gradients run in binary64 or on pairs (checked on entry)
+  } else {
+    const dim3 grid(nblocks, n_items);
+    if (dv.n_c == 6) gen_cg_row_kernel<Real, 6><<<grid, nthreads, smem, st>>>(dv, a, cg);
+    else gen_cg_row_kernel<Real, 3><<<grid, nthreads, smem, st>>>(dv, a, cg);
+  }
+}
+template void launch_gen_cg_row<double>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t,
+                                        cudaStream_t);
+template void launch_gen_cg_row<float>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t,
+                                       cudaStream_t);
+template void launch_gen_cg_row<dfloat>(const LatDev&, const RowArgs&, const CgArgs&, int, int, int, size_t,
+                                        cudaStream_t);
+
 // ------------------------------------------------------------------ chirp-z rows (Bluestein)
 // A largest divisor p with no split into two lines that fit in shared memory is transformed as
 // X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_n = exp(-i pi n^2 / p): the sum is a cyclic convolution of
@@ -544,6 +736,10 @@ int lat_gen_kernel_attrs(int optin) {
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<double, 6>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 3>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<dfloat, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_cg_row_kernel<double, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_cg_row_kernel<double, 6>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_cg_row_kernel<dfloat, 3>, optin);
+  if (e == cudaSuccess) e = gen_set_smem(gen_cg_row_kernel<dfloat, 6>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<float, 3>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_row_kernel<float, 6>, optin);
   if (e == cudaSuccess) e = gen_set_smem(gen_col_kernel<float, 3>, optin);

@@ -1047,9 +1047,9 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
   if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON && o.scheme != LAT_SCHEME_CG)
     return lat_fail(LAT_ERR_ARG, "bad scheme");
-  if (P && P->general && o.scheme == LAT_SCHEME_CG)
-    return lat_fail(LAT_ERR_UNSUPPORTED, "lattices with an elementary divisor that is not a power of two run "
-                                         "Algorithm 1 and the Eyre-Milton scheme");
+  if (P && P->blue && o.scheme == LAT_SCHEME_CG)
+    return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run Algorithm 1 "
+                                         "and the Eyre-Milton scheme");
   if (P && P->blue && o.precision != LAT_FP64)
     return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run in LAT_FP64");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)

@@ -721,8 +721,12 @@ def test_eyre_milton_solution_and_iterations(cuda, M):
 # the rank-1 lattices with one point along x2 sample a line that misses the inclusions: a laminate there,
 # with f1 = 3/10 (at f1 = 1/2 the square wave excites only odd harmonics, the boundary frequencies of
 # these lattices, which are zeroed)
+# The last five are general plans (mixed-radix kernels): (3, 5), (1, 60), rank-1 m = 3072 (four-step),
+# 3-D (1, 3, 45) and (3, 3, 15).
 CG_MATS = [[[16, 4], [0, 8]], [[256, 16], [0, 256]], [[64, 32], [0, 1]], [[4096, 12288], [0, 1]],
-           [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]], [[2, 0], [0, 1]]]
+           [[8, 1, 0], [0, 8, 1], [0, 0, 8]], [[16, 4, 0], [0, 16, 4], [0, 0, 16]], [[2, 0], [0, 1]],
+           [[3, 0], [0, 5]], [[6, 1], [0, 10]], [[3072, 0], [0, 1]], [[1, 0, 0], [0, 3, 0], [0, 0, 45]],
+           [[3, 0, 0], [0, 3, 0], [0, 0, 15]]]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
@@ -751,7 +755,7 @@ def test_cg_transformed_cell_fixed_iterations(cuda, M, prec):
     check_pair(*out, d=d, hist_atol=1e-13)
 
 
-@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]], [[96, 1], [0, 96]]])
 def test_cg_solution_and_iterations(cuda, M):
     import torch
     from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
@@ -944,10 +948,6 @@ def test_general_plan_warm_start_batch_multi_and_refusals(cuda):
     assert torch.equal(s1["eps"], outs[0]["eps"])
     s2 = basic_scheme_solve(P2, ph2, LAM2, (5.5, 5.5), Es[:1], tol=1e-9, maxit=500)
     assert torch.equal(s2["eps"], outs[1]["eps"])
-    # conjugate gradients need the power-of-two kernels
-    with pytest.raises(LatticeError) as ei:
-        basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, scheme="cg", boundary="zero")
-    assert ei.value.code == -5
 
 
 @pytest.mark.parametrize("M", [[[6, 1], [0, 10]], [[3, 0, 0], [0, 3, 0], [0, 0, 15]]])
@@ -1000,7 +1000,7 @@ def test_prime_length_lattice(cuda, M, prec):
 def test_chirp_z_lattice(cuda, M):
     # the chirp-z rows (Bluestein) against the oracle: Algorithm 1 on a laminate (rank-1 patterns lie on a
     # line, along which the laminate with normal (1, 3[, 2]) is heterogeneous) or on inclusions, then the
-    # Eyre-Milton scheme; binary64 only (the other precisions are refused)
+    # Eyre-Milton scheme; binary64 only (the other precisions and conjugate gradients are refused)
     from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
     import torch
     d = len(M)
@@ -1015,9 +1015,9 @@ def test_chirp_z_lattice(cuda, M):
     out = run_pair(M, ph, LAM2, (np.sqrt(10.0),) * 2, E, tol=0.0, maxit=4, cuda=cuda, scheme="eyre_milton")
     check_pair(*out, d=d, hist_atol=1e-14)
     php = torch.from_numpy(ph(P.points(), P.m)).to(cuda)
-    for prec in ("df64", "mixed"):
+    for kw in (dict(precision="df64"), dict(precision="mixed"), dict(scheme="cg", boundary="zero")):
         with pytest.raises(LatticeError) as ei:
-            basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, precision=prec)
+            basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, **kw)
         assert ei.value.code == -5
 
 
