@@ -29,6 +29,14 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def _fft_ws(P, n_fields):
+    from paper_1605_05712_gb300.api import lib
+    f = lib().lattice_fft_workspace_bytes
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_size_t
+    return int(f(P.handle, n_fields))
+
+
 def test_host_side_plan_without_gpu():
     # plan construction, points and frequencies are host code; they work with no GPU present
     import numpy as np
@@ -41,6 +49,7 @@ def test_host_side_plan_without_gpu():
         assert P.m == L.m and P.divisors == L.e
         assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
         assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
+        assert _fft_ws(P, 2) == 0   # in-place passes: no scratch
     # a largest divisor with no split into two passes (a prime beyond the pass length, or such a prime
     # times a small factor) keeps its rows whole for the chirp-z transform: layout split = 2
     for M in ([[4099, 0], [0, 1]], [[2053, 7], [0, 1]], [[2, 0], [0, 4106]], [[1031, 0, 0], [5, 1, 0], [7, 0, 1]],
@@ -49,6 +58,14 @@ def test_host_side_plan_without_gpu():
         L = Lattice(M)
         lay = P.layout()
         assert lay["split"] == 2 and lay["ax_len"][-1] == L.e[-1]
+        # the convolution lines: n_c planes x m / p rows x L >= 2p - 1 (power of two) complex binary64 per
+        # load case, in the solve workspace and in lattice_fft's
+        p = L.e[-1]
+        Lc = 1 << (2 * p - 2).bit_length()
+        lines = P.n_c * (P.m // p)
+        assert P.workspace_bytes(1) >= lines * Lc * 16
+        assert P.workspace_bytes(2) - P.workspace_bytes(1) >= lines * Lc * 16
+        assert _fft_ws(P, 3) == 3 * (P.m // p) * Lc * 16
         assert P.m == L.m and P.divisors == L.e
         assert set(map(tuple, P.points().tolist())) == set(map(tuple, L.p.tolist()))
         assert set(map(tuple, P.freqs().tolist())) == set(map(tuple, L.h.tolist()))
