@@ -1093,7 +1093,9 @@ def test_field_solve_matches_oracle(cuda, M, prec):
         assert np.all(np.abs(np.array(g["history"][lc]) - ho) <= 1e-9 * ho + atol)
 
 
-@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]]])
+# the last two are general plans: rank-1 m = 9216 (four-step 96 x 96, mixed-radix) and the 24^3 grid
+@pytest.mark.parametrize("M", [[[256, 16], [0, 256]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]], [[96, 1], [0, 96]],
+                               [[24, 0, 0], [0, 24, 0], [0, 0, 24]]])
 def test_field_solve_equals_phase_solve(cuda, M):
     # the field built from a phase field and its table solves the same problem as the phase form: binary64
     # and df64 to rounding, mixed within its stated bounds against binary64
@@ -1117,3 +1119,24 @@ def test_field_solve_equals_phase_solve(cuda, M):
     assert fm["status"] == 0
     assert float((fm["eps"] - r6["eps"]).abs().max() / r6["eps"].abs().max()) <= MIXED_STRAIN_RTOL
     assert np.abs(fm["sigma_bar"] - r6["sigma_bar"]).max() <= MIXED_CEFF_RTOL * np.abs(r6["sigma_bar"]).max()
+
+
+@pytest.mark.parametrize("M", [[[2053, 7], [0, 1]], [[3, 0, 0], [0, 1, 0], [0, 0, 3093]]])
+def test_field_solve_on_chirp_z_lattice(cuda, M):
+    # a largest divisor with no split into two passes (chirp-z rows, binary64): the field built from a
+    # phase field and its table solves the phase problem to rounding
+    import torch
+    from paper_1605_05712_gb300 import basic_scheme_solve, basic_scheme_solve_field, lattice_plan, voigt_field
+    P = lattice_plan(M)
+    assert P.layout()["split"] == 2
+    d = len(M)
+    ph = inclusions(5, d, 3, 0.3)(P.points(), P.m)
+    V = np.array(LAM2)[ph]
+    field = torch.from_numpy(voigt_field(V)).to(cuda)
+    phd = torch.from_numpy(ph).to(cuda)
+    E = np.eye(P.n_c)[:2]
+    ref = basic_scheme_solve(P, phd, LAM2, (5.5, 5.5), E, tol=1e-8, maxit=2000)
+    f = basic_scheme_solve_field(P, field, (5.5, 5.5), E, tol=1e-8, maxit=2000)
+    assert ref["status"] == 0 and f["status"] == 0 and np.array_equal(f["iters"], ref["iters"])
+    assert float((f["eps"] - ref["eps"]).abs().max() / ref["eps"].abs().max()) < 1e-11
+    assert np.abs(f["sigma_bar"] - ref["sigma_bar"]).max() < 1e-11 * np.abs(ref["sigma_bar"]).max()
