@@ -48,3 +48,19 @@ def test_aliasing_lemma(M):
         cong = np.all(np.abs(diff - np.round(diff)) < 1e-9, axis=1)
         assert cong.sum() == 1
         assert abs(c[cong][0] - 1) < 1e-12 and np.abs(c[~cong]).max() < 1e-12
+
+
+@pytest.mark.parametrize("M", MATS)
+def test_phase_index_is_the_divisor_box_product(M):
+    # Sec. 2.2: with y(lambda) = R^{-1} E^{-1} lambda and h(k) = R^T k (mod the lattices),
+    # h(k)^T y(lambda) = sum_j k_j lambda_j / e_j (mod 1), so the exact phase index of F(M) is
+    # m sum_j k_j lambda_j / e_j mod m; k and lambda run over the same box in the same order, so the
+    # phase matrix is symmetric (F(M) of the plan orderings equals its transpose)
+    from oracle.transform import phase_index
+    L = Lattice(M)
+    lam = np.asarray(L.lam, dtype=np.int64)
+    scale = np.array([L.m // e for e in L.e], dtype=np.int64)
+    ref = ((lam * scale) @ lam.T) % L.m
+    P = phase_index(L)
+    assert np.array_equal(P, ref)
+    assert np.array_equal(P, P.T)

@@ -119,3 +119,27 @@ def test_targets_and_strain_reconstruction_agree():
     Eu[3:] *= 2.0
     ref = np.einsum('j,jixyz->ixyz', Eu, eps_unit)
     assert np.abs(ws.localization_to_strain(y, E) - ref).max() < 1e-12
+
+
+def test_features_are_the_voigt_upper_triangle_over_mu0():
+    # the 21 input channels are the upper triangle of the 6x6 Voigt stiffness (row by row) divided by
+    # mu0, then 11 zero channels; written out for isotropic phases (lam, mu): diagonal lam + 2 mu on the
+    # normal block, lam off the diagonal of the normal block, mu on the shear diagonal, zero elsewhere
+    from oracle.elasticity import iso_voigt6
+    mu0 = 2.5
+    phases = [(1.0, 3.0), (7.0, 0.5)]
+    phase = np.array([[[0, 1], [1, 0]], [[1, 1], [0, 0]]], dtype=np.int64)   # a 2x2x2 grid
+    f = ws.features([iso_voigt6(*p) for p in phases], phase, mu0)
+    assert f.shape == (32,) + phase.shape
+    for q, (lam, mu) in enumerate(phases):
+        a, b = (lam + 2 * mu) / mu0, lam / mu0
+        s = mu / mu0
+        expect = [a, b, b, 0, 0, 0,
+                  a, b, 0, 0, 0,
+                  a, 0, 0, 0,
+                  s, 0, 0,
+                  s, 0,
+                  s] + [0] * 11
+        sel = phase == q
+        for c in range(32):
+            assert np.all(f[c][sel] == expect[c]), c
