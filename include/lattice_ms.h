@@ -105,7 +105,8 @@ typedef struct lat_plan lat_plan;
  * (2048 points in 2-D, 1024 in 3-D) is split four-step into two passes; when
  * no such split exists (a large prime factor) its rows are transformed by
  * Bluestein's chirp-z convolution (lattice_plan_layout reports split = 2):
- * Algorithm 1 and the Eyre-Milton scheme in LAT_FP64 only, and lattice_fft
+ * Algorithm 1, the Eyre-Milton scheme and conjugate gradients, in LAT_FP64
+ * only (LAT_DF64 and LAT_MIXED return LAT_ERR_UNSUPPORTED), and lattice_fft
  * then needs lattice_fft_workspace_bytes.
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
  * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a general plan's

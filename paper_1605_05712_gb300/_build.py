@@ -18,8 +18,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["plan.cpp", "kernels.cu", "kernels_gen.cu", "solve.cu", "noalloc.cu", "warmstart.cu", "tune.cu",
-           "gather.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "kernels_gen.cu", "kernels_blue_cg.cu", "solve.cu", "noalloc.cu", "warmstart.cu",
+           "tune.cu", "gather.cu"]
 
 
 def _newer(target, deps):

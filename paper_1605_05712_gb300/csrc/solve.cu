@@ -220,6 +220,7 @@ Work layout(const lat_plan* P, int n_items, int precision, int phases_per_table,
   w.tn_per_lc = P->general ? (P->blue ? (size_t)n_c * P->nrows * P->blue_L * 16 : 0) : (size_t)n_c * P->nrows * cs;
   // two values per row block (conjugate gradients), n_c per block of the effective stress
   w.pstride = std::max<int64_t>(2 * P->nrows, (int64_t)kEffBlocksMax * 6);
+  if (P->blue) w.pstride = std::max<int64_t>(w.pstride, 2 * 1024);   // chirp-z: up to 1024 point blocks
   w.table_bytes = (size_t)phases_per_table * n_c * n_c * sizeof(double);
   size_t off = 0;
   w.T = off;
@@ -418,6 +419,35 @@ static void blue_row_pass(const LatDev& dv, const RowArgs& a, int nblocks, int n
   if (a.flags & ROW_GAMMA) launch_blue_green(dv, a, n_items, st);
 }
 
+// a conjugate-gradient stage on a chirp-z plan: inverse row transforms of the spectrum (stages that start
+// from it), the stage's pointwise part, and for every stage but A the forward row transforms and the Green
+// operator when the row is the only logical axis (the order of gen_cg_row_kernel)
+static void blue_cg_row_pass(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items,
+                             cudaStream_t st) {
+  const int lines = (int)(dv.n_c * dv.nrows);
+  double2* T = (double2*)a.T;
+  double2* Y = (double2*)a.TN;
+  const int64_t y_lines = (int64_t)lines * n_items;
+  if (cg.stage == CG_FULL0 || cg.stage == CG_A)
+    blue_rows(dv, T, a.t_stride, T, a.t_stride, lines, n_items, Y, y_lines, 1, 1.0, st);
+  launch_blue_cg_point(dv, a, cg, nblocks, n_items, st);
+  if (cg.stage == CG_A) return;
+  blue_rows(dv, T, a.t_stride, T, a.t_stride, lines, n_items, Y, y_lines, 0, 1.0, st);
+  if (a.flags & ROW_GAMMA) launch_blue_green(dv, a, n_items, st);
+}
+
+// a conjugate-gradient stage of a plan's rows: the chirp-z stages (binary64 only: other precisions are
+// refused on entry for these plans) or the row kernels
+template <typename Real>
+void cg_row(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items, size_t smem,
+            cudaStream_t st) {
+  if (dv.blue) {
+    if constexpr (std::is_same<Real, double>::value) blue_cg_row_pass(dv, a, cg, nblocks, n_items, st);
+    return;
+  }
+  launch_cg_row<Real>(dv, a, cg, nblocks, n_items, kThreads, smem, st);
+}
+
 int lat_blue_transform_bh_impl(lat_plan* P) {
   if (int rc = ensure_attrs()) return lat_fail(LAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString((cudaError_t)rc));
   const lat_plan* S = P->blue_sub;
@@ -465,10 +495,10 @@ void enqueue_body(const GroupRun& g, const RowArgs& full, cudaStream_t st) {
   if (g.cg) {
     CgArgs cb = g.cga;
     cb.stage = CG_B;
-    launch_cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+    cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, g.geo.row_smem, st);
     enqueue_columns<Real>(g.dv, g.P, g.geo, g.cl, g.n_items, st);
     cb.stage = CG_A;
-    launch_cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, kThreads, g.geo.row_smem, st);
+    cg_row<Real>(g.dv, full, cb, g.geo.row_blocks, g.n_items, g.geo.row_smem, st);
     return;
   }
   launch_row<Real>(g.dv, full, g.geo.row_blocks, g.n_items, g.geo.row_smem, st);
@@ -821,13 +851,13 @@ int group_prepare(const lat_plan* P, const std::vector<ItemHost>& items, const s
         typedef decltype(tag) Real;
         CgArgs cs = cg;
         cs.stage = CG_FWD_X;
-        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, geo.row_smem, st);
         enqueue_columns<Real>(dv, P, geo, c0, n_items, st);
         cs.stage = CG_FULL0;
-        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, geo.row_smem, st);
         enqueue_columns<Real>(dv, P, geo, g.cl, n_items, st);
         cs.stage = CG_A;
-        launch_cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, kThreads, geo.row_smem, st);
+        cg_row<Real>(dv, ra, cs, geo.row_blocks, n_items, geo.row_smem, st);
         return 0;
       });
       CK(cudaGetLastError());
@@ -1047,9 +1077,6 @@ int check_common(const lat_plan* P, double tol, int maxit, const lat_solve_opts&
   if (o.boundary != LAT_BOUNDARY_AVERAGE && o.boundary != LAT_BOUNDARY_ZERO) return lat_fail(LAT_ERR_ARG, "bad boundary");
   if (o.scheme != LAT_SCHEME_BASIC && o.scheme != LAT_SCHEME_EYRE_MILTON && o.scheme != LAT_SCHEME_CG)
     return lat_fail(LAT_ERR_ARG, "bad scheme");
-  if (P && P->blue && o.scheme == LAT_SCHEME_CG)
-    return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run Algorithm 1 "
-                                         "and the Eyre-Milton scheme");
   if (P && P->blue && o.precision != LAT_FP64)
     return lat_fail(LAT_ERR_UNSUPPORTED, "lattices whose largest divisor takes the chirp-z transform run in LAT_FP64");
   if (o.scheme == LAT_SCHEME_EYRE_MILTON && o.boundary == LAT_BOUNDARY_ZERO)

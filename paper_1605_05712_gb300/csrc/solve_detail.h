@@ -145,6 +145,10 @@ void blue_rows(const LatDev& dv, const double2* src, int64_t src_stride, double2
                int lines_per_item, int n_items, double2* Y, int64_t y_lines, int inverse, double scale,
                cudaStream_t st);
 int lat_blue_transform_bh_impl(lat_plan* P);
+// the pointwise part of a conjugate-gradient stage on a chirp-z plan (kernels_blue_cg.cu): vector updates,
+// inner products, step lengths or residual report; tau = C : v except in stage A; grid nblocks x items
+void launch_blue_cg_point(const LatDev& dv, const RowArgs& a, const CgArgs& cg, int nblocks, int n_items,
+                          cudaStream_t st);
 
 }  // namespace latms_detail
 

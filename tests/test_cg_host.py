@@ -54,3 +54,24 @@ def test_boundary_zero_passes_the_checks():
     # any device access
     rc, msg = _solve_rc([[16, 4], [0, 8]], api.LAT_DF64, api.LAT_BOUNDARY_ZERO, 0)
     assert rc == -4 and "workspace" in msg
+
+
+def test_chirp_z_plans_take_conjugate_gradients_in_binary64():
+    # a largest divisor with no split into two passes (chirp-z rows): binary64 CG passes the argument
+    # checks (odd largest divisor: either boundary option; even: boundary frequencies zeroed), pairs are
+    # refused as for every scheme on these plans; the workspace holds the four vectors and two partial sums
+    # for each of up to 1024 point blocks
+    for M, bnd in (([[2053, 7], [0, 1]], api.LAT_BOUNDARY_AVERAGE), ([[2, 0], [0, 4106]], api.LAT_BOUNDARY_ZERO),
+                   ([[3, 0, 0], [0, 1, 0], [0, 0, 3093]], api.LAT_BOUNDARY_ZERO)):
+        P = lattice_plan(M)
+        assert P.layout()["split"] == 2
+        rc, msg = _solve_rc(M, api.LAT_FP64, bnd, 0)
+        assert rc == -4 and "workspace" in msg, msg
+        rc, msg = _solve_rc(M, api.LAT_DF64, bnd, 0)
+        assert rc == -5 and "LAT_FP64" in msg, msg
+        for n in (1, 2):
+            base = P.workspace_bytes(n, api.LAT_FP64)
+            assert P.workspace_bytes(n, api.LAT_FP64 | api.LAT_WS_CG) >= base + 4 * n * P.n_c * P.m * 8
+            assert base >= n * 2 * 1024 * 8
+    rc, msg = _solve_rc([[2, 0], [0, 4106]], api.LAT_FP64, api.LAT_BOUNDARY_AVERAGE, 0)
+    assert rc == api.LAT_ERR_ARG and "LAT_BOUNDARY_ZERO" in msg

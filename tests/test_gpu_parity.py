@@ -1000,7 +1000,7 @@ def test_prime_length_lattice(cuda, M, prec):
 def test_chirp_z_lattice(cuda, M):
     # the chirp-z rows (Bluestein) against the oracle: Algorithm 1 on a laminate (rank-1 patterns lie on a
     # line, along which the laminate with normal (1, 3[, 2]) is heterogeneous) or on inclusions, then the
-    # Eyre-Milton scheme; binary64 only (the other precisions and conjugate gradients are refused)
+    # Eyre-Milton scheme and conjugate gradients; binary64 only (the other precisions are refused)
     from paper_1605_05712_gb300 import LatticeError, basic_scheme_solve, lattice_plan
     import torch
     d = len(M)
@@ -1014,8 +1014,15 @@ def test_chirp_z_lattice(cuda, M):
     check_pair(*out, d=d, hist_atol=1e-14)
     out = run_pair(M, ph, LAM2, (np.sqrt(10.0),) * 2, E, tol=0.0, maxit=4, cuda=cuda, scheme="eyre_milton")
     check_pair(*out, d=d, hist_atol=1e-14)
+    # conjugate gradients (the boundary frequencies of an even largest divisor zeroed); a laminate with
+    # f1 = 3/10 on the rank-1 lines, so that the even lattices' load is not all boundary harmonics
+    phc = ((lambda p, m: synth.laminate_phase(p, m, [1, 3] if d == 2 else [1, 3, 2], Fraction(3, 10))) if rank1
+           else ph)
+    out = run_pair(M, phc, LAM2, (5.5, 5.5), E, tol=0.0, maxit=5, cuda=cuda, scheme="cg", boundary="zero")
+    assert 0 < np.count_nonzero(phc(out[1].p, out[1].m)) < out[1].m
+    check_pair(*out, d=d, hist_atol=1e-13)
     php = torch.from_numpy(ph(P.points(), P.m)).to(cuda)
-    for kw in (dict(precision="df64"), dict(precision="mixed"), dict(scheme="cg", boundary="zero")):
+    for kw in (dict(precision="df64"), dict(precision="mixed"), dict(precision="df64", scheme="cg", boundary="zero")):
         with pytest.raises(LatticeError) as ei:
             basic_scheme_solve(P, php, LAM2, (5.5, 5.5), E, tol=1e-6, maxit=10, **kw)
         assert ei.value.code == -5
