@@ -109,9 +109,11 @@ typedef struct lat_plan lat_plan;
  * only (LAT_DF64 and LAT_MIXED return LAT_ERR_UNSUPPORTED), and lattice_fft
  * then needs lattice_fft_workspace_bytes.
  * Errors: LAT_ERR_DIM, LAT_ERR_SINGULAR, LAT_ERR_SIZE (m > 2^28 or entries
- * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (a general plan's
- * divisor other than the largest that is longer than one mixed-radix pass,
- * or a chirp-z row longer than 2^22 points), LAT_ERR_CUDA.
+ * beyond the exact int64 range), LAT_ERR_UNSUPPORTED (no decomposition fits:
+ * a divisor other than the largest longer than one pass -- 2048 points in
+ * 2-D, 1024 in 3-D, e.g. diag(4096, 4096) --, or a largest divisor that needs
+ * more than two passes and is not a chirp-z row of at most 2^22 points, e.g.
+ * rank-1 lattices of 2^24 points in 2-D or 2^22 in 3-D), LAT_ERR_CUDA.
  */
 int lattice_plan(const int64_t* M, int d, lat_plan** out);
 

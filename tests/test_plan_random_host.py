@@ -15,6 +15,7 @@ from itertools import combinations
 from math import gcd
 
 import numpy as np
+import pytest
 
 from oracle.lattice import brute_force_pattern
 
@@ -112,3 +113,19 @@ def test_random_plans_match_the_definitions():
         if m ** d <= 40000:
             assert set(map(tuple, p.tolist())) == brute_force_pattern(M), M
     assert kinds == {"pow2", "general", "chirp-z"}
+
+
+def test_plan_size_limits():
+    # a divisor other than the largest takes one pass (2048 points in 2-D, 1024 in 3-D); the largest takes
+    # at most two (one four-step split) or chirp-z rows of at most 2^22 points
+    from paper_1605_05712_gb300 import LatticeError, lattice_plan
+    planned = {((1, 0), (0, 1 << 23)): 1, ((1, 0, 0), (0, 1, 0), (0, 0, 1 << 21)): 1,
+               ((1, 0), (0, 3 << 20)): 1, ((1, 0), (0, 5 ** 9)): 2, ((2048, 0), (0, 2048)): 0,
+               ((1, 0, 0), (0, 1024, 0), (0, 0, 1024)): 0, ((1536, 0), (0, 1536)): 0}
+    for M, split in planned.items():
+        assert lattice_plan([list(r) for r in M]).layout()["split"] == split, M
+    for M in ([[4096, 0], [0, 4096]], [[3072, 0], [0, 3072]], [[1, 0, 0], [0, 1155, 0], [0, 0, 1155]],
+              [[1, 0], [0, 1 << 24]], [[1, 0, 0], [0, 1, 0], [0, 0, 1 << 22]], [[1, 0], [0, 9 << 20]]):
+        with pytest.raises(LatticeError) as ei:
+            lattice_plan(M)
+        assert ei.value.code == -5, M
