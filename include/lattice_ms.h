@@ -96,13 +96,14 @@ typedef struct lat_plan lat_plan;
  * dimension d_M, the FFT decomposition over the elementary divisors and
  * uploads twiddle tables to the current device (the plan's device; without a
  * CUDA device the plan is host-only).
- * Every regular M is planned: divisors that are powers of two take radix-4/2
- * kernels with bit-reversed spectra; any other divisor takes mixed-radix
- * kernels (radix 4, 2, 3, 5 and a direct p-point DFT for other primes) in
- * natural order, with the full complex spectrum.  Those "general" plans run
- * every scheme and precision the power-of-two plans run and take strain
- * buffers aligned to 8 bytes.  A largest divisor longer than one mixed-radix pass
- * (2048 points in 2-D, 1024 in 3-D) is split four-step into two passes; when
+ * Every regular M within the size limits below is planned: divisors that are
+ * powers of two take radix-4/2 kernels with bit-reversed spectra; any other
+ * divisor takes mixed-radix kernels (radix 4, 2, 3, 5 and a direct p-point
+ * DFT for other primes) in natural order, with the full complex spectrum.
+ * Those "general" plans run every scheme and precision the power-of-two
+ * plans run and take strain buffers aligned to 8 bytes.  A largest divisor
+ * longer than one pass (2048 points in 2-D, 1024 in 3-D) is split four-step
+ * into two passes; when
  * no such split exists (a large prime factor) its rows are transformed by
  * Bluestein's chirp-z convolution (lattice_plan_layout reports split = 2):
  * Algorithm 1, the Eyre-Milton scheme and conjugate gradients, in LAT_FP64
