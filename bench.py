@@ -354,18 +354,37 @@ def bench_gpu(args):
 
     variants = {}
     if not args.no_variants:
+        # a variant that fails is recorded as such; the headline line above it still prints
+        def variant(name, fn):
+            try:
+                variants[name] = fn()
+            except Exception as e:          # noqa: BLE001 -- reported in the JSON line, not hidden
+                torch.cuda.synchronize()
+                variants[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+
         ttt = {}
-        for form in ("mixed", "df64", "mixed_eyre_milton", "fp64_eyre_milton", "df64_cg", "fp64_cg"):
+
+        def time_form(form):
             run_step(w, work, ws, form)
             ms_v, u_v, it_v = timed(lambda: run_step(w, work, ws, form), max(1, min(args.steps, 3)), flush, st)
-            ttt[form] = {"ms": round(ms_v, 3), "value": round(u_v / (ms_v / 1e3), 1), "iterations": it_v,
-                         "speedup_vs_fp64": round(ms_step / ms_v, 2)}
+            return {"ms": round(ms_v, 3), "value": round(u_v / (ms_v / 1e3), 1), "iterations": it_v,
+                    "speedup_vs_fp64": round(ms_step / ms_v, 2)}
+
+        for form in ("mixed", "df64", "mixed_eyre_milton", "fp64_eyre_milton", "df64_cg", "fp64_cg"):
+            try:
+                ttt[form] = time_form(form)
+            except Exception as e:          # noqa: BLE001
+                torch.cuda.synchronize()
+                ttt[form] = {"error": "%s: %s" % (type(e).__name__, e)}
         ttt["fp64"] = {"ms": round(ms_step, 3), "value": round(value, 1), "iterations": iters}
         variants["time_to_resid_1e-6_ms"] = ttt
-        run_step(w, work, ws, "mixed")
-        variants["mixed_roofline"] = roofline_of(w, work, "mixed", ttt["mixed"]["iterations"], pk, "hbm")
-        variants["laminate2d_262144"] = bench_laminate2d(dev, args, flush, st)
-        variants["laminate4096_latency"] = bench_laminate4096(dev, args, flush, st)
+        if "iterations" in ttt["mixed"]:
+            def mixed_roof():
+                run_step(w, work, ws, "mixed")
+                return roofline_of(w, work, "mixed", ttt["mixed"]["iterations"], pk, "hbm")
+            variant("mixed_roofline", mixed_roof)
+        variant("laminate2d_262144", lambda: bench_laminate2d(dev, args, flush, st))
+        variant("laminate4096_latency", lambda: bench_laminate4096(dev, args, flush, st))
 
     gpu_launches = sum(launches_per_solve(it["plan"], its, "fp64") for it, its in zip(work, iters))
     m_total = sum(it["plan"].m for it in work)
