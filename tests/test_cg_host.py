@@ -75,3 +75,15 @@ def test_chirp_z_plans_take_conjugate_gradients_in_binary64():
             assert base >= n * 2 * 1024 * 8
     rc, msg = _solve_rc([[2, 0], [0, 4106]], api.LAT_FP64, api.LAT_BOUNDARY_AVERAGE, 0)
     assert rc == api.LAT_ERR_ARG and "LAT_BOUNDARY_ZERO" in msg
+
+
+def test_multi_workspace_with_chirp_z_problems():
+    # a multi call mixing a chirp-z lattice with power-of-two and general ones: the conjugate-gradient
+    # query makes room for every problem's four vectors and is at least each problem's own workspace
+    plans = [lattice_plan(M) for M in ([[2053, 7], [0, 1]], [[64, 1], [0, 64]], [[3, 0], [0, 5]])]
+    probs = [dict(plan=P, stiffness=[np.eye(6)], E=np.zeros((2, P.n_c))) for P in plans]
+    base = multi_workspace_bytes(probs, "fp64")
+    cg = multi_workspace_bytes(probs, "fp64", scheme="cg")
+    assert base > 0 and cg >= base + sum(4 * 2 * P.n_c * P.m * 8 for P in plans)
+    for P in plans:
+        assert cg >= P.workspace_bytes(2, api.LAT_FP64 | api.LAT_WS_CG)
