@@ -456,9 +456,9 @@ def bench_laminate2d(dev, args, flush, st):
 
 
 def bench_laminate4096(dev, args, flush, st):
-    """Config 1, the latency case: the 2-D laminate (layer normal (1,3), phases (1,1) / (10,10), C0 the mean
-    of the extremes) at m = 4096, E = (1,0,0), one binary64 solve to tol 1e-8 per lattice: the aligned
-    rank-1 lattice of config 1, the spread rank-1 lattice [[64,1],[0,64]] and the tensor grid diag(64,64)
+    """The latency case: the 2-D laminate (layer normal (1,3), phases (1,1) / (10,10), C0 the mean of the
+    extremes) at m = 4096, E = (1,0,0), one binary64 solve to tol 1e-8 per lattice: the aligned rank-1
+    lattice [[4096,12288],[0,1]], the spread rank-1 lattice [[64,1],[0,64]] and the tensor grid diag(64,64)
     the paper times (94 iterations, 41.2 s in its Matlab code).  Wall time per solve through the C ABI
     (device inputs, results left on the device), median of the timed repeats."""
     import torch
@@ -490,7 +490,7 @@ def bench_laminate4096(dev, args, flush, st):
 
 
 def bench_hashin(args):
-    """Config-3 workload: the coated-ellipsoid (generalized Hashin) structure at m = 2^21 on the tensor grid,
+    """The coated-ellipsoid workload: the coated-ellipsoid (generalized Hashin) structure at m = 2^21 on the tensor grid,
     the rank-1 and the sheared 3-D lattices; six unit load cases batched in one solve, tol 1e-6, mixed
     precision (binary32 FFT/Gamma0/polarization, binary64 residual, averages and strain), timed against
     the plain binary64 form on the same inputs; C^eff eps0 against the analytic value."""
@@ -550,7 +550,7 @@ def bench_hashin(args):
         for form in forms:
             res[form].pop("sigma_bar")
         out[name] = res
-    print(json.dumps({"workload": "hashin3d (config 3): coated ellipsoid c=(0.1,0.15,0.2), fraction 0.25, "
+    print(json.dumps({"workload": "hashin3d: coated ellipsoid c=(0.1,0.15,0.2), fraction 0.25, "
                                   "core/coating/matrix 10/1/1+rank-one, m=2^21, 6 load cases batched, tol 1e-6",
                       "metric": METRIC, "unit": "point-iterations/s", "results": out}))
 
@@ -609,7 +609,7 @@ def bench_warmstart(args):
     for prec in tot:
         for k in names:
             tot[prec][k]["s"] = round(tot[prec][k]["s"], 3)
-    print(json.dumps({"workload": "warmstart (config 5): train %d samples x %d Adam steps (lr %g) at %d^3, evaluate "
+    print(json.dumps({"workload": "warmstart: train %d samples x %d Adam steps (lr %g) at %d^3, evaluate "
                                   "%d held-out seeds at %d^3, 6 unit load cases batched, tol 1e-6"
                                   % (args.ws_samples, args.ws_steps, args.ws_lr, args.ws_train_n, args.ws_eval, n),
                       "train_s": round(t_train, 1), "train_loss_first_last": [float(np.mean(losses[:100])),
@@ -689,7 +689,7 @@ def bench_sweep(args):
         worst["strain"] = max(worst["strain"], float((o["eps"] - ref["eps"]).abs().max() / ref["eps"].abs().max()))
         worst["sigma_bar"] = max(worst["sigma_bar"], float(np.abs(o["sigma_bar"] - ref["sigma_bar"]).max()
                                                            / np.abs(ref["sigma_bar"]).max()))
-    print(json.dumps({"workload": "sweep (config 4): 256 problems, m = 2^12..2^21 (sum %d points), 2-D and 3-D, "
+    print(json.dumps({"workload": "sweep: 256 problems, m = 2^12..2^21 (sum %d points), 2-D and 3-D, "
                                   "rank-1/rank-2/diagonal, contrast 1e-2..1e2, all unit load cases, mixed, tol 1e-6"
                                   % sum(p_["plan"].m for p_ in probs),
                       "metric": METRIC, "unit": "point-iterations/s", "setup_s": round(t_setup, 1), "results": res,
@@ -823,7 +823,7 @@ def profile_case(args):
 
 
 def _oracle_proc(name, lc, iters, barrier, q):
-    """Spawned worker: build the lattice and phases of one config-3 problem, wait for the others at the
+    """Spawned worker: build the lattice and phases of one coated-ellipsoid problem (m = 2^21), wait for the others at the
     barrier, then run `iters` oracle iterations of unit load case lc (numpy float64, one thread)."""
     sys.path.insert(0, ROOT)
     from oracle import elasticity as el
@@ -856,7 +856,7 @@ ORACLE_BYTES = 3.5e9     # peak memory of one oracle solve at m = 2^21 (measured
 
 def oracle_sample(n_proc, iters):
     """n_proc spawned processes, each running `iters` oracle iterations of its own (lattice, load case) of
-    the config-3 workload at the same time; returns (point-iterations/s over the common wall time, wall
+    the coated-ellipsoid workload at the same time; returns (point-iterations/s over the common wall time, wall
     seconds).  Spawned, so no worker inherits a CUDA context."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -887,7 +887,7 @@ def cpu_baseline(seconds):
             "single_process_value": round(v1, 1),
             "host_cpus": os.cpu_count(),
             "sample": "%d processes, each %d oracle iteration(s) (numpy float64, one thread each) of one unit load "
-                      "case on one m=2^21 config-3 lattice, started together, %.1f s wall; single process: 1 "
+                      "case on one m=2^21 coated-ellipsoid lattice, started together, %.1f s wall; single process: 1 "
                       "iteration in %.1f s" % (n, iters, tn, t1)}
 
 

@@ -337,7 +337,7 @@ def test_edge_cases(cuda):
         basic_scheme_solve(P, ph, LAM2, (1.0, -1.0), np.ones((1, 3)), tol=1e-8, maxit=3)   # mu0 <= 0
 
 
-def test_aligned_laminate_config1_matches_analytic(cuda):
+def test_aligned_laminate_m4096_matches_analytic(cuda):
     # 2-D rank-1 lattice M = [[4096, 12288], [0, 1]]: all frequencies parallel to (1,3); exact laminate
     import torch
     from oracle import analytic as an
@@ -486,7 +486,7 @@ def _hashin_case(M, cuda, precision, tol, maxit):
 @pytest.mark.parametrize("M", [[[32, 0, 0], [0, 32, 0], [0, 0, 32]], [[32, 1, 0], [0, 32, 1], [0, 0, 32]],
                                [[32, 4, 0], [0, 32, 4], [0, 0, 32]]])
 def test_hashin_mixed_six_load_cases_against_oracle(cuda, M):
-    # config-3 shape at m = 32768: mixed precision, the six unit load cases in one batch, tol 1e-6
+    # the coated-ellipsoid shape at m = 32768: mixed precision, the six unit load cases in one batch, tol 1e-6
     w, P, ph, E, g = _hashin_case(M, cuda, "mixed", 1e-6, 2000)
     assert g["status"] == 0
     L = Lattice(M)
@@ -510,7 +510,7 @@ def test_hashin_mixed_six_load_cases_against_oracle(cuda, M):
 
 @pytest.mark.parametrize("name", ["grid128", "rank1_2097152", "sheared128"])
 def test_hashin_full_size_fp64_fixed_iterations(cuda, name):
-    # full config-3 size (m = 2^21), the eps0 load case, binary64, two iterations compared field-wise
+    # the full coated-ellipsoid size (m = 2^21), the eps0 load case, binary64, two iterations compared field-wise
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
     w = synth.hashin_workload()
@@ -530,7 +530,7 @@ def test_hashin_full_size_fp64_fixed_iterations(cuda, name):
 
 @pytest.mark.parametrize("name", ["grid128", "rank1_2097152"])
 def test_hashin_full_size_mixed_against_oracle(cuda, name):
-    # the mixed path at the full config-3 size: the 128^3 grid takes the four-pass column path, the rank-1
+    # the mixed path at the full coated-ellipsoid size (m = 2^21): the 128^3 grid takes the four-pass column path, the rank-1
     # lattice the two-pass four-step split of its 2^21-point axis.  Six unit load cases batched as in the
     # workload; the eps0 load case and one shear unit load case against the oracle (separable FFTs),
     # four fixed iterations, at the stated bounds
@@ -564,7 +564,7 @@ def test_hashin_full_size_mixed_against_oracle(cuda, name):
 
 @pytest.mark.parametrize("name", ["grid128", "rank1_2097152", "sheared128"])
 def test_hashin_full_size_mixed_converged_against_fp64(cuda, name):
-    # converged to r < 1e-6 at the full config-3 size: the mixed path's strain and C^eff against the binary64
+    # converged to r < 1e-6 at the full coated-ellipsoid size (m = 2^21): the mixed path's strain and C^eff against the binary64
     # path (itself held to the oracle at this size above) on the six unit load cases
     import torch
     from paper_1605_05712_gb300 import basic_scheme_solve, lattice_plan
