@@ -88,3 +88,17 @@ def test_set_cell_validates_on_the_host():
         P.set_cell([[1.0, 2.0], [0.5, 1.0]])            # singular
     with pytest.raises(LatticeError):
         P.set_cell([[float("nan"), 0.0], [0.0, 1.0]])
+
+
+def test_binding_constants_equal_the_header():
+    # every LAT_* constant the Python binding defines has the value the C header defines
+    from paper_1605_05712_gb300 import api
+    header = open(os.path.join(ROOT, "include", "lattice_ms.h")).read()
+    defs = {}
+    for name, val in re.findall(r"^#define (LAT_\w+)\s+(-?\d+)", header, flags=re.M):
+        defs[name] = int(val)
+    names = [n for n in dir(api) if n.startswith("LAT_") and isinstance(getattr(api, n), int)]
+    assert {"LAT_OK", "LAT_FP64", "LAT_SCHEME_CG", "LAT_WS_CG", "LAT_BOUNDARY_ZERO"} <= set(names)
+    for n in names:
+        assert n in defs, n
+        assert getattr(api, n) == defs[n], n
