@@ -93,6 +93,40 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _on_device(t, device):
+    """True for a contiguous tensor on the given CUDA device: the kernels receive its raw pointer, so a
+    host tensor, a tensor of another device or a strided view must not reach them."""
+    import torch
+    return isinstance(t, torch.Tensor) and t.is_cuda and t.device == device and t.is_contiguous()
+
+
+def _strain_buffer(t, name, numel, device):
+    """A caller's strain (or stress) buffer: float64, numel entries, on the solve's device."""
+    import torch
+    if not (_on_device(t, device) and t.dtype == torch.float64 and t.numel() == numel):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor of %d entries on %s" % (name, numel, device))
+    return t
+
+
+def _fill_start(eps, eps0, numel):
+    """Copy a warm start (any device, float64, numel entries) into the solve's strain buffer."""
+    import torch
+    if not (isinstance(eps0, torch.Tensor) and eps0.dtype == torch.float64 and eps0.numel() == numel):
+        raise TypeError("eps0 must be a float64 tensor of %d entries (n_loads, n_c, m)" % numel)
+    eps.view(-1).copy_(eps0.reshape(-1))
+
+
+def _workspace(t, nbytes, device):
+    """The caller's workspace (a contiguous CUDA tensor on the solve's device, any dtype) or a new uint8
+    one of nbytes; returns the tensor and its size in bytes (the library checks that it suffices)."""
+    import torch
+    if t is None:
+        t = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    elif not _on_device(t, device):
+        raise TypeError("workspace must be a contiguous CUDA tensor on %s" % device)
+    return t, t.numel() * t.element_size()
+
+
 class LatticePlan:
     """Plan for the pattern P(M) of a regular integer matrix M (d = 2 or 3)."""
 
@@ -209,8 +243,8 @@ def lattice_plan(M):
 def lattice_fft(plan, x, inverse=False, stream=None):
     """Pattern DFT F(M) (forward, with 1/m) or its inverse of complex128 CUDA data (n_fields, m)."""
     import torch
-    if x.dtype != torch.complex128 or not x.is_cuda:
-        raise TypeError("x must be a complex128 CUDA tensor")
+    if x.dtype != torch.complex128 or not x.is_cuda or x.numel() == 0 or x.numel() % plan.m:
+        raise TypeError("x must be a complex128 CUDA tensor of n_fields x m entries")
     x = x.contiguous()
     n_f = x.numel() // plan.m
     out = torch.empty_like(x)
@@ -239,7 +273,11 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     stiffness  (n_phases, 6, 6) Voigt matrices (host)
     C0         (lam0, mu0)
     E          (n_loads, n_c) tensor components (host)
-    eps0       optional CUDA float64 tensor (n_loads, n_c, m): warm start
+    eps0       optional float64 tensor of n_loads x n_c x m entries (n_loads, n_c, m): warm start, copied
+               into the strain buffer (any device, any strides)
+    eps_out    optional strain buffer: a contiguous float64 CUDA tensor of n_loads x n_c x m entries on
+               the phase field's device (refused otherwise: the kernels get its raw pointer)
+    workspace  optional contiguous CUDA tensor on the same device, any dtype (its size in bytes counts)
     """
     import torch
     stiff, stiff_p = _f64(np.asarray(stiffness, dtype=np.float64).reshape(-1, 36))
@@ -253,17 +291,16 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
     dev = phase.device
+    numel = n_loads * plan.n_c * plan.m
     if eps_out is not None:
-        eps = eps_out
-    elif eps0 is not None:
-        eps = eps0.clone()
+        eps = _strain_buffer(eps_out, "eps_out", numel, dev)
     else:
         eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=dev)
-    if eps0 is not None and eps_out is not None:
-        eps.copy_(eps0)
+    if eps0 is not None:
+        _fill_start(eps, eps0, numel)
     sigma = torch.empty_like(eps) if want_sigma else None
     wsb = plan.workspace_bytes(n_loads, prec | (LAT_WS_CG if scheme == "cg" else 0))
-    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws, wsn = _workspace(workspace, wsb, dev)
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
     resid = np.zeros(n_loads)
@@ -277,7 +314,7 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
         ctypes.byref(opts), ctypes.c_void_p(eps.data_ptr()),
         ctypes.c_void_p(sigma.data_ptr()) if sigma is not None else None,
         sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-        resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), wsn,
         _stream(stream))
     _check(rc)
     out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
@@ -315,16 +352,19 @@ def basic_scheme_solve_field(plan, field, C0, E, tol=1e-8, maxit=1000, precision
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     dev = field.device
-    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
-                                                          device=dev)
+    numel = n_loads * plan.n_c * plan.m
+    if eps_out is not None:
+        eps = _strain_buffer(eps_out, "eps_out", numel, dev)
+    else:
+        eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=dev)
     if eps0 is not None:
-        eps.copy_(eps0)
+        _fill_start(eps, eps0, numel)
     sigma = torch.empty_like(eps) if want_sigma else None
     L = lib()
     L.lattice_field_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.lattice_field_workspace_bytes.restype = ctypes.c_size_t
     wsb = int(L.lattice_field_workspace_bytes(plan.handle, n_loads, prec))
-    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws, wsn = _workspace(workspace, wsb, dev)
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
     resid = np.zeros(n_loads)
@@ -343,7 +383,7 @@ def basic_scheme_solve_field(plan, field, C0, E, tol=1e-8, maxit=1000, precision
     rc = f(plan.handle, vp(field.data_ptr()), C0p, Ep, n_loads, float(tol), int(maxit), ctypes.byref(opts),
            vp(eps.data_ptr()), vp(sigma.data_ptr()) if sigma is not None else None,
            sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), vp(ws.data_ptr()), ws.numel(), _stream(stream))
+           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), vp(ws.data_ptr()), wsn, _stream(stream))
     _check(rc)
     out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
     if history:
@@ -369,13 +409,16 @@ def basic_scheme_solve_async(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000
     if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
     dev = phase.device
-    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
-                                                          device=dev)
+    numel = n_loads * plan.n_c * plan.m
+    if eps_out is not None:
+        eps = _strain_buffer(eps_out, "eps_out", numel, dev)
+    else:
+        eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=dev)
     if eps0 is not None:
-        eps.copy_(eps0)
+        _fill_start(eps, eps0, numel)
     sigma = torch.empty_like(eps) if want_sigma else None
     wsb = plan.workspace_bytes(n_loads, prec | (LAT_WS_CG if scheme == "cg" else 0))
-    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws, wsn = _workspace(workspace, wsb, dev)
     sbar = torch.empty((n_loads, plan.n_c), dtype=torch.float64, device=dev)
     iters = torch.empty(n_loads, dtype=torch.int32, device=dev)
     resid = torch.empty(n_loads, dtype=torch.float64, device=dev)
@@ -391,7 +434,7 @@ def basic_scheme_solve_async(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000
     rc = f(plan.handle, vp(phase.data_ptr()), n_ph, stiff_p, C0p, Ep, n_loads, float(tol), int(maxit),
            ctypes.byref(opts), vp(eps.data_ptr()), vp(sigma.data_ptr()) if sigma is not None else None,
            vp(sbar.data_ptr()), vp(iters.data_ptr()), vp(resid.data_ptr()), vp(status.data_ptr()),
-           vp(ws.data_ptr()), ws.numel(), _stream(stream))
+           vp(ws.data_ptr()), wsn, _stream(stream))
     _check(rc)
     # the tensors the enqueued work reads or writes are returned so that they outlive it
     return dict(eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid, status=status, workspace=ws)
@@ -441,8 +484,10 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
-    eps = eps_out if eps_out is not None else torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64,
-                                                          device=phase.device)
+    if eps_out is not None:
+        eps = _strain_buffer(eps_out, "eps_out", n_loads * plan.n_c * plan.m, phase.device)
+    else:
+        eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
     sigma = torch.empty_like(eps) if want_sigma else None
     sbar = np.zeros((n_loads, plan.n_c))
     iters = np.zeros(n_loads, dtype=np.int32)
@@ -486,15 +531,21 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     n = len(phases)
     Es = np.asarray(Es, dtype=np.float64).reshape(n, plan.n_c)
     dev = phases[0].device
-    eps = eps_out if eps_out is not None else torch.empty((n, plan.n_c, plan.m), dtype=torch.float64, device=dev)
+    if eps_out is not None:
+        eps = _strain_buffer(eps_out, "eps_out", n * plan.n_c * plan.m, dev)
+    else:
+        eps = torch.empty((n, plan.n_c, plan.m), dtype=torch.float64, device=dev)
     sigma = torch.empty_like(eps) if want_sigma else None
+    eps_i = eps.view(n, plan.n_c, plan.m)
+    sigma_i = sigma.view(n, plan.n_c, plan.m) if sigma is not None else None
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
     keep = []
     items = (_BatchItem * n)()
     for i in range(n):
-        if phases[i].dtype != torch.uint8 or not phases[i].is_cuda or phases[i].numel() != plan.m:
-            raise TypeError("phase %d must be a uint8 CUDA tensor with m entries" % i)
+        if phases[i].dtype != torch.uint8 or not phases[i].is_cuda or phases[i].numel() != plan.m or \
+                phases[i].device != dev:
+            raise TypeError("phase %d must be a uint8 CUDA tensor with m entries on %s" % (i, dev))
         st_i, st_p = _f64(np.asarray(stiffnesses[i], dtype=np.float64).reshape(-1, 36))
         e_i, e_p = _f64(Es[i])
         keep += [st_i, e_i]
@@ -504,13 +555,13 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
         it.stiffness = st_p
         it.C0[0], it.C0[1] = float(C0s[i][0]), float(C0s[i][1])
         it.E = e_p
-        it.eps = eps[i].data_ptr()
-        it.sigma = sigma[i].data_ptr() if sigma is not None else None
+        it.eps = eps_i[i].data_ptr()
+        it.sigma = sigma_i[i].data_ptr() if sigma is not None else None
     L = lib()
     L.lattice_batch_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.lattice_batch_workspace_bytes.restype = ctypes.c_size_t
     wsb = int(L.lattice_batch_workspace_bytes(plan.handle, n, prec | (LAT_WS_CG if scheme == "cg" else 0)))
-    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws, wsn = _workspace(workspace, wsb, dev)
     sbar = np.zeros((n, plan.n_c))
     iters = np.zeros(n, dtype=np.int32)
     resid = np.zeros(n)
@@ -525,7 +576,7 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     f.restype = ctypes.c_int
     rc = f(plan.handle, items, n, float(tol), int(maxit), ctypes.byref(opts),
            sbar.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(ws.data_ptr()), wsn,
            _stream(stream))
     _check(rc)
     out = dict(status=rc, eps=eps, sigma=sigma, sigma_bar=sbar, iters=iters, resid=resid)
@@ -561,12 +612,16 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     keep, outs = [], []
     for i, pb in enumerate(problems):
         plan, phase = pb["plan"], pb["phase"]
-        if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
-            raise TypeError("problem %d: phase must be a uint8 CUDA tensor with m entries" % i)
+        if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m or \
+                phase.device != problems[0]["phase"].device:
+            raise TypeError("problem %d: phase must be a uint8 CUDA tensor with m entries on the device of "
+                            "problem 0" % i)
         E = np.asarray(pb["E"], dtype=np.float64).reshape(-1, plan.n_c)
         nl = E.shape[0]
         eps = pb.get("eps")
-        if eps is None:
+        if eps is not None:
+            _strain_buffer(eps, "problem %d: eps" % i, nl * plan.n_c * plan.m, phase.device)
+        else:
             if warm_start:
                 raise ValueError("problem %d: warm_start needs eps" % i)
             eps = torch.empty((nl, plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
@@ -597,14 +652,14 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     if wsb == 0:
         raise LatticeError(LAT_ERR_ARG, "lattice_multi_workspace_bytes: invalid items")
     dev = problems[0]["phase"].device
-    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws, wsn = _workspace(workspace, wsb, dev)
     opts = _Opts(prec, bnd, 1 if warm_start else 0, None, 1 if mixed_increment else 0, 0 if mixed_restart else -1,
                  1 if plain_launches else 0, _SCHEMES[scheme])
     f = L.basic_scheme_solve_multi
     f.argtypes = [ctypes.POINTER(_MultiItem), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Opts),
                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     f.restype = ctypes.c_int
-    rc = f(items, n, float(tol), int(maxit), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+    rc = f(items, n, float(tol), int(maxit), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), wsn,
            _stream(stream))
     _check(rc)
     return rc, outs
@@ -645,8 +700,10 @@ def gather(x, index_map, stream=None):
     """out[..., s] = x[..., index_map[s]] on the GPU (lattice_gather): fields (..., m_src) on P(src)
     sampled onto P(dst).  x a contiguous CUDA tensor, index_map a CUDA int32 tensor from gather_map."""
     import torch
-    if not (x.is_cuda and index_map.is_cuda and index_map.dtype == torch.int32 and x.is_contiguous()):
-        raise TypeError("gather: x must be a contiguous CUDA tensor and index_map a CUDA int32 tensor")
+    if not (x.is_cuda and index_map.is_cuda and index_map.dtype == torch.int32 and x.is_contiguous()
+            and index_map.is_contiguous() and index_map.device == x.device):
+        raise TypeError("gather: x must be a contiguous CUDA tensor and index_map a contiguous CUDA int32 tensor "
+                        "on the same device")
     lead = tuple(x.shape[:-1])
     n_f = int(np.prod(lead)) if lead else 1
     n = index_map.numel()
