@@ -102,8 +102,21 @@ class WarmStartNet:
         w = self.work(n)
         return ctypes.c_void_p(w.data_ptr()), w.numel()
 
+    def _arg(self, t, name, dtype, numel=None, per=None):
+        """A device argument of the network's kernels: contiguous, on the parameters' device, of the given
+        type and number of entries (numel, or a positive multiple of per); the kernels get its raw pointer."""
+        import torch
+        ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.pbuf.device and t.is_contiguous()
+              and t.dtype == dtype and (numel is None or t.numel() == numel)
+              and (per is None or (t.numel() > 0 and t.numel() % per == 0)))
+        if not ok:
+            raise TypeError("%s must be a contiguous %s CUDA tensor on %s%s" % (
+                name, dtype, self.pbuf.device, "" if numel is None else " with %d entries" % numel))
+        return t
+
     def features(self, phase, table, n):
         import torch
+        self._arg(phase, "phase", torch.uint8, n ** 3)
         tab = torch.from_numpy(np.ascontiguousarray(table, dtype=np.float32).reshape(-1)).to(self.device)
         w, nb = self._w(n)
         _check(self.L.lat_wsnet_features(ctypes.c_void_p(phase.data_ptr()), ctypes.c_void_p(tab.data_ptr()), n, w, nb,
@@ -118,12 +131,17 @@ class WarmStartNet:
         return y
 
     def backward(self, n, dy):
+        import torch
         w, nb = self._w(n)
-        dy = dy.contiguous()
+        dy = self._arg(dy.contiguous(), "dy", torch.float32, 36 * n ** 3)
         _check(self.L.lat_wsnet_backward(ctypes.c_void_p(self.pbuf.data_ptr()), n, ctypes.c_void_p(dy.data_ptr()), w,
                                          nb, _stream(None)))
 
     def train_step(self, phase, table_dev, eps_unit, n, lr):
+        import torch
+        self._arg(phase, "phase", torch.uint8, n ** 3)
+        self._arg(table_dev, "table_dev", torch.float32, per=21)
+        self._arg(eps_unit, "eps_unit", torch.float64, 36 * n ** 3)
         self.step_count += 1
         loss = ctypes.c_double()
         w, nb = self._w(n)
@@ -147,6 +165,8 @@ class WarmStartNet:
 
     def predict(self, phase, table_dev, n, E):
         import torch
+        self._arg(phase, "phase", torch.uint8, n ** 3)
+        self._arg(table_dev, "table_dev", torch.float32, per=21)
         E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 6))
         eps0 = torch.empty((E.shape[0], 6, n ** 3), dtype=torch.float64, device=self.device)
         w, nb = self._w(n)
@@ -226,7 +246,12 @@ def filter_rho(stiffness, C0):
 
 def start_filter(out, eps_g2, eps0, rho):
     """out = (G^2(eps0) - rho^2 eps0) / (1 - rho^2) on device binary64 tensors of equal size (C-ABI kernel)."""
-    assert out.numel() == eps_g2.numel() == eps0.numel() and out.dtype == eps0.dtype == eps_g2.dtype
+    import torch
+    for name, t in (("out", out), ("eps_g2", eps_g2), ("eps0", eps0)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == out.device and t.is_contiguous()
+                and t.dtype == torch.float64 and t.numel() == out.numel()):
+            raise TypeError("start_filter: %s must be a contiguous float64 CUDA tensor of %d entries on %s"
+                            % (name, out.numel(), out.device))
     _check(_L().lattice_start_filter(ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(eps_g2.data_ptr()),
                                      ctypes.c_void_p(eps0.data_ptr()), float(rho), out.numel(), _stream(None)))
     return out
@@ -244,6 +269,8 @@ def solve_filtered(plan, phase, stiffness, C0, E, tol=1e-6, maxit=5000, precisio
     if eps0 is None:
         m = int(phase.numel())
         eps0 = torch.from_numpy(E).to(phase.device)[:, :, None].expand(E.shape[0], 6, m).contiguous()
+    else:
+        eps0 = eps0.to(device=phase.device, dtype=torch.float64).contiguous()
     g2 = basic_scheme_solve(plan, phase, stiffness, C0, E, tol=0.0, maxit=2, precision=precision, eps0=eps0)["eps"]
     start = start_filter(g2, g2, eps0, rho)
     out = basic_scheme_solve(plan, phase, stiffness, C0, E, tol=tol, maxit=maxit, precision=precision, eps0=start,

@@ -41,3 +41,10 @@ def test_buffer_checks():
     for bad in (torch.randn(1, 3, 10, dtype=torch.float64), torch.randn(2, 3, 10, dtype=torch.float32)):
         with pytest.raises(TypeError):
             api._fill_start(eps, bad, 60)
+
+
+def test_start_filter_refuses_host_tensors():
+    from paper_1605_05712_gb300.warmstart import start_filter
+    a = torch.zeros(2, 3, 5, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        start_filter(a, a, a, 0.5)
