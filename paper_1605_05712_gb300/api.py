@@ -449,6 +449,8 @@ def lattice_pass_times(plan, phase, stiffness, C0, E, precision="fp64", n_reps=2
     Ea, Ep = _f64(np.asarray(E, dtype=np.float64).reshape(-1, plan.n_c))
     n_loads = Ea.shape[0]
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
+    if phase.dtype != torch.uint8 or not phase.is_cuda or not phase.is_contiguous() or phase.numel() != plan.m:
+        raise TypeError("phase must be a contiguous uint8 CUDA tensor with m entries")
     eps = torch.empty((n_loads, plan.n_c, plan.m), dtype=torch.float64, device=phase.device)
     ws = torch.empty(plan.workspace_bytes(n_loads, prec), dtype=torch.uint8, device=phase.device)
     ms = (ctypes.c_float * 8)()
