@@ -288,7 +288,7 @@ def basic_scheme_solve(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000, prec
     Ea, Ep = _f64(E)
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
-    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+    if phase.dtype != torch.uint8 or not phase.is_cuda or not phase.is_contiguous() or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
     dev = phase.device
     numel = n_loads * plan.n_c * plan.m
@@ -406,7 +406,7 @@ def basic_scheme_solve_async(plan, phase, stiffness, C0, E, tol=1e-8, maxit=1000
     Ea, Ep = _f64(E)
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
-    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+    if phase.dtype != torch.uint8 or not phase.is_cuda or not phase.is_contiguous() or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
     dev = phase.device
     numel = n_loads * plan.n_c * plan.m
@@ -484,7 +484,7 @@ def basic_scheme_solve_noalloc(plan, phase, stiffness, C0, E, tol=1e-8, maxit=10
     Ea, Ep = _f64(E)
     prec = {"fp64": LAT_FP64, "mixed": LAT_MIXED, "df64": LAT_DF64}[precision]
     bnd = {"average": LAT_BOUNDARY_AVERAGE, "zero": LAT_BOUNDARY_ZERO}[boundary]
-    if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m:
+    if phase.dtype != torch.uint8 or not phase.is_cuda or not phase.is_contiguous() or phase.numel() != plan.m:
         raise TypeError("phase must be a uint8 CUDA tensor with m entries")
     if eps_out is not None:
         eps = _strain_buffer(eps_out, "eps_out", n_loads * plan.n_c * plan.m, phase.device)
@@ -545,8 +545,8 @@ def basic_scheme_solve_batch(plan, phases, stiffnesses, C0s, Es, tol=1e-8, maxit
     keep = []
     items = (_BatchItem * n)()
     for i in range(n):
-        if phases[i].dtype != torch.uint8 or not phases[i].is_cuda or phases[i].numel() != plan.m or \
-                phases[i].device != dev:
+        if phases[i].dtype != torch.uint8 or not phases[i].is_cuda or not phases[i].is_contiguous() or \
+                phases[i].numel() != plan.m or phases[i].device != dev:
             raise TypeError("phase %d must be a uint8 CUDA tensor with m entries on %s" % (i, dev))
         st_i, st_p = _f64(np.asarray(stiffnesses[i], dtype=np.float64).reshape(-1, 36))
         e_i, e_p = _f64(Es[i])
@@ -614,8 +614,8 @@ def basic_scheme_solve_multi(problems, tol=1e-8, maxit=1000, precision="fp64", b
     keep, outs = [], []
     for i, pb in enumerate(problems):
         plan, phase = pb["plan"], pb["phase"]
-        if phase.dtype != torch.uint8 or not phase.is_cuda or phase.numel() != plan.m or \
-                phase.device != problems[0]["phase"].device:
+        if phase.dtype != torch.uint8 or not phase.is_cuda or not phase.is_contiguous() or \
+                phase.numel() != plan.m or phase.device != problems[0]["phase"].device:
             raise TypeError("problem %d: phase must be a uint8 CUDA tensor with m entries on the device of "
                             "problem 0" % i)
         E = np.asarray(pb["E"], dtype=np.float64).reshape(-1, plan.n_c)
